@@ -617,7 +617,7 @@ int orc_atom_descriptors_fast(const orc_params* p, const double* Q, int n, const
   orc_geom g;
   orc_geom_init(&g, p, Q, n, d);
   orc_mono mo;
-  orc_mono_init(&mo, orc_max_degree(p));
+  orc_mono_init(&mo, imax(0, orc_max_degree(p)));  /* D2 = B_m00 needs degree 0 */
   const int K = g.K, NA = mo.NA;
   double* B = (double*)malloc(sizeof(double) * K * NA);
   orc_atomic_basis(&g, &mo, B);
@@ -703,7 +703,7 @@ double orc_atom_energy_grad_fast(const orc_params* p, const double* Q, const dou
   orc_geom g;
   orc_geom_init(&g, p, Q, n, d);
   orc_mono mo;
-  orc_mono_init(&mo, orc_max_degree(p));
+  orc_mono_init(&mo, imax(0, orc_max_degree(p)));  /* D2 = B_m00 needs degree 0 */
   const int K = g.K, NA = mo.NA;
   double* B = (double*)malloc(sizeof(double) * K * NA);
   double* G = (double*)malloc(sizeof(double) * K * NA);
@@ -722,7 +722,7 @@ int orc_atom_dD_fast(const orc_params* p, const double* Q, int n, const double* 
   orc_geom g;
   orc_geom_init(&g, p, Q, n, d);
   orc_mono mo;
-  orc_mono_init(&mo, orc_max_degree(p));
+  orc_mono_init(&mo, imax(0, orc_max_degree(p)));  /* D2 = B_m00 needs degree 0 */
   const int K = g.K, NA = mo.NA;
   const int M = orc_num_descriptors(p);
   double* B = (double*)malloc(sizeof(double) * K * NA);
