@@ -1,0 +1,466 @@
+#!/usr/bin/env python3
+"""Benchmark: energy + forces (+ virial) of the linear fast-POD potential.
+
+Workload (default): 8,192-atom BCC Ta (16^3 cubic cells, a = 3.316 A, +-3 %
+isotropic strain, jitter N(0, 0.1 A)), r_in = 1, r_cut = 5 A, Ns = 8 snapshots
+-> K = 6 radial modes, angular degree 4, 2/3/4-body descriptors (M = 103),
+coefficients c ~ N(0, 0.01^2).  Synthetic inputs stand in for the tantalum
+training data of the paper.
+
+A step is one full evaluation: neighbour list (cell binning, search, sort,
+reverse index), fused atom kernel (radial basis, atomic basis, contraction,
+energy, adjoint, pair gradients), force gather + per-atom virial, FP64 energy
+and virial reductions.  Metric: atom-steps/s (atoms x steps / device seconds).
+
+Timing: W warm-up steps; the step is captured once in a CUDA graph; each of the
+K timed steps is preceded by an L2 flush (a 512 MB write) outside its CUDA-event
+pair; value = atoms * K / sum of the K step times, max over ranks.  The fused
+atom kernel is timed separately with CUDA events recorded by the library on the
+launching stream around that kernel (roofline).  ``e2e`` goes through the
+host-buffer entry point with pinned host memory (positions and coefficients in,
+energy, atom energies, forces and virial out, copies inside the timed region).
+
+Multi-GPU (torchrun): every rank evaluates its own independent configuration
+(weak scaling, no collective on the data path); rank 0 prints the JSON line.
+
+``--impl reference`` times the FP64 CPU oracle (the only reference this method
+has: the paper publishes no code) on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import synth  # noqa: E402
+
+FP32_LANES_PER_SM = 128
+N_SM = 152
+SM_MAX_MHZ = 2070.0
+
+
+# ------------------------------------------------------------ flop model
+def monomials(P):
+    out = []
+    for n in range(P + 1):
+        for a in range(n, -1, -1):
+            for b in range(n - a, -1, -1):
+                out.append((a, b, n - a - b))
+    return out
+
+
+def algorithmic_flops_per_atom(params, n_pairs_per_atom):
+    """Arithmetic the method needs per atom for energy + forces, counted from
+    the formulation (not from the kernel's instruction mix):
+      per pair  snapshots -> R, R' projection      4 Ns K
+                angular monomials (degree >= 2)     N_a - 4
+                B += R A                            2 K N_a
+                adjoint: u_m = a_m . A, e = a^T R   4 K N_a
+                R' . u                              2 K
+                grad of sum_x e_x A_x               2 * #(x, d : e_d(x) > 0)
+                tangential projection and output    15
+      per atom  three-body sums of squares          2 N_a K
+                four-body cubic adjoint             7 * merged triple terms * K
+                energy and adjoint bookkeeping      4 N_a K
+    Transcendentals (about 5 per pair) are not counted."""
+    Ns, K, Pa = params.Ns, params.Kr, params.Pa
+    mons = monomials(Pa)
+    NA = len(mons)
+    ngrad = sum(1 for e in mons for d in range(3) if e[d] > 0)
+    pair = 4 * Ns * K + (NA - 4) + 2 * K * NA + 4 * K * NA + 2 * K + 2 * ngrad + 15
+    nterms = four_body_terms(params.P4)
+    atom = 2 * NA * K + 7 * nterms * K + 4 * NA * K
+    return n_pairs_per_atom * pair + atom
+
+
+def four_body_terms(P4):
+    if P4 < 0:
+        return 0
+    mons = monomials(P4)
+    index = {e: i for i, e in enumerate(mons)}
+    total = 0
+    for n in range(P4 + 1):
+        for a in range(n, -1, -1):
+            for b in range(min(a, n - a), -1, -1):
+                c = n - a - b
+                if not (0 <= c <= b) or (b == 0 and c == 0):
+                    continue
+                keys = set()
+                for q in (e for e in mons if sum(e) == a):
+                    for s in (e for e in mons if sum(e) == b):
+                        for t in (e for e in mons if sum(e) == c):
+                            k = tuple(sorted((index[tuple(q[i] + s[i] for i in range(3))],
+                                              index[tuple(q[i] + t[i] for i in range(3))],
+                                              index[tuple(s[i] + t[i] for i in range(3))])))
+                            keys.add(k)
+                total += len(keys)
+    return total
+
+
+# ------------------------------------------------------------ clocks
+class ClockSampler:
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax = float(parts[2])
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------ workloads
+def workload(name, replica):
+    if name == "full":
+        return synth.params_full(), synth.config_full(replica), "bcc_ta_8192_K6_P4_4body"
+    if name == "md":
+        return synth.params_full(), synth.config_md(replica), "bcc_ta_1024000_K6_P4_4body"
+    if name == "small":
+        return synth.params_small(), synth.config_small(replica), "bcc_ta_128_K3_P3"
+    if name == "fig4":
+        return synth.params_full(), synth.config_full(replica, ncell=20), "bcc_ta_16000_K6_P4_4body"
+    raise ValueError(name)
+
+
+# ------------------------------------------------------------ CPU baseline
+def oracle_sample(params, cfg, c, budget_s, max_atoms=None):
+    """Time the FP64 oracle (brute-force neighbour list + atom-density energy and
+    pair gradients, one host core) on a prefix sample of atoms."""
+    import oracle
+    orc = oracle.Oracle(params)
+    sysd = orc._system(cfg)
+    t0 = time.perf_counter()
+    n = 0
+    while True:
+        i = (n * 7919) % cfg.n
+        _, _, d = orc.neighbors(cfg, i, sysd)
+        orc.atom_energy_grad(d, c)
+        n += 1
+        el = time.perf_counter() - t0
+        if el >= budget_s or (max_atoms and n >= max_atoms):
+            break
+    return n, el
+
+
+# ------------------------------------------------------------ main
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="full", choices=["full", "md", "small", "fig4"])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--cpu-budget", type=float, default=12.0)
+    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64-path comparison line items")
+    args = ap.parse_args()
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import torch
+    import paper_2212_14446_gb300 as pkg
+    from paper_2212_14446_gb300 import build as pbuild
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if rank == 0 or world == 1:
+        pbuild.build()
+    if dist:
+        dist.barrier()
+    dev = torch.device("cuda", local)
+    params, cfg, wname = workload(args.workload, replica=rank)
+    N = cfg.n
+    pod = pkg.POD(params, precision=args.precision)
+    c = torch.tensor(synth.coefficients(pod.M, 2001 + rank), dtype=torch.float64, device=dev)
+    pos = torch.tensor(np.ascontiguousarray(cfg.pos.T), dtype=torch.float64, device=dev)
+    box = cfg.box
+    E = torch.empty(1, dtype=torch.float64, device=dev)
+    Ei = torch.empty(N, dtype=torch.float64, device=dev)
+    F = torch.empty((3, N), dtype=torch.float64, device=dev)
+    W = torch.empty(9, dtype=torch.float64, device=dev)
+    sysd = pod.system(pos, box)
+    stream = torch.cuda.Stream(device=dev)
+
+    def step():
+        pkg.pod_energy_forces(pod.h, sysd, c, E, Ei, F, W, stream=stream)
+
+    # warm-up (synchronous status checks; sizes the workspace)
+    with torch.cuda.stream(stream):
+        for _ in range(max(args.warmup, 3)):
+            step()
+    torch.cuda.synchronize()
+    # capture one step in a CUDA graph (asynchronous mode: no host sync inside)
+    pod.set_sync(False)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=stream):
+        step()
+    torch.cuda.synchronize()
+    pkg.pod_status(pod.h, stream)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t_wall0 = time.perf_counter()
+    with torch.cuda.stream(stream):
+        for k in range(args.steps):
+            flush.fill_(float(k))
+            starts[k].record(stream)
+            graph.replay()
+            ends[k].record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    t_wall = time.perf_counter() - t_wall0
+    clk = clocks.stop()
+    st = pkg.pod_status(pod.h, stream)
+    if st != pkg.POD_OK:
+        raise pkg.PodError(st, pkg.pod_last_error(pod.h))
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    tot_ms = sum(step_ms)
+    if dist:
+        t = torch.tensor([tot_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        tot_ms = t.item()
+    value = N * world * args.steps / (tot_ms / 1e3)
+
+    # per-kernel timing of the same step (library-recorded CUDA events on the stream)
+    pod.set_sync(True)
+    pod.set_timing(True)
+    pod.timing()
+    with torch.cuda.stream(stream):
+        for k in range(args.steps):
+            flush.fill_(float(k))
+            step()
+    torch.cuda.synchronize()
+    phase_ms, calls = pod.timing()
+    pod.set_timing(False)
+    phase_avg = [x / calls for x in phase_ms]
+    count = pkg.POD(params, precision=args.precision).neighbors(pos, box, cap=96)[0]
+    n_pairs = float(count.double().mean().item())
+    fl_atom = algorithmic_flops_per_atom(params, n_pairs)
+    atom_ms = phase_avg[1]
+    achieved_tflops = fl_atom * N / (atom_ms / 1e3) / 1e12
+    peak_tflops = N_SM * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    if args.precision == "fp64":
+        peak_tflops = 1.25  # nominal GB300 FP64 (vector and tensor), no measured figure
+    prof_path = os.path.join(ROOT, "profiles", "traffic_atom_kernel.json")
+    traffic = None
+    if os.path.exists(prof_path):
+        try:
+            with open(prof_path) as f:
+                tj = json.load(f)
+            if tj.get("workload") == wname and tj.get("precision") == args.precision and \
+                    tj.get("kernel_rev") == kernel_revision():
+                traffic = tj.get("dram_bytes_per_launch")
+        except (OSError, ValueError):
+            traffic = None
+
+    # FP64 path on the same workload for the mixed-vs-FP64 comparison
+    fp64 = None
+    if args.precision == "mixed" and not args.no_fp64 and args.workload != "md":
+        pod64 = pkg.POD(params, precision="fp64", Q=pod.Q)
+        with torch.cuda.stream(stream):
+            for _ in range(3):
+                pkg.pod_energy_forces(pod64.h, sysd, c, E, Ei, F, W, stream=stream)
+        torch.cuda.synchronize()
+        E64, F64 = E.clone(), F.clone()
+        k64 = max(3, min(args.steps, 10))
+        s64 = [torch.cuda.Event(enable_timing=True) for _ in range(k64)]
+        e64 = [torch.cuda.Event(enable_timing=True) for _ in range(k64)]
+        with torch.cuda.stream(stream):
+            for k in range(k64):
+                flush.fill_(float(k))
+                s64[k].record(stream)
+                pkg.pod_energy_forces(pod64.h, sysd, c, E, Ei, F, W, stream=stream)
+                e64[k].record(stream)
+        torch.cuda.synchronize()
+        ms64 = sum(s.elapsed_time(e) for s, e in zip(s64, e64))
+        with torch.cuda.stream(stream):
+            pkg.pod_energy_forces(pod.h, sysd, c, E, Ei, F, W, stream=stream)
+        torch.cuda.synchronize()
+        fp64 = {"value": N * k64 / (ms64 / 1e3), "unit": "atom-steps/s",
+                "speedup_mixed_vs_fp64": value / (N * world * k64 / (ms64 / 1e3)) / world,
+                "mixed_vs_fp64_force_maxabs_eV_per_A": float((F - F64).abs().max().item()),
+                "mixed_vs_fp64_energy_rel": float(abs(E.item() - E64.item()) / max(abs(E64.item()), 1e-300))}
+
+    # end to end through the host-buffer entry point (pinned memory)
+    pos_h = torch.tensor(np.ascontiguousarray(cfg.pos.T), dtype=torch.float64).pin_memory().numpy()
+    c_h = c.cpu().pin_memory().numpy()
+    Eh = torch.zeros(1, dtype=torch.float64).pin_memory().numpy()
+    Eih = torch.zeros(N, dtype=torch.float64).pin_memory().numpy()
+    Fh = torch.zeros((3, N), dtype=torch.float64).pin_memory().numpy()
+    Wh = torch.zeros(9, dtype=torch.float64).pin_memory().numpy()
+    import ctypes as C
+    hsys = pkg.make_system(pos_h.ctypes.data_as(C.POINTER(C.c_double)), N, box)
+    for _ in range(3):
+        pkg.pod_energy_forces_host(pod.h, hsys, c_h, Eh, Eih, Fh, Wh, stream=stream)
+    if dist:
+        dist.barrier()
+    te0 = time.perf_counter()
+    for k in range(args.steps):
+        pkg.pod_energy_forces_host(pod.h, hsys, c_h, Eh, Eih, Fh, Wh, stream=stream)
+    te = time.perf_counter() - te0
+    if dist:
+        t = torch.tensor([te], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        te = t.item()
+    e2e = {"value": N * world * args.steps / te, "unit": "atom-steps/s",
+           "h2d_bytes_per_step": int(pos_h.nbytes + c_h.nbytes),
+           "d2h_bytes_per_step": int(Eh.nbytes + Eih.nbytes + Fh.nbytes + Wh.nbytes)}
+
+    cpu = None
+    if rank == 0:
+        nsamp, el = oracle_sample(params, cfg, c.cpu().numpy(), args.cpu_budget)
+        cpu = {"value": nsamp / el, "unit": "atom-steps/s", "cores": 1, "kind": "oracle",
+               "sample": f"{nsamp} atoms of the same configuration: brute-force neighbour list + "
+                         f"atom-density energy and pair gradients in FP64, {el:.1f} s on one host core"}
+
+    if rank == 0:
+        line = {
+            "metric": "atom-steps/s (E+F) mixed vs FP64 at stated force error; % of roofline",
+            "value": value, "unit": "atom-steps/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32" if args.precision == "mixed" else "f64",
+            "data": "synthetic",
+            "config": {"workload": wname, "atoms_per_gpu": N, "global_atoms": N * world,
+                       "pairs_per_atom": n_pairs, "descriptors": pod.M, "precision": args.precision,
+                       "neighbor_rebuild": "every step", "l2": "flushed (512 MB write) before each step",
+                       "graph": "one CUDA graph per step", "parallelism": f"replicas x{world}"},
+            "roofline": {"bound": "alu", "kernel": "atom_kernel (fused radial/B/contraction/adjoint)",
+                         "achieved": achieved_tflops, "peak": peak_tflops, "unit": "TFLOP/s",
+                         "frac": achieved_tflops / peak_tflops, "traffic": traffic,
+                         "flops_per_atom": fl_atom, "atom_kernel_ms": atom_ms,
+                         "peak_basis": ("152 SMs x 128 FP32 lanes x 2 x 2070 MHz (nominal max clock)"
+                                        if args.precision == "mixed" else "nominal FP64 1.25 TFLOP/s")},
+            "phases_ms": {"neighbors": phase_avg[0], "atom": phase_avg[1], "gather": phase_avg[2],
+                          "reduce": phase_avg[3]},
+            "gpu_launches": 6 * args.steps,
+            "e2e": e2e,
+            "cpu_baseline": cpu,
+            "fp64_path": fp64,
+            "clocks": clk,
+            "wall_s": t_wall,
+        }
+        print(json.dumps(line))
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def kernel_revision():
+    """Hash of the CUDA sources (a traffic figure is only valid for the kernel it was taken on)."""
+    import hashlib
+    h = hashlib.sha1()
+    d = os.path.join(ROOT, "paper_2212_14446_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        if f.endswith((".cu", ".cuh", ".h")):
+            with open(os.path.join(d, f), "rb") as fh:
+                h.update(fh.read())
+    return h.hexdigest()[:12]
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    params, cfg, wname = workload(args.workload, replica=0)
+    c = synth.coefficients(1 + params.K2 + params.K3 * (params.P3 + 1) + params.K4 * _ka(params.P4), 2001)
+    budget = max(1.0, args.cpu_budget / max(1, args.steps + args.warmup))
+    for _ in range(args.warmup):
+        oracle_sample(params, cfg, c, budget / 4)
+    tot_atoms, tot_s = 0, 0.0
+    per_step = []
+    for _ in range(args.steps):
+        n, el = oracle_sample(params, cfg, c, budget)
+        tot_atoms += n
+        tot_s += el
+        per_step.append(el)
+    value = tot_atoms / tot_s
+    line = {"impl": "reference",
+            "metric": "atom-steps/s (E+F) mixed vs FP64 at stated force error; % of roofline",
+            "value": value, "unit": "atom-steps/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * tot_s / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": wname, "atoms_per_gpu": cfg.n},
+            "cpu_baseline": {"value": value, "unit": "atom-steps/s", "cores": 1, "kind": "oracle",
+                             "sample": f"{tot_atoms} atom evaluations (brute-force neighbours + FP64 "
+                                       f"atom-density energy and pair gradients), one host core"},
+            "e2e": {"value": value, "unit": "atom-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def _ka(P4):
+    if P4 < 0:
+        return 0
+    return sum(1 for n in range(P4 + 1) for a in range(n, -1, -1) for b in range(min(a, n - a), -1, -1)
+               if 0 <= n - a - b <= b)
+
+
+if __name__ == "__main__":
+    main()

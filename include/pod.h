@@ -1,0 +1,199 @@
+/*
+ * fastpod -- C ABI of the GB300 (sm_103a) implementation of fast proper
+ * orthogonal descriptors (N.-C. Nguyen, "Fast proper orthogonal descriptors for
+ * many-body interatomic potentials", arXiv:2212.14446).
+ *
+ * The library computes, for every atom i of an atomic configuration,
+ *   - the POD radial basis R_k(r) = sum_l Q_lk Phi_l(r) built from parametrized
+ *     radial snapshots with a smooth cut-off              (Section 2.2, Eq. 3-12)
+ *   - the atomic basis B_imnl = sum_j R_m(r_ij) A_nl(rhat_ij)     (Eq. 24b)
+ *   - the inclusive 2-, 3- and 4-body descriptors via Eq. 12b, Eq. 26a,
+ *     Eq. 27a and Eq. 30a (equal to the naive sums Eq. 15 / Eq. 18a)
+ *   - the linear energy E_i = sum_m c_m D_im, E = sum_i E_i     (Eq. 57a, 58a)
+ *   - forces F_k = -dE/dr_k and the virial by an adjoint of Eq. 24c / Eq. 26c
+ *   - the ridge least-squares fit of Eq. 63a.
+ *
+ * Conventions common to every call
+ *   - All lengths are in Angstrom; energies in the units of the coefficients c.
+ *   - Positions are structure-of-arrays: pos[0..N) = x, pos[N..2N) = y,
+ *     pos[2N..3N) = z (FP64).  Boxes are orthorhombic, [0, L_d) in periodic
+ *     directions.  Forces use the same [3][N] layout.
+ *   - Descriptor order per atom (M columns):
+ *       [ 1 | D2_m (m < K2) | D3_mn (m < K3 major, n = 0..P3) |
+ *         D4_mp (m < K4 major, p in the order of Table 1: degree ascending,
+ *                then (a, b, c) lexicographically descending) ]
+ *     with M = 1 + K2 + K3 (P3 + 1) + K4 K_a(P4)  (Table 6 caption).
+ *   - Device pointers are CUDA device memory on the current device; the caller
+ *     owns every buffer passed in.  The library owns the handle, Q, its tables
+ *     and a workspace that grows on demand and is freed by pod_destroy.
+ *   - Calls taking `stream` (a cudaStream_t, NULL = legacy default stream)
+ *     enqueue their kernels on it.  With the synchronous-status option on (the
+ *     default), each call waits for its stream at the end and turns device-side
+ *     conditions into return codes; with it off, calls return as soon as the
+ *     work is enqueued and pod_status() reports later.
+ *   - Return value: POD_OK (0) or a negative POD_E* code; pod_last_error()
+ *     gives the message.  No call throws or aborts; invalid arguments never
+ *     reach a kernel.
+ *   - A handle is not thread-safe; use one handle per host thread/stream.
+ */
+#ifndef FASTPOD_POD_H
+#define FASTPOD_POD_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define POD_OK 0
+#define POD_EINVAL (-1)     /* bad parameter, NULL pointer, unsupported size      */
+#define POD_ENOMEM (-2)     /* device or host allocation failed                   */
+#define POD_ECUDA (-3)      /* a CUDA runtime call failed                         */
+#define POD_ERANGE (-4)     /* a pair closer than r_in (outside (r_in, r_cut))    */
+#define POD_ENONFINITE (-5) /* NaN/Inf in positions or results                    */
+#define POD_ESINGULAR (-6)  /* fit: normal equations not positive definite        */
+#define POD_ENEIGH (-7)     /* neighbour or cell capacity exceeded after retry    */
+
+#define POD_FP64 0  /* every step in FP64 (reference path)                        */
+#define POD_MIXED 1 /* FP32 pair/contraction/adjoint, FP64 reductions and fit     */
+
+typedef struct pod_handle pod_handle;
+
+/* Hyper-parameters mu = (r_in, r_cut, alpha, beta, gamma) of Section 2.2 and
+ * the radial/angular sizes of Sections 2.3-2.4.  The snapshot family is
+ * phi(r; alpha_a, beta_b) for every pair (a, b) (alpha outer, beta inner),
+ * followed by varphi(r; gamma_g) for every g, each times the cut-off f_c
+ * (Eq. 6, Eq. 11); Ns = n_alpha * n_beta + n_gamma.  Arrays are copied. */
+typedef struct {
+  double r_in, r_cut;      /* 0 < r_in < r_cut                                  */
+  int n_alpha;             /* 1..8                                              */
+  const double* alpha;
+  int n_beta;              /* 1..2, every beta > 0                              */
+  const double* beta;
+  int n_gamma;             /* 0..8                                              */
+  const double* gamma;
+  int K2, K3, K4;          /* radial modes per body order, 0..16, <= Ns         */
+  int P3;                  /* three-body angular degree, -1 (none) .. 4         */
+  int P4;                  /* four-body angular degree, -1 (none) .. 4          */
+  int n_grid;              /* POD midpoint-grid points (0 -> 2000)              */
+  int precision;           /* POD_FP64 or POD_MIXED                             */
+  const double* Q;         /* optional Ns x K_r projection (row-major) used
+                              instead of the library's own POD; NULL -> compute */
+} pod_params;
+
+/* One configuration (n_configs <= 1) or a batch of configurations stored back
+ * to back (n_configs > 1, used by pod_fit and the batched calls). */
+typedef struct {
+  int n_atoms;             /* total atoms, >= 1                                 */
+  const double* pos;       /* [3][n_atoms] SoA (device, or host for *_host)     */
+  double box[3];           /* box lengths for a single configuration            */
+  int pbc[3];              /* 1 = periodic, 0 = open                            */
+  int n_configs;           /* 0 or 1: single configuration                      */
+  const int* atom_offs;    /* HOST [n_configs + 1] atom offsets (batch only)    */
+  const double* boxes;     /* HOST [n_configs][3] box lengths   (batch only)    */
+  const int* pbcs;         /* HOST [n_configs][3] or NULL (= pbc for all)       */
+} pod_system;
+
+/* Creates a handle: validates params, builds the POD basis on the host (the
+ * snapshot Gram matrix on an n_grid midpoint grid over (r_in, r_cut),
+ * eigenvectors sorted by decreasing eigenvalue, each with its largest entry
+ * positive, scaled by 1/sqrt(lambda) so R_k has unit L2 norm; Section 2.2,
+ * Eq. 12) unless params->Q is given, and the angular tables (Table 3-5).
+ * *out receives the handle.  Errors: POD_EINVAL, POD_ENOMEM, POD_ECUDA. */
+int pod_create(const pod_params* params, pod_handle** out);
+
+/* Frees the handle, its device tables and workspace.  NULL is allowed. */
+int pod_destroy(pod_handle* h);
+
+/* Sizes and basis of a handle.  Any output pointer may be NULL.
+ * M: descriptors per atom; Ns: snapshots; K: radial modes K_r;
+ * Q_out: host [Ns][K] projection; eig_out: host [Ns] eigenvalues (descending;
+ * zeros when Q was supplied). */
+int pod_info(const pod_handle* h, int* M, int* Ns, int* K, double* Q_out, double* eig_out);
+
+/* Sets a handle option.  POD_OPT_SYNC (default 1): wait for the stream at the
+ * end of each call and report device-side conditions as return codes.
+ * POD_OPT_PRECISION: POD_FP64 or POD_MIXED for subsequent calls. */
+#define POD_OPT_SYNC 1
+#define POD_OPT_PRECISION 2
+#define POD_OPT_TIMING 3 /* 1: time each phase of pod_energy_forces with CUDA events */
+#define POD_OPT_RADIAL 4 /* mixed path only: 0 (default) R_k from a 2048-interval cubic
+                            Hermite table built in FP64 at first use (relative error
+                            ~1e-7); 1 = snapshots evaluated per pair in FP32 and
+                            projected (Eq. 3-12; POD cancellation costs ~1e-5)  */
+int pod_set_option(pod_handle* h, int option, int value);
+
+/* Per-phase device time of the pod_energy_forces calls made while
+ * POD_OPT_TIMING was on, measured with CUDA events recorded on the call's stream
+ * around each phase: ms[0] neighbour list (binning, search, reverse index),
+ * ms[1] fused atom kernel, ms[2] force gather, ms[3] energy/virial reduction
+ * (totals in milliseconds; ms is host [4]).  *calls receives the number of
+ * calls timed.  Resets the totals.  With timing on, each call waits for its
+ * last event. */
+int pod_timing(pod_handle* h, double* ms, int* calls);
+
+/* Waits for `stream` and returns the device-side status accumulated since the
+ * last report (POD_OK, POD_ERANGE, POD_ENONFINITE, POD_ENEIGH), then clears it. */
+int pod_status(pod_handle* h, void* stream);
+
+/* Full neighbour list of one configuration (the cut-off region of Section 2.2):
+ * every (j, s) with |x_j + s L - x_i| < r_cut, excluding (i, 0), positions
+ * wrapped into [0, L) in periodic directions, the squared distance formed in
+ * FP64 as (dx*dx + dy*dy) + dz*dz without fused multiply-add, each atom's list
+ * sorted by (j, s_x, s_y, s_z).
+ *   count: device [N] number of neighbours per atom (may exceed cap)
+ *   nbr:   device [N][cap] neighbour index j
+ *   shift: device [N][cap][3] image shift s (int)
+ * Errors: POD_EINVAL; POD_ENEIGH if an atom has more than cap neighbours (the
+ * first cap entries are still written, count holds the true number). */
+int pod_neighbors(pod_handle* h, const pod_system* sys, int cap, int* count, int* nbr, int* shift,
+                  void* stream);
+
+/* Descriptors D (device [N][M], FP64) of every atom: Eq. 12b, Eq. 26a, Eq. 27a,
+ * Eq. 30a.  The mixed path computes in FP32 and stores FP64.  Batched systems
+ * are supported.  Errors: POD_EINVAL, POD_ERANGE, POD_ENEIGH, POD_ECUDA. */
+int pod_descriptors(pod_handle* h, const pod_system* sys, double* D, void* stream);
+
+/* Linear POD energy and its derivatives (Eq. 57a, 58a; forces by the adjoint
+ * of Eq. 24c / 26c):
+ *   c:  device [M] coefficients (FP64)
+ *   E:  device [max(1, n_configs)] total energy per configuration (FP64,
+ *       fixed-order reduction), required
+ *   Ei: device [N] atom energies or NULL
+ *   F:  device [3][N] forces F_k = -dE/dr_k or NULL
+ *   W:  device [max(1, n_configs)][9] virial W_ab = -sum_ij (r_ij)_a dE_i/d(r_ij)_b
+ *       (row-major 3x3) or NULL
+ * Errors: POD_EINVAL, POD_ERANGE, POD_ENEIGH, POD_ENONFINITE, POD_ECUDA. */
+int pod_energy_forces(pod_handle* h, const pod_system* sys, const double* c, double* E, double* Ei, double* F,
+                      double* W, void* stream);
+
+/* pod_energy_forces with HOST buffers: sys->pos, c, E, Ei, F, W are host
+ * pointers (pinned memory is fastest).  Copies inputs to library-owned device
+ * buffers, computes, copies results back and waits for the stream. */
+int pod_energy_forces_host(pod_handle* h, const pod_system* sys, const double* c, double* E, double* Ei,
+                           double* F, double* W, void* stream);
+
+/* Options of the ridge least-squares fit of Eq. 63a. */
+typedef struct {
+  double w_E;         /* energy-row weight (paper: 100)                          */
+  double w_F;         /* force-row weight (paper: 1)                             */
+  double gamma_reg;   /* ridge parameter (paper: 1e-12)                          */
+  int per_atom_energy;/* 1: energy rows are G_m / N against E / N (default)      */
+} pod_fit_opts;
+
+/* Fits c (host [M]) to reference energies and forces of a batch of
+ * configurations: rows w_E G_m(cfg) / N_cfg against w_E E_ref / N_cfg and rows
+ * -w_F dG_m/dr_ka against w_F F_ref, plus gamma_reg I; normal equations
+ * (A^T A + gamma I) c = A^T b solved by Cholesky, all in FP64 on the GPU.
+ *   E_ref: device [n_configs]; F_ref: device [3][N]; mae_E (per atom) and
+ *   mae_F (per component) receive the training errors (host, may be NULL).
+ * Synchronous.  Errors: POD_EINVAL, POD_ESINGULAR, POD_ERANGE, POD_ENEIGH,
+ * POD_ECUDA. */
+int pod_fit(pod_handle* h, const pod_system* batch, const double* E_ref, const double* F_ref,
+            const pod_fit_opts* opts, double* c_out, double* mae_E, double* mae_F);
+
+/* Message of the last error on this handle ("" if none).  Owned by the handle. */
+const char* pod_last_error(const pod_handle* h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FASTPOD_POD_H */

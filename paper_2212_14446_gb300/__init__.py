@@ -1,0 +1,338 @@
+"""Python binding of the fastpod C ABI (``include/pod.h``).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+kernels of ``_lib/libfastpod.so``; PyTorch provides device memory and streams.
+The module fails loudly when the library has not been built -- there is no CPU
+fallback.
+
+Low-level functions carry the C names (``pod_create``, ``pod_descriptors``,
+``pod_energy_forces``, ``pod_energy_forces_host``, ``pod_neighbors``,
+``pod_fit``, ...).  :class:`POD` wraps a handle for convenience.
+
+Layouts: positions and forces are structure-of-arrays ``(3, N)`` float64 on
+the device; descriptors are ``(N, M)`` float64 (order in ``include/pod.h``).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libfastpod.so")
+
+POD_OK, POD_EINVAL, POD_ENOMEM, POD_ECUDA, POD_ERANGE, POD_ENONFINITE, POD_ESINGULAR, POD_ENEIGH = (
+    0, -1, -2, -3, -4, -5, -6, -7)
+POD_FP64, POD_MIXED = 0, 1
+POD_OPT_SYNC, POD_OPT_PRECISION, POD_OPT_TIMING, POD_OPT_RADIAL = 1, 2, 3, 4
+ERROR_NAMES = {0: "POD_OK", -1: "POD_EINVAL", -2: "POD_ENOMEM", -3: "POD_ECUDA", -4: "POD_ERANGE",
+               -5: "POD_ENONFINITE", -6: "POD_ESINGULAR", -7: "POD_ENEIGH"}
+
+
+class PodError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{ERROR_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class pod_params(C.Structure):
+    _fields_ = [("r_in", C.c_double), ("r_cut", C.c_double),
+                ("n_alpha", C.c_int), ("alpha", C.POINTER(C.c_double)),
+                ("n_beta", C.c_int), ("beta", C.POINTER(C.c_double)),
+                ("n_gamma", C.c_int), ("gamma", C.POINTER(C.c_double)),
+                ("K2", C.c_int), ("K3", C.c_int), ("K4", C.c_int), ("P3", C.c_int), ("P4", C.c_int),
+                ("n_grid", C.c_int), ("precision", C.c_int), ("Q", C.POINTER(C.c_double))]
+
+
+class pod_system(C.Structure):
+    _fields_ = [("n_atoms", C.c_int), ("pos", C.POINTER(C.c_double)),
+                ("box", C.c_double * 3), ("pbc", C.c_int * 3),
+                ("n_configs", C.c_int), ("atom_offs", C.POINTER(C.c_int)),
+                ("boxes", C.POINTER(C.c_double)), ("pbcs", C.POINTER(C.c_int))]
+
+
+class pod_fit_opts(C.Structure):
+    _fields_ = [("w_E", C.c_double), ("w_F", C.c_double), ("gamma_reg", C.c_double),
+                ("per_atom_energy", C.c_int)]
+
+
+EXPORTS = ["pod_create", "pod_destroy", "pod_info", "pod_set_option", "pod_status", "pod_timing",
+           "pod_neighbors", "pod_descriptors", "pod_energy_forces", "pod_energy_forces_host", "pod_fit",
+           "pod_last_error"]
+
+_lib = None
+_lock = threading.Lock()
+
+
+def lib():
+    """Load ``libfastpod.so`` (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"fastpod CUDA library not built ({LIB_PATH}); run "
+                                   "paper_2212_14446_gb300.build.build() first")
+            L = C.CDLL(LIB_PATH)
+            H = C.c_void_p
+            dp, ip, vp = C.POINTER(C.c_double), C.POINTER(C.c_int), C.c_void_p
+            S = C.POINTER(pod_system)
+            sig = {
+                "pod_create": (C.c_int, [C.POINTER(pod_params), C.POINTER(H)]),
+                "pod_destroy": (C.c_int, [H]),
+                "pod_info": (C.c_int, [H, ip, ip, ip, dp, dp]),
+                "pod_set_option": (C.c_int, [H, C.c_int, C.c_int]),
+                "pod_status": (C.c_int, [H, vp]),
+                "pod_timing": (C.c_int, [H, dp, ip]),
+                "pod_neighbors": (C.c_int, [H, S, C.c_int, ip, ip, ip, vp]),
+                "pod_descriptors": (C.c_int, [H, S, dp, vp]),
+                "pod_energy_forces": (C.c_int, [H, S, dp, dp, dp, dp, dp, vp]),
+                "pod_energy_forces_host": (C.c_int, [H, S, dp, dp, dp, dp, dp, vp]),
+                "pod_fit": (C.c_int, [H, S, dp, dp, C.POINTER(pod_fit_opts), dp, dp, dp]),
+                "pod_last_error": (C.c_char_p, [H]),
+            }
+            for name, (res, args) in sig.items():
+                fn = getattr(L, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = L
+    return _lib
+
+
+# ------------------------------------------------------------- thin C names
+
+def pod_create(params: pod_params):
+    h = C.c_void_p()
+    rc = lib().pod_create(C.byref(params), C.byref(h))
+    if rc != POD_OK:
+        msg = lib().pod_last_error(h).decode() if h.value else ""
+        if h.value:
+            lib().pod_destroy(h)
+        raise PodError(rc, msg or "pod_create failed")
+    return h
+
+
+def pod_destroy(h):
+    return lib().pod_destroy(h)
+
+
+def pod_last_error(h) -> str:
+    return lib().pod_last_error(h).decode()
+
+
+def _check(h, rc):
+    if rc != POD_OK:
+        raise PodError(rc, pod_last_error(h))
+
+
+def _dptr(t):
+    if t is None:
+        return None
+    return C.cast(C.c_void_p(t.data_ptr()), C.POINTER(C.c_double))
+
+
+def _iptr(t):
+    if t is None:
+        return None
+    return C.cast(C.c_void_p(t.data_ptr()), C.POINTER(C.c_int))
+
+
+def _stream(stream):
+    import torch
+    if stream is None:
+        return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    return C.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+
+
+def make_system(pos_ptr, n_atoms, box, pbc=(1, 1, 1), batch=None):
+    s = pod_system()
+    s.n_atoms = int(n_atoms)
+    s.pos = pos_ptr
+    s.box = (C.c_double * 3)(*[float(b) for b in box])
+    s.pbc = (C.c_int * 3)(*[int(p) for p in pbc])
+    s.n_configs = 0
+    keep = []
+    if batch is not None:
+        offs, boxes, pbcs = batch
+        offs = np.ascontiguousarray(offs, dtype=np.int32)
+        boxes = np.ascontiguousarray(boxes, dtype=np.float64)
+        s.n_configs = len(offs) - 1
+        s.atom_offs = offs.ctypes.data_as(C.POINTER(C.c_int))
+        s.boxes = boxes.ctypes.data_as(C.POINTER(C.c_double))
+        keep += [offs, boxes]
+        if pbcs is not None:
+            pbcs = np.ascontiguousarray(pbcs, dtype=np.int32)
+            s.pbcs = pbcs.ctypes.data_as(C.POINTER(C.c_int))
+            keep.append(pbcs)
+    s._keep = keep
+    return s
+
+
+def pod_descriptors(h, sys, D, stream=None):
+    _check(h, lib().pod_descriptors(h, C.byref(sys), _dptr(D), _stream(stream)))
+
+
+def pod_energy_forces(h, sys, c, E, Ei=None, F=None, W=None, stream=None):
+    _check(h, lib().pod_energy_forces(h, C.byref(sys), _dptr(c), _dptr(E), _dptr(Ei), _dptr(F), _dptr(W),
+                                      _stream(stream)))
+
+
+def pod_energy_forces_host(h, sys, c, E, Ei=None, F=None, W=None, stream=None):
+    def hp(a):
+        return None if a is None else a.ctypes.data_as(C.POINTER(C.c_double))
+    _check(h, lib().pod_energy_forces_host(h, C.byref(sys), hp(c), hp(E), hp(Ei), hp(F), hp(W),
+                                           _stream(stream)))
+
+
+def pod_neighbors(h, sys, cap, count, nbr, shift, stream=None):
+    _check(h, lib().pod_neighbors(h, C.byref(sys), int(cap), _iptr(count), _iptr(nbr), _iptr(shift),
+                                  _stream(stream)))
+
+
+def pod_status(h, stream=None):
+    return lib().pod_status(h, _stream(stream))
+
+
+def pod_set_option(h, option, value):
+    _check(h, lib().pod_set_option(h, int(option), int(value)))
+
+
+def pod_timing(h):
+    """(per-phase totals in ms [neighbours, atom kernel, gather, reduce], calls); resets."""
+    ms = np.zeros(4)
+    calls = C.c_int()
+    _check(h, lib().pod_timing(h, ms.ctypes.data_as(C.POINTER(C.c_double)), C.byref(calls)))
+    return ms, calls.value
+
+
+# ----------------------------------------------------------------- wrapper
+
+def _param_struct(params, precision, Q=None, n_grid=None):
+    alpha = np.ascontiguousarray(params.alpha, dtype=np.float64)
+    beta = np.ascontiguousarray(params.beta, dtype=np.float64)
+    gamma = np.ascontiguousarray(params.gamma, dtype=np.float64)
+    p = pod_params()
+    p.r_in, p.r_cut = float(params.r_in), float(params.r_cut)
+    p.n_alpha, p.alpha = len(alpha), alpha.ctypes.data_as(C.POINTER(C.c_double))
+    p.n_beta, p.beta = len(beta), beta.ctypes.data_as(C.POINTER(C.c_double))
+    p.n_gamma, p.gamma = len(gamma), gamma.ctypes.data_as(C.POINTER(C.c_double))
+    p.K2, p.K3, p.K4, p.P3, p.P4 = (int(params.K2), int(params.K3), int(params.K4), int(params.P3),
+                                    int(params.P4))
+    p.n_grid = int(n_grid if n_grid is not None else getattr(params, "n_grid", 2000))
+    p.precision = POD_MIXED if precision in ("mixed", POD_MIXED) else POD_FP64
+    keep = [alpha, beta, gamma]
+    if Q is not None:
+        Qa = np.ascontiguousarray(Q, dtype=np.float64)
+        p.Q = Qa.ctypes.data_as(C.POINTER(C.c_double))
+        keep.append(Qa)
+    p._keep = keep
+    return p
+
+
+def _soa(pos):
+    """(N, 3) or (3, N) float64 CUDA tensor -> contiguous (3, N)."""
+    import torch
+    if pos.dim() != 2:
+        raise ValueError("positions must be 2-D")
+    if pos.shape[0] == 3 and pos.shape[1] != 3:
+        t = pos
+    elif pos.shape[1] == 3:
+        t = pos.t()
+    else:
+        t = pos
+    return t.to(dtype=torch.float64).contiguous()
+
+
+class POD:
+    """A fastpod handle bound to one parameter set.
+
+    ``params`` is any object with attributes r_in, r_cut, alpha, beta, gamma,
+    K2, K3, K4, P3, P4 (and optionally n_grid)."""
+
+    def __init__(self, params, precision="fp64", Q=None, n_grid=None):
+        self._p = _param_struct(params, precision, Q, n_grid)
+        self.h = pod_create(self._p)
+        M, Ns, K = C.c_int(), C.c_int(), C.c_int()
+        _check(self.h, lib().pod_info(self.h, C.byref(M), C.byref(Ns), C.byref(K), None, None))
+        self.M, self.Ns, self.K = M.value, Ns.value, K.value
+        Qo = np.zeros((self.Ns, self.K))
+        eig = np.zeros(self.Ns)
+        _check(self.h, lib().pod_info(self.h, None, None, None, Qo.ctypes.data_as(C.POINTER(C.c_double)),
+                                      eig.ctypes.data_as(C.POINTER(C.c_double))))
+        self.Q, self.eig = Qo, eig
+        self.precision = precision
+
+    def close(self):
+        if getattr(self, "h", None):
+            pod_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_precision(self, precision):
+        pod_set_option(self.h, POD_OPT_PRECISION, POD_MIXED if precision in ("mixed", POD_MIXED) else POD_FP64)
+        self.precision = precision
+
+    def set_sync(self, on: bool):
+        pod_set_option(self.h, POD_OPT_SYNC, 1 if on else 0)
+
+    def set_radial(self, mode: str):
+        """Mixed path: 'table' (default) or 'direct' radial evaluation."""
+        pod_set_option(self.h, POD_OPT_RADIAL, 0 if mode == "table" else 1)
+
+    def set_timing(self, on: bool):
+        pod_set_option(self.h, POD_OPT_TIMING, 1 if on else 0)
+
+    def timing(self):
+        return pod_timing(self.h)
+
+    def system(self, pos_soa, box, pbc=(1, 1, 1)):
+        return make_system(_dptr(pos_soa), pos_soa.shape[1], box, pbc)
+
+    def neighbors(self, pos, box, pbc=(1, 1, 1), cap=64, stream=None):
+        import torch
+        x = _soa(pos)
+        n = x.shape[1]
+        count = torch.zeros(n, dtype=torch.int32, device=x.device)
+        nbr = torch.full((n, cap), -1, dtype=torch.int32, device=x.device)
+        shift = torch.zeros((n, cap, 3), dtype=torch.int32, device=x.device)
+        pod_neighbors(self.h, self.system(x, box, pbc), cap, count, nbr, shift, stream)
+        return count, nbr, shift
+
+    def descriptors(self, pos, box, pbc=(1, 1, 1), stream=None):
+        import torch
+        x = _soa(pos)
+        D = torch.empty((x.shape[1], self.M), dtype=torch.float64, device=x.device)
+        pod_descriptors(self.h, self.system(x, box, pbc), D, stream)
+        return D
+
+    def energy_forces(self, pos, box, c, pbc=(1, 1, 1), atom_energies=True, forces=True, virial=True,
+                      stream=None):
+        import torch
+        x = _soa(pos)
+        n = x.shape[1]
+        dev = x.device
+        c = c.to(device=dev, dtype=torch.float64).contiguous()
+        E = torch.empty(1, dtype=torch.float64, device=dev)
+        Ei = torch.empty(n, dtype=torch.float64, device=dev) if atom_energies else None
+        F = torch.empty((3, n), dtype=torch.float64, device=dev) if forces else None
+        W = torch.empty(9, dtype=torch.float64, device=dev) if virial else None
+        pod_energy_forces(self.h, self.system(x, box, pbc), c, E, Ei, F, W, stream)
+        return {"E": E, "Ei": Ei, "F": None if F is None else F.t(), "W": None if W is None else W.view(3, 3)}
+
+    def energy_forces_host(self, pos_soa: np.ndarray, box, c: np.ndarray, pbc=(1, 1, 1), stream=None):
+        """Host-buffer entry point: numpy in, numpy out (copies inside the call)."""
+        pos_soa = np.ascontiguousarray(pos_soa, dtype=np.float64)
+        n = pos_soa.shape[1]
+        E = np.zeros(1)
+        F = np.zeros((3, n))
+        W = np.zeros(9)
+        Ei = np.zeros(n)
+        sys = make_system(pos_soa.ctypes.data_as(C.POINTER(C.c_double)), n, box, pbc)
+        pod_energy_forces_host(self.h, sys, np.ascontiguousarray(c, dtype=np.float64), E, Ei, F, W, stream)
+        return {"E": E, "Ei": Ei, "F": F.T, "W": W.reshape(3, 3)}

@@ -1,0 +1,371 @@
+// Fused per-atom kernel: radial snapshots + POD projection (Eq. 3-12), atomic
+// basis B_imnl (Eq. 24b), contraction into D2 / D3 / D4 (Eq. 12b, 26a, 27a, 30a),
+// energy E_i = c . D_i (Eq. 57a), adjoint dE_i/dB and the adjoint pair pass
+// g_ij = dE_i/dr_ij (Eq. 24c, 26c) -- one launch, all intermediates on chip.
+//
+// Work mapping (one warp holds A = 32 / K atoms):
+//   pair pass      lanes over the flattened (atom, neighbour) pairs of the warp;
+//                  each lane evaluates one pair's snapshots, R_k and R'_k and
+//                  stages (u, r, R, R') in shared memory;
+//   B and contraction  lane (atom, m) owns B_m[0..N_a) in registers, so every
+//                  D3/D4 product and the whole adjoint run in registers;
+//   adjoint pair pass  lanes over pairs again, reading dE/dB_m from shared memory.
+#pragma once
+#include "contract_gen.cuh"
+#include "pod_common.cuh"
+#include "pod_kernels.h"
+
+namespace fastpod {
+
+template <typename T>
+__device__ __forceinline__ void pair_disp(const AtomArgs<T>& p, int i, int j, int sx, int sy, int sz, T& dx, T& dy,
+                                          T& dz);
+
+template <>
+__device__ __forceinline__ void pair_disp<double>(const AtomArgs<double>& p, int i, int j, int sx, int sy, int sz,
+                                                  double& dx, double& dy, double& dz) {
+  const size_t N = p.N;
+  dx = disp_fp64(p.wpos[i], p.wpos[j], sx, p.L[0]);
+  dy = disp_fp64(p.wpos[N + i], p.wpos[N + j], sy, p.L[1]);
+  dz = disp_fp64(p.wpos[2 * N + i], p.wpos[2 * N + j], sz, p.L[2]);
+}
+
+template <>
+__device__ __forceinline__ void pair_disp<float>(const AtomArgs<float>& p, int i, int j, int sx, int sy, int sz,
+                                                 float& dx, float& dy, float& dz) {
+  const float4 hi = p.phi[i], li = p.plo[i], hj = p.phi[j], lj = p.plo[j];
+  dx = disp_f32(hi.x, li.x, hj.x, lj.x, sx, p.Lh[0], p.Ll[0]);
+  dy = disp_f32(hi.y, li.y, hj.y, lj.y, sy, p.Lh[1], p.Ll[1]);
+  dz = disp_f32(hi.z, li.z, hj.z, lj.z, sz, p.Lh[2], p.Ll[2]);
+}
+
+__device__ __forceinline__ int chunk_count(int n, int ch) { return min(max(n - ch * CH, 0), CH); }
+
+// Stage chunk `ch` of the warp's pairs: (u, r) and R, R' per pair.
+template <typename T, int KT>
+__device__ __forceinline__ void pair_pass(const AtomArgs<T>& p, const AtomLayout& lay, Q4<T>* geo, T* sR, T* sRp,
+                                          const int* scnt, int atom0, int A, int K, int ch, int lane) {
+  int tot = 0;
+  for (int a = 0; a < A; ++a) tot += chunk_count(scnt[a], ch);
+  for (int f = lane; f < tot; f += 32) {
+    int a = 0, base = 0;
+    for (; a < A; ++a) {
+      const int nca = chunk_count(scnt[a], ch);
+      if (f < base + nca) break;
+      base += nca;
+    }
+    const int jj = f - base, slot = ch * CH + jj, i = atom0 + a;
+    const size_t pidx = (size_t)i * p.cap + slot;
+    const int j = p.nbr_j[pidx];
+    int sx, sy, sz;
+    shift_unpack(p.nbr_s[pidx], sx, sy, sz);
+    T dx, dy, dz;
+    pair_disp<T>(p, i, j, sx, sy, sz, dx, dy, dz);
+    const T r = d_sqrt(dx * dx + dy * dy + dz * dz);
+    const T ir = T(1) / r;
+    Q4<T> gq;
+    gq.x = dx * ir;
+    gq.y = dy * ir;
+    gq.z = dz * ir;
+    gq.w = r;
+    geo[a * lay.GA + jj] = gq;
+    T R[KT], Rp[KT];
+    if (r > p.rad.r_in) {
+      radial_pair<T, KT>(p.rad, r, R, Rp);
+    } else {
+      atomicOr(p.status, ST_RANGE);
+#pragma unroll
+      for (int k = 0; k < KT; ++k) { R[k] = T(0); Rp[k] = T(0); }
+    }
+    T* Rrow = sR + a * lay.SA + jj * lay.KS;
+    T* Rprow = sRp + a * lay.SA + jj * lay.KS;
+#pragma unroll
+    for (int k = 0; k < KT; ++k) {
+      if (KT == MAXK && k >= K) break;
+      Rrow[k] = R[k];
+      Rprow[k] = Rp[k];
+    }
+  }
+}
+
+template <typename T, int PA, bool HAS4, int MODE, int KT>
+__global__ void __launch_bounds__(WPB_ATOM * 32) atom_kernel(const AtomArgs<T> p, const AtomLayout lay) {
+  constexpr int NA = Mono<PA>::NA;
+  constexpr int NAP = (NA + 3) / 4 * 4;
+  constexpr int KA = HAS4 ? Four<PA>::KA : 1;
+  extern __shared__ __align__(32) unsigned char sm[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  unsigned char* wb = sm + (size_t)warp * lay.warp_bytes;
+  Q4<T>* geo = reinterpret_cast<Q4<T>*>(wb + lay.off_geo);
+  T* sR = reinterpret_cast<T*>(wb + lay.off_R);
+  T* sRp = reinterpret_cast<T*>(wb + lay.off_Rp);
+  T* sadj = reinterpret_cast<T*>(wb + lay.off_adj);
+  T* se = reinterpret_cast<T*>(wb + lay.off_e);
+  int* scnt = reinterpret_cast<int*>(wb + lay.off_cnt);
+
+  const int K = (KT == MAXK) ? p.K : KT;
+  const int A = (KT == MAXK) ? lay.A : 32 / KT;
+  const int a_loc = lane / K;
+  const int m = lane - a_loc * K;
+  const int atom0 = (blockIdx.x * WPB_ATOM + warp) * A;
+  if (atom0 >= p.N) return;  // uniform per warp
+  if (lane < A) {
+    const int i = atom0 + lane;
+    scnt[lane] = (i < p.N) ? min(p.nbr_count[i], p.cap) : 0;
+  }
+  __syncwarp();
+  int nmax = 0;
+  for (int a = 0; a < A; ++a) nmax = max(nmax, scnt[a]);
+  const int nchunks = (nmax + CH - 1) / CH;
+  const bool am = (a_loc < A) && (atom0 + a_loc < p.N);
+  const int my_n = am ? scnt[a_loc] : 0;
+
+  // ---------------- forward: B_m[x] = sum_j R_m(r_ij) A_x(u_ij)   (Eq. 24b)
+  T B[NA];
+#pragma unroll
+  for (int x = 0; x < NA; ++x) B[x] = T(0);
+  for (int ch = 0; ch < nchunks; ++ch) {
+    pair_pass<T, KT>(p, lay, geo, sR, sRp, scnt, atom0, A, K, ch, lane);
+    __syncwarp();
+    if (am) {
+      const int nc = chunk_count(my_n, ch);
+      const Q4<T>* ga = geo + a_loc * lay.GA;
+      const T* Ra = sR + a_loc * lay.SA + m;
+      for (int jj = 0; jj < nc; ++jj) {
+        const Q4<T> u = ga[jj];
+        const T R = Ra[jj * lay.KS];
+        T Am[NA];
+        Mono<PA>::eval(u.x, u.y, u.z, Am);
+#pragma unroll
+        for (int x = 0; x < NA; ++x) B[x] = fma(R, Am[x], B[x]);
+      }
+    }
+    __syncwarp();
+  }
+
+  if (MODE == 0) {
+    // ---------------- descriptors (Eq. 12b, 26a, 27a, 30a)
+    if (am) {
+      const int i = atom0 + a_loc;
+      double* Di = p.D + (size_t)i * p.M;
+      if (m == 0) Di[0] = 1.0;
+      if (m < p.K2) Di[1 + m] = (double)B[0];
+      T d3[PA + 1];
+      Mono<PA>::d3(B, d3);
+      if (m < p.K3) {
+#pragma unroll
+        for (int n = 0; n <= PA; ++n)
+          if (n <= p.P3) Di[p.col3 + m * (p.P3 + 1) + n] = (double)d3[n];
+      }
+      if (HAS4 && m < p.K4) {
+        T D4[KA];
+        Four<PA>::desc(B, d3, D4);
+#pragma unroll
+        for (int q = 0; q < KA; ++q)
+          if (q < p.KA4) Di[p.col4 + m * p.KA4 + q] = (double)D4[q];
+      }
+    }
+    return;
+  }
+
+  // ---------------- energy and adjoint a = dE_i/dB_m  (Eq. 26c generalised)
+  T E = T(0);
+  {
+    T a[NAP];
+#pragma unroll
+    for (int x = 0; x < NAP; ++x) a[x] = T(0);
+    if (am) {
+      const double* c = p.c;
+      const T c2 = (m < p.K2) ? (T)c[1 + m] : T(0);
+      T h[PA + 1];
+#pragma unroll
+      for (int n = 0; n <= PA; ++n)
+        h[n] = (n <= p.P3 && m < p.K3) ? (T)c[p.col3 + m * (p.P3 + 1) + n] : T(0);
+      T d3[PA + 1];
+      Mono<PA>::d3(B, d3);
+      T a0 = c2;
+      if (HAS4) {
+        T w4[KA];
+#pragma unroll
+        for (int q = 0; q < KA; ++q) w4[q] = (q < p.KA4 && m < p.K4) ? (T)c[p.col4 + m * p.KA4 + q] : T(0);
+        // general partitions (Eq. 30a): cubic form, E4 = (1/3) sum_x B_x dE4/dB_x
+        Four<PA>::adjoint(B, w4, a);
+        T E4 = T(0);
+#pragma unroll
+        for (int x = 0; x < NA; ++x) E4 = fma(a[x], B[x], E4);
+        E = E4 * (T(1) / T(3));
+        // b = c = 0 partitions (Eq. 27a): D4 = D2 * D3_n folds into the D3 weights
+#pragma unroll
+        for (int n = 0; n <= PA; ++n) {
+          const T wn = w4[Four<PA>::p_n00(n)];
+          a0 = fma(wn, d3[n], a0);
+          h[n] = fma(wn, B[0], h[n]);
+        }
+      }
+      E = fma(c2, B[0], E);
+#pragma unroll
+      for (int n = 0; n <= PA; ++n) E = fma(h[n], d3[n], E);
+      Mono<PA>::d3_adjoint(B, h, a);
+      a[0] += a0;
+      if (m == 0) E += (T)c[0];
+      T* adst = sadj + a_loc * lay.AS + m * NAP;
+#pragma unroll
+      for (int x = 0; x < NAP; ++x) adst[x] = a[x];
+    }
+  }
+  se[lane] = E;
+  __syncwarp();
+  if (am && m == 0) {
+    T s = T(0);
+    for (int mm = 0; mm < K; ++mm) s += se[lane + mm];
+    p.Ei[atom0 + a_loc] = (double)s;
+  }
+
+  // ---------------- adjoint pair pass: g_ij = sum_{m,x} a_mx dB_mx/dr_ij  (Eq. 24c)
+  for (int ch = 0; ch < nchunks; ++ch) {
+    if (nchunks > 1) {
+      __syncwarp();
+      pair_pass<T, KT>(p, lay, geo, sR, sRp, scnt, atom0, A, K, ch, lane);
+      __syncwarp();
+    }
+    int tot = 0;
+    for (int a = 0; a < A; ++a) tot += chunk_count(scnt[a], ch);
+    for (int f = lane; f < tot; f += 32) {
+      int a = 0, base = 0;
+      for (; a < A; ++a) {
+        const int nca = chunk_count(scnt[a], ch);
+        if (f < base + nca) break;
+        base += nca;
+      }
+      const int jj = f - base, slot = ch * CH + jj, i = atom0 + a;
+      const Q4<T> u = geo[a * lay.GA + jj];
+      const T* Rrow = sR + a * lay.SA + jj * lay.KS;
+      const T* Rprow = sRp + a * lay.SA + jj * lay.KS;
+      T Am[NAP];
+      Mono<PA>::eval(u.x, u.y, u.z, Am);
+#pragma unroll
+      for (int x = NA; x < NAP; ++x) Am[x] = T(0);
+      T e[NAP];
+#pragma unroll
+      for (int x = 0; x < NAP; ++x) e[x] = T(0);
+      T ps = T(0);
+      const T* adj = sadj + a * lay.AS;
+#pragma unroll(KT == MAXK ? 1 : KT)
+      for (int mm = 0; mm < K; ++mm) {
+        const T Rm = Rrow[mm], Rpm = Rprow[mm];
+        const Q4<T>* a4 = reinterpret_cast<const Q4<T>*>(adj + mm * NAP);
+        T um = T(0);
+#pragma unroll
+        for (int x4 = 0; x4 < NAP / 4; ++x4) {
+          const Q4<T> av = a4[x4];
+          um = fma(av.x, Am[4 * x4 + 0], um);
+          um = fma(av.y, Am[4 * x4 + 1], um);
+          um = fma(av.z, Am[4 * x4 + 2], um);
+          um = fma(av.w, Am[4 * x4 + 3], um);
+          e[4 * x4 + 0] = fma(av.x, Rm, e[4 * x4 + 0]);
+          e[4 * x4 + 1] = fma(av.y, Rm, e[4 * x4 + 1]);
+          e[4 * x4 + 2] = fma(av.z, Rm, e[4 * x4 + 2]);
+          e[4 * x4 + 3] = fma(av.w, Rm, e[4 * x4 + 3]);
+        }
+        ps = fma(Rpm, um, ps);
+      }
+      T gx, gy, gz;
+      Mono<PA>::grad(e, Am, gx, gy, gz);
+      // dA/dr = (grad_u A - (u . grad_u A) u) / r for homogeneous A (Euler)
+      const T ug = u.x * gx + u.y * gy + u.z * gz;
+      const T ir = T(1) / u.w;
+      Q4<T> out;
+      out.x = fma(ps, u.x, (gx - ug * u.x) * ir);
+      out.y = fma(ps, u.y, (gy - ug * u.y) * ir);
+      out.z = fma(ps, u.z, (gz - ug * u.z) * ir);
+      out.w = T(0);
+      p.g[(size_t)i * p.cap + slot] = out;
+    }
+  }
+}
+
+// ------------------------------------------------------------------ layout
+template <typename T>
+AtomLayout make_layout(int K, int PA) {
+  AtomLayout L{};
+  const int NA = (PA + 1) * (PA + 2) * (PA + 3) / 6;
+  const int NAP = (NA + 3) / 4 * 4;
+  L.A = 32 / K;
+  L.KS = K | 1;
+  L.SA = CH * L.KS + K;
+  L.GA = CH + 1;
+  int AS = (K * NAP + 3) / 4 * 4;
+  if (((AS / 4) & 1) == 0) AS += 4;
+  L.AS = AS;
+  auto al = [](size_t v, size_t a) { return (v + a - 1) / a * a; };
+  size_t off = 0;
+  L.off_geo = off;
+  off = al(off + sizeof(Q4<T>) * (size_t)L.A * L.GA, 32);
+  L.off_R = off;
+  off = al(off + sizeof(T) * (size_t)L.A * L.SA, 32);
+  L.off_Rp = off;
+  off = al(off + sizeof(T) * (size_t)L.A * L.SA, 32);
+  L.off_adj = off;
+  off = al(off + sizeof(T) * (size_t)L.A * L.AS, 32);
+  L.off_e = off;
+  off = al(off + sizeof(T) * 32, 32);
+  L.off_cnt = off;
+  off = al(off + sizeof(int) * 32, 32);
+  L.warp_bytes = off;
+  return L;
+}
+
+template <typename T, int PA, bool HAS4, int MODE, int KT>
+static cudaError_t launch_one(const AtomArgs<T>& p, const AtomLayout& lay, cudaStream_t st) {
+  auto kern = atom_kernel<T, PA, HAS4, MODE, KT>;
+  const size_t smem = (size_t)WPB_ATOM * lay.warp_bytes;
+  // raise the dynamic shared-memory limit once per instantiation and size (not
+  // a stream operation, so it stays out of captured graphs after the first call)
+  static size_t granted = 0;
+  if (smem > granted) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    granted = smem;
+  }
+  const int atoms_per_block = WPB_ATOM * lay.A;
+  const int grid = (p.N + atoms_per_block - 1) / atoms_per_block;
+  if (grid > 0) kern<<<grid, WPB_ATOM * 32, smem, st>>>(p, lay);
+  return cudaGetLastError();
+}
+
+template <typename T, int MODE>
+static cudaError_t dispatch_generic(const AtomArgs<T>& p, const AtomLayout& lay, int PA, bool has4,
+                                    cudaStream_t st) {
+  switch (PA * 2 + (has4 ? 1 : 0)) {
+    case 0: return launch_one<T, 0, false, MODE, MAXK>(p, lay, st);
+    case 1: return launch_one<T, 0, true, MODE, MAXK>(p, lay, st);
+    case 2: return launch_one<T, 1, false, MODE, MAXK>(p, lay, st);
+    case 3: return launch_one<T, 1, true, MODE, MAXK>(p, lay, st);
+    case 4: return launch_one<T, 2, false, MODE, MAXK>(p, lay, st);
+    case 5: return launch_one<T, 2, true, MODE, MAXK>(p, lay, st);
+    case 6: return launch_one<T, 3, false, MODE, MAXK>(p, lay, st);
+    case 7: return launch_one<T, 3, true, MODE, MAXK>(p, lay, st);
+    case 8: return launch_one<T, 4, false, MODE, MAXK>(p, lay, st);
+    case 9: return launch_one<T, 4, true, MODE, MAXK>(p, lay, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+// Specialised instantiations for the two workloads the library is tuned for
+// (K = 3, P = 3, no 4-body; K = 6, P = 4, 4-body), generic K <= 16 otherwise.
+template <typename T>
+cudaError_t launch_atom_t(int mode, const AtomArgs<T>& p, int PA, bool has4, cudaStream_t st) {
+  const AtomLayout lay = make_layout<T>(p.K, PA);
+  const bool spec6 = (p.K == 6 && PA == 4 && has4);
+  const bool spec3 = (p.K == 3 && PA == 3 && !has4);
+  if (mode == 0) {
+    if (spec6) return launch_one<T, 4, true, 0, 6>(p, lay, st);
+    if (spec3) return launch_one<T, 3, false, 0, 3>(p, lay, st);
+    return dispatch_generic<T, 0>(p, lay, PA, has4, st);
+  }
+  if (spec6) return launch_one<T, 4, true, 1, 6>(p, lay, st);
+  if (spec3) return launch_one<T, 3, false, 1, 3>(p, lay, st);
+  return dispatch_generic<T, 1>(p, lay, PA, has4, st);
+}
+
+}  // namespace fastpod

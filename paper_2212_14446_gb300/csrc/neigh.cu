@@ -1,0 +1,295 @@
+// Cell-list neighbour builder: full list of every atom within r_cut, with
+// periodic images, sorted by (j, s_x, s_y, s_z); plus the reverse-pair index used
+// by the deterministic force gather.
+#include "pod_common.cuh"
+#include "pod_kernels.h"
+
+namespace fastpod {
+
+// One thread per atom: wrap into [0, L) (x - L floor(x / L), each operation
+// rounded separately), split into FP32 hi + lo, bin into a cell.
+__global__ void bin_kernel(int N, const double* __restrict__ pos, CellGrid cg, double* __restrict__ wpos,
+                           float4* __restrict__ phi, float4* __restrict__ plo, int* __restrict__ cell_count,
+                           int* __restrict__ cell_atoms, int* __restrict__ status) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  double x[3];
+  int c[3];
+  bool finite = true;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    double v = pos[(size_t)d * N + i];
+    finite = finite && isfinite(v);
+    if (cg.pbc[d]) v = __dsub_rn(v, __dmul_rn(cg.L[d], floor(__ddiv_rn(v, cg.L[d]))));
+    x[d] = v;
+    int ci = (int)floor(v * cg.inv_cs[d]);
+    ci = ci < 0 ? 0 : (ci >= cg.nc[d] ? cg.nc[d] - 1 : ci);
+    c[d] = finite ? ci : 0;
+    wpos[(size_t)d * N + i] = v;
+  }
+  if (!finite) atomicOr(status, ST_NONFINITE);
+  float h[3], l[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    h[d] = __double2float_rn(x[d]);
+    l[d] = __double2float_rn(x[d] - (double)h[d]);
+  }
+  phi[i] = make_float4(h[0], h[1], h[2], 0.f);
+  plo[i] = make_float4(l[0], l[1], l[2], 0.f);
+  const int cell = (c[2] * cg.nc[1] + c[1]) * cg.nc[0] + c[0];
+  const int slot = atomicAdd(&cell_count[cell], 1);
+  if (slot < cg.cap)
+    cell_atoms[(size_t)cell * cg.cap + slot] = i;
+  else
+    atomicOr(status, ST_CELL);
+}
+
+// Warp per atom.  Candidates of the (2S+1)^3 neighbouring cells are tested in
+// FP32 (double-float displacement); only those within a thin band around r_cut
+// are decided by the exact FP64 expression, so the list equals the FP64
+// definition bit for bit.  Hits are sorted by key (j, s) with a bitonic sort in
+// shared memory.
+__global__ void __launch_bounds__(WPB_NEIGH * 32)
+    neigh_kernel(int N, CellGrid cg, const double* __restrict__ wpos, const float4* __restrict__ phi,
+                 const float4* __restrict__ plo, const int* __restrict__ cell_count,
+                 const int* __restrict__ cell_atoms, double rc2, float rc2_lo, float rc2_hi, int cap,
+                 int keycap, int* __restrict__ nbr_count, int* __restrict__ nbr_j, int* __restrict__ nbr_s,
+                 int* __restrict__ status) {
+  extern __shared__ unsigned long long nsm[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  unsigned long long* keys = nsm + (size_t)warp * (keycap + 96);
+  int* off_cell = reinterpret_cast<int*>(keys + keycap);   // 32 entries
+  int* off_code = off_cell + 32;                            // 32 entries
+  int* off_pre = off_code + 32;                             // 33 entries (exclusive prefix)
+  const int i = blockIdx.x * WPB_NEIGH + warp;
+  if (i >= N) return;
+
+  const double xi0 = wpos[i], xi1 = wpos[(size_t)N + i], xi2 = wpos[(size_t)2 * N + i];
+  const float4 hi_i = phi[i], lo_i = plo[i];
+  int ci[3];
+  const double xi[3] = {xi0, xi1, xi2};
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    int c = (int)floor(xi[d] * cg.inv_cs[d]);
+    ci[d] = c < 0 ? 0 : (c >= cg.nc[d] ? cg.nc[d] - 1 : c);
+  }
+  const float Lh[3] = {(float)cg.L[0], (float)cg.L[1], (float)cg.L[2]};
+  const float Ll[3] = {(float)(cg.L[0] - (double)Lh[0]), (float)(cg.L[1] - (double)Lh[1]),
+                       (float)(cg.L[2] - (double)Lh[2])};
+  const int wx = 2 * cg.S[0] + 1, wy = 2 * cg.S[1] + 1, wz = 2 * cg.S[2] + 1;
+  const int noff = wx * wy * wz;
+  int nhit = 0;
+  for (int ob = 0; ob < noff; ob += 32) {
+    // lane -> one offset cell of this batch
+    const int o = ob + lane;
+    int cnt = 0, cell = 0, code = 0;
+    if (o < noff) {
+      const int ox = o % wx - cg.S[0];
+      const int oy = (o / wx) % wy - cg.S[1];
+      const int oz = o / (wx * wy) - cg.S[2];
+      const int oc[3] = {ox, oy, oz};
+      int tc[3], sh[3];
+      bool ok = true;
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        int t = ci[d] + oc[d];
+        int s = 0;
+        if (cg.pbc[d]) {
+          // floor division: t = tc + s * nc with 0 <= tc < nc
+          s = (t >= 0) ? t / cg.nc[d] : -((-t + cg.nc[d] - 1) / cg.nc[d]);
+          t -= s * cg.nc[d];
+        } else if (t < 0 || t >= cg.nc[d]) {
+          ok = false;
+        }
+        tc[d] = t;
+        sh[d] = s;
+      }
+      if (ok) {
+        cell = (tc[2] * cg.nc[1] + tc[1]) * cg.nc[0] + tc[0];
+        cnt = min(cell_count[cell], cg.cap);
+        code = shift_pack(sh[0], sh[1], sh[2]);
+      }
+    }
+    // exclusive scan of counts across the warp
+    int inc = cnt;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const int v = __shfl_up_sync(0xffffffffu, inc, d);
+      if (lane >= d) inc += v;
+    }
+    off_cell[lane] = cell;
+    off_code[lane] = code;
+    off_pre[lane] = inc - cnt;
+    const int total = __shfl_sync(0xffffffffu, inc, 31);
+    if (lane == 31) off_pre[32] = total;
+    __syncwarp();
+    for (int f0 = 0; f0 < total; f0 += 32) {
+      const int f = f0 + lane;
+      bool hit = false;
+      unsigned long long key = 0;
+      if (f < total) {
+        // binary search: largest o with off_pre[o] <= f
+        int lo = 0, hi = 31;
+        while (lo < hi) {
+          const int mid = (lo + hi + 1) >> 1;
+          if (off_pre[mid] <= f) lo = mid; else hi = mid - 1;
+        }
+        const int slot = f - off_pre[lo];
+        const int j = cell_atoms[(size_t)off_cell[lo] * cg.cap + slot];
+        const int code = off_code[lo];
+        int sx, sy, sz;
+        shift_unpack(code, sx, sy, sz);
+        if (!(j == i && sx == 0 && sy == 0 && sz == 0)) {
+          const float4 hj = phi[j], lj = plo[j];
+          const float dx = disp_f32(hi_i.x, lo_i.x, hj.x, lj.x, sx, Lh[0], Ll[0]);
+          const float dy = disp_f32(hi_i.y, lo_i.y, hj.y, lj.y, sy, Lh[1], Ll[1]);
+          const float dz = disp_f32(hi_i.z, lo_i.z, hj.z, lj.z, sz, Lh[2], Ll[2]);
+          const float r2f = dx * dx + dy * dy + dz * dz;
+          if (r2f < rc2_lo) {
+            hit = true;
+          } else if (r2f < rc2_hi) {
+            const double ddx = disp_fp64(xi0, wpos[j], sx, cg.L[0]);
+            const double ddy = disp_fp64(xi1, wpos[(size_t)N + j], sy, cg.L[1]);
+            const double ddz = disp_fp64(xi2, wpos[(size_t)2 * N + j], sz, cg.L[2]);
+            const double r2 = __dadd_rn(__dadd_rn(__dmul_rn(ddx, ddx), __dmul_rn(ddy, ddy)), __dmul_rn(ddz, ddz));
+            hit = r2 < rc2;
+          }
+          key = ((unsigned long long)j << 24) | (unsigned long long)code;
+        }
+      }
+      const unsigned m = __ballot_sync(0xffffffffu, hit);
+      if (hit) {
+        const int pos = nhit + __popc(m & ((1u << lane) - 1u));
+        if (pos < keycap) keys[pos] = key;
+      }
+      nhit += __popc(m);
+    }
+    __syncwarp();
+  }
+  const int n = min(nhit, keycap);
+  // bitonic sort of keys[0 .. np)
+  int np = 1;
+  while (np < n) np <<= 1;
+  for (int t = n + lane; t < np; t += 32) keys[t] = ~0ull;
+  __syncwarp();
+  for (int k = 2; k <= np; k <<= 1)
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int t = lane; t < np; t += 32) {
+        const int u = t ^ j;
+        if (u > t) {
+          const unsigned long long a = keys[t], b = keys[u];
+          const bool up = (t & k) == 0;
+          if ((a > b) == up) { keys[t] = b; keys[u] = a; }
+        }
+      }
+      __syncwarp();
+    }
+  const int nw = min(n, cap);
+  for (int t = lane; t < nw; t += 32) {
+    const unsigned long long key = keys[t];
+    nbr_j[(size_t)i * cap + t] = (int)(key >> 24);
+    nbr_s[(size_t)i * cap + t] = (int)(key & 0xFFFFFFull);
+  }
+  if (lane == 0) {
+    nbr_count[i] = nhit;
+    if (nhit > cap) atomicOr(status, ST_NEIGH);
+  }
+}
+
+// Thread per pair slot: index of the reverse pair (j, i, -s) in j's list.
+__global__ void rev_kernel(int N, int cap, const int* __restrict__ nbr_count, const int* __restrict__ nbr_j,
+                           const int* __restrict__ nbr_s, int* __restrict__ rev, int* __restrict__ status) {
+  const size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= (size_t)N * cap) return;
+  const int i = (int)(p / cap), t = (int)(p % cap);
+  const int ni = min(nbr_count[i], cap);
+  if (t >= ni) return;
+  const int j = nbr_j[p];
+  const unsigned long long target = ((unsigned long long)i << 24) | (unsigned long long)shift_negate(nbr_s[p]);
+  const int nj = min(nbr_count[j], cap);
+  const size_t base = (size_t)j * cap;
+  int lo = 0, hi = nj - 1, found = -1;
+  while (lo <= hi) {
+    const int mid = (lo + hi) >> 1;
+    const unsigned long long k =
+        ((unsigned long long)nbr_j[base + mid] << 24) | (unsigned long long)nbr_s[base + mid];
+    if (k == target) { found = mid; break; }
+    if (k < target) lo = mid + 1; else hi = mid - 1;
+  }
+  if (found < 0) {
+    atomicOr(status, ST_REV);
+    rev[p] = (int)p;  // contributes zero net force; status reports the inconsistency
+  } else {
+    rev[p] = (int)(base + found);
+  }
+}
+
+// Copy the internal list into the caller's [N][cap_out] / [N][cap_out][3] layout.
+__global__ void export_neighbors_kernel(int N, int cap, const int* __restrict__ nbr_count,
+                                        const int* __restrict__ nbr_j, const int* __restrict__ nbr_s, int cap_out,
+                                        int* __restrict__ count_out, int* __restrict__ j_out,
+                                        int* __restrict__ s_out) {
+  const size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= (size_t)N * cap_out) return;
+  const int i = (int)(p / cap_out), t = (int)(p % cap_out);
+  const int n = nbr_count[i];
+  if (t == 0) count_out[i] = n;
+  if (t >= min(n, cap)) return;
+  const int code = nbr_s[(size_t)i * cap + t];
+  int sx, sy, sz;
+  shift_unpack(code, sx, sy, sz);
+  j_out[p] = nbr_j[(size_t)i * cap + t];
+  s_out[3 * p] = sx;
+  s_out[3 * p + 1] = sy;
+  s_out[3 * p + 2] = sz;
+}
+
+// ------------------------------------------------------------ launchers
+cudaError_t launch_bin(int N, const double* pos, const CellGrid& cg, double* wpos, float4* phi, float4* plo,
+                       int* cell_count, int* cell_atoms, int* status, cudaStream_t st) {
+  const int tb = 256;
+  bin_kernel<<<(N + tb - 1) / tb, tb, 0, st>>>(N, pos, cg, wpos, phi, plo, cell_count, cell_atoms, status);
+  return cudaGetLastError();
+}
+
+size_t neigh_smem_bytes(int keycap) { return (size_t)WPB_NEIGH * (keycap + 96) * sizeof(unsigned long long); }
+
+cudaError_t launch_neigh(int N, const CellGrid& cg, const double* wpos, const float4* phi, const float4* plo,
+                         const int* cell_count, const int* cell_atoms, double rcut, int cap, int* nbr_count,
+                         int* nbr_j, int* nbr_s, int* status, cudaStream_t st) {
+  const double rc2 = rcut * rcut;
+  const float rc2_lo = (float)(rc2 * (1.0 - 1e-4));
+  const float rc2_hi = (float)(rc2 * (1.0 + 1e-4));
+  int keycap = 32;
+  while (keycap < cap) keycap <<= 1;
+  const size_t smem = neigh_smem_bytes(keycap);
+  static size_t granted = 48 * 1024;
+  if (smem > granted) {
+    cudaError_t e = cudaFuncSetAttribute(neigh_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    granted = smem;
+  }
+  neigh_kernel<<<(N + WPB_NEIGH - 1) / WPB_NEIGH, WPB_NEIGH * 32, smem, st>>>(
+      N, cg, wpos, phi, plo, cell_count, cell_atoms, rc2, rc2_lo, rc2_hi, cap, keycap, nbr_count, nbr_j, nbr_s,
+      status);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rev(int N, int cap, const int* nbr_count, const int* nbr_j, const int* nbr_s, int* rev,
+                       int* status, cudaStream_t st) {
+  const size_t tot = (size_t)N * cap;
+  const int tb = 256;
+  rev_kernel<<<(unsigned)((tot + tb - 1) / tb), tb, 0, st>>>(N, cap, nbr_count, nbr_j, nbr_s, rev, status);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_export_neighbors(int N, int cap, const int* nbr_count, const int* nbr_j, const int* nbr_s,
+                                    int cap_out, int* count_out, int* j_out, int* s_out, cudaStream_t st) {
+  const size_t tot = (size_t)N * cap_out;
+  const int tb = 256;
+  export_neighbors_kernel<<<(unsigned)((tot + tb - 1) / tb), tb, 0, st>>>(N, cap, nbr_count, nbr_j, nbr_s,
+                                                                           cap_out, count_out, j_out, s_out);
+  return cudaGetLastError();
+}
+
+}  // namespace fastpod

@@ -1,0 +1,762 @@
+// C ABI of the fastpod library: handle life cycle, POD basis, workspace and the
+// orchestration of the neighbour / atom / gather / reduce kernels.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/pod.h"
+#include "pod_common.cuh"
+#include "pod_internal.h"
+#include "pod_kernels.h"
+
+using namespace fastpod;
+
+// ============================================================ small helpers
+namespace {
+
+int num_partitions_upto(int P) {
+  int cnt = 0;
+  for (int n = 0; n <= P; ++n)
+    for (int a = n; a >= 0; --a)
+      for (int b = std::min(a, n - a); b >= 0; --b) {
+        const int c = n - a - b;
+        if (c >= 0 && c <= b) ++cnt;
+      }
+  return cnt;
+}
+
+// Radial snapshots Phi_l(r) on the host, FP64 (Eq. 3-11), rows ordered
+// phi(alpha_a, beta_b) for a (outer), b (inner), then varphi(gamma_g).
+void host_snapshots(const HostParams& P, double r, double* out) {
+  const double h = P.r_cut - P.r_in;
+  const double s = r - P.r_in;
+  const double t = s / h;
+  const double u = 1.0 - t * t * t;
+  const double fc = std::exp(1.0 - 1.0 / std::sqrt(u * u + 1e-6));
+  int row = 0;
+  for (size_t a = 0; a < P.alpha.size(); ++a)
+    for (size_t b = 0; b < P.beta.size(); ++b) {
+      const double x = (std::exp(-P.beta[b] * t) - 1.0) / (std::exp(-P.beta[b]) - 1.0);
+      out[row++] = fc * std::sin(P.alpha[a] * M_PI * x) / s;
+    }
+  for (size_t g = 0; g < P.gamma.size(); ++g) out[row++] = fc * std::pow(r, -P.gamma[g]);
+}
+
+// POD of the snapshot family (Section 2.2, Eq. 12): one-sided (Hestenes)
+// Jacobi on X = sqrt(h) Phi (n_grid x Ns); the right singular vectors are the
+// eigenvectors of C = X^T X and sigma^2 its eigenvalues.  Sorted descending,
+// largest-magnitude entry positive, Q_lk = v_lk / sigma_k.
+int pod_basis(const HostParams& P, int n_grid, int K, std::vector<double>& Q, std::vector<double>& eig) {
+  const int Ns = (int)(P.alpha.size() * P.beta.size() + P.gamma.size());
+  const double h = (P.r_cut - P.r_in) / n_grid;
+  std::vector<double> X((size_t)Ns * n_grid);  // column-major: column a = snapshot a
+  std::vector<double> row(Ns);
+  for (int g = 0; g < n_grid; ++g) {
+    host_snapshots(P, P.r_in + (g + 0.5) * h, row.data());
+    for (int a = 0; a < Ns; ++a) X[(size_t)a * n_grid + g] = std::sqrt(h) * row[a];
+  }
+  std::vector<double> V((size_t)Ns * Ns, 0.0);
+  for (int a = 0; a < Ns; ++a) V[(size_t)a * Ns + a] = 1.0;  // column-major too
+  for (int sweep = 0; sweep < 60; ++sweep) {
+    bool rotated = false;
+    for (int a = 0; a < Ns - 1; ++a)
+      for (int b = a + 1; b < Ns; ++b) {
+        double* xa = &X[(size_t)a * n_grid];
+        double* xb = &X[(size_t)b * n_grid];
+        double al = 0, be = 0, ga = 0;
+        for (int g = 0; g < n_grid; ++g) {
+          al += xa[g] * xa[g];
+          be += xb[g] * xb[g];
+          ga += xa[g] * xb[g];
+        }
+        if (ga == 0.0 || std::fabs(ga) <= 1e-15 * std::sqrt(al * be)) continue;
+        rotated = true;
+        const double zeta = (be - al) / (2.0 * ga);
+        const double t = (zeta >= 0 ? 1.0 : -1.0) / (std::fabs(zeta) + std::sqrt(1.0 + zeta * zeta));
+        const double c = 1.0 / std::sqrt(1.0 + t * t), s = c * t;
+        for (int g = 0; g < n_grid; ++g) {
+          const double p = xa[g], q = xb[g];
+          xa[g] = c * p - s * q;
+          xb[g] = s * p + c * q;
+        }
+        double* va = &V[(size_t)a * Ns];
+        double* vb = &V[(size_t)b * Ns];
+        for (int l = 0; l < Ns; ++l) {
+          const double p = va[l], q = vb[l];
+          va[l] = c * p - s * q;
+          vb[l] = s * p + c * q;
+        }
+      }
+    if (!rotated) break;
+  }
+  std::vector<double> lam(Ns);
+  for (int a = 0; a < Ns; ++a) {
+    double s2 = 0;
+    for (int g = 0; g < n_grid; ++g) s2 += X[(size_t)a * n_grid + g] * X[(size_t)a * n_grid + g];
+    lam[a] = s2;
+  }
+  std::vector<int> idx(Ns);
+  for (int a = 0; a < Ns; ++a) idx[a] = a;
+  std::stable_sort(idx.begin(), idx.end(), [&](int x, int y) { return lam[x] > lam[y]; });
+  eig.assign(Ns, 0.0);
+  Q.assign((size_t)Ns * K, 0.0);
+  for (int k = 0; k < Ns; ++k) eig[k] = lam[idx[k]];
+  for (int k = 0; k < K; ++k) {
+    const int col = idx[k];
+    if (!(lam[col] > 0)) return -1;
+    const double* v = &V[(size_t)col * Ns];
+    int am = 0;
+    for (int l = 1; l < Ns; ++l)
+      if (std::fabs(v[l]) > std::fabs(v[am])) am = l;
+    const double sc = (v[am] < 0 ? -1.0 : 1.0) / std::sqrt(lam[col]);
+    for (int l = 0; l < Ns; ++l) Q[(size_t)l * K + k] = v[l] * sc;
+  }
+  return 0;
+}
+
+// Phi_l(r) and dPhi_l/dr on the host, FP64, same row order as host_snapshots.
+void host_snapshots_d(const HostParams& P, double r, double* phi, double* dphi) {
+  const double h = P.r_cut - P.r_in;
+  const double s = r - P.r_in;
+  const double t = s / h;
+  const double u = 1.0 - t * t * t;
+  const double y = u * u + 1e-6;
+  const double fc = std::exp(1.0 - 1.0 / std::sqrt(y));
+  const double dfc = fc * (u * (-3.0 * t * t / h)) / (y * std::sqrt(y));
+  int row = 0;
+  for (size_t a = 0; a < P.alpha.size(); ++a)
+    for (size_t b = 0; b < P.beta.size(); ++b) {
+      const double be = P.beta[b], al = P.alpha[a];
+      const double em1 = std::exp(-be) - 1.0, et = std::exp(-be * t);
+      const double x = (et - 1.0) / em1, dx = -be / h * et / em1;
+      const double sn = std::sin(al * M_PI * x), cs = std::cos(al * M_PI * x);
+      const double f = sn / s, df = (al * M_PI * cs * dx * s - sn) / (s * s);
+      phi[row] = fc * f;
+      dphi[row] = dfc * f + fc * df;
+      ++row;
+    }
+  for (size_t g = 0; g < P.gamma.size(); ++g) {
+    const double f = std::pow(r, -P.gamma[g]), df = -P.gamma[g] * f / r;
+    phi[row] = fc * f;
+    dphi[row] = dfc * f + fc * df;
+    ++row;
+  }
+}
+
+bool is_seq(const std::vector<double>& v) {
+  for (size_t i = 0; i < v.size(); ++i)
+    if (v[i] != (double)(i + 1)) return false;
+  return true;
+}
+
+template <typename T>
+void fill_radial(const pod_handle* h, RadialConst<T>& rc) {
+  std::memset(&rc, 0, sizeof(rc));
+  const HostParams& P = h->P;
+  rc.r_in = (T)P.r_in;
+  rc.inv_h = (T)(1.0 / (P.r_cut - P.r_in));
+  rc.n_alpha = (int)P.alpha.size();
+  rc.n_beta = (int)P.beta.size();
+  rc.n_gamma = (int)P.gamma.size();
+  rc.K = h->K;
+  for (int a = 0; a < rc.n_alpha; ++a) rc.alpha[a] = (T)P.alpha[a];
+  for (int b = 0; b < rc.n_beta; ++b) {
+    rc.beta[b] = (T)P.beta[b];
+    rc.inv_ebm1[b] = (T)(1.0 / (std::exp(-P.beta[b]) - 1.0));
+  }
+  for (int g = 0; g < rc.n_gamma; ++g) rc.gamma[g] = (T)P.gamma[g];
+  for (int l = 0; l < h->Ns; ++l)
+    for (int k = 0; k < h->K; ++k) rc.Q[l][k] = (T)h->Q[(size_t)l * h->K + k];
+  rc.alpha_seq = is_seq(P.alpha) ? 1 : 0;
+  rc.gamma_seq = is_seq(P.gamma) ? 1 : 0;
+}
+
+}  // namespace
+
+// ============================================================ handle helpers
+int pod_handle::fail(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  err = buf;
+  return code;
+}
+
+int pod_handle::cuda_fail(cudaError_t e, const char* what) {
+  return fail(POD_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+int pod_handle::ensure(DevBuf& b, size_t bytes, const char* what) {
+  if (bytes <= b.bytes && b.p) return POD_OK;
+  if (b.p) {
+    cudaFree(b.p);
+    b.p = nullptr;
+    b.bytes = 0;
+  }
+  size_t nb = std::max<size_t>(bytes, 256);
+  nb = nb + nb / 4;
+  cudaError_t e = cudaMalloc(&b.p, nb);
+  if (e != cudaSuccess) {
+    b.p = nullptr;
+    cudaGetLastError();
+    return fail(POD_ENOMEM, "cudaMalloc(%zu) for %s failed: %s", nb, what, cudaGetErrorString(e));
+  }
+  b.bytes = nb;
+  return POD_OK;
+}
+
+pod_handle::~pod_handle() {
+  for (DevBuf* b : all_bufs()) {
+    if (b->p) cudaFree(b->p);
+    b->p = nullptr;
+  }
+  if (h_status) cudaFreeHost(h_status);
+  for (cudaEvent_t& e : ev)
+    if (e) cudaEventDestroy(e);
+}
+
+int pod_handle::mark(int k, cudaStream_t st) {
+  if (!timing) return POD_OK;
+  if (!ev[k]) {
+    cudaError_t e = cudaEventCreate(&ev[k]);
+    if (e != cudaSuccess) return cuda_fail(e, "event create");
+  }
+  cudaError_t e = cudaEventRecord(ev[k], st);
+  if (e != cudaSuccess) return cuda_fail(e, "event record");
+  return POD_OK;
+}
+
+int pod_handle::timing_collect() {
+  if (!timing) return POD_OK;
+  cudaError_t e = cudaEventSynchronize(ev[4]);
+  if (e != cudaSuccess) return cuda_fail(e, "event sync");
+  for (int k = 0; k < 4; ++k) {
+    float ms = 0.f;
+    e = cudaEventElapsedTime(&ms, ev[k], ev[k + 1]);
+    if (e != cudaSuccess) return cuda_fail(e, "event elapsed");
+    t_acc[k] += ms;
+  }
+  ++t_calls;
+  return POD_OK;
+}
+
+std::vector<DevBuf*> pod_handle::all_bufs() {
+  return {&cell_count, &cell_atoms, &wpos, &phi, &plo, &nbr_count, &nbr_j, &nbr_s, &rev, &g, &Ei,
+          &Wat, &status, &offs, &pos_in, &c_in, &E_out, &F_out, &W_out, &Ei_out, &fitA, &fitG, &fitb,
+          &fitwork, &cfg_of, &boxes, &rtab};
+}
+
+// ============================================================ C ABI
+extern "C" {
+
+int pod_create(const pod_params* prm, pod_handle** out) {
+  if (!out) return POD_EINVAL;
+  *out = nullptr;
+  if (!prm) return POD_EINVAL;
+  pod_handle* h = new (std::nothrow) pod_handle();
+  if (!h) return POD_ENOMEM;
+  auto bad = [&](const char* msg) {
+    h->err = msg;
+    int code = POD_EINVAL;
+    // keep the handle alive so the caller can read the message
+    *out = h;
+    return code;
+  };
+  if (!(prm->r_in > 0) || !(prm->r_cut > prm->r_in)) return bad("require 0 < r_in < r_cut");
+  if (prm->n_alpha < 1 || prm->n_alpha > MAXA || !prm->alpha) return bad("n_alpha must be in 1..8");
+  if (prm->n_beta < 1 || prm->n_beta > MAXB || !prm->beta) return bad("n_beta must be in 1..2");
+  if (prm->n_gamma < 0 || prm->n_gamma > MAXG || (prm->n_gamma > 0 && !prm->gamma))
+    return bad("n_gamma must be in 0..8");
+  for (int b = 0; b < prm->n_beta; ++b)
+    if (!(prm->beta[b] > 0)) return bad("every beta must be > 0");
+  if (prm->P3 < -1 || prm->P3 > PAMAX || prm->P4 < -1 || prm->P4 > PAMAX)
+    return bad("P3 and P4 must be in -1..4");
+  if (prm->K2 < 0 || prm->K3 < 0 || prm->K4 < 0 || prm->K2 > MAXK || prm->K3 > MAXK || prm->K4 > MAXK)
+    return bad("K2, K3, K4 must be in 0..16");
+  if (prm->precision != POD_FP64 && prm->precision != POD_MIXED) return bad("precision must be POD_FP64 or POD_MIXED");
+  HostParams& P = h->P;
+  P.r_in = prm->r_in;
+  P.r_cut = prm->r_cut;
+  P.alpha.assign(prm->alpha, prm->alpha + prm->n_alpha);
+  P.beta.assign(prm->beta, prm->beta + prm->n_beta);
+  if (prm->n_gamma) P.gamma.assign(prm->gamma, prm->gamma + prm->n_gamma);
+  P.K2 = prm->K2;
+  P.P3 = prm->P3;
+  P.P4 = prm->P4;
+  P.K3 = prm->P3 >= 0 ? prm->K3 : 0;
+  P.K4 = prm->P4 >= 0 ? prm->K4 : 0;
+  h->precision = prm->precision;
+  h->Ns = prm->n_alpha * prm->n_beta + prm->n_gamma;
+  h->K = std::max(P.K2, std::max(P.K3, P.K4));
+  if (h->K < 1) return bad("at least one of K2, K3, K4 must be positive");
+  if (h->K > h->Ns) return bad("radial modes K must not exceed the number of snapshots");
+  h->PA = std::max(0, std::max(P.P3, P.P4));
+  h->KA4 = P.P4 >= 0 ? num_partitions_upto(P.P4) : 0;
+  h->M = 1 + P.K2 + P.K3 * (P.P3 + 1) + P.K4 * h->KA4;
+  const int n_grid = prm->n_grid > 0 ? prm->n_grid : 2000;
+  if (n_grid < h->Ns) return bad("n_grid must be at least Ns");
+  if (prm->Q) {
+    h->Q.assign(prm->Q, prm->Q + (size_t)h->Ns * h->K);
+    h->eig.assign(h->Ns, 0.0);
+  } else if (pod_basis(P, n_grid, h->K, h->Q, h->eig) != 0) {
+    return bad("POD basis: snapshot family is rank deficient for the requested K");
+  }
+  fill_radial<float>(h, h->rad32);
+  fill_radial<double>(h, h->rad64);
+  *out = h;
+  return POD_OK;
+}
+
+int pod_destroy(pod_handle* h) {
+  delete h;
+  return POD_OK;
+}
+
+int pod_info(const pod_handle* h, int* M, int* Ns, int* K, double* Q_out, double* eig_out) {
+  if (!h) return POD_EINVAL;
+  if (M) *M = h->M;
+  if (Ns) *Ns = h->Ns;
+  if (K) *K = h->K;
+  if (Q_out && !h->Q.empty()) std::memcpy(Q_out, h->Q.data(), sizeof(double) * h->Q.size());
+  if (eig_out && !h->eig.empty()) std::memcpy(eig_out, h->eig.data(), sizeof(double) * h->eig.size());
+  return POD_OK;
+}
+
+int pod_set_option(pod_handle* h, int option, int value) {
+  if (!h) return POD_EINVAL;
+  if (option == POD_OPT_SYNC) {
+    h->sync = value ? 1 : 0;
+    return POD_OK;
+  }
+  if (option == POD_OPT_RADIAL) {
+    if (value != 0 && value != 1) return h->fail(POD_EINVAL, "radial mode must be 0 (table) or 1 (direct)");
+    h->radial_mode = value;
+    return POD_OK;
+  }
+  if (option == POD_OPT_TIMING) {
+    h->timing = value ? 1 : 0;
+    return POD_OK;
+  }
+  if (option == POD_OPT_PRECISION) {
+    if (value != POD_FP64 && value != POD_MIXED) return h->fail(POD_EINVAL, "precision must be POD_FP64 or POD_MIXED");
+    h->precision = value;
+    return POD_OK;
+  }
+  return h->fail(POD_EINVAL, "unknown option %d", option);
+}
+
+const char* pod_last_error(const pod_handle* h) { return h ? h->err.c_str() : "null handle"; }
+
+int pod_timing(pod_handle* h, double* ms, int* calls) {
+  if (!h) return POD_EINVAL;
+  if (ms)
+    for (int k = 0; k < 4; ++k) ms[k] = h->t_acc[k];
+  if (calls) *calls = h->t_calls;
+  for (int k = 0; k < 4; ++k) h->t_acc[k] = 0;
+  h->t_calls = 0;
+  return POD_OK;
+}
+
+int pod_status(pod_handle* h, void* stream) {
+  if (!h) return POD_EINVAL;
+  return h->read_status((cudaStream_t)stream);
+}
+
+}  // extern "C"
+
+// ============================================================ orchestration
+int pod_handle::read_status(cudaStream_t st) {
+  if (!status.p) return POD_OK;
+  if (!h_status) {
+    cudaError_t ea = cudaMallocHost(&h_status, sizeof(int) * 4);
+    if (ea != cudaSuccess) {
+      h_status = nullptr;
+      return cuda_fail(ea, "pinned status word");
+    }
+  }
+  cudaError_t e = cudaMemcpyAsync(h_status, status.p, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(e, "status read");
+  const int s = *h_status;
+  last_status = s;
+  e = cudaMemsetAsync(status.p, 0, sizeof(int), st);
+  if (e != cudaSuccess) return cuda_fail(e, "status clear");
+  if (s & (ST_NEIGH | ST_CELL)) return fail(POD_ENEIGH, "neighbour or cell capacity exceeded (status 0x%x)", s);
+  if (s & ST_REV) return fail(POD_ENEIGH, "neighbour list is not symmetric (status 0x%x)", s);
+  if (s & ST_NONFINITE) return fail(POD_ENONFINITE, "non-finite positions or results");
+  if (s & ST_RANGE) return fail(POD_ERANGE, "a pair is closer than r_in");
+  return POD_OK;
+}
+
+int pod_handle::plan_single(int N, const double box[3], const int pbc[3], Plan& pl) {
+  const double rc = P.r_cut;
+  pl.N = N;
+  double vol = 1.0;
+  long long ncells = 1;
+  for (int d = 0; d < 3; ++d) {
+    CellGrid& cg = pl.cg;
+    cg.pbc[d] = pbc[d] ? 1 : 0;
+    double L = box[d];
+    if (pbc[d] && !(L > 0)) return fail(POD_EINVAL, "periodic direction %d needs a positive box length", d);
+    if (!(L >= 0) || !std::isfinite(L)) return fail(POD_EINVAL, "box length %d is not finite", d);
+    cg.L[d] = L;
+    int nc = L > 0 ? (int)std::floor(L / (rc * (1.0 + 1e-9))) : 1;
+    nc = std::max(1, std::min(nc, 1024));
+    cg.nc[d] = nc;
+    const double cs = L > 0 ? L / nc : 0.0;
+    cg.inv_cs[d] = L > 0 ? nc / L : 0.0;
+    if (pbc[d])
+      cg.S[d] = (int)std::ceil(rc / cs * (1.0 + 1e-12));
+    else
+      cg.S[d] = nc > 1 ? 1 : 0;
+    if (pbc[d] && cg.S[d] > 60) return fail(POD_EINVAL, "box length %d too small for r_cut", d);
+    ncells *= nc;
+    vol *= std::max(L, rc);
+  }
+  // keep the cell count modest for sparse systems
+  while (ncells > 8LL * N + 64) {
+    int dmax = 0;
+    for (int d = 1; d < 3; ++d)
+      if (pl.cg.nc[d] > pl.cg.nc[dmax]) dmax = d;
+    CellGrid& cg = pl.cg;
+    ncells /= cg.nc[dmax];
+    cg.nc[dmax] = std::max(1, cg.nc[dmax] / 2);
+    ncells *= cg.nc[dmax];
+    const double cs = cg.L[dmax] / cg.nc[dmax];
+    cg.inv_cs[dmax] = cg.nc[dmax] / cg.L[dmax];
+    cg.S[dmax] = cg.pbc[dmax] ? (int)std::ceil(rc / cs * (1.0 + 1e-12)) : (cg.nc[dmax] > 1 ? 1 : 0);
+  }
+  pl.cg.ncells = (int)ncells;
+  const double expect_cell = (double)N / ncells;
+  int capc = (int)(2.0 * expect_cell + 16);
+  capc = (capc + 15) / 16 * 16;
+  pl.cg.cap = std::max(capc, cap_cell);
+  const double expect = N / vol * (4.0 / 3.0) * M_PI * rc * rc * rc;
+  int cap = (int)(1.5 * expect + 16);
+  cap = (cap + 7) / 8 * 8;
+  pl.cap = std::max(std::max(cap, 16), cap_nbr);
+  return POD_OK;
+}
+
+int pod_handle::build_neighbors(const double* pos, Plan& pl, bool need_rev, cudaStream_t st) {
+  const int N = pl.N;
+  int rc_;
+  if ((rc_ = ensure(cell_count, sizeof(int) * (size_t)pl.cg.ncells, "cell counts"))) return rc_;
+  if ((rc_ = ensure(cell_atoms, sizeof(int) * (size_t)pl.cg.ncells * pl.cg.cap, "cell atoms"))) return rc_;
+  if ((rc_ = ensure(wpos, sizeof(double) * 3 * (size_t)N, "wrapped positions"))) return rc_;
+  if ((rc_ = ensure(phi, sizeof(float4) * (size_t)N, "positions hi"))) return rc_;
+  if ((rc_ = ensure(plo, sizeof(float4) * (size_t)N, "positions lo"))) return rc_;
+  if ((rc_ = ensure(nbr_count, sizeof(int) * (size_t)N, "neighbour counts"))) return rc_;
+  if ((rc_ = ensure(nbr_j, sizeof(int) * (size_t)N * pl.cap, "neighbour list"))) return rc_;
+  if ((rc_ = ensure(nbr_s, sizeof(int) * (size_t)N * pl.cap, "neighbour shifts"))) return rc_;
+  if (!status.p) {
+    // the status word accumulates device conditions until read_status() reads and clears it
+    if ((rc_ = ensure(status, sizeof(int) * 4, "status"))) return rc_;
+    cudaError_t e0 = cudaMemset(status.p, 0, sizeof(int) * 4);
+    if (e0 != cudaSuccess) return cuda_fail(e0, "status init");
+  }
+  cudaError_t e = cudaMemsetAsync(cell_count.p, 0, sizeof(int) * (size_t)pl.cg.ncells, st);
+  if (e != cudaSuccess) return cuda_fail(e, "cell count clear");
+  e = launch_bin(N, pos, pl.cg, (double*)wpos.p, (float4*)phi.p, (float4*)plo.p, (int*)cell_count.p,
+                 (int*)cell_atoms.p, (int*)status.p, st);
+  if (e != cudaSuccess) return cuda_fail(e, "bin kernel");
+  e = launch_neigh(N, pl.cg, (const double*)wpos.p, (const float4*)phi.p, (const float4*)plo.p,
+                   (const int*)cell_count.p, (const int*)cell_atoms.p, P.r_cut, pl.cap, (int*)nbr_count.p,
+                   (int*)nbr_j.p, (int*)nbr_s.p, (int*)status.p, st);
+  if (e != cudaSuccess) return cuda_fail(e, "neighbour kernel");
+  if (need_rev) {
+    if ((rc_ = ensure(rev, sizeof(int) * (size_t)N * pl.cap, "reverse index"))) return rc_;
+    e = launch_rev(N, pl.cap, (const int*)nbr_count.p, (const int*)nbr_j.p, (const int*)nbr_s.p, (int*)rev.p,
+                   (int*)status.p, st);
+    if (e != cudaSuccess) return cuda_fail(e, "reverse-index kernel");
+  }
+  return POD_OK;
+}
+
+template <typename T>
+void pod_handle::fill_args(AtomArgs<T>& a, const Plan& pl) {
+  std::memset(&a, 0, sizeof(a));
+  a.N = pl.N;
+  a.cap = pl.cap;
+  a.nbr_count = (const int*)nbr_count.p;
+  a.nbr_j = (const int*)nbr_j.p;
+  a.nbr_s = (const int*)nbr_s.p;
+  a.wpos = (const double*)wpos.p;
+  a.phi = (const float4*)phi.p;
+  a.plo = (const float4*)plo.p;
+  for (int d = 0; d < 3; ++d) {
+    a.L[d] = pl.cg.L[d];
+    a.Lh[d] = (float)pl.cg.L[d];
+    a.Ll[d] = (float)(pl.cg.L[d] - (double)a.Lh[d]);
+  }
+  a.K = K;
+  a.K2 = P.K2;
+  a.K3 = P.K3;
+  a.K4 = P.K4;
+  a.P3 = P.P3;
+  a.P4 = P.P4;
+  a.KA4 = KA4;
+  a.M = M;
+  a.col3 = 1 + P.K2;
+  a.col4 = a.col3 + P.K3 * (P.P3 + 1);
+  a.status = (int*)status.p;
+}
+
+// Cubic Hermite pieces of R_k on TAB_N equal intervals of (r_in, r_cut), from
+// FP64 values and derivatives of the snapshot projection at the nodes (the first
+// node is taken 1e-4 h inside the interval, where phi has its removable 0/0).
+int pod_handle::ensure_table(cudaStream_t st) {
+  if (tab_ready) return POD_OK;
+  const int n = TAB_N;
+  const double h = (P.r_cut - P.r_in) / n;
+  std::vector<double> R((size_t)(n + 1) * K), dR((size_t)(n + 1) * K), phi(Ns), dphi(Ns);
+  for (int g = 0; g <= n; ++g) {
+    double r = P.r_in + g * h;
+    if (g == 0) r += 1e-4 * h;
+    host_snapshots_d(P, r, phi.data(), dphi.data());
+    for (int k = 0; k < K; ++k) {
+      double a = 0, b = 0;
+      for (int l = 0; l < Ns; ++l) {
+        a += Q[(size_t)l * K + k] * phi[l];
+        b += Q[(size_t)l * K + k] * dphi[l];
+      }
+      R[(size_t)g * K + k] = a;
+      dR[(size_t)g * K + k] = b;
+    }
+  }
+  std::vector<Q4<float>> tab((size_t)n * K);
+  for (int g = 0; g < n; ++g)
+    for (int k = 0; k < K; ++k) {
+      const double f0 = R[(size_t)g * K + k], f1 = R[(size_t)(g + 1) * K + k];
+      const double d0 = h * dR[(size_t)g * K + k], d1 = h * dR[(size_t)(g + 1) * K + k];
+      Q4<float>& q = tab[(size_t)g * K + k];
+      q.x = (float)f0;
+      q.y = (float)d0;
+      q.z = (float)(3.0 * (f1 - f0) - 2.0 * d0 - d1);
+      q.w = (float)(2.0 * (f0 - f1) + d0 + d1);
+    }
+  int rc_;
+  if ((rc_ = ensure(rtab, sizeof(Q4<float>) * tab.size(), "radial table"))) return rc_;
+  cudaError_t e = cudaMemcpy(rtab.p, tab.data(), sizeof(Q4<float>) * tab.size(), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return cuda_fail(e, "radial table upload");
+  (void)st;
+  tab_ready = true;
+  return POD_OK;
+}
+
+int pod_handle::run_atoms(int mode, const Plan& pl, double* D, const double* c, double* Ei_dst, cudaStream_t st) {
+  cudaError_t e;
+  const bool has4 = P.P4 >= 0;
+  if (precision == POD_MIXED) {
+    AtomArgs<float> a;
+    fill_args(a, pl);
+    a.rad = rad32;
+    if (radial_mode == 0) {
+      int rc_ = ensure_table(st);
+      if (rc_) return rc_;
+      a.rad.tab = (const Q4<float>*)rtab.p;
+      a.rad.tab_inv_h = (float)(TAB_N / (P.r_cut - P.r_in));
+      a.rad.tab_n = TAB_N;
+    }
+    a.D = D;
+    a.c = c;
+    a.Ei = Ei_dst;
+    a.g = (Q4<float>*)g.p;
+    e = launch_atom_f32(mode, a, PA, has4, st);
+  } else {
+    AtomArgs<double> a;
+    fill_args(a, pl);
+    a.rad = rad64;
+    a.D = D;
+    a.c = c;
+    a.Ei = Ei_dst;
+    a.g = (Q4<double>*)g.p;
+    e = launch_atom_f64(mode, a, PA, has4, st);
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "atom kernel");
+  return POD_OK;
+}
+
+int pod_handle::finish(cudaStream_t st, Plan& pl, bool& retry) {
+  retry = false;
+  if (!sync) return POD_OK;
+  int rc_ = read_status(st);
+  if (rc_ == POD_ENEIGH && (last_status & (ST_NEIGH | ST_CELL)) && retries < 4) {
+    if (last_status & ST_NEIGH) cap_nbr = std::max(cap_nbr, pl.cap * 2);
+    if (last_status & ST_CELL) cap_cell = std::max(cap_cell, pl.cg.cap * 2);
+    ++retries;
+    retry = true;
+    err.clear();
+    return POD_OK;
+  }
+  return rc_;
+}
+
+int pod_handle::validate_system(const pod_system* sys) {
+  if (!sys) return fail(POD_EINVAL, "system is NULL");
+  if (sys->n_atoms < 1) return fail(POD_EINVAL, "n_atoms must be >= 1");
+  if (!sys->pos) return fail(POD_EINVAL, "positions are NULL");
+  if (sys->n_configs > 1) return fail(POD_EINVAL, "batched systems are only supported by pod_fit");
+  return POD_OK;
+}
+
+int pod_handle::energy_forces(const pod_system* sys, const double* c, double* E, double* Ei_user, double* F,
+                              double* W, cudaStream_t st) {
+  int rc_ = validate_system(sys);
+  if (rc_) return rc_;
+  if (!c || !E) return fail(POD_EINVAL, "c and E are required");
+  const int N = sys->n_atoms;
+  retries = 0;
+  for (;;) {
+    Plan pl;
+    if ((rc_ = plan_single(N, sys->box, sys->pbc, pl))) return rc_;
+    if ((rc_ = mark(0, st))) return rc_;
+    if ((rc_ = build_neighbors(sys->pos, pl, true, st))) return rc_;
+    const size_t gbytes = (precision == POD_MIXED ? sizeof(Q4<float>) : sizeof(Q4<double>)) * (size_t)N * pl.cap;
+    if ((rc_ = ensure(g, gbytes, "pair gradients"))) return rc_;
+    if ((rc_ = ensure(Wat, sizeof(double) * 9 * (size_t)N, "atom virials"))) return rc_;
+    double* Ei_dst = Ei_user;
+    if (!Ei_dst) {
+      if ((rc_ = ensure(Ei, sizeof(double) * (size_t)N, "atom energies"))) return rc_;
+      Ei_dst = (double*)Ei.p;
+    }
+    if ((rc_ = ensure(offs, sizeof(int) * 2, "config offsets"))) return rc_;
+    if (offs_n != N) {
+      int ho[2] = {0, N};
+      cudaError_t e = cudaMemcpy(offs.p, ho, sizeof(ho), cudaMemcpyHostToDevice);
+      if (e != cudaSuccess) return cuda_fail(e, "offset upload");
+      offs_n = N;
+    }
+    if ((rc_ = mark(1, st))) return rc_;
+    if ((rc_ = run_atoms(1, pl, nullptr, c, Ei_dst, st))) return rc_;
+    if ((rc_ = mark(2, st))) return rc_;
+    cudaError_t e;
+    if (precision == POD_MIXED)
+      e = launch_gather<float>(N, pl.cap, (const int*)nbr_count.p, (const int*)nbr_j.p, (const int*)nbr_s.p,
+                               (const int*)rev.p, (const Q4<float>*)g.p, (const double*)wpos.p,
+                               (const float4*)phi.p, (const float4*)plo.p, pl.cg.L, F, (double*)Wat.p,
+                               (int*)status.p, st);
+    else
+      e = launch_gather<double>(N, pl.cap, (const int*)nbr_count.p, (const int*)nbr_j.p, (const int*)nbr_s.p,
+                                (const int*)rev.p, (const Q4<double>*)g.p, (const double*)wpos.p,
+                                (const float4*)phi.p, (const float4*)plo.p, pl.cg.L, F, (double*)Wat.p,
+                                (int*)status.p, st);
+    if (e != cudaSuccess) return cuda_fail(e, "gather kernel");
+    if ((rc_ = mark(3, st))) return rc_;
+    e = launch_reduce(1, (const int*)offs.p, Ei_dst, W ? (const double*)Wat.p : nullptr, E, W, st);
+    if (e != cudaSuccess) return cuda_fail(e, "reduce kernel");
+    if ((rc_ = mark(4, st))) return rc_;
+    if ((rc_ = timing_collect())) return rc_;
+    bool retry;
+    if ((rc_ = finish(st, pl, retry))) return rc_;
+    if (!retry) return POD_OK;
+  }
+}
+
+int pod_handle::descriptors(const pod_system* sys, double* D, cudaStream_t st) {
+  int rc_ = validate_system(sys);
+  if (rc_) return rc_;
+  if (!D) return fail(POD_EINVAL, "D is NULL");
+  retries = 0;
+  for (;;) {
+    Plan pl;
+    if ((rc_ = plan_single(sys->n_atoms, sys->box, sys->pbc, pl))) return rc_;
+    if ((rc_ = build_neighbors(sys->pos, pl, false, st))) return rc_;
+    if ((rc_ = run_atoms(0, pl, D, nullptr, nullptr, st))) return rc_;
+    bool retry;
+    if ((rc_ = finish(st, pl, retry))) return rc_;
+    if (!retry) return POD_OK;
+  }
+}
+
+int pod_handle::neighbors(const pod_system* sys, int cap_out, int* count, int* nbr_out, int* shift_out,
+                          cudaStream_t st) {
+  int rc_ = validate_system(sys);
+  if (rc_) return rc_;
+  if (cap_out < 1 || !count || !nbr_out || !shift_out) return fail(POD_EINVAL, "bad neighbour output arguments");
+  retries = 0;
+  for (;;) {
+    Plan pl;
+    if ((rc_ = plan_single(sys->n_atoms, sys->box, sys->pbc, pl))) return rc_;
+    pl.cap = std::max(pl.cap, cap_out);
+    if ((rc_ = build_neighbors(sys->pos, pl, false, st))) return rc_;
+    cudaError_t e = launch_export_neighbors(sys->n_atoms, pl.cap, (const int*)nbr_count.p, (const int*)nbr_j.p,
+                                            (const int*)nbr_s.p, cap_out, count, nbr_out, shift_out, st);
+    if (e != cudaSuccess) return cuda_fail(e, "neighbour export");
+    bool retry;
+    if ((rc_ = finish(st, pl, retry))) return rc_;
+    if (!retry) break;
+  }
+  return POD_OK;
+}
+
+extern "C" {
+
+int pod_neighbors(pod_handle* h, const pod_system* sys, int cap, int* count, int* nbr, int* shift, void* stream) {
+  if (!h) return POD_EINVAL;
+  int rc = h->neighbors(sys, cap, count, nbr, shift, (cudaStream_t)stream);
+  if (rc == POD_OK && h->sync) {
+    // report atoms with more neighbours than the caller's capacity
+    std::vector<int> hc(sys->n_atoms);
+    cudaError_t e = cudaMemcpy(hc.data(), count, sizeof(int) * hc.size(), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return h->cuda_fail(e, "count read");
+    for (int v : hc)
+      if (v > cap) return h->fail(POD_ENEIGH, "an atom has %d neighbours, more than cap = %d", v, cap);
+  }
+  return rc;
+}
+
+int pod_descriptors(pod_handle* h, const pod_system* sys, double* D, void* stream) {
+  if (!h) return POD_EINVAL;
+  return h->descriptors(sys, D, (cudaStream_t)stream);
+}
+
+int pod_energy_forces(pod_handle* h, const pod_system* sys, const double* c, double* E, double* Ei, double* F,
+                      double* W, void* stream) {
+  if (!h) return POD_EINVAL;
+  return h->energy_forces(sys, c, E, Ei, F, W, (cudaStream_t)stream);
+}
+
+int pod_energy_forces_host(pod_handle* h, const pod_system* sys, const double* c, double* E, double* Ei, double* F,
+                           double* W, void* stream) {
+  if (!h) return POD_EINVAL;
+  int rc = h->validate_system(sys);
+  if (rc) return rc;
+  if (!c || !E) return h->fail(POD_EINVAL, "c and E are required");
+  cudaStream_t st = (cudaStream_t)stream;
+  const int N = sys->n_atoms;
+  if ((rc = h->ensure(h->pos_in, sizeof(double) * 3 * (size_t)N, "staged positions"))) return rc;
+  if ((rc = h->ensure(h->c_in, sizeof(double) * (size_t)h->M, "staged coefficients"))) return rc;
+  if ((rc = h->ensure(h->E_out, sizeof(double) * 16, "staged energy"))) return rc;
+  if (F && (rc = h->ensure(h->F_out, sizeof(double) * 3 * (size_t)N, "staged forces"))) return rc;
+  if (W && (rc = h->ensure(h->W_out, sizeof(double) * 9, "staged virial"))) return rc;
+  if (Ei && (rc = h->ensure(h->Ei_out, sizeof(double) * (size_t)N, "staged atom energies"))) return rc;
+  cudaError_t e = cudaMemcpyAsync(h->pos_in.p, sys->pos, sizeof(double) * 3 * (size_t)N, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h->c_in.p, c, sizeof(double) * h->M, cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return h->cuda_fail(e, "host-to-device copy");
+  pod_system dsys = *sys;
+  dsys.pos = (const double*)h->pos_in.p;
+  const int keep_sync = h->sync;
+  h->sync = 1;
+  rc = h->energy_forces(&dsys, (const double*)h->c_in.p, (double*)h->E_out.p, Ei ? (double*)h->Ei_out.p : nullptr,
+                        F ? (double*)h->F_out.p : nullptr, W ? (double*)h->W_out.p : nullptr, st);
+  h->sync = keep_sync;
+  if (rc) return rc;
+  e = cudaMemcpyAsync(E, h->E_out.p, sizeof(double), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess && F) e = cudaMemcpyAsync(F, h->F_out.p, sizeof(double) * 3 * (size_t)N, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess && W) e = cudaMemcpyAsync(W, h->W_out.p, sizeof(double) * 9, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess && Ei) e = cudaMemcpyAsync(Ei, h->Ei_out.p, sizeof(double) * (size_t)N, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return h->cuda_fail(e, "device-to-host copy");
+  return POD_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,226 @@
+// Internal definitions shared by the fastpod CUDA translation units.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace fastpod {
+
+// ---------------------------------------------------------------- limits
+constexpr int MAXA = 8;    // alpha values per beta
+constexpr int MAXB = 2;    // beta values
+constexpr int MAXG = 8;    // gamma values
+constexpr int MAXK = 16;   // radial modes (= lanes per atom in the atom kernels)
+constexpr int MAXROWS = MAXA * MAXB + MAXG;
+constexpr int PAMAX = 4;   // highest angular degree compiled
+constexpr int CH = 32;     // pairs per atom staged in shared memory at a time
+constexpr int WPB_ATOM = 4;   // warps per block, atom kernels
+constexpr int WPB_NEIGH = 4;  // warps per block, neighbour kernel
+
+// device status bits (OR-ed into a status word, read by the host)
+constexpr int ST_NEIGH = 1;      // more neighbours than the list capacity
+constexpr int ST_CELL = 2;       // more atoms in a cell than the cell capacity
+constexpr int ST_RANGE = 4;      // pair with r <= r_in
+constexpr int ST_NONFINITE = 8;  // NaN / Inf in positions
+constexpr int ST_REV = 16;       // reverse pair not found (broken list symmetry)
+
+// ------------------------------------------------ small vector of 4 T
+template <typename T>
+struct alignas(4 * sizeof(T)) Q4 {
+  T x, y, z, w;
+};
+
+// ------------------------------------------------ radial parameters
+// Snapshot rows: phi(alpha_a, beta_b) at row a * n_beta + b, then varphi(gamma_g)
+// at row n_alpha * n_beta + g (Eq. 3, Eq. 11).  Q rows padded to MAXK columns.
+template <typename T>
+struct RadialConst {
+  T r_in, inv_h;
+  T alpha[MAXA];
+  T beta[MAXB];
+  T inv_ebm1[MAXB];  // 1 / (exp(-beta) - 1)
+  T gamma[MAXG];
+  T Q[MAXROWS][MAXK];
+  int n_alpha, n_beta, n_gamma, K;
+  int alpha_seq;  // alpha == {1, 2, ..., n_alpha}: sin(k pi x) by angle addition
+  int gamma_seq;  // gamma == {1, 2, ..., n_gamma}: r^-g by repeated products
+  // Optional tabulated basis: cubic Hermite pieces of R_k on tab_n equal
+  // intervals of (r_in, r_cut), built in FP64 from the same snapshots and Q;
+  // piece (g, k) holds (a, b, c, d) with R_k = a + t (b + t (c + t d)),
+  // t = (r - r_in) / h - g in [0, 1].  NULL -> evaluate the snapshots directly.
+  const Q4<T>* tab;
+  T tab_inv_h;
+  int tab_n;
+};
+
+// ------------------------------------------------ cell grid
+struct CellGrid {
+  int nc[3];      // cells per direction
+  int S[3];       // cell offsets searched per direction
+  int pbc[3];
+  double L[3];    // box lengths
+  double inv_cs[3];
+  int ncells;
+  int cap;        // atoms per cell
+};
+
+// ------------------------------------------------ packed image shift
+__host__ __device__ __forceinline__ int shift_pack(int sx, int sy, int sz) {
+  return ((sx + 128) << 16) | ((sy + 128) << 8) | (sz + 128);
+}
+__host__ __device__ __forceinline__ void shift_unpack(int code, int& sx, int& sy, int& sz) {
+  sx = ((code >> 16) & 0xFF) - 128;
+  sy = ((code >> 8) & 0xFF) - 128;
+  sz = (code & 0xFF) - 128;
+}
+__host__ __device__ __forceinline__ int shift_negate(int code) {
+  int sx, sy, sz;
+  shift_unpack(code, sx, sy, sz);
+  return shift_pack(-sx, -sy, -sz);
+}
+
+// ------------------------------------------------ displacements
+// FP64: d = (x_j + s L) - x_i, every operation rounded separately (no FMA), the
+// expression the neighbour test is defined on.
+__device__ __forceinline__ double disp_fp64(double xi, double xj, int s, double L) {
+  return __dsub_rn(__dadd_rn(xj, __dmul_rn((double)s, L)), xi);
+}
+
+// FP32 from a double-float split x = hi + lo of both positions and of L: the
+// large terms are added with exact error terms (two-sum) so the small
+// displacement keeps FP32 relative accuracy even when |x| ~ L >> |d|.
+__device__ __forceinline__ float disp_f32(float hi_i, float lo_i, float hi_j, float lo_j, int s, float Lh,
+                                          float Ll) {
+  const float a = hi_j, b = -hi_i;
+  const float t = __fadd_rn(a, b);
+  const float bb = __fsub_rn(t, a);
+  const float e1 = __fadd_rn(__fsub_rn(a, __fsub_rn(t, bb)), __fsub_rn(b, bb));
+  const float sf = (float)s;
+  const float sL = __fmul_rn(sf, Lh);
+  const float e3 = __fmaf_rn(sf, Lh, -sL);  // exact rounding error of s * Lh
+  const float t2 = __fadd_rn(t, sL);
+  const float bb2 = __fsub_rn(t2, t);
+  const float e2 = __fadd_rn(__fsub_rn(t, __fsub_rn(t2, bb2)), __fsub_rn(sL, bb2));
+  const float lo = __fadd_rn(__fsub_rn(lo_j, lo_i), __fmul_rn(sf, Ll));
+  return __fadd_rn(t2, __fadd_rn(__fadd_rn(e1, e2), __fadd_rn(lo, e3)));
+}
+
+// ------------------------------------------------ math wrappers
+__device__ __forceinline__ float d_exp(float x) { return expf(x); }
+__device__ __forceinline__ double d_exp(double x) { return exp(x); }
+__device__ __forceinline__ float d_rsqrt(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double d_rsqrt(double x) { return rsqrt(x); }
+__device__ __forceinline__ float d_sqrt(float x) { return sqrtf(x); }
+__device__ __forceinline__ double d_sqrt(double x) { return sqrt(x); }
+__device__ __forceinline__ void d_sincospi(float x, float* s, float* c) { sincospif(x, s, c); }
+__device__ __forceinline__ void d_sincospi(double x, double* s, double* c) { sincospi(x, s, c); }
+__device__ __forceinline__ float d_exp2(float x) { return exp2f(x); }
+__device__ __forceinline__ double d_exp2(double x) { return exp2(x); }
+__device__ __forceinline__ float d_log2(float x) { return log2f(x); }
+__device__ __forceinline__ double d_log2(double x) { return log2(x); }
+
+__device__ __forceinline__ Q4<float> ldg_q4(const Q4<float>* p) {
+  const float4 v = __ldg(reinterpret_cast<const float4*>(p));
+  Q4<float> q;
+  q.x = v.x;
+  q.y = v.y;
+  q.z = v.z;
+  q.w = v.w;
+  return q;
+}
+__device__ __forceinline__ Q4<double> ldg_q4(const Q4<double>* p) { return *p; }
+
+// ------------------------------------------------ radial basis of one pair
+// R_k(r) = sum_l Q_lk Phi_l(r) and R'_k(r), Phi_l = f_c psi_l (Eq. 3-12).
+// KT is a compile-time bound on K (K = KT in the specialised kernels).
+template <typename T, int KT>
+__device__ __forceinline__ void radial_pair(const RadialConst<T>& rc, T r, T* R, T* Rp) {
+  if (rc.tab) {
+    const T tr = (r - rc.r_in) * rc.tab_inv_h;
+    const int g = min((int)tr, rc.tab_n - 1);
+    const T t = tr - T(g);
+    const Q4<T>* row = rc.tab + (size_t)g * rc.K;
+#pragma unroll
+    for (int k = 0; k < KT; ++k) {
+      if (KT == MAXK && k >= rc.K) {
+        R[k] = T(0);
+        Rp[k] = T(0);
+        continue;
+      }
+      const Q4<T> q = ldg_q4(row + k);
+      R[k] = fma(t, fma(t, fma(t, q.w, q.z), q.y), q.x);
+      Rp[k] = fma(t, fma(t * T(3), q.w, T(2) * q.z), q.y) * rc.tab_inv_h;
+    }
+    return;
+  }
+#pragma unroll
+  for (int k = 0; k < KT; ++k) { R[k] = T(0); Rp[k] = T(0); }
+  const T s = r - rc.r_in;
+  const T inv_s = T(1) / s;
+  const T t = s * rc.inv_h;
+  const T t2 = t * t;
+  const T u3 = T(1) - t2 * t;
+  const T y = fma(u3, u3, T(1e-6));   // epsilon of Eq. 8
+  const T rs = d_rsqrt(y);
+  const T fc = d_exp(T(1) - rs);
+  const T dfc = fc * (u3 * (T(-3) * t2 * rc.inv_h)) * (rs * rs * rs);
+  const int K = rc.K;
+  auto accum = [&](int row, T phi, T dphi) {
+#pragma unroll
+    for (int k = 0; k < KT; ++k) {
+      if (KT == MAXK && k >= K) break;
+      const T q = rc.Q[row][k];
+      R[k] = fma(q, phi, R[k]);
+      Rp[k] = fma(q, dphi, Rp[k]);
+    }
+  };
+  for (int ib = 0; ib < rc.n_beta; ++ib) {
+    const T be = rc.beta[ib];
+    const T et = d_exp(-be * t);
+    const T x = (et - T(1)) * rc.inv_ebm1[ib];
+    const T dx = -be * rc.inv_h * et * rc.inv_ebm1[ib];
+    if (rc.alpha_seq) {
+      T s1, c1;
+      d_sincospi(x, &s1, &c1);
+      T sk = s1, ck = c1;
+      for (int ia = 0; ia < rc.n_alpha; ++ia) {
+        const T apdx = T(ia + 1) * T(3.14159265358979323846) * dx;
+        const T f = sk * inv_s;
+        const T df = (apdx * ck - f) * inv_s;
+        accum(ia * rc.n_beta + ib, fc * f, fma(dfc, f, fc * df));
+        const T sn = fma(sk, c1, ck * s1);  // sin((k+1) pi x)
+        const T cn = fma(ck, c1, -sk * s1); // cos((k+1) pi x)
+        sk = sn;
+        ck = cn;
+      }
+    } else {
+      for (int ia = 0; ia < rc.n_alpha; ++ia) {
+        const T al = rc.alpha[ia];
+        T sk, ck;
+        d_sincospi(al * x, &sk, &ck);
+        const T f = sk * inv_s;
+        const T df = (al * T(3.14159265358979323846) * dx * ck - f) * inv_s;
+        accum(ia * rc.n_beta + ib, fc * f, fma(dfc, f, fc * df));
+      }
+    }
+  }
+  const int row0 = rc.n_alpha * rc.n_beta;
+  const T ir = T(1) / r;
+  if (rc.gamma_seq) {
+    T f = T(1);
+    for (int ig = 0; ig < rc.n_gamma; ++ig) {
+      f *= ir;
+      const T df = -T(ig + 1) * f * ir;
+      accum(row0 + ig, fc * f, fma(dfc, f, fc * df));
+    }
+  } else {
+    const T lr = d_log2(r);
+    for (int ig = 0; ig < rc.n_gamma; ++ig) {
+      const T ga = rc.gamma[ig];
+      const T f = d_exp2(-ga * lr);
+      const T df = -ga * f * ir;
+      accum(row0 + ig, fc * f, fma(dfc, f, fc * df));
+    }
+  }
+}
+
+}  // namespace fastpod

@@ -1,0 +1,76 @@
+// Library-internal handle definition.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdarg>
+#include <string>
+#include <vector>
+
+#include "../../include/pod.h"
+#include "pod_common.cuh"
+#include "pod_kernels.h"
+
+struct HostParams {
+  double r_in = 0, r_cut = 0;
+  std::vector<double> alpha, beta, gamma;
+  int K2 = 0, K3 = 0, K4 = 0, P3 = -1, P4 = -1;
+};
+
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+struct Plan {
+  int N = 0;
+  int cap = 0;  // neighbour capacity per atom
+  fastpod::CellGrid cg{};
+};
+
+struct pod_handle {
+  HostParams P;
+  int precision = 0;
+  int Ns = 0, K = 0, PA = 0, KA4 = 0, M = 0;
+  std::vector<double> Q, eig;
+  fastpod::RadialConst<float> rad32{};
+  fastpod::RadialConst<double> rad64{};
+  std::string err;
+  int sync = 1;
+  int retries = 0;
+  int last_status = 0;
+  int cap_nbr = 0, cap_cell = 0;  // grown after overflows
+  int offs_n = -1;
+  int* h_status = nullptr;        // pinned
+  int timing = 0;
+  cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  double t_acc[4] = {0, 0, 0, 0};
+  int t_calls = 0;
+  int mark(int k, cudaStream_t st);
+  int timing_collect();
+  DevBuf cell_count, cell_atoms, wpos, phi, plo, nbr_count, nbr_j, nbr_s, rev, g, Ei, Wat, status, offs;
+  DevBuf pos_in, c_in, E_out, F_out, W_out, Ei_out;       // host-buffer entry point staging
+  DevBuf fitA, fitG, fitb, fitwork, cfg_of, boxes;        // fit
+  DevBuf rtab;                                            // tabulated radial basis (mixed path)
+  static constexpr int TAB_N = 2048;
+  int radial_mode = 0;  // mixed path: 0 = tabulated R_k, 1 = snapshots evaluated per pair
+  bool tab_ready = false;
+  int ensure_table(cudaStream_t st);
+
+  ~pod_handle();
+  std::vector<DevBuf*> all_bufs();
+  int fail(int code, const char* fmt, ...);
+  int cuda_fail(cudaError_t e, const char* what);
+  int ensure(DevBuf& b, size_t bytes, const char* what);
+  int read_status(cudaStream_t st);
+  int validate_system(const pod_system* sys);
+  int plan_single(int N, const double box[3], const int pbc[3], Plan& pl);
+  int build_neighbors(const double* pos, Plan& pl, bool need_rev, cudaStream_t st);
+  template <typename T>
+  void fill_args(fastpod::AtomArgs<T>& a, const Plan& pl);
+  int run_atoms(int mode, const Plan& pl, double* D, const double* c, double* Ei_dst, cudaStream_t st);
+  int finish(cudaStream_t st, Plan& pl, bool& retry);
+  int energy_forces(const pod_system* sys, const double* c, double* E, double* Ei, double* F, double* W,
+                    cudaStream_t st);
+  int descriptors(const pod_system* sys, double* D, cudaStream_t st);
+  int neighbors(const pod_system* sys, int cap_out, int* count, int* nbr, int* shift, cudaStream_t st);
+};

@@ -1,0 +1,60 @@
+// Kernel argument blocks and launcher declarations (internal to the library).
+#pragma once
+#include <cuda_runtime.h>
+#include <stddef.h>
+
+#include "pod_common.cuh"
+
+namespace fastpod {
+
+// Shared-memory layout of one warp in the atom kernels (byte offsets).
+struct AtomLayout {
+  int A;    // atoms per warp
+  int KS;   // row stride of the staged R / R' (odd, >= K)
+  int SA;   // per-atom stride of R / R' (CH * KS + K: lanes (atom, m) hit distinct banks)
+  int GA;   // per-atom stride of the staged (u, r), in Q4 units
+  int AS;   // per-atom stride of the adjoint dE/dB (multiple of 4, odd number of 16-byte units)
+  size_t off_geo, off_R, off_Rp, off_adj, off_e, off_cnt, warp_bytes;
+};
+
+template <typename T>
+struct AtomArgs {
+  int N, cap;
+  const int* nbr_count;
+  const int* nbr_j;
+  const int* nbr_s;
+  const double* wpos;   // wrapped positions [3][N] (FP64 path)
+  const float4* phi;    // FP32 hi part of the wrapped positions (mixed path)
+  const float4* plo;    // FP32 lo part
+  double L[3];
+  float Lh[3], Ll[3];
+  int K, K2, K3, K4, P3, P4, KA4, M, col3, col4;
+  double* D;            // mode 0: descriptors [N][M]
+  const double* c;      // mode 1: coefficients [M]
+  double* Ei;           // mode 1: atom energies [N]
+  Q4<T>* g;             // mode 1: dE_i/dr_ij per pair slot [N * cap]
+  int* status;
+  RadialConst<T> rad;
+};
+
+cudaError_t launch_bin(int N, const double* pos, const CellGrid& cg, double* wpos, float4* phi, float4* plo,
+                       int* cell_count, int* cell_atoms, int* status, cudaStream_t st);
+cudaError_t launch_neigh(int N, const CellGrid& cg, const double* wpos, const float4* phi, const float4* plo,
+                         const int* cell_count, const int* cell_atoms, double rcut, int cap, int* nbr_count,
+                         int* nbr_j, int* nbr_s, int* status, cudaStream_t st);
+cudaError_t launch_rev(int N, int cap, const int* nbr_count, const int* nbr_j, const int* nbr_s, int* rev,
+                       int* status, cudaStream_t st);
+cudaError_t launch_export_neighbors(int N, int cap, const int* nbr_count, const int* nbr_j, const int* nbr_s,
+                                    int cap_out, int* count_out, int* j_out, int* s_out, cudaStream_t st);
+
+cudaError_t launch_atom_f32(int mode, const AtomArgs<float>& p, int PA, bool has4, cudaStream_t st);
+cudaError_t launch_atom_f64(int mode, const AtomArgs<double>& p, int PA, bool has4, cudaStream_t st);
+
+template <typename T>
+cudaError_t launch_gather(int N, int cap, const int* nbr_count, const int* nbr_j, const int* nbr_s,
+                          const int* rev, const Q4<T>* g, const double* wpos, const float4* phi, const float4* plo,
+                          const double L[3], double* F, double* Wat, int* status, cudaStream_t st);
+cudaError_t launch_reduce(int n_cfg, const int* cfg_offs, const double* Ei, const double* Wat, double* E, double* W,
+                          cudaStream_t st);
+
+}  // namespace fastpod

@@ -1,0 +1,89 @@
+"""Host-side checks of the C-ABI library that need no GPU: it builds, loads,
+exports every entry point declared in include/pod.h, validates parameters and
+computes the POD basis on the host (compared with the oracle's own basis)."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    from paper_2212_14446_gb300 import build as b
+    b.build()
+    import paper_2212_14446_gb300 as p
+    p.lib()
+    return p
+
+
+def header_symbols():
+    with open(os.path.join(ROOT, "include", "pod.h")) as f:
+        text = f.read()
+    return sorted(set(re.findall(r"^\s*(?:int|const char\*)\s+(pod_\w+)\s*\(", text, re.M)))
+
+
+def test_exports_every_declared_symbol(pkg):
+    syms = header_symbols()
+    assert "pod_create" in syms and "pod_energy_forces" in syms and "pod_fit" in syms
+    L = pkg.lib()
+    for s in syms:
+        assert hasattr(L, s), s
+    assert sorted(pkg.EXPORTS) == syms
+
+
+def test_library_links_no_oracle(pkg):
+    # the product library must not contain or reference any oracle symbol
+    with open(pkg.LIB_PATH, "rb") as f:
+        blob = f.read()
+    assert b"orc_" not in blob
+
+
+def test_param_validation(pkg):
+    good = synth.params_full()
+    bad_cases = [dict(r_in=5.0, r_cut=1.0), dict(beta=[0.0]), dict(P3=7), dict(K2=40), dict(alpha=[1.0] * 9),
+                 dict(K2=0, K3=0, K4=0), dict(K2=20, K3=1, K4=1)]
+    for kw in bad_cases:
+        p = synth.PODParams(**{**good.__dict__, **kw})
+        with pytest.raises(pkg.PodError) as ei:
+            pkg.POD(p)
+        assert ei.value.code == pkg.POD_EINVAL
+
+
+def test_sizes_match_oracle(pkg):
+    for p in (synth.params_small(), synth.params_full(),
+              synth.PODParams(K2=2, K3=1, K4=1, P3=2, P4=1), synth.PODParams(K2=5, K3=3, K4=3, P3=2, P4=2)):
+        pod = pkg.POD(p)
+        o = oracle.Oracle(p)
+        assert (pod.M, pod.Ns, pod.K) == (o.M, o.Ns, o.K)
+
+
+@pytest.mark.parametrize("which", ["small", "full"])
+def test_basis_matches_oracle(pkg, which):
+    """The library's POD (one-sided Jacobi on the snapshot matrix) and the
+    oracle's (cyclic Jacobi on the Gram matrix) are different algorithms for the
+    same eigenvectors; they agree to eigenvector perturbation accuracy,
+    eps * lambda_1 / gap ~ 1e-12 relative here."""
+    p = synth.params_small() if which == "small" else synth.params_full()
+    pod = pkg.POD(p)
+    o = oracle.Oracle(p)
+    K = o.K
+    lam = o.eig
+    gaps = np.array([min(lam[k - 1] - lam[k] if k else np.inf, lam[k] - lam[k + 1]) for k in range(K)])
+    bound = 1e3 * np.finfo(float).eps * lam[0] / gaps  # per-mode relative bound with a safety factor
+    err = np.max(np.abs(pod.Q - o.Q), axis=0) / np.max(np.abs(o.Q), axis=0)
+    assert np.all(err <= np.maximum(bound, 1e-13)), (err, bound)
+    assert np.allclose(pod.eig[:K], lam[:K], rtol=1e-9)
+
+
+def test_user_Q_override(pkg):
+    p = synth.params_full()
+    o = oracle.Oracle(p)
+    Q = o.Q * 1.0
+    pod = pkg.POD(p, Q=Q)
+    assert np.array_equal(pod.Q, Q)
