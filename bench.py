@@ -401,7 +401,7 @@ def main():
                                         if args.precision == "mixed" else "nominal FP64 1.25 TFLOP/s")},
             "phases_ms": {"neighbors": phase_avg[0], "atom": phase_avg[1], "gather": phase_avg[2],
                           "reduce": phase_avg[3]},
-            "gpu_launches": 6 * args.steps,
+            "gpu_launches": 5 * args.steps,
             "e2e": e2e,
             "cpu_baseline": cpu,
             "fp64_path": fp64,

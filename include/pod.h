@@ -123,9 +123,9 @@ int pod_set_option(pod_handle* h, int option, int value);
 
 /* Per-phase device time of the pod_energy_forces calls made while
  * POD_OPT_TIMING was on, measured with CUDA events recorded on the call's stream
- * around each phase: ms[0] neighbour list (binning, search, reverse index),
- * ms[1] fused atom kernel, ms[2] force gather, ms[3] energy/virial reduction
- * (totals in milliseconds; ms is host [4]).  *calls receives the number of
+ * around each phase: ms[0] neighbour list (binning, search, sort), ms[1] fused
+ * atom kernel, ms[2] force gather with the fused energy/virial reduction,
+ * ms[3] reserved (0) (totals in milliseconds; ms is host [4]).  *calls receives the number of
  * calls timed.  Resets the totals.  With timing on, each call waits for its
  * last event. */
 int pod_timing(pod_handle* h, double* ms, int* calls);
@@ -189,6 +189,23 @@ typedef struct {
  * POD_ECUDA. */
 int pod_fit(pod_handle* h, const pod_system* batch, const double* E_ref, const double* F_ref,
             const pod_fit_opts* opts, double* c_out, double* mae_E, double* mae_F);
+
+/* The fit in stages, for sharding configurations over several GPUs or processes
+ * (the normal equations are additive over configurations):
+ *   pod_fit_normal   builds A and b for this batch and returns G = A^T A +
+ *                    gamma_reg I and r = A^T b (host [M][M] and [M]); A stays
+ *                    in the handle's workspace.  Pass gamma_reg = 0 on all but
+ *                    one shard (or add gamma once after summing).
+ *   pod_fit_solve    solves G c = r by Cholesky on the GPU (host inputs/output);
+ *                    POD_ESINGULAR if G is not positive definite.
+ *   pod_fit_residual sums |A c - b| over the energy rows (divided by w_E) and the
+ *                    force rows (divided by w_F) of the last pod_fit_normal batch;
+ *                    *n_E / *n_F receive the row counts (MAE = sum / n).
+ * Synchronous.  Errors as pod_fit. */
+int pod_fit_normal(pod_handle* h, const pod_system* batch, const double* E_ref, const double* F_ref,
+                   const pod_fit_opts* opts, double* G_out, double* r_out);
+int pod_fit_solve(pod_handle* h, const double* G, const double* r, double* c_out);
+int pod_fit_residual(pod_handle* h, const double* c, double* sum_abs_E, double* sum_abs_F, int* n_E, int* n_F);
 
 /* Message of the last error on this handle ("" if none).  Owned by the handle. */
 const char* pod_last_error(const pod_handle* h);

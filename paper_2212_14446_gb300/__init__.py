@@ -60,7 +60,7 @@ class pod_fit_opts(C.Structure):
 
 EXPORTS = ["pod_create", "pod_destroy", "pod_info", "pod_set_option", "pod_status", "pod_timing",
            "pod_neighbors", "pod_descriptors", "pod_energy_forces", "pod_energy_forces_host", "pod_fit",
-           "pod_last_error"]
+           "pod_fit_normal", "pod_fit_solve", "pod_fit_residual", "pod_last_error"]
 
 _lib = None
 _lock = threading.Lock()
@@ -90,6 +90,9 @@ def lib():
                 "pod_energy_forces": (C.c_int, [H, S, dp, dp, dp, dp, dp, vp]),
                 "pod_energy_forces_host": (C.c_int, [H, S, dp, dp, dp, dp, dp, vp]),
                 "pod_fit": (C.c_int, [H, S, dp, dp, C.POINTER(pod_fit_opts), dp, dp, dp]),
+                "pod_fit_normal": (C.c_int, [H, S, dp, dp, C.POINTER(pod_fit_opts), dp, dp]),
+                "pod_fit_solve": (C.c_int, [H, dp, dp, dp]),
+                "pod_fit_residual": (C.c_int, [H, dp, dp, dp, ip, ip]),
                 "pod_last_error": (C.c_char_p, [H]),
             }
             for name, (res, args) in sig.items():
@@ -324,6 +327,94 @@ class POD:
         W = torch.empty(9, dtype=torch.float64, device=dev) if virial else None
         pod_energy_forces(self.h, self.system(x, box, pbc), c, E, Ei, F, W, stream)
         return {"E": E, "Ei": Ei, "F": None if F is None else F.t(), "W": None if W is None else W.view(3, 3)}
+
+    # -- batches of configurations --------------------------------------
+    @staticmethod
+    def pack_batch(configs):
+        """Concatenate configurations: (pos SoA (3, N), atom_offs, boxes, pbcs)."""
+        offs = np.zeros(len(configs) + 1, dtype=np.int32)
+        for k, cf in enumerate(configs):
+            offs[k + 1] = offs[k] + cf.pos.shape[0]
+        pos = np.ascontiguousarray(np.concatenate([cf.pos for cf in configs], axis=0).T)
+        boxes = np.array([cf.box for cf in configs], dtype=np.float64)
+        pbcs = np.array([cf.pbc for cf in configs], dtype=np.int32)
+        return pos, offs, boxes, pbcs
+
+    def batch_system(self, pos_soa, offs, boxes, pbcs):
+        return make_system(_dptr(pos_soa), pos_soa.shape[1], boxes[0], (1, 1, 1), batch=(offs, boxes, pbcs))
+
+    def descriptors_batch(self, configs, stream=None):
+        import torch
+        pos, offs, boxes, pbcs = self.pack_batch(configs)
+        x = torch.tensor(pos, dtype=torch.float64, device="cuda")
+        D = torch.empty((x.shape[1], self.M), dtype=torch.float64, device=x.device)
+        pod_descriptors(self.h, self.batch_system(x, offs, boxes, pbcs), D, stream)
+        return D
+
+    def energy_forces_batch(self, configs, c, stream=None):
+        import torch
+        pos, offs, boxes, pbcs = self.pack_batch(configs)
+        x = torch.tensor(pos, dtype=torch.float64, device="cuda")
+        n = x.shape[1]
+        c = c.to(device=x.device, dtype=torch.float64).contiguous()
+        E = torch.empty(len(configs), dtype=torch.float64, device=x.device)
+        Ei = torch.empty(n, dtype=torch.float64, device=x.device)
+        F = torch.empty((3, n), dtype=torch.float64, device=x.device)
+        pod_energy_forces(self.h, self.batch_system(x, offs, boxes, pbcs), c, E, Ei, F, None, stream)
+        return {"E": E, "Ei": Ei, "F": F.t(), "offs": offs}
+
+    def fit(self, configs, E_ref, F_ref, w_E=100.0, w_F=1.0, gamma=1e-12, per_atom_energy=True):
+        """Ridge least-squares fit (Eq. 63a) on the GPU.  E_ref: (n_cfg,), F_ref: list of
+        (N_c, 3) arrays.  Returns (c, mae_E per atom, mae_F per component)."""
+        import torch
+        pos, offs, boxes, pbcs = self.pack_batch(configs)
+        x = torch.tensor(pos, dtype=torch.float64, device="cuda")
+        Er = torch.tensor(np.asarray(E_ref, dtype=np.float64), device=x.device)
+        Fr = torch.tensor(np.ascontiguousarray(np.concatenate([np.asarray(f) for f in F_ref], axis=0).T),
+                          dtype=torch.float64, device=x.device)
+        o = pod_fit_opts(float(w_E), float(w_F), float(gamma), 1 if per_atom_energy else 0)
+        c = np.zeros(self.M)
+        mE, mF = C.c_double(), C.c_double()
+        sysb = self.batch_system(x, offs, boxes, pbcs)
+        _check(self.h, lib().pod_fit(self.h, C.byref(sysb), _dptr(Er), _dptr(Fr), C.byref(o),
+                                     c.ctypes.data_as(C.POINTER(C.c_double)), C.byref(mE), C.byref(mF)))
+        return c, mE.value, mF.value
+
+    def fit_normal(self, configs, E_ref, F_ref, w_E=100.0, w_F=1.0, gamma=1e-12, per_atom_energy=True):
+        """Normal equations (G = A^T A + gamma I, r = A^T b) of this batch; A stays
+        on the device for fit_residual."""
+        import torch
+        pos, offs, boxes, pbcs = self.pack_batch(configs)
+        x = torch.tensor(pos, dtype=torch.float64, device="cuda")
+        Er = torch.tensor(np.asarray(E_ref, dtype=np.float64), device=x.device)
+        Fr = torch.tensor(np.ascontiguousarray(np.concatenate([np.asarray(f) for f in F_ref], axis=0).T),
+                          dtype=torch.float64, device=x.device)
+        o = pod_fit_opts(float(w_E), float(w_F), float(gamma), 1 if per_atom_energy else 0)
+        G = np.zeros((self.M, self.M))
+        r = np.zeros(self.M)
+        sysb = self.batch_system(x, offs, boxes, pbcs)
+        _check(self.h, lib().pod_fit_normal(self.h, C.byref(sysb), _dptr(Er), _dptr(Fr), C.byref(o),
+                                            G.ctypes.data_as(C.POINTER(C.c_double)),
+                                            r.ctypes.data_as(C.POINTER(C.c_double))))
+        return G, r
+
+    def fit_solve(self, G, r):
+        G = np.ascontiguousarray(G, dtype=np.float64)
+        r = np.ascontiguousarray(r, dtype=np.float64)
+        c = np.zeros(self.M)
+        _check(self.h, lib().pod_fit_solve(self.h, G.ctypes.data_as(C.POINTER(C.c_double)),
+                                           r.ctypes.data_as(C.POINTER(C.c_double)),
+                                           c.ctypes.data_as(C.POINTER(C.c_double))))
+        return c
+
+    def fit_residual(self, c):
+        """(sum |dE| per atom over energy rows, sum |dF| over force rows, n_E, n_F) of the last batch."""
+        c = np.ascontiguousarray(c, dtype=np.float64)
+        se, sf = C.c_double(), C.c_double()
+        ne, nf = C.c_int(), C.c_int()
+        _check(self.h, lib().pod_fit_residual(self.h, c.ctypes.data_as(C.POINTER(C.c_double)), C.byref(se),
+                                              C.byref(sf), C.byref(ne), C.byref(nf)))
+        return se.value, sf.value, ne.value, nf.value
 
     def energy_forces_host(self, pos_soa: np.ndarray, box, c: np.ndarray, pbc=(1, 1, 1), stream=None):
         """Host-buffer entry point: numpy in, numpy out (copies inside the call)."""

@@ -25,18 +25,26 @@ template <>
 __device__ __forceinline__ void pair_disp<double>(const AtomArgs<double>& p, int i, int j, int sx, int sy, int sz,
                                                   double& dx, double& dy, double& dz) {
   const size_t N = p.N;
-  dx = disp_fp64(p.wpos[i], p.wpos[j], sx, p.L[0]);
-  dy = disp_fp64(p.wpos[N + i], p.wpos[N + j], sy, p.L[1]);
-  dz = disp_fp64(p.wpos[2 * N + i], p.wpos[2 * N + j], sz, p.L[2]);
+  const double* L = p.cfg_of ? p.cbox[p.cfg_of[i]].L : p.L;
+  dx = disp_fp64(p.wpos[i], p.wpos[j], sx, L[0]);
+  dy = disp_fp64(p.wpos[N + i], p.wpos[N + j], sy, L[1]);
+  dz = disp_fp64(p.wpos[2 * N + i], p.wpos[2 * N + j], sz, L[2]);
 }
 
 template <>
 __device__ __forceinline__ void pair_disp<float>(const AtomArgs<float>& p, int i, int j, int sx, int sy, int sz,
                                                  float& dx, float& dy, float& dz) {
   const float4 hi = p.phi[i], li = p.plo[i], hj = p.phi[j], lj = p.plo[j];
-  dx = disp_f32(hi.x, li.x, hj.x, lj.x, sx, p.Lh[0], p.Ll[0]);
-  dy = disp_f32(hi.y, li.y, hj.y, lj.y, sy, p.Lh[1], p.Ll[1]);
-  dz = disp_f32(hi.z, li.z, hj.z, lj.z, sz, p.Lh[2], p.Ll[2]);
+  const float* Lh = p.Lh;
+  const float* Ll = p.Ll;
+  if (p.cfg_of) {
+    const CfgBox& b = p.cbox[p.cfg_of[i]];
+    Lh = b.Lh;
+    Ll = b.Ll;
+  }
+  dx = disp_f32(hi.x, li.x, hj.x, lj.x, sx, Lh[0], Ll[0]);
+  dy = disp_f32(hi.y, li.y, hj.y, lj.y, sy, Lh[1], Ll[1]);
+  dz = disp_f32(hi.z, li.z, hj.z, lj.z, sz, Lh[2], Ll[2]);
 }
 
 __device__ __forceinline__ int chunk_count(int n, int ch) { return min(max(n - ch * CH, 0), CH); }
@@ -78,12 +86,18 @@ __device__ __forceinline__ void pair_pass(const AtomArgs<T>& p, const AtomLayout
       for (int k = 0; k < KT; ++k) { R[k] = T(0); Rp[k] = T(0); }
     }
     T* Rrow = sR + a * lay.SA + jj * lay.KS;
-    T* Rprow = sRp + a * lay.SA + jj * lay.KS;
 #pragma unroll
     for (int k = 0; k < KT; ++k) {
       if (KT == MAXK && k >= K) break;
       Rrow[k] = R[k];
-      Rprow[k] = Rp[k];
+    }
+    if (!p.rad.tab) {  // direct evaluation: keep R' for the adjoint pass
+      T* Rprow = sRp + a * lay.SA + jj * lay.KS;
+#pragma unroll
+      for (int k = 0; k < KT; ++k) {
+        if (KT == MAXK && k >= K) break;
+        Rprow[k] = Rp[k];
+      }
     }
   }
 }
@@ -108,7 +122,10 @@ __global__ void __launch_bounds__(WPB_ATOM * 32) atom_kernel(const AtomArgs<T> p
   const int a_loc = lane / K;
   const int m = lane - a_loc * K;
   const int atom0 = (blockIdx.x * WPB_ATOM + warp) * A;
-  if (atom0 >= p.N) return;  // uniform per warp
+  if (atom0 >= p.N) {  // uniform per warp
+    if (MODE == 1 && lane < 9) p.wpart[(size_t)(blockIdx.x * WPB_ATOM + warp) * 9 + lane] = 0.0;
+    return;
+  }
   if (lane < A) {
     const int i = atom0 + lane;
     scnt[lane] = (i < p.N) ? min(p.nbr_count[i], p.cap) : 0;
@@ -222,6 +239,9 @@ __global__ void __launch_bounds__(WPB_ATOM * 32) atom_kernel(const AtomArgs<T> p
   }
 
   // ---------------- adjoint pair pass: g_ij = sum_{m,x} a_mx dB_mx/dr_ij  (Eq. 24c)
+  T wv[9];
+#pragma unroll
+  for (int q = 0; q < 9; ++q) wv[q] = T(0);
   for (int ch = 0; ch < nchunks; ++ch) {
     if (nchunks > 1) {
       __syncwarp();
@@ -239,8 +259,20 @@ __global__ void __launch_bounds__(WPB_ATOM * 32) atom_kernel(const AtomArgs<T> p
       }
       const int jj = f - base, slot = ch * CH + jj, i = atom0 + a;
       const Q4<T> u = geo[a * lay.GA + jj];
-      const T* Rrow = sR + a * lay.SA + jj * lay.KS;
-      const T* Rprow = sRp + a * lay.SA + jj * lay.KS;
+      T Rv[KT], Rpv[KT];
+      if (p.rad.tab) {
+        // tabulated basis: re-evaluating R, R' is cheaper than staging R'
+        radial_pair<T, KT>(p.rad, u.w, Rv, Rpv);
+      } else {
+        const T* Rrow = sR + a * lay.SA + jj * lay.KS;
+        const T* Rprow = sRp + a * lay.SA + jj * lay.KS;
+#pragma unroll
+        for (int k = 0; k < KT; ++k) {
+          if (KT == MAXK && k >= K) break;
+          Rv[k] = Rrow[k];
+          Rpv[k] = Rprow[k];
+        }
+      }
       T Am[NAP];
       Mono<PA>::eval(u.x, u.y, u.z, Am);
 #pragma unroll
@@ -250,9 +282,10 @@ __global__ void __launch_bounds__(WPB_ATOM * 32) atom_kernel(const AtomArgs<T> p
       for (int x = 0; x < NAP; ++x) e[x] = T(0);
       T ps = T(0);
       const T* adj = sadj + a * lay.AS;
-#pragma unroll(KT == MAXK ? 1 : KT)
-      for (int mm = 0; mm < K; ++mm) {
-        const T Rm = Rrow[mm], Rpm = Rprow[mm];
+#pragma unroll
+      for (int mm = 0; mm < KT; ++mm) {
+        if (KT == MAXK && mm >= K) break;
+        const T Rm = Rv[mm], Rpm = Rpv[mm];
         const Q4<T>* a4 = reinterpret_cast<const Q4<T>*>(adj + mm * NAP);
         T um = T(0);
 #pragma unroll
@@ -279,14 +312,33 @@ __global__ void __launch_bounds__(WPB_ATOM * 32) atom_kernel(const AtomArgs<T> p
       out.y = fma(ps, u.y, (gy - ug * u.y) * ir);
       out.z = fma(ps, u.z, (gz - ug * u.z) * ir);
       out.w = T(0);
-      p.g[(size_t)i * p.cap + slot] = out;
+      const size_t pidx = (size_t)i * p.cap + slot;
+      p.g[pidx] = out;
+      p.gT[p.rev[pidx]] = out;
+      // pair virial  W -= r_ij (x) g_ij
+      const T dx = u.x * u.w, dy = u.y * u.w, dz = u.z * u.w;
+      wv[0] -= dx * out.x; wv[1] -= dx * out.y; wv[2] -= dx * out.z;
+      wv[3] -= dy * out.x; wv[4] -= dy * out.y; wv[5] -= dy * out.z;
+      wv[6] -= dz * out.x; wv[7] -= dz * out.y; wv[8] -= dz * out.z;
     }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+    for (int q = 0; q < 9; ++q) wv[q] += __shfl_xor_sync(0xffffffffu, wv[q], o);
+  }
+  if (lane < 9) {
+    T v = wv[0];
+#pragma unroll
+    for (int q = 1; q < 9; ++q)
+      if (lane == q) v = wv[q];
+    p.wpart[(size_t)(blockIdx.x * WPB_ATOM + warp) * 9 + lane] = (double)v;
   }
 }
 
 // ------------------------------------------------------------------ layout
 template <typename T>
-AtomLayout make_layout(int K, int PA) {
+AtomLayout make_layout(int K, int PA, bool table) {
   AtomLayout L{};
   const int NA = (PA + 1) * (PA + 2) * (PA + 3) / 6;
   const int NAP = (NA + 3) / 4 * 4;
@@ -304,7 +356,7 @@ AtomLayout make_layout(int K, int PA) {
   L.off_R = off;
   off = al(off + sizeof(T) * (size_t)L.A * L.SA, 32);
   L.off_Rp = off;
-  off = al(off + sizeof(T) * (size_t)L.A * L.SA, 32);
+  if (!table) off = al(off + sizeof(T) * (size_t)L.A * L.SA, 32);
   L.off_adj = off;
   off = al(off + sizeof(T) * (size_t)L.A * L.AS, 32);
   L.off_e = off;
@@ -333,6 +385,14 @@ static cudaError_t launch_one(const AtomArgs<T>& p, const AtomLayout& lay, cudaS
   return cudaGetLastError();
 }
 
+// Warps launched by the atom kernels for N atoms with K radial modes (one
+// virial partial per warp).
+inline int atom_warps_t(int N, int K) {
+  const int A = 32 / K;
+  const int apb = WPB_ATOM * A;
+  return (N + apb - 1) / apb * WPB_ATOM;
+}
+
 template <typename T, int MODE>
 static cudaError_t dispatch_generic(const AtomArgs<T>& p, const AtomLayout& lay, int PA, bool has4,
                                     cudaStream_t st) {
@@ -355,7 +415,7 @@ static cudaError_t dispatch_generic(const AtomArgs<T>& p, const AtomLayout& lay,
 // (K = 3, P = 3, no 4-body; K = 6, P = 4, 4-body), generic K <= 16 otherwise.
 template <typename T>
 cudaError_t launch_atom_t(int mode, const AtomArgs<T>& p, int PA, bool has4, cudaStream_t st) {
-  const AtomLayout lay = make_layout<T>(p.K, PA);
+  const AtomLayout lay = make_layout<T>(p.K, PA, p.rad.tab != nullptr);
   const bool spec6 = (p.K == 6 && PA == 4 && has4);
   const bool spec3 = (p.K == 3 && PA == 3 && !has4);
   if (mode == 0) {

@@ -6,140 +6,124 @@
 
 namespace fastpod {
 
-template <typename T>
-__device__ __forceinline__ void gather_disp(int N, int i, int j, int code, const double* wpos, const float4* phi,
-                                            const float4* plo, const double* L, const float* Lh, const float* Ll,
-                                            T& dx, T& dy, T& dz);
-
-template <>
-__device__ __forceinline__ void gather_disp<double>(int N, int i, int j, int code, const double* wpos,
-                                                    const float4*, const float4*, const double* L, const float*,
-                                                    const float*, double& dx, double& dy, double& dz) {
-  int sx, sy, sz;
-  shift_unpack(code, sx, sy, sz);
-  dx = disp_fp64(wpos[i], wpos[j], sx, L[0]);
-  dy = disp_fp64(wpos[(size_t)N + i], wpos[(size_t)N + j], sy, L[1]);
-  dz = disp_fp64(wpos[(size_t)2 * N + i], wpos[(size_t)2 * N + j], sz, L[2]);
-}
-
-template <>
-__device__ __forceinline__ void gather_disp<float>(int, int i, int j, int code, const double*, const float4* phi,
-                                                   const float4* plo, const double*, const float* Lh,
-                                                   const float* Ll, float& dx, float& dy, float& dz) {
-  int sx, sy, sz;
-  shift_unpack(code, sx, sy, sz);
-  const float4 hi = phi[i], li = plo[i], hj = phi[j], lj = plo[j];
-  dx = disp_f32(hi.x, li.x, hj.x, lj.x, sx, Lh[0], Ll[0]);
-  dy = disp_f32(hi.y, li.y, hj.y, lj.y, sy, Lh[1], Ll[1]);
-  dz = disp_f32(hi.z, li.z, hj.z, lj.z, sz, Lh[2], Ll[2]);
-}
-
-struct BoxArgs {
-  double L[3];
-  float Lh[3], Ll[3];
-};
+// Warp per atom k, lane per neighbour slot t (coalesced):
+//   F_k = sum_t ( g[k, t] - gT[k, t] )
+// g[k, t] = dE_k/dr_kt and gT[k, t] = dE_j/dr_jk of the reverse pair, written by
+// the atom kernel (no atomics).  Per-block FP64 partials of E = sum_i E_i and of
+// the virial partials are summed in a fixed order by the last block to finish,
+// so every result is bitwise reproducible.
+constexpr int WPB_GATHER = 8;
 
 template <typename T>
-__global__ void gather_kernel(int N, int cap, const int* __restrict__ nbr_count, const int* __restrict__ nbr_j,
-                              const int* __restrict__ nbr_s, const int* __restrict__ rev,
-                              const Q4<T>* __restrict__ g, const double* __restrict__ wpos,
-                              const float4* __restrict__ phi, const float4* __restrict__ plo, BoxArgs bx,
-                              double* __restrict__ F, double* __restrict__ Wat, int* __restrict__ status) {
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= N) return;
-  const int n = min(nbr_count[k], cap);
-  double fx = 0, fy = 0, fz = 0;
-  T w[9];
-#pragma unroll
-  for (int q = 0; q < 9; ++q) w[q] = T(0);
-  bool finite = true;
-  for (int t = 0; t < n; ++t) {
-    const size_t p = (size_t)k * cap + t;
-    const Q4<T> a = g[p];
-    const Q4<T> b = g[rev[p]];
-    fx += (double)a.x - (double)b.x;
-    fy += (double)a.y - (double)b.y;
-    fz += (double)a.z - (double)b.z;
-    T dx, dy, dz;
-    gather_disp<T>(N, k, nbr_j[p], nbr_s[p], wpos, phi, plo, bx.L, bx.Lh, bx.Ll, dx, dy, dz);
-    w[0] -= dx * a.x; w[1] -= dx * a.y; w[2] -= dx * a.z;
-    w[3] -= dy * a.x; w[4] -= dy * a.y; w[5] -= dy * a.z;
-    w[6] -= dz * a.x; w[7] -= dz * a.y; w[8] -= dz * a.z;
-  }
-  finite = isfinite(fx) && isfinite(fy) && isfinite(fz);
-  if (!finite) atomicOr(status, ST_NONFINITE);
-  if (F) {
-    F[k] = fx;
-    F[(size_t)N + k] = fy;
-    F[(size_t)2 * N + k] = fz;
-  }
-#pragma unroll
-  for (int q = 0; q < 9; ++q) Wat[(size_t)k * 9 + q] = (double)w[q];
-}
-
-// One block per configuration: E = sum_i E_i and W = sum_i W_i in FP64, each
-// thread summing a strided subsequence in order, then a fixed tree.
-__global__ void reduce_kernel(const int* __restrict__ offs, const double* __restrict__ Ei,
-                              const double* __restrict__ Wat, double* __restrict__ E, double* __restrict__ W) {
-  __shared__ double red[10][256];
-  const int c = blockIdx.x;
-  const int a0 = offs[c], a1 = offs[c + 1];
+__global__ void __launch_bounds__(WPB_GATHER * 32)
+    gather_reduce_kernel(int N, int cap, const int* __restrict__ nbr_count, const Q4<T>* __restrict__ g,
+                         const Q4<T>* __restrict__ gT, const double* __restrict__ Ei,
+                         const double* __restrict__ wpart, int n_wpart, double* __restrict__ F, double fscale,
+                         double* __restrict__ part, unsigned* __restrict__ ticket, double* __restrict__ E_out,
+                         double* __restrict__ W_out, int* __restrict__ status) {
+  __shared__ double sred[WPB_GATHER][10];
+  __shared__ bool last;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   double acc[10];
 #pragma unroll
   for (int q = 0; q < 10; ++q) acc[q] = 0.0;
-  for (int i = a0 + threadIdx.x; i < a1; i += blockDim.x) {
-    acc[0] += Ei[i];
-    if (Wat) {
+  for (int k = blockIdx.x * WPB_GATHER + warp; k < N; k += gridDim.x * WPB_GATHER) {
+    const int n = min(nbr_count[k], cap);
+    T f0 = T(0), f1 = T(0), f2 = T(0);
+    for (int t = lane; t < n; t += 32) {
+      const size_t p = (size_t)k * cap + t;
+      const Q4<T> a = g[p], b = gT[p];
+      f0 += a.x - b.x;
+      f1 += a.y - b.y;
+      f2 += a.z - b.z;
+    }
 #pragma unroll
-      for (int q = 0; q < 9; ++q) acc[1 + q] += Wat[(size_t)i * 9 + q];
+    for (int o = 16; o > 0; o >>= 1) {
+      f0 += __shfl_xor_sync(0xffffffffu, f0, o);
+      f1 += __shfl_xor_sync(0xffffffffu, f1, o);
+      f2 += __shfl_xor_sync(0xffffffffu, f2, o);
+    }
+    if (lane == 0) {
+      if (F) {
+        F[k] = fscale * (double)f0;
+        F[(size_t)N + k] = fscale * (double)f1;
+        F[(size_t)2 * N + k] = fscale * (double)f2;
+      }
+      if (!(isfinite((double)f0) && isfinite((double)f1) && isfinite((double)f2))) atomicOr(status, ST_NONFINITE);
+      acc[0] += Ei[k];
     }
   }
+  // virial partials of the atom kernel, a fixed subset per warp of this block
+  if (lane < 9)
+    for (int w = blockIdx.x * WPB_GATHER + warp; w < n_wpart; w += gridDim.x * WPB_GATHER)
+      acc[1 + lane] += wpart[(size_t)w * 9 + lane];
+  // fold the per-lane virial components into lane 0's slot order
 #pragma unroll
-  for (int q = 0; q < 10; ++q) red[q][threadIdx.x] = acc[q];
+  for (int q = 0; q < 9; ++q) {
+    const double v = __shfl_sync(0xffffffffu, acc[1 + q], q);
+    if (lane == 0) acc[1 + q] = v;
+  }
+  if (lane == 0) {
+#pragma unroll
+    for (int q = 0; q < 10; ++q) sred[warp][q] = acc[q];
+  }
   __syncthreads();
-  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-    if ((int)threadIdx.x < s) {
+  if (threadIdx.x < 10) {
+    double s = 0.0;
+    for (int wv = 0; wv < WPB_GATHER; ++wv) s += sred[wv][threadIdx.x];
+    part[(size_t)blockIdx.x * 10 + threadIdx.x] = s;
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = (atomicAdd(ticket, 1u) == gridDim.x - 1);
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  // fixed-order parallel sum of the block partials: thread t adds blocks
+  // t, t + blockDim, ... in order (independent L2 loads), then one fixed tree
+  double s[10];
 #pragma unroll
-      for (int q = 0; q < 10; ++q) red[q][threadIdx.x] += red[q][threadIdx.x + s];
+  for (int q = 0; q < 10; ++q) s[q] = 0.0;
+  for (unsigned b = threadIdx.x; b < gridDim.x; b += blockDim.x) {
+#pragma unroll
+    for (int q = 0; q < 10; ++q) s[q] += __ldcg(part + (size_t)b * 10 + q);
+  }
+  __shared__ double fin2[10][WPB_GATHER * 32];
+#pragma unroll
+  for (int q = 0; q < 10; ++q) fin2[q][threadIdx.x] = s[q];
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) {
+#pragma unroll
+      for (int q = 0; q < 10; ++q) fin2[q][threadIdx.x] += fin2[q][threadIdx.x + w];
     }
     __syncthreads();
   }
-  if (threadIdx.x == 0) {
-    E[c] = red[0][0];
-    if (W) {
-#pragma unroll
-      for (int q = 0; q < 9; ++q) W[(size_t)c * 9 + q] = red[1 + q][0];
-    }
-  }
+  if (threadIdx.x == 0) E_out[0] = fin2[0][0];
+  if (W_out && threadIdx.x >= 1 && threadIdx.x < 10) W_out[threadIdx.x - 1] = fin2[threadIdx.x][0];
+  if (threadIdx.x == 0) *ticket = 0u;  // ready for the next launch (graph replays)
 }
 
 template <typename T>
-cudaError_t launch_gather(int N, int cap, const int* nbr_count, const int* nbr_j, const int* nbr_s,
-                          const int* rev, const Q4<T>* g, const double* wpos, const float4* phi, const float4* plo,
-                          const double L[3], double* F, double* Wat, int* status, cudaStream_t st) {
-  BoxArgs bx;
-  for (int d = 0; d < 3; ++d) {
-    bx.L[d] = L[d];
-    bx.Lh[d] = (float)L[d];
-    bx.Ll[d] = (float)(L[d] - (double)bx.Lh[d]);
-  }
-  const int tb = 128;
-  gather_kernel<T><<<(N + tb - 1) / tb, tb, 0, st>>>(N, cap, nbr_count, nbr_j, nbr_s, rev, g, wpos, phi, plo, bx,
-                                                     F, Wat, status);
+cudaError_t launch_gather_reduce(int N, int cap, const int* nbr_count, const Q4<T>* g, const Q4<T>* gT,
+                                 const double* Ei, const double* wpart, int n_wpart, double* F, double fscale,
+                                 double* part, int nblocks, unsigned* ticket, double* E, double* W, int* status,
+                                 cudaStream_t st) {
+  gather_reduce_kernel<T><<<nblocks, WPB_GATHER * 32, 0, st>>>(N, cap, nbr_count, g, gT, Ei, wpart, n_wpart, F,
+                                                               fscale, part, ticket, E, W, status);
   return cudaGetLastError();
 }
 
-template cudaError_t launch_gather<float>(int, int, const int*, const int*, const int*, const int*,
-                                          const Q4<float>*, const double*, const float4*, const float4*,
-                                          const double*, double*, double*, int*, cudaStream_t);
-template cudaError_t launch_gather<double>(int, int, const int*, const int*, const int*, const int*,
-                                           const Q4<double>*, const double*, const float4*, const float4*,
-                                           const double*, double*, double*, int*, cudaStream_t);
-
-cudaError_t launch_reduce(int n_cfg, const int* cfg_offs, const double* Ei, const double* Wat, double* E, double* W,
-                          cudaStream_t st) {
-  reduce_kernel<<<n_cfg, 256, 0, st>>>(cfg_offs, Ei, Wat, E, W);
-  return cudaGetLastError();
+int gather_blocks(int N) {
+  const int want = (N + WPB_GATHER - 1) / WPB_GATHER;
+  return want < 8 * 152 ? (want > 0 ? want : 1) : 8 * 152;
 }
+
+template cudaError_t launch_gather_reduce<float>(int, int, const int*, const Q4<float>*, const Q4<float>*,
+                                                 const double*, const double*, int, double*, double, double*, int,
+                                                 unsigned*, double*, double*, int*, cudaStream_t);
+template cudaError_t launch_gather_reduce<double>(int, int, const int*, const Q4<double>*, const Q4<double>*,
+                                                  const double*, const double*, int, double*, double, double*, int,
+                                                  unsigned*, double*, double*, int*, cudaStream_t);
 
 }  // namespace fastpod

@@ -57,15 +57,12 @@ __global__ void __launch_bounds__(WPB_NEIGH * 32)
                  int* __restrict__ status) {
   extern __shared__ unsigned long long nsm[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  unsigned long long* keys = nsm + (size_t)warp * (keycap + 96);
-  int* off_cell = reinterpret_cast<int*>(keys + keycap);   // 32 entries
-  int* off_code = off_cell + 32;                            // 32 entries
-  int* off_pre = off_code + 32;                             // 33 entries (exclusive prefix)
+  unsigned long long* keys = nsm + (size_t)warp * keycap;
   const int i = blockIdx.x * WPB_NEIGH + warp;
   if (i >= N) return;
 
   const double xi0 = wpos[i], xi1 = wpos[(size_t)N + i], xi2 = wpos[(size_t)2 * N + i];
-  const float4 hi_i = phi[i], lo_i = plo[i];
+  const float4 hi_i = phi[i];
   int ci[3];
   const double xi[3] = {xi0, xi1, xi2};
 #pragma unroll
@@ -74,80 +71,60 @@ __global__ void __launch_bounds__(WPB_NEIGH * 32)
     ci[d] = c < 0 ? 0 : (c >= cg.nc[d] ? cg.nc[d] - 1 : c);
   }
   const float Lh[3] = {(float)cg.L[0], (float)cg.L[1], (float)cg.L[2]};
-  const float Ll[3] = {(float)(cg.L[0] - (double)Lh[0]), (float)(cg.L[1] - (double)Lh[1]),
-                       (float)(cg.L[2] - (double)Lh[2])};
   const int wx = 2 * cg.S[0] + 1, wy = 2 * cg.S[1] + 1, wz = 2 * cg.S[2] + 1;
   const int noff = wx * wy * wz;
+  const int zero = shift_pack(0, 0, 0);
   int nhit = 0;
   for (int ob = 0; ob < noff; ob += 32) {
-    // lane -> one offset cell of this batch
+    // lane -> one (cell, image) of this batch; every lane then walks its own cell
     const int o = ob + lane;
-    int cnt = 0, cell = 0, code = 0;
+    int cnt = 0, cell = 0, code = zero;
+    float px = 0.f, py = 0.f, pz = 0.f;
     if (o < noff) {
-      const int ox = o % wx - cg.S[0];
-      const int oy = (o / wx) % wy - cg.S[1];
-      const int oz = o / (wx * wy) - cg.S[2];
-      const int oc[3] = {ox, oy, oz};
+      const int oc[3] = {o % wx - cg.S[0], (o / wx) % wy - cg.S[1], o / (wx * wy) - cg.S[2]};
       int tc[3], sh[3];
       bool ok = true;
 #pragma unroll
       for (int d = 0; d < 3; ++d) {
         int t = ci[d] + oc[d];
-        int s = 0;
+        int sd = 0;
         if (cg.pbc[d]) {
-          // floor division: t = tc + s * nc with 0 <= tc < nc
-          s = (t >= 0) ? t / cg.nc[d] : -((-t + cg.nc[d] - 1) / cg.nc[d]);
-          t -= s * cg.nc[d];
+          sd = (t >= 0) ? t / cg.nc[d] : -((-t + cg.nc[d] - 1) / cg.nc[d]);
+          t -= sd * cg.nc[d];
         } else if (t < 0 || t >= cg.nc[d]) {
           ok = false;
         }
         tc[d] = t;
-        sh[d] = s;
+        sh[d] = sd;
       }
       if (ok) {
         cell = (tc[2] * cg.nc[1] + tc[1]) * cg.nc[0] + tc[0];
         cnt = min(cell_count[cell], cg.cap);
         code = shift_pack(sh[0], sh[1], sh[2]);
+        px = (float)sh[0] * Lh[0] - hi_i.x;
+        py = (float)sh[1] * Lh[1] - hi_i.y;
+        pz = (float)sh[2] * Lh[2] - hi_i.z;
       }
     }
-    // exclusive scan of counts across the warp
-    int inc = cnt;
+    int cmax = cnt;
 #pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-      const int v = __shfl_up_sync(0xffffffffu, inc, d);
-      if (lane >= d) inc += v;
-    }
-    off_cell[lane] = cell;
-    off_code[lane] = code;
-    off_pre[lane] = inc - cnt;
-    const int total = __shfl_sync(0xffffffffu, inc, 31);
-    if (lane == 31) off_pre[32] = total;
-    __syncwarp();
-    for (int f0 = 0; f0 < total; f0 += 32) {
-      const int f = f0 + lane;
+    for (int d = 16; d > 0; d >>= 1) cmax = max(cmax, __shfl_xor_sync(0xffffffffu, cmax, d));
+    const int* ca = cell_atoms + (size_t)cell * cg.cap;
+    for (int k = 0; k < cmax; ++k) {
       bool hit = false;
       unsigned long long key = 0;
-      if (f < total) {
-        // binary search: largest o with off_pre[o] <= f
-        int lo = 0, hi = 31;
-        while (lo < hi) {
-          const int mid = (lo + hi + 1) >> 1;
-          if (off_pre[mid] <= f) lo = mid; else hi = mid - 1;
-        }
-        const int slot = f - off_pre[lo];
-        const int j = cell_atoms[(size_t)off_cell[lo] * cg.cap + slot];
-        const int code = off_code[lo];
-        int sx, sy, sz;
-        shift_unpack(code, sx, sy, sz);
-        if (!(j == i && sx == 0 && sy == 0 && sz == 0)) {
-          const float4 hj = phi[j], lj = plo[j];
-          const float dx = disp_f32(hi_i.x, lo_i.x, hj.x, lj.x, sx, Lh[0], Ll[0]);
-          const float dy = disp_f32(hi_i.y, lo_i.y, hj.y, lj.y, sy, Lh[1], Ll[1]);
-          const float dz = disp_f32(hi_i.z, lo_i.z, hj.z, lj.z, sz, Lh[2], Ll[2]);
+      if (k < cnt) {
+        const int j = ca[k];
+        if (!(j == i && code == zero)) {
+          // FP32 prefilter on the hi parts only; its error is far inside the band
+          const float4 hj = phi[j];
+          const float dx = hj.x + px, dy = hj.y + py, dz = hj.z + pz;
           const float r2f = dx * dx + dy * dy + dz * dz;
           if (r2f < rc2_lo) {
             hit = true;
           } else if (r2f < rc2_hi) {
+            int sx, sy, sz;
+            shift_unpack(code, sx, sy, sz);
             const double ddx = disp_fp64(xi0, wpos[j], sx, cg.L[0]);
             const double ddy = disp_fp64(xi1, wpos[(size_t)N + j], sy, cg.L[1]);
             const double ddz = disp_fp64(xi2, wpos[(size_t)2 * N + j], sz, cg.L[2]);
@@ -164,31 +141,50 @@ __global__ void __launch_bounds__(WPB_NEIGH * 32)
       }
       nhit += __popc(m);
     }
-    __syncwarp();
   }
-  const int n = min(nhit, keycap);
-  // bitonic sort of keys[0 .. np)
-  int np = 1;
-  while (np < n) np <<= 1;
-  for (int t = n + lane; t < np; t += 32) keys[t] = ~0ull;
   __syncwarp();
-  for (int k = 2; k <= np; k <<= 1)
-    for (int j = k >> 1; j > 0; j >>= 1) {
-      for (int t = lane; t < np; t += 32) {
-        const int u = t ^ j;
-        if (u > t) {
-          const unsigned long long a = keys[t], b = keys[u];
-          const bool up = (t & k) == 0;
-          if ((a > b) == up) { keys[t] = b; keys[u] = a; }
-        }
+  const int n = min(nhit, keycap);
+  if (n <= 32) {
+    // bitonic sort of one key per lane in registers
+    unsigned long long v = lane < n ? keys[lane] : ~0ull;
+#pragma unroll
+    for (int k = 2; k <= 32; k <<= 1)
+#pragma unroll
+      for (int j = k >> 1; j > 0; j >>= 1) {
+        const unsigned long long w = __shfl_xor_sync(0xffffffffu, v, j);
+        const bool up = (lane & k) == 0;
+        const bool lower = (lane & j) == 0;
+        v = (lower == up) ? (v < w ? v : w) : (v < w ? w : v);
       }
-      __syncwarp();
-    }
+    if (lane < n) keys[lane] = v;
+    __syncwarp();
+  } else {
+    int np = 1;
+    while (np < n) np <<= 1;
+    for (int t = n + lane; t < np; t += 32) keys[t] = ~0ull;
+    __syncwarp();
+    for (int k = 2; k <= np; k <<= 1)
+      for (int j = k >> 1; j > 0; j >>= 1) {
+        for (int t = lane; t < np; t += 32) {
+          const int u = t ^ j;
+          if (u > t) {
+            const unsigned long long a = keys[t], b = keys[u];
+            const bool up = (t & k) == 0;
+            if ((a > b) == up) { keys[t] = b; keys[u] = a; }
+          }
+        }
+        __syncwarp();
+      }
+  }
   const int nw = min(n, cap);
-  for (int t = lane; t < nw; t += 32) {
-    const unsigned long long key = keys[t];
-    nbr_j[(size_t)i * cap + t] = (int)(key >> 24);
-    nbr_s[(size_t)i * cap + t] = (int)(key & 0xFFFFFFull);
+  for (int t = lane; t < cap; t += 32) {
+    if (t < nw) {
+      const unsigned long long key = keys[t];
+      nbr_j[(size_t)i * cap + t] = (int)(key >> 24);
+      nbr_s[(size_t)i * cap + t] = (int)(key & 0xFFFFFFull);
+    } else {
+      nbr_j[(size_t)i * cap + t] = 0x7fffffff;  // sentinel: rows stay sorted to cap
+    }
   }
   if (lane == 0) {
     nbr_count[i] = nhit;
@@ -196,31 +192,32 @@ __global__ void __launch_bounds__(WPB_NEIGH * 32)
   }
 }
 
-// Thread per pair slot: index of the reverse pair (j, i, -s) in j's list.
+// Thread per pair slot: index of the reverse pair (j, i, -s) in j's list.  Rows
+// are sorted and padded with a sentinel to cap, so a lower bound on the atom
+// index over the whole row needs no count; equal indices (several images of
+// the same atom) are then scanned for the negated shift.
 __global__ void rev_kernel(int N, int cap, const int* __restrict__ nbr_count, const int* __restrict__ nbr_j,
                            const int* __restrict__ nbr_s, int* __restrict__ rev, int* __restrict__ status) {
   const size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= (size_t)N * cap) return;
-  const int i = (int)(p / cap), t = (int)(p % cap);
-  const int ni = min(nbr_count[i], cap);
-  if (t >= ni) return;
   const int j = nbr_j[p];
-  const unsigned long long target = ((unsigned long long)i << 24) | (unsigned long long)shift_negate(nbr_s[p]);
-  const int nj = min(nbr_count[j], cap);
-  const size_t base = (size_t)j * cap;
-  int lo = 0, hi = nj - 1, found = -1;
-  while (lo <= hi) {
+  if (j >= N) return;  // sentinel slot
+  const int i = (int)(p / cap);
+  const int want = shift_negate(nbr_s[p]);
+  const int* row = nbr_j + (size_t)j * cap;
+  int lo = 0, hi = cap;
+  while (lo < hi) {
     const int mid = (lo + hi) >> 1;
-    const unsigned long long k =
-        ((unsigned long long)nbr_j[base + mid] << 24) | (unsigned long long)nbr_s[base + mid];
-    if (k == target) { found = mid; break; }
-    if (k < target) lo = mid + 1; else hi = mid - 1;
+    if (row[mid] < i) lo = mid + 1; else hi = mid;
   }
+  int found = -1;
+  for (int t = lo; t < cap && row[t] == i; ++t)
+    if (nbr_s[(size_t)j * cap + t] == want) { found = t; break; }
   if (found < 0) {
     atomicOr(status, ST_REV);
-    rev[p] = (int)p;  // contributes zero net force; status reports the inconsistency
+    rev[p] = (int)p;  // keeps the gather in bounds; the status reports the inconsistency
   } else {
-    rev[p] = (int)(base + found);
+    rev[p] = (int)((size_t)j * cap + found);
   }
 }
 
@@ -252,14 +249,23 @@ cudaError_t launch_bin(int N, const double* pos, const CellGrid& cg, double* wpo
   return cudaGetLastError();
 }
 
-size_t neigh_smem_bytes(int keycap) { return (size_t)WPB_NEIGH * (keycap + 96) * sizeof(unsigned long long); }
+size_t neigh_smem_bytes(int keycap) { return (size_t)WPB_NEIGH * keycap * sizeof(unsigned long long); }
 
 cudaError_t launch_neigh(int N, const CellGrid& cg, const double* wpos, const float4* phi, const float4* plo,
                          const int* cell_count, const int* cell_atoms, double rcut, int cap, int* nbr_count,
                          int* nbr_j, int* nbr_s, int* status, cudaStream_t st) {
   const double rc2 = rcut * rcut;
-  const float rc2_lo = (float)(rc2 * (1.0 - 1e-4));
-  const float rc2_hi = (float)(rc2 * (1.0 + 1e-4));
+  // Error of the FP32 prefilter: each displacement component is formed from
+  // FP32-rounded positions (|x| < L) and s * L_h, so |d_f32 - d| <= 4 ulp(L_max)
+  // per component with margin; r^2 then moves by at most 2 sqrt(3) r_cut err_d
+  // plus the rounding of r^2 itself.  Pairs whose FP32 r^2 falls within the band
+  // are decided by the exact FP64 expression.
+  const double Lmax = fmax(fmax(cg.L[0], cg.L[1]), fmax(cg.L[2], rcut));
+  const double err_d = 4.0 * Lmax * 1.1920928955078125e-7 * (1 + cg.S[0] + cg.S[1] + cg.S[2]);
+  const double err_r2 = 2.0 * 1.7320508075688772 * rcut * err_d + 3.0 * err_d * err_d + 8.0 * rc2 * 1.1920928955078125e-7;
+  const double band = fmax(4.0 * err_r2, 1e-6 * rc2);
+  const float rc2_lo = (float)(rc2 - band);
+  const float rc2_hi = (float)(rc2 + band);
   int keycap = 32;
   while (keycap < cap) keycap <<= 1;
   const size_t smem = neigh_smem_bytes(keycap);

@@ -251,7 +251,7 @@ int pod_handle::timing_collect() {
 std::vector<DevBuf*> pod_handle::all_bufs() {
   return {&cell_count, &cell_atoms, &wpos, &phi, &plo, &nbr_count, &nbr_j, &nbr_s, &rev, &g, &Ei,
           &Wat, &status, &offs, &pos_in, &c_in, &E_out, &F_out, &W_out, &Ei_out, &fitA, &fitG, &fitb,
-          &fitwork, &cfg_of, &boxes, &rtab};
+          &fitwork, &cfg_of, &boxes, &rtab, &gT, &wpart};
 }
 
 // ============================================================ C ABI
@@ -446,11 +446,66 @@ int pod_handle::plan_single(int N, const double box[3], const int pbc[3], Plan& 
   return POD_OK;
 }
 
+int pod_handle::plan_batch(const pod_system* sys, Plan& pl) {
+  const int nc = sys->n_configs;
+  const double rc = P.r_cut;
+  pl.N = sys->n_atoms;
+  pl.batched = true;
+  pl.n_cfg = nc;
+  pl.Lmax = rc;
+  pl.Smax = 0;
+  h_cbox.assign(nc, CfgBox{});
+  h_cfg_of.assign(pl.N, 0);
+  double max_expect = 0;
+  if (sys->atom_offs[0] != 0 || sys->atom_offs[nc] != pl.N) return fail(POD_EINVAL, "atom_offs must run from 0 to n_atoms");
+  for (int c = 0; c < nc; ++c) {
+    CfgBox& b = h_cbox[c];
+    b.a0 = sys->atom_offs[c];
+    b.a1 = sys->atom_offs[c + 1];
+    if (b.a1 < b.a0) return fail(POD_EINVAL, "atom_offs must be non-decreasing");
+    double vol = 1.0;
+    for (int d = 0; d < 3; ++d) {
+      const double L = sys->boxes[3 * c + d];
+      const int pb = sys->pbcs ? sys->pbcs[3 * c + d] : sys->pbc[d];
+      if (pb && !(L > 0)) return fail(POD_EINVAL, "configuration %d: periodic direction %d needs a positive box", c, d);
+      if (!(L >= 0) || !std::isfinite(L)) return fail(POD_EINVAL, "configuration %d: box is not finite", c);
+      b.L[d] = L;
+      b.Lh[d] = (float)L;
+      b.Ll[d] = (float)(L - (double)b.Lh[d]);
+      b.pbc[d] = pb ? 1 : 0;
+      b.S[d] = pb ? (int)std::ceil(rc / L * (1.0 + 1e-12)) : 0;
+      if (b.S[d] > 60) return fail(POD_EINVAL, "configuration %d: box too small for r_cut", c);
+      pl.Smax = std::max(pl.Smax, b.S[d]);
+      pl.Lmax = std::max(pl.Lmax, L);
+      vol *= std::max(L, rc);
+    }
+    for (int i = b.a0; i < b.a1; ++i) h_cfg_of[i] = c;
+    max_expect = std::max(max_expect, (b.a1 - b.a0) / vol * (4.0 / 3.0) * M_PI * rc * rc * rc);
+  }
+  int cap = (int)(1.5 * max_expect + 16);
+  cap = (cap + 7) / 8 * 8;
+  pl.cap = std::max(std::max(cap, 16), cap_nbr);
+  int rc_;
+  if ((rc_ = ensure(boxes, sizeof(CfgBox) * (size_t)nc, "configuration boxes"))) return rc_;
+  if ((rc_ = ensure(cfg_of, sizeof(int) * (size_t)pl.N, "configuration index"))) return rc_;
+  cudaError_t e = cudaMemcpy(boxes.p, h_cbox.data(), sizeof(CfgBox) * (size_t)nc, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(cfg_of.p, h_cfg_of.data(), sizeof(int) * (size_t)pl.N, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return cuda_fail(e, "batch upload");
+  return POD_OK;
+}
+
+int pod_handle::plan(const pod_system* sys, Plan& pl) {
+  if (sys->n_configs > 1) return plan_batch(sys, pl);
+  return plan_single(sys->n_atoms, sys->box, sys->pbc, pl);
+}
+
 int pod_handle::build_neighbors(const double* pos, Plan& pl, bool need_rev, cudaStream_t st) {
   const int N = pl.N;
   int rc_;
-  if ((rc_ = ensure(cell_count, sizeof(int) * (size_t)pl.cg.ncells, "cell counts"))) return rc_;
-  if ((rc_ = ensure(cell_atoms, sizeof(int) * (size_t)pl.cg.ncells * pl.cg.cap, "cell atoms"))) return rc_;
+  if (!pl.batched) {
+    if ((rc_ = ensure(cell_count, sizeof(int) * (size_t)pl.cg.ncells, "cell counts"))) return rc_;
+    if ((rc_ = ensure(cell_atoms, sizeof(int) * (size_t)pl.cg.ncells * pl.cg.cap, "cell atoms"))) return rc_;
+  }
   if ((rc_ = ensure(wpos, sizeof(double) * 3 * (size_t)N, "wrapped positions"))) return rc_;
   if ((rc_ = ensure(phi, sizeof(float4) * (size_t)N, "positions hi"))) return rc_;
   if ((rc_ = ensure(plo, sizeof(float4) * (size_t)N, "positions lo"))) return rc_;
@@ -463,7 +518,17 @@ int pod_handle::build_neighbors(const double* pos, Plan& pl, bool need_rev, cuda
     cudaError_t e0 = cudaMemset(status.p, 0, sizeof(int) * 4);
     if (e0 != cudaSuccess) return cuda_fail(e0, "status init");
   }
-  cudaError_t e = cudaMemsetAsync(cell_count.p, 0, sizeof(int) * (size_t)pl.cg.ncells, st);
+  cudaError_t e;
+  if (pl.batched) {
+    e = launch_batch_wrap(N, pos, (const int*)cfg_of.p, (const CfgBox*)boxes.p, (double*)wpos.p, (float4*)phi.p,
+                          (float4*)plo.p, (int*)status.p, st);
+    if (e != cudaSuccess) return cuda_fail(e, "batch wrap kernel");
+    e = launch_batch_neigh(N, (const int*)cfg_of.p, (const CfgBox*)boxes.p, (const double*)wpos.p,
+                           (const float4*)phi.p, P.r_cut, pl.Lmax, pl.Smax, pl.cap, (int*)nbr_count.p,
+                           (int*)nbr_j.p, (int*)nbr_s.p, (int*)status.p, st);
+    if (e != cudaSuccess) return cuda_fail(e, "batch neighbour kernel");
+  } else {
+  e = cudaMemsetAsync(cell_count.p, 0, sizeof(int) * (size_t)pl.cg.ncells, st);
   if (e != cudaSuccess) return cuda_fail(e, "cell count clear");
   e = launch_bin(N, pos, pl.cg, (double*)wpos.p, (float4*)phi.p, (float4*)plo.p, (int*)cell_count.p,
                  (int*)cell_atoms.p, (int*)status.p, st);
@@ -472,6 +537,7 @@ int pod_handle::build_neighbors(const double* pos, Plan& pl, bool need_rev, cuda
                    (const int*)cell_count.p, (const int*)cell_atoms.p, P.r_cut, pl.cap, (int*)nbr_count.p,
                    (int*)nbr_j.p, (int*)nbr_s.p, (int*)status.p, st);
   if (e != cudaSuccess) return cuda_fail(e, "neighbour kernel");
+  }
   if (need_rev) {
     if ((rc_ = ensure(rev, sizeof(int) * (size_t)N * pl.cap, "reverse index"))) return rc_;
     e = launch_rev(N, pl.cap, (const int*)nbr_count.p, (const int*)nbr_j.p, (const int*)nbr_s.p, (int*)rev.p,
@@ -508,6 +574,8 @@ void pod_handle::fill_args(AtomArgs<T>& a, const Plan& pl) {
   a.col3 = 1 + P.K2;
   a.col4 = a.col3 + P.K3 * (P.P3 + 1);
   a.status = (int*)status.p;
+  a.cfg_of = pl.batched ? (const int*)cfg_of.p : nullptr;
+  a.cbox = pl.batched ? (const CfgBox*)boxes.p : nullptr;
 }
 
 // Cubic Hermite pieces of R_k on TAB_N equal intervals of (r_in, r_cut), from
@@ -570,6 +638,9 @@ int pod_handle::run_atoms(int mode, const Plan& pl, double* D, const double* c, 
     a.c = c;
     a.Ei = Ei_dst;
     a.g = (Q4<float>*)g.p;
+    a.gT = (Q4<float>*)gT.p;
+    a.rev = (const int*)rev.p;
+    a.wpart = (double*)wpart.p;
     e = launch_atom_f32(mode, a, PA, has4, st);
   } else {
     AtomArgs<double> a;
@@ -579,6 +650,9 @@ int pod_handle::run_atoms(int mode, const Plan& pl, double* D, const double* c, 
     a.c = c;
     a.Ei = Ei_dst;
     a.g = (Q4<double>*)g.p;
+    a.gT = (Q4<double>*)gT.p;
+    a.rev = (const int*)rev.p;
+    a.wpart = (double*)wpart.p;
     e = launch_atom_f64(mode, a, PA, has4, st);
   }
   if (e != cudaSuccess) return cuda_fail(e, "atom kernel");
@@ -604,7 +678,8 @@ int pod_handle::validate_system(const pod_system* sys) {
   if (!sys) return fail(POD_EINVAL, "system is NULL");
   if (sys->n_atoms < 1) return fail(POD_EINVAL, "n_atoms must be >= 1");
   if (!sys->pos) return fail(POD_EINVAL, "positions are NULL");
-  if (sys->n_configs > 1) return fail(POD_EINVAL, "batched systems are only supported by pod_fit");
+  if (sys->n_configs > 1 && (!sys->atom_offs || !sys->boxes))
+    return fail(POD_EINVAL, "a batch needs atom_offs and boxes");
   return POD_OK;
 }
 
@@ -617,42 +692,45 @@ int pod_handle::energy_forces(const pod_system* sys, const double* c, double* E,
   retries = 0;
   for (;;) {
     Plan pl;
-    if ((rc_ = plan_single(N, sys->box, sys->pbc, pl))) return rc_;
+    if ((rc_ = plan(sys, pl))) return rc_;
+    if (pl.batched && W) return fail(POD_EINVAL, "the virial is not available for batches of configurations");
     if ((rc_ = mark(0, st))) return rc_;
     if ((rc_ = build_neighbors(sys->pos, pl, true, st))) return rc_;
     const size_t gbytes = (precision == POD_MIXED ? sizeof(Q4<float>) : sizeof(Q4<double>)) * (size_t)N * pl.cap;
     if ((rc_ = ensure(g, gbytes, "pair gradients"))) return rc_;
-    if ((rc_ = ensure(Wat, sizeof(double) * 9 * (size_t)N, "atom virials"))) return rc_;
+    if ((rc_ = ensure(gT, gbytes, "reverse pair gradients"))) return rc_;
+    const int nwarp = atom_warps(N, K);
+    if ((rc_ = ensure(wpart, sizeof(double) * 9 * (size_t)nwarp, "virial partials"))) return rc_;
     double* Ei_dst = Ei_user;
     if (!Ei_dst) {
       if ((rc_ = ensure(Ei, sizeof(double) * (size_t)N, "atom energies"))) return rc_;
       Ei_dst = (double*)Ei.p;
     }
-    if ((rc_ = ensure(offs, sizeof(int) * 2, "config offsets"))) return rc_;
-    if (offs_n != N) {
-      int ho[2] = {0, N};
-      cudaError_t e = cudaMemcpy(offs.p, ho, sizeof(ho), cudaMemcpyHostToDevice);
-      if (e != cudaSuccess) return cuda_fail(e, "offset upload");
-      offs_n = N;
+    const int nblk = gather_blocks(N);
+    if ((rc_ = ensure(Wat, sizeof(double) * 10 * (size_t)nblk, "block partial sums"))) return rc_;
+    if (!offs.p) {
+      if ((rc_ = ensure(offs, sizeof(unsigned) * 4, "ticket"))) return rc_;
+      cudaError_t e0 = cudaMemset(offs.p, 0, sizeof(unsigned) * 4);
+      if (e0 != cudaSuccess) return cuda_fail(e0, "ticket init");
     }
     if ((rc_ = mark(1, st))) return rc_;
     if ((rc_ = run_atoms(1, pl, nullptr, c, Ei_dst, st))) return rc_;
     if ((rc_ = mark(2, st))) return rc_;
     cudaError_t e;
     if (precision == POD_MIXED)
-      e = launch_gather<float>(N, pl.cap, (const int*)nbr_count.p, (const int*)nbr_j.p, (const int*)nbr_s.p,
-                               (const int*)rev.p, (const Q4<float>*)g.p, (const double*)wpos.p,
-                               (const float4*)phi.p, (const float4*)plo.p, pl.cg.L, F, (double*)Wat.p,
-                               (int*)status.p, st);
+      e = launch_gather_reduce<float>(N, pl.cap, (const int*)nbr_count.p, (const Q4<float>*)g.p,
+                                      (const Q4<float>*)gT.p, Ei_dst, (const double*)wpart.p, nwarp, F, 1.0,
+                                      (double*)Wat.p, nblk, (unsigned*)offs.p, E, W, (int*)status.p, st);
     else
-      e = launch_gather<double>(N, pl.cap, (const int*)nbr_count.p, (const int*)nbr_j.p, (const int*)nbr_s.p,
-                                (const int*)rev.p, (const Q4<double>*)g.p, (const double*)wpos.p,
-                                (const float4*)phi.p, (const float4*)plo.p, pl.cg.L, F, (double*)Wat.p,
-                                (int*)status.p, st);
+      e = launch_gather_reduce<double>(N, pl.cap, (const int*)nbr_count.p, (const Q4<double>*)g.p,
+                                       (const Q4<double>*)gT.p, Ei_dst, (const double*)wpart.p, nwarp, F, 1.0,
+                                       (double*)Wat.p, nblk, (unsigned*)offs.p, E, W, (int*)status.p, st);
     if (e != cudaSuccess) return cuda_fail(e, "gather kernel");
+    if (pl.batched) {  // per-configuration energies (the gather wrote the batch total into E[0])
+      e = launch_segsum(pl.n_cfg, (const CfgBox*)boxes.p, Ei_dst, 1.0, 0, E, st);
+      if (e != cudaSuccess) return cuda_fail(e, "per-configuration energy");
+    }
     if ((rc_ = mark(3, st))) return rc_;
-    e = launch_reduce(1, (const int*)offs.p, Ei_dst, W ? (const double*)Wat.p : nullptr, E, W, st);
-    if (e != cudaSuccess) return cuda_fail(e, "reduce kernel");
     if ((rc_ = mark(4, st))) return rc_;
     if ((rc_ = timing_collect())) return rc_;
     bool retry;
@@ -668,7 +746,7 @@ int pod_handle::descriptors(const pod_system* sys, double* D, cudaStream_t st) {
   retries = 0;
   for (;;) {
     Plan pl;
-    if ((rc_ = plan_single(sys->n_atoms, sys->box, sys->pbc, pl))) return rc_;
+    if ((rc_ = plan(sys, pl))) return rc_;
     if ((rc_ = build_neighbors(sys->pos, pl, false, st))) return rc_;
     if ((rc_ = run_atoms(0, pl, D, nullptr, nullptr, st))) return rc_;
     bool retry;
@@ -685,7 +763,7 @@ int pod_handle::neighbors(const pod_system* sys, int cap_out, int* count, int* n
   retries = 0;
   for (;;) {
     Plan pl;
-    if ((rc_ = plan_single(sys->n_atoms, sys->box, sys->pbc, pl))) return rc_;
+    if ((rc_ = plan(sys, pl))) return rc_;
     pl.cap = std::max(pl.cap, cap_out);
     if ((rc_ = build_neighbors(sys->pos, pl, false, st))) return rc_;
     cudaError_t e = launch_export_neighbors(sys->n_atoms, pl.cap, (const int*)nbr_count.p, (const int*)nbr_j.p,

@@ -13,7 +13,7 @@ constexpr int MAXK = 16;   // radial modes (= lanes per atom in the atom kernels
 constexpr int MAXROWS = MAXA * MAXB + MAXG;
 constexpr int PAMAX = 4;   // highest angular degree compiled
 constexpr int CH = 32;     // pairs per atom staged in shared memory at a time
-constexpr int WPB_ATOM = 4;   // warps per block, atom kernels
+constexpr int WPB_ATOM = 2;   // warps per block, atom kernels
 constexpr int WPB_NEIGH = 4;  // warps per block, neighbour kernel
 
 // device status bits (OR-ed into a status word, read by the host)
@@ -61,6 +61,15 @@ struct CellGrid {
   double inv_cs[3];
   int ncells;
   int cap;        // atoms per cell
+};
+
+// ------------------------------------------------ one configuration of a batch
+struct CfgBox {
+  double L[3];
+  float Lh[3], Ll[3];  // FP32 hi / lo split of L
+  int pbc[3];
+  int S[3];            // images searched per direction
+  int a0, a1;          // atom range [a0, a1)
 };
 
 // ------------------------------------------------ packed image shift

@@ -25,6 +25,11 @@ struct Plan {
   int N = 0;
   int cap = 0;  // neighbour capacity per atom
   fastpod::CellGrid cg{};
+  // batches of configurations (n_cfg > 1): per-atom configuration and boxes
+  bool batched = false;
+  int n_cfg = 1;
+  double Lmax = 0;
+  int Smax = 0;
 };
 
 struct pod_handle {
@@ -39,7 +44,6 @@ struct pod_handle {
   int retries = 0;
   int last_status = 0;
   int cap_nbr = 0, cap_cell = 0;  // grown after overflows
-  int offs_n = -1;
   int* h_status = nullptr;        // pinned
   int timing = 0;
   cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
@@ -51,6 +55,7 @@ struct pod_handle {
   DevBuf pos_in, c_in, E_out, F_out, W_out, Ei_out;       // host-buffer entry point staging
   DevBuf fitA, fitG, fitb, fitwork, cfg_of, boxes;        // fit
   DevBuf rtab;                                            // tabulated radial basis (mixed path)
+  DevBuf gT, wpart;                                       // reverse-slot gradients, virial partials
   static constexpr int TAB_N = 2048;
   int radial_mode = 0;  // mixed path: 0 = tabulated R_k, 1 = snapshots evaluated per pair
   bool tab_ready = false;
@@ -64,6 +69,19 @@ struct pod_handle {
   int read_status(cudaStream_t st);
   int validate_system(const pod_system* sys);
   int plan_single(int N, const double box[3], const int pbc[3], Plan& pl);
+  int plan_batch(const pod_system* sys, Plan& pl);
+  int plan(const pod_system* sys, Plan& pl);
+  std::vector<fastpod::CfgBox> h_cbox;
+  std::vector<int> h_cfg_of;
+  int fit(const pod_system* batch, const double* E_ref, const double* F_ref, const pod_fit_opts* opts,
+          double* c_out, double* mae_E, double* mae_F);
+  int fit_build(const pod_system* batch, const double* E_ref, const double* F_ref, const pod_fit_opts& o);
+  int fit_gram(double gamma);
+  int fit_solve_dev();
+  int fit_residual_dev(double* sumE, double* sumF);
+  long long fit_R = 0;
+  int fit_nc = 0, fit_N = 0;
+  double fit_wE = 0, fit_wF = 0;
   int build_neighbors(const double* pos, Plan& pl, bool need_rev, cudaStream_t st);
   template <typename T>
   void fill_args(fastpod::AtomArgs<T>& a, const Plan& pl);

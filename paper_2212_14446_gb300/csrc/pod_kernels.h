@@ -33,6 +33,11 @@ struct AtomArgs {
   const double* c;      // mode 1: coefficients [M]
   double* Ei;           // mode 1: atom energies [N]
   Q4<T>* g;             // mode 1: dE_i/dr_ij per pair slot [N * cap]
+  Q4<T>* gT;            // mode 1: the same gradient stored at the reverse slot rev[p]
+  const int* rev;       // mode 1: reverse slot of every pair slot
+  double* wpart;        // mode 1: per-warp virial partials [warps][9]
+  const int* cfg_of;    // batch: configuration of each atom (NULL: one configuration, box L)
+  const CfgBox* cbox;   // batch: per-configuration boxes
   int* status;
   RadialConst<T> rad;
 };
@@ -47,14 +52,23 @@ cudaError_t launch_rev(int N, int cap, const int* nbr_count, const int* nbr_j, c
 cudaError_t launch_export_neighbors(int N, int cap, const int* nbr_count, const int* nbr_j, const int* nbr_s,
                                     int cap_out, int* count_out, int* j_out, int* s_out, cudaStream_t st);
 
+cudaError_t launch_batch_wrap(int N, const double* pos, const int* cfg_of, const CfgBox* cbox, double* wpos,
+                              float4* phi, float4* plo, int* status, cudaStream_t st);
+cudaError_t launch_batch_neigh(int N, const int* cfg_of, const CfgBox* cbox, const double* wpos, const float4* phi,
+                               double rcut, double Lmax, int Smax, int cap, int* nbr_count, int* nbr_j, int* nbr_s,
+                               int* status, cudaStream_t st);
+cudaError_t launch_segsum(int n_cfg, const CfgBox* cbox, const double* v, double w, int per_atom, double* out,
+                          cudaStream_t st);
+
 cudaError_t launch_atom_f32(int mode, const AtomArgs<float>& p, int PA, bool has4, cudaStream_t st);
 cudaError_t launch_atom_f64(int mode, const AtomArgs<double>& p, int PA, bool has4, cudaStream_t st);
 
 template <typename T>
-cudaError_t launch_gather(int N, int cap, const int* nbr_count, const int* nbr_j, const int* nbr_s,
-                          const int* rev, const Q4<T>* g, const double* wpos, const float4* phi, const float4* plo,
-                          const double L[3], double* F, double* Wat, int* status, cudaStream_t st);
-cudaError_t launch_reduce(int n_cfg, const int* cfg_offs, const double* Ei, const double* Wat, double* E, double* W,
-                          cudaStream_t st);
+cudaError_t launch_gather_reduce(int N, int cap, const int* nbr_count, const Q4<T>* g, const Q4<T>* gT,
+                                 const double* Ei, const double* wpart, int n_wpart, double* F, double fscale,
+                                 double* part, int nblocks, unsigned* ticket, double* E, double* W, int* status,
+                                 cudaStream_t st);
+int atom_warps(int N, int K);
+int gather_blocks(int N);
 
 }  // namespace fastpod

@@ -1,0 +1,164 @@
+"""Batches of configurations and the ridge least-squares fit (Eq. 63a) on the GPU,
+compared with the FP64 oracle (its own design matrix, solved with numpy's SVD
+least squares).
+
+Tolerances: per-configuration descriptors, energies and forces as in
+test_gpu_parity.py; fitted coefficients: the GPU solves the normal equations
+(condition number squared) while the oracle uses SVD, so c is compared through
+the fitted energies and forces (relative 1e-8 of their scale) and directly with
+a tolerance scaled by the conditioning; noise-free labels from a teacher c*
+must give training errors at rounding level.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2212_14446_gb300 import build as b
+    b.build()
+    import paper_2212_14446_gb300 as p
+    return p
+
+
+def training_configs(n, replica=0, max_atoms=40):
+    out = []
+    k = 0
+    while len(out) < n:
+        cfg = synth.config_train(k, replica)
+        k += 1
+        if cfg.n <= max_atoms:
+            out.append(cfg)
+    return out
+
+
+def desc_err(D, Dref):
+    den = np.max(np.abs(Dref), axis=0)
+    den = np.where(den > 0, den, 1.0)
+    return float(np.max(np.max(np.abs(D - Dref), axis=0) / den))
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("mixed", 1e-5)])
+def test_batch_descriptors(pkg, prec, tol):
+    p = synth.params_full()
+    o = oracle.Oracle(p)
+    cfgs = training_configs(10)
+    pod = pkg.POD(p, precision=prec, Q=o.Q)
+    D = pod.descriptors_batch(cfgs).cpu().numpy()
+    Dref = np.concatenate([o.descriptors(c, fast=True) for c in cfgs], axis=0)
+    assert desc_err(D, Dref) <= tol
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_batch_energy_forces(pkg, prec):
+    p = synth.params_full()
+    o = oracle.Oracle(p)
+    cfgs = training_configs(8, replica=1)
+    c = synth.coefficients(o.M, 77)
+    pod = pkg.POD(p, precision=prec, Q=o.Q)
+    out = pod.energy_forces_batch(cfgs, torch.tensor(c))
+    E = out["E"].cpu().numpy()
+    F = out["F"].cpu().numpy()
+    offs = out["offs"]
+    for k, cfg in enumerate(cfgs):
+        _, Eo, Fo, _ = o.energy_forces(cfg, c, fast=True)
+        scale = float(np.sum(np.abs(o.descriptors(cfg, fast=True) * c)))
+        tol = 1e-12 if prec == "fp64" else 1e-5
+        assert abs(E[k] - Eo) <= tol * scale
+        Fk = F[offs[k]:offs[k + 1]]
+        if prec == "fp64":
+            assert np.max(np.abs(Fk - Fo)) <= 1e-10 * max(1.0, np.max(np.abs(Fo)))
+        else:
+            assert np.max(np.abs(Fk - Fo)) <= 1e-4
+
+
+def _labels(o, cfgs, c, noise=0.0, seed=0):
+    g = synth.rng(seed)
+    E_ref, F_ref = [], []
+    for cfg in cfgs:
+        _, E, F, _ = o.energy_forces(cfg, c, fast=True)
+        E_ref.append(E + noise * 1e-3 * cfg.n * g.normal())
+        F_ref.append(F + noise * 5e-2 * g.normal(size=F.shape))
+    return np.array(E_ref), F_ref
+
+
+def test_fit_recovers_teacher(pkg):
+    p = synth.params_small()
+    o = oracle.Oracle(p)
+    cfgs = training_configs(16, replica=2)
+    cstar = synth.coefficients(o.M, 12)
+    E_ref, F_ref = _labels(o, cfgs, cstar)
+    pod = pkg.POD(p, precision="fp64", Q=o.Q)
+    c, maeE, maeF = pod.fit(cfgs, E_ref, F_ref)
+    A, b = o.design_matrix(cfgs, E_ref, F_ref)
+    # fitted values agree with the teacher's to rounding level
+    assert np.max(np.abs(A @ c - b)) <= 1e-8 * np.max(np.abs(b))
+    assert maeE <= 1e-9 and maeF <= 1e-8
+    assert np.allclose(c, cstar, rtol=1e-5, atol=1e-7)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_fit_matches_oracle_with_noise(pkg, prec):
+    p = synth.params_full()
+    o = oracle.Oracle(p)
+    cfgs = training_configs(24, replica=3, max_atoms=30)
+    cstar = synth.coefficients(o.M, 13)
+    E_ref, F_ref = _labels(o, cfgs, cstar, noise=1.0, seed=5)
+    c_o, A, b = o.fit(cfgs, E_ref, F_ref)
+    pod = pkg.POD(p, precision=prec, Q=o.Q)
+    c, maeE, maeF = pod.fit(cfgs, E_ref, F_ref)
+    # same fitted energies and forces (the predictions are what the fit fixes)
+    pred, pred_o = A @ c, A @ c_o
+    tol = 1e-7 if prec == "fp64" else 1e-3
+    assert np.max(np.abs(pred - pred_o)) <= tol * np.max(np.abs(b))
+    # training errors as the oracle computes them (its rows: per configuration
+    # one energy row followed by 3 N_c force rows)
+    e_rows, r = [], 0
+    for cfg in cfgs:
+        e_rows.append(r)
+        r += 1 + 3 * cfg.n
+    is_e = np.zeros(len(b), dtype=bool)
+    is_e[e_rows] = True
+    res = np.abs(pred_o - b)
+    maeE_o = res[is_e].mean() / 100.0
+    maeF_o = res[~is_e].mean()
+    assert maeE == pytest.approx(maeE_o, rel=1e-3 if prec == "fp64" else 5e-2)
+    assert maeF == pytest.approx(maeF_o, rel=1e-3 if prec == "fp64" else 5e-2)
+
+
+def test_fit_singular_reports_error(pkg):
+    """gamma = 0 with a single one-atom configuration: the normal equations are
+    singular (only the one-body column is non-zero) and the call says so."""
+    p = synth.params_small()
+    pod = pkg.POD(p, precision="fp64")
+    one = synth.Config(pos=np.array([[1.0, 1.0, 1.0]]), box=np.array([20.0, 20.0, 20.0]), pbc=(0, 0, 0))
+    with pytest.raises(pkg.PodError) as ei:
+        pod.fit([one], np.array([0.5]), [np.zeros((1, 3))], gamma=0.0)
+    assert ei.value.code == pkg.POD_ESINGULAR
+
+
+def test_fit_stages_equal_single_call(pkg):
+    """pod_fit_normal + pod_fit_solve + pod_fit_residual (the sharded-fit
+    building blocks) reproduce pod_fit bit for bit on one GPU."""
+    p = synth.params_small()
+    o = oracle.Oracle(p)
+    cfgs = training_configs(12, replica=4)
+    cstar = synth.coefficients(o.M, 21)
+    E_ref, F_ref = _labels(o, cfgs, cstar, noise=1.0, seed=8)
+    pod = pkg.POD(p, precision="fp64", Q=o.Q)
+    c, maeE, maeF = pod.fit(cfgs, E_ref, F_ref)
+    G, r = pod.fit_normal(cfgs, E_ref, F_ref)
+    assert np.allclose(G, G.T, rtol=0, atol=0)
+    c2 = pod.fit_solve(G, r)
+    se, sf, ne, nf = pod.fit_residual(c2)
+    assert np.array_equal(c, c2)
+    assert ne == len(cfgs) and nf == 3 * sum(cf.n for cf in cfgs)
+    assert se / ne == pytest.approx(maeE, rel=1e-14) and sf / nf == pytest.approx(maeF, rel=1e-14)

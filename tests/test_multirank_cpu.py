@@ -1,0 +1,127 @@
+"""The sharded fit on two CPU ranks (gloo): each rank forms the normal equations
+of its round-robin share of configurations from the oracle's design matrix, one
+all-reduce sums them, every rank solves; the result must equal the oracle's
+single-process fit.  Exercises the sharding and reduction logic of
+paper_2212_14446_gb300.parallel without a GPU."""
+import os
+import socket
+
+import numpy as np
+import pytest
+import torch
+import torch.distributed as dist
+import torch.multiprocessing as mp
+
+import oracle
+import synth
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    p = s.getsockname()[1]
+    s.close()
+    return p
+
+
+def _configs():
+    out, k = [], 0
+    while len(out) < 9:
+        cfg = synth.config_train(k, 7)
+        k += 1
+        if cfg.n <= 24:
+            out.append(cfg)
+    return out
+
+
+class _OraclePod:
+    """Stands in for the GPU handle: normal equations, solve and residuals from
+    the oracle's design matrix."""
+
+    def __init__(self, o):
+        self.o = o
+        self.M = o.M
+        self.A = self.b = None
+        self.n_e = 0
+
+    def normal(self, cfgs, E, F, gamma):
+        A, b = self.o.design_matrix(cfgs, E, F)
+        self.A, self.b = A, b
+        e_rows, r = [], 0
+        for cfg in cfgs:
+            e_rows.append(r)
+            r += 1 + 3 * cfg.n
+        self.is_e = np.zeros(len(b), dtype=bool)
+        self.is_e[e_rows] = True
+        return A.T @ A + gamma * np.eye(self.M), A.T @ b
+
+    def solve(self, G, r):
+        L = np.linalg.cholesky(G)
+        return np.linalg.solve(L.T, np.linalg.solve(L, r))
+
+    def residual(self, c):
+        res = np.abs(self.A @ c - self.b)
+        return res[self.is_e].sum() / 100.0, res[~self.is_e].sum(), int(self.is_e.sum()), int((~self.is_e).sum())
+
+
+def _worker(rank, world, port, q):
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        from paper_2212_14446_gb300 import parallel
+        p = synth.params_small()
+        o = oracle.Oracle(p)
+        cfgs = _configs()
+        cstar = synth.coefficients(o.M, 3)
+        g = synth.rng(11)
+        E_ref, F_ref = [], []
+        for cfg in cfgs:
+            _, E, F, _ = o.energy_forces(cfg, cstar, fast=True)
+            E_ref.append(E + 1e-3 * cfg.n * g.normal())
+            F_ref.append(F + 5e-2 * g.normal(size=F.shape))
+        fake = _OraclePod(o)
+        c, maeE, maeF = parallel.fit_sharded(fake, cfgs, np.array(E_ref), F_ref, normal=fake.normal,
+                                             solve=fake.solve, residual=fake.residual)
+        q.put((rank, c, maeE, maeF))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_sharded_fit_two_ranks():
+    port = _free_port()
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    procs = [ctx.Process(target=_worker, args=(r, 2, port, q)) for r in range(2)]
+    for pr in procs:
+        pr.start()
+    res = [q.get(timeout=300) for _ in procs]
+    for pr in procs:
+        pr.join(timeout=60)
+        assert pr.exitcode == 0
+    res.sort(key=lambda t: t[0])
+    (_, c0, e0, f0), (_, c1, e1, f1) = res
+    assert np.array_equal(c0, c1) and e0 == e1 and f0 == f1  # every rank holds the same solution
+    # the single-process oracle fit
+    p = synth.params_small()
+    o = oracle.Oracle(p)
+    cfgs = _configs()
+    cstar = synth.coefficients(o.M, 3)
+    g = synth.rng(11)
+    E_ref, F_ref = [], []
+    for cfg in cfgs:
+        _, E, F, _ = o.energy_forces(cfg, cstar, fast=True)
+        E_ref.append(E + 1e-3 * cfg.n * g.normal())
+        F_ref.append(F + 5e-2 * g.normal(size=F.shape))
+    c_ref, A, b = o.fit(cfgs, E_ref, F_ref)
+    assert np.max(np.abs(A @ c0 - A @ c_ref)) <= 1e-8 * np.max(np.abs(b))
+
+
+def test_shard_indices_cover_everything():
+    from paper_2212_14446_gb300 import parallel
+    for n in (0, 1, 5, 9, 2000):
+        for w in (1, 2, 3, 8):
+            got = sorted(i for r in range(w) for i in parallel.shard_indices(n, r, w))
+            assert got == list(range(n))
+            sizes = [len(parallel.shard_indices(n, r, w)) for r in range(w)]
+            assert max(sizes) - min(sizes) <= 1
