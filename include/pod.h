@@ -207,6 +207,27 @@ int pod_fit_normal(pod_handle* h, const pod_system* batch, const double* E_ref, 
 int pod_fit_solve(pod_handle* h, const double* G, const double* r, double* c_out);
 int pod_fit_residual(pod_handle* h, const double* c, double* sum_abs_E, double* sum_abs_F, int* n_E, int* n_F);
 
+/* pod_descriptors without any memory allocation.  The paper has no counterpart:
+ * this is a deployment variant for callers that cannot let a library allocate
+ * device memory -- for example molecular-dynamics engines and plugins that keep
+ * all device memory in their own pool with a fixed budget and forbid other code
+ * from calling cudaMalloc / cudaFree (which synchronise the device and fragment
+ * the pool).  The caller passes the positions (device [3][N]) and the output D
+ * (device [N][M]), as for pod_descriptors; every intermediate buffer lives in one
+ * file-scope device array of about 4.3 MB that each GPU loading the library holds
+ * until the process exits.
+ *   Limits: one configuration of 1..4096 atoms (POD_EINVAL beyond), at most 64
+ *   neighbours per atom and 64 atoms per cell (POD_ENEIGH beyond).
+ *   The mixed path evaluates the radial snapshots per pair (POD_OPT_RADIAL = 1
+ *   behaviour; descriptor error ~1e-5); the FP64 path is identical to
+ *   pod_descriptors.
+ *   The first call on a device looks up the array's device address with that
+ *   device current (cudaGetSymbolAddress) and caches it.
+ *   All calls share the array and it keeps the previous call's contents: calls
+ *   that overlap on the GPU (other streams or host threads) race and must be
+ *   serialised by the caller.  Waits for `stream` before returning. */
+int pod_descriptors_static(pod_handle* h, const pod_system* sys, double* D, void* stream);
+
 /* Message of the last error on this handle ("" if none).  Owned by the handle. */
 const char* pod_last_error(const pod_handle* h);
 

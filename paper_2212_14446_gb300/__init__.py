@@ -60,7 +60,7 @@ class pod_fit_opts(C.Structure):
 
 EXPORTS = ["pod_create", "pod_destroy", "pod_info", "pod_set_option", "pod_status", "pod_timing",
            "pod_neighbors", "pod_descriptors", "pod_energy_forces", "pod_energy_forces_host", "pod_fit",
-           "pod_fit_normal", "pod_fit_solve", "pod_fit_residual", "pod_last_error"]
+           "pod_fit_normal", "pod_fit_solve", "pod_fit_residual", "pod_descriptors_static", "pod_last_error"]
 
 _lib = None
 _lock = threading.Lock()
@@ -87,6 +87,7 @@ def lib():
                 "pod_timing": (C.c_int, [H, dp, ip]),
                 "pod_neighbors": (C.c_int, [H, S, C.c_int, ip, ip, ip, vp]),
                 "pod_descriptors": (C.c_int, [H, S, dp, vp]),
+                "pod_descriptors_static": (C.c_int, [H, S, dp, vp]),
                 "pod_energy_forces": (C.c_int, [H, S, dp, dp, dp, dp, dp, vp]),
                 "pod_energy_forces_host": (C.c_int, [H, S, dp, dp, dp, dp, dp, vp]),
                 "pod_fit": (C.c_int, [H, S, dp, dp, C.POINTER(pod_fit_opts), dp, dp, dp]),
@@ -174,6 +175,11 @@ def make_system(pos_ptr, n_atoms, box, pbc=(1, 1, 1), batch=None):
 
 def pod_descriptors(h, sys, D, stream=None):
     _check(h, lib().pod_descriptors(h, C.byref(sys), _dptr(D), _stream(stream)))
+
+
+def pod_descriptors_static(h, sys, D, stream=None):
+    """Descriptors of one configuration (<= 4096 atoms) without any allocation."""
+    _check(h, lib().pod_descriptors_static(h, C.byref(sys), _dptr(D), _stream(stream)))
 
 
 def pod_energy_forces(h, sys, c, E, Ei=None, F=None, W=None, stream=None):
