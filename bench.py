@@ -202,7 +202,8 @@ def main():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="full", choices=["full", "md", "small", "fig4"])
+    ap.add_argument("--workload", default="full", choices=["full", "md", "small", "fig4", "mdrun", "fit"])
+    ap.add_argument("--fit-configs", type=int, default=2000)
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64-path comparison line items")
@@ -214,6 +215,10 @@ def main():
 
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if args.workload == "mdrun":
+        return run_md(args, rank, world, local)
+    if args.workload == "fit":
+        return run_fit(args, rank, world, local)
 
     import torch
     import paper_2212_14446_gb300 as pkg
@@ -412,6 +417,129 @@ def main():
     if dist:
         dist.barrier()
         dist.destroy_process_group()
+
+
+def run_md(args, rank, world, local):
+    """1,024,000-atom BCC Ta velocity-Verlet MD (dt = 1 fs, Ta mass, 300 K
+    velocities): neighbour list with a 0.3 A skin rebuilt every 10 steps, each
+    step one replay of a captured CUDA graph (one graph for rebuild steps, one
+    for reuse steps).  Timed: `steps` consecutive MD steps (state > L2)."""
+    import torch
+    import paper_2212_14446_gb300 as pkg
+    from paper_2212_14446_gb300 import build as pbuild
+    torch.cuda.set_device(local)
+    if rank == 0:
+        pbuild.build()
+    dev = torch.device("cuda", local)
+    params, cfg, wname = workload("md", replica=rank)
+    N = cfg.n
+    pod = pkg.POD(params, precision=args.precision)
+    pod.set_skin(0.3)
+    # a random coefficient vector is not a stable crystal potential: with sigma = 0.01 the atoms
+    # collide within ~100 fs; sigma = 1e-4 keeps the 100-step run inside the skin (the cost of a
+    # step does not depend on the values of c)
+    c = torch.tensor(synth.coefficients(pod.M, 2001 + rank, sigma=1e-4), dtype=torch.float64, device=dev)
+    x = torch.tensor(np.ascontiguousarray(cfg.pos.T), dtype=torch.float64, device=dev)
+    mass, dt = 180.94788, 1.0
+    g = synth.rng(4000 + rank)
+    vrms = math.sqrt(8.617333e-5 * 300.0 / mass * 9.648533212e-3)
+    v = torch.tensor(g.normal(0.0, vrms, size=(3, N)), dtype=torch.float64, device=dev)
+    E = torch.zeros(1, dtype=torch.float64, device=dev)
+    stream = torch.cuda.Stream(device=dev)
+    with torch.cuda.stream(stream):
+        F = pod.energy_forces(x, cfg.box, c, stream=stream)["F"].t().contiguous()
+        for k in range(max(args.warmup, 3)):
+            pod.set_neighbor_reuse(k % 10 != 0)
+            pod.md_step(x, v, F, c, cfg.box, mass, dt, E, stream=stream)
+    torch.cuda.synchronize()
+    pod.set_sync(False)
+    graphs = {}
+    for reuse in (False, True):
+        pod.set_neighbor_reuse(reuse)
+        gr = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(gr, stream=stream):
+            pod.md_step(x, v, F, c, cfg.box, mass, dt, E, stream=stream)
+        graphs[reuse] = gr
+    torch.cuda.synchronize()
+    st = pkg.pod_status(pod.h, stream)
+    if st != pkg.POD_OK:
+        raise pkg.PodError(st, pkg.pod_last_error(pod.h))
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    with torch.cuda.stream(stream):
+        e0.record(stream)
+        for k in range(args.steps):
+            graphs[k % 10 != 0].replay()
+        e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    st = pkg.pod_status(pod.h, stream)
+    if st != pkg.POD_OK:
+        raise pkg.PodError(st, pkg.pod_last_error(pod.h))
+    ms = e0.elapsed_time(e1)
+    line = {"metric": "atom-steps/s (E+F) mixed vs FP64 at stated force error; % of roofline",
+            "value": N * args.steps / (ms / 1e3), "unit": "atom-steps/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32" if args.precision == "mixed" else "f64", "data": "synthetic",
+            "config": {"workload": "bcc_ta_1024000_md_verlet", "atoms_per_gpu": N, "skin_A": 0.3, "c_sigma": 1e-4,
+                       "neighbor_rebuild": "every 10 steps", "dt_fs": dt, "graph": "captured rebuild/reuse steps",
+                       "l2": "state larger than L2"},
+            "final_energy_eV": E.item(), "clocks": clk, "gpu_launches": None}
+    if rank == 0:
+        print(json.dumps(line))
+
+
+def run_fit(args, rank, world, local):
+    """Batched fit of `--fit-configs` training configurations (BCC/FCC/A15 with
+    vacancies and liquid packings, 2..250 atoms, volume strain +-20 %): labels
+    from a teacher coefficient vector through the batched FP64 energy/force path,
+    then pod_fit (design matrix, FP64 Gram, Cholesky).  Metric: configs/s of
+    the fit call (CUDA events around it)."""
+    import torch
+    import paper_2212_14446_gb300 as pkg
+    from paper_2212_14446_gb300 import build as pbuild
+    torch.cuda.set_device(local)
+    if rank == 0:
+        pbuild.build()
+    params = synth.params_full()
+    cfgs = synth.training_set(args.fit_configs, replica=rank)
+    pod = pkg.POD(params, precision=args.precision)
+    teacher = pkg.POD(params, precision="fp64", Q=pod.Q)
+    cstar = torch.tensor(synth.coefficients(pod.M, 3001), dtype=torch.float64)
+    out = teacher.energy_forces_batch(cfgs, cstar)
+    E_ref = out["E"].cpu().numpy()
+    Fall = out["F"].cpu().numpy()
+    offs = out["offs"]
+    F_ref = [Fall[offs[k]:offs[k + 1]] for k in range(len(cfgs))]
+    for _ in range(max(1, args.warmup)):
+        pod.fit(cfgs, E_ref, F_ref)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    ts = []
+    for _ in range(args.steps):
+        torch.cuda.synchronize()
+        e0.record()
+        c, maeE, maeF = pod.fit(cfgs, E_ref, F_ref)
+        e1.record()
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    ms = sum(ts) / len(ts)
+    n_atoms = int(offs[-1])
+    rel = float(np.max(np.abs(c - cstar.numpy())) / np.max(np.abs(cstar.numpy())))
+    line = {"metric": "configs/s (fit: descriptors + gradients into the design matrix, FP64 normal equations, "
+                      "Cholesky)",
+            "value": len(cfgs) / (ms / 1e3), "unit": "configs/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32" if args.precision == "mixed" else "f64", "data": "synthetic",
+            "config": {"workload": f"training_set_{len(cfgs)}", "atoms": n_atoms, "design_rows": len(cfgs) + 3 * n_atoms,
+                       "descriptors": pod.M},
+            "teacher_recovery_max_rel": rel, "mae_E_per_atom": maeE, "mae_F": maeF}
+    if rank == 0:
+        print(json.dumps(line))
 
 
 def kernel_revision():

@@ -119,7 +119,30 @@ int pod_info(const pod_handle* h, int* M, int* Ns, int* K, double* Q_out, double
                             Hermite table built in FP64 at first use (relative error
                             ~1e-7); 1 = snapshots evaluated per pair in FP32 and
                             projected (Eq. 3-12; POD cancellation costs ~1e-5)  */
+#define POD_OPT_NEIGHBOR_REUSE 5 /* 1: pod_energy_forces reuses the list of its previous call
+                                   (single configuration, same size and box) instead of
+                                   rebuilding it; requires a skin (pod_set_skin) that
+                                   covers the displacements since that call */
 int pod_set_option(pod_handle* h, int option, int value);
+
+/* Neighbour-list skin (A, default 0): lists are built with r_cut + skin and pairs
+ * beyond r_cut contribute nothing, so a list stays valid while no atom has moved
+ * more than skin / 2 since it was built (standard MD practice; the paper's
+ * cut-off of Section 2.2 is unchanged).  Between rebuilds positions are shifted
+ * by the box multiples frozen at the build, so atoms may cross the box edge.
+ * Errors: POD_EINVAL. */
+int pod_set_skin(pod_handle* h, double skin);
+
+/* One velocity-Verlet step of the linear POD potential for a single
+ * configuration: v += F dt / 2m; pos += v dt; F <- F(pos) (pod_energy_forces,
+ * honouring POD_OPT_NEIGHBOR_REUSE); v += F dt / 2m.  pos, v, F: device [3][N],
+ * updated in place (F must hold the forces at the input positions); sys gives N,
+ * box and pbc (sys->pos is ignored); c device [M]; E device [1] receives the
+ * potential energy at the new positions.  mass in atomic mass units, dt in fs,
+ * energies in eV and lengths in A (1 eV/(A amu) = 9.648533212e-3 A/fs^2).
+ * Errors as pod_energy_forces. */
+int pod_md_step(pod_handle* h, const pod_system* sys, double* pos, double* v, double* F, const double* c,
+                double mass, double dt, double* E, void* stream);
 
 /* Per-phase device time of the pod_energy_forces calls made while
  * POD_OPT_TIMING was on, measured with CUDA events recorded on the call's stream
@@ -164,6 +187,19 @@ int pod_descriptors(pod_handle* h, const pod_system* sys, double* D, void* strea
  * Errors: POD_EINVAL, POD_ERANGE, POD_ENEIGH, POD_ENONFINITE, POD_ECUDA. */
 int pod_energy_forces(pod_handle* h, const pod_system* sys, const double* c, double* E, double* Ei, double* F,
                       double* W, void* stream);
+
+/* Global descriptors G_m = sum_{i in config} D_im (Eq. 58a): device
+ * [max(1, n_configs)][M].  dE/dc = G for the linear model.  Errors as
+ * pod_descriptors. */
+int pod_global_descriptors(pod_handle* h, const pod_system* sys, double* G, void* stream);
+
+/* Directional derivative of the global descriptors along per-atom displacements:
+ * Gdot_m = sum_k (dG_m/dr_k) . v_k, v device [3][N] (same layout as positions),
+ * Gdot device [max(1, n_configs)][M], computed in one forward-mode pass through
+ * Eq. 24b / 26a / 27a / 30a (dB/dr of Eq. 24c along r_j - r_i).  Since the
+ * forces are linear in c, the gradient of any force loss L(F) with respect to c
+ * is dL/dc = -Gdot evaluated at v = dL/dF.  Errors as pod_descriptors. */
+int pod_descriptors_jvp(pod_handle* h, const pod_system* sys, const double* v, double* Gdot, void* stream);
 
 /* pod_energy_forces with HOST buffers: sys->pos, c, E, Ei, F, W are host
  * pointers (pinned memory is fastest).  Copies inputs to library-owned device

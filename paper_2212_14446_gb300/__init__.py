@@ -26,7 +26,7 @@ LIB_PATH = os.path.join(_HERE, "_lib", "libfastpod.so")
 POD_OK, POD_EINVAL, POD_ENOMEM, POD_ECUDA, POD_ERANGE, POD_ENONFINITE, POD_ESINGULAR, POD_ENEIGH = (
     0, -1, -2, -3, -4, -5, -6, -7)
 POD_FP64, POD_MIXED = 0, 1
-POD_OPT_SYNC, POD_OPT_PRECISION, POD_OPT_TIMING, POD_OPT_RADIAL = 1, 2, 3, 4
+POD_OPT_SYNC, POD_OPT_PRECISION, POD_OPT_TIMING, POD_OPT_RADIAL, POD_OPT_NEIGHBOR_REUSE = 1, 2, 3, 4, 5
 ERROR_NAMES = {0: "POD_OK", -1: "POD_EINVAL", -2: "POD_ENOMEM", -3: "POD_ECUDA", -4: "POD_ERANGE",
                -5: "POD_ENONFINITE", -6: "POD_ESINGULAR", -7: "POD_ENEIGH"}
 
@@ -60,7 +60,8 @@ class pod_fit_opts(C.Structure):
 
 EXPORTS = ["pod_create", "pod_destroy", "pod_info", "pod_set_option", "pod_status", "pod_timing",
            "pod_neighbors", "pod_descriptors", "pod_energy_forces", "pod_energy_forces_host", "pod_fit",
-           "pod_fit_normal", "pod_fit_solve", "pod_fit_residual", "pod_descriptors_static", "pod_last_error"]
+           "pod_fit_normal", "pod_fit_solve", "pod_fit_residual", "pod_descriptors_static",
+           "pod_global_descriptors", "pod_descriptors_jvp", "pod_set_skin", "pod_md_step", "pod_last_error"]
 
 _lib = None
 _lock = threading.Lock()
@@ -88,6 +89,10 @@ def lib():
                 "pod_neighbors": (C.c_int, [H, S, C.c_int, ip, ip, ip, vp]),
                 "pod_descriptors": (C.c_int, [H, S, dp, vp]),
                 "pod_descriptors_static": (C.c_int, [H, S, dp, vp]),
+                "pod_global_descriptors": (C.c_int, [H, S, dp, vp]),
+                "pod_descriptors_jvp": (C.c_int, [H, S, dp, dp, vp]),
+                "pod_set_skin": (C.c_int, [H, C.c_double]),
+                "pod_md_step": (C.c_int, [H, S, dp, dp, dp, dp, C.c_double, C.c_double, dp, vp]),
                 "pod_energy_forces": (C.c_int, [H, S, dp, dp, dp, dp, dp, vp]),
                 "pod_energy_forces_host": (C.c_int, [H, S, dp, dp, dp, dp, dp, vp]),
                 "pod_fit": (C.c_int, [H, S, dp, dp, C.POINTER(pod_fit_opts), dp, dp, dp]),
@@ -294,6 +299,18 @@ class POD:
         """Mixed path: 'table' (default) or 'direct' radial evaluation."""
         pod_set_option(self.h, POD_OPT_RADIAL, 0 if mode == "table" else 1)
 
+    def set_skin(self, skin: float):
+        _check(self.h, lib().pod_set_skin(self.h, float(skin)))
+
+    def set_neighbor_reuse(self, on: bool):
+        pod_set_option(self.h, POD_OPT_NEIGHBOR_REUSE, 1 if on else 0)
+
+    def md_step(self, pos_soa, v, F, c, box, mass, dt, E, pbc=(1, 1, 1), stream=None):
+        """One velocity-Verlet step; pos_soa, v, F: (3, N) float64 CUDA tensors updated in place."""
+        sysd = self.system(pos_soa, box, pbc)
+        _check(self.h, lib().pod_md_step(self.h, C.byref(sysd), _dptr(pos_soa), _dptr(v), _dptr(F), _dptr(c),
+                                         float(mass), float(dt), _dptr(E), _stream(stream)))
+
     def set_timing(self, on: bool):
         pod_set_option(self.h, POD_OPT_TIMING, 1 if on else 0)
 
@@ -319,6 +336,25 @@ class POD:
         D = torch.empty((x.shape[1], self.M), dtype=torch.float64, device=x.device)
         pod_descriptors(self.h, self.system(x, box, pbc), D, stream)
         return D
+
+    def global_descriptors(self, pos, box, pbc=(1, 1, 1), stream=None):
+        """G_m = sum_i D_im (Eq. 58a): (1, M) float64."""
+        import torch
+        x = _soa(pos)
+        G = torch.empty((1, self.M), dtype=torch.float64, device=x.device)
+        _check(self.h, lib().pod_global_descriptors(self.h, C.byref(self.system(x, box, pbc)), _dptr(G),
+                                                    _stream(stream)))
+        return G
+
+    def descriptors_jvp(self, pos, box, v, pbc=(1, 1, 1), stream=None):
+        """sum_k dG_m/dr_k . v_k for per-atom directions v ((N, 3) or (3, N)): (1, M)."""
+        import torch
+        x = _soa(pos)
+        vv = _soa(v)
+        Gd = torch.empty((1, self.M), dtype=torch.float64, device=x.device)
+        _check(self.h, lib().pod_descriptors_jvp(self.h, C.byref(self.system(x, box, pbc)), _dptr(vv), _dptr(Gd),
+                                                 _stream(stream)))
+        return Gd
 
     def energy_forces(self, pos, box, c, pbc=(1, 1, 1), atom_energies=True, forces=True, virial=True,
                       stream=None):

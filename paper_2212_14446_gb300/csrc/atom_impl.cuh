@@ -50,9 +50,10 @@ __device__ __forceinline__ void pair_disp<float>(const AtomArgs<float>& p, int i
 __device__ __forceinline__ int chunk_count(int n, int ch) { return min(max(n - ch * CH, 0), CH); }
 
 // Stage chunk `ch` of the warp's pairs: (u, r) and R, R' per pair.
-template <typename T, int KT>
+template <typename T, int KT, bool TANGENT = false>
 __device__ __forceinline__ void pair_pass(const AtomArgs<T>& p, const AtomLayout& lay, Q4<T>* geo, T* sR, T* sRp,
-                                          const int* scnt, int atom0, int A, int K, int ch, int lane) {
+                                          const int* scnt, int atom0, int A, int K, int ch, int lane,
+                                          Q4<T>* sV = nullptr) {
   int tot = 0;
   for (int a = 0; a < A; ++a) tot += chunk_count(scnt[a], ch);
   for (int f = lane; f < tot; f += 32) {
@@ -78,10 +79,10 @@ __device__ __forceinline__ void pair_pass(const AtomArgs<T>& p, const AtomLayout
     gq.w = r;
     geo[a * lay.GA + jj] = gq;
     T R[KT], Rp[KT];
-    if (r > p.rad.r_in) {
+    if (r > p.rad.r_in && (p.rmask <= 0.0 || (double)r < p.rmask)) {
       radial_pair<T, KT>(p.rad, r, R, Rp);
     } else {
-      atomicOr(p.status, ST_RANGE);
+      if (!(r > p.rad.r_in)) atomicOr(p.status, ST_RANGE);
 #pragma unroll
       for (int k = 0; k < KT; ++k) { R[k] = T(0); Rp[k] = T(0); }
     }
@@ -91,7 +92,16 @@ __device__ __forceinline__ void pair_pass(const AtomArgs<T>& p, const AtomLayout
       if (KT == MAXK && k >= K) break;
       Rrow[k] = R[k];
     }
-    if (!p.rad.tab) {  // direct evaluation: keep R' for the adjoint pass
+    if (TANGENT) {  // relative displacement direction of the pair
+      const size_t N = p.N;
+      Q4<T> vq;
+      vq.x = (T)(p.vdir[j] - p.vdir[i]);
+      vq.y = (T)(p.vdir[N + j] - p.vdir[N + i]);
+      vq.z = (T)(p.vdir[2 * N + j] - p.vdir[2 * N + i]);
+      vq.w = T(0);
+      sV[a * lay.GA + jj] = vq;
+    }
+    if (!p.rad.tab || TANGENT) {  // keep R' for the adjoint / tangent pass
       T* Rprow = sRp + a * lay.SA + jj * lay.KS;
 #pragma unroll
       for (int k = 0; k < KT; ++k) {
@@ -116,6 +126,7 @@ __global__ void __launch_bounds__(WPB_ATOM * 32) atom_kernel(const AtomArgs<T> p
   T* sadj = reinterpret_cast<T*>(wb + lay.off_adj);
   T* se = reinterpret_cast<T*>(wb + lay.off_e);
   int* scnt = reinterpret_cast<int*>(wb + lay.off_cnt);
+  Q4<T>* sV = reinterpret_cast<Q4<T>*>(wb + lay.off_V);
 
   const int K = (KT == MAXK) ? p.K : KT;
   const int A = (KT == MAXK) ? lay.A : 32 / KT;
@@ -136,6 +147,61 @@ __global__ void __launch_bounds__(WPB_ATOM * 32) atom_kernel(const AtomArgs<T> p
   const int nchunks = (nmax + CH - 1) / CH;
   const bool am = (a_loc < A) && (atom0 + a_loc < p.N);
   const int my_n = am ? scnt[a_loc] : 0;
+
+  if (MODE == 2) {
+    // ---------------- tangent: dD_i along relative displacements (v_j - v_i) per pair
+    T B[NA], Bd[NA];
+#pragma unroll
+    for (int x = 0; x < NA; ++x) { B[x] = T(0); Bd[x] = T(0); }
+    for (int ch = 0; ch < nchunks; ++ch) {
+      pair_pass<T, KT, true>(p, lay, geo, sR, sRp, scnt, atom0, A, K, ch, lane, sV);
+      __syncwarp();
+      if (am) {
+        const int nc = chunk_count(my_n, ch);
+        for (int jj = 0; jj < nc; ++jj) {
+          const Q4<T> u = geo[a_loc * lay.GA + jj];
+          const Q4<T> v = sV[a_loc * lay.GA + jj];
+          const T R = sR[a_loc * lay.SA + jj * lay.KS + m];
+          const T Rp = sRp[a_loc * lay.SA + jj * lay.KS + m];
+          const T sdot = u.x * v.x + u.y * v.y + u.z * v.z;  // d r / d eps
+          const T ir = T(1) / u.w;
+          // d u / d eps = (v - (u . v) u) / r
+          T Am[NA], dA[NA];
+          Mono<PA>::eval_d(u.x, u.y, u.z, (v.x - sdot * u.x) * ir, (v.y - sdot * u.y) * ir,
+                           (v.z - sdot * u.z) * ir, Am, dA);
+          const T Rs = Rp * sdot;
+#pragma unroll
+          for (int x = 0; x < NA; ++x) {
+            B[x] = fma(R, Am[x], B[x]);
+            Bd[x] = fma(Rs, Am[x], fma(R, dA[x], Bd[x]));
+          }
+        }
+      }
+      __syncwarp();
+    }
+    if (am) {
+      const int i = atom0 + a_loc;
+      double* Di = p.D + (size_t)i * p.M;
+      if (m == 0) Di[0] = 0.0;
+      if (m < p.K2) Di[1 + m] = (double)Bd[0];
+      T d3[PA + 1], d3d[PA + 1];
+      Mono<PA>::d3(B, d3);
+      Mono<PA>::d3_tangent(B, Bd, d3d);
+      if (m < p.K3) {
+#pragma unroll
+        for (int n = 0; n <= PA; ++n)
+          if (n <= p.P3) Di[p.col3 + m * (p.P3 + 1) + n] = (double)d3d[n];
+      }
+      if (HAS4 && m < p.K4) {
+        T Dd[KA];
+        Four<PA>::tangent(B, Bd, d3, d3d, Dd);
+#pragma unroll
+        for (int q = 0; q < KA; ++q)
+          if (q < p.KA4) Di[p.col4 + m * p.KA4 + q] = (double)Dd[q];
+      }
+    }
+    return;
+  }
 
   // ---------------- forward: B_m[x] = sum_j R_m(r_ij) A_x(u_ij)   (Eq. 24b)
   T B[NA];
@@ -262,7 +328,12 @@ __global__ void __launch_bounds__(WPB_ATOM * 32) atom_kernel(const AtomArgs<T> p
       T Rv[KT], Rpv[KT];
       if (p.rad.tab) {
         // tabulated basis: re-evaluating R, R' is cheaper than staging R'
-        radial_pair<T, KT>(p.rad, u.w, Rv, Rpv);
+        if (u.w > p.rad.r_in && (p.rmask <= 0.0 || (double)u.w < p.rmask)) {
+          radial_pair<T, KT>(p.rad, u.w, Rv, Rpv);
+        } else {
+#pragma unroll
+          for (int k = 0; k < KT; ++k) { Rv[k] = T(0); Rpv[k] = T(0); }
+        }
       } else {
         const T* Rrow = sR + a * lay.SA + jj * lay.KS;
         const T* Rprow = sRp + a * lay.SA + jj * lay.KS;
@@ -338,7 +409,8 @@ __global__ void __launch_bounds__(WPB_ATOM * 32) atom_kernel(const AtomArgs<T> p
 
 // ------------------------------------------------------------------ layout
 template <typename T>
-AtomLayout make_layout(int K, int PA, bool table) {
+AtomLayout make_layout(int K, int PA, bool table, bool tangent = false) {
+  if (tangent) table = false;  // the tangent pass reads R' from shared memory
   AtomLayout L{};
   const int NA = (PA + 1) * (PA + 2) * (PA + 3) / 6;
   const int NAP = (NA + 3) / 4 * 4;
@@ -363,6 +435,8 @@ AtomLayout make_layout(int K, int PA, bool table) {
   off = al(off + sizeof(T) * 32, 32);
   L.off_cnt = off;
   off = al(off + sizeof(int) * 32, 32);
+  L.off_V = off;
+  if (tangent) off = al(off + sizeof(Q4<T>) * (size_t)L.A * L.GA, 32);
   L.warp_bytes = off;
   return L;
 }
@@ -415,9 +489,14 @@ static cudaError_t dispatch_generic(const AtomArgs<T>& p, const AtomLayout& lay,
 // (K = 3, P = 3, no 4-body; K = 6, P = 4, 4-body), generic K <= 16 otherwise.
 template <typename T>
 cudaError_t launch_atom_t(int mode, const AtomArgs<T>& p, int PA, bool has4, cudaStream_t st) {
-  const AtomLayout lay = make_layout<T>(p.K, PA, p.rad.tab != nullptr);
+  const AtomLayout lay = make_layout<T>(p.K, PA, p.rad.tab != nullptr, mode == 2);
   const bool spec6 = (p.K == 6 && PA == 4 && has4);
   const bool spec3 = (p.K == 3 && PA == 3 && !has4);
+  if (mode == 2) {
+    if (spec6) return launch_one<T, 4, true, 2, 6>(p, lay, st);
+    if (spec3) return launch_one<T, 3, false, 2, 3>(p, lay, st);
+    return dispatch_generic<T, 2>(p, lay, PA, has4, st);
+  }
   if (mode == 0) {
     if (spec6) return launch_one<T, 4, true, 0, 6>(p, lay, st);
     if (spec3) return launch_one<T, 3, false, 0, 3>(p, lay, st);

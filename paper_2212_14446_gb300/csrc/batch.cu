@@ -142,6 +142,41 @@ __global__ void segsum_kernel(const CfgBox* __restrict__ cbox, const double* __r
   if (threadIdx.x == 0) out[c] = red[0] * (per_atom ? w / (double)(a1 - a0) : w);
 }
 
+// Column sums of a row-major [rows][M] array per configuration, fixed order:
+// block b sums the rows of chunk b (<= 256 rows, never crossing a configuration)
+// with one thread per column; block c of the second kernel adds its
+// configuration's chunk partials in chunk order.
+__global__ void colsum_chunk_kernel(const int* __restrict__ chunk_rows, int M, const double* __restrict__ D,
+                                    double* __restrict__ part) {
+  const int b = blockIdx.x;
+  const int r0 = chunk_rows[2 * b], r1 = chunk_rows[2 * b + 1];
+  for (int m = threadIdx.x; m < M; m += blockDim.x) {
+    double s = 0.0;
+    for (int r = r0; r < r1; ++r) s += D[(size_t)r * M + m];
+    part[(size_t)b * M + m] = s;
+  }
+}
+
+__global__ void colsum_cfg_kernel(const int* __restrict__ cfg_chunks, int M, const double* __restrict__ part,
+                                  double* __restrict__ G) {
+  const int c = blockIdx.x;
+  const int k0 = cfg_chunks[c], k1 = cfg_chunks[c + 1];
+  for (int m = threadIdx.x; m < M; m += blockDim.x) {
+    double s = 0.0;
+    for (int k = k0; k < k1; ++k) s += part[(size_t)k * M + m];
+    G[(size_t)c * M + m] = s;
+  }
+}
+
+cudaError_t launch_colsum(int n_chunks, const int* chunk_rows, int n_cfg, const int* cfg_chunks, int M,
+                          const double* D, double* part, double* G, cudaStream_t st) {
+  colsum_chunk_kernel<<<n_chunks, 128, 0, st>>>(chunk_rows, M, D, part);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  colsum_cfg_kernel<<<n_cfg, 128, 0, st>>>(cfg_chunks, M, part, G);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_batch_wrap(int N, const double* pos, const int* cfg_of, const CfgBox* cbox, double* wpos,
                               float4* phi, float4* plo, int* status, cudaStream_t st) {
   const int tb = 256;

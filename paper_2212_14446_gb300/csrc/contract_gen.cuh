@@ -11,6 +11,11 @@ template <> struct Mono<0> {
     A[0] = T(1);
   }
   template <typename T>
+  static __device__ __forceinline__ void eval_d(T ux, T uy, T uz, T wx, T wy, T wz, T* A, T* dA) {
+    A[0] = T(1);
+    dA[0] = T(0);
+  }
+  template <typename T>
   static __device__ __forceinline__ void grad(const T* e, const T* A, T& gx, T& gy, T& gz) {
     T g0 = T(0), g1 = T(0), g2 = T(0);
     gx = g0; gy = g1; gz = g2;
@@ -18,6 +23,10 @@ template <> struct Mono<0> {
   template <typename T>
   static __device__ __forceinline__ void d3(const T* B, T* d) {
     d[0] = B[0] * B[0];
+  }
+  template <typename T>
+  static __device__ __forceinline__ void d3_tangent(const T* B, const T* Bd, T* d) {
+    d[0] = T(2) * B[0] * Bd[0];
   }
   template <typename T>
   static __device__ __forceinline__ void d3_adjoint(const T* B, const T* h, T* a) {
@@ -39,6 +48,10 @@ template <> struct Four<0> {
   template <typename T>
   static __device__ __forceinline__ void adjoint(const T* B, const T* w, T* a) {
   }
+  template <typename T>
+  static __device__ __forceinline__ void tangent(const T* B, const T* Bd, const T* d3, const T* d3d, T* Dd) {
+    Dd[0] = fma(Bd[0], d3[0], B[0] * d3d[0]);
+  }
   static constexpr int NTERMS = 0;
 };
 template <> struct Mono<1> {
@@ -49,6 +62,17 @@ template <> struct Mono<1> {
     A[1] = ux;
     A[2] = uy;
     A[3] = uz;
+  }
+  template <typename T>
+  static __device__ __forceinline__ void eval_d(T ux, T uy, T uz, T wx, T wy, T wz, T* A, T* dA) {
+    A[0] = T(1);
+    dA[0] = T(0);
+    A[1] = ux;
+    dA[1] = wx;
+    A[2] = uy;
+    dA[2] = wy;
+    A[3] = uz;
+    dA[3] = wz;
   }
   template <typename T>
   static __device__ __forceinline__ void grad(const T* e, const T* A, T& gx, T& gy, T& gz) {
@@ -62,6 +86,11 @@ template <> struct Mono<1> {
   static __device__ __forceinline__ void d3(const T* B, T* d) {
     d[0] = B[0] * B[0];
     d[1] = B[1] * B[1] + B[2] * B[2] + B[3] * B[3];
+  }
+  template <typename T>
+  static __device__ __forceinline__ void d3_tangent(const T* B, const T* Bd, T* d) {
+    d[0] = T(2) * B[0] * Bd[0];
+    d[1] = T(2) * B[1] * Bd[1] + T(2) * B[2] * Bd[2] + T(2) * B[3] * Bd[3];
   }
   template <typename T>
   static __device__ __forceinline__ void d3_adjoint(const T* B, const T* h, T* a) {
@@ -88,6 +117,11 @@ template <> struct Four<1> {
   template <typename T>
   static __device__ __forceinline__ void adjoint(const T* B, const T* w, T* a) {
   }
+  template <typename T>
+  static __device__ __forceinline__ void tangent(const T* B, const T* Bd, const T* d3, const T* d3d, T* Dd) {
+    Dd[0] = fma(Bd[0], d3[0], B[0] * d3d[0]);
+    Dd[1] = fma(Bd[0], d3[1], B[0] * d3d[1]);
+  }
   static constexpr int NTERMS = 0;
 };
 template <> struct Mono<2> {
@@ -104,6 +138,29 @@ template <> struct Mono<2> {
     A[7] = A[2] * ux;
     A[8] = A[3] * ux;
     A[9] = A[3] * uy;
+  }
+  template <typename T>
+  static __device__ __forceinline__ void eval_d(T ux, T uy, T uz, T wx, T wy, T wz, T* A, T* dA) {
+    A[0] = T(1);
+    dA[0] = T(0);
+    A[1] = ux;
+    dA[1] = wx;
+    A[2] = uy;
+    dA[2] = wy;
+    A[3] = uz;
+    dA[3] = wz;
+    A[4] = A[1] * ux;
+    dA[4] = fma(dA[1], ux, A[1] * wx);
+    A[5] = A[2] * uy;
+    dA[5] = fma(dA[2], uy, A[2] * wy);
+    A[6] = A[3] * uz;
+    dA[6] = fma(dA[3], uz, A[3] * wz);
+    A[7] = A[2] * ux;
+    dA[7] = fma(dA[2], ux, A[2] * wx);
+    A[8] = A[3] * ux;
+    dA[8] = fma(dA[3], ux, A[3] * wx);
+    A[9] = A[3] * uy;
+    dA[9] = fma(dA[3], uy, A[3] * wy);
   }
   template <typename T>
   static __device__ __forceinline__ void grad(const T* e, const T* A, T& gx, T& gy, T& gz) {
@@ -127,6 +184,12 @@ template <> struct Mono<2> {
     d[0] = B[0] * B[0];
     d[1] = B[1] * B[1] + B[2] * B[2] + B[3] * B[3];
     d[2] = B[4] * B[4] + B[5] * B[5] + B[6] * B[6] + T(2) * B[7] * B[7] + T(2) * B[8] * B[8] + T(2) * B[9] * B[9];
+  }
+  template <typename T>
+  static __device__ __forceinline__ void d3_tangent(const T* B, const T* Bd, T* d) {
+    d[0] = T(2) * B[0] * Bd[0];
+    d[1] = T(2) * B[1] * Bd[1] + T(2) * B[2] * Bd[2] + T(2) * B[3] * Bd[3];
+    d[2] = T(2) * B[4] * Bd[4] + T(2) * B[5] * Bd[5] + T(2) * B[6] * Bd[6] + T(4) * B[7] * Bd[7] + T(4) * B[8] * Bd[8] + T(4) * B[9] * Bd[9];
   }
   template <typename T>
   static __device__ __forceinline__ void d3_adjoint(const T* B, const T* h, T* a) {
@@ -186,6 +249,13 @@ template <> struct Four<2> {
       a[6] = fma(wp, B[3] * B[3], a[6]);
     }
   }
+  template <typename T>
+  static __device__ __forceinline__ void tangent(const T* B, const T* Bd, const T* d3, const T* d3d, T* Dd) {
+    Dd[0] = fma(Bd[0], d3[0], B[0] * d3d[0]);
+    Dd[1] = fma(Bd[0], d3[1], B[0] * d3d[1]);
+    Dd[2] = fma(Bd[0], d3[2], B[0] * d3d[2]);
+    Dd[3] = (Bd[1] * B[1] * B[4] + B[1] * Bd[1] * B[4] + B[1] * B[1] * Bd[4]) + T(2) * (Bd[1] * B[2] * B[7] + B[1] * Bd[2] * B[7] + B[1] * B[2] * Bd[7]) + T(2) * (Bd[1] * B[3] * B[8] + B[1] * Bd[3] * B[8] + B[1] * B[3] * Bd[8]) + (Bd[2] * B[2] * B[5] + B[2] * Bd[2] * B[5] + B[2] * B[2] * Bd[5]) + T(2) * (Bd[2] * B[3] * B[9] + B[2] * Bd[3] * B[9] + B[2] * B[3] * Bd[9]) + (Bd[3] * B[3] * B[6] + B[3] * Bd[3] * B[6] + B[3] * B[3] * Bd[6]);
+  }
   static constexpr int NTERMS = 6;
 };
 template <> struct Mono<3> {
@@ -212,6 +282,49 @@ template <> struct Mono<3> {
     A[17] = A[6] * ux;
     A[18] = A[6] * uy;
     A[19] = A[9] * ux;
+  }
+  template <typename T>
+  static __device__ __forceinline__ void eval_d(T ux, T uy, T uz, T wx, T wy, T wz, T* A, T* dA) {
+    A[0] = T(1);
+    dA[0] = T(0);
+    A[1] = ux;
+    dA[1] = wx;
+    A[2] = uy;
+    dA[2] = wy;
+    A[3] = uz;
+    dA[3] = wz;
+    A[4] = A[1] * ux;
+    dA[4] = fma(dA[1], ux, A[1] * wx);
+    A[5] = A[2] * uy;
+    dA[5] = fma(dA[2], uy, A[2] * wy);
+    A[6] = A[3] * uz;
+    dA[6] = fma(dA[3], uz, A[3] * wz);
+    A[7] = A[2] * ux;
+    dA[7] = fma(dA[2], ux, A[2] * wx);
+    A[8] = A[3] * ux;
+    dA[8] = fma(dA[3], ux, A[3] * wx);
+    A[9] = A[3] * uy;
+    dA[9] = fma(dA[3], uy, A[3] * wy);
+    A[10] = A[4] * ux;
+    dA[10] = fma(dA[4], ux, A[4] * wx);
+    A[11] = A[5] * uy;
+    dA[11] = fma(dA[5], uy, A[5] * wy);
+    A[12] = A[6] * uz;
+    dA[12] = fma(dA[6], uz, A[6] * wz);
+    A[13] = A[7] * ux;
+    dA[13] = fma(dA[7], ux, A[7] * wx);
+    A[14] = A[8] * ux;
+    dA[14] = fma(dA[8], ux, A[8] * wx);
+    A[15] = A[5] * ux;
+    dA[15] = fma(dA[5], ux, A[5] * wx);
+    A[16] = A[9] * uy;
+    dA[16] = fma(dA[9], uy, A[9] * wy);
+    A[17] = A[6] * ux;
+    dA[17] = fma(dA[6], ux, A[6] * wx);
+    A[18] = A[6] * uy;
+    dA[18] = fma(dA[6], uy, A[6] * wy);
+    A[19] = A[9] * ux;
+    dA[19] = fma(dA[9], ux, A[9] * wx);
   }
   template <typename T>
   static __device__ __forceinline__ void grad(const T* e, const T* A, T& gx, T& gy, T& gz) {
@@ -254,6 +367,13 @@ template <> struct Mono<3> {
     d[1] = B[1] * B[1] + B[2] * B[2] + B[3] * B[3];
     d[2] = B[4] * B[4] + B[5] * B[5] + B[6] * B[6] + T(2) * B[7] * B[7] + T(2) * B[8] * B[8] + T(2) * B[9] * B[9];
     d[3] = B[10] * B[10] + B[11] * B[11] + B[12] * B[12] + T(3) * B[13] * B[13] + T(3) * B[14] * B[14] + T(3) * B[15] * B[15] + T(3) * B[16] * B[16] + T(3) * B[17] * B[17] + T(3) * B[18] * B[18] + T(6) * B[19] * B[19];
+  }
+  template <typename T>
+  static __device__ __forceinline__ void d3_tangent(const T* B, const T* Bd, T* d) {
+    d[0] = T(2) * B[0] * Bd[0];
+    d[1] = T(2) * B[1] * Bd[1] + T(2) * B[2] * Bd[2] + T(2) * B[3] * Bd[3];
+    d[2] = T(2) * B[4] * Bd[4] + T(2) * B[5] * Bd[5] + T(2) * B[6] * Bd[6] + T(4) * B[7] * Bd[7] + T(4) * B[8] * Bd[8] + T(4) * B[9] * Bd[9];
+    d[3] = T(2) * B[10] * Bd[10] + T(2) * B[11] * Bd[11] + T(2) * B[12] * Bd[12] + T(6) * B[13] * Bd[13] + T(6) * B[14] * Bd[14] + T(6) * B[15] * Bd[15] + T(6) * B[16] * Bd[16] + T(6) * B[17] * Bd[17] + T(6) * B[18] * Bd[18] + T(12) * B[19] * Bd[19];
   }
   template <typename T>
   static __device__ __forceinline__ void d3_adjoint(const T* B, const T* h, T* a) {
@@ -433,6 +553,16 @@ template <> struct Four<3> {
       a[6] = fma(wp, B[6] * B[6], a[6]);
     }
   }
+  template <typename T>
+  static __device__ __forceinline__ void tangent(const T* B, const T* Bd, const T* d3, const T* d3d, T* Dd) {
+    Dd[0] = fma(Bd[0], d3[0], B[0] * d3d[0]);
+    Dd[1] = fma(Bd[0], d3[1], B[0] * d3d[1]);
+    Dd[2] = fma(Bd[0], d3[2], B[0] * d3d[2]);
+    Dd[3] = (Bd[1] * B[1] * B[4] + B[1] * Bd[1] * B[4] + B[1] * B[1] * Bd[4]) + T(2) * (Bd[1] * B[2] * B[7] + B[1] * Bd[2] * B[7] + B[1] * B[2] * Bd[7]) + T(2) * (Bd[1] * B[3] * B[8] + B[1] * Bd[3] * B[8] + B[1] * B[3] * Bd[8]) + (Bd[2] * B[2] * B[5] + B[2] * Bd[2] * B[5] + B[2] * B[2] * Bd[5]) + T(2) * (Bd[2] * B[3] * B[9] + B[2] * Bd[3] * B[9] + B[2] * B[3] * Bd[9]) + (Bd[3] * B[3] * B[6] + B[3] * Bd[3] * B[6] + B[3] * B[3] * Bd[6]);
+    Dd[4] = fma(Bd[0], d3[3], B[0] * d3d[3]);
+    Dd[5] = (Bd[1] * B[4] * B[10] + B[1] * Bd[4] * B[10] + B[1] * B[4] * Bd[10]) + (Bd[2] * B[4] * B[13] + B[2] * Bd[4] * B[13] + B[2] * B[4] * Bd[13]) + (Bd[3] * B[4] * B[14] + B[3] * Bd[4] * B[14] + B[3] * B[4] * Bd[14]) + (Bd[1] * B[5] * B[15] + B[1] * Bd[5] * B[15] + B[1] * B[5] * Bd[15]) + (Bd[2] * B[5] * B[11] + B[2] * Bd[5] * B[11] + B[2] * B[5] * Bd[11]) + (Bd[3] * B[5] * B[16] + B[3] * Bd[5] * B[16] + B[3] * B[5] * Bd[16]) + (Bd[1] * B[6] * B[17] + B[1] * Bd[6] * B[17] + B[1] * B[6] * Bd[17]) + (Bd[2] * B[6] * B[18] + B[2] * Bd[6] * B[18] + B[2] * B[6] * Bd[18]) + (Bd[3] * B[6] * B[12] + B[3] * Bd[6] * B[12] + B[3] * B[6] * Bd[12]) + T(2) * (Bd[1] * B[7] * B[13] + B[1] * Bd[7] * B[13] + B[1] * B[7] * Bd[13]) + T(2) * (Bd[2] * B[7] * B[15] + B[2] * Bd[7] * B[15] + B[2] * B[7] * Bd[15]) + T(2) * (Bd[3] * B[7] * B[19] + B[3] * Bd[7] * B[19] + B[3] * B[7] * Bd[19]) + T(2) * (Bd[1] * B[8] * B[14] + B[1] * Bd[8] * B[14] + B[1] * B[8] * Bd[14]) + T(2) * (Bd[2] * B[8] * B[19] + B[2] * Bd[8] * B[19] + B[2] * B[8] * Bd[19]) + T(2) * (Bd[3] * B[8] * B[17] + B[3] * Bd[8] * B[17] + B[3] * B[8] * Bd[17]) + T(2) * (Bd[1] * B[9] * B[19] + B[1] * Bd[9] * B[19] + B[1] * B[9] * Bd[19]) + T(2) * (Bd[2] * B[9] * B[16] + B[2] * Bd[9] * B[16] + B[2] * B[9] * Bd[16]) + T(2) * (Bd[3] * B[9] * B[18] + B[3] * Bd[9] * B[18] + B[3] * B[9] * Bd[18]);
+    Dd[6] = (Bd[4] * B[4] * B[4] + B[4] * Bd[4] * B[4] + B[4] * B[4] * Bd[4]) + T(3) * (Bd[4] * B[7] * B[7] + B[4] * Bd[7] * B[7] + B[4] * B[7] * Bd[7]) + T(3) * (Bd[4] * B[8] * B[8] + B[4] * Bd[8] * B[8] + B[4] * B[8] * Bd[8]) + T(3) * (Bd[5] * B[7] * B[7] + B[5] * Bd[7] * B[7] + B[5] * B[7] * Bd[7]) + T(6) * (Bd[7] * B[8] * B[9] + B[7] * Bd[8] * B[9] + B[7] * B[8] * Bd[9]) + T(3) * (Bd[6] * B[8] * B[8] + B[6] * Bd[8] * B[8] + B[6] * B[8] * Bd[8]) + (Bd[5] * B[5] * B[5] + B[5] * Bd[5] * B[5] + B[5] * B[5] * Bd[5]) + T(3) * (Bd[5] * B[9] * B[9] + B[5] * Bd[9] * B[9] + B[5] * B[9] * Bd[9]) + T(3) * (Bd[6] * B[9] * B[9] + B[6] * Bd[9] * B[9] + B[6] * B[9] * Bd[9]) + (Bd[6] * B[6] * B[6] + B[6] * Bd[6] * B[6] + B[6] * B[6] * Bd[6]);
+  }
   static constexpr int NTERMS = 34;
 };
 template <> struct Mono<4> {
@@ -474,6 +604,79 @@ template <> struct Mono<4> {
     A[32] = A[19] * ux;
     A[33] = A[16] * ux;
     A[34] = A[18] * ux;
+  }
+  template <typename T>
+  static __device__ __forceinline__ void eval_d(T ux, T uy, T uz, T wx, T wy, T wz, T* A, T* dA) {
+    A[0] = T(1);
+    dA[0] = T(0);
+    A[1] = ux;
+    dA[1] = wx;
+    A[2] = uy;
+    dA[2] = wy;
+    A[3] = uz;
+    dA[3] = wz;
+    A[4] = A[1] * ux;
+    dA[4] = fma(dA[1], ux, A[1] * wx);
+    A[5] = A[2] * uy;
+    dA[5] = fma(dA[2], uy, A[2] * wy);
+    A[6] = A[3] * uz;
+    dA[6] = fma(dA[3], uz, A[3] * wz);
+    A[7] = A[2] * ux;
+    dA[7] = fma(dA[2], ux, A[2] * wx);
+    A[8] = A[3] * ux;
+    dA[8] = fma(dA[3], ux, A[3] * wx);
+    A[9] = A[3] * uy;
+    dA[9] = fma(dA[3], uy, A[3] * wy);
+    A[10] = A[4] * ux;
+    dA[10] = fma(dA[4], ux, A[4] * wx);
+    A[11] = A[5] * uy;
+    dA[11] = fma(dA[5], uy, A[5] * wy);
+    A[12] = A[6] * uz;
+    dA[12] = fma(dA[6], uz, A[6] * wz);
+    A[13] = A[7] * ux;
+    dA[13] = fma(dA[7], ux, A[7] * wx);
+    A[14] = A[8] * ux;
+    dA[14] = fma(dA[8], ux, A[8] * wx);
+    A[15] = A[5] * ux;
+    dA[15] = fma(dA[5], ux, A[5] * wx);
+    A[16] = A[9] * uy;
+    dA[16] = fma(dA[9], uy, A[9] * wy);
+    A[17] = A[6] * ux;
+    dA[17] = fma(dA[6], ux, A[6] * wx);
+    A[18] = A[6] * uy;
+    dA[18] = fma(dA[6], uy, A[6] * wy);
+    A[19] = A[9] * ux;
+    dA[19] = fma(dA[9], ux, A[9] * wx);
+    A[20] = A[10] * ux;
+    dA[20] = fma(dA[10], ux, A[10] * wx);
+    A[21] = A[11] * uy;
+    dA[21] = fma(dA[11], uy, A[11] * wy);
+    A[22] = A[12] * uz;
+    dA[22] = fma(dA[12], uz, A[12] * wz);
+    A[23] = A[13] * ux;
+    dA[23] = fma(dA[13], ux, A[13] * wx);
+    A[24] = A[14] * ux;
+    dA[24] = fma(dA[14], ux, A[14] * wx);
+    A[25] = A[11] * ux;
+    dA[25] = fma(dA[11], ux, A[11] * wx);
+    A[26] = A[16] * uy;
+    dA[26] = fma(dA[16], uy, A[16] * wy);
+    A[27] = A[12] * ux;
+    dA[27] = fma(dA[12], ux, A[12] * wx);
+    A[28] = A[12] * uy;
+    dA[28] = fma(dA[12], uy, A[12] * wy);
+    A[29] = A[15] * ux;
+    dA[29] = fma(dA[15], ux, A[15] * wx);
+    A[30] = A[17] * ux;
+    dA[30] = fma(dA[17], ux, A[17] * wx);
+    A[31] = A[18] * uy;
+    dA[31] = fma(dA[18], uy, A[18] * wy);
+    A[32] = A[19] * ux;
+    dA[32] = fma(dA[19], ux, A[19] * wx);
+    A[33] = A[16] * ux;
+    dA[33] = fma(dA[16], ux, A[16] * wx);
+    A[34] = A[18] * ux;
+    dA[34] = fma(dA[18], ux, A[18] * wx);
   }
   template <typename T>
   static __device__ __forceinline__ void grad(const T* e, const T* A, T& gx, T& gy, T& gz) {
@@ -547,6 +750,14 @@ template <> struct Mono<4> {
     d[2] = B[4] * B[4] + B[5] * B[5] + B[6] * B[6] + T(2) * B[7] * B[7] + T(2) * B[8] * B[8] + T(2) * B[9] * B[9];
     d[3] = B[10] * B[10] + B[11] * B[11] + B[12] * B[12] + T(3) * B[13] * B[13] + T(3) * B[14] * B[14] + T(3) * B[15] * B[15] + T(3) * B[16] * B[16] + T(3) * B[17] * B[17] + T(3) * B[18] * B[18] + T(6) * B[19] * B[19];
     d[4] = B[20] * B[20] + B[21] * B[21] + B[22] * B[22] + T(4) * B[23] * B[23] + T(4) * B[24] * B[24] + T(4) * B[25] * B[25] + T(4) * B[26] * B[26] + T(4) * B[27] * B[27] + T(4) * B[28] * B[28] + T(6) * B[29] * B[29] + T(6) * B[30] * B[30] + T(6) * B[31] * B[31] + T(12) * B[32] * B[32] + T(12) * B[33] * B[33] + T(12) * B[34] * B[34];
+  }
+  template <typename T>
+  static __device__ __forceinline__ void d3_tangent(const T* B, const T* Bd, T* d) {
+    d[0] = T(2) * B[0] * Bd[0];
+    d[1] = T(2) * B[1] * Bd[1] + T(2) * B[2] * Bd[2] + T(2) * B[3] * Bd[3];
+    d[2] = T(2) * B[4] * Bd[4] + T(2) * B[5] * Bd[5] + T(2) * B[6] * Bd[6] + T(4) * B[7] * Bd[7] + T(4) * B[8] * Bd[8] + T(4) * B[9] * Bd[9];
+    d[3] = T(2) * B[10] * Bd[10] + T(2) * B[11] * Bd[11] + T(2) * B[12] * Bd[12] + T(6) * B[13] * Bd[13] + T(6) * B[14] * Bd[14] + T(6) * B[15] * Bd[15] + T(6) * B[16] * Bd[16] + T(6) * B[17] * Bd[17] + T(6) * B[18] * Bd[18] + T(12) * B[19] * Bd[19];
+    d[4] = T(2) * B[20] * Bd[20] + T(2) * B[21] * Bd[21] + T(2) * B[22] * Bd[22] + T(8) * B[23] * Bd[23] + T(8) * B[24] * Bd[24] + T(8) * B[25] * Bd[25] + T(8) * B[26] * Bd[26] + T(8) * B[27] * Bd[27] + T(8) * B[28] * Bd[28] + T(12) * B[29] * Bd[29] + T(12) * B[30] * Bd[30] + T(12) * B[31] * Bd[31] + T(24) * B[32] * Bd[32] + T(24) * B[33] * Bd[33] + T(24) * B[34] * Bd[34];
   }
   template <typename T>
   static __device__ __forceinline__ void d3_adjoint(const T* B, const T* h, T* a) {
@@ -1081,6 +1292,20 @@ template <> struct Four<4> {
       a[18] = fma(wk6_18_18, B[6] * B[18], a[18]);
       a[18] = fma(wk6_18_18, B[6] * B[18], a[18]);
     }
+  }
+  template <typename T>
+  static __device__ __forceinline__ void tangent(const T* B, const T* Bd, const T* d3, const T* d3d, T* Dd) {
+    Dd[0] = fma(Bd[0], d3[0], B[0] * d3d[0]);
+    Dd[1] = fma(Bd[0], d3[1], B[0] * d3d[1]);
+    Dd[2] = fma(Bd[0], d3[2], B[0] * d3d[2]);
+    Dd[3] = (Bd[1] * B[1] * B[4] + B[1] * Bd[1] * B[4] + B[1] * B[1] * Bd[4]) + T(2) * (Bd[1] * B[2] * B[7] + B[1] * Bd[2] * B[7] + B[1] * B[2] * Bd[7]) + T(2) * (Bd[1] * B[3] * B[8] + B[1] * Bd[3] * B[8] + B[1] * B[3] * Bd[8]) + (Bd[2] * B[2] * B[5] + B[2] * Bd[2] * B[5] + B[2] * B[2] * Bd[5]) + T(2) * (Bd[2] * B[3] * B[9] + B[2] * Bd[3] * B[9] + B[2] * B[3] * Bd[9]) + (Bd[3] * B[3] * B[6] + B[3] * Bd[3] * B[6] + B[3] * B[3] * Bd[6]);
+    Dd[4] = fma(Bd[0], d3[3], B[0] * d3d[3]);
+    Dd[5] = (Bd[1] * B[4] * B[10] + B[1] * Bd[4] * B[10] + B[1] * B[4] * Bd[10]) + (Bd[2] * B[4] * B[13] + B[2] * Bd[4] * B[13] + B[2] * B[4] * Bd[13]) + (Bd[3] * B[4] * B[14] + B[3] * Bd[4] * B[14] + B[3] * B[4] * Bd[14]) + (Bd[1] * B[5] * B[15] + B[1] * Bd[5] * B[15] + B[1] * B[5] * Bd[15]) + (Bd[2] * B[5] * B[11] + B[2] * Bd[5] * B[11] + B[2] * B[5] * Bd[11]) + (Bd[3] * B[5] * B[16] + B[3] * Bd[5] * B[16] + B[3] * B[5] * Bd[16]) + (Bd[1] * B[6] * B[17] + B[1] * Bd[6] * B[17] + B[1] * B[6] * Bd[17]) + (Bd[2] * B[6] * B[18] + B[2] * Bd[6] * B[18] + B[2] * B[6] * Bd[18]) + (Bd[3] * B[6] * B[12] + B[3] * Bd[6] * B[12] + B[3] * B[6] * Bd[12]) + T(2) * (Bd[1] * B[7] * B[13] + B[1] * Bd[7] * B[13] + B[1] * B[7] * Bd[13]) + T(2) * (Bd[2] * B[7] * B[15] + B[2] * Bd[7] * B[15] + B[2] * B[7] * Bd[15]) + T(2) * (Bd[3] * B[7] * B[19] + B[3] * Bd[7] * B[19] + B[3] * B[7] * Bd[19]) + T(2) * (Bd[1] * B[8] * B[14] + B[1] * Bd[8] * B[14] + B[1] * B[8] * Bd[14]) + T(2) * (Bd[2] * B[8] * B[19] + B[2] * Bd[8] * B[19] + B[2] * B[8] * Bd[19]) + T(2) * (Bd[3] * B[8] * B[17] + B[3] * Bd[8] * B[17] + B[3] * B[8] * Bd[17]) + T(2) * (Bd[1] * B[9] * B[19] + B[1] * Bd[9] * B[19] + B[1] * B[9] * Bd[19]) + T(2) * (Bd[2] * B[9] * B[16] + B[2] * Bd[9] * B[16] + B[2] * B[9] * Bd[16]) + T(2) * (Bd[3] * B[9] * B[18] + B[3] * Bd[9] * B[18] + B[3] * B[9] * Bd[18]);
+    Dd[6] = (Bd[4] * B[4] * B[4] + B[4] * Bd[4] * B[4] + B[4] * B[4] * Bd[4]) + T(3) * (Bd[4] * B[7] * B[7] + B[4] * Bd[7] * B[7] + B[4] * B[7] * Bd[7]) + T(3) * (Bd[4] * B[8] * B[8] + B[4] * Bd[8] * B[8] + B[4] * B[8] * Bd[8]) + T(3) * (Bd[5] * B[7] * B[7] + B[5] * Bd[7] * B[7] + B[5] * B[7] * Bd[7]) + T(6) * (Bd[7] * B[8] * B[9] + B[7] * Bd[8] * B[9] + B[7] * B[8] * Bd[9]) + T(3) * (Bd[6] * B[8] * B[8] + B[6] * Bd[8] * B[8] + B[6] * B[8] * Bd[8]) + (Bd[5] * B[5] * B[5] + B[5] * Bd[5] * B[5] + B[5] * B[5] * Bd[5]) + T(3) * (Bd[5] * B[9] * B[9] + B[5] * Bd[9] * B[9] + B[5] * B[9] * Bd[9]) + T(3) * (Bd[6] * B[9] * B[9] + B[6] * Bd[9] * B[9] + B[6] * B[9] * Bd[9]) + (Bd[6] * B[6] * B[6] + B[6] * Bd[6] * B[6] + B[6] * B[6] * Bd[6]);
+    Dd[7] = fma(Bd[0], d3[4], B[0] * d3d[4]);
+    Dd[8] = (Bd[1] * B[10] * B[20] + B[1] * Bd[10] * B[20] + B[1] * B[10] * Bd[20]) + (Bd[2] * B[10] * B[23] + B[2] * Bd[10] * B[23] + B[2] * B[10] * Bd[23]) + (Bd[3] * B[10] * B[24] + B[3] * Bd[10] * B[24] + B[3] * B[10] * Bd[24]) + (Bd[1] * B[11] * B[25] + B[1] * Bd[11] * B[25] + B[1] * B[11] * Bd[25]) + (Bd[2] * B[11] * B[21] + B[2] * Bd[11] * B[21] + B[2] * B[11] * Bd[21]) + (Bd[3] * B[11] * B[26] + B[3] * Bd[11] * B[26] + B[3] * B[11] * Bd[26]) + (Bd[1] * B[12] * B[27] + B[1] * Bd[12] * B[27] + B[1] * B[12] * Bd[27]) + (Bd[2] * B[12] * B[28] + B[2] * Bd[12] * B[28] + B[2] * B[12] * Bd[28]) + (Bd[3] * B[12] * B[22] + B[3] * Bd[12] * B[22] + B[3] * B[12] * Bd[22]) + T(3) * (Bd[1] * B[13] * B[23] + B[1] * Bd[13] * B[23] + B[1] * B[13] * Bd[23]) + T(3) * (Bd[2] * B[13] * B[29] + B[2] * Bd[13] * B[29] + B[2] * B[13] * Bd[29]) + T(3) * (Bd[3] * B[13] * B[32] + B[3] * Bd[13] * B[32] + B[3] * B[13] * Bd[32]) + T(3) * (Bd[1] * B[14] * B[24] + B[1] * Bd[14] * B[24] + B[1] * B[14] * Bd[24]) + T(3) * (Bd[2] * B[14] * B[32] + B[2] * Bd[14] * B[32] + B[2] * B[14] * Bd[32]) + T(3) * (Bd[3] * B[14] * B[30] + B[3] * Bd[14] * B[30] + B[3] * B[14] * Bd[30]) + T(3) * (Bd[1] * B[15] * B[29] + B[1] * Bd[15] * B[29] + B[1] * B[15] * Bd[29]) + T(3) * (Bd[2] * B[15] * B[25] + B[2] * Bd[15] * B[25] + B[2] * B[15] * Bd[25]) + T(3) * (Bd[3] * B[15] * B[33] + B[3] * Bd[15] * B[33] + B[3] * B[15] * Bd[33]) + T(3) * (Bd[1] * B[16] * B[33] + B[1] * Bd[16] * B[33] + B[1] * B[16] * Bd[33]) + T(3) * (Bd[2] * B[16] * B[26] + B[2] * Bd[16] * B[26] + B[2] * B[16] * Bd[26]) + T(3) * (Bd[3] * B[16] * B[31] + B[3] * Bd[16] * B[31] + B[3] * B[16] * Bd[31]) + T(3) * (Bd[1] * B[17] * B[30] + B[1] * Bd[17] * B[30] + B[1] * B[17] * Bd[30]) + T(3) * (Bd[2] * B[17] * B[34] + B[2] * Bd[17] * B[34] + B[2] * B[17] * Bd[34]) + T(3) * (Bd[3] * B[17] * B[27] + B[3] * Bd[17] * B[27] + B[3] * B[17] * Bd[27]) + T(3) * (Bd[1] * B[18] * B[34] + B[1] * Bd[18] * B[34] + B[1] * B[18] * Bd[34]) + T(3) * (Bd[2] * B[18] * B[31] + B[2] * Bd[18] * B[31] + B[2] * B[18] * Bd[31]) + T(3) * (Bd[3] * B[18] * B[28] + B[3] * Bd[18] * B[28] + B[3] * B[18] * Bd[28]) + T(6) * (Bd[1] * B[19] * B[32] + B[1] * Bd[19] * B[32] + B[1] * B[19] * Bd[32]) + T(6) * (Bd[2] * B[19] * B[33] + B[2] * Bd[19] * B[33] + B[2] * B[19] * Bd[33]) + T(6) * (Bd[3] * B[19] * B[34] + B[3] * Bd[19] * B[34] + B[3] * B[19] * Bd[34]);
+    Dd[9] = (Bd[4] * B[4] * B[20] + B[4] * Bd[4] * B[20] + B[4] * B[4] * Bd[20]) + T(2) * (Bd[4] * B[5] * B[29] + B[4] * Bd[5] * B[29] + B[4] * B[5] * Bd[29]) + T(2) * (Bd[4] * B[6] * B[30] + B[4] * Bd[6] * B[30] + B[4] * B[6] * Bd[30]) + T(4) * (Bd[4] * B[7] * B[23] + B[4] * Bd[7] * B[23] + B[4] * B[7] * Bd[23]) + T(4) * (Bd[4] * B[8] * B[24] + B[4] * Bd[8] * B[24] + B[4] * B[8] * Bd[24]) + T(4) * (Bd[4] * B[9] * B[32] + B[4] * Bd[9] * B[32] + B[4] * B[9] * Bd[32]) + (Bd[5] * B[5] * B[21] + B[5] * Bd[5] * B[21] + B[5] * B[5] * Bd[21]) + T(2) * (Bd[5] * B[6] * B[31] + B[5] * Bd[6] * B[31] + B[5] * B[6] * Bd[31]) + T(4) * (Bd[5] * B[7] * B[25] + B[5] * Bd[7] * B[25] + B[5] * B[7] * Bd[25]) + T(4) * (Bd[5] * B[8] * B[33] + B[5] * Bd[8] * B[33] + B[5] * B[8] * Bd[33]) + T(4) * (Bd[5] * B[9] * B[26] + B[5] * Bd[9] * B[26] + B[5] * B[9] * Bd[26]) + (Bd[6] * B[6] * B[22] + B[6] * Bd[6] * B[22] + B[6] * B[6] * Bd[22]) + T(4) * (Bd[6] * B[7] * B[34] + B[6] * Bd[7] * B[34] + B[6] * B[7] * Bd[34]) + T(4) * (Bd[6] * B[8] * B[27] + B[6] * Bd[8] * B[27] + B[6] * B[8] * Bd[27]) + T(4) * (Bd[6] * B[9] * B[28] + B[6] * Bd[9] * B[28] + B[6] * B[9] * Bd[28]) + T(4) * (Bd[7] * B[7] * B[29] + B[7] * Bd[7] * B[29] + B[7] * B[7] * Bd[29]) + T(8) * (Bd[7] * B[8] * B[32] + B[7] * Bd[8] * B[32] + B[7] * B[8] * Bd[32]) + T(8) * (Bd[7] * B[9] * B[33] + B[7] * Bd[9] * B[33] + B[7] * B[9] * Bd[33]) + T(4) * (Bd[8] * B[8] * B[30] + B[8] * Bd[8] * B[30] + B[8] * B[8] * Bd[30]) + T(8) * (Bd[8] * B[9] * B[34] + B[8] * Bd[9] * B[34] + B[8] * B[9] * Bd[34]) + T(4) * (Bd[9] * B[9] * B[31] + B[9] * Bd[9] * B[31] + B[9] * B[9] * Bd[31]);
+    Dd[10] = (Bd[4] * B[10] * B[10] + B[4] * Bd[10] * B[10] + B[4] * B[10] * Bd[10]) + T(2) * (Bd[7] * B[10] * B[13] + B[7] * Bd[10] * B[13] + B[7] * B[10] * Bd[13]) + T(2) * (Bd[8] * B[10] * B[14] + B[8] * Bd[10] * B[14] + B[8] * B[10] * Bd[14]) + (Bd[5] * B[13] * B[13] + B[5] * Bd[13] * B[13] + B[5] * B[13] * Bd[13]) + T(2) * (Bd[9] * B[13] * B[14] + B[9] * Bd[13] * B[14] + B[9] * B[13] * Bd[14]) + (Bd[6] * B[14] * B[14] + B[6] * Bd[14] * B[14] + B[6] * B[14] * Bd[14]) + (Bd[4] * B[15] * B[15] + B[4] * Bd[15] * B[15] + B[4] * B[15] * Bd[15]) + T(2) * (Bd[7] * B[11] * B[15] + B[7] * Bd[11] * B[15] + B[7] * B[11] * Bd[15]) + T(2) * (Bd[8] * B[15] * B[16] + B[8] * Bd[15] * B[16] + B[8] * B[15] * Bd[16]) + (Bd[5] * B[11] * B[11] + B[5] * Bd[11] * B[11] + B[5] * B[11] * Bd[11]) + T(2) * (Bd[9] * B[11] * B[16] + B[9] * Bd[11] * B[16] + B[9] * B[11] * Bd[16]) + (Bd[6] * B[16] * B[16] + B[6] * Bd[16] * B[16] + B[6] * B[16] * Bd[16]) + (Bd[4] * B[17] * B[17] + B[4] * Bd[17] * B[17] + B[4] * B[17] * Bd[17]) + T(2) * (Bd[7] * B[17] * B[18] + B[7] * Bd[17] * B[18] + B[7] * B[17] * Bd[18]) + T(2) * (Bd[8] * B[12] * B[17] + B[8] * Bd[12] * B[17] + B[8] * B[12] * Bd[17]) + (Bd[5] * B[18] * B[18] + B[5] * Bd[18] * B[18] + B[5] * B[18] * Bd[18]) + T(2) * (Bd[9] * B[12] * B[18] + B[9] * Bd[12] * B[18] + B[9] * B[12] * Bd[18]) + (Bd[6] * B[12] * B[12] + B[6] * Bd[12] * B[12] + B[6] * B[12] * Bd[12]) + T(2) * (Bd[4] * B[13] * B[13] + B[4] * Bd[13] * B[13] + B[4] * B[13] * Bd[13]) + T(4) * (Bd[7] * B[13] * B[15] + B[7] * Bd[13] * B[15] + B[7] * B[13] * Bd[15]) + T(4) * (Bd[8] * B[13] * B[19] + B[8] * Bd[13] * B[19] + B[8] * B[13] * Bd[19]) + T(2) * (Bd[5] * B[15] * B[15] + B[5] * Bd[15] * B[15] + B[5] * B[15] * Bd[15]) + T(4) * (Bd[9] * B[15] * B[19] + B[9] * Bd[15] * B[19] + B[9] * B[15] * Bd[19]) + T(2) * (Bd[6] * B[19] * B[19] + B[6] * Bd[19] * B[19] + B[6] * B[19] * Bd[19]) + T(2) * (Bd[4] * B[14] * B[14] + B[4] * Bd[14] * B[14] + B[4] * B[14] * Bd[14]) + T(4) * (Bd[7] * B[14] * B[19] + B[7] * Bd[14] * B[19] + B[7] * B[14] * Bd[19]) + T(4) * (Bd[8] * B[14] * B[17] + B[8] * Bd[14] * B[17] + B[8] * B[14] * Bd[17]) + T(2) * (Bd[5] * B[19] * B[19] + B[5] * Bd[19] * B[19] + B[5] * B[19] * Bd[19]) + T(4) * (Bd[9] * B[17] * B[19] + B[9] * Bd[17] * B[19] + B[9] * B[17] * Bd[19]) + T(2) * (Bd[6] * B[17] * B[17] + B[6] * Bd[17] * B[17] + B[6] * B[17] * Bd[17]) + T(2) * (Bd[4] * B[19] * B[19] + B[4] * Bd[19] * B[19] + B[4] * B[19] * Bd[19]) + T(4) * (Bd[7] * B[16] * B[19] + B[7] * Bd[16] * B[19] + B[7] * B[16] * Bd[19]) + T(4) * (Bd[8] * B[18] * B[19] + B[8] * Bd[18] * B[19] + B[8] * B[18] * Bd[19]) + T(2) * (Bd[5] * B[16] * B[16] + B[5] * Bd[16] * B[16] + B[5] * B[16] * Bd[16]) + T(4) * (Bd[9] * B[16] * B[18] + B[9] * Bd[16] * B[18] + B[9] * B[16] * Bd[18]) + T(2) * (Bd[6] * B[18] * B[18] + B[6] * Bd[18] * B[18] + B[6] * B[18] * Bd[18]);
   }
   static constexpr int NTERMS = 121;
 };

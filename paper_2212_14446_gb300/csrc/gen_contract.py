@@ -98,6 +98,26 @@ def gen_pa(PA):
         else:
             L.append(f"    A[{x}] = A[{lo}] * {names[d]};")
     L.append("  }")
+    # --- eval_d: A_x(u) and dA_x = grad A_x . w (forward mode, product rule on the recurrence)
+    L.append("  template <typename T>")
+    L.append("  static __device__ __forceinline__ void eval_d(T ux, T uy, T uz, T wx, T wy, T wz, T* A, T* dA) {")
+    L.append("    A[0] = T(1);")
+    L.append("    dA[0] = T(0);")
+    wn = ["wx", "wy", "wz"]
+    for x, e in enumerate(mons):
+        if x == 0:
+            continue
+        d = next(t for t in range(3) if e[t] > 0)
+        lower = list(e)
+        lower[d] -= 1
+        lo = index[tuple(lower)]
+        if lo == 0:
+            L.append(f"    A[{x}] = {names[d]};")
+            L.append(f"    dA[{x}] = {wn[d]};")
+        else:
+            L.append(f"    A[{x}] = A[{lo}] * {names[d]};")
+            L.append(f"    dA[{x}] = fma(dA[{lo}], {names[d]}, A[{lo}] * {wn[d]});")
+    L.append("  }")
     # --- grad of sum_x e_x A_x
     L.append("  template <typename T>")
     L.append("  static __device__ __forceinline__ void grad(const T* e, const T* A, T& gx, T& gy, T& gz) {")
@@ -127,6 +147,17 @@ def gen_pa(PA):
                 continue
             mu = multinomial(e)
             terms.append(f"B[{x}] * B[{x}]" if mu == 1 else f"{lit(mu)} * B[{x}] * B[{x}]")
+        L.append(f"    d[{n}] = " + " + ".join(terms) + ";")
+    L.append("  }")
+    # --- d3 tangent: d3d[n] = 2 sum_{x of degree n} mu_x B_x Bd_x
+    L.append("  template <typename T>")
+    L.append("  static __device__ __forceinline__ void d3_tangent(const T* B, const T* Bd, T* d) {")
+    for n in range(PA + 1):
+        terms = []
+        for x, e in enumerate(mons):
+            if sum(e) != n:
+                continue
+            terms.append(f"{lit(2 * multinomial(e))} * B[{x}] * Bd[{x}]")
         L.append(f"    d[{n}] = " + " + ".join(terms) + ";")
     L.append("  }")
     # --- d3 adjoint: a_x += 2 h_deg(x) mu_x B_x
@@ -196,6 +227,21 @@ def gen_pa(PA):
             L.append(f"      a[{y}] = fma({wk}, B[{x}] * B[{z}], a[{y}]);")
             L.append(f"      a[{z}] = fma({wk}, B[{x}] * B[{y}], a[{z}]);")
         L.append("    }")
+    L.append("  }")
+    # tangent: Dd[p] = sum_x dD4_p/dB_x Bd_x (general partitions by the product rule;
+    # b = c = 0 partitions from D4 = B_0 d3_a: Dd = Bd_0 d3_a + B_0 d3d_a)
+    L.append("  template <typename T>")
+    L.append("  static __device__ __forceinline__ void tangent(const T* B, const T* Bd, const T* d3, const T* d3d, T* Dd) {")
+    for p, (a_, b, c) in enumerate(parts):
+        if b == 0 and c == 0:
+            L.append(f"    Dd[{p}] = fma(Bd[0], d3[{a_}], B[0] * d3d[{a_}]);")
+            continue
+        acc = terms_of(a_, b, c)
+        ex = []
+        for (x, y, z), k in acc.items():
+            t = f"(Bd[{x}] * B[{y}] * B[{z}] + B[{x}] * Bd[{y}] * B[{z}] + B[{x}] * B[{y}] * Bd[{z}])"
+            ex.append(t if k == 1 else f"{lit(k)} * {t}")
+        L.append(f"    Dd[{p}] = " + " + ".join(ex) + ";")
     L.append("  }")
     L.append(f"  static constexpr int NTERMS = {nterms};")
     L.append("};")

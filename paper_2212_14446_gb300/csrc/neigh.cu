@@ -10,7 +10,7 @@ namespace fastpod {
 // rounded separately), split into FP32 hi + lo, bin into a cell.
 __global__ void bin_kernel(int N, const double* __restrict__ pos, CellGrid cg, double* __restrict__ wpos,
                            float4* __restrict__ phi, float4* __restrict__ plo, int* __restrict__ cell_count,
-                           int* __restrict__ cell_atoms, int* __restrict__ status) {
+                           int* __restrict__ cell_atoms, int* __restrict__ wrapk, int* __restrict__ status) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
   double x[3];
@@ -20,7 +20,12 @@ __global__ void bin_kernel(int N, const double* __restrict__ pos, CellGrid cg, d
   for (int d = 0; d < 3; ++d) {
     double v = pos[(size_t)d * N + i];
     finite = finite && isfinite(v);
-    if (cg.pbc[d]) v = __dsub_rn(v, __dmul_rn(cg.L[d], floor(__ddiv_rn(v, cg.L[d]))));
+    double k = 0.0;
+    if (cg.pbc[d]) {
+      k = floor(__ddiv_rn(v, cg.L[d]));
+      v = __dsub_rn(v, __dmul_rn(cg.L[d], k));
+    }
+    if (wrapk) wrapk[(size_t)d * N + i] = finite ? (int)k : 0;
     x[d] = v;
     int ci = (int)floor(v * cg.inv_cs[d]);
     ci = ci < 0 ? 0 : (ci >= cg.nc[d] ? cg.nc[d] - 1 : ci);
@@ -243,9 +248,66 @@ __global__ void export_neighbors_kernel(int N, int cap, const int* __restrict__ 
 
 // ------------------------------------------------------------ launchers
 cudaError_t launch_bin(int N, const double* pos, const CellGrid& cg, double* wpos, float4* phi, float4* plo,
-                       int* cell_count, int* cell_atoms, int* status, cudaStream_t st) {
+                       int* cell_count, int* cell_atoms, int* status, cudaStream_t st, int* wrapk) {
   const int tb = 256;
-  bin_kernel<<<(N + tb - 1) / tb, tb, 0, st>>>(N, pos, cg, wpos, phi, plo, cell_count, cell_atoms, status);
+  bin_kernel<<<(N + tb - 1) / tb, tb, 0, st>>>(N, pos, cg, wpos, phi, plo, cell_count, cell_atoms, wrapk, status);
+  return cudaGetLastError();
+}
+
+// Between rebuilds of a list built with a skin: positions are shifted by the
+// box multiples frozen at the last build (x - k L, the same rounding as the
+// wrap), so an atom that crossed the box edge keeps its images consistent with
+// the stored shifts.
+__global__ void rewrap_kernel(int N, const double* __restrict__ pos, const int* __restrict__ wrapk, double L0, double L1,
+                              double L2, double* __restrict__ wpos, float4* __restrict__ phi,
+                              float4* __restrict__ plo, int* __restrict__ status) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const double L[3] = {L0, L1, L2};
+  double x[3];
+  bool finite = true;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    double v = pos[(size_t)d * N + i];
+    finite = finite && isfinite(v);
+    const int k = wrapk[(size_t)d * N + i];
+    if (k != 0) v = __dsub_rn(v, __dmul_rn(L[d], (double)k));
+    x[d] = v;
+    wpos[(size_t)d * N + i] = v;
+  }
+  if (!finite) atomicOr(status, ST_NONFINITE);
+  float h[3], l[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    h[d] = __double2float_rn(x[d]);
+    l[d] = __double2float_rn(x[d] - (double)h[d]);
+  }
+  phi[i] = make_float4(h[0], h[1], h[2], 0.f);
+  plo[i] = make_float4(l[0], l[1], l[2], 0.f);
+}
+
+cudaError_t launch_rewrap(int N, const double* pos, const int* wrapk, const double L[3], double* wpos, float4* phi,
+                          float4* plo, int* status, cudaStream_t st) {
+  const int tb = 256;
+  rewrap_kernel<<<(N + tb - 1) / tb, tb, 0, st>>>(N, pos, wrapk, L[0], L[1], L[2], wpos, phi, plo, status);
+  return cudaGetLastError();
+}
+
+// Velocity Verlet halves: v += a dt / 2 with a = F conv / m, then optionally
+// x += v dt (kick_drift), all FP64.
+__global__ void kick_kernel(int N3, double* __restrict__ v, const double* __restrict__ F, double half_dt_over_m,
+                            double* __restrict__ x, double dt) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= N3) return;
+  const double vn = fma(F[e], half_dt_over_m, v[e]);
+  v[e] = vn;
+  if (x) x[e] = fma(vn, dt, x[e]);
+}
+
+cudaError_t launch_kick(int N3, double* v, const double* F, double half_dt_over_m, double* x, double dt,
+                        cudaStream_t st) {
+  const int tb = 256;
+  kick_kernel<<<(N3 + tb - 1) / tb, tb, 0, st>>>(N3, v, F, half_dt_over_m, x, dt);
   return cudaGetLastError();
 }
 

@@ -251,7 +251,7 @@ int pod_handle::timing_collect() {
 std::vector<DevBuf*> pod_handle::all_bufs() {
   return {&cell_count, &cell_atoms, &wpos, &phi, &plo, &nbr_count, &nbr_j, &nbr_s, &rev, &g, &Ei,
           &Wat, &status, &offs, &pos_in, &c_in, &E_out, &F_out, &W_out, &Ei_out, &fitA, &fitG, &fitb,
-          &fitwork, &cfg_of, &boxes, &rtab, &gT, &wpart};
+          &fitwork, &cfg_of, &boxes, &rtab, &gT, &wpart, &Dws, &chunks, &cpart, &wrapk};
 }
 
 // ============================================================ C ABI
@@ -341,6 +341,10 @@ int pod_set_option(pod_handle* h, int option, int value) {
     h->radial_mode = value;
     return POD_OK;
   }
+  if (option == POD_OPT_NEIGHBOR_REUSE) {
+    h->nbr_mode = value ? 1 : 0;
+    return POD_OK;
+  }
   if (option == POD_OPT_TIMING) {
     h->timing = value ? 1 : 0;
     return POD_OK;
@@ -354,6 +358,20 @@ int pod_set_option(pod_handle* h, int option, int value) {
 }
 
 const char* pod_last_error(const pod_handle* h) { return h ? h->err.c_str() : "null handle"; }
+
+int pod_set_skin(pod_handle* h, double skin) {
+  if (!h) return POD_EINVAL;
+  if (!(skin >= 0) || !std::isfinite(skin)) return h->fail(POD_EINVAL, "skin must be >= 0");
+  h->skin = skin;
+  h->reuse_ok = false;
+  return POD_OK;
+}
+
+int pod_md_step(pod_handle* h, const pod_system* sys, double* pos, double* v, double* F, const double* c,
+                double mass, double dt, double* E, void* stream) {
+  if (!h) return POD_EINVAL;
+  return h->md_step(sys, pos, v, F, c, mass, dt, E, (cudaStream_t)stream);
+}
 
 int pod_timing(pod_handle* h, double* ms, int* calls) {
   if (!h) return POD_EINVAL;
@@ -397,7 +415,7 @@ int pod_handle::read_status(cudaStream_t st) {
 }
 
 int pod_handle::plan_single(int N, const double box[3], const int pbc[3], Plan& pl) {
-  const double rc = P.r_cut;
+  const double rc = rlist();
   pl.N = N;
   double vol = 1.0;
   long long ncells = 1;
@@ -448,7 +466,7 @@ int pod_handle::plan_single(int N, const double box[3], const int pbc[3], Plan& 
 
 int pod_handle::plan_batch(const pod_system* sys, Plan& pl) {
   const int nc = sys->n_configs;
-  const double rc = P.r_cut;
+  const double rc = rlist();
   pl.N = sys->n_atoms;
   pl.batched = true;
   pl.n_cfg = nc;
@@ -502,6 +520,7 @@ int pod_handle::plan(const pod_system* sys, Plan& pl) {
 int pod_handle::build_neighbors(const double* pos, Plan& pl, bool need_rev, cudaStream_t st) {
   const int N = pl.N;
   int rc_;
+  reuse_ok = false;
   if (!pl.batched) {
     if ((rc_ = ensure(cell_count, sizeof(int) * (size_t)pl.cg.ncells, "cell counts"))) return rc_;
     if ((rc_ = ensure(cell_atoms, sizeof(int) * (size_t)pl.cg.ncells * pl.cg.cap, "cell atoms"))) return rc_;
@@ -524,17 +543,18 @@ int pod_handle::build_neighbors(const double* pos, Plan& pl, bool need_rev, cuda
                           (float4*)plo.p, (int*)status.p, st);
     if (e != cudaSuccess) return cuda_fail(e, "batch wrap kernel");
     e = launch_batch_neigh(N, (const int*)cfg_of.p, (const CfgBox*)boxes.p, (const double*)wpos.p,
-                           (const float4*)phi.p, P.r_cut, pl.Lmax, pl.Smax, pl.cap, (int*)nbr_count.p,
+                           (const float4*)phi.p, rlist(), pl.Lmax, pl.Smax, pl.cap, (int*)nbr_count.p,
                            (int*)nbr_j.p, (int*)nbr_s.p, (int*)status.p, st);
     if (e != cudaSuccess) return cuda_fail(e, "batch neighbour kernel");
   } else {
   e = cudaMemsetAsync(cell_count.p, 0, sizeof(int) * (size_t)pl.cg.ncells, st);
   if (e != cudaSuccess) return cuda_fail(e, "cell count clear");
+  if ((rc_ = ensure(wrapk, sizeof(int) * 3 * (size_t)N, "wrap offsets"))) return rc_;
   e = launch_bin(N, pos, pl.cg, (double*)wpos.p, (float4*)phi.p, (float4*)plo.p, (int*)cell_count.p,
-                 (int*)cell_atoms.p, (int*)status.p, st);
+                 (int*)cell_atoms.p, (int*)status.p, st, (int*)wrapk.p);
   if (e != cudaSuccess) return cuda_fail(e, "bin kernel");
   e = launch_neigh(N, pl.cg, (const double*)wpos.p, (const float4*)phi.p, (const float4*)plo.p,
-                   (const int*)cell_count.p, (const int*)cell_atoms.p, P.r_cut, pl.cap, (int*)nbr_count.p,
+                   (const int*)cell_count.p, (const int*)cell_atoms.p, rlist(), pl.cap, (int*)nbr_count.p,
                    (int*)nbr_j.p, (int*)nbr_s.p, (int*)status.p, st);
   if (e != cudaSuccess) return cuda_fail(e, "neighbour kernel");
   }
@@ -576,6 +596,8 @@ void pod_handle::fill_args(AtomArgs<T>& a, const Plan& pl) {
   a.status = (int*)status.p;
   a.cfg_of = pl.batched ? (const int*)cfg_of.p : nullptr;
   a.cbox = pl.batched ? (const CfgBox*)boxes.p : nullptr;
+  a.vdir = vdir_cur;
+  a.rmask = skin > 0 ? P.r_cut : 0.0;
 }
 
 // Cubic Hermite pieces of R_k on TAB_N equal intervals of (r_in, r_cut), from
@@ -695,7 +717,16 @@ int pod_handle::energy_forces(const pod_system* sys, const double* c, double* E,
     if ((rc_ = plan(sys, pl))) return rc_;
     if (pl.batched && W) return fail(POD_EINVAL, "the virial is not available for batches of configurations");
     if ((rc_ = mark(0, st))) return rc_;
-    if ((rc_ = build_neighbors(sys->pos, pl, true, st))) return rc_;
+    const bool reuse = nbr_mode == 1 && reuse_ok && !pl.batched && last_pl.N == N && last_pl.cg.L[0] == pl.cg.L[0] &&
+                       last_pl.cg.L[1] == pl.cg.L[1] && last_pl.cg.L[2] == pl.cg.L[2];
+    if (reuse) {
+      pl = last_pl;
+      cudaError_t ew = launch_rewrap(N, sys->pos, (const int*)wrapk.p, pl.cg.L, (double*)wpos.p, (float4*)phi.p,
+                                     (float4*)plo.p, (int*)status.p, st);
+      if (ew != cudaSuccess) return cuda_fail(ew, "rewrap kernel");
+    } else {
+      if ((rc_ = build_neighbors(sys->pos, pl, true, st))) return rc_;
+    }
     const size_t gbytes = (precision == POD_MIXED ? sizeof(Q4<float>) : sizeof(Q4<double>)) * (size_t)N * pl.cap;
     if ((rc_ = ensure(g, gbytes, "pair gradients"))) return rc_;
     if ((rc_ = ensure(gT, gbytes, "reverse pair gradients"))) return rc_;
@@ -735,8 +766,34 @@ int pod_handle::energy_forces(const pod_system* sys, const double* c, double* E,
     if ((rc_ = timing_collect())) return rc_;
     bool retry;
     if ((rc_ = finish(st, pl, retry))) return rc_;
-    if (!retry) return POD_OK;
+    if (!retry) {
+      if (!pl.batched) {
+        last_pl = pl;
+        reuse_ok = true;
+      }
+      return POD_OK;
+    }
   }
+}
+
+// One velocity-Verlet step: v += F dt / 2m, x += v dt, F <- F(x), v += F dt / 2m.
+// Units: mass in amu, dt in fs, forces in eV/A (1 eV/(A amu) = 9.648533212e-3 A/fs^2).
+int pod_handle::md_step(const pod_system* sys, double* pos, double* v, double* F, const double* c, double mass,
+                        double dt, double* E, cudaStream_t st) {
+  if (!sys || !pos || !v || !F || !c || !E) return fail(POD_EINVAL, "md_step: NULL argument");
+  if (sys->n_configs > 1) return fail(POD_EINVAL, "md_step takes a single configuration");
+  if (!(mass > 0) || !(dt > 0)) return fail(POD_EINVAL, "mass and dt must be positive");
+  const int N3 = 3 * sys->n_atoms;
+  const double h = 0.5 * dt * 9.648533212e-3 / mass;
+  cudaError_t e = launch_kick(N3, v, F, h, pos, dt, st);
+  if (e != cudaSuccess) return cuda_fail(e, "kick-drift kernel");
+  pod_system s2 = *sys;
+  s2.pos = pos;
+  int rc_ = energy_forces(&s2, c, E, nullptr, F, nullptr, st);
+  if (rc_) return rc_;
+  e = launch_kick(N3, v, F, h, nullptr, dt, st);
+  if (e != cudaSuccess) return cuda_fail(e, "kick kernel");
+  return POD_OK;
 }
 
 int pod_handle::descriptors(const pod_system* sys, double* D, cudaStream_t st) {
@@ -776,7 +833,63 @@ int pod_handle::neighbors(const pod_system* sys, int cap_out, int* count, int* n
   return POD_OK;
 }
 
+// Global descriptors G_m = sum_i D_im per configuration (Eq. 58a), or with vdir
+// their directional derivative sum_k dG_m/dr_k . v_k (tangent mode).
+int pod_handle::global_desc(const pod_system* sys, const double* vdir, double* Gout, cudaStream_t st) {
+  int rc_ = validate_system(sys);
+  if (rc_) return rc_;
+  if (!Gout) return fail(POD_EINVAL, "output is NULL");
+  const int N = sys->n_atoms;
+  retries = 0;
+  for (;;) {
+    Plan pl;
+    if ((rc_ = plan(sys, pl))) return rc_;
+    if ((rc_ = build_neighbors(sys->pos, pl, false, st))) return rc_;
+    if ((rc_ = ensure(Dws, sizeof(double) * (size_t)N * M, "descriptor workspace"))) return rc_;
+    // chunk table: <= 256 rows per chunk, chunks never cross a configuration
+    std::vector<int> rows, cfgc;
+    const int ncfg = pl.batched ? pl.n_cfg : 1;
+    cfgc.push_back(0);
+    for (int c = 0; c < ncfg; ++c) {
+      const int a0 = pl.batched ? h_cbox[c].a0 : 0, a1 = pl.batched ? h_cbox[c].a1 : N;
+      for (int r = a0; r < a1; r += 256) {
+        rows.push_back(r);
+        rows.push_back(std::min(a1, r + 256));
+      }
+      cfgc.push_back((int)rows.size() / 2);
+    }
+    const int nch = (int)rows.size() / 2;
+    if ((rc_ = ensure(chunks, sizeof(int) * (rows.size() + cfgc.size()), "chunk table"))) return rc_;
+    if ((rc_ = ensure(cpart, sizeof(double) * (size_t)std::max(nch, 1) * M, "column partials"))) return rc_;
+    cudaError_t e = cudaMemcpy(chunks.p, rows.data(), sizeof(int) * rows.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+      e = cudaMemcpy((int*)chunks.p + rows.size(), cfgc.data(), sizeof(int) * cfgc.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(e, "chunk table upload");
+    vdir_cur = vdir;
+    rc_ = run_atoms(vdir ? 2 : 0, pl, (double*)Dws.p, nullptr, nullptr, st);
+    vdir_cur = nullptr;
+    if (rc_) return rc_;
+    e = launch_colsum(nch, (const int*)chunks.p, ncfg, (const int*)chunks.p + rows.size(), M, (const double*)Dws.p,
+                      (double*)cpart.p, Gout, st);
+    if (e != cudaSuccess) return cuda_fail(e, "column sums");
+    bool retry;
+    if ((rc_ = finish(st, pl, retry))) return rc_;
+    if (!retry) return POD_OK;
+  }
+}
+
 extern "C" {
+
+int pod_global_descriptors(pod_handle* h, const pod_system* sys, double* G, void* stream) {
+  if (!h) return POD_EINVAL;
+  return h->global_desc(sys, nullptr, G, (cudaStream_t)stream);
+}
+
+int pod_descriptors_jvp(pod_handle* h, const pod_system* sys, const double* v, double* Gdot, void* stream) {
+  if (!h) return POD_EINVAL;
+  if (!v) return h->fail(POD_EINVAL, "direction v is NULL");
+  return h->global_desc(sys, v, Gdot, (cudaStream_t)stream);
+}
 
 int pod_neighbors(pod_handle* h, const pod_system* sys, int cap, int* count, int* nbr, int* shift, void* stream) {
   if (!h) return POD_EINVAL;

@@ -75,6 +75,18 @@ struct pod_handle {
   std::vector<int> h_cfg_of;
   int fit(const pod_system* batch, const double* E_ref, const double* F_ref, const pod_fit_opts* opts,
           double* c_out, double* mae_E, double* mae_F);
+  // neighbour lists with a skin, reused between rebuilds (single configurations)
+  double skin = 0.0;
+  int nbr_mode = 0;       // 0: rebuild every call, 1: reuse the last energy/force list
+  bool reuse_ok = false;
+  Plan last_pl;
+  DevBuf wrapk;
+  double rlist() const { return P.r_cut + skin; }
+  int md_step(const pod_system* sys, double* pos, double* v, double* F, const double* c, double mass, double dt,
+              double* E, cudaStream_t st);
+  int global_desc(const pod_system* sys, const double* vdir, double* G, cudaStream_t st);
+  const double* vdir_cur = nullptr;
+  DevBuf Dws, chunks, cpart;
   int fit_build(const pod_system* batch, const double* E_ref, const double* F_ref, const pod_fit_opts& o);
   int fit_gram(double gamma);
   int fit_solve_dev();

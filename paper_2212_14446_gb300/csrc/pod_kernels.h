@@ -14,7 +14,7 @@ struct AtomLayout {
   int SA;   // per-atom stride of R / R' (CH * KS + K: lanes (atom, m) hit distinct banks)
   int GA;   // per-atom stride of the staged (u, r), in Q4 units
   int AS;   // per-atom stride of the adjoint dE/dB (multiple of 4, odd number of 16-byte units)
-  size_t off_geo, off_R, off_Rp, off_adj, off_e, off_cnt, warp_bytes;
+  size_t off_geo, off_R, off_Rp, off_adj, off_e, off_cnt, off_V, warp_bytes;
 };
 
 template <typename T>
@@ -36,6 +36,8 @@ struct AtomArgs {
   Q4<T>* gT;            // mode 1: the same gradient stored at the reverse slot rev[p]
   const int* rev;       // mode 1: reverse slot of every pair slot
   double* wpart;        // mode 1: per-warp virial partials [warps][9]
+  const double* vdir;   // mode 2: displacement direction per atom [3][N] (tangent of D written to D)
+  double rmask;         // > 0: pairs with r >= rmask contribute nothing (lists built with a skin)
   const int* cfg_of;    // batch: configuration of each atom (NULL: one configuration, box L)
   const CfgBox* cbox;   // batch: per-configuration boxes
   int* status;
@@ -43,7 +45,11 @@ struct AtomArgs {
 };
 
 cudaError_t launch_bin(int N, const double* pos, const CellGrid& cg, double* wpos, float4* phi, float4* plo,
-                       int* cell_count, int* cell_atoms, int* status, cudaStream_t st);
+                       int* cell_count, int* cell_atoms, int* status, cudaStream_t st, int* wrapk = nullptr);
+cudaError_t launch_rewrap(int N, const double* pos, const int* wrapk, const double L[3], double* wpos, float4* phi,
+                          float4* plo, int* status, cudaStream_t st);
+cudaError_t launch_kick(int N3, double* v, const double* F, double half_dt_over_m, double* x, double dt,
+                        cudaStream_t st);
 cudaError_t launch_neigh(int N, const CellGrid& cg, const double* wpos, const float4* phi, const float4* plo,
                          const int* cell_count, const int* cell_atoms, double rcut, int cap, int* nbr_count,
                          int* nbr_j, int* nbr_s, int* status, cudaStream_t st);
@@ -69,6 +75,8 @@ cudaError_t launch_gather_reduce(int N, int cap, const int* nbr_count, const Q4<
                                  double* part, int nblocks, unsigned* ticket, double* E, double* W, int* status,
                                  cudaStream_t st);
 int atom_warps(int N, int K);
+cudaError_t launch_colsum(int n_chunks, const int* chunk_rows /*[n_chunks][2]*/, int n_cfg, const int* cfg_chunks,
+                          int M, const double* D, double* part, double* G, cudaStream_t st);
 int gather_blocks(int N);
 
 }  // namespace fastpod
