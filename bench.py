@@ -163,6 +163,25 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------ workloads
+def measure_fma_peaks(pkg, torch, stream, reps=5):
+    """Vector-pipe throughput of this GPU (TFLOP/s), timed with CUDA events on
+    ``stream`` around the library's FMA probe kernels."""
+    out = {}
+    for kind, name, iters in ((0, "fp32_fma", 2048), (1, "fp32x2_fma", 2048), (2, "fp64_fma", 64)):
+        with torch.cuda.stream(stream):
+            for _ in range(2):
+                pkg.pod_fma_probe(kind, iters, stream)
+            t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            t0.record(stream)
+            fl = 0.0
+            for _ in range(reps):
+                fl += pkg.pod_fma_probe(kind, iters, stream)
+            t1.record(stream)
+        torch.cuda.synchronize()
+        out[name] = fl / (t0.elapsed_time(t1) / 1e3) / 1e12
+    return out
+
+
 def workload(name, replica):
     if name == "full":
         return synth.params_full(), synth.config_full(replica), "bcc_ta_8192_K6_P4_4body"
@@ -306,6 +325,7 @@ def main():
     phase_ms, calls = pod.timing()
     pod.set_timing(False)
     phase_avg = [x / calls for x in phase_ms]
+    vec_peaks = measure_fma_peaks(pkg, torch, stream)
     count = pkg.POD(params, precision=args.precision).neighbors(pos, box, cap=96)[0]
     n_pairs = float(count.double().mean().item())
     fl_atom = algorithmic_flops_per_atom(params, n_pairs)
@@ -403,10 +423,14 @@ def main():
                          "frac": achieved_tflops / peak_tflops, "traffic": traffic,
                          "flops_per_atom": fl_atom, "atom_kernel_ms": atom_ms,
                          "peak_basis": ("152 SMs x 128 FP32 lanes x 2 x 2070 MHz (nominal max clock)"
-                                        if args.precision == "mixed" else "nominal FP64 1.25 TFLOP/s")},
+                                        if args.precision == "mixed" else "nominal FP64 1.25 TFLOP/s"),
+                         "measured_vector_tflops": vec_peaks,
+                         "frac_of_measured_fma": (achieved_tflops / vec_peaks["fp32_fma"]
+                                                       if args.precision == "mixed"
+                                                       else achieved_tflops / vec_peaks["fp64_fma"])},
             "phases_ms": {"neighbors": phase_avg[0], "atom": phase_avg[1], "gather": phase_avg[2],
                           "reduce": phase_avg[3]},
-            "gpu_launches": 5 * args.steps,
+            "gpu_launches": 4 * args.steps,
             "e2e": e2e,
             "cpu_baseline": cpu,
             "fp64_path": fp64,

@@ -250,10 +250,10 @@ int pod_fit_residual(pod_handle* h, const double* c, double* sum_abs_E, double* 
  * from calling cudaMalloc / cudaFree (which synchronise the device and fragment
  * the pool).  The caller passes the positions (device [3][N]) and the output D
  * (device [N][M]), as for pod_descriptors; every intermediate buffer lives in one
- * file-scope device array of about 4.3 MB that each GPU loading the library holds
+ * file-scope device array of about 6.3 MB that each GPU loading the library holds
  * until the process exits.
  *   Limits: one configuration of 1..4096 atoms (POD_EINVAL beyond), at most 64
- *   neighbours per atom and 64 atoms per cell (POD_ENEIGH beyond).
+ *   neighbours per atom and 32 atoms per cell (POD_ENEIGH beyond).
  *   The mixed path evaluates the radial snapshots per pair (POD_OPT_RADIAL = 1
  *   behaviour; descriptor error ~1e-5); the FP64 path is identical to
  *   pod_descriptors.
@@ -263,6 +263,16 @@ int pod_fit_residual(pod_handle* h, const double* c, double* sum_abs_E, double* 
  *   that overlap on the GPU (other streams or host threads) race and must be
  *   serialised by the caller.  Waits for `stream` before returning. */
 int pod_descriptors_static(pod_handle* h, const pod_system* sys, double* D, void* stream);
+
+/* Throughput probe for the vector pipes that bound the fused atom kernel (not a
+ * step of the method; the paper has no counterpart).  Launches, on `stream`, one
+ * grid of independent fused multiply-add chains filling every SM of the current
+ * device and stores in *flops the floating-point operations it performs (an FMA
+ * counts 2).  kind: 0 = FP32 fmaf, 1 = FP32 paired FMA (two lanes of float2 per
+ * instruction), 2 = FP64 fma.  The caller times the launch on `stream` (CUDA
+ * events) and divides.  Touches no caller memory; iters >= 1; POD_EINVAL on a
+ * bad kind/iters/null flops, POD_ECUDA on a launch failure. */
+int pod_fma_probe(int kind, int iters, double* flops, void* stream);
 
 /* Message of the last error on this handle ("" if none).  Owned by the handle. */
 const char* pod_last_error(const pod_handle* h);

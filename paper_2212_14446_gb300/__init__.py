@@ -61,7 +61,8 @@ class pod_fit_opts(C.Structure):
 EXPORTS = ["pod_create", "pod_destroy", "pod_info", "pod_set_option", "pod_status", "pod_timing",
            "pod_neighbors", "pod_descriptors", "pod_energy_forces", "pod_energy_forces_host", "pod_fit",
            "pod_fit_normal", "pod_fit_solve", "pod_fit_residual", "pod_descriptors_static",
-           "pod_global_descriptors", "pod_descriptors_jvp", "pod_set_skin", "pod_md_step", "pod_last_error"]
+           "pod_global_descriptors", "pod_descriptors_jvp", "pod_set_skin", "pod_md_step", "pod_fma_probe",
+           "pod_last_error"]
 
 _lib = None
 _lock = threading.Lock()
@@ -99,6 +100,7 @@ def lib():
                 "pod_fit_normal": (C.c_int, [H, S, dp, dp, C.POINTER(pod_fit_opts), dp, dp]),
                 "pod_fit_solve": (C.c_int, [H, dp, dp, dp]),
                 "pod_fit_residual": (C.c_int, [H, dp, dp, dp, ip, ip]),
+                "pod_fma_probe": (C.c_int, [C.c_int, C.c_int, dp, vp]),
                 "pod_last_error": (C.c_char_p, [H]),
             }
             for name, (res, args) in sig.items():
@@ -128,6 +130,16 @@ def pod_destroy(h):
 
 def pod_last_error(h) -> str:
     return lib().pod_last_error(h).decode()
+
+
+def pod_fma_probe(kind: int, iters: int, stream=None) -> float:
+    """Launch the vector-pipe throughput probe on ``stream`` (kind 0 FP32 FMA,
+    1 FP32 paired FMA, 2 FP64 FMA); returns the launch's flop count."""
+    fl = C.c_double(0.0)
+    rc = lib().pod_fma_probe(int(kind), int(iters), C.byref(fl), _stream(stream))
+    if rc != POD_OK:
+        raise PodError(rc, "pod_fma_probe failed")
+    return fl.value
 
 
 def _check(h, rc):

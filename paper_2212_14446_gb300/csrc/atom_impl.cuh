@@ -66,8 +66,9 @@ __device__ __forceinline__ void pair_pass(const AtomArgs<T>& p, const AtomLayout
     const int jj = f - base, slot = ch * CH + jj, i = atom0 + a;
     const size_t pidx = (size_t)i * p.cap + slot;
     const int j = p.nbr_j[pidx];
+    const int code = p.nbr_s[pidx];
     int sx, sy, sz;
-    shift_unpack(p.nbr_s[pidx], sx, sy, sz);
+    shift_unpack(code, sx, sy, sz);
     T dx, dy, dz;
     pair_disp<T>(p, i, j, sx, sy, sz, dx, dy, dz);
     const T r = d_sqrt(dx * dx + dy * dy + dz * dz);
@@ -208,7 +209,7 @@ __global__ void __launch_bounds__(WPB_ATOM * 32) atom_kernel(const AtomArgs<T> p
 #pragma unroll
   for (int x = 0; x < NA; ++x) B[x] = T(0);
   for (int ch = 0; ch < nchunks; ++ch) {
-    pair_pass<T, KT>(p, lay, geo, sR, sRp, scnt, atom0, A, K, ch, lane);
+    pair_pass<T, KT, false>(p, lay, geo, sR, sRp, scnt, atom0, A, K, ch, lane);
     __syncwarp();
     if (am) {
       const int nc = chunk_count(my_n, ch);
@@ -311,7 +312,7 @@ __global__ void __launch_bounds__(WPB_ATOM * 32) atom_kernel(const AtomArgs<T> p
   for (int ch = 0; ch < nchunks; ++ch) {
     if (nchunks > 1) {
       __syncwarp();
-      pair_pass<T, KT>(p, lay, geo, sR, sRp, scnt, atom0, A, K, ch, lane);
+      pair_pass<T, KT, false>(p, lay, geo, sR, sRp, scnt, atom0, A, K, ch, lane);
       __syncwarp();
     }
     int tot = 0;
@@ -385,7 +386,6 @@ __global__ void __launch_bounds__(WPB_ATOM * 32) atom_kernel(const AtomArgs<T> p
       out.w = T(0);
       const size_t pidx = (size_t)i * p.cap + slot;
       p.g[pidx] = out;
-      p.gT[p.rev[pidx]] = out;
       // pair virial  W -= r_ij (x) g_ij
       const T dx = u.x * u.w, dy = u.y * u.w, dz = u.z * u.w;
       wv[0] -= dx * out.x; wv[1] -= dx * out.y; wv[2] -= dx * out.z;

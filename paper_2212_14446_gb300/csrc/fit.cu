@@ -254,7 +254,6 @@ int pod_handle::fit_build(const pod_system* bsys, const double* E_ref, const dou
   const long long R = (long long)nc + 3LL * N;
   const size_t gbytes = (precision == POD_MIXED ? sizeof(Q4<float>) : sizeof(Q4<double>)) * (size_t)N * pl.cap;
   if ((rc_ = ensure(g, gbytes, "pair gradients"))) return rc_;
-  if ((rc_ = ensure(gT, gbytes, "reverse pair gradients"))) return rc_;
   const int nwarp = atom_warps(N, K);
   if ((rc_ = ensure(wpart, sizeof(double) * 9 * (size_t)nwarp, "virial partials"))) return rc_;
   if ((rc_ = ensure(Ei, sizeof(double) * (size_t)N, "atom energies"))) return rc_;
@@ -277,19 +276,20 @@ int pod_handle::fit_build(const pod_system* bsys, const double* E_ref, const dou
   if (e != cudaSuccess) return cuda_fail(e, "identity upload");
   double* AT = (double*)fitA.p;
   double* bvec = (double*)fitb.p;
+  const int* rev_in = (const int*)rev.p;  // the batch's reverse index, built once above
   for (int m = 0; m < M; ++m) {
     if ((rc_ = run_atoms(1, pl, nullptr, dI + (size_t)m * M, (double*)Ei.p, st))) return rc_;
     double* col = AT + (size_t)m * R;
     if (precision == POD_MIXED)
-      e = launch_gather_reduce<float>(N, pl.cap, (const int*)nbr_count.p, (const Q4<float>*)g.p,
-                                      (const Q4<float>*)gT.p, (const double*)Ei.p, (const double*)wpart.p, nwarp,
-                                      col + nc, o.w_F, (double*)Wat.p, nblk, (unsigned*)offs.p, dtot, nullptr,
-                                      (int*)status.p, st);
+      e = launch_gather_reduce<float>(N, pl.cap, (const int*)nbr_count.p, (const int*)nbr_j.p, (const int*)nbr_s.p,
+                                      rev_in, nullptr, (const Q4<float>*)g.p, (const double*)Ei.p,
+                                      (const double*)wpart.p, nwarp, col + nc, o.w_F, (double*)Wat.p, nblk,
+                                      (unsigned*)offs.p, dtot, nullptr, (int*)status.p, st);
     else
-      e = launch_gather_reduce<double>(N, pl.cap, (const int*)nbr_count.p, (const Q4<double>*)g.p,
-                                       (const Q4<double>*)gT.p, (const double*)Ei.p, (const double*)wpart.p, nwarp,
-                                       col + nc, o.w_F, (double*)Wat.p, nblk, (unsigned*)offs.p, dtot, nullptr,
-                                       (int*)status.p, st);
+      e = launch_gather_reduce<double>(N, pl.cap, (const int*)nbr_count.p, (const int*)nbr_j.p,
+                                       (const int*)nbr_s.p, rev_in, nullptr, (const Q4<double>*)g.p,
+                                       (const double*)Ei.p, (const double*)wpart.p, nwarp, col + nc, o.w_F,
+                                       (double*)Wat.p, nblk, (unsigned*)offs.p, dtot, nullptr, (int*)status.p, st);
     if (e != cudaSuccess) return cuda_fail(e, "design-matrix force rows");
     e = launch_segsum(nc, (const CfgBox*)boxes.p, (const double*)Ei.p, o.w_E, o.per_atom_energy, col, st);
     if (e != cudaSuccess) return cuda_fail(e, "design-matrix energy rows");

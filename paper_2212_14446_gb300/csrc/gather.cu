@@ -6,67 +6,141 @@
 
 namespace fastpod {
 
-// Warp per atom k, lane per neighbour slot t (coalesced):
-//   F_k = sum_t ( g[k, t] - gT[k, t] )
-// g[k, t] = dE_k/dr_kt and gT[k, t] = dE_j/dr_jk of the reverse pair, written by
-// the atom kernel (no atomics).  Per-block FP64 partials of E = sum_i E_i and of
-// the virial partials are summed in a fixed order by the last block to finish,
-// so every result is bitwise reproducible.
-constexpr int WPB_GATHER = 8;
+// Lower bounds of atom i0 in row j0 and of i1 in row j1, searched in lockstep
+// (branch-free binary search over the sentinel-padded sorted rows, so the two
+// chains of dependent loads overlap), then the scans over equal indices for the
+// negated shifts.  q = -1 if absent; an invalid query (v = false) returns -1 and
+// reads row 0 only.
+__device__ __forceinline__ void find_reverse2(const int* __restrict__ nbr_j, const int* __restrict__ nbr_s, int cap,
+                                              bool v0, int i0, int j0, int c0, bool v1, int i1, int j1, int c1,
+                                              int& q0, int& q1) {
+  const size_t b0 = (size_t)(v0 ? j0 : 0) * cap, b1 = (size_t)(v1 ? j1 : 0) * cap;
+  int lo0 = 0, lo1 = 0;
+  int step = 1;
+  while (2 * step <= cap) step *= 2;
+  for (; step > 0; step >>= 1) {
+    const bool t0 = lo0 + step <= cap && __ldg(nbr_j + b0 + lo0 + step - 1) < i0;
+    const bool t1 = lo1 + step <= cap && __ldg(nbr_j + b1 + lo1 + step - 1) < i1;
+    lo0 += t0 ? step : 0;
+    lo1 += t1 ? step : 0;
+  }
+  q0 = -1;
+  q1 = -1;
+  if (v0) {
+    const int want = shift_negate(c0);
+    for (int t = lo0; t < cap && __ldg(nbr_j + b0 + t) == i0; ++t)
+      if (__ldg(nbr_s + b0 + t) == want) { q0 = (int)(b0 + t); break; }
+  }
+  if (v1) {
+    const int want = shift_negate(c1);
+    for (int t = lo1; t < cap && __ldg(nbr_j + b1 + t) == i1; ++t)
+      if (__ldg(nbr_s + b1 + t) == want) { q1 = (int)(b1 + t); break; }
+  }
+}
+
+// Warp per atom k, lane per neighbour slot t (coalesced own slots):
+//   F_k = sum_t ( g[k, t] - g[rev(k, t)] )
+// g[k, t] = dE_k/dr_kt, written by the atom kernel; rev(k, t) is the slot of the
+// reverse pair in j's row, read from rev_in or searched (and then stored in
+// rev_out when given, for steps that reuse the list).  Each warp takes two atoms
+// per iteration so that their dependent loads overlap.  No atomics.  Per-block
+// FP64 partials of E = sum_i E_i and of the virial partials are summed in a fixed
+// order by the last block to finish, so every result is bitwise reproducible.
+constexpr int WPB_GATHER = 16;
+constexpr int GATHER_BLOCKS_PER_SM = 3;
 
 template <typename T>
-__global__ void __launch_bounds__(WPB_GATHER * 32)
-    gather_reduce_kernel(int N, int cap, const int* __restrict__ nbr_count, const Q4<T>* __restrict__ g,
-                         const Q4<T>* __restrict__ gT, const double* __restrict__ Ei,
+__global__ void __launch_bounds__(WPB_GATHER * 32, GATHER_BLOCKS_PER_SM)
+    gather_reduce_kernel(int N, int cap, const int* __restrict__ nbr_count, const int* __restrict__ nbr_j,
+                         const int* __restrict__ nbr_s, const int* __restrict__ rev_in, int* __restrict__ rev_out,
+                         const Q4<T>* __restrict__ g, const double* __restrict__ Ei,
                          const double* __restrict__ wpart, int n_wpart, double* __restrict__ F, double fscale,
                          double* __restrict__ part, unsigned* __restrict__ ticket, double* __restrict__ E_out,
                          double* __restrict__ W_out, int* __restrict__ status) {
   __shared__ double sred[WPB_GATHER][10];
   __shared__ bool last;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  double acc[10];
-#pragma unroll
-  for (int q = 0; q < 10; ++q) acc[q] = 0.0;
-  for (int k = blockIdx.x * WPB_GATHER + warp; k < N; k += gridDim.x * WPB_GATHER) {
-    const int n = min(nbr_count[k], cap);
-    T f0 = T(0), f1 = T(0), f2 = T(0);
-    for (int t = lane; t < n; t += 32) {
-      const size_t p = (size_t)k * cap + t;
-      const Q4<T> a = g[p], b = gT[p];
-      f0 += a.x - b.x;
-      f1 += a.y - b.y;
-      f2 += a.z - b.z;
+  const int stride = gridDim.x * WPB_GATHER;
+  double eacc = 0.0, wacc = 0.0;  // lane 0: atom energies; lane q < 9: virial component q
+  for (int k0 = blockIdx.x * WPB_GATHER + warp; k0 < N; k0 += 2 * stride) {
+    const int k1 = k0 + stride;
+    const bool has1 = k1 < N;
+    const int n0 = min(nbr_count[k0], cap);
+    const int n1 = has1 ? min(nbr_count[k1], cap) : 0;
+    T f0 = T(0), f1 = T(0), f2 = T(0), h0 = T(0), h1 = T(0), h2 = T(0);
+    const int nmax = max(n0, n1);
+    for (int t = lane; t < nmax; t += 32) {
+      const bool v0 = t < n0, v1 = t < n1;
+      const size_t p0 = (size_t)k0 * cap + t, p1 = (size_t)(has1 ? k1 : k0) * cap + t;
+      int q0 = -1, q1 = -1;
+      if (rev_in) {
+        if (v0) q0 = rev_in[p0];
+        if (v1) q1 = rev_in[p1];
+      } else {
+        const int j0 = v0 ? nbr_j[p0] : 0, c0 = v0 ? nbr_s[p0] : 0;
+        const int j1 = v1 ? nbr_j[p1] : 0, c1 = v1 ? nbr_s[p1] : 0;
+        find_reverse2(nbr_j, nbr_s, cap, v0, k0, j0, c0, v1, k1, j1, c1, q0, q1);
+        if (rev_out) {
+          if (v0) rev_out[p0] = q0;
+          if (v1) rev_out[p1] = q1;
+        }
+      }
+      if ((v0 && q0 < 0) || (v1 && q1 < 0))
+        atomicOr(status, ST_REV);  // a list without its reverse pair: reported, never read out of bounds
+      if (v0) {
+        const Q4<T> a = g[p0];
+        f0 += a.x;
+        f1 += a.y;
+        f2 += a.z;
+      }
+      if (v1) {
+        const Q4<T> a = g[p1];
+        h0 += a.x;
+        h1 += a.y;
+        h2 += a.z;
+      }
+      if (q0 >= 0) {
+        const Q4<T> b = g[q0];
+        f0 -= b.x;
+        f1 -= b.y;
+        f2 -= b.z;
+      }
+      if (q1 >= 0) {
+        const Q4<T> b = g[q1];
+        h0 -= b.x;
+        h1 -= b.y;
+        h2 -= b.z;
+      }
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       f0 += __shfl_xor_sync(0xffffffffu, f0, o);
       f1 += __shfl_xor_sync(0xffffffffu, f1, o);
       f2 += __shfl_xor_sync(0xffffffffu, f2, o);
+      h0 += __shfl_xor_sync(0xffffffffu, h0, o);
+      h1 += __shfl_xor_sync(0xffffffffu, h1, o);
+      h2 += __shfl_xor_sync(0xffffffffu, h2, o);
+    }
+    if (lane < 2 && (lane == 0 || has1)) {
+      const int k = lane == 0 ? k0 : k1;
+      const T x = lane == 0 ? f0 : h0, y = lane == 0 ? f1 : h1, z = lane == 0 ? f2 : h2;
+      if (F) {
+        F[k] = fscale * (double)x;
+        F[(size_t)N + k] = fscale * (double)y;
+        F[(size_t)2 * N + k] = fscale * (double)z;
+      }
+      if (!(isfinite((double)x) && isfinite((double)y) && isfinite((double)z))) atomicOr(status, ST_NONFINITE);
     }
     if (lane == 0) {
-      if (F) {
-        F[k] = fscale * (double)f0;
-        F[(size_t)N + k] = fscale * (double)f1;
-        F[(size_t)2 * N + k] = fscale * (double)f2;
-      }
-      if (!(isfinite((double)f0) && isfinite((double)f1) && isfinite((double)f2))) atomicOr(status, ST_NONFINITE);
-      acc[0] += Ei[k];
+      eacc += Ei[k0];
+      if (has1) eacc += Ei[k1];
     }
   }
   // virial partials of the atom kernel, a fixed subset per warp of this block
   if (lane < 9)
-    for (int w = blockIdx.x * WPB_GATHER + warp; w < n_wpart; w += gridDim.x * WPB_GATHER)
-      acc[1 + lane] += wpart[(size_t)w * 9 + lane];
-  // fold the per-lane virial components into lane 0's slot order
-#pragma unroll
-  for (int q = 0; q < 9; ++q) {
-    const double v = __shfl_sync(0xffffffffu, acc[1 + q], q);
-    if (lane == 0) acc[1 + q] = v;
-  }
-  if (lane == 0) {
-#pragma unroll
-    for (int q = 0; q < 10; ++q) sred[warp][q] = acc[q];
-  }
+    for (int w = blockIdx.x * WPB_GATHER + warp; w < n_wpart; w += stride) wacc += wpart[(size_t)w * 9 + lane];
+  if (lane == 0) sred[warp][0] = eacc;
+  if (lane < 9) sred[warp][1 + lane] = wacc;
   __syncthreads();
   if (threadIdx.x < 10) {
     double s = 0.0;
@@ -79,51 +153,48 @@ __global__ void __launch_bounds__(WPB_GATHER * 32)
   __syncthreads();
   if (!last) return;
   __threadfence();
-  // fixed-order parallel sum of the block partials: thread t adds blocks
-  // t, t + blockDim, ... in order (independent L2 loads), then one fixed tree
-  double s[10];
+  // fixed-order sum of the block partials: warp q adds component q; lane l adds
+  // blocks l, l + 32, ... in order, then a fixed butterfly across the lanes
+  if (warp < 10) {
+    double s = 0.0;
+    for (unsigned b = lane; b < gridDim.x; b += 32) s += __ldcg(part + (size_t)b * 10 + warp);
 #pragma unroll
-  for (int q = 0; q < 10; ++q) s[q] = 0.0;
-  for (unsigned b = threadIdx.x; b < gridDim.x; b += blockDim.x) {
-#pragma unroll
-    for (int q = 0; q < 10; ++q) s[q] += __ldcg(part + (size_t)b * 10 + q);
-  }
-  __shared__ double fin2[10][WPB_GATHER * 32];
-#pragma unroll
-  for (int q = 0; q < 10; ++q) fin2[q][threadIdx.x] = s[q];
-  __syncthreads();
-  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
-    if ((int)threadIdx.x < w) {
-#pragma unroll
-      for (int q = 0; q < 10; ++q) fin2[q][threadIdx.x] += fin2[q][threadIdx.x + w];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) {
+      if (warp == 0) E_out[0] = s;
+      else if (W_out) W_out[warp - 1] = s;
     }
-    __syncthreads();
   }
-  if (threadIdx.x == 0) E_out[0] = fin2[0][0];
-  if (W_out && threadIdx.x >= 1 && threadIdx.x < 10) W_out[threadIdx.x - 1] = fin2[threadIdx.x][0];
   if (threadIdx.x == 0) *ticket = 0u;  // ready for the next launch (graph replays)
 }
 
 template <typename T>
-cudaError_t launch_gather_reduce(int N, int cap, const int* nbr_count, const Q4<T>* g, const Q4<T>* gT,
-                                 const double* Ei, const double* wpart, int n_wpart, double* F, double fscale,
-                                 double* part, int nblocks, unsigned* ticket, double* E, double* W, int* status,
-                                 cudaStream_t st) {
-  gather_reduce_kernel<T><<<nblocks, WPB_GATHER * 32, 0, st>>>(N, cap, nbr_count, g, gT, Ei, wpart, n_wpart, F,
-                                                               fscale, part, ticket, E, W, status);
+cudaError_t launch_gather_reduce(int N, int cap, const int* nbr_count, const int* nbr_j, const int* nbr_s,
+                                 const int* rev_in, int* rev_out, const Q4<T>* g, const double* Ei,
+                                 const double* wpart, int n_wpart, double* F, double fscale, double* part,
+                                 int nblocks, unsigned* ticket, double* E, double* W, int* status, cudaStream_t st) {
+  gather_reduce_kernel<T><<<nblocks, WPB_GATHER * 32, 0, st>>>(N, cap, nbr_count, nbr_j, nbr_s, rev_in, rev_out, g,
+                                                               Ei, wpart, n_wpart, F, fscale, part, ticket, E, W,
+                                                               status);
   return cudaGetLastError();
 }
 
+// One wave of fat blocks (GATHER_BLOCKS_PER_SM per SM at most) striding over the
+// atoms keeps the number of block partials, and so the last block's fixed-order
+// sum, small.
 int gather_blocks(int N) {
   const int want = (N + WPB_GATHER - 1) / WPB_GATHER;
-  return want < 8 * 152 ? (want > 0 ? want : 1) : 8 * 152;
+  const int full = GATHER_BLOCKS_PER_SM * 152;
+  return want < full ? (want > 0 ? want : 1) : full;
 }
 
-template cudaError_t launch_gather_reduce<float>(int, int, const int*, const Q4<float>*, const Q4<float>*,
-                                                 const double*, const double*, int, double*, double, double*, int,
-                                                 unsigned*, double*, double*, int*, cudaStream_t);
-template cudaError_t launch_gather_reduce<double>(int, int, const int*, const Q4<double>*, const Q4<double>*,
-                                                  const double*, const double*, int, double*, double, double*, int,
-                                                  unsigned*, double*, double*, int*, cudaStream_t);
+template cudaError_t launch_gather_reduce<float>(int, int, const int*, const int*, const int*, const int*, int*,
+                                                 const Q4<float>*, const double*, const double*, int, double*,
+                                                 double, double*, int, unsigned*, double*, double*, int*,
+                                                 cudaStream_t);
+template cudaError_t launch_gather_reduce<double>(int, int, const int*, const int*, const int*, const int*, int*,
+                                                  const Q4<double>*, const double*, const double*, int, double*,
+                                                  double, double*, int, unsigned*, double*, double*, int*,
+                                                  cudaStream_t);
 
 }  // namespace fastpod

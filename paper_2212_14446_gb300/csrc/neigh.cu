@@ -7,10 +7,12 @@
 namespace fastpod {
 
 // One thread per atom: wrap into [0, L) (x - L floor(x / L), each operation
-// rounded separately), split into FP32 hi + lo, bin into a cell.
+// rounded separately), split into FP32 hi + lo, bin into a cell: the cell slot
+// holds the FP32 hi position and the atom index (in .w), so the search reads a
+// candidate with one load.
 __global__ void bin_kernel(int N, const double* __restrict__ pos, CellGrid cg, double* __restrict__ wpos,
                            float4* __restrict__ phi, float4* __restrict__ plo, int* __restrict__ cell_count,
-                           int* __restrict__ cell_atoms, int* __restrict__ wrapk, int* __restrict__ status) {
+                           float4* __restrict__ cell_pos, int* __restrict__ wrapk, int* __restrict__ status) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
   double x[3];
@@ -44,7 +46,7 @@ __global__ void bin_kernel(int N, const double* __restrict__ pos, CellGrid cg, d
   const int cell = (c[2] * cg.nc[1] + c[1]) * cg.nc[0] + c[0];
   const int slot = atomicAdd(&cell_count[cell], 1);
   if (slot < cg.cap)
-    cell_atoms[(size_t)cell * cg.cap + slot] = i;
+    cell_pos[(size_t)cell * cg.cap + slot] = make_float4(h[0], h[1], h[2], __int_as_float(i));
   else
     atomicOr(status, ST_CELL);
 }
@@ -57,7 +59,7 @@ __global__ void bin_kernel(int N, const double* __restrict__ pos, CellGrid cg, d
 __global__ void __launch_bounds__(WPB_NEIGH * 32)
     neigh_kernel(int N, CellGrid cg, const double* __restrict__ wpos, const float4* __restrict__ phi,
                  const float4* __restrict__ plo, const int* __restrict__ cell_count,
-                 const int* __restrict__ cell_atoms, double rc2, float rc2_lo, float rc2_hi, int cap,
+                 const float4* __restrict__ cell_pos, double rc2, float rc2_lo, float rc2_hi, int cap,
                  int keycap, int* __restrict__ nbr_count, int* __restrict__ nbr_j, int* __restrict__ nbr_s,
                  int* __restrict__ status) {
   extern __shared__ unsigned long long nsm[];
@@ -114,16 +116,19 @@ __global__ void __launch_bounds__(WPB_NEIGH * 32)
     int cmax = cnt;
 #pragma unroll
     for (int d = 16; d > 0; d >>= 1) cmax = max(cmax, __shfl_xor_sync(0xffffffffu, cmax, d));
-    const int* ca = cell_atoms + (size_t)cell * cg.cap;
-    for (int k = 0; k < cmax; ++k) {
-      bool hit = false;
-      unsigned long long key = 0;
-      if (k < cnt) {
-        const int j = ca[k];
-        if (!(j == i && code == zero)) {
+    const float4* cp = cell_pos + (size_t)cell * cg.cap;
+    for (int k0 = 0; k0 < cmax; k0 += 8) {
+      float4 q[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) q[u] = (k0 + u < cnt) ? cp[k0 + u] : make_float4(0.f, 0.f, 0.f, __int_as_float(-1));
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int j = __float_as_int(q[u].w);
+        bool hit = false;
+        unsigned long long key = 0;
+        if (j >= 0 && !(j == i && code == zero)) {
           // FP32 prefilter on the hi parts only; its error is far inside the band
-          const float4 hj = phi[j];
-          const float dx = hj.x + px, dy = hj.y + py, dz = hj.z + pz;
+          const float dx = q[u].x + px, dy = q[u].y + py, dz = q[u].z + pz;
           const float r2f = dx * dx + dy * dy + dz * dz;
           if (r2f < rc2_lo) {
             hit = true;
@@ -138,13 +143,13 @@ __global__ void __launch_bounds__(WPB_NEIGH * 32)
           }
           key = ((unsigned long long)j << 24) | (unsigned long long)code;
         }
+        const unsigned m = __ballot_sync(0xffffffffu, hit);
+        if (hit) {
+          const int pos = nhit + __popc(m & ((1u << lane) - 1u));
+          if (pos < keycap) keys[pos] = key;
+        }
+        nhit += __popc(m);
       }
-      const unsigned m = __ballot_sync(0xffffffffu, hit);
-      if (hit) {
-        const int pos = nhit + __popc(m & ((1u << lane) - 1u));
-        if (pos < keycap) keys[pos] = key;
-      }
-      nhit += __popc(m);
     }
   }
   __syncwarp();
@@ -208,22 +213,9 @@ __global__ void rev_kernel(int N, int cap, const int* __restrict__ nbr_count, co
   const int j = nbr_j[p];
   if (j >= N) return;  // sentinel slot
   const int i = (int)(p / cap);
-  const int want = shift_negate(nbr_s[p]);
-  const int* row = nbr_j + (size_t)j * cap;
-  int lo = 0, hi = cap;
-  while (lo < hi) {
-    const int mid = (lo + hi) >> 1;
-    if (row[mid] < i) lo = mid + 1; else hi = mid;
-  }
-  int found = -1;
-  for (int t = lo; t < cap && row[t] == i; ++t)
-    if (nbr_s[(size_t)j * cap + t] == want) { found = t; break; }
-  if (found < 0) {
-    atomicOr(status, ST_REV);
-    rev[p] = (int)p;  // keeps the gather in bounds; the status reports the inconsistency
-  } else {
-    rev[p] = (int)((size_t)j * cap + found);
-  }
+  const int q = find_reverse(nbr_j, nbr_s, cap, i, j, nbr_s[p]);
+  if (q < 0) atomicOr(status, ST_REV);
+  rev[p] = q;  // -1: the gather skips it (and the status reports the broken list)
 }
 
 // Copy the internal list into the caller's [N][cap_out] / [N][cap_out][3] layout.
@@ -248,9 +240,9 @@ __global__ void export_neighbors_kernel(int N, int cap, const int* __restrict__ 
 
 // ------------------------------------------------------------ launchers
 cudaError_t launch_bin(int N, const double* pos, const CellGrid& cg, double* wpos, float4* phi, float4* plo,
-                       int* cell_count, int* cell_atoms, int* status, cudaStream_t st, int* wrapk) {
+                       int* cell_count, float4* cell_pos, int* status, cudaStream_t st, int* wrapk) {
   const int tb = 256;
-  bin_kernel<<<(N + tb - 1) / tb, tb, 0, st>>>(N, pos, cg, wpos, phi, plo, cell_count, cell_atoms, wrapk, status);
+  bin_kernel<<<(N + tb - 1) / tb, tb, 0, st>>>(N, pos, cg, wpos, phi, plo, cell_count, cell_pos, wrapk, status);
   return cudaGetLastError();
 }
 
@@ -314,7 +306,7 @@ cudaError_t launch_kick(int N3, double* v, const double* F, double half_dt_over_
 size_t neigh_smem_bytes(int keycap) { return (size_t)WPB_NEIGH * keycap * sizeof(unsigned long long); }
 
 cudaError_t launch_neigh(int N, const CellGrid& cg, const double* wpos, const float4* phi, const float4* plo,
-                         const int* cell_count, const int* cell_atoms, double rcut, int cap, int* nbr_count,
+                         const int* cell_count, const float4* cell_pos, double rcut, int cap, int* nbr_count,
                          int* nbr_j, int* nbr_s, int* status, cudaStream_t st) {
   const double rc2 = rcut * rcut;
   // Error of the FP32 prefilter: each displacement component is formed from
@@ -338,7 +330,7 @@ cudaError_t launch_neigh(int N, const CellGrid& cg, const double* wpos, const fl
     granted = smem;
   }
   neigh_kernel<<<(N + WPB_NEIGH - 1) / WPB_NEIGH, WPB_NEIGH * 32, smem, st>>>(
-      N, cg, wpos, phi, plo, cell_count, cell_atoms, rc2, rc2_lo, rc2_hi, cap, keycap, nbr_count, nbr_j, nbr_s,
+      N, cg, wpos, phi, plo, cell_count, cell_pos, rc2, rc2_lo, rc2_hi, cap, keycap, nbr_count, nbr_j, nbr_s,
       status);
   return cudaGetLastError();
 }

@@ -251,7 +251,7 @@ int pod_handle::timing_collect() {
 std::vector<DevBuf*> pod_handle::all_bufs() {
   return {&cell_count, &cell_atoms, &wpos, &phi, &plo, &nbr_count, &nbr_j, &nbr_s, &rev, &g, &Ei,
           &Wat, &status, &offs, &pos_in, &c_in, &E_out, &F_out, &W_out, &Ei_out, &fitA, &fitG, &fitb,
-          &fitwork, &cfg_of, &boxes, &rtab, &gT, &wpart, &Dws, &chunks, &cpart, &wrapk};
+          &fitwork, &cfg_of, &boxes, &rtab, &wpart, &Dws, &chunks, &cpart, &wrapk};
 }
 
 // ============================================================ C ABI
@@ -523,7 +523,7 @@ int pod_handle::build_neighbors(const double* pos, Plan& pl, bool need_rev, cuda
   reuse_ok = false;
   if (!pl.batched) {
     if ((rc_ = ensure(cell_count, sizeof(int) * (size_t)pl.cg.ncells, "cell counts"))) return rc_;
-    if ((rc_ = ensure(cell_atoms, sizeof(int) * (size_t)pl.cg.ncells * pl.cg.cap, "cell atoms"))) return rc_;
+    if ((rc_ = ensure(cell_atoms, sizeof(float4) * (size_t)pl.cg.ncells * pl.cg.cap, "cell slots"))) return rc_;
   }
   if ((rc_ = ensure(wpos, sizeof(double) * 3 * (size_t)N, "wrapped positions"))) return rc_;
   if ((rc_ = ensure(phi, sizeof(float4) * (size_t)N, "positions hi"))) return rc_;
@@ -551,10 +551,10 @@ int pod_handle::build_neighbors(const double* pos, Plan& pl, bool need_rev, cuda
   if (e != cudaSuccess) return cuda_fail(e, "cell count clear");
   if ((rc_ = ensure(wrapk, sizeof(int) * 3 * (size_t)N, "wrap offsets"))) return rc_;
   e = launch_bin(N, pos, pl.cg, (double*)wpos.p, (float4*)phi.p, (float4*)plo.p, (int*)cell_count.p,
-                 (int*)cell_atoms.p, (int*)status.p, st, (int*)wrapk.p);
+                 (float4*)cell_atoms.p, (int*)status.p, st, (int*)wrapk.p);
   if (e != cudaSuccess) return cuda_fail(e, "bin kernel");
   e = launch_neigh(N, pl.cg, (const double*)wpos.p, (const float4*)phi.p, (const float4*)plo.p,
-                   (const int*)cell_count.p, (const int*)cell_atoms.p, rlist(), pl.cap, (int*)nbr_count.p,
+                   (const int*)cell_count.p, (const float4*)cell_atoms.p, rlist(), pl.cap, (int*)nbr_count.p,
                    (int*)nbr_j.p, (int*)nbr_s.p, (int*)status.p, st);
   if (e != cudaSuccess) return cuda_fail(e, "neighbour kernel");
   }
@@ -660,8 +660,6 @@ int pod_handle::run_atoms(int mode, const Plan& pl, double* D, const double* c, 
     a.c = c;
     a.Ei = Ei_dst;
     a.g = (Q4<float>*)g.p;
-    a.gT = (Q4<float>*)gT.p;
-    a.rev = (const int*)rev.p;
     a.wpart = (double*)wpart.p;
     e = launch_atom_f32(mode, a, PA, has4, st);
   } else {
@@ -672,8 +670,6 @@ int pod_handle::run_atoms(int mode, const Plan& pl, double* D, const double* c, 
     a.c = c;
     a.Ei = Ei_dst;
     a.g = (Q4<double>*)g.p;
-    a.gT = (Q4<double>*)gT.p;
-    a.rev = (const int*)rev.p;
     a.wpart = (double*)wpart.p;
     e = launch_atom_f64(mode, a, PA, has4, st);
   }
@@ -725,11 +721,16 @@ int pod_handle::energy_forces(const pod_system* sys, const double* c, double* E,
                                      (float4*)plo.p, (int*)status.p, st);
       if (ew != cudaSuccess) return cuda_fail(ew, "rewrap kernel");
     } else {
-      if ((rc_ = build_neighbors(sys->pos, pl, true, st))) return rc_;
+      // the gather searches the reverse slots; when the list may be reused (a
+      // skin, or reuse switched on) it also stores them for the reusing steps
+      if ((rc_ = build_neighbors(sys->pos, pl, false, st))) return rc_;
     }
+    const bool keep_rev = !reuse && !pl.batched && (skin > 0 || nbr_mode == 1);
+    if (keep_rev && (rc_ = ensure(rev, sizeof(int) * (size_t)N * pl.cap, "reverse index"))) return rc_;
+    const int* rev_in = reuse ? (const int*)rev.p : nullptr;
+    int* rev_out = keep_rev ? (int*)rev.p : nullptr;
     const size_t gbytes = (precision == POD_MIXED ? sizeof(Q4<float>) : sizeof(Q4<double>)) * (size_t)N * pl.cap;
     if ((rc_ = ensure(g, gbytes, "pair gradients"))) return rc_;
-    if ((rc_ = ensure(gT, gbytes, "reverse pair gradients"))) return rc_;
     const int nwarp = atom_warps(N, K);
     if ((rc_ = ensure(wpart, sizeof(double) * 9 * (size_t)nwarp, "virial partials"))) return rc_;
     double* Ei_dst = Ei_user;
@@ -749,13 +750,14 @@ int pod_handle::energy_forces(const pod_system* sys, const double* c, double* E,
     if ((rc_ = mark(2, st))) return rc_;
     cudaError_t e;
     if (precision == POD_MIXED)
-      e = launch_gather_reduce<float>(N, pl.cap, (const int*)nbr_count.p, (const Q4<float>*)g.p,
-                                      (const Q4<float>*)gT.p, Ei_dst, (const double*)wpart.p, nwarp, F, 1.0,
-                                      (double*)Wat.p, nblk, (unsigned*)offs.p, E, W, (int*)status.p, st);
+      e = launch_gather_reduce<float>(N, pl.cap, (const int*)nbr_count.p, (const int*)nbr_j.p, (const int*)nbr_s.p,
+                                      rev_in, rev_out, (const Q4<float>*)g.p, Ei_dst, (const double*)wpart.p, nwarp,
+                                      F, 1.0, (double*)Wat.p, nblk, (unsigned*)offs.p, E, W, (int*)status.p, st);
     else
-      e = launch_gather_reduce<double>(N, pl.cap, (const int*)nbr_count.p, (const Q4<double>*)g.p,
-                                       (const Q4<double>*)gT.p, Ei_dst, (const double*)wpart.p, nwarp, F, 1.0,
-                                       (double*)Wat.p, nblk, (unsigned*)offs.p, E, W, (int*)status.p, st);
+      e = launch_gather_reduce<double>(N, pl.cap, (const int*)nbr_count.p, (const int*)nbr_j.p,
+                                       (const int*)nbr_s.p, rev_in, rev_out, (const Q4<double>*)g.p, Ei_dst,
+                                       (const double*)wpart.p, nwarp, F, 1.0, (double*)Wat.p, nblk,
+                                       (unsigned*)offs.p, E, W, (int*)status.p, st);
     if (e != cudaSuccess) return cuda_fail(e, "gather kernel");
     if (pl.batched) {  // per-configuration energies (the gather wrote the batch total into E[0])
       e = launch_segsum(pl.n_cfg, (const CfgBox*)boxes.p, Ei_dst, 1.0, 0, E, st);
@@ -767,7 +769,7 @@ int pod_handle::energy_forces(const pod_system* sys, const double* c, double* E,
     bool retry;
     if ((rc_ = finish(st, pl, retry))) return rc_;
     if (!retry) {
-      if (!pl.batched) {
+      if (!pl.batched && (reuse || rev_out)) {  // a list can be reused once its reverse slots are stored
         last_pl = pl;
         reuse_ok = true;
       }

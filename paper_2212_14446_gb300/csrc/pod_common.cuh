@@ -87,6 +87,23 @@ __host__ __device__ __forceinline__ int shift_negate(int code) {
   return shift_pack(-sx, -sy, -sz);
 }
 
+// Slot of the reverse pair (j, i, -s) in j's row: lower bound on the atom index
+// over the sentinel-padded sorted row, then a scan over equal indices for the
+// negated shift.  -1 if absent.
+__device__ __forceinline__ int find_reverse(const int* __restrict__ nbr_j, const int* __restrict__ nbr_s, int cap,
+                                            int i, int j, int code) {
+  const int want = shift_negate(code);
+  const int* row = nbr_j + (size_t)j * cap;
+  int lo = 0, hi = cap;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (__ldg(row + mid) < i) lo = mid + 1; else hi = mid;
+  }
+  for (int t = lo; t < cap && __ldg(row + t) == i; ++t)
+    if (__ldg(nbr_s + (size_t)j * cap + t) == want) return (int)((size_t)j * cap + t);
+  return -1;
+}
+
 // ------------------------------------------------ displacements
 // FP64: d = (x_j + s L) - x_i, every operation rounded separately (no FMA), the
 // expression the neighbour test is defined on.

@@ -55,7 +55,7 @@ struct pod_handle {
   DevBuf pos_in, c_in, E_out, F_out, W_out, Ei_out;       // host-buffer entry point staging
   DevBuf fitA, fitG, fitb, fitwork, cfg_of, boxes;        // fit
   DevBuf rtab;                                            // tabulated radial basis (mixed path)
-  DevBuf gT, wpart;                                       // reverse-slot gradients, virial partials
+  DevBuf wpart;                                           // virial partials
   static constexpr int TAB_N = 2048;
   int radial_mode = 0;  // mixed path: 0 = tabulated R_k, 1 = snapshots evaluated per pair
   bool tab_ready = false;

@@ -33,8 +33,6 @@ struct AtomArgs {
   const double* c;      // mode 1: coefficients [M]
   double* Ei;           // mode 1: atom energies [N]
   Q4<T>* g;             // mode 1: dE_i/dr_ij per pair slot [N * cap]
-  Q4<T>* gT;            // mode 1: the same gradient stored at the reverse slot rev[p]
-  const int* rev;       // mode 1: reverse slot of every pair slot
   double* wpart;        // mode 1: per-warp virial partials [warps][9]
   const double* vdir;   // mode 2: displacement direction per atom [3][N] (tangent of D written to D)
   double rmask;         // > 0: pairs with r >= rmask contribute nothing (lists built with a skin)
@@ -45,13 +43,13 @@ struct AtomArgs {
 };
 
 cudaError_t launch_bin(int N, const double* pos, const CellGrid& cg, double* wpos, float4* phi, float4* plo,
-                       int* cell_count, int* cell_atoms, int* status, cudaStream_t st, int* wrapk = nullptr);
+                       int* cell_count, float4* cell_pos, int* status, cudaStream_t st, int* wrapk = nullptr);
 cudaError_t launch_rewrap(int N, const double* pos, const int* wrapk, const double L[3], double* wpos, float4* phi,
                           float4* plo, int* status, cudaStream_t st);
 cudaError_t launch_kick(int N3, double* v, const double* F, double half_dt_over_m, double* x, double dt,
                         cudaStream_t st);
 cudaError_t launch_neigh(int N, const CellGrid& cg, const double* wpos, const float4* phi, const float4* plo,
-                         const int* cell_count, const int* cell_atoms, double rcut, int cap, int* nbr_count,
+                         const int* cell_count, const float4* cell_pos, double rcut, int cap, int* nbr_count,
                          int* nbr_j, int* nbr_s, int* status, cudaStream_t st);
 cudaError_t launch_rev(int N, int cap, const int* nbr_count, const int* nbr_j, const int* nbr_s, int* rev,
                        int* status, cudaStream_t st);
@@ -70,10 +68,10 @@ cudaError_t launch_atom_f32(int mode, const AtomArgs<float>& p, int PA, bool has
 cudaError_t launch_atom_f64(int mode, const AtomArgs<double>& p, int PA, bool has4, cudaStream_t st);
 
 template <typename T>
-cudaError_t launch_gather_reduce(int N, int cap, const int* nbr_count, const Q4<T>* g, const Q4<T>* gT,
-                                 const double* Ei, const double* wpart, int n_wpart, double* F, double fscale,
-                                 double* part, int nblocks, unsigned* ticket, double* E, double* W, int* status,
-                                 cudaStream_t st);
+cudaError_t launch_gather_reduce(int N, int cap, const int* nbr_count, const int* nbr_j, const int* nbr_s,
+                                 const int* rev_in, int* rev_out, const Q4<T>* g, const double* Ei,
+                                 const double* wpart, int n_wpart, double* F, double fscale, double* part,
+                                 int nblocks, unsigned* ticket, double* E, double* W, int* status, cudaStream_t st);
 int atom_warps(int N, int K);
 cudaError_t launch_colsum(int n_chunks, const int* chunk_rows /*[n_chunks][2]*/, int n_cfg, const int* cfg_chunks,
                           int M, const double* D, double* part, double* G, cudaStream_t st);

@@ -14,7 +14,7 @@
 // Limits: at most STATIC_MAX_ATOMS atoms, STATIC_NBR_CAP neighbours per atom,
 // STATIC_MAX_CELLS cells of STATIC_CELL_CAP atoms; larger inputs are rejected
 // with POD_EINVAL, more neighbours or a fuller cell with POD_ENEIGH.  The
-// scratch array (about 4.3 MB) is part of every GPU that loads the library and
+// scratch array (about 6.3 MB) is part of every GPU that loads the library and
 // stays allocated until the process exits.  All calls share it: calls that
 // overlap on the GPU (other streams, other host threads) race, so serialise
 // them.  The first call on each device looks up the array's device address
@@ -34,7 +34,7 @@ namespace {
 constexpr int STATIC_MAX_ATOMS = 4096;
 constexpr int STATIC_NBR_CAP = 64;
 constexpr int STATIC_MAX_CELLS = 8192;
-constexpr int STATIC_CELL_CAP = 64;
+constexpr int STATIC_CELL_CAP = 32;
 constexpr size_t al256(size_t v) { return (v + 255) / 256 * 256; }
 constexpr size_t OFF_WPOS = 0;
 constexpr size_t OFF_PHI = al256(OFF_WPOS + sizeof(double) * 3 * STATIC_MAX_ATOMS);
@@ -44,7 +44,7 @@ constexpr size_t OFF_NBRJ = al256(OFF_CNT + sizeof(int) * STATIC_MAX_ATOMS);
 constexpr size_t OFF_NBRS = al256(OFF_NBRJ + sizeof(int) * (size_t)STATIC_MAX_ATOMS * STATIC_NBR_CAP);
 constexpr size_t OFF_CELLC = al256(OFF_NBRS + sizeof(int) * (size_t)STATIC_MAX_ATOMS * STATIC_NBR_CAP);
 constexpr size_t OFF_CELLA = al256(OFF_CELLC + sizeof(int) * STATIC_MAX_CELLS);
-constexpr size_t OFF_STATUS = al256(OFF_CELLA + sizeof(int) * (size_t)STATIC_MAX_CELLS * STATIC_CELL_CAP);
+constexpr size_t OFF_STATUS = al256(OFF_CELLA + sizeof(float4) * (size_t)STATIC_MAX_CELLS * STATIC_CELL_CAP);
 constexpr size_t SCRATCH_BYTES = al256(OFF_STATUS + 256);
 }  // namespace
 
@@ -141,11 +141,11 @@ extern "C" int pod_descriptors_static(pod_handle* h, const pod_system* sys, doub
   if (e == cudaSuccess) e = cudaMemsetAsync(cellc, 0, sizeof(int) * (size_t)ncells, st);
   if (e != cudaSuccess) return h->cuda_fail(e, "static scratch clear");
   e = launch_bin(N, sys->pos, pl.cg, reinterpret_cast<double*>(base + OFF_WPOS), reinterpret_cast<float4*>(base + OFF_PHI),
-                 reinterpret_cast<float4*>(base + OFF_PLO), cellc, reinterpret_cast<int*>(base + OFF_CELLA), status, st);
+                 reinterpret_cast<float4*>(base + OFF_PLO), cellc, reinterpret_cast<float4*>(base + OFF_CELLA), status, st);
   if (e != cudaSuccess) return h->cuda_fail(e, "bin kernel");
   e = launch_neigh(N, pl.cg, reinterpret_cast<const double*>(base + OFF_WPOS),
                    reinterpret_cast<const float4*>(base + OFF_PHI), reinterpret_cast<const float4*>(base + OFF_PLO),
-                   cellc, reinterpret_cast<const int*>(base + OFF_CELLA), h->P.r_cut, pl.cap,
+                   cellc, reinterpret_cast<const float4*>(base + OFF_CELLA), h->P.r_cut, pl.cap,
                    reinterpret_cast<int*>(base + OFF_CNT), reinterpret_cast<int*>(base + OFF_NBRJ),
                    reinterpret_cast<int*>(base + OFF_NBRS), status, st);
   if (e != cudaSuccess) return h->cuda_fail(e, "neighbour kernel");

@@ -331,3 +331,23 @@ def test_capacity_retry(pkg):
     D = pod.descriptors(soa(cfg), cfg.box, cfg.pbc).cpu().numpy()
     Dref = o.descriptors(cfg, atoms=range(0, 60, 6), fast=True)
     assert desc_err(D[::6], Dref) <= 1e-12
+
+
+def test_fma_probe(pkg):
+    """The vector-pipe probe launches, reports its flop count and gives a rate
+    below any physical ceiling (a far higher one would mean elided work)."""
+    s = torch.cuda.Stream()
+    nsm = torch.cuda.get_device_properties(0).multi_processor_count
+    for kind, iters in ((0, 64), (1, 64), (2, 4)):
+        fl = pkg.pod_fma_probe(kind, iters, s)
+        assert fl == 2 * 16 * 8 * iters * nsm * 8 * 256
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(s):
+            t0.record(s)
+            pkg.pod_fma_probe(kind, iters * 16, s)
+            t1.record(s)
+        torch.cuda.synchronize()
+        tflops = 16 * fl / (t0.elapsed_time(t1) / 1e3) / 1e12
+        assert 0.1 < tflops < 400.0
+    with pytest.raises(pkg.PodError):
+        pkg.pod_fma_probe(3, 1, s)
