@@ -52,10 +52,14 @@ __global__ void bin_kernel(int N, const double* __restrict__ pos, CellGrid cg, d
 }
 
 // Warp per atom.  Candidates of the (2S+1)^3 neighbouring cells are tested in
-// FP32 (double-float displacement); only those within a thin band around r_cut
-// are decided by the exact FP64 expression, so the list equals the FP64
-// definition bit for bit.  Hits are sorted by key (j, s) with a bitonic sort in
-// shared memory.
+// FP32 on the hi parts; those inside r_cut^2 - band are hits, those within the
+// thin band around r_cut^2 are kept with a mark and decided afterwards by the
+// exact FP64 expression, so the list equals the FP64 definition bit for bit
+// while the scan loop holds no FP64 state.  Hits are sorted by key (j, s) with a
+// bitonic sort (registers for <= 32 keys, else shared memory).
+constexpr int NEIGH_PREFETCH = 4;
+constexpr unsigned long long BAND_MARK = 1ull << 62;
+
 __global__ void __launch_bounds__(WPB_NEIGH * 32)
     neigh_kernel(int N, CellGrid cg, const double* __restrict__ wpos, const float4* __restrict__ phi,
                  const float4* __restrict__ plo, const int* __restrict__ cell_count,
@@ -68,16 +72,13 @@ __global__ void __launch_bounds__(WPB_NEIGH * 32)
   const int i = blockIdx.x * WPB_NEIGH + warp;
   if (i >= N) return;
 
-  const double xi0 = wpos[i], xi1 = wpos[(size_t)N + i], xi2 = wpos[(size_t)2 * N + i];
   const float4 hi_i = phi[i];
   int ci[3];
-  const double xi[3] = {xi0, xi1, xi2};
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
-    int c = (int)floor(xi[d] * cg.inv_cs[d]);
+    int c = (int)floor(wpos[(size_t)d * N + i] * cg.inv_cs[d]);
     ci[d] = c < 0 ? 0 : (c >= cg.nc[d] ? cg.nc[d] - 1 : c);
   }
-  const float Lh[3] = {(float)cg.L[0], (float)cg.L[1], (float)cg.L[2]};
   const int wx = 2 * cg.S[0] + 1, wy = 2 * cg.S[1] + 1, wz = 2 * cg.S[2] + 1;
   const int noff = wx * wy * wz;
   const int zero = shift_pack(0, 0, 0);
@@ -108,21 +109,22 @@ __global__ void __launch_bounds__(WPB_NEIGH * 32)
         cell = (tc[2] * cg.nc[1] + tc[1]) * cg.nc[0] + tc[0];
         cnt = min(cell_count[cell], cg.cap);
         code = shift_pack(sh[0], sh[1], sh[2]);
-        px = (float)sh[0] * Lh[0] - hi_i.x;
-        py = (float)sh[1] * Lh[1] - hi_i.y;
-        pz = (float)sh[2] * Lh[2] - hi_i.z;
+        px = (float)sh[0] * (float)cg.L[0] - hi_i.x;
+        py = (float)sh[1] * (float)cg.L[1] - hi_i.y;
+        pz = (float)sh[2] * (float)cg.L[2] - hi_i.z;
       }
     }
     int cmax = cnt;
 #pragma unroll
     for (int d = 16; d > 0; d >>= 1) cmax = max(cmax, __shfl_xor_sync(0xffffffffu, cmax, d));
     const float4* cp = cell_pos + (size_t)cell * cg.cap;
-    for (int k0 = 0; k0 < cmax; k0 += 8) {
-      float4 q[8];
+    for (int k0 = 0; k0 < cmax; k0 += NEIGH_PREFETCH) {
+      float4 q[NEIGH_PREFETCH];
 #pragma unroll
-      for (int u = 0; u < 8; ++u) q[u] = (k0 + u < cnt) ? cp[k0 + u] : make_float4(0.f, 0.f, 0.f, __int_as_float(-1));
+      for (int u = 0; u < NEIGH_PREFETCH; ++u)
+        q[u] = (k0 + u < cnt) ? cp[k0 + u] : make_float4(0.f, 0.f, 0.f, __int_as_float(-1));
 #pragma unroll
-      for (int u = 0; u < 8; ++u) {
+      for (int u = 0; u < NEIGH_PREFETCH; ++u) {
         const int j = __float_as_int(q[u].w);
         bool hit = false;
         unsigned long long key = 0;
@@ -130,18 +132,8 @@ __global__ void __launch_bounds__(WPB_NEIGH * 32)
           // FP32 prefilter on the hi parts only; its error is far inside the band
           const float dx = q[u].x + px, dy = q[u].y + py, dz = q[u].z + pz;
           const float r2f = dx * dx + dy * dy + dz * dz;
-          if (r2f < rc2_lo) {
-            hit = true;
-          } else if (r2f < rc2_hi) {
-            int sx, sy, sz;
-            shift_unpack(code, sx, sy, sz);
-            const double ddx = disp_fp64(xi0, wpos[j], sx, cg.L[0]);
-            const double ddy = disp_fp64(xi1, wpos[(size_t)N + j], sy, cg.L[1]);
-            const double ddz = disp_fp64(xi2, wpos[(size_t)2 * N + j], sz, cg.L[2]);
-            const double r2 = __dadd_rn(__dadd_rn(__dmul_rn(ddx, ddx), __dmul_rn(ddy, ddy)), __dmul_rn(ddz, ddz));
-            hit = r2 < rc2;
-          }
-          key = ((unsigned long long)j << 24) | (unsigned long long)code;
+          hit = r2f < rc2_hi;
+          key = ((unsigned long long)j << 24) | (unsigned long long)code | (r2f < rc2_lo ? 0ull : BAND_MARK);
         }
         const unsigned m = __ballot_sync(0xffffffffu, hit);
         if (hit) {
@@ -153,9 +145,37 @@ __global__ void __launch_bounds__(WPB_NEIGH * 32)
     }
   }
   __syncwarp();
-  const int n = min(nhit, keycap);
+  int n = min(nhit, keycap);
+  // decide the band candidates exactly in FP64 (R6): drop the misses
+  {
+    const double xi0 = wpos[i], xi1 = wpos[(size_t)N + i], xi2 = wpos[(size_t)2 * N + i];
+    int dropped = 0;
+    for (int t = lane; t < n; t += 32) {
+      unsigned long long key = keys[t];
+      bool drop = false;
+      if (key & BAND_MARK) {
+        key &= ~BAND_MARK;
+        const int j = (int)(key >> 24);
+        int sx, sy, sz;
+        shift_unpack((int)(key & 0xFFFFFFull), sx, sy, sz);
+        const double ddx = disp_fp64(xi0, wpos[j], sx, cg.L[0]);
+        const double ddy = disp_fp64(xi1, wpos[(size_t)N + j], sy, cg.L[1]);
+        const double ddz = disp_fp64(xi2, wpos[(size_t)2 * N + j], sz, cg.L[2]);
+        const double r2 = __dadd_rn(__dadd_rn(__dmul_rn(ddx, ddx), __dmul_rn(ddy, ddy)), __dmul_rn(ddz, ddz));
+        drop = !(r2 < rc2);
+        keys[t] = drop ? ~0ull : key;
+      }
+      dropped += drop ? 1 : 0;
+    }
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) dropped += __shfl_xor_sync(0xffffffffu, dropped, d);
+    // an overflowed key buffer lost candidates: keep the preliminary count (> cap)
+    // so the call reports it and retries with a larger capacity
+    if (nhit <= keycap) nhit -= dropped;
+    __syncwarp();
+  }
   if (n <= 32) {
-    // bitonic sort of one key per lane in registers
+    // bitonic sort of one key per lane in registers (dropped keys sort last)
     unsigned long long v = lane < n ? keys[lane] : ~0ull;
 #pragma unroll
     for (int k = 2; k <= 32; k <<= 1)
@@ -186,7 +206,8 @@ __global__ void __launch_bounds__(WPB_NEIGH * 32)
         __syncwarp();
       }
   }
-  const int nw = min(n, cap);
+  // the nhit valid keys lead the sorted array (when nothing overflowed)
+  const int nw = min(min(n, nhit), cap);
   for (int t = lane; t < cap; t += 32) {
     if (t < nw) {
       const unsigned long long key = keys[t];
