@@ -80,7 +80,7 @@ __device__ __forceinline__ void pair_pass(const AtomArgs<T>& p, const AtomLayout
     gq.w = r;
     geo[a * lay.GA + jj] = gq;
     T R[KT], Rp[KT];
-    if (r > p.rad.r_in && (p.rmask <= 0.0 || (double)r < p.rmask)) {
+    if (r > p.rad.r_in && r < p.rmask) {
       radial_pair<T, KT>(p.rad, r, R, Rp);
     } else {
       if (!(r > p.rad.r_in)) atomicOr(p.status, ST_RANGE);
@@ -134,6 +134,12 @@ __global__ void __launch_bounds__(WPB_ATOM * 32) atom_kernel(const AtomArgs<T> p
   const int a_loc = lane / K;
   const int m = lane - a_loc * K;
   const int atom0 = (blockIdx.x * WPB_ATOM + warp) * A;
+  // energy mode: the block converts the coefficients to T once (shared memory)
+  __shared__ T sc[MAXM];
+  if (MODE == 1) {
+    for (int q = threadIdx.x; q < p.M; q += blockDim.x) sc[q] = (T)p.c[q];
+    __syncthreads();
+  }
   if (atom0 >= p.N) {  // uniform per warp
     if (MODE == 1 && lane < 9) p.wpart[(size_t)(blockIdx.x * WPB_ATOM + warp) * 9 + lane] = 0.0;
     return;
@@ -259,19 +265,19 @@ __global__ void __launch_bounds__(WPB_ATOM * 32) atom_kernel(const AtomArgs<T> p
 #pragma unroll
     for (int x = 0; x < NAP; ++x) a[x] = T(0);
     if (am) {
-      const double* c = p.c;
-      const T c2 = (m < p.K2) ? (T)c[1 + m] : T(0);
+      const T* c = sc;
+      const T c2 = (m < p.K2) ? c[1 + m] : T(0);
       T h[PA + 1];
 #pragma unroll
       for (int n = 0; n <= PA; ++n)
-        h[n] = (n <= p.P3 && m < p.K3) ? (T)c[p.col3 + m * (p.P3 + 1) + n] : T(0);
+        h[n] = (n <= p.P3 && m < p.K3) ? c[p.col3 + m * (p.P3 + 1) + n] : T(0);
       T d3[PA + 1];
       Mono<PA>::d3(B, d3);
       T a0 = c2;
       if (HAS4) {
         T w4[KA];
 #pragma unroll
-        for (int q = 0; q < KA; ++q) w4[q] = (q < p.KA4 && m < p.K4) ? (T)c[p.col4 + m * p.KA4 + q] : T(0);
+        for (int q = 0; q < KA; ++q) w4[q] = (q < p.KA4 && m < p.K4) ? c[p.col4 + m * p.KA4 + q] : T(0);
         // general partitions (Eq. 30a): cubic form, E4 = (1/3) sum_x B_x dE4/dB_x
         Four<PA>::adjoint(B, w4, a);
         T E4 = T(0);
@@ -291,7 +297,7 @@ __global__ void __launch_bounds__(WPB_ATOM * 32) atom_kernel(const AtomArgs<T> p
       for (int n = 0; n <= PA; ++n) E = fma(h[n], d3[n], E);
       Mono<PA>::d3_adjoint(B, h, a);
       a[0] += a0;
-      if (m == 0) E += (T)c[0];
+      if (m == 0) E += c[0];
       T* adst = sadj + a_loc * lay.AS + m * NAP;
 #pragma unroll
       for (int x = 0; x < NAP; ++x) adst[x] = a[x];
@@ -329,7 +335,7 @@ __global__ void __launch_bounds__(WPB_ATOM * 32) atom_kernel(const AtomArgs<T> p
       T Rv[KT], Rpv[KT];
       if (p.rad.tab) {
         // tabulated basis: re-evaluating R, R' is cheaper than staging R'
-        if (u.w > p.rad.r_in && (p.rmask <= 0.0 || (double)u.w < p.rmask)) {
+        if (u.w > p.rad.r_in && u.w < p.rmask) {
           radial_pair<T, KT>(p.rad, u.w, Rv, Rpv);
         } else {
 #pragma unroll

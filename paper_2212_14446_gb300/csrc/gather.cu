@@ -1,6 +1,8 @@
 // Deterministic force gather, per-atom virial and fixed-order FP64 reductions.
 //   F_k = sum_{t in N(k)} ( g[k, t] - g[rev(k, t)] )   (F = -dE/dr, no atomics)
 //   W_k = - sum_{t in N(k)} d_kt (x) g[k, t]            (pair virial, summed later)
+#include <climits>
+
 #include "pod_common.cuh"
 #include "pod_kernels.h"
 
@@ -121,15 +123,13 @@ __global__ void __launch_bounds__(WPB_GATHER * 32, GATHER_BLOCKS_PER_SM)
       h1 += __shfl_xor_sync(0xffffffffu, h1, o);
       h2 += __shfl_xor_sync(0xffffffffu, h2, o);
     }
-    if (lane < 2 && (lane == 0 || has1)) {
-      const int k = lane == 0 ? k0 : k1;
-      const T x = lane == 0 ? f0 : h0, y = lane == 0 ? f1 : h1, z = lane == 0 ? f2 : h2;
-      if (F) {
-        F[k] = fscale * (double)x;
-        F[(size_t)N + k] = fscale * (double)y;
-        F[(size_t)2 * N + k] = fscale * (double)z;
-      }
-      if (!(isfinite((double)x) && isfinite((double)y) && isfinite((double)z))) atomicOr(status, ST_NONFINITE);
+    // lane c < 6 stores component c % 3 of atom c < 3 ? k0 : k1 (one conversion
+    // instruction per warp instead of six)
+    if (lane < 6 && (lane < 3 || has1)) {
+      const int k = lane < 3 ? k0 : k1, d = lane < 3 ? lane : lane - 3;
+      const T v = lane == 0 ? f0 : lane == 1 ? f1 : lane == 2 ? f2 : lane == 3 ? h0 : lane == 4 ? h1 : h2;
+      if (F) F[(size_t)d * N + k] = fscale * (double)v;
+      if (!isfinite(v)) atomicOr(status, ST_NONFINITE);
     }
     if (lane == 0) {
       eacc += Ei[k0];
@@ -173,6 +173,7 @@ cudaError_t launch_gather_reduce(int N, int cap, const int* nbr_count, const int
                                  const int* rev_in, int* rev_out, const Q4<T>* g, const double* Ei,
                                  const double* wpart, int n_wpart, double* F, double fscale, double* part,
                                  int nblocks, unsigned* ticket, double* E, double* W, int* status, cudaStream_t st) {
+  if (cap % 8 != 0) return cudaErrorInvalidValue;  // rows are read as 16-byte vectors
   gather_reduce_kernel<T><<<nblocks, WPB_GATHER * 32, 0, st>>>(N, cap, nbr_count, nbr_j, nbr_s, rev_in, rev_out, g,
                                                                Ei, wpart, n_wpart, F, fscale, part, ticket, E, W,
                                                                status);

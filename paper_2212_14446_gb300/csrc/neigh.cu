@@ -9,7 +9,10 @@ namespace fastpod {
 // One thread per atom: wrap into [0, L) (x - L floor(x / L), each operation
 // rounded separately), split into FP32 hi + lo, bin into a cell: the cell slot
 // holds the FP32 hi position and the atom index (in .w), so the search reads a
-// candidate with one load.
+// candidate with one load; phi[i].w holds the atom's own cell index.
+// A coordinate already in [0, L) has floor(x / L) = 0 exactly (the rounded
+// quotient of x < L by L stays below 1), so the FP64 division, slow on this
+// part, only runs for atoms outside the box.
 __global__ void bin_kernel(int N, const double* __restrict__ pos, CellGrid cg, double* __restrict__ wpos,
                            float4* __restrict__ phi, float4* __restrict__ plo, int* __restrict__ cell_count,
                            float4* __restrict__ cell_pos, int* __restrict__ wrapk, int* __restrict__ status) {
@@ -23,7 +26,7 @@ __global__ void bin_kernel(int N, const double* __restrict__ pos, CellGrid cg, d
     double v = pos[(size_t)d * N + i];
     finite = finite && isfinite(v);
     double k = 0.0;
-    if (cg.pbc[d]) {
+    if (cg.pbc[d] && !(v >= 0.0 && v < cg.L[d])) {
       k = floor(__ddiv_rn(v, cg.L[d]));
       v = __dsub_rn(v, __dmul_rn(cg.L[d], k));
     }
@@ -41,9 +44,9 @@ __global__ void bin_kernel(int N, const double* __restrict__ pos, CellGrid cg, d
     h[d] = __double2float_rn(x[d]);
     l[d] = __double2float_rn(x[d] - (double)h[d]);
   }
-  phi[i] = make_float4(h[0], h[1], h[2], 0.f);
-  plo[i] = make_float4(l[0], l[1], l[2], 0.f);
   const int cell = (c[2] * cg.nc[1] + c[1]) * cg.nc[0] + c[0];
+  phi[i] = make_float4(h[0], h[1], h[2], __int_as_float(cell));
+  plo[i] = make_float4(l[0], l[1], l[2], 0.f);
   const int slot = atomicAdd(&cell_count[cell], 1);
   if (slot < cg.cap)
     cell_pos[(size_t)cell * cg.cap + slot] = make_float4(h[0], h[1], h[2], __int_as_float(i));
@@ -73,12 +76,8 @@ __global__ void __launch_bounds__(WPB_NEIGH * 32)
   if (i >= N) return;
 
   const float4 hi_i = phi[i];
-  int ci[3];
-#pragma unroll
-  for (int d = 0; d < 3; ++d) {
-    int c = (int)floor(wpos[(size_t)d * N + i] * cg.inv_cs[d]);
-    ci[d] = c < 0 ? 0 : (c >= cg.nc[d] ? cg.nc[d] - 1 : c);
-  }
+  const int own = __float_as_int(hi_i.w);  // the atom's cell, from the bin kernel
+  const int ci[3] = {own % cg.nc[0], (own / cg.nc[0]) % cg.nc[1], own / (cg.nc[0] * cg.nc[1])};
   const int wx = 2 * cg.S[0] + 1, wy = 2 * cg.S[1] + 1, wz = 2 * cg.S[2] + 1;
   const int noff = wx * wy * wz;
   const int zero = shift_pack(0, 0, 0);
@@ -109,9 +108,9 @@ __global__ void __launch_bounds__(WPB_NEIGH * 32)
         cell = (tc[2] * cg.nc[1] + tc[1]) * cg.nc[0] + tc[0];
         cnt = min(cell_count[cell], cg.cap);
         code = shift_pack(sh[0], sh[1], sh[2]);
-        px = (float)sh[0] * (float)cg.L[0] - hi_i.x;
-        py = (float)sh[1] * (float)cg.L[1] - hi_i.y;
-        pz = (float)sh[2] * (float)cg.L[2] - hi_i.z;
+        px = (float)sh[0] * cg.Lf[0] - hi_i.x;
+        py = (float)sh[1] * cg.Lf[1] - hi_i.y;
+        pz = (float)sh[2] * cg.Lf[2] - hi_i.z;
       }
     }
     int cmax = cnt;
@@ -262,7 +261,7 @@ __global__ void export_neighbors_kernel(int N, int cap, const int* __restrict__ 
 // ------------------------------------------------------------ launchers
 cudaError_t launch_bin(int N, const double* pos, const CellGrid& cg, double* wpos, float4* phi, float4* plo,
                        int* cell_count, float4* cell_pos, int* status, cudaStream_t st, int* wrapk) {
-  const int tb = 256;
+  const int tb = 64;  // small blocks spread the FP64 work of small systems over all SMs
   bin_kernel<<<(N + tb - 1) / tb, tb, 0, st>>>(N, pos, cg, wpos, phi, plo, cell_count, cell_pos, wrapk, status);
   return cudaGetLastError();
 }

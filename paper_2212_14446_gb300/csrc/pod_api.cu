@@ -426,6 +426,7 @@ int pod_handle::plan_single(int N, const double box[3], const int pbc[3], Plan& 
     if (pbc[d] && !(L > 0)) return fail(POD_EINVAL, "periodic direction %d needs a positive box length", d);
     if (!(L >= 0) || !std::isfinite(L)) return fail(POD_EINVAL, "box length %d is not finite", d);
     cg.L[d] = L;
+    cg.Lf[d] = (float)L;
     int nc = L > 0 ? (int)std::floor(L / (rc * (1.0 + 1e-9))) : 1;
     nc = std::max(1, std::min(nc, 1024));
     cg.nc[d] = nc;
@@ -597,7 +598,7 @@ void pod_handle::fill_args(AtomArgs<T>& a, const Plan& pl) {
   a.cfg_of = pl.batched ? (const int*)cfg_of.p : nullptr;
   a.cbox = pl.batched ? (const CfgBox*)boxes.p : nullptr;
   a.vdir = vdir_cur;
-  a.rmask = skin > 0 ? P.r_cut : 0.0;
+  a.rmask = mask_radius<T>(skin > 0 ? P.r_cut : 0.0);
 }
 
 // Cubic Hermite pieces of R_k on TAB_N equal intervals of (r_in, r_cut), from
@@ -823,7 +824,7 @@ int pod_handle::neighbors(const pod_system* sys, int cap_out, int* count, int* n
   for (;;) {
     Plan pl;
     if ((rc_ = plan(sys, pl))) return rc_;
-    pl.cap = std::max(pl.cap, cap_out);
+    pl.cap = (std::max(pl.cap, cap_out) + 7) / 8 * 8;
     if ((rc_ = build_neighbors(sys->pos, pl, false, st))) return rc_;
     cudaError_t e = launch_export_neighbors(sys->n_atoms, pl.cap, (const int*)nbr_count.p, (const int*)nbr_j.p,
                                             (const int*)nbr_s.p, cap_out, count, nbr_out, shift_out, st);

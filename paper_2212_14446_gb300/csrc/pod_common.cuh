@@ -12,6 +12,7 @@ constexpr int MAXG = 8;    // gamma values
 constexpr int MAXK = 16;   // radial modes (= lanes per atom in the atom kernels)
 constexpr int MAXROWS = MAXA * MAXB + MAXG;
 constexpr int PAMAX = 4;   // highest angular degree compiled
+constexpr int MAXM = 1 + MAXK + MAXK * (PAMAX + 1) + MAXK * 11;  // descriptors (11 = four-body K_a at P = 4)
 constexpr int CH = 32;     // pairs per atom staged in shared memory at a time
 constexpr int WPB_ATOM = 2;   // warps per block, atom kernels
 constexpr int WPB_NEIGH = 4;  // warps per block, neighbour kernel
@@ -58,6 +59,7 @@ struct CellGrid {
   int S[3];       // cell offsets searched per direction
   int pbc[3];
   double L[3];    // box lengths
+  float Lf[3];    // box lengths rounded to FP32 (image offsets of the FP32 prefilter)
   double inv_cs[3];
   int ncells;
   int cap;        // atoms per cell

@@ -3,6 +3,8 @@
 #include <cuda_runtime.h>
 #include <stddef.h>
 
+#include <cmath>
+
 #include "pod_common.cuh"
 
 namespace fastpod {
@@ -35,12 +37,22 @@ struct AtomArgs {
   Q4<T>* g;             // mode 1: dE_i/dr_ij per pair slot [N * cap]
   double* wpart;        // mode 1: per-warp virial partials [warps][9]
   const double* vdir;   // mode 2: displacement direction per atom [3][N] (tangent of D written to D)
-  double rmask;         // > 0: pairs with r >= rmask contribute nothing (lists built with a skin)
+  T rmask;              // pairs with r >= rmask contribute nothing (lists built with a skin; +inf: none)
   const int* cfg_of;    // batch: configuration of each atom (NULL: one configuration, box L)
   const CfgBox* cbox;   // batch: per-configuration boxes
   int* status;
   RadialConst<T> rad;
 };
+
+// Mask radius in the pair arithmetic's type: the smallest T >= r (so that, for
+// every T value x, x < result exactly when x < r), or +inf when r <= 0 (no mask).
+template <typename T>
+inline T mask_radius(double r) {
+  if (!(r > 0)) return (T)INFINITY;
+  T v = (T)r;
+  if ((double)v < r) v = std::nextafter(v, (T)INFINITY);
+  return v;
+}
 
 cudaError_t launch_bin(int N, const double* pos, const CellGrid& cg, double* wpos, float4* phi, float4* plo,
                        int* cell_count, float4* cell_pos, int* status, cudaStream_t st, int* wrapk = nullptr);

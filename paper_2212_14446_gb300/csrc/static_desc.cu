@@ -101,7 +101,7 @@ void static_args(const pod_handle* h, const Plan& pl, const unsigned char* base,
   a.col4 = a.col3 + h->P.K3 * (h->P.P3 + 1);
   a.D = D;
   a.status = reinterpret_cast<int*>(const_cast<unsigned char*>(base) + OFF_STATUS);
-  a.rmask = h->skin > 0 ? h->P.r_cut : 0.0;  // a list built with a skin keeps only pairs inside r_cut
+  a.rmask = mask_radius<T>(h->skin > 0 ? h->P.r_cut : 0.0);  // a list built with a skin keeps only pairs inside r_cut
 }
 }  // namespace
 
