@@ -1,8 +1,6 @@
 // Deterministic force gather, per-atom virial and fixed-order FP64 reductions.
 //   F_k = sum_{t in N(k)} ( g[k, t] - g[rev(k, t)] )   (F = -dE/dr, no atomics)
 //   W_k = - sum_{t in N(k)} d_kt (x) g[k, t]            (pair virial, summed later)
-#include <climits>
-
 #include "pod_common.cuh"
 #include "pod_kernels.h"
 
@@ -173,7 +171,6 @@ cudaError_t launch_gather_reduce(int N, int cap, const int* nbr_count, const int
                                  const int* rev_in, int* rev_out, const Q4<T>* g, const double* Ei,
                                  const double* wpart, int n_wpart, double* F, double fscale, double* part,
                                  int nblocks, unsigned* ticket, double* E, double* W, int* status, cudaStream_t st) {
-  if (cap % 8 != 0) return cudaErrorInvalidValue;  // rows are read as 16-byte vectors
   gather_reduce_kernel<T><<<nblocks, WPB_GATHER * 32, 0, st>>>(N, cap, nbr_count, nbr_j, nbr_s, rev_in, rev_out, g,
                                                                Ei, wpart, n_wpart, F, fscale, part, ticket, E, W,
                                                                status);
