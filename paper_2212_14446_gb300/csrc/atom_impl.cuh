@@ -11,6 +11,8 @@
 //                  D3/D4 product and the whole adjoint run in registers;
 //   adjoint pair pass  lanes over pairs again, reading dE/dB_m from shared memory.
 #pragma once
+#include <type_traits>
+
 #include "contract_gen.cuh"
 #include "pod_common.cuh"
 #include "pod_kernels.h"
@@ -113,8 +115,16 @@ __device__ __forceinline__ void pair_pass(const AtomArgs<T>& p, const AtomLayout
   }
 }
 
+// FP32 specialised kernels are held to 128 registers (8 blocks per SM): the
+// paired multiply-add operands otherwise push them past that without a gain.
+template <typename T, int MODE, int KT>
+constexpr int atom_min_blocks() {
+  return (std::is_same<T, float>::value && MODE != 2 && KT != MAXK) ? 8 : 1;
+}
+
 template <typename T, int PA, bool HAS4, int MODE, int KT>
-__global__ void __launch_bounds__(WPB_ATOM * 32) atom_kernel(const AtomArgs<T> p, const AtomLayout lay) {
+__global__ void __launch_bounds__(WPB_ATOM * 32, atom_min_blocks<T, MODE, KT>())
+    atom_kernel(const AtomArgs<T> p, const AtomLayout lay) {
   constexpr int NA = Mono<PA>::NA;
   constexpr int NAP = (NA + 3) / 4 * 4;
   constexpr int KA = HAS4 ? Four<PA>::KA : 1;
@@ -214,6 +224,9 @@ __global__ void __launch_bounds__(WPB_ATOM * 32) atom_kernel(const AtomArgs<T> p
   T B[NA];
 #pragma unroll
   for (int x = 0; x < NA; ++x) B[x] = T(0);
+  float2 B2[Mono<PA>::NA2];  // FP32 path: B accumulated in pairs
+#pragma unroll
+  for (int k = 0; k < Mono<PA>::NA2; ++k) B2[k] = make_float2(0.f, 0.f);
   for (int ch = 0; ch < nchunks; ++ch) {
     pair_pass<T, KT, false>(p, lay, geo, sR, sRp, scnt, atom0, A, K, ch, lane);
     __syncwarp();
@@ -221,16 +234,33 @@ __global__ void __launch_bounds__(WPB_ATOM * 32) atom_kernel(const AtomArgs<T> p
       const int nc = chunk_count(my_n, ch);
       const Q4<T>* ga = geo + a_loc * lay.GA;
       const T* Ra = sR + a_loc * lay.SA + m;
-      for (int jj = 0; jj < nc; ++jj) {
-        const Q4<T> u = ga[jj];
-        const T R = Ra[jj * lay.KS];
-        T Am[NA];
-        Mono<PA>::eval(u.x, u.y, u.z, Am);
+      if constexpr (std::is_same<T, float>::value) {
+        // paired FP32 multiply-add: two basis components per instruction
+        for (int jj = 0; jj < nc; ++jj) {
+          const Q4<T> u = ga[jj];
+          const float R = Ra[jj * lay.KS];
+          float2 A2[Mono<PA>::NA2];
+          Mono<PA>::eval2(u.x, u.y, u.z, A2);
+          const float2 R2 = make_float2(R, R);
 #pragma unroll
-        for (int x = 0; x < NA; ++x) B[x] = fma(R, Am[x], B[x]);
+          for (int k = 0; k < Mono<PA>::NA2; ++k) B2[k] = __ffma2_rn(A2[k], R2, B2[k]);
+        }
+      } else {
+        for (int jj = 0; jj < nc; ++jj) {
+          const Q4<T> u = ga[jj];
+          const T R = Ra[jj * lay.KS];
+          T Am[NA];
+          Mono<PA>::eval(u.x, u.y, u.z, Am);
+#pragma unroll
+          for (int x = 0; x < NA; ++x) B[x] = fma(R, Am[x], B[x]);
+        }
       }
     }
     __syncwarp();
+  }
+  if constexpr (std::is_same<T, float>::value) {
+#pragma unroll
+    for (int x = 0; x < NA; ++x) B[x] = (x & 1) ? B2[x >> 1].y : B2[x >> 1].x;
   }
 
   if (MODE == 0) {
@@ -352,33 +382,65 @@ __global__ void __launch_bounds__(WPB_ATOM * 32) atom_kernel(const AtomArgs<T> p
         }
       }
       T Am[NAP];
-      Mono<PA>::eval(u.x, u.y, u.z, Am);
-#pragma unroll
-      for (int x = NA; x < NAP; ++x) Am[x] = T(0);
       T e[NAP];
-#pragma unroll
-      for (int x = 0; x < NAP; ++x) e[x] = T(0);
       T ps = T(0);
       const T* adj = sadj + a * lay.AS;
+      if constexpr (std::is_same<T, float>::value) {
+        // paired FP32 multiply-add over the basis components (a_m loaded as float4)
+        float2 A2[NAP / 2], e2[NAP / 2];
+        Mono<PA>::eval2(u.x, u.y, u.z, A2);
 #pragma unroll
-      for (int mm = 0; mm < KT; ++mm) {
-        if (KT == MAXK && mm >= K) break;
-        const T Rm = Rv[mm], Rpm = Rpv[mm];
-        const Q4<T>* a4 = reinterpret_cast<const Q4<T>*>(adj + mm * NAP);
-        T um = T(0);
+        for (int k = Mono<PA>::NA2; k < NAP / 2; ++k) A2[k] = make_float2(0.f, 0.f);
 #pragma unroll
-        for (int x4 = 0; x4 < NAP / 4; ++x4) {
-          const Q4<T> av = a4[x4];
-          um = fma(av.x, Am[4 * x4 + 0], um);
-          um = fma(av.y, Am[4 * x4 + 1], um);
-          um = fma(av.z, Am[4 * x4 + 2], um);
-          um = fma(av.w, Am[4 * x4 + 3], um);
-          e[4 * x4 + 0] = fma(av.x, Rm, e[4 * x4 + 0]);
-          e[4 * x4 + 1] = fma(av.y, Rm, e[4 * x4 + 1]);
-          e[4 * x4 + 2] = fma(av.z, Rm, e[4 * x4 + 2]);
-          e[4 * x4 + 3] = fma(av.w, Rm, e[4 * x4 + 3]);
+        for (int k = 0; k < NAP / 2; ++k) e2[k] = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int mm = 0; mm < KT; ++mm) {
+          if (KT == MAXK && mm >= K) break;
+          const float2 R2 = make_float2(Rv[mm], Rv[mm]);
+          const float4* a4 = reinterpret_cast<const float4*>(adj + mm * NAP);
+          float2 u2 = make_float2(0.f, 0.f);
+#pragma unroll
+          for (int x4 = 0; x4 < NAP / 4; ++x4) {
+            const float4 av = a4[x4];
+            const float2 lo = make_float2(av.x, av.y), hi = make_float2(av.z, av.w);
+            u2 = __ffma2_rn(lo, A2[2 * x4], u2);
+            u2 = __ffma2_rn(hi, A2[2 * x4 + 1], u2);
+            e2[2 * x4] = __ffma2_rn(lo, R2, e2[2 * x4]);
+            e2[2 * x4 + 1] = __ffma2_rn(hi, R2, e2[2 * x4 + 1]);
+          }
+          ps = fma(Rpv[mm], u2.x + u2.y, ps);
         }
-        ps = fma(Rpm, um, ps);
+#pragma unroll
+        for (int x = 0; x < NAP; ++x) {
+          Am[x] = (x & 1) ? A2[x >> 1].y : A2[x >> 1].x;
+          e[x] = (x & 1) ? e2[x >> 1].y : e2[x >> 1].x;
+        }
+      } else {
+        Mono<PA>::eval(u.x, u.y, u.z, Am);
+#pragma unroll
+        for (int x = NA; x < NAP; ++x) Am[x] = T(0);
+#pragma unroll
+        for (int x = 0; x < NAP; ++x) e[x] = T(0);
+#pragma unroll
+        for (int mm = 0; mm < KT; ++mm) {
+          if (KT == MAXK && mm >= K) break;
+          const T Rm = Rv[mm], Rpm = Rpv[mm];
+          const Q4<T>* a4 = reinterpret_cast<const Q4<T>*>(adj + mm * NAP);
+          T um = T(0);
+#pragma unroll
+          for (int x4 = 0; x4 < NAP / 4; ++x4) {
+            const Q4<T> av = a4[x4];
+            um = fma(av.x, Am[4 * x4 + 0], um);
+            um = fma(av.y, Am[4 * x4 + 1], um);
+            um = fma(av.z, Am[4 * x4 + 2], um);
+            um = fma(av.w, Am[4 * x4 + 3], um);
+            e[4 * x4 + 0] = fma(av.x, Rm, e[4 * x4 + 0]);
+            e[4 * x4 + 1] = fma(av.y, Rm, e[4 * x4 + 1]);
+            e[4 * x4 + 2] = fma(av.z, Rm, e[4 * x4 + 2]);
+            e[4 * x4 + 3] = fma(av.w, Rm, e[4 * x4 + 3]);
+          }
+          ps = fma(Rpm, um, ps);
+        }
       }
       T gx, gy, gz;
       Mono<PA>::grad(e, Am, gx, gy, gz);

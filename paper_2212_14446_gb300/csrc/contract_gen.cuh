@@ -10,6 +10,11 @@ template <> struct Mono<0> {
   static __device__ __forceinline__ void eval(T ux, T uy, T uz, T* A) {
     A[0] = T(1);
   }
+  static constexpr int NA2 = 1;
+  static __device__ __forceinline__ void eval2(float ux, float uy, float uz, float2* A2) {
+    A2[0].x = 1.0f;
+    A2[0].y = 0.0f;
+  }
   template <typename T>
   static __device__ __forceinline__ void eval_d(T ux, T uy, T uz, T wx, T wy, T wz, T* A, T* dA) {
     A[0] = T(1);
@@ -62,6 +67,13 @@ template <> struct Mono<1> {
     A[1] = ux;
     A[2] = uy;
     A[3] = uz;
+  }
+  static constexpr int NA2 = 2;
+  static __device__ __forceinline__ void eval2(float ux, float uy, float uz, float2* A2) {
+    A2[0].x = 1.0f;
+    A2[0].y = ux;
+    A2[1].x = uy;
+    A2[1].y = uz;
   }
   template <typename T>
   static __device__ __forceinline__ void eval_d(T ux, T uy, T uz, T wx, T wy, T wz, T* A, T* dA) {
@@ -138,6 +150,19 @@ template <> struct Mono<2> {
     A[7] = A[2] * ux;
     A[8] = A[3] * ux;
     A[9] = A[3] * uy;
+  }
+  static constexpr int NA2 = 5;
+  static __device__ __forceinline__ void eval2(float ux, float uy, float uz, float2* A2) {
+    A2[0].x = 1.0f;
+    A2[0].y = ux;
+    A2[1].x = uy;
+    A2[1].y = uz;
+    A2[2].x = A2[0].y * ux;
+    A2[2].y = A2[1].x * uy;
+    A2[3].x = A2[1].y * uz;
+    A2[3].y = A2[1].x * ux;
+    A2[4].x = A2[1].y * ux;
+    A2[4].y = A2[1].y * uy;
   }
   template <typename T>
   static __device__ __forceinline__ void eval_d(T ux, T uy, T uz, T wx, T wy, T wz, T* A, T* dA) {
@@ -282,6 +307,29 @@ template <> struct Mono<3> {
     A[17] = A[6] * ux;
     A[18] = A[6] * uy;
     A[19] = A[9] * ux;
+  }
+  static constexpr int NA2 = 10;
+  static __device__ __forceinline__ void eval2(float ux, float uy, float uz, float2* A2) {
+    A2[0].x = 1.0f;
+    A2[0].y = ux;
+    A2[1].x = uy;
+    A2[1].y = uz;
+    A2[2].x = A2[0].y * ux;
+    A2[2].y = A2[1].x * uy;
+    A2[3].x = A2[1].y * uz;
+    A2[3].y = A2[1].x * ux;
+    A2[4].x = A2[1].y * ux;
+    A2[4].y = A2[1].y * uy;
+    A2[5].x = A2[2].x * ux;
+    A2[5].y = A2[2].y * uy;
+    A2[6].x = A2[3].x * uz;
+    A2[6].y = A2[3].y * ux;
+    A2[7].x = A2[4].x * ux;
+    A2[7].y = A2[2].y * ux;
+    A2[8].x = A2[4].y * uy;
+    A2[8].y = A2[3].x * ux;
+    A2[9].x = A2[3].x * uy;
+    A2[9].y = A2[4].y * ux;
   }
   template <typename T>
   static __device__ __forceinline__ void eval_d(T ux, T uy, T uz, T wx, T wy, T wz, T* A, T* dA) {
@@ -604,6 +652,45 @@ template <> struct Mono<4> {
     A[32] = A[19] * ux;
     A[33] = A[16] * ux;
     A[34] = A[18] * ux;
+  }
+  static constexpr int NA2 = 18;
+  static __device__ __forceinline__ void eval2(float ux, float uy, float uz, float2* A2) {
+    A2[0].x = 1.0f;
+    A2[0].y = ux;
+    A2[1].x = uy;
+    A2[1].y = uz;
+    A2[2].x = A2[0].y * ux;
+    A2[2].y = A2[1].x * uy;
+    A2[3].x = A2[1].y * uz;
+    A2[3].y = A2[1].x * ux;
+    A2[4].x = A2[1].y * ux;
+    A2[4].y = A2[1].y * uy;
+    A2[5].x = A2[2].x * ux;
+    A2[5].y = A2[2].y * uy;
+    A2[6].x = A2[3].x * uz;
+    A2[6].y = A2[3].y * ux;
+    A2[7].x = A2[4].x * ux;
+    A2[7].y = A2[2].y * ux;
+    A2[8].x = A2[4].y * uy;
+    A2[8].y = A2[3].x * ux;
+    A2[9].x = A2[3].x * uy;
+    A2[9].y = A2[4].y * ux;
+    A2[10].x = A2[5].x * ux;
+    A2[10].y = A2[5].y * uy;
+    A2[11].x = A2[6].x * uz;
+    A2[11].y = A2[6].y * ux;
+    A2[12].x = A2[7].x * ux;
+    A2[12].y = A2[5].y * ux;
+    A2[13].x = A2[8].x * uy;
+    A2[13].y = A2[6].x * ux;
+    A2[14].x = A2[6].x * uy;
+    A2[14].y = A2[7].y * ux;
+    A2[15].x = A2[8].y * ux;
+    A2[15].y = A2[9].x * uy;
+    A2[16].x = A2[9].y * ux;
+    A2[16].y = A2[8].x * ux;
+    A2[17].x = A2[9].x * ux;
+    A2[17].y = 0.0f;
   }
   template <typename T>
   static __device__ __forceinline__ void eval_d(T ux, T uy, T uz, T wx, T wy, T wz, T* A, T* dA) {

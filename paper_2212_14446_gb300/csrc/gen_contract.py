@@ -6,6 +6,8 @@ For each PA the generated structs hold
   * ``Mono<PA>::eval``   angular monomials A_x(u) of degree <= PA in the order of
                          the paper's Table 3 (Eq. 23b), each as a product of a
                          lower-degree monomial and one coordinate;
+  * ``Mono<PA>::eval2``  the same monomials packed two per float2 (operands of the
+                         paired FP32 multiply-add);
   * ``Mono<PA>::grad``   gradient with respect to u of the polynomial
                          sum_x e_x A_x(u)  (used by the adjoint pair pass, Eq. 24c);
   * ``Mono<PA>::d3``     three-body contraction sum_l c_nl B_nl^2 per degree n
@@ -97,6 +99,27 @@ def gen_pa(PA):
             L.append(f"    A[{x}] = {names[d]};")
         else:
             L.append(f"    A[{x}] = A[{lo}] * {names[d]};")
+    L.append("  }")
+    # --- eval2: the same monomials packed two per float2 (A_x in A2[x / 2].x or .y),
+    # the operand layout of the paired FP32 fused multiply-add
+    NP2 = (NA + 1) // 2
+    L.append(f"  static constexpr int NA2 = {NP2};")
+    L.append("  static __device__ __forceinline__ void eval2(float ux, float uy, float uz, float2* A2) {")
+    comp = lambda x: f"A2[{x // 2}].{'x' if x % 2 == 0 else 'y'}"
+    L.append(f"    {comp(0)} = 1.0f;")
+    for x, e in enumerate(mons):
+        if x == 0:
+            continue
+        d = next(t for t in range(3) if e[t] > 0)
+        lower = list(e)
+        lower[d] -= 1
+        lo = index[tuple(lower)]
+        if lo == 0:
+            L.append(f"    {comp(x)} = {names[d]};")
+        else:
+            L.append(f"    {comp(x)} = {comp(lo)} * {names[d]};")
+    if NA % 2:
+        L.append(f"    {comp(NA)} = 0.0f;")
     L.append("  }")
     # --- eval_d: A_x(u) and dA_x = grad A_x . w (forward mode, product rule on the recurrence)
     L.append("  template <typename T>")
