@@ -226,6 +226,7 @@ def main():
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64-path comparison line items")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shapes")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -268,6 +269,11 @@ def main():
 
     def step():
         pkg.pod_energy_forces(pod.h, sysd, c, E, Ei, F, W, stream=stream)
+
+    shape = None
+    if not args.no_autotune:  # launch shapes for this system size (untimed setup)
+        with torch.cuda.stream(stream):
+            shape = pod.autotune(pos, box, c, reps=5, stream=stream)
 
     # warm-up (synchronous status checks; sizes the workspace)
     with torch.cuda.stream(stream):
@@ -417,7 +423,8 @@ def main():
             "config": {"workload": wname, "atoms_per_gpu": N, "global_atoms": N * world,
                        "pairs_per_atom": n_pairs, "descriptors": pod.M, "precision": args.precision,
                        "neighbor_rebuild": "every step", "l2": "flushed (512 MB write) before each step",
-                       "graph": "one CUDA graph per step", "parallelism": f"replicas x{world}"},
+                       "graph": "one CUDA graph per step", "parallelism": f"replicas x{world}",
+                       "launch_shape": shape},
             "roofline": {"bound": "alu", "kernel": "atom_kernel (fused radial/B/contraction/adjoint)",
                          "achieved": achieved_tflops, "peak": peak_tflops, "unit": "TFLOP/s",
                          "frac": achieved_tflops / peak_tflops, "traffic": traffic,
@@ -470,6 +477,10 @@ def run_md(args, rank, world, local):
     v = torch.tensor(g.normal(0.0, vrms, size=(3, N)), dtype=torch.float64, device=dev)
     E = torch.zeros(1, dtype=torch.float64, device=dev)
     stream = torch.cuda.Stream(device=dev)
+    shape = None
+    if not args.no_autotune:
+        with torch.cuda.stream(stream):
+            shape = pod.autotune(x, cfg.box, c, reps=3, stream=stream)
     with torch.cuda.stream(stream):
         F = pod.energy_forces(x, cfg.box, c, stream=stream)["F"].t().contiguous()
         for k in range(max(args.warmup, 3)):
@@ -511,7 +522,7 @@ def run_md(args, rank, world, local):
             "vs_baseline": None, "dtype": "f32" if args.precision == "mixed" else "f64", "data": "synthetic",
             "config": {"workload": "bcc_ta_1024000_md_verlet", "atoms_per_gpu": N, "skin_A": 0.3, "c_sigma": 1e-4,
                        "neighbor_rebuild": "every 10 steps", "dt_fs": dt, "graph": "captured rebuild/reuse steps",
-                       "l2": "state larger than L2"},
+                       "l2": "state larger than L2", "launch_shape": shape},
             "final_energy_eV": E.item(), "clocks": clk, "gpu_launches": None}
     if rank == 0:
         print(json.dumps(line))

@@ -61,7 +61,7 @@ class pod_fit_opts(C.Structure):
 EXPORTS = ["pod_create", "pod_destroy", "pod_info", "pod_set_option", "pod_status", "pod_timing",
            "pod_neighbors", "pod_descriptors", "pod_energy_forces", "pod_energy_forces_host", "pod_fit",
            "pod_fit_normal", "pod_fit_solve", "pod_fit_residual", "pod_descriptors_static",
-           "pod_global_descriptors", "pod_descriptors_jvp", "pod_set_skin", "pod_md_step", "pod_fma_probe",
+           "pod_global_descriptors", "pod_descriptors_jvp", "pod_set_skin", "pod_md_step", "pod_fma_probe", "pod_autotune",
            "pod_last_error"]
 
 _lib = None
@@ -101,6 +101,7 @@ def lib():
                 "pod_fit_solve": (C.c_int, [H, dp, dp, dp]),
                 "pod_fit_residual": (C.c_int, [H, dp, dp, dp, ip, ip]),
                 "pod_fma_probe": (C.c_int, [C.c_int, C.c_int, dp, vp]),
+                "pod_autotune": (C.c_int, [H, S, dp, C.c_int, ip, dp, vp]),
                 "pod_last_error": (C.c_char_p, [H]),
             }
             for name, (res, args) in sig.items():
@@ -202,6 +203,14 @@ def pod_descriptors_static(h, sys, D, stream=None):
 def pod_energy_forces(h, sys, c, E, Ei=None, F=None, W=None, stream=None):
     _check(h, lib().pod_energy_forces(h, C.byref(sys), _dptr(c), _dptr(E), _dptr(Ei), _dptr(F), _dptr(W),
                                       _stream(stream)))
+
+
+def pod_autotune(h, sys, c, reps=5, stream=None):
+    """Returns ([neigh wpb, atom wpb, gather wpb, gather blocks per SM], [ms neigh, atom, gather])."""
+    shape = (C.c_int * 4)()
+    ms = (C.c_double * 3)()
+    _check(h, lib().pod_autotune(h, C.byref(sys), _dptr(c), int(reps), shape, ms, _stream(stream)))
+    return list(shape), list(ms)
 
 
 def pod_energy_forces_host(h, sys, c, E, Ei=None, F=None, W=None, stream=None):
@@ -381,6 +390,16 @@ class POD:
         W = torch.empty(9, dtype=torch.float64, device=dev) if virial else None
         pod_energy_forces(self.h, self.system(x, box, pbc), c, E, Ei, F, W, stream)
         return {"E": E, "Ei": Ei, "F": None if F is None else F.t(), "W": None if W is None else W.view(3, 3)}
+
+    def autotune(self, pos, box, c, pbc=(1, 1, 1), reps=5, stream=None):
+        """Pick the launch shape for this system size (pod_autotune); returns
+        {"neigh_wpb", "atom_wpb", "gather_wpb", "gather_bps", "ms": [neigh, atom, gather]}."""
+        import torch
+        x = _soa(pos)
+        c = c.to(device=x.device, dtype=torch.float64).contiguous()
+        shape, ms = pod_autotune(self.h, self.system(x, box, pbc), c, reps, stream)
+        return {"neigh_wpb": shape[0], "atom_wpb": shape[1], "gather_wpb": shape[2], "gather_bps": shape[3],
+                "ms": ms}
 
     # -- batches of configurations --------------------------------------
     @staticmethod

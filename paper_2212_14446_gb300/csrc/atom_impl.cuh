@@ -115,15 +115,15 @@ __device__ __forceinline__ void pair_pass(const AtomArgs<T>& p, const AtomLayout
   }
 }
 
-// FP32 specialised kernels are held to 128 registers (8 blocks per SM): the
+// FP32 specialised kernels are held to 128 registers (4 blocks of 4 warps per SM): the
 // paired multiply-add operands otherwise push them past that without a gain.
 template <typename T, int MODE, int KT>
 constexpr int atom_min_blocks() {
-  return (std::is_same<T, float>::value && MODE != 2 && KT != MAXK) ? 8 : 1;
+  return (std::is_same<T, float>::value && MODE != 2 && KT != MAXK) ? 4 : 1;
 }
 
 template <typename T, int PA, bool HAS4, int MODE, int KT>
-__global__ void __launch_bounds__(WPB_ATOM * 32, atom_min_blocks<T, MODE, KT>())
+__global__ void __launch_bounds__(ATOM_MAX_WPB * 32, atom_min_blocks<T, MODE, KT>())
     atom_kernel(const AtomArgs<T> p, const AtomLayout lay) {
   constexpr int NA = Mono<PA>::NA;
   constexpr int NAP = (NA + 3) / 4 * 4;
@@ -143,7 +143,8 @@ __global__ void __launch_bounds__(WPB_ATOM * 32, atom_min_blocks<T, MODE, KT>())
   const int A = (KT == MAXK) ? lay.A : 32 / KT;
   const int a_loc = lane / K;
   const int m = lane - a_loc * K;
-  const int atom0 = (blockIdx.x * WPB_ATOM + warp) * A;
+  const int gwarp = blockIdx.x * (blockDim.x >> 5) + warp;  // global warp index
+  const int atom0 = gwarp * A;
   // energy mode: the block converts the coefficients to T once (shared memory)
   __shared__ T sc[MAXM];
   if (MODE == 1) {
@@ -151,7 +152,7 @@ __global__ void __launch_bounds__(WPB_ATOM * 32, atom_min_blocks<T, MODE, KT>())
     __syncthreads();
   }
   if (atom0 >= p.N) {  // uniform per warp
-    if (MODE == 1 && lane < 9) p.wpart[(size_t)(blockIdx.x * WPB_ATOM + warp) * 9 + lane] = 0.0;
+    if (MODE == 1 && lane < 9) p.wpart[(size_t)gwarp * 9 + lane] = 0.0;
     return;
   }
   if (lane < A) {
@@ -471,7 +472,7 @@ __global__ void __launch_bounds__(WPB_ATOM * 32, atom_min_blocks<T, MODE, KT>())
 #pragma unroll
     for (int q = 1; q < 9; ++q)
       if (lane == q) v = wv[q];
-    p.wpart[(size_t)(blockIdx.x * WPB_ATOM + warp) * 9 + lane] = (double)v;
+    p.wpart[(size_t)gwarp * 9 + lane] = (double)v;
   }
 }
 
@@ -512,7 +513,9 @@ AtomLayout make_layout(int K, int PA, bool table, bool tangent = false) {
 template <typename T, int PA, bool HAS4, int MODE, int KT>
 static cudaError_t launch_one(const AtomArgs<T>& p, const AtomLayout& lay, cudaStream_t st) {
   auto kern = atom_kernel<T, PA, HAS4, MODE, KT>;
-  const size_t smem = (size_t)WPB_ATOM * lay.warp_bytes;
+  const int wpb = p.wpb > 0 ? p.wpb : WPB_ATOM;
+  if (wpb > ATOM_MAX_WPB) return cudaErrorInvalidValue;
+  const size_t smem = (size_t)wpb * lay.warp_bytes;
   // raise the dynamic shared-memory limit once per instantiation and size (not
   // a stream operation, so it stays out of captured graphs after the first call)
   static size_t granted = 0;
@@ -521,18 +524,18 @@ static cudaError_t launch_one(const AtomArgs<T>& p, const AtomLayout& lay, cudaS
     if (e != cudaSuccess) return e;
     granted = smem;
   }
-  const int atoms_per_block = WPB_ATOM * lay.A;
+  const int atoms_per_block = wpb * lay.A;
   const int grid = (p.N + atoms_per_block - 1) / atoms_per_block;
-  if (grid > 0) kern<<<grid, WPB_ATOM * 32, smem, st>>>(p, lay);
+  if (grid > 0) kern<<<grid, wpb * 32, smem, st>>>(p, lay);
   return cudaGetLastError();
 }
 
 // Warps launched by the atom kernels for N atoms with K radial modes (one
 // virial partial per warp).
-inline int atom_warps_t(int N, int K) {
+inline int atom_warps_t(int N, int K, int wpb) {
   const int A = 32 / K;
-  const int apb = WPB_ATOM * A;
-  return (N + apb - 1) / apb * WPB_ATOM;
+  const int apb = wpb * A;
+  return (N + apb - 1) / apb * wpb;
 }
 
 template <typename T, int MODE>

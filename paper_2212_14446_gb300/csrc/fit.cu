@@ -254,10 +254,10 @@ int pod_handle::fit_build(const pod_system* bsys, const double* E_ref, const dou
   const long long R = (long long)nc + 3LL * N;
   const size_t gbytes = (precision == POD_MIXED ? sizeof(Q4<float>) : sizeof(Q4<double>)) * (size_t)N * pl.cap;
   if ((rc_ = ensure(g, gbytes, "pair gradients"))) return rc_;
-  const int nwarp = atom_warps(N, K);
+  const int nwarp = atom_warps(N, K, pl.shape.atom_wpb);
   if ((rc_ = ensure(wpart, sizeof(double) * 9 * (size_t)nwarp, "virial partials"))) return rc_;
   if ((rc_ = ensure(Ei, sizeof(double) * (size_t)N, "atom energies"))) return rc_;
-  const int nblk = gather_blocks(N);
+  const int nblk = gather_blocks(N, pl.shape.gather_wpb, pl.shape.gather_bps);
   if ((rc_ = ensure(Wat, sizeof(double) * 10 * (size_t)nblk, "block partial sums"))) return rc_;
   if (!offs.p) {
     if ((rc_ = ensure(offs, sizeof(unsigned) * 4, "ticket"))) return rc_;
@@ -284,12 +284,13 @@ int pod_handle::fit_build(const pod_system* bsys, const double* E_ref, const dou
       e = launch_gather_reduce<float>(N, pl.cap, (const int*)nbr_count.p, (const int*)nbr_j.p, (const int*)nbr_s.p,
                                       rev_in, nullptr, (const Q4<float>*)g.p, (const double*)Ei.p,
                                       (const double*)wpart.p, nwarp, col + nc, o.w_F, (double*)Wat.p, nblk,
-                                      (unsigned*)offs.p, dtot, nullptr, (int*)status.p, st);
+                                      (unsigned*)offs.p, dtot, nullptr, (int*)status.p, st, pl.shape.gather_wpb);
     else
       e = launch_gather_reduce<double>(N, pl.cap, (const int*)nbr_count.p, (const int*)nbr_j.p,
                                        (const int*)nbr_s.p, rev_in, nullptr, (const Q4<double>*)g.p,
                                        (const double*)Ei.p, (const double*)wpart.p, nwarp, col + nc, o.w_F,
-                                       (double*)Wat.p, nblk, (unsigned*)offs.p, dtot, nullptr, (int*)status.p, st);
+                                       (double*)Wat.p, nblk, (unsigned*)offs.p, dtot, nullptr, (int*)status.p, st,
+                                       pl.shape.gather_wpb);
     if (e != cudaSuccess) return cuda_fail(e, "design-matrix force rows");
     e = launch_segsum(nc, (const CfgBox*)boxes.p, (const double*)Ei.p, o.w_E, o.per_atom_energy, col, st);
     if (e != cudaSuccess) return cuda_fail(e, "design-matrix energy rows");

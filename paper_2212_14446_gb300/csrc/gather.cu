@@ -46,23 +46,23 @@ __device__ __forceinline__ void find_reverse2(const int* __restrict__ nbr_j, con
 // per iteration so that their dependent loads overlap.  No atomics.  Per-block
 // FP64 partials of E = sum_i E_i and of the virial partials are summed in a fixed
 // order by the last block to finish, so every result is bitwise reproducible.
-constexpr int WPB_GATHER = 16;
-constexpr int GATHER_BLOCKS_PER_SM = 3;
+constexpr int GATHER_MIN_BLOCKS = 3;  // 16-warp blocks: 40 registers
 
 template <typename T>
-__global__ void __launch_bounds__(WPB_GATHER * 32, GATHER_BLOCKS_PER_SM)
+__global__ void __launch_bounds__(GATHER_MAX_WPB * 32, GATHER_MIN_BLOCKS)
     gather_reduce_kernel(int N, int cap, const int* __restrict__ nbr_count, const int* __restrict__ nbr_j,
                          const int* __restrict__ nbr_s, const int* __restrict__ rev_in, int* __restrict__ rev_out,
                          const Q4<T>* __restrict__ g, const double* __restrict__ Ei,
                          const double* __restrict__ wpart, int n_wpart, double* __restrict__ F, double fscale,
                          double* __restrict__ part, unsigned* __restrict__ ticket, double* __restrict__ E_out,
                          double* __restrict__ W_out, int* __restrict__ status) {
-  __shared__ double sred[WPB_GATHER][10];
+  __shared__ double sred[GATHER_MAX_WPB][10];
   __shared__ bool last;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int stride = gridDim.x * WPB_GATHER;
+  const int nwarps = blockDim.x >> 5;
+  const int stride = gridDim.x * nwarps;
   double eacc = 0.0, wacc = 0.0;  // lane 0: atom energies; lane q < 9: virial component q
-  for (int k0 = blockIdx.x * WPB_GATHER + warp; k0 < N; k0 += 2 * stride) {
+  for (int k0 = blockIdx.x * nwarps + warp; k0 < N; k0 += 2 * stride) {
     const int k1 = k0 + stride;
     const bool has1 = k1 < N;
     const int n0 = min(nbr_count[k0], cap);
@@ -136,13 +136,13 @@ __global__ void __launch_bounds__(WPB_GATHER * 32, GATHER_BLOCKS_PER_SM)
   }
   // virial partials of the atom kernel, a fixed subset per warp of this block
   if (lane < 9)
-    for (int w = blockIdx.x * WPB_GATHER + warp; w < n_wpart; w += stride) wacc += wpart[(size_t)w * 9 + lane];
+    for (int w = blockIdx.x * nwarps + warp; w < n_wpart; w += stride) wacc += wpart[(size_t)w * 9 + lane];
   if (lane == 0) sred[warp][0] = eacc;
   if (lane < 9) sred[warp][1 + lane] = wacc;
   __syncthreads();
   if (threadIdx.x < 10) {
     double s = 0.0;
-    for (int wv = 0; wv < WPB_GATHER; ++wv) s += sred[wv][threadIdx.x];
+    for (int wv = 0; wv < nwarps; ++wv) s += sred[wv][threadIdx.x];
     part[(size_t)blockIdx.x * 10 + threadIdx.x] = s;
   }
   __threadfence();
@@ -151,16 +151,17 @@ __global__ void __launch_bounds__(WPB_GATHER * 32, GATHER_BLOCKS_PER_SM)
   __syncthreads();
   if (!last) return;
   __threadfence();
-  // fixed-order sum of the block partials: warp q adds component q; lane l adds
-  // blocks l, l + 32, ... in order, then a fixed butterfly across the lanes
-  if (warp < 10) {
+  // fixed-order sum of the block partials: component q is added by warp q mod
+  // (warps per block); lane l adds blocks l, l + 32, ... in order, then a fixed
+  // butterfly across the lanes
+  for (int q = warp; q < 10; q += nwarps) {
     double s = 0.0;
-    for (unsigned b = lane; b < gridDim.x; b += 32) s += __ldcg(part + (size_t)b * 10 + warp);
+    for (unsigned b = lane; b < gridDim.x; b += 32) s += __ldcg(part + (size_t)b * 10 + q);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     if (lane == 0) {
-      if (warp == 0) E_out[0] = s;
-      else if (W_out) W_out[warp - 1] = s;
+      if (q == 0) E_out[0] = s;
+      else if (W_out) W_out[q - 1] = s;
     }
   }
   if (threadIdx.x == 0) *ticket = 0u;  // ready for the next launch (graph replays)
@@ -170,29 +171,30 @@ template <typename T>
 cudaError_t launch_gather_reduce(int N, int cap, const int* nbr_count, const int* nbr_j, const int* nbr_s,
                                  const int* rev_in, int* rev_out, const Q4<T>* g, const double* Ei,
                                  const double* wpart, int n_wpart, double* F, double fscale, double* part,
-                                 int nblocks, unsigned* ticket, double* E, double* W, int* status, cudaStream_t st) {
-  gather_reduce_kernel<T><<<nblocks, WPB_GATHER * 32, 0, st>>>(N, cap, nbr_count, nbr_j, nbr_s, rev_in, rev_out, g,
+                                 int nblocks, unsigned* ticket, double* E, double* W, int* status, cudaStream_t st,
+                                 int wpb) {
+  if (wpb < 1 || wpb > GATHER_MAX_WPB) return cudaErrorInvalidValue;
+  gather_reduce_kernel<T><<<nblocks, wpb * 32, 0, st>>>(N, cap, nbr_count, nbr_j, nbr_s, rev_in, rev_out, g,
                                                                Ei, wpart, n_wpart, F, fscale, part, ticket, E, W,
                                                                status);
   return cudaGetLastError();
 }
 
-// One wave of fat blocks (GATHER_BLOCKS_PER_SM per SM at most) striding over the
-// atoms keeps the number of block partials, and so the last block's fixed-order
-// sum, small.
-int gather_blocks(int N) {
-  const int want = (N + WPB_GATHER - 1) / WPB_GATHER;
-  const int full = GATHER_BLOCKS_PER_SM * 152;
+// One wave of fat blocks (bps per SM at most) striding over the atoms keeps the
+// number of block partials, and so the last block's fixed-order sum, small.
+int gather_blocks(int N, int wpb, int bps) {
+  const int want = (N + wpb - 1) / wpb;
+  const int full = bps * 152;
   return want < full ? (want > 0 ? want : 1) : full;
 }
 
 template cudaError_t launch_gather_reduce<float>(int, int, const int*, const int*, const int*, const int*, int*,
                                                  const Q4<float>*, const double*, const double*, int, double*,
                                                  double, double*, int, unsigned*, double*, double*, int*,
-                                                 cudaStream_t);
+                                                 cudaStream_t, int);
 template cudaError_t launch_gather_reduce<double>(int, int, const int*, const int*, const int*, const int*, int*,
                                                   const Q4<double>*, const double*, const double*, int, double*,
                                                   double, double*, int, unsigned*, double*, double*, int*,
-                                                  cudaStream_t);
+                                                  cudaStream_t, int);
 
 }  // namespace fastpod

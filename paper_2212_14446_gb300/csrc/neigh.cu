@@ -63,7 +63,7 @@ __global__ void bin_kernel(int N, const double* __restrict__ pos, CellGrid cg, d
 constexpr int NEIGH_PREFETCH = 4;
 constexpr unsigned long long BAND_MARK = 1ull << 62;
 
-__global__ void __launch_bounds__(WPB_NEIGH * 32)
+__global__ void __launch_bounds__(NEIGH_MAX_WPB * 32)
     neigh_kernel(int N, CellGrid cg, const double* __restrict__ wpos, const float4* __restrict__ phi,
                  const float4* __restrict__ plo, const int* __restrict__ cell_count,
                  const float4* __restrict__ cell_pos, double rc2, float rc2_lo, float rc2_hi, int cap,
@@ -72,7 +72,7 @@ __global__ void __launch_bounds__(WPB_NEIGH * 32)
   extern __shared__ unsigned long long nsm[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   unsigned long long* keys = nsm + (size_t)warp * keycap;
-  const int i = blockIdx.x * WPB_NEIGH + warp;
+  const int i = blockIdx.x * (blockDim.x >> 5) + warp;
   if (i >= N) return;
 
   const float4 hi_i = phi[i];
@@ -323,11 +323,12 @@ cudaError_t launch_kick(int N3, double* v, const double* F, double half_dt_over_
   return cudaGetLastError();
 }
 
-size_t neigh_smem_bytes(int keycap) { return (size_t)WPB_NEIGH * keycap * sizeof(unsigned long long); }
+static size_t neigh_smem_bytes(int keycap, int wpb) { return (size_t)wpb * keycap * sizeof(unsigned long long); }
 
 cudaError_t launch_neigh(int N, const CellGrid& cg, const double* wpos, const float4* phi, const float4* plo,
                          const int* cell_count, const float4* cell_pos, double rcut, int cap, int* nbr_count,
-                         int* nbr_j, int* nbr_s, int* status, cudaStream_t st) {
+                         int* nbr_j, int* nbr_s, int* status, cudaStream_t st, int wpb) {
+  if (wpb < 1 || wpb > NEIGH_MAX_WPB) return cudaErrorInvalidValue;
   const double rc2 = rcut * rcut;
   // Error of the FP32 prefilter: each displacement component is formed from
   // FP32-rounded positions (|x| < L) and s * L_h, so |d_f32 - d| <= 4 ulp(L_max)
@@ -342,14 +343,14 @@ cudaError_t launch_neigh(int N, const CellGrid& cg, const double* wpos, const fl
   const float rc2_hi = (float)(rc2 + band);
   int keycap = 32;
   while (keycap < cap) keycap <<= 1;
-  const size_t smem = neigh_smem_bytes(keycap);
+  const size_t smem = neigh_smem_bytes(keycap, wpb);
   static size_t granted = 48 * 1024;
   if (smem > granted) {
     cudaError_t e = cudaFuncSetAttribute(neigh_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     granted = smem;
   }
-  neigh_kernel<<<(N + WPB_NEIGH - 1) / WPB_NEIGH, WPB_NEIGH * 32, smem, st>>>(
+  neigh_kernel<<<(N + wpb - 1) / wpb, wpb * 32, smem, st>>>(
       N, cg, wpos, phi, plo, cell_count, cell_pos, rc2, rc2_lo, rc2_hi, cap, keycap, nbr_count, nbr_j, nbr_s,
       status);
   return cudaGetLastError();

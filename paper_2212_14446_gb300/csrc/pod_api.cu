@@ -248,6 +248,85 @@ int pod_handle::timing_collect() {
   return POD_OK;
 }
 
+// Launch-shape autotuner: times the step's three phases (neighbour build, atom
+// kernel, gather) with CUDA events for each candidate shape on the caller's
+// system and keeps, per phase, the fastest (coordinate search; the phases are
+// independent kernels).  The winner is stored for the system's size class and
+// used by every later call on systems of that class.
+int pod_handle::autotune(const pod_system* sys, const double* c, int reps, cudaStream_t st, LaunchShape& best,
+                         double ms[3]) {
+  int rc_ = validate_system(sys);
+  if (rc_) return rc_;
+  if (sys->n_configs > 1) return fail(POD_EINVAL, "autotune takes a single configuration");
+  if (!c) return fail(POD_EINVAL, "coefficients are required");
+  if (reps < 1) reps = 5;
+  if ((rc_ = ensure(E_out, sizeof(double), "energy"))) return rc_;
+  double* E = (double*)E_out.p;
+  const int cls = size_class(sys->n_atoms);
+  const int keep_sync = sync, keep_timing = timing, keep_nbr = nbr_mode;
+  const double keep_acc[4] = {t_acc[0], t_acc[1], t_acc[2], t_acc[3]};
+  const int keep_calls = t_calls;
+  sync = 1;
+  timing = 1;
+  nbr_mode = 0;  // every timed call builds its list
+  auto measure = [&](const LaunchShape& s, double out[3]) -> int {
+    tuned[cls] = s;
+    int r = energy_forces(sys, c, E, nullptr, nullptr, nullptr, st);  // warm-up (sizes the workspace)
+    if (r) return r;
+    for (int k = 0; k < 4; ++k) t_acc[k] = 0;
+    t_calls = 0;
+    for (int i = 0; i < reps && !r; ++i) r = energy_forces(sys, c, E, nullptr, nullptr, nullptr, st);
+    for (int k = 0; k < 3; ++k) out[k] = t_calls ? t_acc[k] / t_calls : 0.0;
+    return r;
+  };
+  LaunchShape cur{};
+  double t[3];
+  static const int atom_c[] = {1, 2, 4};
+  static const int neigh_c[] = {2, 4, 8};
+  static const int gather_c[][2] = {{16, 3}, {16, 2}, {8, 6}, {8, 4}, {4, 12}};
+  double best_atom = 1e30, best_neigh = 1e30, best_gather = 1e30;
+  LaunchShape win = cur;
+  for (int a : atom_c) {
+    LaunchShape s = win;
+    s.atom_wpb = a;
+    if ((rc_ = measure(s, t))) break;
+    if (t[1] < best_atom) { best_atom = t[1]; win.atom_wpb = a; }
+  }
+  for (int n = 0; !rc_ && n < 3; ++n) {
+    LaunchShape s = win;
+    s.neigh_wpb = neigh_c[n];
+    if ((rc_ = measure(s, t))) break;
+    if (t[0] < best_neigh) { best_neigh = t[0]; win.neigh_wpb = neigh_c[n]; }
+  }
+  for (int g = 0; !rc_ && g < 5; ++g) {
+    LaunchShape s = win;
+    s.gather_wpb = gather_c[g][0];
+    s.gather_bps = gather_c[g][1];
+    if ((rc_ = measure(s, t))) break;
+    if (t[2] < best_gather) {
+      best_gather = t[2];
+      win.gather_wpb = gather_c[g][0];
+      win.gather_bps = gather_c[g][1];
+    }
+  }
+  sync = keep_sync;
+  timing = keep_timing;
+  nbr_mode = keep_nbr;
+  for (int k = 0; k < 4; ++k) t_acc[k] = keep_acc[k];
+  t_calls = keep_calls;
+  reuse_ok = false;
+  if (rc_) {
+    tuned.erase(cls);
+    return rc_;
+  }
+  tuned[cls] = win;
+  best = win;
+  ms[0] = best_neigh;
+  ms[1] = best_atom;
+  ms[2] = best_gather;
+  return POD_OK;
+}
+
 std::vector<DevBuf*> pod_handle::all_bufs() {
   return {&cell_count, &cell_atoms, &wpos, &phi, &plo, &nbr_count, &nbr_j, &nbr_s, &rev, &g, &Ei,
           &Wat, &status, &offs, &pos_in, &c_in, &E_out, &F_out, &W_out, &Ei_out, &fitA, &fitG, &fitb,
@@ -355,6 +434,24 @@ int pod_set_option(pod_handle* h, int option, int value) {
     return POD_OK;
   }
   return h->fail(POD_EINVAL, "unknown option %d", option);
+}
+
+int pod_autotune(pod_handle* h, const pod_system* sys, const double* c, int reps, int* shape, double* ms,
+                 void* stream) {
+  if (!h) return POD_EINVAL;
+  LaunchShape best{};
+  double t[3] = {0, 0, 0};
+  const int rc = h->autotune(sys, c, reps, (cudaStream_t)stream, best, t);
+  if (rc) return rc;
+  if (shape) {
+    shape[0] = best.neigh_wpb;
+    shape[1] = best.atom_wpb;
+    shape[2] = best.gather_wpb;
+    shape[3] = best.gather_bps;
+  }
+  if (ms)
+    for (int k = 0; k < 3; ++k) ms[k] = t[k];
+  return POD_OK;
 }
 
 const char* pod_last_error(const pod_handle* h) { return h ? h->err.c_str() : "null handle"; }
@@ -513,9 +610,17 @@ int pod_handle::plan_batch(const pod_system* sys, Plan& pl) {
   return POD_OK;
 }
 
+int pod_handle::size_class(int N) {
+  int c = 0;
+  while ((2LL << c) <= N) ++c;
+  return c;
+}
+
 int pod_handle::plan(const pod_system* sys, Plan& pl) {
-  if (sys->n_configs > 1) return plan_batch(sys, pl);
-  return plan_single(sys->n_atoms, sys->box, sys->pbc, pl);
+  const int rc_ = sys->n_configs > 1 ? plan_batch(sys, pl) : plan_single(sys->n_atoms, sys->box, sys->pbc, pl);
+  auto it = tuned.find(size_class(sys->n_atoms));
+  pl.shape = it != tuned.end() ? it->second : LaunchShape{};
+  return rc_;
 }
 
 int pod_handle::build_neighbors(const double* pos, Plan& pl, bool need_rev, cudaStream_t st) {
@@ -556,7 +661,7 @@ int pod_handle::build_neighbors(const double* pos, Plan& pl, bool need_rev, cuda
   if (e != cudaSuccess) return cuda_fail(e, "bin kernel");
   e = launch_neigh(N, pl.cg, (const double*)wpos.p, (const float4*)phi.p, (const float4*)plo.p,
                    (const int*)cell_count.p, (const float4*)cell_atoms.p, rlist(), pl.cap, (int*)nbr_count.p,
-                   (int*)nbr_j.p, (int*)nbr_s.p, (int*)status.p, st);
+                   (int*)nbr_j.p, (int*)nbr_s.p, (int*)status.p, st, pl.shape.neigh_wpb);
   if (e != cudaSuccess) return cuda_fail(e, "neighbour kernel");
   }
   if (need_rev) {
@@ -599,6 +704,7 @@ void pod_handle::fill_args(AtomArgs<T>& a, const Plan& pl) {
   a.cbox = pl.batched ? (const CfgBox*)boxes.p : nullptr;
   a.vdir = vdir_cur;
   a.rmask = mask_radius<T>(skin > 0 ? P.r_cut : 0.0);
+  a.wpb = pl.shape.atom_wpb;
 }
 
 // Cubic Hermite pieces of R_k on TAB_N equal intervals of (r_in, r_cut), from
@@ -732,14 +838,14 @@ int pod_handle::energy_forces(const pod_system* sys, const double* c, double* E,
     int* rev_out = keep_rev ? (int*)rev.p : nullptr;
     const size_t gbytes = (precision == POD_MIXED ? sizeof(Q4<float>) : sizeof(Q4<double>)) * (size_t)N * pl.cap;
     if ((rc_ = ensure(g, gbytes, "pair gradients"))) return rc_;
-    const int nwarp = atom_warps(N, K);
+    const int nwarp = atom_warps(N, K, pl.shape.atom_wpb);
     if ((rc_ = ensure(wpart, sizeof(double) * 9 * (size_t)nwarp, "virial partials"))) return rc_;
     double* Ei_dst = Ei_user;
     if (!Ei_dst) {
       if ((rc_ = ensure(Ei, sizeof(double) * (size_t)N, "atom energies"))) return rc_;
       Ei_dst = (double*)Ei.p;
     }
-    const int nblk = gather_blocks(N);
+    const int nblk = gather_blocks(N, pl.shape.gather_wpb, pl.shape.gather_bps);
     if ((rc_ = ensure(Wat, sizeof(double) * 10 * (size_t)nblk, "block partial sums"))) return rc_;
     if (!offs.p) {
       if ((rc_ = ensure(offs, sizeof(unsigned) * 4, "ticket"))) return rc_;
@@ -753,12 +859,13 @@ int pod_handle::energy_forces(const pod_system* sys, const double* c, double* E,
     if (precision == POD_MIXED)
       e = launch_gather_reduce<float>(N, pl.cap, (const int*)nbr_count.p, (const int*)nbr_j.p, (const int*)nbr_s.p,
                                       rev_in, rev_out, (const Q4<float>*)g.p, Ei_dst, (const double*)wpart.p, nwarp,
-                                      F, 1.0, (double*)Wat.p, nblk, (unsigned*)offs.p, E, W, (int*)status.p, st);
+                                      F, 1.0, (double*)Wat.p, nblk, (unsigned*)offs.p, E, W, (int*)status.p, st,
+                                      pl.shape.gather_wpb);
     else
       e = launch_gather_reduce<double>(N, pl.cap, (const int*)nbr_count.p, (const int*)nbr_j.p,
                                        (const int*)nbr_s.p, rev_in, rev_out, (const Q4<double>*)g.p, Ei_dst,
                                        (const double*)wpart.p, nwarp, F, 1.0, (double*)Wat.p, nblk,
-                                       (unsigned*)offs.p, E, W, (int*)status.p, st);
+                                       (unsigned*)offs.p, E, W, (int*)status.p, st, pl.shape.gather_wpb);
     if (e != cudaSuccess) return cuda_fail(e, "gather kernel");
     if (pl.batched) {  // per-configuration energies (the gather wrote the batch total into E[0])
       e = launch_segsum(pl.n_cfg, (const CfgBox*)boxes.p, Ei_dst, 1.0, 0, E, st);

@@ -14,8 +14,11 @@ constexpr int MAXROWS = MAXA * MAXB + MAXG;
 constexpr int PAMAX = 4;   // highest angular degree compiled
 constexpr int MAXM = 1 + MAXK + MAXK * (PAMAX + 1) + MAXK * 11;  // descriptors (11 = four-body K_a at P = 4)
 constexpr int CH = 32;     // pairs per atom staged in shared memory at a time
-constexpr int WPB_ATOM = 2;   // warps per block, atom kernels
-constexpr int WPB_NEIGH = 4;  // warps per block, neighbour kernel
+constexpr int WPB_ATOM = 2;   // warps per block, atom kernels (default launch shape)
+constexpr int WPB_NEIGH = 4;  // warps per block, neighbour kernels (default launch shape)
+constexpr int ATOM_MAX_WPB = 4;   // launch shapes the kernels accept (autotuned per system size)
+constexpr int NEIGH_MAX_WPB = 8;
+constexpr int GATHER_MAX_WPB = 16;
 
 // device status bits (OR-ed into a status word, read by the host)
 constexpr int ST_NEIGH = 1;      // more neighbours than the list capacity

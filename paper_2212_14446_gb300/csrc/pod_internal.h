@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdarg>
+#include <map>
 #include <string>
 #include <vector>
 
@@ -30,6 +31,7 @@ struct Plan {
   int n_cfg = 1;
   double Lmax = 0;
   int Smax = 0;
+  fastpod::LaunchShape shape{};  // launch shape for this system size (autotuned or default)
 };
 
 struct pod_handle {
@@ -47,6 +49,10 @@ struct pod_handle {
   int* h_status = nullptr;        // pinned
   int timing = 0;
   cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  std::map<int, fastpod::LaunchShape> tuned;  // autotuned launch shapes by size class (floor log2 N)
+  static int size_class(int N);
+  int autotune(const pod_system* sys, const double* c, int reps, cudaStream_t st, fastpod::LaunchShape& best,
+               double ms[3]);
   double t_acc[4] = {0, 0, 0, 0};
   int t_calls = 0;
   int mark(int k, cudaStream_t st);

@@ -10,6 +10,14 @@
 namespace fastpod {
 
 // Shared-memory layout of one warp in the atom kernels (byte offsets).
+// Launch shape of the step's kernels (warps per block; gather blocks per SM).
+struct LaunchShape {
+  int atom_wpb = WPB_ATOM;
+  int neigh_wpb = WPB_NEIGH;
+  int gather_wpb = 16;
+  int gather_bps = 3;
+};
+
 struct AtomLayout {
   int A;    // atoms per warp
   int KS;   // row stride of the staged R / R' (odd, >= K)
@@ -22,6 +30,7 @@ struct AtomLayout {
 template <typename T>
 struct AtomArgs {
   int N, cap;
+  int wpb;              // warps per block of the launch (0: default)
   const int* nbr_count;
   const int* nbr_j;
   const int* nbr_s;
@@ -62,7 +71,7 @@ cudaError_t launch_kick(int N3, double* v, const double* F, double half_dt_over_
                         cudaStream_t st);
 cudaError_t launch_neigh(int N, const CellGrid& cg, const double* wpos, const float4* phi, const float4* plo,
                          const int* cell_count, const float4* cell_pos, double rcut, int cap, int* nbr_count,
-                         int* nbr_j, int* nbr_s, int* status, cudaStream_t st);
+                         int* nbr_j, int* nbr_s, int* status, cudaStream_t st, int wpb = WPB_NEIGH);
 cudaError_t launch_rev(int N, int cap, const int* nbr_count, const int* nbr_j, const int* nbr_s, int* rev,
                        int* status, cudaStream_t st);
 cudaError_t launch_export_neighbors(int N, int cap, const int* nbr_count, const int* nbr_j, const int* nbr_s,
@@ -83,10 +92,11 @@ template <typename T>
 cudaError_t launch_gather_reduce(int N, int cap, const int* nbr_count, const int* nbr_j, const int* nbr_s,
                                  const int* rev_in, int* rev_out, const Q4<T>* g, const double* Ei,
                                  const double* wpart, int n_wpart, double* F, double fscale, double* part,
-                                 int nblocks, unsigned* ticket, double* E, double* W, int* status, cudaStream_t st);
-int atom_warps(int N, int K);
+                                 int nblocks, unsigned* ticket, double* E, double* W, int* status, cudaStream_t st,
+                                 int wpb);
+int atom_warps(int N, int K, int wpb);
 cudaError_t launch_colsum(int n_chunks, const int* chunk_rows /*[n_chunks][2]*/, int n_cfg, const int* cfg_chunks,
                           int M, const double* D, double* part, double* G, cudaStream_t st);
-int gather_blocks(int N);
+int gather_blocks(int N, int wpb, int bps);
 
 }  // namespace fastpod
