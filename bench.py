@@ -563,6 +563,13 @@ def run_fit(args, rank, world, local):
         torch.cuda.synchronize()
         ts.append(e0.elapsed_time(e1))
     ms = sum(ts) / len(ts)
+    # per-phase device time of one more fit (library CUDA events)
+    pod.set_timing(True)
+    pod.timing()
+    pod.fit(cfgs, E_ref, F_ref)
+    ph, calls = pod.timing()
+    pod.set_timing(False)
+    phases = {"neighbors": ph[0], "design_matrix": ph[1], "gram": ph[2], "solve": ph[3]} if calls else None
     n_atoms = int(offs[-1])
     rel = float(np.max(np.abs(c - cstar.numpy())) / np.max(np.abs(cstar.numpy())))
     line = {"metric": "configs/s (fit: descriptors + gradients into the design matrix, FP64 normal equations, "
@@ -572,7 +579,7 @@ def run_fit(args, rank, world, local):
             "vs_baseline": None, "dtype": "f32" if args.precision == "mixed" else "f64", "data": "synthetic",
             "config": {"workload": f"training_set_{len(cfgs)}", "atoms": n_atoms, "design_rows": len(cfgs) + 3 * n_atoms,
                        "descriptors": pod.M},
-            "teacher_recovery_max_rel": rel, "mae_E_per_atom": maeE, "mae_F": maeF}
+            "teacher_recovery_max_rel": rel, "mae_E_per_atom": maeE, "mae_F": maeF, "phases_ms": phases}
     if rank == 0:
         print(json.dumps(line))
 

@@ -264,7 +264,7 @@ __global__ void __launch_bounds__(ATOM_MAX_WPB * 32, atom_min_blocks<T, MODE, KT
     for (int x = 0; x < NA; ++x) B[x] = (x & 1) ? B2[x >> 1].y : B2[x >> 1].x;
   }
 
-  if (MODE == 0) {
+  if (MODE == 0 || (MODE == 3 && p.D)) {
     // ---------------- descriptors (Eq. 12b, 26a, 27a, 30a)
     if (am) {
       const int i = atom0 + a_loc;
@@ -284,6 +284,131 @@ __global__ void __launch_bounds__(ATOM_MAX_WPB * 32, atom_min_blocks<T, MODE, KT
 #pragma unroll
         for (int q = 0; q < KA; ++q)
           if (q < p.KA4) Di[p.col4 + m * p.KA4 + q] = (double)D4[q];
+      }
+    }
+    if (MODE == 0) return;
+  }
+
+  if (MODE == 3) {
+    // ---------------- design-matrix pair gradients.  Descriptor q of mode m is
+    // the column col(q, m) of the linear model; its pair gradient
+    // dD_{i,col}/dr_ij is the adjoint pair pass (Eq. 24c) with c = e_col: the
+    // lane (atom, m) forms a = dD_{i,col}/dB_m (one row of the sparse Jacobian of
+    // Eq. 12b, 26a, 27a, 30a), then lanes over pairs contract it with dB_m/dr_ij.
+    T d3v[PA + 1];
+    Mono<PA>::d3(B, d3v);
+    const int n3 = p.P3 + 1;
+    const int Qd = 1 + n3 + p.KA4;
+    for (int q = p.q0; q < p.q1 && q < Qd; ++q) {
+      __syncwarp();
+      if (am) {
+        T a[NAP];
+#pragma unroll
+        for (int x = 0; x < NAP; ++x) a[x] = T(0);
+        if (q == 0) {
+          if (m < p.K2) a[0] = T(1);  // D2 = B_m00
+        } else if (q <= n3) {
+          if (m < p.K3) {  // D3_mn = sum_x mu_x B_x^2 over degree n
+            T h[PA + 1];
+#pragma unroll
+            for (int n = 0; n <= PA; ++n) h[n] = (n == q - 1) ? T(1) : T(0);
+            Mono<PA>::d3_adjoint(B, h, a);
+          }
+        } else if (HAS4) {
+          const int pp = q - 1 - n3;
+          if (m < p.K4 && pp < p.KA4) {
+            int n00 = -1;
+#pragma unroll
+            for (int n = 0; n <= PA; ++n)
+              if (Four<PA>::p_n00(n) == pp) n00 = n;
+            if (n00 >= 0) {  // D4 = B_0 D3_n (Eq. 27a)
+              T h[PA + 1];
+#pragma unroll
+              for (int n = 0; n <= PA; ++n) h[n] = (n == n00) ? B[0] : T(0);
+              Mono<PA>::d3_adjoint(B, h, a);
+#pragma unroll
+              for (int n = 0; n <= PA; ++n)
+                if (n == n00) a[0] += d3v[n];
+            } else {  // general partition (Eq. 30a)
+              T w4[KA];
+#pragma unroll
+              for (int qq = 0; qq < KA; ++qq) w4[qq] = (qq == pp) ? T(1) : T(0);
+              Four<PA>::adjoint(B, w4, a);
+            }
+          }
+        }
+        T* adst = sadj + a_loc * lay.AS + m * NAP;
+#pragma unroll
+        for (int x = 0; x < NAP; ++x) adst[x] = a[x];
+      }
+      __syncwarp();
+      for (int ch = 0; ch < nchunks; ++ch) {
+        if (nchunks > 1) {
+          __syncwarp();
+          pair_pass<T, KT, false>(p, lay, geo, sR, sRp, scnt, atom0, A, K, ch, lane);
+          __syncwarp();
+        }
+        int tot = 0;
+        for (int a = 0; a < A; ++a) tot += chunk_count(scnt[a], ch);
+        for (int f = lane; f < tot; f += 32) {
+          int a = 0, base = 0;
+          for (; a < A; ++a) {
+            const int nca = chunk_count(scnt[a], ch);
+            if (f < base + nca) break;
+            base += nca;
+          }
+          const int jj = f - base, slot = ch * CH + jj, i = atom0 + a;
+          const Q4<T> u = geo[a * lay.GA + jj];
+          T Rv[KT], Rpv[KT];
+          if (p.rad.tab) {
+            if (u.w > p.rad.r_in && u.w < p.rmask) {
+              radial_pair<T, KT>(p.rad, u.w, Rv, Rpv);
+            } else {
+#pragma unroll
+              for (int k = 0; k < KT; ++k) { Rv[k] = T(0); Rpv[k] = T(0); }
+            }
+          } else {
+            const T* Rrow = sR + a * lay.SA + jj * lay.KS;
+            const T* Rprow = sRp + a * lay.SA + jj * lay.KS;
+#pragma unroll
+            for (int k = 0; k < KT; ++k) {
+              if (KT == MAXK && k >= K) break;
+              Rv[k] = Rrow[k];
+              Rpv[k] = Rprow[k];
+            }
+          }
+          T Am[NAP];
+          Mono<PA>::eval(u.x, u.y, u.z, Am);
+#pragma unroll
+          for (int x = NA; x < NAP; ++x) Am[x] = T(0);
+          const T ir = T(1) / u.w;
+          const T* adj = sadj + a * lay.AS;
+          T* out = p.gdm + (((size_t)(q - p.q0) * p.N + i) * p.cap + slot) * (size_t)K * 3;
+#pragma unroll
+          for (int mm = 0; mm < KT; ++mm) {
+            if (KT == MAXK && mm >= K) break;
+            T am_[NAP];
+            const Q4<T>* a4 = reinterpret_cast<const Q4<T>*>(adj + mm * NAP);
+#pragma unroll
+            for (int x4 = 0; x4 < NAP / 4; ++x4) {
+              const Q4<T> av = a4[x4];
+              am_[4 * x4 + 0] = av.x;
+              am_[4 * x4 + 1] = av.y;
+              am_[4 * x4 + 2] = av.z;
+              am_[4 * x4 + 3] = av.w;
+            }
+            T dot = T(0);
+#pragma unroll
+            for (int x = 0; x < NA; ++x) dot = fma(am_[x], Am[x], dot);
+            T gx, gy, gz;
+            Mono<PA>::grad(am_, Am, gx, gy, gz);
+            const T ug = u.x * gx + u.y * gy + u.z * gz;
+            const T s1 = Rpv[mm] * dot, s2 = Rv[mm] * ir;
+            out[3 * mm + 0] = fma(s1, u.x, s2 * (gx - ug * u.x));
+            out[3 * mm + 1] = fma(s1, u.y, s2 * (gy - ug * u.y));
+            out[3 * mm + 2] = fma(s1, u.z, s2 * (gz - ug * u.z));
+          }
+        }
       }
     }
     return;
@@ -572,6 +697,11 @@ cudaError_t launch_atom_t(int mode, const AtomArgs<T>& p, int PA, bool has4, cud
     if (spec6) return launch_one<T, 4, true, 0, 6>(p, lay, st);
     if (spec3) return launch_one<T, 3, false, 0, 3>(p, lay, st);
     return dispatch_generic<T, 0>(p, lay, PA, has4, st);
+  }
+  if (mode == 3) {
+    if (spec6) return launch_one<T, 4, true, 3, 6>(p, lay, st);
+    if (spec3) return launch_one<T, 3, false, 3, 3>(p, lay, st);
+    return dispatch_generic<T, 3>(p, lay, PA, has4, st);
   }
   if (spec6) return launch_one<T, 4, true, 1, 6>(p, lay, st);
   if (spec3) return launch_one<T, 3, false, 1, 3>(p, lay, st);

@@ -4,10 +4,14 @@
 // Eq. 58a), and one row per force component, -w_F dG_m / dr_ka; b holds
 // w_E E_ref / N_c and w_F F_ref.
 //
-// Column m of A is assembled with the energy/force kernels themselves: with the
-// coefficient vector e_m the atom energies are E_i = D_im, their per-configuration
-// sum is G_m, and the "forces" are -dG_m/dr, so the adjoint pair pass and the
-// coalesced gather write column m directly (A is stored column-major, AT[m][row]).
+// A is stored column-major (AT[m][row]).  Energy rows come from the per-atom
+// descriptors summed per configuration.  Force rows come from one fused pass of
+// the atom kernel (mode 3) per group of descriptor indices: it keeps B_i on chip,
+// forms for every descriptor column the row dD_{i,col}/dB of the sparse
+// Jacobian of the contractions and contracts it with dB/dr_ij for every pair
+// (the adjoint pair pass of Eq. 24c with c = e_col), storing the pair
+// gradients; a gather then forms -dG_col/dr_k = sum_t (g[k,t] - g[rev(k,t)]) for
+// every column at once, without atomics.
 // The normal equations (A^T A + gamma I) c = A^T b are formed in FP64 by a
 // blocked SYRK with a fixed-order reduction of per-block partials, then solved
 // by Cholesky on the GPU.
@@ -202,6 +206,65 @@ __global__ void residual_kernel(int M, long long R, long long n_e, const double*
   }
 }
 
+// Column of the linear model for per-mode descriptor index q of radial mode m
+// (q = 0: two-body; 1..P3+1: three-body degree q - 1; then four-body partitions),
+// or -1 where the model has no such descriptor.
+__device__ __forceinline__ int design_column(int q, int m, int K2, int K3, int P3, int K4, int KA4, int col3,
+                                             int col4) {
+  const int n3 = P3 + 1;
+  if (q == 0) return m < K2 ? 1 + m : -1;
+  if (q <= n3) return m < K3 ? col3 + m * n3 + (q - 1) : -1;
+  const int pp = q - 1 - n3;
+  return (m < K4 && pp < KA4) ? col4 + m * KA4 + pp : -1;
+}
+
+// Force rows of the design matrix, warp per atom k: lane v of the Qc x K x 3
+// (descriptor index, mode, component) values adds g[k,t] - g[rev(k,t)] over the
+// atom's slots t in order, then writes w_F times the sum to AT[col][nc + c N + k].
+template <typename T>
+__global__ void __launch_bounds__(256)
+    design_gather_kernel(int N, int cap, int K, int q0, int Qc, const int* __restrict__ nbr_count,
+                         const int* __restrict__ rev, const T* __restrict__ gdm, int K2, int K3, int P3, int K4,
+                         int KA4, int col3, int col4, long long R, int nc, double wF, double* __restrict__ AT,
+                         int* __restrict__ status) {
+  const int lane = threadIdx.x & 31;
+  const int k = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (k >= N) return;
+  const int n = min(nbr_count[k], cap);
+  const int per = Qc * K * 3;
+  const size_t plane = (size_t)N * cap * K * 3;
+  for (int v = lane; v < per; v += 32) {
+    const int ql = v / (K * 3), rem = v - ql * (K * 3);
+    const T* base = gdm + ql * plane + rem;
+    T s = T(0);
+    for (int t = 0; t < n; ++t) {
+      const size_t pidx = (size_t)k * cap + t;
+      const int q = rev[pidx];
+      s += base[pidx * K * 3];
+      if (q >= 0) s -= base[(size_t)q * K * 3];
+      else atomicOr(status, ST_REV);
+    }
+    const int m = rem / 3, comp = rem - 3 * m;
+    const int col = design_column(q0 + ql, m, K2, K3, P3, K4, KA4, col3, col4);
+    if (col >= 0) AT[(size_t)col * R + nc + (size_t)comp * N + k] = wF * (double)s;
+  }
+}
+
+// Energy rows AT[col][c] = w_E G[c][col] (/ N_c), and zero force rows of column 0
+// (the one-body descriptor does not depend on positions).
+__global__ void design_energy_rows_kernel(int n_cfg, int M, long long R, const CfgBox* __restrict__ cbox,
+                                          const double* __restrict__ G, double wE, int per_atom,
+                                          double* __restrict__ AT) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < (long long)n_cfg * M) {
+    const int c = (int)(e / M), col = (int)(e - (long long)c * M);
+    const int n = cbox[c].a1 - cbox[c].a0;
+    AT[(size_t)col * R + c] = wE * G[e] / (per_atom ? (double)n : 1.0);
+  } else if (e < (long long)n_cfg * M + (R - n_cfg)) {
+    AT[n_cfg + (e - (long long)n_cfg * M)] = 0.0;
+  }
+}
+
 // b: energy rows w_E E_ref[c] (/ N_c), force rows w_F F_ref (SoA [3][N]).
 __global__ void fit_rhs_kernel(int n_cfg, int N, const CfgBox* __restrict__ cbox, const double* __restrict__ E_ref,
                                const double* __restrict__ F_ref, double wE, double wF, int per_atom,
@@ -241,6 +304,7 @@ int pod_handle::fit_build(const pod_system* bsys, const double* E_ref, const dou
   this->sync = 1;
   Plan pl;
   retries = 0;
+  if ((rc_ = mark(0, st))) return rc_;  // timing phases: neighbours, design matrix, Gram, solve
   for (;;) {
     if ((rc_ = plan_batch(&sys, pl))) break;
     if ((rc_ = build_neighbors(sys.pos, pl, true, st))) break;
@@ -250,55 +314,64 @@ int pod_handle::fit_build(const pod_system* bsys, const double* E_ref, const dou
   }
   this->sync = keep_sync;
   if (rc_) return rc_;
+  if ((rc_ = mark(1, st))) return rc_;
   const int nc = pl.n_cfg;
   const long long R = (long long)nc + 3LL * N;
-  const size_t gbytes = (precision == POD_MIXED ? sizeof(Q4<float>) : sizeof(Q4<double>)) * (size_t)N * pl.cap;
-  if ((rc_ = ensure(g, gbytes, "pair gradients"))) return rc_;
-  const int nwarp = atom_warps(N, K, pl.shape.atom_wpb);
-  if ((rc_ = ensure(wpart, sizeof(double) * 9 * (size_t)nwarp, "virial partials"))) return rc_;
-  if ((rc_ = ensure(Ei, sizeof(double) * (size_t)N, "atom energies"))) return rc_;
-  const int nblk = gather_blocks(N, pl.shape.gather_wpb, pl.shape.gather_bps);
-  if ((rc_ = ensure(Wat, sizeof(double) * 10 * (size_t)nblk, "block partial sums"))) return rc_;
-  if (!offs.p) {
-    if ((rc_ = ensure(offs, sizeof(unsigned) * 4, "ticket"))) return rc_;
-    cudaError_t e0 = cudaMemset(offs.p, 0, sizeof(unsigned) * 4);
-    if (e0 != cudaSuccess) return cuda_fail(e0, "ticket init");
-  }
   if ((rc_ = ensure(fitA, sizeof(double) * (size_t)M * R, "design matrix"))) return rc_;
   if ((rc_ = ensure(fitb, sizeof(double) * (size_t)R, "right-hand side"))) return rc_;
   const size_t work_bytes = sizeof(double) * ((size_t)M * M + (size_t)M * M + 4 * (size_t)M + 2 * 1024 + 8) + 64;
   if ((rc_ = ensure(fitwork, work_bytes, "fit workspace"))) return rc_;
-  std::vector<double> eye((size_t)M * M, 0.0);
-  for (int m = 0; m < M; ++m) eye[(size_t)m * M + m] = 1.0;
-  double* dI = (double*)fitwork.p;
-  double* dtot = dI + (size_t)M * M * 2 + 2 * (size_t)M + 2 * 1024;
-  cudaError_t e = cudaMemcpy(dI, eye.data(), sizeof(double) * eye.size(), cudaMemcpyHostToDevice);
-  if (e != cudaSuccess) return cuda_fail(e, "identity upload");
   double* AT = (double*)fitA.p;
   double* bvec = (double*)fitb.p;
-  const int* rev_in = (const int*)rev.p;  // the batch's reverse index, built once above
-  for (int m = 0; m < M; ++m) {
-    if ((rc_ = run_atoms(1, pl, nullptr, dI + (size_t)m * M, (double*)Ei.p, st))) return rc_;
-    double* col = AT + (size_t)m * R;
+  // descriptors of every atom (energy rows) and the pair gradients of every
+  // column (force rows), in groups of descriptor indices q bounded by memory
+  const int n3 = P.P3 + 1;
+  const int Qd = 1 + n3 + KA4;
+  const size_t esz = precision == POD_MIXED ? sizeof(float) : sizeof(double);
+  const size_t per_q = esz * (size_t)N * pl.cap * K * 3;
+  const size_t budget = (size_t)4 << 30;
+  const int qchunk = (int)std::max<size_t>(1, std::min<size_t>((size_t)Qd, budget / std::max<size_t>(per_q, 1)));
+  if ((rc_ = ensure(gdm, per_q * qchunk, "design-matrix pair gradients"))) return rc_;
+  if ((rc_ = ensure(Dws, sizeof(double) * (size_t)N * M, "descriptor workspace"))) return rc_;
+  if ((rc_ = ensure(dmG, sizeof(double) * (size_t)nc * M, "configuration descriptor sums"))) return rc_;
+  int nch = 0, nrows2 = 0;
+  if ((rc_ = colsum_table(pl, nch, nrows2))) return rc_;
+  cudaError_t e;
+  const int* rev_in = (const int*)rev.p;  // the batch's reverse index, built with the list above
+  const int col3 = 1 + P.K2, col4 = col3 + P.K3 * n3;
+  for (int q0 = 0; q0 < Qd; q0 += qchunk) {
+    dm_q0 = q0;
+    dm_q1 = std::min(Qd, q0 + qchunk);
+    rc_ = run_atoms(3, pl, q0 == 0 ? (double*)Dws.p : nullptr, nullptr, nullptr, st);
+    if (rc_) return rc_;
+    const int wpb = 8;
+    const unsigned blocks = (unsigned)((N + wpb - 1) / wpb);
     if (precision == POD_MIXED)
-      e = launch_gather_reduce<float>(N, pl.cap, (const int*)nbr_count.p, (const int*)nbr_j.p, (const int*)nbr_s.p,
-                                      rev_in, nullptr, (const Q4<float>*)g.p, (const double*)Ei.p,
-                                      (const double*)wpart.p, nwarp, col + nc, o.w_F, (double*)Wat.p, nblk,
-                                      (unsigned*)offs.p, dtot, nullptr, (int*)status.p, st, pl.shape.gather_wpb);
+      design_gather_kernel<float><<<blocks, wpb * 32, 0, st>>>(
+          N, pl.cap, K, q0, dm_q1 - q0, (const int*)nbr_count.p, rev_in, (const float*)gdm.p, P.K2, P.K3, P.P3,
+          P.K4, KA4, col3, col4, R, nc, o.w_F, AT, (int*)status.p);
     else
-      e = launch_gather_reduce<double>(N, pl.cap, (const int*)nbr_count.p, (const int*)nbr_j.p,
-                                       (const int*)nbr_s.p, rev_in, nullptr, (const Q4<double>*)g.p,
-                                       (const double*)Ei.p, (const double*)wpart.p, nwarp, col + nc, o.w_F,
-                                       (double*)Wat.p, nblk, (unsigned*)offs.p, dtot, nullptr, (int*)status.p, st,
-                                       pl.shape.gather_wpb);
-    if (e != cudaSuccess) return cuda_fail(e, "design-matrix force rows");
-    e = launch_segsum(nc, (const CfgBox*)boxes.p, (const double*)Ei.p, o.w_E, o.per_atom_energy, col, st);
-    if (e != cudaSuccess) return cuda_fail(e, "design-matrix energy rows");
+      design_gather_kernel<double><<<blocks, wpb * 32, 0, st>>>(
+          N, pl.cap, K, q0, dm_q1 - q0, (const int*)nbr_count.p, rev_in, (const double*)gdm.p, P.K2, P.K3, P.P3,
+          P.K4, KA4, col3, col4, R, nc, o.w_F, AT, (int*)status.p);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "design-matrix force rows");
+  }
+  dm_q0 = dm_q1 = 0;
+  e = launch_colsum(nch, (const int*)chunks.p, nc, (const int*)chunks.p + nrows2, M, (const double*)Dws.p,
+                    (double*)cpart.p, (double*)dmG.p, st);
+  if (e != cudaSuccess) return cuda_fail(e, "configuration descriptor sums");
+  {
+    const long long tot = (long long)nc * M + (R - nc);
+    const int tb = 256;
+    design_energy_rows_kernel<<<(unsigned)((tot + tb - 1) / tb), tb, 0, st>>>(
+        nc, M, R, (const CfgBox*)boxes.p, (const double*)dmG.p, o.w_E, o.per_atom_energy, AT);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "design-matrix energy rows");
   }
   const int tb = 256;
   fit_rhs_kernel<<<(unsigned)((R + tb - 1) / tb), tb, 0, st>>>(nc, N, (const CfgBox*)boxes.p, E_ref, F_ref, o.w_E,
                                                                o.w_F, o.per_atom_energy, bvec);
   if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "rhs kernel");
+  if ((rc_ = mark(2, st))) return rc_;
   fit_R = R;
   fit_nc = nc;
   fit_N = N;
@@ -379,7 +452,10 @@ int pod_handle::fit(const pod_system* bsys, const double* E_ref, const double* F
   int rc_;
   if ((rc_ = fit_build(bsys, E_ref, F_ref, o))) return rc_;
   if ((rc_ = fit_gram(o.gamma_reg))) return rc_;
+  if ((rc_ = mark(3, nullptr))) return rc_;
   if ((rc_ = fit_solve_dev())) return rc_;
+  if ((rc_ = mark(4, nullptr))) return rc_;
+  if ((rc_ = timing_collect())) return rc_;
   double se = 0, sf = 0;
   if ((rc_ = fit_residual_dev(&se, &sf))) return rc_;
   double* dc = (double*)fitwork.p + 2 * (size_t)M * M + M;

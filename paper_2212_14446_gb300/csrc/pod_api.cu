@@ -330,7 +330,7 @@ int pod_handle::autotune(const pod_system* sys, const double* c, int reps, cudaS
 std::vector<DevBuf*> pod_handle::all_bufs() {
   return {&cell_count, &cell_atoms, &wpos, &phi, &plo, &nbr_count, &nbr_j, &nbr_s, &rev, &g, &Ei,
           &Wat, &status, &offs, &pos_in, &c_in, &E_out, &F_out, &W_out, &Ei_out, &fitA, &fitG, &fitb,
-          &fitwork, &cfg_of, &boxes, &rtab, &wpart, &Dws, &chunks, &cpart, &wrapk};
+          &fitwork, &cfg_of, &boxes, &rtab, &wpart, &Dws, &chunks, &cpart, &wrapk, &gdm, &dmG};
 }
 
 // ============================================================ C ABI
@@ -768,6 +768,9 @@ int pod_handle::run_atoms(int mode, const Plan& pl, double* D, const double* c, 
     a.Ei = Ei_dst;
     a.g = (Q4<float>*)g.p;
     a.wpart = (double*)wpart.p;
+    a.gdm = (float*)gdm.p;
+    a.q0 = dm_q0;
+    a.q1 = dm_q1;
     e = launch_atom_f32(mode, a, PA, has4, st);
   } else {
     AtomArgs<double> a;
@@ -778,6 +781,9 @@ int pod_handle::run_atoms(int mode, const Plan& pl, double* D, const double* c, 
     a.Ei = Ei_dst;
     a.g = (Q4<double>*)g.p;
     a.wpart = (double*)wpart.p;
+    a.gdm = (double*)gdm.p;
+    a.q0 = dm_q0;
+    a.q1 = dm_q1;
     e = launch_atom_f64(mode, a, PA, has4, st);
   }
   if (e != cudaSuccess) return cuda_fail(e, "atom kernel");
@@ -945,6 +951,33 @@ int pod_handle::neighbors(const pod_system* sys, int cap_out, int* count, int* n
 
 // Global descriptors G_m = sum_i D_im per configuration (Eq. 58a), or with vdir
 // their directional derivative sum_k dG_m/dr_k . v_k (tangent mode).
+// Chunk table of the per-configuration column sums: <= 256 rows per chunk,
+// chunks never cross a configuration (rows: [nch][2], then configuration chunk
+// offsets [n_cfg + 1]; nrows2 = 2 nch).
+int pod_handle::colsum_table(const Plan& pl, int& nch, int& nrows2) {
+  std::vector<int> rows, cfgc;
+  const int ncfg = pl.batched ? pl.n_cfg : 1;
+  cfgc.push_back(0);
+  for (int c = 0; c < ncfg; ++c) {
+    const int a0 = pl.batched ? h_cbox[c].a0 : 0, a1 = pl.batched ? h_cbox[c].a1 : pl.N;
+    for (int r = a0; r < a1; r += 256) {
+      rows.push_back(r);
+      rows.push_back(std::min(a1, r + 256));
+    }
+    cfgc.push_back((int)rows.size() / 2);
+  }
+  nch = (int)rows.size() / 2;
+  nrows2 = (int)rows.size();
+  int rc_;
+  if ((rc_ = ensure(chunks, sizeof(int) * (rows.size() + cfgc.size()), "chunk table"))) return rc_;
+  if ((rc_ = ensure(cpart, sizeof(double) * (size_t)std::max(nch, 1) * M, "column partials"))) return rc_;
+  cudaError_t e = cudaMemcpy(chunks.p, rows.data(), sizeof(int) * rows.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy((int*)chunks.p + rows.size(), cfgc.data(), sizeof(int) * cfgc.size(), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return cuda_fail(e, "chunk table upload");
+  return POD_OK;
+}
+
 int pod_handle::global_desc(const pod_system* sys, const double* vdir, double* Gout, cudaStream_t st) {
   int rc_ = validate_system(sys);
   if (rc_) return rc_;
@@ -956,31 +989,15 @@ int pod_handle::global_desc(const pod_system* sys, const double* vdir, double* G
     if ((rc_ = plan(sys, pl))) return rc_;
     if ((rc_ = build_neighbors(sys->pos, pl, false, st))) return rc_;
     if ((rc_ = ensure(Dws, sizeof(double) * (size_t)N * M, "descriptor workspace"))) return rc_;
-    // chunk table: <= 256 rows per chunk, chunks never cross a configuration
-    std::vector<int> rows, cfgc;
-    const int ncfg = pl.batched ? pl.n_cfg : 1;
-    cfgc.push_back(0);
-    for (int c = 0; c < ncfg; ++c) {
-      const int a0 = pl.batched ? h_cbox[c].a0 : 0, a1 = pl.batched ? h_cbox[c].a1 : N;
-      for (int r = a0; r < a1; r += 256) {
-        rows.push_back(r);
-        rows.push_back(std::min(a1, r + 256));
-      }
-      cfgc.push_back((int)rows.size() / 2);
-    }
-    const int nch = (int)rows.size() / 2;
-    if ((rc_ = ensure(chunks, sizeof(int) * (rows.size() + cfgc.size()), "chunk table"))) return rc_;
-    if ((rc_ = ensure(cpart, sizeof(double) * (size_t)std::max(nch, 1) * M, "column partials"))) return rc_;
-    cudaError_t e = cudaMemcpy(chunks.p, rows.data(), sizeof(int) * rows.size(), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess)
-      e = cudaMemcpy((int*)chunks.p + rows.size(), cfgc.data(), sizeof(int) * cfgc.size(), cudaMemcpyHostToDevice);
-    if (e != cudaSuccess) return cuda_fail(e, "chunk table upload");
+    int nch = 0, nrows2 = 0;
+    if ((rc_ = colsum_table(pl, nch, nrows2))) return rc_;
     vdir_cur = vdir;
     rc_ = run_atoms(vdir ? 2 : 0, pl, (double*)Dws.p, nullptr, nullptr, st);
     vdir_cur = nullptr;
     if (rc_) return rc_;
-    e = launch_colsum(nch, (const int*)chunks.p, ncfg, (const int*)chunks.p + rows.size(), M, (const double*)Dws.p,
-                      (double*)cpart.p, Gout, st);
+    const int ncfg = pl.batched ? pl.n_cfg : 1;
+    cudaError_t e = launch_colsum(nch, (const int*)chunks.p, ncfg, (const int*)chunks.p + nrows2, M,
+                                  (const double*)Dws.p, (double*)cpart.p, Gout, st);
     if (e != cudaSuccess) return cuda_fail(e, "column sums");
     bool retry;
     if ((rc_ = finish(st, pl, retry))) return rc_;

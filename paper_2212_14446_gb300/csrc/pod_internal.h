@@ -93,6 +93,9 @@ struct pod_handle {
   int global_desc(const pod_system* sys, const double* vdir, double* G, cudaStream_t st);
   const double* vdir_cur = nullptr;
   DevBuf Dws, chunks, cpart;
+  DevBuf gdm, dmG;  // fit: design-matrix pair gradients, per-configuration descriptor sums
+  int dm_q0 = 0, dm_q1 = 0;  // fit: descriptor-index range of the current design pass
+  int colsum_table(const Plan& pl, int& nch, int& nrows2);
   int fit_build(const pod_system* batch, const double* E_ref, const double* F_ref, const pod_fit_opts& o);
   int fit_gram(double gamma);
   int fit_solve_dev();

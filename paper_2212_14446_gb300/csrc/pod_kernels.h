@@ -46,6 +46,8 @@ struct AtomArgs {
   Q4<T>* g;             // mode 1: dE_i/dr_ij per pair slot [N * cap]
   double* wpart;        // mode 1: per-warp virial partials [warps][9]
   const double* vdir;   // mode 2: displacement direction per atom [3][N] (tangent of D written to D)
+  T* gdm;               // mode 3: design-matrix pair gradients [q - q0][N * cap][K][3]
+  int q0, q1;           // mode 3: range of per-mode descriptor indices q (0: 2-body, 1..P3+1: 3-body, then 4-body)
   T rmask;              // pairs with r >= rmask contribute nothing (lists built with a skin; +inf: none)
   const int* cfg_of;    // batch: configuration of each atom (NULL: one configuration, box L)
   const CfgBox* cbox;   // batch: per-configuration boxes
