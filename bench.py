@@ -550,23 +550,32 @@ def run_fit(args, rank, world, local):
     Fall = out["F"].cpu().numpy()
     offs = out["offs"]
     F_ref = [Fall[offs[k]:offs[k + 1]] for k in range(len(cfgs))]
+    # the batch resident on the device (packed once, outside the timed region)
+    pos, boffs, boxes, pbcs = pod.pack_batch(cfgs)
+    x = torch.tensor(pos, dtype=torch.float64, device="cuda")
+    Er = torch.tensor(np.asarray(E_ref, dtype=np.float64), device="cuda")
+    Fr = torch.tensor(np.ascontiguousarray(np.concatenate(F_ref, axis=0).T), dtype=torch.float64, device="cuda")
     for _ in range(max(1, args.warmup)):
-        pod.fit(cfgs, E_ref, F_ref)
+        pod.fit_device(x, boffs, boxes, pbcs, Er, Fr)
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     ts = []
     for _ in range(args.steps):
         torch.cuda.synchronize()
         e0.record()
-        c, maeE, maeF = pod.fit(cfgs, E_ref, F_ref)
+        c, maeE, maeF = pod.fit_device(x, boffs, boxes, pbcs, Er, Fr)
         e1.record()
         torch.cuda.synchronize()
         ts.append(e0.elapsed_time(e1))
     ms = sum(ts) / len(ts)
+    # end to end: host configurations in, coefficients out (packing and copies timed)
+    te0 = time.perf_counter()
+    pod.fit(cfgs, E_ref, F_ref)
+    te = time.perf_counter() - te0
     # per-phase device time of one more fit (library CUDA events)
     pod.set_timing(True)
     pod.timing()
-    pod.fit(cfgs, E_ref, F_ref)
+    pod.fit_device(x, boffs, boxes, pbcs, Er, Fr)
     ph, calls = pod.timing()
     pod.set_timing(False)
     phases = {"neighbors": ph[0], "design_matrix": ph[1], "gram": ph[2], "solve": ph[3]} if calls else None
@@ -579,7 +588,11 @@ def run_fit(args, rank, world, local):
             "vs_baseline": None, "dtype": "f32" if args.precision == "mixed" else "f64", "data": "synthetic",
             "config": {"workload": f"training_set_{len(cfgs)}", "atoms": n_atoms, "design_rows": len(cfgs) + 3 * n_atoms,
                        "descriptors": pod.M},
-            "teacher_recovery_max_rel": rel, "mae_E_per_atom": maeE, "mae_F": maeF, "phases_ms": phases}
+            "teacher_recovery_max_rel": rel, "mae_E_per_atom": maeE, "mae_F": maeF, "phases_ms": phases,
+            "e2e": {"value": len(cfgs) / te, "unit": "configs/s",
+                    "h2d_bytes_per_step": int(pos.nbytes + Er.numel() * 8 + Fr.numel() * 8),
+                    "d2h_bytes_per_step": int(pod.M * 8 + 16)},
+            "gpu_launches": None}
     if rank == 0:
         print(json.dumps(line))
 

@@ -453,6 +453,18 @@ class POD:
                                      c.ctypes.data_as(C.POINTER(C.c_double)), C.byref(mE), C.byref(mF)))
         return c, mE.value, mF.value
 
+    def fit_device(self, pos_soa, offs, boxes, pbcs, E_ref, F_ref, w_E=100.0, w_F=1.0, gamma=1e-12,
+                   per_atom_energy=True):
+        """pod_fit on a batch already on the device (pos_soa (3, N), E_ref (n_cfg,), F_ref (3, N)
+        CUDA float64 tensors; offs/boxes/pbcs host arrays from pack_batch)."""
+        o = pod_fit_opts(float(w_E), float(w_F), float(gamma), 1 if per_atom_energy else 0)
+        c = np.zeros(self.M)
+        mE, mF = C.c_double(), C.c_double()
+        sysb = self.batch_system(pos_soa, offs, boxes, pbcs)
+        _check(self.h, lib().pod_fit(self.h, C.byref(sysb), _dptr(E_ref), _dptr(F_ref), C.byref(o),
+                                     c.ctypes.data_as(C.POINTER(C.c_double)), C.byref(mE), C.byref(mF)))
+        return c, mE.value, mF.value
+
     def fit_normal(self, configs, E_ref, F_ref, w_E=100.0, w_F=1.0, gamma=1e-12, per_atom_energy=True):
         """Normal equations (G = A^T A + gamma I, r = A^T b) of this batch; A stays
         on the device for fit_residual."""

@@ -49,7 +49,23 @@ __global__ void __launch_bounds__(WPB_NEIGH * 32)
   const CfgBox b = cbox[cfg_of[i]];
   const float4 hi = phi[i];
   const float Lh[3] = {(float)b.L[0], (float)b.L[1], (float)b.L[2]};
-  const int wx = 2 * b.S[0] + 1, wy = 2 * b.S[1] + 1, wz = 2 * b.S[2] + 1;
+  // images whose box comes within r_cut of this atom (a conservative superset:
+  // the margin covers the FP32 position and the band; the exact test decides)
+  int smin[3], smax[3];
+  {
+    const float rcm = sqrtf(rc2_hi) * 1.0001f + 1e-4f;
+    const float xi[3] = {hi.x, hi.y, hi.z};
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      if (b.S[d] == 0) {
+        smin[d] = smax[d] = 0;
+      } else {
+        smin[d] = max(-b.S[d], (int)floorf((xi[d] - rcm) / Lh[d]));
+        smax[d] = min(b.S[d], (int)floorf((xi[d] + rcm) / Lh[d]));
+      }
+    }
+  }
+  const int wx = smax[0] - smin[0] + 1, wy = smax[1] - smin[1] + 1, wz = smax[2] - smin[2] + 1;
   const int nimg = wx * wy * wz;
   const int nat = b.a1 - b.a0;
   const long long total = (long long)nimg * nat;
@@ -62,7 +78,7 @@ __global__ void __launch_bounds__(WPB_NEIGH * 32)
     if (f < total) {
       const int img = (int)(f / nat);
       const int j = b.a0 + (int)(f - (long long)img * nat);
-      const int sx = img % wx - b.S[0], sy = (img / wx) % wy - b.S[1], sz = img / (wx * wy) - b.S[2];
+      const int sx = img % wx + smin[0], sy = (img / wx) % wy + smin[1], sz = img / (wx * wy) + smin[2];
       const int code = shift_pack(sx, sy, sz);
       if (!(j == i && code == zero)) {
         const float4 hj = phi[j];
