@@ -329,7 +329,11 @@ int pod_handle::fit_build(const pod_system* bsys, const double* E_ref, const dou
   const int Qd = 1 + n3 + KA4;
   const size_t esz = precision == POD_MIXED ? sizeof(float) : sizeof(double);
   const size_t per_q = esz * (size_t)N * pl.cap * K * 3;
-  const size_t budget = (size_t)4 << 30;
+  // all descriptor indices in one pass when memory allows (every pass re-forms
+  // B): half of the free device memory, at most 32 GB
+  size_t free_b = 0, total_b = 0;
+  if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) free_b = (size_t)8 << 30;
+  const size_t budget = std::max<size_t>((size_t)256 << 20, std::min<size_t>((size_t)32 << 30, free_b / 2));
   const int qchunk = (int)std::max<size_t>(1, std::min<size_t>((size_t)Qd, budget / std::max<size_t>(per_q, 1)));
   if ((rc_ = ensure(gdm, per_q * qchunk, "design-matrix pair gradients"))) return rc_;
   if ((rc_ = ensure(Dws, sizeof(double) * (size_t)N * M, "descriptor workspace"))) return rc_;
@@ -384,7 +388,9 @@ int pod_handle::fit_build(const pod_system* bsys, const double* E_ref, const dou
 int pod_handle::fit_gram(double gamma) {
   const int Mp = (M + 3) / 4 * 4;
   const long long R = fit_R;
-  const size_t gram_blocks = (size_t)std::max<long long>(1, std::min<long long>(2 * 152, (R + 4095) / 4096));
+  // two blocks on every SM (the kernel is FP64-pipe bound: an SM holding more
+  // blocks than another sets the time), at least 256 rows per block
+  const size_t gram_blocks = (size_t)std::max<long long>(1, std::min<long long>(2 * 152, (R + 255) / 256));
   const size_t part_bytes = sizeof(double) * gram_blocks * ((size_t)Mp * Mp + Mp);
   int rc_;
   if ((rc_ = ensure(fitG, part_bytes, "Gram partials"))) return rc_;
