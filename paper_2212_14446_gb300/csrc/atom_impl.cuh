@@ -579,7 +579,25 @@ __global__ void __launch_bounds__(ATOM_MAX_WPB * 32, atom_min_blocks<T, MODE, KT
       out.z = fma(ps, u.z, (gz - ug * u.z) * ir);
       out.w = T(0);
       const size_t pidx = (size_t)i * p.cap + slot;
-      p.g[pidx] = out;
+      if constexpr (std::is_same<T, float>::value) {
+        // F_i += g_ij, F_j -= g_ij as fixed-point integers (order-independent sums)
+        const int j = p.nbr_j[pidx];
+        if (!(fabsf(out.x) < FIX_GMAX && fabsf(out.y) < FIX_GMAX && fabsf(out.z) < FIX_GMAX)) {
+          atomicOr(p.status, isfinite(out.x) && isfinite(out.y) && isfinite(out.z) ? ST_RANGE : ST_NONFINITE);
+        } else {
+          const long long fx = __float2ll_rn(out.x * FIX_SCALE_F);
+          const long long fy = __float2ll_rn(out.y * FIX_SCALE_F);
+          const long long fz = __float2ll_rn(out.z * FIX_SCALE_F);
+          atomicAdd(p.facc + 4 * (size_t)i + 0, (unsigned long long)fx);
+          atomicAdd(p.facc + 4 * (size_t)i + 1, (unsigned long long)fy);
+          atomicAdd(p.facc + 4 * (size_t)i + 2, (unsigned long long)fz);
+          atomicAdd(p.facc + 4 * (size_t)j + 0, (unsigned long long)(-fx));
+          atomicAdd(p.facc + 4 * (size_t)j + 1, (unsigned long long)(-fy));
+          atomicAdd(p.facc + 4 * (size_t)j + 2, (unsigned long long)(-fz));
+        }
+      } else {
+        p.g[pidx] = out;
+      }
       // pair virial  W -= r_ij (x) g_ij
       const T dx = u.x * u.w, dy = u.y * u.w, dz = u.z * u.w;
       wv[0] -= dx * out.x; wv[1] -= dx * out.y; wv[2] -= dx * out.z;

@@ -8,9 +8,15 @@ namespace fastpod {
 
 __global__ void batch_wrap_kernel(int N, const double* __restrict__ pos, const int* __restrict__ cfg_of,
                                   const CfgBox* __restrict__ cbox, double* __restrict__ wpos,
-                                  float4* __restrict__ phi, float4* __restrict__ plo, int* __restrict__ status) {
+                                  float4* __restrict__ phi, float4* __restrict__ plo, int* __restrict__ status,
+                                  unsigned long long* __restrict__ facc) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
+  if (facc) {  // fixed-point force accumulators of this call start at zero
+    ulonglong2* fz = reinterpret_cast<ulonglong2*>(facc + 4 * (size_t)i);
+    fz[0] = make_ulonglong2(0ull, 0ull);
+    fz[1] = make_ulonglong2(0ull, 0ull);
+  }
   const CfgBox& b = cbox[cfg_of[i]];
   double x[3];
   bool finite = true;
@@ -194,9 +200,9 @@ cudaError_t launch_colsum(int n_chunks, const int* chunk_rows, int n_cfg, const 
 }
 
 cudaError_t launch_batch_wrap(int N, const double* pos, const int* cfg_of, const CfgBox* cbox, double* wpos,
-                              float4* phi, float4* plo, int* status, cudaStream_t st) {
+                              float4* phi, float4* plo, int* status, cudaStream_t st, unsigned long long* facc) {
   const int tb = 256;
-  batch_wrap_kernel<<<(N + tb - 1) / tb, tb, 0, st>>>(N, pos, cfg_of, cbox, wpos, phi, plo, status);
+  batch_wrap_kernel<<<(N + tb - 1) / tb, tb, 0, st>>>(N, pos, cfg_of, cbox, wpos, phi, plo, status, facc);
   return cudaGetLastError();
 }
 

@@ -15,9 +15,15 @@ namespace fastpod {
 // part, only runs for atoms outside the box.
 __global__ void bin_kernel(int N, const double* __restrict__ pos, CellGrid cg, double* __restrict__ wpos,
                            float4* __restrict__ phi, float4* __restrict__ plo, int* __restrict__ cell_count,
-                           float4* __restrict__ cell_pos, int* __restrict__ wrapk, int* __restrict__ status) {
+                           float4* __restrict__ cell_pos, int* __restrict__ wrapk, int* __restrict__ status,
+                           unsigned long long* __restrict__ facc) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
+  if (facc) {  // fixed-point force accumulators of this call start at zero
+    ulonglong2* fz = reinterpret_cast<ulonglong2*>(facc + 4 * (size_t)i);
+    fz[0] = make_ulonglong2(0ull, 0ull);
+    fz[1] = make_ulonglong2(0ull, 0ull);
+  }
   double x[3];
   int c[3];
   bool finite = true;
@@ -260,9 +266,11 @@ __global__ void export_neighbors_kernel(int N, int cap, const int* __restrict__ 
 
 // ------------------------------------------------------------ launchers
 cudaError_t launch_bin(int N, const double* pos, const CellGrid& cg, double* wpos, float4* phi, float4* plo,
-                       int* cell_count, float4* cell_pos, int* status, cudaStream_t st, int* wrapk) {
+                       int* cell_count, float4* cell_pos, int* status, cudaStream_t st, int* wrapk,
+                       unsigned long long* facc) {
   const int tb = 64;  // small blocks spread the FP64 work of small systems over all SMs
-  bin_kernel<<<(N + tb - 1) / tb, tb, 0, st>>>(N, pos, cg, wpos, phi, plo, cell_count, cell_pos, wrapk, status);
+  bin_kernel<<<(N + tb - 1) / tb, tb, 0, st>>>(N, pos, cg, wpos, phi, plo, cell_count, cell_pos, wrapk, status,
+                                               facc);
   return cudaGetLastError();
 }
 
@@ -272,9 +280,15 @@ cudaError_t launch_bin(int N, const double* pos, const CellGrid& cg, double* wpo
 // the stored shifts.
 __global__ void rewrap_kernel(int N, const double* __restrict__ pos, const int* __restrict__ wrapk, double L0, double L1,
                               double L2, double* __restrict__ wpos, float4* __restrict__ phi,
-                              float4* __restrict__ plo, int* __restrict__ status) {
+                              float4* __restrict__ plo, int* __restrict__ status,
+                              unsigned long long* __restrict__ facc) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
+  if (facc) {  // fixed-point force accumulators of this call start at zero
+    ulonglong2* fz = reinterpret_cast<ulonglong2*>(facc + 4 * (size_t)i);
+    fz[0] = make_ulonglong2(0ull, 0ull);
+    fz[1] = make_ulonglong2(0ull, 0ull);
+  }
   const double L[3] = {L0, L1, L2};
   double x[3];
   bool finite = true;
@@ -299,9 +313,9 @@ __global__ void rewrap_kernel(int N, const double* __restrict__ pos, const int* 
 }
 
 cudaError_t launch_rewrap(int N, const double* pos, const int* wrapk, const double L[3], double* wpos, float4* phi,
-                          float4* plo, int* status, cudaStream_t st) {
+                          float4* plo, int* status, cudaStream_t st, unsigned long long* facc) {
   const int tb = 256;
-  rewrap_kernel<<<(N + tb - 1) / tb, tb, 0, st>>>(N, pos, wrapk, L[0], L[1], L[2], wpos, phi, plo, status);
+  rewrap_kernel<<<(N + tb - 1) / tb, tb, 0, st>>>(N, pos, wrapk, L[0], L[1], L[2], wpos, phi, plo, status, facc);
   return cudaGetLastError();
 }
 

@@ -298,7 +298,8 @@ int pod_handle::autotune(const pod_system* sys, const double* c, int reps, cudaS
     if ((rc_ = measure(s, t))) break;
     if (t[0] < best_neigh) { best_neigh = t[0]; win.neigh_wpb = neigh_c[n]; }
   }
-  for (int g = 0; !rc_ && g < 5; ++g) {
+  // the FP32 path sums forces in the atom kernel (fixed point) and has no gather
+  for (int g = 0; !rc_ && precision != POD_MIXED && g < 5; ++g) {
     LaunchShape s = win;
     s.gather_wpb = gather_c[g][0];
     s.gather_bps = gather_c[g][1];
@@ -323,14 +324,14 @@ int pod_handle::autotune(const pod_system* sys, const double* c, int reps, cudaS
   best = win;
   ms[0] = best_neigh;
   ms[1] = best_atom;
-  ms[2] = best_gather;
+  ms[2] = best_gather < 1e29 ? best_gather : t[2];
   return POD_OK;
 }
 
 std::vector<DevBuf*> pod_handle::all_bufs() {
   return {&cell_count, &cell_atoms, &wpos, &phi, &plo, &nbr_count, &nbr_j, &nbr_s, &rev, &g, &Ei,
           &Wat, &status, &offs, &pos_in, &c_in, &E_out, &F_out, &W_out, &Ei_out, &fitA, &fitG, &fitb,
-          &fitwork, &cfg_of, &boxes, &rtab, &wpart, &Dws, &chunks, &cpart, &wrapk, &gdm, &dmG};
+          &fitwork, &cfg_of, &boxes, &rtab, &wpart, &Dws, &chunks, &cpart, &wrapk, &gdm, &dmG, &facc};
 }
 
 // ============================================================ C ABI
@@ -623,7 +624,8 @@ int pod_handle::plan(const pod_system* sys, Plan& pl) {
   return rc_;
 }
 
-int pod_handle::build_neighbors(const double* pos, Plan& pl, bool need_rev, cudaStream_t st) {
+int pod_handle::build_neighbors(const double* pos, Plan& pl, bool need_rev, cudaStream_t st,
+                                unsigned long long* facc_zero) {
   const int N = pl.N;
   int rc_;
   reuse_ok = false;
@@ -646,7 +648,7 @@ int pod_handle::build_neighbors(const double* pos, Plan& pl, bool need_rev, cuda
   cudaError_t e;
   if (pl.batched) {
     e = launch_batch_wrap(N, pos, (const int*)cfg_of.p, (const CfgBox*)boxes.p, (double*)wpos.p, (float4*)phi.p,
-                          (float4*)plo.p, (int*)status.p, st);
+                          (float4*)plo.p, (int*)status.p, st, facc_zero);
     if (e != cudaSuccess) return cuda_fail(e, "batch wrap kernel");
     e = launch_batch_neigh(N, (const int*)cfg_of.p, (const CfgBox*)boxes.p, (const double*)wpos.p,
                            (const float4*)phi.p, rlist(), pl.Lmax, pl.Smax, pl.cap, (int*)nbr_count.p,
@@ -657,7 +659,7 @@ int pod_handle::build_neighbors(const double* pos, Plan& pl, bool need_rev, cuda
   if (e != cudaSuccess) return cuda_fail(e, "cell count clear");
   if ((rc_ = ensure(wrapk, sizeof(int) * 3 * (size_t)N, "wrap offsets"))) return rc_;
   e = launch_bin(N, pos, pl.cg, (double*)wpos.p, (float4*)phi.p, (float4*)plo.p, (int*)cell_count.p,
-                 (float4*)cell_atoms.p, (int*)status.p, st, (int*)wrapk.p);
+                 (float4*)cell_atoms.p, (int*)status.p, st, (int*)wrapk.p, facc_zero);
   if (e != cudaSuccess) return cuda_fail(e, "bin kernel");
   e = launch_neigh(N, pl.cg, (const double*)wpos.p, (const float4*)phi.p, (const float4*)plo.p,
                    (const int*)cell_count.p, (const float4*)cell_atoms.p, rlist(), pl.cap, (int*)nbr_count.p,
@@ -766,7 +768,8 @@ int pod_handle::run_atoms(int mode, const Plan& pl, double* D, const double* c, 
     a.D = D;
     a.c = c;
     a.Ei = Ei_dst;
-    a.g = (Q4<float>*)g.p;
+    a.g = nullptr;
+    a.facc = (unsigned long long*)facc.p;
     a.wpart = (double*)wpart.p;
     a.gdm = (float*)gdm.p;
     a.q0 = dm_q0;
@@ -828,22 +831,26 @@ int pod_handle::energy_forces(const pod_system* sys, const double* c, double* E,
     if ((rc_ = mark(0, st))) return rc_;
     const bool reuse = nbr_mode == 1 && reuse_ok && !pl.batched && last_pl.N == N && last_pl.cg.L[0] == pl.cg.L[0] &&
                        last_pl.cg.L[1] == pl.cg.L[1] && last_pl.cg.L[2] == pl.cg.L[2];
+    // FP32 path: forces accumulate in fixed point, zeroed by this call's wrap
+    // kernel; FP64 path: pair gradients per slot and the gather
+    const bool fixp = precision == POD_MIXED;
+    if (fixp && (rc_ = ensure(facc, sizeof(unsigned long long) * 4 * (size_t)N, "force accumulators"))) return rc_;
+    unsigned long long* fa = fixp ? (unsigned long long*)facc.p : nullptr;
     if (reuse) {
       pl = last_pl;
       cudaError_t ew = launch_rewrap(N, sys->pos, (const int*)wrapk.p, pl.cg.L, (double*)wpos.p, (float4*)phi.p,
-                                     (float4*)plo.p, (int*)status.p, st);
+                                     (float4*)plo.p, (int*)status.p, st, fa);
       if (ew != cudaSuccess) return cuda_fail(ew, "rewrap kernel");
     } else {
-      // the gather searches the reverse slots; when the list may be reused (a
-      // skin, or reuse switched on) it also stores them for the reusing steps
-      if ((rc_ = build_neighbors(sys->pos, pl, false, st))) return rc_;
+      // the FP64 gather searches the reverse slots; when the list may be reused
+      // (a skin, or reuse switched on) it also stores them for the reusing steps
+      if ((rc_ = build_neighbors(sys->pos, pl, false, st, fa))) return rc_;
     }
-    const bool keep_rev = !reuse && !pl.batched && (skin > 0 || nbr_mode == 1);
+    const bool keep_rev = !fixp && !reuse && !pl.batched && (skin > 0 || nbr_mode == 1);
     if (keep_rev && (rc_ = ensure(rev, sizeof(int) * (size_t)N * pl.cap, "reverse index"))) return rc_;
     const int* rev_in = reuse ? (const int*)rev.p : nullptr;
     int* rev_out = keep_rev ? (int*)rev.p : nullptr;
-    const size_t gbytes = (precision == POD_MIXED ? sizeof(Q4<float>) : sizeof(Q4<double>)) * (size_t)N * pl.cap;
-    if ((rc_ = ensure(g, gbytes, "pair gradients"))) return rc_;
+    if (!fixp && (rc_ = ensure(g, sizeof(Q4<double>) * (size_t)N * pl.cap, "pair gradients"))) return rc_;
     const int nwarp = atom_warps(N, K, pl.shape.atom_wpb);
     if ((rc_ = ensure(wpart, sizeof(double) * 9 * (size_t)nwarp, "virial partials"))) return rc_;
     double* Ei_dst = Ei_user;
@@ -851,7 +858,7 @@ int pod_handle::energy_forces(const pod_system* sys, const double* c, double* E,
       if ((rc_ = ensure(Ei, sizeof(double) * (size_t)N, "atom energies"))) return rc_;
       Ei_dst = (double*)Ei.p;
     }
-    const int nblk = gather_blocks(N, pl.shape.gather_wpb, pl.shape.gather_bps);
+    const int nblk = fixp ? finalize_blocks(N) : gather_blocks(N, pl.shape.gather_wpb, pl.shape.gather_bps);
     if ((rc_ = ensure(Wat, sizeof(double) * 10 * (size_t)nblk, "block partial sums"))) return rc_;
     if (!offs.p) {
       if ((rc_ = ensure(offs, sizeof(unsigned) * 4, "ticket"))) return rc_;
@@ -862,11 +869,9 @@ int pod_handle::energy_forces(const pod_system* sys, const double* c, double* E,
     if ((rc_ = run_atoms(1, pl, nullptr, c, Ei_dst, st))) return rc_;
     if ((rc_ = mark(2, st))) return rc_;
     cudaError_t e;
-    if (precision == POD_MIXED)
-      e = launch_gather_reduce<float>(N, pl.cap, (const int*)nbr_count.p, (const int*)nbr_j.p, (const int*)nbr_s.p,
-                                      rev_in, rev_out, (const Q4<float>*)g.p, Ei_dst, (const double*)wpart.p, nwarp,
-                                      F, 1.0, (double*)Wat.p, nblk, (unsigned*)offs.p, E, W, (int*)status.p, st,
-                                      pl.shape.gather_wpb);
+    if (fixp)
+      e = launch_finalize(N, fa, Ei_dst, (const double*)wpart.p, nwarp, F, 1.0, (double*)Wat.p, nblk,
+                          (unsigned*)offs.p, E, W, st);
     else
       e = launch_gather_reduce<double>(N, pl.cap, (const int*)nbr_count.p, (const int*)nbr_j.p,
                                        (const int*)nbr_s.p, rev_in, rev_out, (const Q4<double>*)g.p, Ei_dst,
@@ -883,7 +888,8 @@ int pod_handle::energy_forces(const pod_system* sys, const double* c, double* E,
     bool retry;
     if ((rc_ = finish(st, pl, retry))) return rc_;
     if (!retry) {
-      if (!pl.batched && (reuse || rev_out)) {  // a list can be reused once its reverse slots are stored
+      // a list can be reused (FP64 path: once its reverse slots are stored)
+      if (!pl.batched && (fixp || reuse || rev_out)) {
         last_pl = pl;
         reuse_ok = true;
       }

@@ -12,6 +12,12 @@ constexpr int MAXG = 8;    // gamma values
 constexpr int MAXK = 16;   // radial modes (= lanes per atom in the atom kernels)
 constexpr int MAXROWS = MAXA * MAXB + MAXG;
 constexpr int PAMAX = 4;   // highest angular degree compiled
+// FP32 path: forces accumulate as 64-bit fixed-point integers with 32 fraction
+// bits (integer addition is associative, so the sums are reproducible whatever
+// the order of the atomic adds); |F| up to 2^30 eV/A, resolution 2.3e-10 eV/A.
+constexpr float FIX_SCALE_F = 4294967296.0f;     // 2^32
+constexpr double FIX_INV_SCALE = 1.0 / 4294967296.0;
+constexpr float FIX_GMAX = 1073741824.0f;        // 2^30: larger pair gradients are reported
 constexpr int MAXM = 1 + MAXK + MAXK * (PAMAX + 1) + MAXK * 11;  // descriptors (11 = four-body K_a at P = 4)
 constexpr int CH = 32;     // pairs per atom staged in shared memory at a time
 constexpr int WPB_ATOM = 2;   // warps per block, atom kernels (default launch shape)

@@ -93,7 +93,8 @@ struct pod_handle {
   int global_desc(const pod_system* sys, const double* vdir, double* G, cudaStream_t st);
   const double* vdir_cur = nullptr;
   DevBuf Dws, chunks, cpart;
-  DevBuf gdm, dmG;  // fit: design-matrix pair gradients, per-configuration descriptor sums
+  DevBuf gdm, dmG;
+  DevBuf facc;  // FP32 path: fixed-point force accumulators [N][4]  // fit: design-matrix pair gradients, per-configuration descriptor sums
   int dm_q0 = 0, dm_q1 = 0;  // fit: descriptor-index range of the current design pass
   int colsum_table(const Plan& pl, int& nch, int& nrows2);
   int fit_build(const pod_system* batch, const double* E_ref, const double* F_ref, const pod_fit_opts& o);
@@ -103,7 +104,8 @@ struct pod_handle {
   long long fit_R = 0;
   int fit_nc = 0, fit_N = 0;
   double fit_wE = 0, fit_wF = 0;
-  int build_neighbors(const double* pos, Plan& pl, bool need_rev, cudaStream_t st);
+  int build_neighbors(const double* pos, Plan& pl, bool need_rev, cudaStream_t st,
+                      unsigned long long* facc = nullptr);
   template <typename T>
   void fill_args(fastpod::AtomArgs<T>& a, const Plan& pl);
   int run_atoms(int mode, const Plan& pl, double* D, const double* c, double* Ei_dst, cudaStream_t st);

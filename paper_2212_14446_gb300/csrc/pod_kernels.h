@@ -43,7 +43,8 @@ struct AtomArgs {
   double* D;            // mode 0: descriptors [N][M]
   const double* c;      // mode 1: coefficients [M]
   double* Ei;           // mode 1: atom energies [N]
-  Q4<T>* g;             // mode 1: dE_i/dr_ij per pair slot [N * cap]
+  Q4<T>* g;             // mode 1, FP64 path: dE_i/dr_ij per pair slot [N * cap]
+  unsigned long long* facc;  // mode 1, FP32 path: fixed-point force accumulators [N][4]
   double* wpart;        // mode 1: per-warp virial partials [warps][9]
   const double* vdir;   // mode 2: displacement direction per atom [3][N] (tangent of D written to D)
   T* gdm;               // mode 3: design-matrix pair gradients [q - q0][N * cap][K][3]
@@ -66,9 +67,10 @@ inline T mask_radius(double r) {
 }
 
 cudaError_t launch_bin(int N, const double* pos, const CellGrid& cg, double* wpos, float4* phi, float4* plo,
-                       int* cell_count, float4* cell_pos, int* status, cudaStream_t st, int* wrapk = nullptr);
+                       int* cell_count, float4* cell_pos, int* status, cudaStream_t st, int* wrapk = nullptr,
+                       unsigned long long* facc = nullptr);
 cudaError_t launch_rewrap(int N, const double* pos, const int* wrapk, const double L[3], double* wpos, float4* phi,
-                          float4* plo, int* status, cudaStream_t st);
+                          float4* plo, int* status, cudaStream_t st, unsigned long long* facc = nullptr);
 cudaError_t launch_kick(int N3, double* v, const double* F, double half_dt_over_m, double* x, double dt,
                         cudaStream_t st);
 cudaError_t launch_neigh(int N, const CellGrid& cg, const double* wpos, const float4* phi, const float4* plo,
@@ -80,7 +82,8 @@ cudaError_t launch_export_neighbors(int N, int cap, const int* nbr_count, const 
                                     int cap_out, int* count_out, int* j_out, int* s_out, cudaStream_t st);
 
 cudaError_t launch_batch_wrap(int N, const double* pos, const int* cfg_of, const CfgBox* cbox, double* wpos,
-                              float4* phi, float4* plo, int* status, cudaStream_t st);
+                              float4* phi, float4* plo, int* status, cudaStream_t st,
+                              unsigned long long* facc = nullptr);
 cudaError_t launch_batch_neigh(int N, const int* cfg_of, const CfgBox* cbox, const double* wpos, const float4* phi,
                                double rcut, double Lmax, int Smax, int cap, int* nbr_count, int* nbr_j, int* nbr_s,
                                int* status, cudaStream_t st);
@@ -100,5 +103,9 @@ int atom_warps(int N, int K, int wpb);
 cudaError_t launch_colsum(int n_chunks, const int* chunk_rows /*[n_chunks][2]*/, int n_cfg, const int* cfg_chunks,
                           int M, const double* D, double* part, double* G, cudaStream_t st);
 int gather_blocks(int N, int wpb, int bps);
+int finalize_blocks(int N);
+cudaError_t launch_finalize(int N, const unsigned long long* facc, const double* Ei, const double* wpart,
+                            int n_wpart, double* F, double fscale, double* part, int nblocks, unsigned* ticket,
+                            double* E, double* W, cudaStream_t st);
 
 }  // namespace fastpod
