@@ -293,6 +293,32 @@ class Oracle:
         Ei = {i: pg[i][0] for i in need}
         return Ei, None, F, None
 
+    def energy_forces_quadratic(self, cfg, c, beta, fast: bool = True):
+        """Quadratic model of Sec. 4 (the extension of Eq. 57a by products of
+        descriptors): E_i = sum_m c_m D_im + sum_{m <= n} beta_mn D_im D_in, with
+        the upper triangle of ``beta`` read.  Forces from the explicit descriptor
+        derivatives: dE_i/dr_ij = sum_m (c_m + sum_n S_mn D_in) dD_im/dr_ij with
+        S = beta_upper + beta_upper^T, assembled like ``energy_forces``."""
+        c = np.asarray(c, dtype=np.float64)
+        bu = np.triu(np.asarray(beta, dtype=np.float64))
+        S = bu + bu.T
+        sysd = self._system(cfg)
+        Ei = np.zeros(cfg.n)
+        F = np.zeros((cfg.n, 3))
+        W = np.zeros((3, 3))
+        for i in range(cfg.n):
+            js, _, d = self.neighbors(cfg, i, sysd)
+            D = self.atom_descriptors(d, fast)
+            Ei[i] = D @ c + D @ bu @ D
+            if len(js) == 0:
+                continue
+            dD = self.atom_dD(d, fast)              # (n_j, M, 3): dD_im / dr_ij
+            g = np.einsum("jmt,m->jt", dD, c + S @ D)
+            F[i] += g.sum(axis=0)
+            np.subtract.at(F, js, g)
+            W -= d.T @ g
+        return Ei, math.fsum(Ei), F, W
+
     # -- fit (Eq. 63a)
     def config_rows(self, cfg, fast: bool = True):
         """Global descriptors G (M,) and dG/dr_k (N, 3, M) of one configuration."""

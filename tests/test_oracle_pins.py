@@ -467,3 +467,53 @@ def test_fit_recovers_teacher():
     c, A, b = o.fit(cfgs, E_ref, F_ref)
     assert np.linalg.norm(A @ cstar - b) <= 1e-10 * np.linalg.norm(b)
     assert np.allclose(c, cstar, rtol=1e-6, atol=1e-8)
+
+
+# ----------------------------------------------------------- quadratic model
+
+def _quad_beta(M, seed, scale=1e-5):
+    b = synth.rng(seed).normal(0.0, scale, size=(M, M))
+    return b
+
+
+def test_quadratic_model_reduces_to_linear():
+    """beta = 0: the quadratic model of Sec. 4 is the linear model (Eq. 57a)."""
+    o = oracle.Oracle(synth.params_full())
+    cfg = synth.jitter(synth.bcc(2), 0.1, synth.rng(71))
+    c = synth.coefficients(o.M, 72)
+    Ei, E, F, W = o.energy_forces(cfg, c, fast=True)
+    Eq_i, Eq, Fq, Wq = o.energy_forces_quadratic(cfg, c, np.zeros((o.M, o.M)))
+    assert np.allclose(Eq_i, Ei, rtol=1e-13, atol=1e-15)
+    assert np.allclose(Fq, F, atol=1e-12) and np.allclose(Wq, W, atol=1e-12)
+
+
+def test_quadratic_model_energy_and_forces():
+    """Energy = c.D + D^T beta_upper D per atom (only the upper triangle of beta
+    counts), forces = minus central differences of that energy, virial
+    symmetric, net force zero."""
+    o = oracle.Oracle(synth.params_full())
+    cfg = synth.jitter(synth.bcc(2), 0.1, synth.rng(73))
+    c = synth.coefficients(o.M, 74)
+    beta = _quad_beta(o.M, 75)
+    Ei, E, F, W = o.energy_forces_quadratic(cfg, c, beta)
+    # the lower triangle is ignored
+    Ei2, _, F2, _ = o.energy_forces_quadratic(cfg, c, np.triu(beta) + 7.0 * np.tril(np.ones_like(beta), -1))
+    assert np.array_equal(Ei, Ei2) and np.array_equal(F, F2)
+
+    def energy(cf):
+        D = o.descriptors(cf, fast=False)  # naive sums, independent of the fast path
+        return float(np.sum(D @ c) + sum(Di @ np.triu(beta) @ Di for Di in D))
+
+    assert E == pytest.approx(energy(cfg), rel=1e-11)
+    h = 1e-5
+    for k in [0, 9]:
+        for t in range(3):
+            cp = synth.Config(pos=cfg.pos.copy(), box=cfg.box)
+            cm = synth.Config(pos=cfg.pos.copy(), box=cfg.box)
+            cp.pos[k, t] += h
+            cm.pos[k, t] -= h
+            fd = -(energy(cp) - energy(cm)) / (2 * h)
+            assert F[k, t] == pytest.approx(fd, rel=1e-7, abs=1e-7)
+    fs = np.max(np.abs(F))
+    assert np.allclose(F.sum(0), 0.0, atol=1e-12 * max(fs, 1.0) * cfg.n)
+    assert np.allclose(W, W.T, atol=1e-10 * max(np.max(np.abs(W)), 1.0))
