@@ -264,6 +264,16 @@ int pod_fit_residual(pod_handle* h, const double* c, double* sum_abs_E, double* 
  *   serialised by the caller.  Waits for `stream` before returning. */
 int pod_descriptors_static(pod_handle* h, const pod_system* sys, double* D, void* stream);
 
+/* Quadratic POD model (Sec. 4, the extension of Eq. 57a with products of
+ * descriptors): E_i = sum_m c_m D_im + sum_m sum_{n >= m} beta_mn D_im D_in.
+ * beta: host [M][M] row-major; only the entries with m <= n are read (the
+ * one-body column 0 included); copied to the device.  NULL returns the handle to
+ * the linear model.  While set, pod_energy_forces, pod_energy_forces_host and
+ * pod_md_step evaluate the quadratic model (forces by the same adjoint pass with
+ * dE_i/dD_im = c_m + sum_n (beta_mn + beta_nm) D_in per atom); the fit entry
+ * points fit the linear model only.  POD_EINVAL for non-finite weights. */
+int pod_set_quadratic(pod_handle* h, const double* beta);
+
 /* Launch-shape autotuner (a deployment feature; the paper has no counterpart).
  * Times the three phases of pod_energy_forces on `sys` (one configuration,
  * device positions as for pod_energy_forces; c: device [M]) for a small set of

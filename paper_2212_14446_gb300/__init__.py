@@ -61,7 +61,7 @@ class pod_fit_opts(C.Structure):
 EXPORTS = ["pod_create", "pod_destroy", "pod_info", "pod_set_option", "pod_status", "pod_timing",
            "pod_neighbors", "pod_descriptors", "pod_energy_forces", "pod_energy_forces_host", "pod_fit",
            "pod_fit_normal", "pod_fit_solve", "pod_fit_residual", "pod_descriptors_static",
-           "pod_global_descriptors", "pod_descriptors_jvp", "pod_set_skin", "pod_md_step", "pod_fma_probe", "pod_autotune",
+           "pod_global_descriptors", "pod_descriptors_jvp", "pod_set_skin", "pod_md_step", "pod_fma_probe", "pod_autotune", "pod_set_quadratic",
            "pod_last_error"]
 
 _lib = None
@@ -102,6 +102,7 @@ def lib():
                 "pod_fit_residual": (C.c_int, [H, dp, dp, dp, ip, ip]),
                 "pod_fma_probe": (C.c_int, [C.c_int, C.c_int, dp, vp]),
                 "pod_autotune": (C.c_int, [H, S, dp, C.c_int, ip, dp, vp]),
+                "pod_set_quadratic": (C.c_int, [H, dp]),
                 "pod_last_error": (C.c_char_p, [H]),
             }
             for name, (res, args) in sig.items():
@@ -390,6 +391,17 @@ class POD:
         W = torch.empty(9, dtype=torch.float64, device=dev) if virial else None
         pod_energy_forces(self.h, self.system(x, box, pbc), c, E, Ei, F, W, stream)
         return {"E": E, "Ei": Ei, "F": None if F is None else F.t(), "W": None if W is None else W.view(3, 3)}
+
+    def set_quadratic(self, beta=None):
+        """Quadratic model E_i = c.D_i + sum_{m<=n} beta_mn D_im D_in (beta: (M, M), upper
+        triangle read), or None for the linear model."""
+        if beta is None:
+            _check(self.h, lib().pod_set_quadratic(self.h, None))
+            return
+        b = np.ascontiguousarray(np.asarray(beta, dtype=np.float64))
+        if b.shape != (self.M, self.M):
+            raise ValueError(f"beta must be ({self.M}, {self.M})")
+        _check(self.h, lib().pod_set_quadratic(self.h, b.ctypes.data_as(C.POINTER(C.c_double))))
 
     def autotune(self, pos, box, c, pbc=(1, 1, 1), reps=5, stream=None):
         """Pick the launch shape for this system size (pod_autotune); returns

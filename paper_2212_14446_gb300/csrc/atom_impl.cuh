@@ -145,14 +145,16 @@ __global__ void __launch_bounds__(ATOM_MAX_WPB * 32, atom_min_blocks<T, MODE, KT
   const int m = lane - a_loc * K;
   const int gwarp = blockIdx.x * (blockDim.x >> 5) + warp;  // global warp index
   const int atom0 = gwarp * A;
-  // energy mode: the block converts the coefficients to T once (shared memory)
+  // energy modes (1: linear model, 4: quadratic model): the block converts the
+  // coefficients to T once (shared memory)
+  constexpr bool EMODE = (MODE == 1 || MODE == 4);
   __shared__ T sc[MAXM];
-  if (MODE == 1) {
+  if (EMODE) {
     for (int q = threadIdx.x; q < p.M; q += blockDim.x) sc[q] = (T)p.c[q];
     __syncthreads();
   }
   if (atom0 >= p.N) {  // uniform per warp
-    if (MODE == 1 && lane < 9) p.wpart[(size_t)gwarp * 9 + lane] = 0.0;
+    if (EMODE && lane < 9) p.wpart[(size_t)gwarp * 9 + lane] = 0.0;
     return;
   }
   if (lane < A) {
@@ -414,6 +416,31 @@ __global__ void __launch_bounds__(ATOM_MAX_WPB * 32, atom_min_blocks<T, MODE, KT
     return;
   }
 
+  if (MODE == 4) {
+    // ---------------- quadratic model: stage this atom's descriptors (all
+    // columns) so each lane can form dE_i/dD_col = c_col + sum_n S_col,n D_in
+    T* sDa = reinterpret_cast<T*>(wb + lay.off_D) + a_loc * lay.MS;
+    if (am) {
+      T d3[PA + 1];
+      Mono<PA>::d3(B, d3);
+      if (m == 0) sDa[0] = T(1);
+      if (m < p.K2) sDa[1 + m] = B[0];
+      if (m < p.K3) {
+#pragma unroll
+        for (int n = 0; n <= PA; ++n)
+          if (n <= p.P3) sDa[p.col3 + m * (p.P3 + 1) + n] = d3[n];
+      }
+      if (HAS4 && m < p.K4) {
+        T D4[KA];
+        Four<PA>::desc(B, d3, D4);
+#pragma unroll
+        for (int q = 0; q < KA; ++q)
+          if (q < p.KA4) sDa[p.col4 + m * p.KA4 + q] = D4[q];
+      }
+    }
+    __syncwarp();
+  }
+
   // ---------------- energy and adjoint a = dE_i/dB_m  (Eq. 26c generalised)
   T E = T(0);
   {
@@ -422,18 +449,51 @@ __global__ void __launch_bounds__(ATOM_MAX_WPB * 32, atom_min_blocks<T, MODE, KT
     for (int x = 0; x < NAP; ++x) a[x] = T(0);
     if (am) {
       const T* c = sc;
-      const T c2 = (m < p.K2) ? c[1 + m] : T(0);
+      T c2 = (m < p.K2) ? c[1 + m] : T(0);
+      T c0 = c[0];
       T h[PA + 1];
 #pragma unroll
       for (int n = 0; n <= PA; ++n)
         h[n] = (n <= p.P3 && m < p.K3) ? c[p.col3 + m * (p.P3 + 1) + n] : T(0);
+      T w4[KA];
+#pragma unroll
+      for (int q = 0; q < KA; ++q) w4[q] = (HAS4 && q < p.KA4 && m < p.K4) ? c[p.col4 + m * p.KA4 + q] : T(0);
+      T Elin = T(0);  // quadratic model: the linear part c . D of this lane's columns
+      if (MODE == 4) {
+        const T* Da = reinterpret_cast<const T*>(wb + lay.off_D) + a_loc * lay.MS;
+        auto ceff = [&](int col) {
+          const T* row = p.qbeta + (size_t)col * p.M;
+          T s = c[col];
+          for (int n = 0; n < p.M; ++n) s = fma(row[n], Da[n], s);
+          return s;
+        };
+        if (m < p.K2) {
+          Elin = fma(c2, Da[1 + m], Elin);
+          c2 = ceff(1 + m);
+        }
+#pragma unroll
+        for (int n = 0; n <= PA; ++n)
+          if (n <= p.P3 && m < p.K3) {
+            const int col = p.col3 + m * (p.P3 + 1) + n;
+            Elin = fma(h[n], Da[col], Elin);
+            h[n] = ceff(col);
+          }
+#pragma unroll
+        for (int q = 0; q < KA; ++q)
+          if (HAS4 && q < p.KA4 && m < p.K4) {
+            const int col = p.col4 + m * p.KA4 + q;
+            Elin = fma(w4[q], Da[col], Elin);
+            w4[q] = ceff(col);
+          }
+        if (m == 0) {
+          Elin += c0;
+          c0 = ceff(0);
+        }
+      }
       T d3[PA + 1];
       Mono<PA>::d3(B, d3);
       T a0 = c2;
       if (HAS4) {
-        T w4[KA];
-#pragma unroll
-        for (int q = 0; q < KA; ++q) w4[q] = (q < p.KA4 && m < p.K4) ? c[p.col4 + m * p.KA4 + q] : T(0);
         // general partitions (Eq. 30a): cubic form, E4 = (1/3) sum_x B_x dE4/dB_x
         Four<PA>::adjoint(B, w4, a);
         T E4 = T(0);
@@ -453,7 +513,10 @@ __global__ void __launch_bounds__(ATOM_MAX_WPB * 32, atom_min_blocks<T, MODE, KT
       for (int n = 0; n <= PA; ++n) E = fma(h[n], d3[n], E);
       Mono<PA>::d3_adjoint(B, h, a);
       a[0] += a0;
-      if (m == 0) E += c[0];
+      if (m == 0) E += c0;
+      // quadratic model: E above is sum_col (dE/dD_col) D_col = c.D + 2 E_quad, so
+      // E_i = (c.D + that) / 2
+      if (MODE == 4) E = T(0.5) * (E + Elin);
       T* adst = sadj + a_loc * lay.AS + m * NAP;
 #pragma unroll
       for (int x = 0; x < NAP; ++x) adst[x] = a[x];
@@ -621,7 +684,7 @@ __global__ void __launch_bounds__(ATOM_MAX_WPB * 32, atom_min_blocks<T, MODE, KT
 
 // ------------------------------------------------------------------ layout
 template <typename T>
-AtomLayout make_layout(int K, int PA, bool table, bool tangent = false) {
+AtomLayout make_layout(int K, int PA, bool table, bool tangent = false, int quadM = 0) {
   if (tangent) table = false;  // the tangent pass reads R' from shared memory
   AtomLayout L{};
   const int NA = (PA + 1) * (PA + 2) * (PA + 3) / 6;
@@ -649,6 +712,9 @@ AtomLayout make_layout(int K, int PA, bool table, bool tangent = false) {
   off = al(off + sizeof(int) * 32, 32);
   L.off_V = off;
   if (tangent) off = al(off + sizeof(Q4<T>) * (size_t)L.A * L.GA, 32);
+  L.off_D = off;  // quadratic model: descriptors of the warp's atoms
+  L.MS = quadM > 0 ? (quadM | 1) : 0;
+  off = al(off + sizeof(T) * (size_t)L.A * L.MS, 32);
   L.warp_bytes = off;
   return L;
 }
@@ -703,7 +769,7 @@ static cudaError_t dispatch_generic(const AtomArgs<T>& p, const AtomLayout& lay,
 // (K = 3, P = 3, no 4-body; K = 6, P = 4, 4-body), generic K <= 16 otherwise.
 template <typename T>
 cudaError_t launch_atom_t(int mode, const AtomArgs<T>& p, int PA, bool has4, cudaStream_t st) {
-  const AtomLayout lay = make_layout<T>(p.K, PA, p.rad.tab != nullptr, mode == 2);
+  const AtomLayout lay = make_layout<T>(p.K, PA, p.rad.tab != nullptr, mode == 2, mode == 4 ? p.M : 0);
   const bool spec6 = (p.K == 6 && PA == 4 && has4);
   const bool spec3 = (p.K == 3 && PA == 3 && !has4);
   if (mode == 2) {
@@ -720,6 +786,12 @@ cudaError_t launch_atom_t(int mode, const AtomArgs<T>& p, int PA, bool has4, cud
     if (spec6) return launch_one<T, 4, true, 3, 6>(p, lay, st);
     if (spec3) return launch_one<T, 3, false, 3, 3>(p, lay, st);
     return dispatch_generic<T, 3>(p, lay, PA, has4, st);
+  }
+  if (mode == 4) {
+    if (!p.qbeta) return cudaErrorInvalidValue;
+    if (spec6) return launch_one<T, 4, true, 4, 6>(p, lay, st);
+    if (spec3) return launch_one<T, 3, false, 4, 3>(p, lay, st);
+    return dispatch_generic<T, 4>(p, lay, PA, has4, st);
   }
   if (spec6) return launch_one<T, 4, true, 1, 6>(p, lay, st);
   if (spec3) return launch_one<T, 3, false, 1, 3>(p, lay, st);

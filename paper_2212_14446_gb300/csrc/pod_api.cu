@@ -331,7 +331,7 @@ int pod_handle::autotune(const pod_system* sys, const double* c, int reps, cudaS
 std::vector<DevBuf*> pod_handle::all_bufs() {
   return {&cell_count, &cell_atoms, &wpos, &phi, &plo, &nbr_count, &nbr_j, &nbr_s, &rev, &g, &Ei,
           &Wat, &status, &offs, &pos_in, &c_in, &E_out, &F_out, &W_out, &Ei_out, &fitA, &fitG, &fitb,
-          &fitwork, &cfg_of, &boxes, &rtab, &wpart, &Dws, &chunks, &cpart, &wrapk, &gdm, &dmG, &facc};
+          &fitwork, &cfg_of, &boxes, &rtab, &wpart, &Dws, &chunks, &cpart, &wrapk, &gdm, &dmG, &facc, &qS32, &qS64};
 }
 
 // ============================================================ C ABI
@@ -435,6 +435,33 @@ int pod_set_option(pod_handle* h, int option, int value) {
     return POD_OK;
   }
   return h->fail(POD_EINVAL, "unknown option %d", option);
+}
+
+int pod_set_quadratic(pod_handle* h, const double* beta) {
+  if (!h) return POD_EINVAL;
+  if (!beta) {
+    h->quad = false;
+    return POD_OK;
+  }
+  const int M = h->M;
+  std::vector<double> S((size_t)M * M);
+  std::vector<float> S32((size_t)M * M);
+  for (int m = 0; m < M; ++m)
+    for (int n = 0; n < M; ++n) {
+      // S_mn = beta_mn + beta_nm over the upper triangle (diagonal: 2 beta_mm)
+      const double v = m == n ? 2.0 * beta[(size_t)m * M + m] : beta[(size_t)std::min(m, n) * M + std::max(m, n)];
+      if (!std::isfinite(v)) return h->fail(POD_EINVAL, "quadratic weights must be finite");
+      S[(size_t)m * M + n] = v;
+      S32[(size_t)m * M + n] = (float)v;
+    }
+  int rc;
+  if ((rc = h->ensure(h->qS64, sizeof(double) * S.size(), "quadratic weights"))) return rc;
+  if ((rc = h->ensure(h->qS32, sizeof(float) * S32.size(), "quadratic weights"))) return rc;
+  cudaError_t e = cudaMemcpy(h->qS64.p, S.data(), sizeof(double) * S.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(h->qS32.p, S32.data(), sizeof(float) * S32.size(), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return h->cuda_fail(e, "quadratic weights upload");
+  h->quad = true;
+  return POD_OK;
 }
 
 int pod_autotune(pod_handle* h, const pod_system* sys, const double* c, int reps, int* shape, double* ms,
@@ -770,6 +797,7 @@ int pod_handle::run_atoms(int mode, const Plan& pl, double* D, const double* c, 
     a.Ei = Ei_dst;
     a.g = nullptr;
     a.facc = (unsigned long long*)facc.p;
+    a.qbeta = (const float*)qS32.p;
     a.wpart = (double*)wpart.p;
     a.gdm = (float*)gdm.p;
     a.q0 = dm_q0;
@@ -783,6 +811,7 @@ int pod_handle::run_atoms(int mode, const Plan& pl, double* D, const double* c, 
     a.c = c;
     a.Ei = Ei_dst;
     a.g = (Q4<double>*)g.p;
+    a.qbeta = (const double*)qS64.p;
     a.wpart = (double*)wpart.p;
     a.gdm = (double*)gdm.p;
     a.q0 = dm_q0;
@@ -866,7 +895,7 @@ int pod_handle::energy_forces(const pod_system* sys, const double* c, double* E,
       if (e0 != cudaSuccess) return cuda_fail(e0, "ticket init");
     }
     if ((rc_ = mark(1, st))) return rc_;
-    if ((rc_ = run_atoms(1, pl, nullptr, c, Ei_dst, st))) return rc_;
+    if ((rc_ = run_atoms(quad ? 4 : 1, pl, nullptr, c, Ei_dst, st))) return rc_;
     if ((rc_ = mark(2, st))) return rc_;
     cudaError_t e;
     if (fixp)

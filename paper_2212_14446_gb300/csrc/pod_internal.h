@@ -94,7 +94,9 @@ struct pod_handle {
   const double* vdir_cur = nullptr;
   DevBuf Dws, chunks, cpart;
   DevBuf gdm, dmG;
-  DevBuf facc;  // FP32 path: fixed-point force accumulators [N][4]  // fit: design-matrix pair gradients, per-configuration descriptor sums
+  DevBuf facc;  // FP32 path: fixed-point force accumulators [N][4]
+  DevBuf qS32, qS64;  // quadratic model: symmetric weights S = beta + beta^T (FP32 and FP64 copies)
+  bool quad = false;  // fit: design-matrix pair gradients, per-configuration descriptor sums
   int dm_q0 = 0, dm_q1 = 0;  // fit: descriptor-index range of the current design pass
   int colsum_table(const Plan& pl, int& nch, int& nrows2);
   int fit_build(const pod_system* batch, const double* E_ref, const double* F_ref, const pod_fit_opts& o);

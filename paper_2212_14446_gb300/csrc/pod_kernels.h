@@ -24,7 +24,8 @@ struct AtomLayout {
   int SA;   // per-atom stride of R / R' (CH * KS + K: lanes (atom, m) hit distinct banks)
   int GA;   // per-atom stride of the staged (u, r), in Q4 units
   int AS;   // per-atom stride of the adjoint dE/dB (multiple of 4, odd number of 16-byte units)
-  size_t off_geo, off_R, off_Rp, off_adj, off_e, off_cnt, off_V, warp_bytes;
+  size_t off_geo, off_R, off_Rp, off_adj, off_e, off_cnt, off_V, off_D, warp_bytes;
+  int MS;   // per-atom stride of the staged descriptors (quadratic model)
 };
 
 template <typename T>
@@ -41,7 +42,8 @@ struct AtomArgs {
   float Lh[3], Ll[3];
   int K, K2, K3, K4, P3, P4, KA4, M, col3, col4;
   double* D;            // mode 0: descriptors [N][M]
-  const double* c;      // mode 1: coefficients [M]
+  const double* c;      // modes 1, 4: coefficients [M]
+  const T* qbeta;       // mode 4: symmetric quadratic weights S [M][M], S_mn = beta_mn + beta_nm
   double* Ei;           // mode 1: atom energies [N]
   Q4<T>* g;             // mode 1, FP64 path: dE_i/dr_ij per pair slot [N * cap]
   unsigned long long* facc;  // mode 1, FP32 path: fixed-point force accumulators [N][4]
