@@ -222,15 +222,16 @@ __global__ void __launch_bounds__(256)
   if (threadIdx.x == 0) *ticket = 0u;  // ready for the next launch (graph replays)
 }
 
+constexpr int FINALIZE_THREADS = 256;
 int finalize_blocks(int N) {
-  const int want = (N + 255) / 256;
+  const int want = (N + FINALIZE_THREADS - 1) / FINALIZE_THREADS;
   return want < 2 * 152 ? (want > 0 ? want : 1) : 2 * 152;
 }
 
 cudaError_t launch_finalize(int N, const unsigned long long* facc, const double* Ei, const double* wpart,
                             int n_wpart, double* F, double fscale, double* part, int nblocks, unsigned* ticket,
                             double* E, double* W, cudaStream_t st) {
-  finalize_kernel<<<nblocks, 256, 0, st>>>(N, facc, Ei, wpart, n_wpart, F, fscale, part, ticket, E, W);
+  finalize_kernel<<<nblocks, FINALIZE_THREADS, 0, st>>>(N, facc, Ei, wpart, n_wpart, F, fscale, part, ticket, E, W);
   return cudaGetLastError();
 }
 

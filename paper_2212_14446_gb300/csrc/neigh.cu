@@ -86,6 +86,7 @@ __global__ void __launch_bounds__(NEIGH_MAX_WPB * 32)
   const int ci[3] = {own % cg.nc[0], (own / cg.nc[0]) % cg.nc[1], own / (cg.nc[0] * cg.nc[1])};
   const int wx = 2 * cg.S[0] + 1, wy = 2 * cg.S[1] + 1, wz = 2 * cg.S[2] + 1;
   const int noff = wx * wy * wz;
+  const bool s1 = cg.S[0] == 1 && cg.S[1] == 1 && cg.S[2] == 1;
   const int zero = shift_pack(0, 0, 0);
   int nhit = 0;
   for (int ob = 0; ob < noff; ob += 32) {
@@ -94,7 +95,16 @@ __global__ void __launch_bounds__(NEIGH_MAX_WPB * 32)
     int cnt = 0, cell = 0, code = zero;
     float px = 0.f, py = 0.f, pz = 0.f;
     if (o < noff) {
-      const int oc[3] = {o % wx - cg.S[0], (o / wx) % wy - cg.S[1], o / (wx * wy) - cg.S[2]};
+      int oc[3];
+      if (s1) {  // one cell of search depth: constant divisors
+        oc[0] = o % 3 - 1;
+        oc[1] = (o / 3) % 3 - 1;
+        oc[2] = o / 9 - 1;
+      } else {
+        oc[0] = o % wx - cg.S[0];
+        oc[1] = (o / wx) % wy - cg.S[1];
+        oc[2] = o / (wx * wy) - cg.S[2];
+      }
       int tc[3], sh[3];
       bool ok = true;
 #pragma unroll
@@ -102,7 +112,10 @@ __global__ void __launch_bounds__(NEIGH_MAX_WPB * 32)
         int t = ci[d] + oc[d];
         int sd = 0;
         if (cg.pbc[d]) {
-          sd = (t >= 0) ? t / cg.nc[d] : -((-t + cg.nc[d] - 1) / cg.nc[d]);
+          if (s1)  // |offset| <= 1 <= nc: at most one box length to wrap
+            sd = t < 0 ? -1 : (t >= cg.nc[d] ? 1 : 0);
+          else
+            sd = (t >= 0) ? t / cg.nc[d] : -((-t + cg.nc[d] - 1) / cg.nc[d]);
           t -= sd * cg.nc[d];
         } else if (t < 0 || t >= cg.nc[d]) {
           ok = false;
