@@ -631,15 +631,19 @@ def run_fit(args, rank, world, local):
         print(json.dumps(line))
 
 
+ATOM_KERNEL_SOURCES = ("atom_impl.cuh", "atom_f32.cu", "atom_f64.cu", "pod_common.cuh", "pod_kernels.h",
+                       "gen_contract.py")
+
+
 def kernel_revision():
-    """Hash of the CUDA sources (a traffic figure is only valid for the kernel it was taken on)."""
+    """Hash of the fused atom kernel's sources (a traffic figure is only valid for
+    the kernel it was taken on)."""
     import hashlib
     h = hashlib.sha1()
     d = os.path.join(ROOT, "paper_2212_14446_gb300", "csrc")
-    for f in sorted(os.listdir(d)):
-        if f.endswith((".cu", ".cuh", ".h")):
-            with open(os.path.join(d, f), "rb") as fh:
-                h.update(fh.read())
+    for f in ATOM_KERNEL_SOURCES:
+        with open(os.path.join(d, f), "rb") as fh:
+            h.update(fh.read())
     return h.hexdigest()[:12]
 
 
