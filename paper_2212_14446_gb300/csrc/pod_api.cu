@@ -197,6 +197,7 @@ int pod_handle::cuda_fail(cudaError_t e, const char* what) {
 int pod_handle::ensure(DevBuf& b, size_t bytes, const char* what) {
   if (bytes <= b.bytes && b.p) return POD_OK;
   if (b.p) {
+    drop_host_graph();  // a captured host graph may hold this buffer's address
     cudaFree(b.p);
     b.p = nullptr;
     b.bytes = 0;
@@ -221,6 +222,21 @@ pod_handle::~pod_handle() {
   if (h_status) cudaFreeHost(h_status);
   for (cudaEvent_t& e : ev)
     if (e) cudaEventDestroy(e);
+  drop_host_graph();
+}
+
+bool pod_handle::HostKey::operator==(const HostKey& o) const {
+  for (int k = 0; k < 6; ++k)
+    if (ptr[k] != o.ptr[k]) return false;
+  for (int d = 0; d < 3; ++d)
+    if (pbc[d] != o.pbc[d] || box[d] != o.box[d]) return false;
+  return N == o.N && precision == o.precision && quad == o.quad && radial == o.radial && tune_gen == o.tune_gen;
+}
+
+void pod_handle::drop_host_graph() {
+  if (hgraph) cudaGraphExecDestroy(hgraph);
+  hgraph = nullptr;
+  hkey_valid = false;
 }
 
 int pod_handle::mark(int k, cudaStream_t st) {
@@ -321,6 +337,7 @@ int pod_handle::autotune(const pod_system* sys, const double* c, int reps, cudaS
     return rc_;
   }
   tuned[cls] = win;
+  ++tune_gen;
   best = win;
   ms[0] = best_neigh;
   ms[1] = best_atom;
@@ -1078,6 +1095,25 @@ int pod_energy_forces(pod_handle* h, const pod_system* sys, const double* c, dou
   return h->energy_forces(sys, c, E, Ei, F, W, (cudaStream_t)stream);
 }
 
+namespace {
+bool host_pinned(const void* p) {
+  if (!p) return true;
+  cudaPointerAttributes a{};
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeHost;
+}
+}  // namespace
+
+// Host-buffer energy and forces.  Copies in, one evaluation, copies out.  When
+// calls repeat with the same (pinned) buffers, size, box and settings on a
+// non-default stream, the second such call captures the copies, the step and a
+// read of the status word into a CUDA graph and later calls replay it (one
+// launch instead of one per kernel and copy); a status other than OK after a
+// replay drops the graph and re-runs the call on the direct path (capacity
+// retries, or the error).
 int pod_energy_forces_host(pod_handle* h, const pod_system* sys, const double* c, double* E, double* Ei, double* F,
                            double* W, void* stream) {
   if (!h) return POD_EINVAL;
@@ -1092,23 +1128,102 @@ int pod_energy_forces_host(pod_handle* h, const pod_system* sys, const double* c
   if (F && (rc = h->ensure(h->F_out, sizeof(double) * 3 * (size_t)N, "staged forces"))) return rc;
   if (W && (rc = h->ensure(h->W_out, sizeof(double) * 9, "staged virial"))) return rc;
   if (Ei && (rc = h->ensure(h->Ei_out, sizeof(double) * (size_t)N, "staged atom energies"))) return rc;
-  cudaError_t e = cudaMemcpyAsync(h->pos_in.p, sys->pos, sizeof(double) * 3 * (size_t)N, cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(h->c_in.p, c, sizeof(double) * h->M, cudaMemcpyHostToDevice, st);
-  if (e != cudaSuccess) return h->cuda_fail(e, "host-to-device copy");
   pod_system dsys = *sys;
   dsys.pos = (const double*)h->pos_in.p;
-  const int keep_sync = h->sync;
-  h->sync = 1;
-  rc = h->energy_forces(&dsys, (const double*)h->c_in.p, (double*)h->E_out.p, Ei ? (double*)h->Ei_out.p : nullptr,
-                        F ? (double*)h->F_out.p : nullptr, W ? (double*)h->W_out.p : nullptr, st);
-  h->sync = keep_sync;
+
+  pod_handle::HostKey key{};
+  key.ptr[0] = sys->pos;
+  key.ptr[1] = c;
+  key.ptr[2] = E;
+  key.ptr[3] = Ei;
+  key.ptr[4] = F;
+  key.ptr[5] = W;
+  key.N = N;
+  for (int d = 0; d < 3; ++d) {
+    key.pbc[d] = sys->pbc[d];
+    key.box[d] = sys->box[d];
+  }
+  key.precision = h->precision;
+  key.quad = h->quad ? 1 : 0;
+  key.radial = h->radial_mode;
+  key.tune_gen = h->tune_gen;
+  const bool graphable = !h->hgraph_off && st != nullptr && !h->timing && h->nbr_mode == 0 && h->skin == 0 &&
+                         sys->n_configs <= 1;
+
+  auto enqueue_step = [&](int sync_mode) -> int {
+    cudaError_t e = cudaMemcpyAsync(h->pos_in.p, sys->pos, sizeof(double) * 3 * (size_t)N, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h->c_in.p, c, sizeof(double) * h->M, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return h->cuda_fail(e, "host-to-device copy");
+    const int keep_sync = h->sync;
+    h->sync = sync_mode;
+    const int r = h->energy_forces(&dsys, (const double*)h->c_in.p, (double*)h->E_out.p,
+                                   Ei ? (double*)h->Ei_out.p : nullptr, F ? (double*)h->F_out.p : nullptr,
+                                   W ? (double*)h->W_out.p : nullptr, st);
+    h->sync = keep_sync;
+    if (r) return r;
+    e = cudaMemcpyAsync(E, h->E_out.p, sizeof(double), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && F) e = cudaMemcpyAsync(F, h->F_out.p, sizeof(double) * 3 * (size_t)N, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && W) e = cudaMemcpyAsync(W, h->W_out.p, sizeof(double) * 9, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && Ei) e = cudaMemcpyAsync(Ei, h->Ei_out.p, sizeof(double) * (size_t)N, cudaMemcpyDeviceToHost, st);
+    if (e != cudaSuccess) return h->cuda_fail(e, "device-to-host copy");
+    return POD_OK;
+  };
+
+  if (graphable && h->hgraph && h->hkey_valid && h->hkey == key) {
+    cudaError_t e = cudaGraphLaunch(h->hgraph, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return h->cuda_fail(e, "host graph replay");
+    if (*h->h_status == 0) return POD_OK;
+    h->drop_host_graph();  // capacity overflow or an error: redo the call on the direct path
+  }
+  rc = enqueue_step(1);
   if (rc) return rc;
-  e = cudaMemcpyAsync(E, h->E_out.p, sizeof(double), cudaMemcpyDeviceToHost, st);
-  if (e == cudaSuccess && F) e = cudaMemcpyAsync(F, h->F_out.p, sizeof(double) * 3 * (size_t)N, cudaMemcpyDeviceToHost, st);
-  if (e == cudaSuccess && W) e = cudaMemcpyAsync(W, h->W_out.p, sizeof(double) * 9, cudaMemcpyDeviceToHost, st);
-  if (e == cudaSuccess && Ei) e = cudaMemcpyAsync(Ei, h->Ei_out.p, sizeof(double) * (size_t)N, cudaMemcpyDeviceToHost, st);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaError_t e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return h->cuda_fail(e, "device-to-host copy");
+  if (!graphable) return POD_OK;
+  if (!(host_pinned(sys->pos) && host_pinned(c) && host_pinned(E) && host_pinned(Ei) && host_pinned(F) &&
+        host_pinned(W))) {
+    return POD_OK;
+  }
+  if (!(h->hkey_prev == key)) {  // capture on the second call with the same key
+    h->hkey_prev = key;
+    return POD_OK;
+  }
+  if (!h->h_status || !h->status.p) return POD_OK;
+  // capture: copies in, the asynchronous step, copies out, status word out and clear
+  h->drop_host_graph();
+  cudaGraph_t g = nullptr;
+  e = cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    h->hgraph_off = true;
+    return POD_OK;
+  }
+  rc = enqueue_step(0);
+  cudaError_t ec = cudaSuccess;
+  if (rc == POD_OK) {
+    ec = cudaMemcpyAsync(h->h_status, h->status.p, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (ec == cudaSuccess) ec = cudaMemsetAsync(h->status.p, 0, sizeof(int), st);
+  }
+  cudaError_t ee = cudaStreamEndCapture(st, &g);
+  if (rc != POD_OK || ec != cudaSuccess || ee != cudaSuccess || !g) {
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    h->err.clear();
+    h->hgraph_off = true;  // this handle stays on the direct path
+    return POD_OK;
+  }
+  cudaGraphExec_t ex = nullptr;
+  ee = cudaGraphInstantiate(&ex, g, 0);
+  cudaGraphDestroy(g);
+  if (ee != cudaSuccess || !ex) {
+    cudaGetLastError();
+    h->hgraph_off = true;
+    return POD_OK;
+  }
+  h->hgraph = ex;
+  h->hkey = key;
+  h->hkey_valid = true;
   return POD_OK;
 }
 

@@ -50,6 +50,19 @@ struct pod_handle {
   int timing = 0;
   cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
   std::map<int, fastpod::LaunchShape> tuned;  // autotuned launch shapes by size class (floor log2 N)
+  int tune_gen = 0;                            // bumped by every autotune (invalidates host graphs)
+  // host-buffer entry point: one CUDA graph (copies in, step, copies out, status)
+  // replayed while calls repeat with the same buffers, sizes, box and settings
+  struct HostKey {
+    const void* ptr[6];
+    int N, pbc[3], precision, quad, radial, tune_gen;
+    double box[3];
+    bool operator==(const HostKey& o) const;
+  };
+  HostKey hkey{}, hkey_prev{};
+  bool hkey_valid = false, hgraph_off = false;
+  cudaGraphExec_t hgraph = nullptr;
+  void drop_host_graph();
   static int size_class(int N);
   int autotune(const pod_system* sys, const double* c, int reps, cudaStream_t st, fastpod::LaunchShape& best,
                double ms[3]);

@@ -351,3 +351,35 @@ def test_fma_probe(pkg):
         assert 0.1 < tflops < 400.0
     with pytest.raises(pkg.PodError):
         pkg.pod_fma_probe(3, 1, s)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_host_entry_graph_replay(pkg, prec):
+    """Repeated host-buffer calls with the same pinned buffers on a stream replay a
+    captured graph: every call (direct, capturing, replayed) equals the device
+    entry point bit for bit, including after the positions change in place."""
+    import ctypes as C
+    p = synth.params_full()
+    cfg = synth.jitter(synth.bcc(4), 0.1, synth.rng(91))
+    n = cfg.n
+    pod = pkg.POD(p, precision=prec)
+    c = synth.coefficients(pod.M, 92)
+    s = torch.cuda.Stream()
+    pos_t = torch.tensor(np.ascontiguousarray(cfg.pos.T)).pin_memory()
+    c_t = torch.tensor(c).pin_memory()
+    E_t = torch.zeros(1, dtype=torch.float64).pin_memory()
+    Ei_t = torch.zeros(n, dtype=torch.float64).pin_memory()
+    F_t = torch.zeros((3, n), dtype=torch.float64).pin_memory()
+    W_t = torch.zeros(9, dtype=torch.float64).pin_memory()
+    pos_h, c_h, E_h, Ei_h, F_h, W_h = (t.numpy() for t in (pos_t, c_t, E_t, Ei_t, F_t, W_t))
+    sysd = pkg.make_system(pos_h.ctypes.data_as(C.POINTER(C.c_double)), n, cfg.box)
+    rng = synth.rng(93)
+    for call in range(6):
+        if call == 4:  # new positions in the same buffer: the replay must copy them in
+            pos_h[...] = np.ascontiguousarray((cfg.pos + rng.normal(0, 0.02, size=cfg.pos.shape)).T)
+        pkg.pod_energy_forces_host(pod.h, sysd, c_h, E_h, Ei_h, F_h, W_h, stream=s)
+        dev = pod.energy_forces(torch.tensor(pos_h, device=DEV), cfg.box, torch.tensor(c, device=DEV))
+        assert E_h[0] == dev["E"].item(), call
+        assert np.array_equal(F_h.T, dev["F"].cpu().numpy()), call
+        assert np.array_equal(Ei_h, dev["Ei"].cpu().numpy()), call
+        assert np.array_equal(W_h, dev["W"].cpu().numpy().ravel()), call
