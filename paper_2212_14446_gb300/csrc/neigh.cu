@@ -16,7 +16,7 @@ namespace fastpod {
 __global__ void bin_kernel(int N, const double* __restrict__ pos, CellGrid cg, double* __restrict__ wpos,
                            float4* __restrict__ phi, float4* __restrict__ plo, int* __restrict__ cell_count,
                            float4* __restrict__ cell_pos, int* __restrict__ wrapk, int* __restrict__ status,
-                           unsigned long long* __restrict__ facc) {
+                           unsigned long long* __restrict__ facc, int* __restrict__ nbr_count) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
   if (facc) {  // fixed-point force accumulators of this call start at zero
@@ -54,10 +54,105 @@ __global__ void bin_kernel(int N, const double* __restrict__ pos, CellGrid cg, d
   phi[i] = make_float4(h[0], h[1], h[2], __int_as_float(cell));
   plo[i] = make_float4(l[0], l[1], l[2], 0.f);
   const int slot = atomicAdd(&cell_count[cell], 1);
-  if (slot < cg.cap)
+  if (slot < cg.cap) {
     cell_pos[(size_t)cell * cg.cap + slot] = make_float4(h[0], h[1], h[2], __int_as_float(i));
-  else
+  } else {
+    // a full cell: the call is reported and retried with larger cells; the
+    // block-per-cell search never sees this atom, so give it an empty row now
     atomicOr(status, ST_CELL);
+    if (nbr_count) nbr_count[i] = 0;
+  }
+}
+
+constexpr int NEIGH_PREFETCH = 4;
+constexpr unsigned long long BAND_MARK = 1ull << 62;
+
+// Finish atom i's row from the warp's candidate keys (nhit of them, at most
+// keycap stored): decide the band candidates exactly in FP64 (R6) and drop the
+// misses, sort the keys (j, s) ascending, write the row padded with a sentinel,
+// and the count (a count above cap raises ST_NEIGH).
+__device__ __forceinline__ void neigh_finish_row(int N, const CellGrid& cg, const double* __restrict__ wpos,
+                                                 double rc2, int cap, int keycap, int i, int lane, int nhit,
+                                                 unsigned long long* keys, int* __restrict__ nbr_count,
+                                                 int* __restrict__ nbr_j, int* __restrict__ nbr_s,
+                                                 int* __restrict__ status) {
+  __syncwarp();
+  int n = min(nhit, keycap);
+  // decide the band candidates exactly in FP64 (R6): drop the misses
+  {
+    const double xi0 = wpos[i], xi1 = wpos[(size_t)N + i], xi2 = wpos[(size_t)2 * N + i];
+    int dropped = 0;
+    for (int t = lane; t < n; t += 32) {
+      unsigned long long key = keys[t];
+      bool drop = false;
+      if (key & BAND_MARK) {
+        key &= ~BAND_MARK;
+        const int j = (int)(key >> 24);
+        int sx, sy, sz;
+        shift_unpack((int)(key & 0xFFFFFFull), sx, sy, sz);
+        const double ddx = disp_fp64(xi0, wpos[j], sx, cg.L[0]);
+        const double ddy = disp_fp64(xi1, wpos[(size_t)N + j], sy, cg.L[1]);
+        const double ddz = disp_fp64(xi2, wpos[(size_t)2 * N + j], sz, cg.L[2]);
+        const double r2 = __dadd_rn(__dadd_rn(__dmul_rn(ddx, ddx), __dmul_rn(ddy, ddy)), __dmul_rn(ddz, ddz));
+        drop = !(r2 < rc2);
+        keys[t] = drop ? ~0ull : key;
+      }
+      dropped += drop ? 1 : 0;
+    }
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) dropped += __shfl_xor_sync(0xffffffffu, dropped, d);
+    // an overflowed key buffer lost candidates: keep the preliminary count (> cap)
+    // so the call reports it and retries with a larger capacity
+    if (nhit <= keycap) nhit -= dropped;
+    __syncwarp();
+  }
+  if (n <= 32) {
+    // bitonic sort of one key per lane in registers (dropped keys sort last)
+    unsigned long long v = lane < n ? keys[lane] : ~0ull;
+#pragma unroll
+    for (int k = 2; k <= 32; k <<= 1)
+#pragma unroll
+      for (int j = k >> 1; j > 0; j >>= 1) {
+        const unsigned long long w = __shfl_xor_sync(0xffffffffu, v, j);
+        const bool up = (lane & k) == 0;
+        const bool lower = (lane & j) == 0;
+        v = (lower == up) ? (v < w ? v : w) : (v < w ? w : v);
+      }
+    if (lane < n) keys[lane] = v;
+    __syncwarp();
+  } else {
+    int np = 1;
+    while (np < n) np <<= 1;
+    for (int t = n + lane; t < np; t += 32) keys[t] = ~0ull;
+    __syncwarp();
+    for (int k = 2; k <= np; k <<= 1)
+      for (int j = k >> 1; j > 0; j >>= 1) {
+        for (int t = lane; t < np; t += 32) {
+          const int u = t ^ j;
+          if (u > t) {
+            const unsigned long long a = keys[t], b = keys[u];
+            const bool up = (t & k) == 0;
+            if ((a > b) == up) { keys[t] = b; keys[u] = a; }
+          }
+        }
+        __syncwarp();
+      }
+  }
+  // the nhit valid keys lead the sorted array (when nothing overflowed)
+  const int nw = min(min(n, nhit), cap);
+  for (int t = lane; t < cap; t += 32) {
+    if (t < nw) {
+      const unsigned long long key = keys[t];
+      nbr_j[(size_t)i * cap + t] = (int)(key >> 24);
+      nbr_s[(size_t)i * cap + t] = (int)(key & 0xFFFFFFull);
+    } else {
+      nbr_j[(size_t)i * cap + t] = 0x7fffffff;  // sentinel: rows stay sorted to cap
+    }
+  }
+  if (lane == 0) {
+    nbr_count[i] = nhit;
+    if (nhit > cap) atomicOr(status, ST_NEIGH);
+  }
 }
 
 // Warp per atom.  Candidates of the (2S+1)^3 neighbouring cells are tested in
@@ -66,8 +161,6 @@ __global__ void bin_kernel(int N, const double* __restrict__ pos, CellGrid cg, d
 // exact FP64 expression, so the list equals the FP64 definition bit for bit
 // while the scan loop holds no FP64 state.  Hits are sorted by key (j, s) with a
 // bitonic sort (registers for <= 32 keys, else shared memory).
-constexpr int NEIGH_PREFETCH = 4;
-constexpr unsigned long long BAND_MARK = 1ull << 62;
 
 __global__ void __launch_bounds__(NEIGH_MAX_WPB * 32)
     neigh_kernel(int N, CellGrid cg, const double* __restrict__ wpos, const float4* __restrict__ phi,
@@ -162,82 +255,125 @@ __global__ void __launch_bounds__(NEIGH_MAX_WPB * 32)
       }
     }
   }
-  __syncwarp();
-  int n = min(nhit, keycap);
-  // decide the band candidates exactly in FP64 (R6): drop the misses
-  {
-    const double xi0 = wpos[i], xi1 = wpos[(size_t)N + i], xi2 = wpos[(size_t)2 * N + i];
-    int dropped = 0;
-    for (int t = lane; t < n; t += 32) {
-      unsigned long long key = keys[t];
-      bool drop = false;
-      if (key & BAND_MARK) {
-        key &= ~BAND_MARK;
-        const int j = (int)(key >> 24);
-        int sx, sy, sz;
-        shift_unpack((int)(key & 0xFFFFFFull), sx, sy, sz);
-        const double ddx = disp_fp64(xi0, wpos[j], sx, cg.L[0]);
-        const double ddy = disp_fp64(xi1, wpos[(size_t)N + j], sy, cg.L[1]);
-        const double ddz = disp_fp64(xi2, wpos[(size_t)2 * N + j], sz, cg.L[2]);
-        const double r2 = __dadd_rn(__dadd_rn(__dmul_rn(ddx, ddx), __dmul_rn(ddy, ddy)), __dmul_rn(ddz, ddz));
-        drop = !(r2 < rc2);
-        keys[t] = drop ? ~0ull : key;
-      }
-      dropped += drop ? 1 : 0;
-    }
+  neigh_finish_row(N, cg, wpos, rc2, cap, keycap, i, lane, nhit, keys, nbr_count, nbr_j, nbr_s, status);
+}
+
+// Block per cell, for a search depth of one cell in every direction: the
+// candidates of the 27 neighbouring (cell, image) pairs are staged once in
+// shared memory as image-shifted FP32 positions with their shift codes (one
+// coalesced copy per neighbouring cell, shared by all of the cell's atoms), then
+// each warp takes one of the cell's atoms and tests every candidate with lanes
+// over candidates (full lanes, no per-cell imbalance).  The row is finished as
+// in the warp-per-atom kernel (FP64 band decision, sort, sentinel padding), so
+// the list is the same bit for bit.  Atoms that did not fit in their cell are
+// given an empty row by the bin kernel (and the call is retried).
+__global__ void __launch_bounds__(NEIGH_MAX_WPB * 32)
+    neigh_cell_kernel(int N, CellGrid cg, const double* __restrict__ wpos, const int* __restrict__ cell_count,
+                      const float4* __restrict__ cell_pos, double rc2, float rc2_lo, float rc2_hi, int cap,
+                      int keycap, int* __restrict__ nbr_count, int* __restrict__ nbr_j, int* __restrict__ nbr_s,
+                      int* __restrict__ status) {
+  extern __shared__ __align__(16) unsigned char csm[];
+  __shared__ int soff[28], scell[27], scode[27];
+  __shared__ float spx[27], spy[27], spz[27];
+  const int ccap = 27 * cg.cap;
+  float4* cand = reinterpret_cast<float4*>(csm);
+  int* ccode = reinterpret_cast<int*>(cand + ccap);
+  unsigned long long* kbuf =
+      reinterpret_cast<unsigned long long*>(csm + ((sizeof(float4) + sizeof(int)) * (size_t)ccap + 15) / 16 * 16);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  const int cell = blockIdx.x;
+  const int zero = shift_pack(0, 0, 0);
+  if (warp == 0) {
+    const int ci[3] = {cell % cg.nc[0], (cell / cg.nc[0]) % cg.nc[1], cell / (cg.nc[0] * cg.nc[1])};
+    int cnt = 0, tcell = 0, code = zero;
+    float px = 0.f, py = 0.f, pz = 0.f;
+    if (lane < 27) {
+      const int oc[3] = {lane % 3 - 1, (lane / 3) % 3 - 1, lane / 9 - 1};
+      int tc[3], sh[3];
+      bool ok = true;
 #pragma unroll
-    for (int d = 16; d > 0; d >>= 1) dropped += __shfl_xor_sync(0xffffffffu, dropped, d);
-    // an overflowed key buffer lost candidates: keep the preliminary count (> cap)
-    // so the call reports it and retries with a larger capacity
-    if (nhit <= keycap) nhit -= dropped;
-    __syncwarp();
-  }
-  if (n <= 32) {
-    // bitonic sort of one key per lane in registers (dropped keys sort last)
-    unsigned long long v = lane < n ? keys[lane] : ~0ull;
-#pragma unroll
-    for (int k = 2; k <= 32; k <<= 1)
-#pragma unroll
-      for (int j = k >> 1; j > 0; j >>= 1) {
-        const unsigned long long w = __shfl_xor_sync(0xffffffffu, v, j);
-        const bool up = (lane & k) == 0;
-        const bool lower = (lane & j) == 0;
-        v = (lower == up) ? (v < w ? v : w) : (v < w ? w : v);
-      }
-    if (lane < n) keys[lane] = v;
-    __syncwarp();
-  } else {
-    int np = 1;
-    while (np < n) np <<= 1;
-    for (int t = n + lane; t < np; t += 32) keys[t] = ~0ull;
-    __syncwarp();
-    for (int k = 2; k <= np; k <<= 1)
-      for (int j = k >> 1; j > 0; j >>= 1) {
-        for (int t = lane; t < np; t += 32) {
-          const int u = t ^ j;
-          if (u > t) {
-            const unsigned long long a = keys[t], b = keys[u];
-            const bool up = (t & k) == 0;
-            if ((a > b) == up) { keys[t] = b; keys[u] = a; }
-          }
+      for (int d = 0; d < 3; ++d) {
+        int t = ci[d] + oc[d];
+        int sd = 0;
+        if (cg.pbc[d]) {
+          sd = t < 0 ? -1 : (t >= cg.nc[d] ? 1 : 0);
+          t -= sd * cg.nc[d];
+        } else if (t < 0 || t >= cg.nc[d]) {
+          ok = false;
         }
-        __syncwarp();
+        tc[d] = t;
+        sh[d] = sd;
       }
+      if (ok) {
+        tcell = (tc[2] * cg.nc[1] + tc[1]) * cg.nc[0] + tc[0];
+        cnt = min(cell_count[tcell], cg.cap);
+        code = shift_pack(sh[0], sh[1], sh[2]);
+        px = (float)sh[0] * cg.Lf[0];
+        py = (float)sh[1] * cg.Lf[1];
+        pz = (float)sh[2] * cg.Lf[2];
+      }
+    }
+    int x = cnt;  // inclusive prefix sum over the stencil entries
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane < 27) {
+      soff[lane] = x - cnt;
+      scell[lane] = tcell;
+      scode[lane] = code;
+      spx[lane] = px;
+      spy[lane] = py;
+      spz[lane] = pz;
+    }
+    if (lane == 26) soff[27] = x;
   }
-  // the nhit valid keys lead the sorted array (when nothing overflowed)
-  const int nw = min(min(n, nhit), cap);
-  for (int t = lane; t < cap; t += 32) {
-    if (t < nw) {
-      const unsigned long long key = keys[t];
-      nbr_j[(size_t)i * cap + t] = (int)(key >> 24);
-      nbr_s[(size_t)i * cap + t] = (int)(key & 0xFFFFFFull);
-    } else {
-      nbr_j[(size_t)i * cap + t] = 0x7fffffff;  // sentinel: rows stay sorted to cap
+  __syncthreads();
+  const int ncand = soff[27];
+  for (int e = warp; e < 27; e += nwarps) {
+    const int o0 = soff[e], ne = soff[e + 1] - o0;
+    const float4* src = cell_pos + (size_t)scell[e] * cg.cap;
+    const float ex = spx[e], ey = spy[e], ez = spz[e];
+    const int ecode = scode[e];
+    for (int t = lane; t < ne; t += 32) {
+      const float4 q = src[t];
+      cand[o0 + t] = make_float4(q.x + ex, q.y + ey, q.z + ez, q.w);
+      ccode[o0 + t] = ecode;
     }
   }
-  if (lane == 0) {
-    nbr_count[i] = nhit;
-    if (nhit > cap) atomicOr(status, ST_NEIGH);
+  __syncthreads();
+  // the cell's own atoms are the centre stencil entry (offset 0, image 0)
+  const int own0 = soff[13], own_n = soff[14] - soff[13];
+  unsigned long long* keys = kbuf + (size_t)warp * keycap;
+  for (int k = warp; k < own_n; k += nwarps) {
+    const float4 qi = cand[own0 + k];
+    const int i = __float_as_int(qi.w);
+    int nhit = 0;
+    for (int f0 = 0; f0 < ncand; f0 += 32) {
+      const int f = f0 + lane;
+      bool hit = false;
+      unsigned long long key = 0;
+      if (f < ncand) {
+        const float4 q = cand[f];
+        const int j = __float_as_int(q.w);
+        const int code = ccode[f];
+        if (!(j == i && code == zero)) {
+          const float dx = q.x - qi.x, dy = q.y - qi.y, dz = q.z - qi.z;
+          const float r2f = dx * dx + dy * dy + dz * dz;
+          hit = r2f < rc2_hi;
+          key = ((unsigned long long)j << 24) | (unsigned long long)code | (r2f < rc2_lo ? 0ull : BAND_MARK);
+        }
+      }
+      const unsigned m = __ballot_sync(0xffffffffu, hit);
+      if (hit) {
+        const int pos = nhit + __popc(m & ((1u << lane) - 1u));
+        if (pos < keycap) keys[pos] = key;
+      }
+      nhit += __popc(m);
+    }
+    neigh_finish_row(N, cg, wpos, rc2, cap, keycap, i, lane, nhit, keys, nbr_count, nbr_j, nbr_s, status);
+    __syncwarp();
   }
 }
 
@@ -280,10 +416,10 @@ __global__ void export_neighbors_kernel(int N, int cap, const int* __restrict__ 
 // ------------------------------------------------------------ launchers
 cudaError_t launch_bin(int N, const double* pos, const CellGrid& cg, double* wpos, float4* phi, float4* plo,
                        int* cell_count, float4* cell_pos, int* status, cudaStream_t st, int* wrapk,
-                       unsigned long long* facc) {
+                       unsigned long long* facc, int* nbr_count) {
   const int tb = 64;  // small blocks spread the FP64 work of small systems over all SMs
   bin_kernel<<<(N + tb - 1) / tb, tb, 0, st>>>(N, pos, cg, wpos, phi, plo, cell_count, cell_pos, wrapk, status,
-                                               facc);
+                                               facc, nbr_count);
   return cudaGetLastError();
 }
 
@@ -370,6 +506,21 @@ cudaError_t launch_neigh(int N, const CellGrid& cg, const double* wpos, const fl
   const float rc2_hi = (float)(rc2 + band);
   int keycap = 32;
   while (keycap < cap) keycap <<= 1;
+  const bool s1 = cg.S[0] == 1 && cg.S[1] == 1 && cg.S[2] == 1;
+  const size_t cell_smem = ((sizeof(float4) + sizeof(int)) * 27 * (size_t)cg.cap + 15) / 16 * 16 +
+                           (size_t)wpb * keycap * sizeof(unsigned long long);
+  if (s1 && cell_smem <= 96 * 1024) {
+    static size_t cgranted = 48 * 1024;
+    if (cell_smem > cgranted) {
+      cudaError_t e = cudaFuncSetAttribute(neigh_cell_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)cell_smem);
+      if (e != cudaSuccess) return e;
+      cgranted = cell_smem;
+    }
+    neigh_cell_kernel<<<cg.ncells, wpb * 32, cell_smem, st>>>(N, cg, wpos, cell_count, cell_pos, rc2, rc2_lo,
+                                                              rc2_hi, cap, keycap, nbr_count, nbr_j, nbr_s, status);
+    return cudaGetLastError();
+  }
   const size_t smem = neigh_smem_bytes(keycap, wpb);
   static size_t granted = 48 * 1024;
   if (smem > granted) {

@@ -703,7 +703,7 @@ int pod_handle::build_neighbors(const double* pos, Plan& pl, bool need_rev, cuda
   if (e != cudaSuccess) return cuda_fail(e, "cell count clear");
   if ((rc_ = ensure(wrapk, sizeof(int) * 3 * (size_t)N, "wrap offsets"))) return rc_;
   e = launch_bin(N, pos, pl.cg, (double*)wpos.p, (float4*)phi.p, (float4*)plo.p, (int*)cell_count.p,
-                 (float4*)cell_atoms.p, (int*)status.p, st, (int*)wrapk.p, facc_zero);
+                 (float4*)cell_atoms.p, (int*)status.p, st, (int*)wrapk.p, facc_zero, (int*)nbr_count.p);
   if (e != cudaSuccess) return cuda_fail(e, "bin kernel");
   e = launch_neigh(N, pl.cg, (const double*)wpos.p, (const float4*)phi.p, (const float4*)plo.p,
                    (const int*)cell_count.p, (const float4*)cell_atoms.p, rlist(), pl.cap, (int*)nbr_count.p,

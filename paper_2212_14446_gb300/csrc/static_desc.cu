@@ -141,7 +141,8 @@ extern "C" int pod_descriptors_static(pod_handle* h, const pod_system* sys, doub
   if (e == cudaSuccess) e = cudaMemsetAsync(cellc, 0, sizeof(int) * (size_t)ncells, st);
   if (e != cudaSuccess) return h->cuda_fail(e, "static scratch clear");
   e = launch_bin(N, sys->pos, pl.cg, reinterpret_cast<double*>(base + OFF_WPOS), reinterpret_cast<float4*>(base + OFF_PHI),
-                 reinterpret_cast<float4*>(base + OFF_PLO), cellc, reinterpret_cast<float4*>(base + OFF_CELLA), status, st);
+                 reinterpret_cast<float4*>(base + OFF_PLO), cellc, reinterpret_cast<float4*>(base + OFF_CELLA), status, st,
+                 nullptr, nullptr, reinterpret_cast<int*>(base + OFF_CNT));
   if (e != cudaSuccess) return h->cuda_fail(e, "bin kernel");
   e = launch_neigh(N, pl.cg, reinterpret_cast<const double*>(base + OFF_WPOS),
                    reinterpret_cast<const float4*>(base + OFF_PHI), reinterpret_cast<const float4*>(base + OFF_PLO),
