@@ -509,7 +509,8 @@ cudaError_t launch_neigh(int N, const CellGrid& cg, const double* wpos, const fl
   const bool s1 = cg.S[0] == 1 && cg.S[1] == 1 && cg.S[2] == 1;
   const size_t cell_smem = ((sizeof(float4) + sizeof(int)) * 27 * (size_t)cg.cap + 15) / 16 * 16 +
                            (size_t)wpb * keycap * sizeof(unsigned long long);
-  if (s1 && cell_smem <= 96 * 1024) {
+  // block per cell when there are enough cells to fill the GPU (two per SM)
+  if (s1 && cg.ncells >= 2 * 152 && cell_smem <= 96 * 1024) {
     static size_t cgranted = 48 * 1024;
     if (cell_smem > cgranted) {
       cudaError_t e = cudaFuncSetAttribute(neigh_cell_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
