@@ -95,7 +95,7 @@ def lib():
                 "pod_set_skin": (C.c_int, [H, C.c_double]),
                 "pod_md_step": (C.c_int, [H, S, dp, dp, dp, dp, C.c_double, C.c_double, dp, vp]),
                 "pod_energy_forces": (C.c_int, [H, S, dp, dp, dp, dp, dp, vp]),
-                "pod_energy_forces_host": (C.c_int, [H, S, dp, dp, dp, dp, dp, vp]),
+                "pod_energy_forces_host": (C.c_int, [H, S, vp, vp, vp, vp, vp, vp]),
                 "pod_fit": (C.c_int, [H, S, dp, dp, C.POINTER(pod_fit_opts), dp, dp, dp]),
                 "pod_fit_normal": (C.c_int, [H, S, dp, dp, C.POINTER(pod_fit_opts), dp, dp]),
                 "pod_fit_solve": (C.c_int, [H, dp, dp, dp]),
@@ -215,8 +215,9 @@ def pod_autotune(h, sys, c, reps=5, stream=None):
 
 
 def pod_energy_forces_host(h, sys, c, E, Ei=None, F=None, W=None, stream=None):
+    """Host float64 arrays (C-contiguous) in and out; the addresses are passed as is."""
     def hp(a):
-        return None if a is None else a.ctypes.data_as(C.POINTER(C.c_double))
+        return None if a is None else a.ctypes.data
     _check(h, lib().pod_energy_forces_host(h, C.byref(sys), hp(c), hp(E), hp(Ei), hp(F), hp(W),
                                            _stream(stream)))
 
