@@ -278,8 +278,9 @@ int pod_set_quadratic(pod_handle* h, const double* beta);
  * Times the three phases of pod_energy_forces on `sys` (one configuration,
  * device positions as for pod_energy_forces; c: device [M]) for a small set of
  * candidate launch shapes -- warps per block of the neighbour search {2, 4, 8},
- * of the fused atom kernel {1, 2, 4}, and warps per block x blocks per SM of the
- * gather {16x3, 16x2, 8x6, 8x4, 4x12} -- with CUDA events on `stream`, `reps`
+ * of the fused atom kernel {1, 2, 4} (FP32 table path: each with and without R'
+ * staged in shared memory), and, on the FP64 path, warps per block x blocks per
+ * SM of the gather {16x3, 16x2, 8x6, 8x4, 4x12} -- with CUDA events on `stream`, `reps`
  * timed calls each (after one warm-up call), and keeps the fastest per phase.
  * The result is stored in the handle for the system's size class (floor(log2
  * N)) and used by later calls on systems of that class; the other classes keep
@@ -287,8 +288,10 @@ int pod_set_quadratic(pod_handle* h, const double* beta);
  * for the rounding order of the energy and virial sums.  Synchronous (calls
  * pod_energy_forces about 15 x (reps + 1) times); not for use during stream
  * capture.
- *   shape (host int[4], or NULL): neighbour wpb, atom wpb, gather wpb, gather
- *   blocks per SM.  ms (host double[3], or NULL): mean times of the neighbour,
+ *   shape (host int[5], or NULL): neighbour wpb, atom wpb, gather wpb, gather
+ *   blocks per SM, and 1 when the atom kernel stages R' in shared memory (FP32
+ *   table path; a candidate of the atom-kernel search) instead of re-evaluating
+ *   it in the adjoint pass.  ms (host double[3], or NULL): mean times of the neighbour,
  *   atom and gather phases with the chosen shape.
  * Errors as pod_energy_forces; POD_EINVAL for a batch. */
 int pod_autotune(pod_handle* h, const pod_system* sys, const double* c, int reps, int* shape, double* ms,

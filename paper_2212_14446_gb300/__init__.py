@@ -207,8 +207,9 @@ def pod_energy_forces(h, sys, c, E, Ei=None, F=None, W=None, stream=None):
 
 
 def pod_autotune(h, sys, c, reps=5, stream=None):
-    """Returns ([neigh wpb, atom wpb, gather wpb, gather blocks per SM], [ms neigh, atom, gather])."""
-    shape = (C.c_int * 4)()
+    """Returns ([neigh wpb, atom wpb, gather wpb, gather blocks per SM, atom R' staging],
+    [ms neigh, atom, gather])."""
+    shape = (C.c_int * 5)()
     ms = (C.c_double * 3)()
     _check(h, lib().pod_autotune(h, C.byref(sys), _dptr(c), int(reps), shape, ms, _stream(stream)))
     return list(shape), list(ms)
@@ -412,7 +413,7 @@ class POD:
         c = c.to(device=x.device, dtype=torch.float64).contiguous()
         shape, ms = pod_autotune(self.h, self.system(x, box, pbc), c, reps, stream)
         return {"neigh_wpb": shape[0], "atom_wpb": shape[1], "gather_wpb": shape[2], "gather_bps": shape[3],
-                "ms": ms}
+                "atom_rp": shape[4], "ms": ms}
 
     # -- batches of configurations --------------------------------------
     @staticmethod

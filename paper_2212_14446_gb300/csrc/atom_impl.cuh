@@ -104,7 +104,7 @@ __device__ __forceinline__ void pair_pass(const AtomArgs<T>& p, const AtomLayout
       vq.w = T(0);
       sV[a * lay.GA + jj] = vq;
     }
-    if (!p.rad.tab || TANGENT) {  // keep R' for the adjoint / tangent pass
+    if (!p.rad.tab || TANGENT || p.keep_rp) {  // keep R' for the adjoint / tangent pass
       T* Rprow = sRp + a * lay.SA + jj * lay.KS;
 #pragma unroll
       for (int k = 0; k < KT; ++k) {
@@ -552,8 +552,8 @@ __global__ void __launch_bounds__(ATOM_MAX_WPB * 32, atom_min_blocks<T, MODE, KT
       const int jj = f - base, slot = ch * CH + jj, i = atom0 + a;
       const Q4<T> u = geo[a * lay.GA + jj];
       T Rv[KT], Rpv[KT];
-      if (p.rad.tab) {
-        // tabulated basis: re-evaluating R, R' is cheaper than staging R'
+      if (p.rad.tab && !p.keep_rp) {
+        // tabulated basis: re-evaluate R, R' (or read them staged, keep_rp)
         if (u.w > p.rad.r_in && u.w < p.rmask) {
           radial_pair<T, KT>(p.rad, u.w, Rv, Rpv);
         } else {
@@ -769,7 +769,7 @@ static cudaError_t dispatch_generic(const AtomArgs<T>& p, const AtomLayout& lay,
 // (K = 3, P = 3, no 4-body; K = 6, P = 4, 4-body), generic K <= 16 otherwise.
 template <typename T>
 cudaError_t launch_atom_t(int mode, const AtomArgs<T>& p, int PA, bool has4, cudaStream_t st) {
-  const AtomLayout lay = make_layout<T>(p.K, PA, p.rad.tab != nullptr, mode == 2, mode == 4 ? p.M : 0);
+  const AtomLayout lay = make_layout<T>(p.K, PA, p.rad.tab != nullptr && !p.keep_rp, mode == 2, mode == 4 ? p.M : 0);
   const bool spec6 = (p.K == 6 && PA == 4 && has4);
   const bool spec3 = (p.K == 3 && PA == 3 && !has4);
   if (mode == 2) {

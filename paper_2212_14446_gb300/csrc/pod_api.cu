@@ -302,12 +302,19 @@ int pod_handle::autotune(const pod_system* sys, const double* c, int reps, cudaS
   static const int gather_c[][2] = {{16, 3}, {16, 2}, {8, 6}, {8, 4}, {4, 12}};
   double best_atom = 1e30, best_neigh = 1e30, best_gather = 1e30;
   LaunchShape win = cur;
-  for (int a : atom_c) {
-    LaunchShape s = win;
-    s.atom_wpb = a;
-    if ((rc_ = measure(s, t))) break;
-    if (t[1] < best_atom) { best_atom = t[1]; win.atom_wpb = a; }
-  }
+  for (int a : atom_c)
+    for (int rp = 0; rp < 2 && !rc_; ++rp) {
+      if (rp && (precision != POD_MIXED || radial_mode != 0)) break;  // R' staging: table path only
+      LaunchShape s = win;
+      s.atom_wpb = a;
+      s.atom_rp = rp;
+      if ((rc_ = measure(s, t))) break;
+      if (t[1] < best_atom) {
+        best_atom = t[1];
+        win.atom_wpb = a;
+        win.atom_rp = rp;
+      }
+    }
   for (int n = 0; !rc_ && n < 3; ++n) {
     LaunchShape s = win;
     s.neigh_wpb = neigh_c[n];
@@ -493,6 +500,7 @@ int pod_autotune(pod_handle* h, const pod_system* sys, const double* c, int reps
     shape[1] = best.atom_wpb;
     shape[2] = best.gather_wpb;
     shape[3] = best.gather_bps;
+    shape[4] = best.atom_rp;
   }
   if (ms)
     for (int k = 0; k < 3; ++k) ms[k] = t[k];
@@ -751,6 +759,7 @@ void pod_handle::fill_args(AtomArgs<T>& a, const Plan& pl) {
   a.vdir = vdir_cur;
   a.rmask = mask_radius<T>(skin > 0 ? P.r_cut : 0.0);
   a.wpb = pl.shape.atom_wpb;
+  a.keep_rp = pl.shape.atom_rp;
 }
 
 // Cubic Hermite pieces of R_k on TAB_N equal intervals of (r_in, r_cut), from

@@ -16,6 +16,7 @@ struct LaunchShape {
   int neigh_wpb = WPB_NEIGH;
   int gather_wpb = 16;
   int gather_bps = 3;
+  int atom_rp = 0;  // table path: stage R' in shared memory in the pair pass (else re-evaluate it)
 };
 
 struct AtomLayout {
@@ -32,6 +33,7 @@ template <typename T>
 struct AtomArgs {
   int N, cap;
   int wpb;              // warps per block of the launch (0: default)
+  int keep_rp;          // table path: R' staged in shared memory for the adjoint pass
   const int* nbr_count;
   const int* nbr_j;
   const int* nbr_s;
