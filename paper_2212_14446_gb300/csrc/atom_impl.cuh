@@ -725,14 +725,10 @@ static cudaError_t launch_one(const AtomArgs<T>& p, const AtomLayout& lay, cudaS
   const int wpb = p.wpb > 0 ? p.wpb : WPB_ATOM;
   if (wpb > ATOM_MAX_WPB) return cudaErrorInvalidValue;
   const size_t smem = (size_t)wpb * lay.warp_bytes;
-  // raise the dynamic shared-memory limit once per instantiation and size (not
-  // a stream operation, so it stays out of captured graphs after the first call)
-  static size_t granted = 0;
-  if (smem > granted) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    granted = smem;
-  }
+  // raise the dynamic shared-memory limit once per instantiation, device and size
+  // (not a stream operation, so it stays out of captured graphs after the first call)
+  static size_t granted[64] = {};
+  if (cudaError_t e = grant_smem((const void*)kern, smem, granted)) return e;
   const int atoms_per_block = wpb * lay.A;
   const int grid = (p.N + atoms_per_block - 1) / atoms_per_block;
   if (grid > 0) kern<<<grid, wpb * 32, smem, st>>>(p, lay);

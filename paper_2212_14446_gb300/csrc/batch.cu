@@ -216,12 +216,8 @@ cudaError_t launch_batch_neigh(int N, const int* cfg_of, const CfgBox* cbox, con
   int keycap = 32;
   while (keycap < cap) keycap <<= 1;
   const size_t smem = (size_t)WPB_NEIGH * keycap * sizeof(unsigned long long);
-  static size_t granted = 48 * 1024;
-  if (smem > granted) {
-    cudaError_t e = cudaFuncSetAttribute(batch_neigh_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    granted = smem;
-  }
+  static size_t granted[64] = {};
+  if (cudaError_t e = grant_smem((const void*)batch_neigh_kernel, smem, granted)) return e;
   batch_neigh_kernel<<<(N + WPB_NEIGH - 1) / WPB_NEIGH, WPB_NEIGH * 32, smem, st>>>(
       N, cfg_of, cbox, wpos, phi, rc2, (float)(rc2 - band), (float)(rc2 + band), cap, keycap, nbr_count, nbr_j,
       nbr_s, status);

@@ -511,24 +511,15 @@ cudaError_t launch_neigh(int N, const CellGrid& cg, const double* wpos, const fl
                            (size_t)wpb * keycap * sizeof(unsigned long long);
   // block per cell when there are enough cells to fill the GPU (two per SM)
   if (s1 && cg.ncells >= 2 * 152 && cell_smem <= 96 * 1024) {
-    static size_t cgranted = 48 * 1024;
-    if (cell_smem > cgranted) {
-      cudaError_t e = cudaFuncSetAttribute(neigh_cell_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)cell_smem);
-      if (e != cudaSuccess) return e;
-      cgranted = cell_smem;
-    }
+    static size_t cgranted[64] = {};
+    if (cudaError_t e = grant_smem((const void*)neigh_cell_kernel, cell_smem, cgranted)) return e;
     neigh_cell_kernel<<<cg.ncells, wpb * 32, cell_smem, st>>>(N, cg, wpos, cell_count, cell_pos, rc2, rc2_lo,
                                                               rc2_hi, cap, keycap, nbr_count, nbr_j, nbr_s, status);
     return cudaGetLastError();
   }
   const size_t smem = neigh_smem_bytes(keycap, wpb);
-  static size_t granted = 48 * 1024;
-  if (smem > granted) {
-    cudaError_t e = cudaFuncSetAttribute(neigh_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    granted = smem;
-  }
+  static size_t granted[64] = {};
+  if (cudaError_t e = grant_smem((const void*)neigh_kernel, smem, granted)) return e;
   neigh_kernel<<<(N + wpb - 1) / wpb, wpb * 32, smem, st>>>(
       N, cg, wpos, phi, plo, cell_count, cell_pos, rc2, rc2_lo, rc2_hi, cap, keycap, nbr_count, nbr_j, nbr_s,
       status);

@@ -10,6 +10,21 @@
 namespace fastpod {
 
 // Shared-memory layout of one warp in the atom kernels (byte offsets).
+// Raises a kernel's dynamic shared-memory limit when a launch needs more than the
+// default 48 KB.  The attribute belongs to the current device, so the largest
+// size granted is remembered per device (granted: [64]); it is not a stream
+// operation.
+inline cudaError_t grant_smem(const void* kern, size_t smem, size_t* granted) {
+  if (smem <= 48 * 1024) return cudaSuccess;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev >= 0 && dev < 64 && smem <= granted[dev]) return cudaSuccess;
+  e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess && dev >= 0 && dev < 64) granted[dev] = smem;
+  return e;
+}
+
 // Launch shape of the step's kernels (warps per block; gather blocks per SM).
 struct LaunchShape {
   int atom_wpb = WPB_ATOM;
