@@ -97,7 +97,10 @@ typedef struct {
  * eigenvectors sorted by decreasing eigenvalue, each with its largest entry
  * positive, scaled by 1/sqrt(lambda) so R_k has unit L2 norm; Section 2.2,
  * Eq. 12) unless params->Q is given, and the angular tables (Table 3-5).
- * *out receives the handle.  Errors: POD_EINVAL, POD_ENOMEM, POD_ECUDA. */
+ * *out receives the handle.  The handle belongs to the CUDA device current at
+ * this call (its workspace is allocated there): call it with that device
+ * current; a call with another device current fails with POD_EINVAL.
+ * Errors: POD_EINVAL, POD_ENOMEM, POD_ECUDA. */
 int pod_create(const pod_params* params, pod_handle** out);
 
 /* Frees the handle, its device tables and workspace.  NULL is allowed. */

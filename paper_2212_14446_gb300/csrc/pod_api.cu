@@ -367,6 +367,10 @@ int pod_create(const pod_params* prm, pod_handle** out) {
   if (!prm) return POD_EINVAL;
   pod_handle* h = new (std::nothrow) pod_handle();
   if (!h) return POD_ENOMEM;
+  if (cudaGetDevice(&h->device) != cudaSuccess) {
+    cudaGetLastError();
+    h->device = -1;
+  }
   auto bad = [&](const char* msg) {
     h->err = msg;
     int code = POD_EINVAL;
@@ -869,6 +873,11 @@ int pod_handle::validate_system(const pod_system* sys) {
   if (!sys->pos) return fail(POD_EINVAL, "positions are NULL");
   if (sys->n_configs > 1 && (!sys->atom_offs || !sys->boxes))
     return fail(POD_EINVAL, "a batch needs atom_offs and boxes");
+  if (device >= 0) {
+    int cur = -1;
+    if (cudaGetDevice(&cur) == cudaSuccess && cur != device)
+      return fail(POD_EINVAL, "the handle was created on device %d but device %d is current", device, cur);
+  }
   return POD_OK;
 }
 

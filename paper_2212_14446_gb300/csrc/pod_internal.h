@@ -43,6 +43,7 @@ struct pod_handle {
   fastpod::RadialConst<double> rad64{};
   std::string err;
   int sync = 1;
+  int device = -1;  // the device current at pod_create (its workspace lives there)
   int retries = 0;
   int last_status = 0;
   int cap_nbr = 0, cap_cell = 0;  // grown after overflows
