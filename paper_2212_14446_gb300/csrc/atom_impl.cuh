@@ -439,6 +439,42 @@ __global__ void __launch_bounds__(ATOM_MAX_WPB * 32, atom_min_blocks<T, MODE, KT
       }
     }
     __syncwarp();
+    if constexpr (KT != MAXK) {
+      // dE_i/dD = c + S D_i for the warp's atoms at once: lanes over columns,
+      // each S element loaded once per warp and applied to every atom (the
+      // descriptors are shared-memory broadcasts)
+      constexpr int AW = 32 / KT;
+      const T* sD0 = reinterpret_cast<const T*>(wb + lay.off_D);
+      T* sCe = reinterpret_cast<T*>(wb + lay.off_D) + AW * lay.MS;
+      for (int col0 = 0; col0 < p.M; col0 += 32) {
+        const int col = col0 + lane;
+        if (col < p.M) {
+          T acc[AW];
+#pragma unroll
+          for (int a = 0; a < AW; ++a) acc[a] = T(0);
+          const int M4 = p.M & ~3;
+          for (int n = 0; n < M4; n += 4) {
+            // S is symmetric: rows n..n+3 at column col, coalesced over lanes
+            const T s0 = p.qbeta[(size_t)n * p.M + col], s1 = p.qbeta[(size_t)(n + 1) * p.M + col];
+            const T s2 = p.qbeta[(size_t)(n + 2) * p.M + col], s3 = p.qbeta[(size_t)(n + 3) * p.M + col];
+#pragma unroll
+            for (int a = 0; a < AW; ++a) {
+              const Q4<T> d = *reinterpret_cast<const Q4<T>*>(sD0 + a * lay.MS + n);
+              acc[a] = fma(s0, d.x, fma(s1, d.y, fma(s2, d.z, fma(s3, d.w, acc[a]))));
+            }
+          }
+          for (int n = M4; n < p.M; ++n) {
+            const T sv = p.qbeta[(size_t)n * p.M + col];
+#pragma unroll
+            for (int a = 0; a < AW; ++a) acc[a] = fma(sv, sD0[a * lay.MS + n], acc[a]);
+          }
+          const T cc = sc[col];
+#pragma unroll
+          for (int a = 0; a < AW; ++a) sCe[a * lay.MS + col] = cc + acc[a];
+        }
+      }
+      __syncwarp();
+    }
   }
 
   // ---------------- energy and adjoint a = dE_i/dB_m  (Eq. 26c generalised)
@@ -462,10 +498,14 @@ __global__ void __launch_bounds__(ATOM_MAX_WPB * 32, atom_min_blocks<T, MODE, KT
       if (MODE == 4) {
         const T* Da = reinterpret_cast<const T*>(wb + lay.off_D) + a_loc * lay.MS;
         auto ceff = [&](int col) {
-          const T* row = p.qbeta + (size_t)col * p.M;
-          T s = c[col];
-          for (int n = 0; n < p.M; ++n) s = fma(row[n], Da[n], s);
-          return s;
+          if constexpr (KT != MAXK) {  // formed above for the whole warp
+            return reinterpret_cast<const T*>(wb + lay.off_D)[(32 / KT) * lay.MS + a_loc * lay.MS + col];
+          } else {
+            const T* row = p.qbeta + (size_t)col * p.M;
+            T s = c[col];
+            for (int n = 0; n < p.M; ++n) s = fma(row[n], Da[n], s);
+            return s;
+          }
         };
         if (m < p.K2) {
           Elin = fma(c2, Da[1 + m], Elin);
@@ -712,9 +752,9 @@ AtomLayout make_layout(int K, int PA, bool table, bool tangent = false, int quad
   off = al(off + sizeof(int) * 32, 32);
   L.off_V = off;
   if (tangent) off = al(off + sizeof(Q4<T>) * (size_t)L.A * L.GA, 32);
-  L.off_D = off;  // quadratic model: descriptors of the warp's atoms
-  L.MS = quadM > 0 ? (quadM | 1) : 0;
-  off = al(off + sizeof(T) * (size_t)L.A * L.MS, 32);
+  L.off_D = off;  // quadratic model: descriptors of the warp's atoms, then dE/dD
+  L.MS = quadM > 0 ? (quadM + 3) / 4 * 4 : 0;  // rows of 16-byte multiples (float4 reads)
+  off = al(off + 2 * sizeof(T) * (size_t)L.A * L.MS, 32);
   L.warp_bytes = off;
   return L;
 }
