@@ -162,3 +162,33 @@ def test_fit_stages_equal_single_call(pkg):
     assert np.array_equal(c, c2)
     assert ne == len(cfgs) and nf == 3 * sum(cf.n for cf in cfgs)
     assert se / ne == pytest.approx(maeE, rel=1e-14) and sf / nf == pytest.approx(maeF, rel=1e-14)
+
+
+def test_shards_one_after_another_equal_the_whole_fit(pkg):
+    """The sharded fit (one configuration share per GPU, normal equations summed
+    by an all-reduce) run as three shards one after another on this GPU: the
+    summed G and r equal the unsharded ones to rounding, and the coefficients
+    solved from them equal the one-call fit's."""
+    from paper_2212_14446_gb300.parallel import shard_indices
+    p = synth.params_full()
+    o = oracle.Oracle(p)
+    cfgs = training_configs(15, replica=6, max_atoms=30)
+    cstar = synth.coefficients(o.M, 31)
+    E_ref, F_ref = _labels(o, cfgs, cstar, noise=1.0, seed=9)
+    pod = pkg.POD(p, precision="fp64", Q=o.Q)
+    G_all, r_all = pod.fit_normal(cfgs, E_ref, F_ref)
+    c_all, _, _ = pod.fit(cfgs, E_ref, F_ref)
+    G = np.zeros_like(G_all)
+    r = np.zeros_like(r_all)
+    for rank in range(3):
+        idx = shard_indices(len(cfgs), rank, 3)
+        Gs, rs = pod.fit_normal([cfgs[i] for i in idx], E_ref[idx], [F_ref[i] for i in idx],
+                                gamma=1e-12 if rank == 0 else 0.0)
+        G += Gs
+        r += rs
+    scale = np.max(np.abs(G_all))
+    assert np.max(np.abs(G - G_all)) <= 1e-12 * scale
+    assert np.max(np.abs(r - r_all)) <= 1e-12 * np.max(np.abs(r_all))
+    c = pod.fit_solve(G, r)
+    A, b = o.design_matrix(cfgs, E_ref, F_ref)
+    assert np.max(np.abs(A @ c - A @ c_all)) <= 1e-8 * np.max(np.abs(b))
