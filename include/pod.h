@@ -181,8 +181,10 @@ int pod_descriptors(pod_handle* h, const pod_system* sys, double* D, void* strea
 /* Linear POD energy and its derivatives (Eq. 57a, 58a; forces by the adjoint
  * of Eq. 24c / 26c):
  *   c:  device [M] coefficients (FP64)
- *   E:  device [max(1, n_configs)] total energy per configuration (FP64,
- *       fixed-order reduction), required
+ *   E:  device [max(1, n_configs)] total energy per configuration (FP64;
+ *       order-independent: fixed-order sums, except a single configuration on
+ *       the mixed path, whose E and W are exact fixed-point integer sums with
+ *       2^-36 resolution), required
  *   Ei: device [N] atom energies or NULL
  *   F:  device [3][N] forces F_k = -dE/dr_k or NULL
  *   W:  device [max(1, n_configs)][9] virial W_ab = -sum_ij (r_ij)_a dE_i/d(r_ij)_b

@@ -153,8 +153,11 @@ __global__ void __launch_bounds__(ATOM_MAX_WPB * 32, atom_min_blocks<T, MODE, KT
     for (int q = threadIdx.x; q < p.M; q += blockDim.x) sc[q] = (T)p.c[q];
     __syncthreads();
   }
+  // FP32 energy modes: E and the virial accumulate in fixed point (the tail of
+  // the force accumulators); FP64: per-warp virial partials for the gather
+  constexpr bool FIXP = EMODE && std::is_same<T, float>::value;
   if (atom0 >= p.N) {  // uniform per warp
-    if (EMODE && lane < 9) p.wpart[(size_t)gwarp * 9 + lane] = 0.0;
+    if (EMODE && !FIXP && lane < 9) p.wpart[(size_t)gwarp * 9 + lane] = 0.0;
     return;
   }
   if (lane < A) {
@@ -564,10 +567,24 @@ __global__ void __launch_bounds__(ATOM_MAX_WPB * 32, atom_min_blocks<T, MODE, KT
   }
   se[lane] = E;
   __syncwarp();
+  long long efix = 0;  // FP32 path: this lane's atom energy in fixed point
   if (am && m == 0) {
     T s = T(0);
     for (int mm = 0; mm < K; ++mm) s += se[lane + mm];
     p.Ei[atom0 + a_loc] = (double)s;
+    if constexpr (FIXP) {
+      if (fabsf(s) < EW_MAX_ATOM)
+        efix = __float2ll_rn(s * EW_SCALE_F);
+      else
+        atomicOr(p.status, isfinite(s) ? ST_RANGE : ST_NONFINITE);
+    }
+  }
+  if constexpr (FIXP) {
+    // the warp's energy (exact integer sum of its atoms' fixed-point values)
+    // joins the fixed-point total: one atomic per warp
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) efix += __shfl_xor_sync(0xffffffffu, efix, o);
+    if (lane == 0) ew_add(p.facc + 4 * (size_t)p.N + (gwarp % EW_COPIES) * EW_STRIDE, efix);
   }
 
   // ---------------- adjoint pair pass: g_ij = sum_{m,x} a_mx dB_mx/dr_ij  (Eq. 24c)
@@ -713,7 +730,21 @@ __global__ void __launch_bounds__(ATOM_MAX_WPB * 32, atom_min_blocks<T, MODE, KT
 #pragma unroll
     for (int q = 0; q < 9; ++q) wv[q] += __shfl_xor_sync(0xffffffffu, wv[q], o);
   }
-  if (lane < 9) {
+  if constexpr (FIXP) {
+    // the warp's virial joins the fixed-point totals: one atomic per component
+    if (lane < 9) {
+      T w = wv[0];
+#pragma unroll
+      for (int q = 1; q < 9; ++q)
+        if (lane == q) w = wv[q];
+      long long v = 0;
+      if (fabsf(w) < EW_MAX_WARP)
+        v = __float2ll_rn(w * EW_SCALE_F);
+      else
+        atomicOr(p.status, isfinite(w) ? ST_RANGE : ST_NONFINITE);
+      ew_add(p.facc + 4 * (size_t)p.N + (gwarp % EW_COPIES) * EW_STRIDE + 2 * (1 + lane), v);
+    }
+  } else if (lane < 9) {
     T v = wv[0];
 #pragma unroll
     for (int q = 1; q < 9; ++q)

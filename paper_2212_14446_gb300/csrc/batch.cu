@@ -12,10 +12,12 @@ __global__ void batch_wrap_kernel(int N, const double* __restrict__ pos, const i
                                   unsigned long long* __restrict__ facc) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
-  if (facc) {  // fixed-point force accumulators of this call start at zero
+  if (facc) {  // fixed-point force, energy and virial accumulators of this call start at zero
     ulonglong2* fz = reinterpret_cast<ulonglong2*>(facc + 4 * (size_t)i);
     fz[0] = make_ulonglong2(0ull, 0ull);
     fz[1] = make_ulonglong2(0ull, 0ull);
+    ulonglong2* tz = reinterpret_cast<ulonglong2*>(facc + 4 * (size_t)N);
+    for (int q = i; q < FACC_TAIL / 2; q += N) tz[q] = make_ulonglong2(0ull, 0ull);
   }
   const CfgBox& b = cbox[cfg_of[i]];
   double x[3];

@@ -168,70 +168,44 @@ __global__ void __launch_bounds__(GATHER_MAX_WPB * 32, GATHER_MIN_BLOCKS)
 }
 
 // FP32 path: forces from the fixed-point accumulators the atom kernel filled
-// (F = fscale * acc * 2^-32), E = sum_i E_i and the virial partials in a fixed
-// order (thread-strided atoms, warp and block trees, then the block partials in
-// block order by the last block), so every result is bitwise reproducible.
+// (F = fscale * acc * 2^-32), and E and the virial from the fixed-point totals
+// after the force rows (2^-36).  Integer sums do not depend on the order of the
+// atomics, so every result is bitwise reproducible.
 __global__ void __launch_bounds__(256)
-    finalize_kernel(int N, const unsigned long long* __restrict__ facc, const double* __restrict__ Ei,
-                    const double* __restrict__ wpart, int n_wpart, double* __restrict__ F, double fscale,
-                    double* __restrict__ part, unsigned* __restrict__ ticket, double* __restrict__ E_out,
-                    double* __restrict__ W_out) {
-  __shared__ double sred[8][10];
-  __shared__ bool last;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    finalize_kernel(int N, const unsigned long long* __restrict__ facc, double* __restrict__ F, double fscale,
+                    double* __restrict__ E_out, double* __restrict__ W_out) {
   const double sc = fscale * FIX_INV_SCALE;
-  double eacc = 0.0, wacc = 0.0;
+  if (blockIdx.x == 0) {  // warp w sums quantities w, w + 8 (0: E, 1..9: W)
+    const int lane = threadIdx.x & 31;
+    for (int q = threadIdx.x >> 5; q < 10; q += blockDim.x >> 5) {
+      const double v = ew_value_warp(facc + 4 * (size_t)N + 2 * q, lane);
+      if (lane == 0) {
+        if (q == 0)
+          E_out[0] = v;
+        else if (W_out)
+          W_out[q - 1] = v;
+      }
+    }
+  }
+  if (!F) return;
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < N; k += gridDim.x * blockDim.x) {
-    if (F) {
-      const ulonglong2 a = *reinterpret_cast<const ulonglong2*>(facc + 4 * (size_t)k);
-      const unsigned long long b = facc[4 * (size_t)k + 2];
-      F[k] = sc * (double)(long long)a.x;
-      F[(size_t)N + k] = sc * (double)(long long)a.y;
-      F[(size_t)2 * N + k] = sc * (double)(long long)b;
-    }
-    eacc += Ei[k];
+    const ulonglong2 a = *reinterpret_cast<const ulonglong2*>(facc + 4 * (size_t)k);
+    const unsigned long long b = facc[4 * (size_t)k + 2];
+    F[k] = sc * (double)(long long)a.x;
+    F[(size_t)N + k] = sc * (double)(long long)a.y;
+    F[(size_t)2 * N + k] = sc * (double)(long long)b;
   }
-  if (lane < 9)
-    for (int w = blockIdx.x * nwarps + warp; w < n_wpart; w += gridDim.x * nwarps) wacc += wpart[(size_t)w * 9 + lane];
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) eacc += __shfl_xor_sync(0xffffffffu, eacc, o);
-  if (lane == 0) sred[warp][0] = eacc;
-  if (lane < 9) sred[warp][1 + lane] = wacc;
-  __syncthreads();
-  if (threadIdx.x < 10) {
-    double s = 0.0;
-    for (int wv = 0; wv < nwarps; ++wv) s += sred[wv][threadIdx.x];
-    part[(size_t)blockIdx.x * 10 + threadIdx.x] = s;
-  }
-  __threadfence();
-  __syncthreads();
-  if (threadIdx.x == 0) last = (atomicAdd(ticket, 1u) == gridDim.x - 1);
-  __syncthreads();
-  if (!last) return;
-  __threadfence();
-  for (int q = warp; q < 10; q += nwarps) {
-    double s = 0.0;
-    for (unsigned b = lane; b < gridDim.x; b += 32) s += __ldcg(part + (size_t)b * 10 + q);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (lane == 0) {
-      if (q == 0) E_out[0] = s;
-      else if (W_out) W_out[q - 1] = s;
-    }
-  }
-  if (threadIdx.x == 0) *ticket = 0u;  // ready for the next launch (graph replays)
 }
 
 constexpr int FINALIZE_THREADS = 256;
 int finalize_blocks(int N) {
   const int want = (N + FINALIZE_THREADS - 1) / FINALIZE_THREADS;
-  return want < 2 * 152 ? (want > 0 ? want : 1) : 2 * 152;
+  return want < 8 * 152 ? (want > 0 ? want : 1) : 8 * 152;
 }
 
-cudaError_t launch_finalize(int N, const unsigned long long* facc, const double* Ei, const double* wpart,
-                            int n_wpart, double* F, double fscale, double* part, int nblocks, unsigned* ticket,
-                            double* E, double* W, cudaStream_t st) {
-  finalize_kernel<<<nblocks, FINALIZE_THREADS, 0, st>>>(N, facc, Ei, wpart, n_wpart, F, fscale, part, ticket, E, W);
+cudaError_t launch_finalize(int N, const unsigned long long* facc, double* F, double fscale, int nblocks, double* E,
+                            double* W, cudaStream_t st) {
+  finalize_kernel<<<nblocks, FINALIZE_THREADS, 0, st>>>(N, facc, F, fscale, E, W);
   return cudaGetLastError();
 }
 

@@ -19,10 +19,12 @@ __global__ void bin_kernel(int N, const double* __restrict__ pos, CellGrid cg, d
                            unsigned long long* __restrict__ facc, int* __restrict__ nbr_count) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
-  if (facc) {  // fixed-point force accumulators of this call start at zero
+  if (facc) {  // fixed-point force, energy and virial accumulators of this call start at zero
     ulonglong2* fz = reinterpret_cast<ulonglong2*>(facc + 4 * (size_t)i);
     fz[0] = make_ulonglong2(0ull, 0ull);
     fz[1] = make_ulonglong2(0ull, 0ull);
+    ulonglong2* tz = reinterpret_cast<ulonglong2*>(facc + 4 * (size_t)N);
+    for (int q = i; q < FACC_TAIL / 2; q += N) tz[q] = make_ulonglong2(0ull, 0ull);
   }
   double x[3];
   int c[3];
@@ -433,10 +435,12 @@ __global__ void rewrap_kernel(int N, const double* __restrict__ pos, const int* 
                               unsigned long long* __restrict__ facc) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
-  if (facc) {  // fixed-point force accumulators of this call start at zero
+  if (facc) {  // fixed-point force, energy and virial accumulators of this call start at zero
     ulonglong2* fz = reinterpret_cast<ulonglong2*>(facc + 4 * (size_t)i);
     fz[0] = make_ulonglong2(0ull, 0ull);
     fz[1] = make_ulonglong2(0ull, 0ull);
+    ulonglong2* tz = reinterpret_cast<ulonglong2*>(facc + 4 * (size_t)N);
+    for (int q = i; q < FACC_TAIL / 2; q += N) tz[q] = make_ulonglong2(0ull, 0ull);
   }
   const double L[3] = {L0, L1, L2};
   double x[3];

@@ -898,7 +898,8 @@ int pod_handle::energy_forces(const pod_system* sys, const double* c, double* E,
     // FP32 path: forces accumulate in fixed point, zeroed by this call's wrap
     // kernel; FP64 path: pair gradients per slot and the gather
     const bool fixp = precision == POD_MIXED;
-    if (fixp && (rc_ = ensure(facc, sizeof(unsigned long long) * 4 * (size_t)N, "force accumulators"))) return rc_;
+    if (fixp && (rc_ = ensure(facc, sizeof(unsigned long long) * (4 * (size_t)N + FACC_TAIL), "force accumulators")))
+      return rc_;
     unsigned long long* fa = fixp ? (unsigned long long*)facc.p : nullptr;
     if (reuse) {
       pl = last_pl;
@@ -916,7 +917,7 @@ int pod_handle::energy_forces(const pod_system* sys, const double* c, double* E,
     int* rev_out = keep_rev ? (int*)rev.p : nullptr;
     if (!fixp && (rc_ = ensure(g, sizeof(Q4<double>) * (size_t)N * pl.cap, "pair gradients"))) return rc_;
     const int nwarp = atom_warps(N, K, pl.shape.atom_wpb);
-    if ((rc_ = ensure(wpart, sizeof(double) * 9 * (size_t)nwarp, "virial partials"))) return rc_;
+    if (!fixp && (rc_ = ensure(wpart, sizeof(double) * 9 * (size_t)nwarp, "virial partials"))) return rc_;
     double* Ei_dst = Ei_user;
     if (!Ei_dst) {
       if ((rc_ = ensure(Ei, sizeof(double) * (size_t)N, "atom energies"))) return rc_;
@@ -934,8 +935,7 @@ int pod_handle::energy_forces(const pod_system* sys, const double* c, double* E,
     if ((rc_ = mark(2, st))) return rc_;
     cudaError_t e;
     if (fixp)
-      e = launch_finalize(N, fa, Ei_dst, (const double*)wpart.p, nwarp, F, 1.0, (double*)Wat.p, nblk,
-                          (unsigned*)offs.p, E, W, st);
+      e = launch_finalize(N, fa, F, 1.0, nblk, E, W, st);
     else
       e = launch_gather_reduce<double>(N, pl.cap, (const int*)nbr_count.p, (const int*)nbr_j.p,
                                        (const int*)nbr_s.p, rev_in, rev_out, (const Q4<double>*)g.p, Ei_dst,

@@ -18,6 +18,47 @@ constexpr int PAMAX = 4;   // highest angular degree compiled
 constexpr float FIX_SCALE_F = 4294967296.0f;     // 2^32
 constexpr double FIX_INV_SCALE = 1.0 / 4294967296.0;
 constexpr float FIX_GMAX = 1073741824.0f;        // 2^30: larger pair gradients are reported
+// Energy and virial totals of the FP32 path, fixed point with 2^-36 resolution,
+// in the accumulators after the N force rows.  A contribution X (an energy or a
+// virial component times 2^36) is added as its low 32 bits (unsigned) to one
+// 64-bit sum and its high part X >> 32 (signed) to another, so the totals are
+// exact, independent of the order of the atomics, and cannot overflow for any
+// system the device holds.  Entry 2q is the low sum of quantity q and 2q + 1 the
+// high sum (q = 0: E, q = 1..9: the virial, row major); EW_COPIES copies of these
+// 32 entries (warp w adds to copy w mod EW_COPIES) keep the atomics on any one
+// address few.
+constexpr int EW_STRIDE = 32;
+constexpr int EW_COPIES = 64;
+constexpr int FACC_TAIL = EW_STRIDE * EW_COPIES;
+constexpr float EW_SCALE_F = 68719476736.0f;     // 2^36
+constexpr float EW_MAX_ATOM = 2097152.0f;        // 2^21: larger atom energies are reported
+constexpr float EW_MAX_WARP = 67108864.0f;       // 2^26: larger per-warp virial sums are reported
+
+__device__ __forceinline__ void ew_add(unsigned long long* acc, long long X) {
+  atomicAdd(acc, (unsigned long long)(X & 0xffffffffll));
+  atomicAdd(acc + 1, (unsigned long long)(X >> 32));
+}
+
+// Value of one fixed-point total over the copies, summed by the 32 lanes of a
+// warp (lane l takes copies l, l + 32, ...): (high + carry of low) * 2^-4 +
+// (low mod 2^32) * 2^-36, the integer sums exact in any order.  All lanes
+// return the value.
+__device__ __forceinline__ double ew_value_warp(const unsigned long long* acc, int lane) {
+  unsigned long long lo = 0, hs = 0;
+#pragma unroll
+  for (int c = lane; c < EW_COPIES; c += 32) {
+    const unsigned long long l = acc[c * EW_STRIDE], h = acc[c * EW_STRIDE + 1];
+    hs += h + (l >> 32);
+    lo += l & 0xffffffffull;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    hs += __shfl_xor_sync(0xffffffffu, hs, o);
+    lo += __shfl_xor_sync(0xffffffffu, lo, o);
+  }
+  const long long hi = (long long)hs + (long long)(lo >> 32);
+  return (double)hi * 0.0625 + (double)(lo & 0xffffffffull) * (1.0 / 68719476736.0);
+}
 constexpr int MAXM = 1 + MAXK + MAXK * (PAMAX + 1) + MAXK * 11;  // descriptors (11 = four-body K_a at P = 4)
 constexpr int CH = 32;     // pairs per atom staged in shared memory at a time
 constexpr int WPB_ATOM = 2;   // warps per block, atom kernels (default launch shape)

@@ -123,8 +123,7 @@ cudaError_t launch_colsum(int n_chunks, const int* chunk_rows /*[n_chunks][2]*/,
                           int M, const double* D, double* part, double* G, cudaStream_t st);
 int gather_blocks(int N, int wpb, int bps);
 int finalize_blocks(int N);
-cudaError_t launch_finalize(int N, const unsigned long long* facc, const double* Ei, const double* wpart,
-                            int n_wpart, double* F, double fscale, double* part, int nblocks, unsigned* ticket,
-                            double* E, double* W, cudaStream_t st);
+cudaError_t launch_finalize(int N, const unsigned long long* facc, double* F, double fscale, int nblocks, double* E,
+                            double* W, cudaStream_t st);
 
 }  // namespace fastpod
