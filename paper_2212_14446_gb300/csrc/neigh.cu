@@ -333,15 +333,31 @@ __global__ void __launch_bounds__(NEIGH_MAX_WPB * 32)
   }
   __syncthreads();
   const int ncand = soff[27];
-  for (int e = warp; e < 27; e += nwarps) {
-    const int o0 = soff[e], ne = soff[e + 1] - o0;
-    const float4* src = cell_pos + (size_t)scell[e] * cg.cap;
-    const float ex = spx[e], ey = spy[e], ez = spz[e];
-    const int ecode = scode[e];
-    for (int t = lane; t < ne; t += 32) {
-      const float4 q = src[t];
-      cand[o0 + t] = make_float4(q.x + ex, q.y + ey, q.z + ez, q.w);
-      ccode[o0 + t] = ecode;
+  // copy the candidates with all threads, two per thread per round (both loads
+  // in flight before either is stored); candidate f belongs to the stencil entry
+  // e with soff[e] <= f < soff[e + 1]
+  auto entry_of = [&](int f) {
+    int lo = 0, hi = 27;  // soff[lo] <= f < soff[hi]
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (soff[mid] <= f)
+        lo = mid;
+      else
+        hi = mid;
+    }
+    return lo;
+  };
+  for (int f0 = threadIdx.x; f0 < ncand; f0 += 2 * blockDim.x) {
+    const int f1 = f0 + blockDim.x;
+    const int e0 = entry_of(f0), e1 = f1 < ncand ? entry_of(f1) : 0;
+    const float4 q0 = cell_pos[(size_t)scell[e0] * cg.cap + (f0 - soff[e0])];
+    float4 q1 = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (f1 < ncand) q1 = cell_pos[(size_t)scell[e1] * cg.cap + (f1 - soff[e1])];
+    cand[f0] = make_float4(q0.x + spx[e0], q0.y + spy[e0], q0.z + spz[e0], q0.w);
+    ccode[f0] = scode[e0];
+    if (f1 < ncand) {
+      cand[f1] = make_float4(q1.x + spx[e1], q1.y + spy[e1], q1.z + spz[e1], q1.w);
+      ccode[f1] = scode[e1];
     }
   }
   __syncthreads();
@@ -352,10 +368,10 @@ __global__ void __launch_bounds__(NEIGH_MAX_WPB * 32)
     const float4 qi = cand[own0 + k];
     const int i = __float_as_int(qi.w);
     int nhit = 0;
-    for (int f0 = 0; f0 < ncand; f0 += 32) {
-      const int f = f0 + lane;
+    // candidate f: (hit, key) of the FP32 test (band keys marked for the FP64 decision)
+    auto test = [&](int f, unsigned long long& key) {
       bool hit = false;
-      unsigned long long key = 0;
+      key = 0;
       if (f < ncand) {
         const float4 q = cand[f];
         const int j = __float_as_int(q.w);
@@ -367,12 +383,24 @@ __global__ void __launch_bounds__(NEIGH_MAX_WPB * 32)
           key = ((unsigned long long)j << 24) | (unsigned long long)code | (r2f < rc2_lo ? 0ull : BAND_MARK);
         }
       }
-      const unsigned m = __ballot_sync(0xffffffffu, hit);
-      if (hit) {
-        const int pos = nhit + __popc(m & ((1u << lane) - 1u));
-        if (pos < keycap) keys[pos] = key;
+      return hit;
+    };
+    const unsigned below = (1u << lane) - 1u;
+    for (int f0 = 0; f0 < ncand; f0 += 64) {  // two rounds of 32 candidates per iteration
+      unsigned long long key0, key1;
+      const bool hit0 = test(f0 + lane, key0);
+      const bool hit1 = test(f0 + 32 + lane, key1);
+      const unsigned m0 = __ballot_sync(0xffffffffu, hit0);
+      const unsigned m1 = __ballot_sync(0xffffffffu, hit1);
+      if (hit0) {
+        const int pos = nhit + __popc(m0 & below);
+        if (pos < keycap) keys[pos] = key0;
       }
-      nhit += __popc(m);
+      if (hit1) {
+        const int pos = nhit + __popc(m0) + __popc(m1 & below);
+        if (pos < keycap) keys[pos] = key1;
+      }
+      nhit += __popc(m0) + __popc(m1);
     }
     neigh_finish_row(N, cg, wpos, rc2, cap, keycap, i, lane, nhit, keys, nbr_count, nbr_j, nbr_s, status);
     __syncwarp();
