@@ -265,6 +265,29 @@ def test_deterministic(pkg, full, prec):
         assert torch.equal(a[k], b[k]), k
 
 
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_one_handle_many_systems(pkg, full, prec):
+    """A handle that alternates between systems (cell grids of different sizes;
+    the block-per-cell search for 16^3 and 12^3 cells, the warp-per-atom search
+    for 4^3) gives, on every call, the results of a fresh handle bit for bit:
+    nothing a call leaves in the workspace (cell counts, accumulators, lists)
+    leaks into the next."""
+    p, o, cfg, c = full
+    systems = {"a": cfg, "b": synth.config_full(1, ncell=12), "c": synth.config_full(2, ncell=4)}
+    ct = torch.tensor(c, device=DEV)
+    fresh = {}
+    for name, cf in systems.items():
+        pod = pkg.POD(p, precision=prec, Q=o.Q)
+        fresh[name] = pod.energy_forces(soa(cf), cf.box, ct)
+        pod.close()
+    pod = pkg.POD(p, precision=prec, Q=o.Q)
+    for name in ("a", "b", "a", "c", "a", "a", "c", "b", "b", "a"):
+        cf = systems[name]
+        out = pod.energy_forces(soa(cf), cf.box, ct)
+        for k in ("E", "Ei", "F", "W"):
+            assert torch.equal(out[k], fresh[name][k]), (name, k)
+
+
 def test_host_entry_point(pkg, small):
     p, o, cfg, c = small
     pod = pkg.POD(p, precision="mixed", Q=o.Q)
