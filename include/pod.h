@@ -47,7 +47,11 @@ extern "C" {
 #define POD_EINVAL (-1)     /* bad parameter, NULL pointer, unsupported size      */
 #define POD_ENOMEM (-2)     /* device or host allocation failed                   */
 #define POD_ECUDA (-3)      /* a CUDA runtime call failed                         */
-#define POD_ERANGE (-4)     /* a pair closer than r_in (outside (r_in, r_cut))    */
+#define POD_ERANGE (-4)     /* a pair closer than r_in (outside (r_in, r_cut)); on
+                               the mixed path also a value outside its fixed-point
+                               range: a pair gradient of 2^30 eV/A or more, an atom
+                               energy of 2^21 eV or more, or a per-warp virial sum
+                               of 2^26 eV or more                                   */
 #define POD_ENONFINITE (-5) /* NaN/Inf in positions or results                    */
 #define POD_ESINGULAR (-6)  /* fit: normal equations not positive definite        */
 #define POD_ENEIGH (-7)     /* neighbour or cell capacity exceeded after retry    */

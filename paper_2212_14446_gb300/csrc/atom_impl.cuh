@@ -576,7 +576,7 @@ __global__ void __launch_bounds__(ATOM_MAX_WPB * 32, atom_min_blocks<T, MODE, KT
       if (fabsf(s) < EW_MAX_ATOM)
         efix = __float2ll_rn(s * EW_SCALE_F);
       else
-        atomicOr(p.status, isfinite(s) ? ST_RANGE : ST_NONFINITE);
+        atomicOr(p.status, isfinite(s) ? ST_OVERFLOW : ST_NONFINITE);
     }
   }
   if constexpr (FIXP) {
@@ -703,7 +703,7 @@ __global__ void __launch_bounds__(ATOM_MAX_WPB * 32, atom_min_blocks<T, MODE, KT
         // F_i += g_ij, F_j -= g_ij as fixed-point integers (order-independent sums)
         const int j = p.nbr_j[pidx];
         if (!(fabsf(out.x) < FIX_GMAX && fabsf(out.y) < FIX_GMAX && fabsf(out.z) < FIX_GMAX)) {
-          atomicOr(p.status, isfinite(out.x) && isfinite(out.y) && isfinite(out.z) ? ST_RANGE : ST_NONFINITE);
+          atomicOr(p.status, isfinite(out.x) && isfinite(out.y) && isfinite(out.z) ? ST_OVERFLOW : ST_NONFINITE);
         } else {
           const long long fx = __float2ll_rn(out.x * FIX_SCALE_F);
           const long long fy = __float2ll_rn(out.y * FIX_SCALE_F);
@@ -741,7 +741,7 @@ __global__ void __launch_bounds__(ATOM_MAX_WPB * 32, atom_min_blocks<T, MODE, KT
       if (fabsf(w) < EW_MAX_WARP)
         v = __float2ll_rn(w * EW_SCALE_F);
       else
-        atomicOr(p.status, isfinite(w) ? ST_RANGE : ST_NONFINITE);
+        atomicOr(p.status, isfinite(w) ? ST_OVERFLOW : ST_NONFINITE);
       ew_add(p.facc + 4 * (size_t)p.N + (gwarp % EW_COPIES) * EW_STRIDE + 2 * (1 + lane), v);
     }
   } else if (lane < 9) {

@@ -565,6 +565,8 @@ int pod_handle::read_status(cudaStream_t st) {
   if (s & ST_REV) return fail(POD_ENEIGH, "neighbour list is not symmetric (status 0x%x)", s);
   if (s & ST_NONFINITE) return fail(POD_ENONFINITE, "non-finite positions or results");
   if (s & ST_RANGE) return fail(POD_ERANGE, "a pair is closer than r_in");
+  if (s & ST_OVERFLOW)
+    return fail(POD_ERANGE, "a force, atom energy or virial exceeds the fixed-point range of the mixed path");
   return POD_OK;
 }
 

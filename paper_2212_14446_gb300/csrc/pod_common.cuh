@@ -73,6 +73,7 @@ constexpr int ST_CELL = 2;       // more atoms in a cell than the cell capacity
 constexpr int ST_RANGE = 4;      // pair with r <= r_in
 constexpr int ST_NONFINITE = 8;  // NaN / Inf in positions
 constexpr int ST_REV = 16;       // reverse pair not found (broken list symmetry)
+constexpr int ST_OVERFLOW = 32;  // a force, energy or virial beyond the mixed path's fixed-point range
 
 // ------------------------------------------------ small vector of 4 T
 template <typename T>

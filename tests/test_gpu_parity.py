@@ -338,6 +338,29 @@ def test_error_codes(pkg):
     pod.energy_forces(soa(ok), ok.box, c)
 
 
+def test_mixed_energy_virial_totals(pkg, full):
+    """Mixed path: E and the virial are exact fixed-point sums (2^-36 grid) of the
+    FP32 atom energies and per-warp virial sums.  E equals the exact sum of the
+    returned E_i to within half a grid step per atom; W agrees with the FP64 path
+    within the mixed tolerance; coefficients that push atom energies past the
+    accumulator range are reported (POD_ERANGE) and the handle stays usable."""
+    p, o, cfg, c = full
+    ct = torch.tensor(c, device=DEV)
+    pod = pkg.POD(p, precision="mixed", Q=o.Q)
+    out = pod.energy_forces(soa(cfg), cfg.box, ct)
+    Ei = out["Ei"].cpu().numpy()
+    s = math.fsum(Ei.tolist())
+    assert abs(out["E"].item() - s) <= len(Ei) * 2.0 ** -37 + 1e-15 * abs(s)
+    ref = pkg.POD(p, precision="fp64", Q=o.Q).energy_forces(soa(cfg), cfg.box, ct)
+    W, W64 = out["W"].cpu().numpy(), ref["W"].cpu().numpy()
+    assert np.max(np.abs(W - W64)) <= 1e-5 * np.max(np.abs(W64))
+    with pytest.raises(pkg.PodError) as ei:
+        pod.energy_forces(soa(cfg), cfg.box, ct * 1e9)
+    assert ei.value.code == pkg.POD_ERANGE
+    again = pod.energy_forces(soa(cfg), cfg.box, ct)
+    assert torch.equal(again["E"], out["E"]) and torch.equal(again["F"], out["F"])
+
+
 def test_capacity_retry(pkg):
     """A dense cluster in a large open box: the density-based capacity estimate
     is far too small, the call overflows, grows its lists and succeeds."""
