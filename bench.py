@@ -194,6 +194,16 @@ def workload(name, replica):
     raise ValueError(name)
 
 
+def embedding_weights(params, M, seed):
+    """MEAM-type density weights (two- and three-body columns) and a cubic
+    embedding polynomial for the embedding-model benchmark."""
+    g = synth.rng(seed)
+    a = np.zeros(M)
+    n = 1 + params.K2 + params.K3 * (params.P3 + 1)
+    a[1:n] = g.normal(0.0, 1e-2, size=n - 1)
+    return a, np.array([0.3, -0.2, 5e-3, -1e-4])
+
+
 # ------------------------------------------------------------ CPU baseline
 def host_cores():
     try:
@@ -260,6 +270,9 @@ def main():
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shapes")
     ap.add_argument("--quadratic", action="store_true",
                     help="quadratic model: beta_mn ~ N(0, 1e-5^2) on top of the linear coefficients")
+    ap.add_argument("--embedding", action="store_true",
+                    help="embedding model (MEAM-type): cubic F of a density a.D on the two- and three-body "
+                         "columns, a ~ N(0, 1e-2^2), on top of the linear coefficients")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -293,6 +306,9 @@ def main():
     c = torch.tensor(synth.coefficients(pod.M, 2001 + rank), dtype=torch.float64, device=dev)
     if args.quadratic:
         pod.set_quadratic(synth.rng(2002 + rank).normal(0.0, 1e-5, size=(pod.M, pod.M)))
+    emb = embedding_weights(params, pod.M, 2003 + rank) if args.embedding else None
+    if emb is not None:
+        pod.set_embedding(*emb)
     pos = torch.tensor(np.ascontiguousarray(cfg.pos.T), dtype=torch.float64, device=dev)
     box = cfg.box
     E = torch.empty(1, dtype=torch.float64, device=dev)
@@ -393,6 +409,8 @@ def main():
         pod64 = pkg.POD(params, precision="fp64", Q=pod.Q)
         if args.quadratic:
             pod64.set_quadratic(synth.rng(2002 + rank).normal(0.0, 1e-5, size=(pod.M, pod.M)))
+        if emb is not None:
+            pod64.set_embedding(*emb)
         with torch.cuda.stream(stream):
             for _ in range(3):
                 pkg.pod_energy_forces(pod64.h, sysd, c, E, Ei, F, W, stream=stream)
@@ -458,7 +476,8 @@ def main():
                        "pairs_per_atom": n_pairs, "descriptors": pod.M, "precision": args.precision,
                        "neighbor_rebuild": "every step", "l2": "flushed (512 MB write) before each step",
                        "graph": "one CUDA graph per step", "parallelism": f"replicas x{world}",
-                       "launch_shape": shape, "model": "quadratic" if args.quadratic else "linear"},
+                       "launch_shape": shape,
+                       "model": "quadratic" if args.quadratic else ("embedding" if args.embedding else "linear")},
             "roofline": {"bound": "alu", "kernel": "atom_kernel (fused radial/B/contraction/adjoint)",
                          "achieved": achieved_tflops, "peak": peak_tflops, "unit": "TFLOP/s",
                          "frac": achieved_tflops / peak_tflops, "traffic": traffic,

@@ -283,6 +283,25 @@ int pod_descriptors_static(pod_handle* h, const pod_system* sys, double* D, void
  * points fit the linear model only.  POD_EINVAL for non-finite weights. */
 int pod_set_quadratic(pod_handle* h, const double* beta);
 
+/* Embedding model (Sec. 3: EAM and MEAM expressed with POD descriptors -- a
+ * polynomial embedding of an atom density that is a linear combination of the
+ * two-, three- and four-body descriptors):
+ *   E_i = sum_m c_m D_im + F(rho_i),  rho_i = sum_m a_m D_im,
+ *   F(rho) = sum_{k=0..degree} alpha_k rho^k.
+ * With a on the two-body columns only this is an EAM-type potential, with the
+ * three-body columns too a MEAM-type one; degree 2 is the quadratic model with
+ * beta = alpha_2 a a^T (upper triangle doubled off the diagonal).
+ *   a: host [M] density weights (one-body column 0 included), or NULL to return
+ *      the handle to the linear model;  degree: 1..POD_EMB_MAX_DEGREE;
+ *   alpha: host [degree + 1], alpha_0 first.
+ * Copied to the device.  While set, pod_energy_forces, pod_energy_forces_host and
+ * pod_md_step evaluate this model (forces by the same adjoint pass with
+ * dE_i/dD_im = c_m + F'(rho_i) a_m per atom); it replaces a quadratic model
+ * and is replaced by one; the fit entry points fit the linear model only.
+ * POD_EINVAL for a bad degree or non-finite weights. */
+#define POD_EMB_MAX_DEGREE 8
+int pod_set_embedding(pod_handle* h, const double* a, int degree, const double* alpha);
+
 /* Launch-shape autotuner (a deployment feature; the paper has no counterpart).
  * Times the three phases of pod_energy_forces on `sys` (one configuration,
  * device positions as for pod_energy_forces; c: device [M]) for a small set of

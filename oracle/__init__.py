@@ -319,6 +319,35 @@ class Oracle:
             W -= d.T @ g
         return Ei, math.fsum(Ei), F, W
 
+    def energy_forces_embedding(self, cfg, c, a, alpha, fast: bool = True):
+        """Embedding model of Sec. 3 (EAM and MEAM written with POD descriptors):
+        E_i = sum_m c_m D_im + F(rho_i) with the density rho_i = sum_m a_m D_im and
+        the polynomial embedding F(rho) = sum_k alpha_k rho^k.  Forces from the
+        explicit descriptor derivatives: dE_i/dr_ij = sum_m (c_m + F'(rho_i) a_m)
+        dD_im/dr_ij, assembled like ``energy_forces``."""
+        c = np.asarray(c, dtype=np.float64)
+        a = np.asarray(a, dtype=np.float64)
+        alpha = np.asarray(alpha, dtype=np.float64)
+        F_poly = np.polynomial.Polynomial(alpha)
+        dF_poly = F_poly.deriv()
+        sysd = self._system(cfg)
+        Ei = np.zeros(cfg.n)
+        F = np.zeros((cfg.n, 3))
+        W = np.zeros((3, 3))
+        for i in range(cfg.n):
+            js, _, d = self.neighbors(cfg, i, sysd)
+            D = self.atom_descriptors(d, fast)
+            rho = float(D @ a)
+            Ei[i] = D @ c + F_poly(rho)
+            if len(js) == 0:
+                continue
+            dD = self.atom_dD(d, fast)              # (n_j, M, 3): dD_im / dr_ij
+            g = np.einsum("jmt,m->jt", dD, c + dF_poly(rho) * a)
+            F[i] += g.sum(axis=0)
+            np.subtract.at(F, js, g)
+            W -= d.T @ g
+        return Ei, math.fsum(Ei), F, W
+
     # -- fit (Eq. 63a)
     def config_rows(self, cfg, fast: bool = True):
         """Global descriptors G (M,) and dG/dr_k (N, 3, M) of one configuration."""

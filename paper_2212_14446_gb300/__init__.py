@@ -62,7 +62,7 @@ EXPORTS = ["pod_create", "pod_destroy", "pod_info", "pod_set_option", "pod_statu
            "pod_neighbors", "pod_descriptors", "pod_energy_forces", "pod_energy_forces_host", "pod_fit",
            "pod_fit_normal", "pod_fit_solve", "pod_fit_residual", "pod_descriptors_static",
            "pod_global_descriptors", "pod_descriptors_jvp", "pod_set_skin", "pod_md_step", "pod_fma_probe", "pod_autotune", "pod_set_quadratic",
-           "pod_last_error"]
+           "pod_set_embedding", "pod_last_error"]
 
 _lib = None
 _lock = threading.Lock()
@@ -103,6 +103,7 @@ def lib():
                 "pod_fma_probe": (C.c_int, [C.c_int, C.c_int, dp, vp]),
                 "pod_autotune": (C.c_int, [H, S, dp, C.c_int, ip, dp, vp]),
                 "pod_set_quadratic": (C.c_int, [H, dp]),
+                "pod_set_embedding": (C.c_int, [H, dp, C.c_int, dp]),
                 "pod_last_error": (C.c_char_p, [H]),
             }
             for name, (res, args) in sig.items():
@@ -404,6 +405,21 @@ class POD:
         if b.shape != (self.M, self.M):
             raise ValueError(f"beta must be ({self.M}, {self.M})")
         _check(self.h, lib().pod_set_quadratic(self.h, b.ctypes.data_as(C.POINTER(C.c_double))))
+
+    def set_embedding(self, a=None, alpha=None):
+        """Embedding model E_i = c.D_i + F(a.D_i), F(rho) = sum_k alpha[k] rho^k (a: (M,),
+        alpha: (degree + 1,), 1 <= degree <= 8), or a=None for the linear model."""
+        if a is None:
+            _check(self.h, lib().pod_set_embedding(self.h, None, 0, None))
+            return
+        av = np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+        al = np.ascontiguousarray(np.asarray(alpha, dtype=np.float64))
+        if av.shape != (self.M,):
+            raise ValueError(f"a must be ({self.M},)")
+        if al.ndim != 1 or al.size < 2:
+            raise ValueError("alpha must hold degree + 1 >= 2 coefficients")
+        _check(self.h, lib().pod_set_embedding(self.h, av.ctypes.data_as(C.POINTER(C.c_double)), al.size - 1,
+                                               al.ctypes.data_as(C.POINTER(C.c_double))))
 
     def autotune(self, pos, box, c, pbc=(1, 1, 1), reps=5, stream=None):
         """Pick the launch shape for this system size (pod_autotune); returns

@@ -10,6 +10,9 @@
 //   B and contraction  lane (atom, m) owns B_m[0..N_a) in registers, so every
 //                  D3/D4 product and the whole adjoint run in registers;
 //   adjoint pair pass  lanes over pairs again, reading dE/dB_m from shared memory.
+//
+// Modes: 0 descriptors, 1 linear energy and forces, 2 descriptor tangent, 3
+// design-matrix pair gradients, 4 quadratic model, 5 embedding model.
 #pragma once
 #include <type_traits>
 
@@ -147,7 +150,7 @@ __global__ void __launch_bounds__(ATOM_MAX_WPB * 32, atom_min_blocks<T, MODE, KT
   const int atom0 = gwarp * A;
   // energy modes (1: linear model, 4: quadratic model): the block converts the
   // coefficients to T once (shared memory)
-  constexpr bool EMODE = (MODE == 1 || MODE == 4);
+  constexpr bool EMODE = (MODE == 1 || MODE == 4 || MODE == 5);
   __shared__ T sc[MAXM];
   if (EMODE) {
     for (int q = threadIdx.x; q < p.M; q += blockDim.x) sc[q] = (T)p.c[q];
@@ -480,6 +483,43 @@ __global__ void __launch_bounds__(ATOM_MAX_WPB * 32, atom_min_blocks<T, MODE, KT
     }
   }
 
+  // ---------------- embedding model (Sec. 3: EAM and MEAM written with POD
+  // descriptors, a polynomial embedding of a density that is a linear
+  // combination of descriptors): rho_i = a . D_i summed over the atom's lanes,
+  // then F(rho_i) and F'(rho_i) by Horner's rule
+  T emb_rho = T(0), emb_F = T(0), emb_Fp = T(0);
+  if (MODE == 5) {
+    T part = T(0);
+    if (am) {
+      const double* ea = p.emb_a;
+      if (m == 0) part = (T)ea[0];  // one-body column, D_i0 = 1
+      T d3[PA + 1];
+      Mono<PA>::d3(B, d3);
+      if (m < p.K2) part = fma((T)ea[1 + m], B[0], part);
+#pragma unroll
+      for (int n = 0; n <= PA; ++n)
+        if (n <= p.P3 && m < p.K3) part = fma((T)ea[p.col3 + m * (p.P3 + 1) + n], d3[n], part);
+      if (HAS4 && m < p.K4) {
+        T D4[KA];
+        Four<PA>::desc(B, d3, D4);
+#pragma unroll
+        for (int q = 0; q < KA; ++q)
+          if (q < p.KA4) part = fma((T)ea[p.col4 + m * p.KA4 + q], D4[q], part);
+      }
+    }
+    se[lane] = part;
+    __syncwarp();
+    if (am) {
+      for (int mm = 0; mm < K; ++mm) emb_rho += se[a_loc * K + mm];
+      emb_F = (T)p.emb_alpha[p.emb_deg];
+      for (int k = p.emb_deg - 1; k >= 0; --k) {
+        emb_Fp = fma(emb_Fp, emb_rho, emb_F);
+        emb_F = fma(emb_F, emb_rho, (T)p.emb_alpha[k]);
+      }
+    }
+    __syncwarp();
+  }
+
   // ---------------- energy and adjoint a = dE_i/dB_m  (Eq. 26c generalised)
   T E = T(0);
   {
@@ -533,6 +573,17 @@ __global__ void __launch_bounds__(ATOM_MAX_WPB * 32, atom_min_blocks<T, MODE, KT
           c0 = ceff(0);
         }
       }
+      if (MODE == 5) {  // dE_i/dD_col = c_col + F'(rho_i) a_col
+        const double* ea = p.emb_a;
+        if (m < p.K2) c2 = fma(emb_Fp, (T)ea[1 + m], c2);
+#pragma unroll
+        for (int n = 0; n <= PA; ++n)
+          if (n <= p.P3 && m < p.K3) h[n] = fma(emb_Fp, (T)ea[p.col3 + m * (p.P3 + 1) + n], h[n]);
+#pragma unroll
+        for (int q = 0; q < KA; ++q)
+          if (HAS4 && q < p.KA4 && m < p.K4) w4[q] = fma(emb_Fp, (T)ea[p.col4 + m * p.KA4 + q], w4[q]);
+        if (m == 0) c0 = fma(emb_Fp, (T)ea[0], c0);
+      }
       T d3[PA + 1];
       Mono<PA>::d3(B, d3);
       T a0 = c2;
@@ -560,6 +611,9 @@ __global__ void __launch_bounds__(ATOM_MAX_WPB * 32, atom_min_blocks<T, MODE, KT
       // quadratic model: E above is sum_col (dE/dD_col) D_col = c.D + 2 E_quad, so
       // E_i = (c.D + that) / 2
       if (MODE == 4) E = T(0.5) * (E + Elin);
+      // embedding model: E above is (c + F' a) . D = c . D + F' rho, so
+      // E_i = that - F' rho + F(rho)
+      if (MODE == 5 && m == 0) E += emb_F - emb_Fp * emb_rho;
       T* adst = sadj + a_loc * lay.AS + m * NAP;
 #pragma unroll
       for (int x = 0; x < NAP; ++x) adst[x] = a[x];
@@ -830,6 +884,16 @@ static cudaError_t dispatch_generic(const AtomArgs<T>& p, const AtomLayout& lay,
     case 9: return launch_one<T, 4, true, MODE, MAXK>(p, lay, st);
     default: return cudaErrorInvalidValue;
   }
+}
+
+// Embedding model (mode 5): its own entry so that it is compiled separately.
+template <typename T>
+cudaError_t launch_atom_emb_t(const AtomArgs<T>& p, int PA, bool has4, cudaStream_t st) {
+  if (!p.emb_a || !p.emb_alpha || p.emb_deg < 1) return cudaErrorInvalidValue;
+  const AtomLayout lay = make_layout<T>(p.K, PA, p.rad.tab != nullptr && !p.keep_rp, false, 0);
+  if (p.K == 6 && PA == 4 && has4) return launch_one<T, 4, true, 5, 6>(p, lay, st);
+  if (p.K == 3 && PA == 3 && !has4) return launch_one<T, 3, false, 5, 3>(p, lay, st);
+  return dispatch_generic<T, 5>(p, lay, PA, has4, st);
 }
 
 // Specialised instantiations for the two workloads the library is tuned for

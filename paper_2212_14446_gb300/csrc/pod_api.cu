@@ -230,7 +230,8 @@ bool pod_handle::HostKey::operator==(const HostKey& o) const {
     if (ptr[k] != o.ptr[k]) return false;
   for (int d = 0; d < 3; ++d)
     if (pbc[d] != o.pbc[d] || box[d] != o.box[d]) return false;
-  return N == o.N && precision == o.precision && quad == o.quad && radial == o.radial && tune_gen == o.tune_gen;
+  return N == o.N && precision == o.precision && quad == o.quad && radial == o.radial && tune_gen == o.tune_gen &&
+         emb_deg == o.emb_deg;
 }
 
 void pod_handle::drop_host_graph() {
@@ -355,7 +356,8 @@ int pod_handle::autotune(const pod_system* sys, const double* c, int reps, cudaS
 std::vector<DevBuf*> pod_handle::all_bufs() {
   return {&cell_count, &cell_atoms, &wpos, &phi, &plo, &nbr_count, &nbr_j, &nbr_s, &rev, &g, &Ei,
           &Wat, &status, &offs, &pos_in, &c_in, &E_out, &F_out, &W_out, &Ei_out, &fitA, &fitG, &fitb,
-          &fitwork, &cfg_of, &boxes, &rtab, &wpart, &Dws, &chunks, &cpart, &wrapk, &gdm, &dmG, &facc, &qS32, &qS64};
+          &fitwork, &cfg_of, &boxes, &rtab, &wpart, &Dws, &chunks, &cpart, &wrapk, &gdm, &dmG, &facc, &qS32, &qS64,
+          &embW};
 }
 
 // ============================================================ C ABI
@@ -471,6 +473,7 @@ int pod_set_quadratic(pod_handle* h, const double* beta) {
     h->quad = false;
     return POD_OK;
   }
+  h->emb_deg = 0;
   const int M = h->M;
   std::vector<double> S((size_t)M * M);
   std::vector<float> S32((size_t)M * M);
@@ -489,6 +492,30 @@ int pod_set_quadratic(pod_handle* h, const double* beta) {
   if (e == cudaSuccess) e = cudaMemcpy(h->qS32.p, S32.data(), sizeof(float) * S32.size(), cudaMemcpyHostToDevice);
   if (e != cudaSuccess) return h->cuda_fail(e, "quadratic weights upload");
   h->quad = true;
+  return POD_OK;
+}
+
+int pod_set_embedding(pod_handle* h, const double* a, int degree, const double* alpha) {
+  if (!h) return POD_EINVAL;
+  if (!a) {
+    h->emb_deg = 0;
+    return POD_OK;
+  }
+  if (degree < 1 || degree > POD_EMB_MAX_DEGREE || !alpha)
+    return h->fail(POD_EINVAL, "the embedding polynomial needs 1 <= degree <= %d and its coefficients",
+                   POD_EMB_MAX_DEGREE);
+  const int M = h->M;
+  std::vector<double> w((size_t)M + degree + 1);
+  for (int m = 0; m < M; ++m) w[m] = a[m];
+  for (int k = 0; k <= degree; ++k) w[(size_t)M + k] = alpha[k];
+  for (double v : w)
+    if (!std::isfinite(v)) return h->fail(POD_EINVAL, "embedding weights must be finite");
+  int rc;
+  if ((rc = h->ensure(h->embW, sizeof(double) * w.size(), "embedding weights"))) return rc;
+  cudaError_t e = cudaMemcpy(h->embW.p, w.data(), sizeof(double) * w.size(), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return h->cuda_fail(e, "embedding weights upload");
+  h->quad = false;
+  h->emb_deg = degree;
   return POD_OK;
 }
 
@@ -830,11 +857,14 @@ int pod_handle::run_atoms(int mode, const Plan& pl, double* D, const double* c, 
     a.g = nullptr;
     a.facc = (unsigned long long*)facc.p;
     a.qbeta = (const float*)qS32.p;
+    a.emb_a = (const double*)embW.p;
+    a.emb_alpha = (const double*)embW.p + M;
+    a.emb_deg = emb_deg;
     a.wpart = (double*)wpart.p;
     a.gdm = (float*)gdm.p;
     a.q0 = dm_q0;
     a.q1 = dm_q1;
-    e = launch_atom_f32(mode, a, PA, has4, st);
+    e = mode == 5 ? launch_atom_emb_f32(a, PA, has4, st) : launch_atom_f32(mode, a, PA, has4, st);
   } else {
     AtomArgs<double> a;
     fill_args(a, pl);
@@ -844,11 +874,14 @@ int pod_handle::run_atoms(int mode, const Plan& pl, double* D, const double* c, 
     a.Ei = Ei_dst;
     a.g = (Q4<double>*)g.p;
     a.qbeta = (const double*)qS64.p;
+    a.emb_a = (const double*)embW.p;
+    a.emb_alpha = (const double*)embW.p + M;
+    a.emb_deg = emb_deg;
     a.wpart = (double*)wpart.p;
     a.gdm = (double*)gdm.p;
     a.q0 = dm_q0;
     a.q1 = dm_q1;
-    e = launch_atom_f64(mode, a, PA, has4, st);
+    e = mode == 5 ? launch_atom_emb_f64(a, PA, has4, st) : launch_atom_f64(mode, a, PA, has4, st);
   }
   if (e != cudaSuccess) return cuda_fail(e, "atom kernel");
   return POD_OK;
@@ -933,7 +966,7 @@ int pod_handle::energy_forces(const pod_system* sys, const double* c, double* E,
       if (e0 != cudaSuccess) return cuda_fail(e0, "ticket init");
     }
     if ((rc_ = mark(1, st))) return rc_;
-    if ((rc_ = run_atoms(quad ? 4 : 1, pl, nullptr, c, Ei_dst, st))) return rc_;
+    if ((rc_ = run_atoms(quad ? 4 : (emb_deg > 0 ? 5 : 1), pl, nullptr, c, Ei_dst, st))) return rc_;
     if ((rc_ = mark(2, st))) return rc_;
     cudaError_t e;
     if (fixp)
@@ -1165,6 +1198,7 @@ int pod_energy_forces_host(pod_handle* h, const pod_system* sys, const double* c
   }
   key.precision = h->precision;
   key.quad = h->quad ? 1 : 0;
+  key.emb_deg = h->emb_deg;
   key.radial = h->radial_mode;
   key.tune_gen = h->tune_gen;
   const bool graphable = !h->hgraph_off && st != nullptr && !h->timing && h->nbr_mode == 0 && h->skin == 0 &&

@@ -61,6 +61,9 @@ struct AtomArgs {
   double* D;            // mode 0: descriptors [N][M]
   const double* c;      // modes 1, 4: coefficients [M]
   const T* qbeta;       // mode 4: symmetric quadratic weights S [M][M], S_mn = beta_mn + beta_nm
+  const double* emb_a;      // mode 5: density weights a [M] (rho_i = a . D_i)
+  const double* emb_alpha;  // mode 5: embedding polynomial F(rho) = sum_k alpha_k rho^k, [emb_deg + 1]
+  int emb_deg;
   double* Ei;           // mode 1: atom energies [N]
   Q4<T>* g;             // mode 1, FP64 path: dE_i/dr_ij per pair slot [N * cap]
   unsigned long long* facc;  // mode 1, FP32 path: fixed-point force accumulators [N][4]
@@ -111,6 +114,9 @@ cudaError_t launch_segsum(int n_cfg, const CfgBox* cbox, const double* v, double
 
 cudaError_t launch_atom_f32(int mode, const AtomArgs<float>& p, int PA, bool has4, cudaStream_t st);
 cudaError_t launch_atom_f64(int mode, const AtomArgs<double>& p, int PA, bool has4, cudaStream_t st);
+// Embedding model (energy mode 5), compiled in translation units of their own.
+cudaError_t launch_atom_emb_f32(const AtomArgs<float>& p, int PA, bool has4, cudaStream_t st);
+cudaError_t launch_atom_emb_f64(const AtomArgs<double>& p, int PA, bool has4, cudaStream_t st);
 
 template <typename T>
 cudaError_t launch_gather_reduce(int N, int cap, const int* nbr_count, const int* nbr_j, const int* nbr_s,

@@ -517,3 +517,84 @@ def test_quadratic_model_energy_and_forces():
     fs = np.max(np.abs(F))
     assert np.allclose(F.sum(0), 0.0, atol=1e-12 * max(fs, 1.0) * cfg.n)
     assert np.allclose(W, W.T, atol=1e-10 * max(np.max(np.abs(W)), 1.0))
+
+
+# ----------------------------------------------------------- embedding model
+
+def _emb_weights(o, seed):
+    """Density weights on the two- and three-body columns (a MEAM-type density)
+    and a cubic embedding polynomial."""
+    g = synth.rng(seed)
+    a = np.zeros(o.M)
+    p = o.params
+    col3 = 1 + p.K2
+    a[1:col3 + p.K3 * (p.P3 + 1)] = g.normal(0.0, 1e-2, size=col3 + p.K3 * (p.P3 + 1) - 1)
+    alpha = np.array([0.3, -0.2, 5e-3, -1e-4])
+    return a, alpha
+
+
+def test_embedding_model_reduces_to_linear():
+    """alpha = 0: the embedding model of Sec. 3 is the linear model (Eq. 57a);
+    alpha = (alpha_0, alpha_1): the linear model with c + alpha_1 a, plus alpha_0
+    per atom."""
+    o = oracle.Oracle(synth.params_full())
+    cfg = synth.jitter(synth.bcc(2), 0.1, synth.rng(81))
+    c = synth.coefficients(o.M, 82)
+    a, _ = _emb_weights(o, 83)
+    Ei, E, F, W = o.energy_forces(cfg, c, fast=True)
+    Ee_i, _, Fe, We = o.energy_forces_embedding(cfg, c, a, np.zeros(3))
+    assert np.allclose(Ee_i, Ei, rtol=1e-13, atol=1e-15)
+    assert np.allclose(Fe, F, atol=1e-12) and np.allclose(We, W, atol=1e-12)
+    Ei1, _, F1, W1 = o.energy_forces(cfg, c + 0.7 * a, fast=True)
+    El_i, _, Fl, Wl = o.energy_forces_embedding(cfg, c, a, np.array([0.25, 0.7]))
+    assert np.allclose(El_i, Ei1 + 0.25, rtol=1e-12, atol=1e-13)
+    assert np.allclose(Fl, F1, atol=1e-12) and np.allclose(Wl, W1, atol=1e-12)
+
+
+def test_embedding_degree_two_is_quadratic_model():
+    """F(rho) = alpha_0 + alpha_1 rho + alpha_2 rho^2 with rho = a.D is the
+    quadratic model (Sec. 4) with c + alpha_1 a + alpha_0 e_0 and beta = alpha_2 a a^T
+    (upper triangle: a_m^2 on the diagonal, 2 a_m a_n above it) -- the paper's
+    remark that polynomial embeddings are sums of products of descriptors."""
+    o = oracle.Oracle(synth.params_full())
+    cfg = synth.jitter(synth.bcc(2), 0.1, synth.rng(84))
+    c = synth.coefficients(o.M, 85)
+    a, _ = _emb_weights(o, 86)
+    alpha = np.array([0.1, -0.3, 2e-2])
+    Ee_i, Ee, Fe, We = o.energy_forces_embedding(cfg, c, a, alpha)
+    beta = alpha[2] * (2.0 * np.triu(np.outer(a, a), 1) + np.diag(a * a))
+    cq = c + alpha[1] * a
+    cq[0] += alpha[0]
+    Eq_i, Eq, Fq, Wq = o.energy_forces_quadratic(cfg, cq, beta)
+    assert np.allclose(Ee_i, Eq_i, rtol=1e-12, atol=1e-13)
+    assert np.allclose(Fe, Fq, rtol=1e-10, atol=1e-12) and np.allclose(We, Wq, rtol=1e-10, atol=1e-12)
+
+
+def test_embedding_model_energy_and_forces():
+    """Cubic embedding of a MEAM-type density: energy = c.D + F(a.D) from the
+    naive descriptor sums, forces = minus central differences of that energy,
+    net force zero, virial symmetric."""
+    o = oracle.Oracle(synth.params_full())
+    cfg = synth.jitter(synth.bcc(2), 0.1, synth.rng(87))
+    c = synth.coefficients(o.M, 88)
+    a, alpha = _emb_weights(o, 89)
+    Ei, E, F, W = o.energy_forces_embedding(cfg, c, a, alpha)
+
+    def energy(cf):
+        D = o.descriptors(cf, fast=False)  # naive sums, independent of the fast path
+        rho = D @ a
+        return float(np.sum(D @ c) + np.sum(np.polyval(alpha[::-1], rho)))
+
+    assert E == pytest.approx(energy(cfg), rel=1e-11)
+    h = 1e-5
+    for k in [0, 11]:
+        for t in range(3):
+            cp = synth.Config(pos=cfg.pos.copy(), box=cfg.box)
+            cm = synth.Config(pos=cfg.pos.copy(), box=cfg.box)
+            cp.pos[k, t] += h
+            cm.pos[k, t] -= h
+            fd = -(energy(cp) - energy(cm)) / (2 * h)
+            assert F[k, t] == pytest.approx(fd, rel=1e-7, abs=1e-7)
+    fs = np.max(np.abs(F))
+    assert np.allclose(F.sum(0), 0.0, atol=1e-12 * max(fs, 1.0) * cfg.n)
+    assert np.allclose(W, W.T, atol=1e-10 * max(np.max(np.abs(W)), 1.0))
