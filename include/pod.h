@@ -130,6 +130,15 @@ int pod_info(const pod_handle* h, int* M, int* Ns, int* K, double* Q_out, double
                                    (single configuration, same size and box) instead of
                                    rebuilding it; requires a skin (pod_set_skin) that
                                    covers the displacements since that call */
+#define POD_OPT_DESCRIPTORS 6 /* three-body columns: 0 (default) the fast POD sums over all
+                                 (j, k) (Eq. 23a/26a); 1 the exclusive sums over pairs
+                                 k > j of the original POD (Eq. 15b), formed as
+                                 (D3_mn - sum_j R_m(r_ij)^2) / 2 (Eq. 15c).  Honoured by
+                                 pod_descriptors, pod_global_descriptors and the linear
+                                 model's pod_energy_forces (its adjoint carries the
+                                 extra two-body term); the quadratic and embedding models,
+                                 the descriptor tangent, the fit entry points and
+                                 pod_descriptors_static return POD_EINVAL while it is 1 */
 int pod_set_option(pod_handle* h, int option, int value);
 
 /* Neighbour-list skin (A, default 0): lists are built with r_cut + skin and pairs

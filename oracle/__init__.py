@@ -319,6 +319,53 @@ class Oracle:
             W -= d.T @ g
         return Ei, math.fsum(Ei), F, W
 
+    def exclusive3_descriptors(self, d: np.ndarray, fast: bool = True) -> np.ndarray:
+        """Descriptors of one atom with the three-body columns replaced by the
+        exclusive sums of the original POD over pairs k > j (Eq. 15b), formed from
+        the inclusive ones by Eq. 15c: (D3_mn - sum_j R_m(r_j)^2) / 2."""
+        d = np.ascontiguousarray(d, dtype=np.float64).reshape(-1, 3)
+        D = np.array(self.atom_descriptors(d, fast), dtype=np.float64)
+        if d.shape[0] == 0:
+            return D
+        R, _ = self.radial(np.linalg.norm(d, axis=1))
+        S = np.sum(R * R, axis=0)
+        p = self.params
+        col3, n3 = 1 + p.K2, p.P3 + 1
+        for m in range(p.K3):
+            D[col3 + m * n3: col3 + (m + 1) * n3] = 0.5 * (D[col3 + m * n3: col3 + (m + 1) * n3] - S[m])
+        return D
+
+    def energy_forces_exclusive3(self, cfg, c, fast: bool = True):
+        """Linear model on the exclusive three-body set (Eq. 15b):
+        E_i = c . Dx_i with ``exclusive3_descriptors``.  Forces from the explicit
+        derivatives: dDx_i,col/dr_ij = (dD3_i,col/dr_ij - 2 R_m R'_m r_ij / r) / 2 on
+        the three-body columns of mode m, assembled like ``energy_forces``."""
+        c = np.asarray(c, dtype=np.float64)
+        p = self.params
+        col3, n3 = 1 + p.K2, p.P3 + 1
+        sysd = self._system(cfg)
+        Ei = np.zeros(cfg.n)
+        F = np.zeros((cfg.n, 3))
+        W = np.zeros((3, 3))
+        for i in range(cfg.n):
+            js, _, d = self.neighbors(cfg, i, sysd)
+            Ei[i] = self.exclusive3_descriptors(d, fast) @ c
+            if len(js) == 0:
+                continue
+            dD = np.array(self.atom_dD(d, fast))    # (n_j, M, 3): dD_im / dr_ij
+            r = np.linalg.norm(d, axis=1)
+            R, dR = self.radial(r)
+            u = d / r[:, None]
+            for m in range(p.K3):
+                dS = 2.0 * (R[:, m] * dR[:, m])[:, None] * u    # (n_j, 3)
+                for n in range(n3):
+                    dD[:, col3 + m * n3 + n, :] = 0.5 * (dD[:, col3 + m * n3 + n, :] - dS)
+            g = np.einsum("jmt,m->jt", dD, c)
+            F[i] += g.sum(axis=0)
+            np.subtract.at(F, js, g)
+            W -= d.T @ g
+        return Ei, math.fsum(Ei), F, W
+
     def energy_forces_embedding(self, cfg, c, a, alpha, fast: bool = True):
         """Embedding model of Sec. 3 (EAM and MEAM written with POD descriptors):
         E_i = sum_m c_m D_im + F(rho_i) with the density rho_i = sum_m a_m D_im and

@@ -27,6 +27,7 @@ POD_OK, POD_EINVAL, POD_ENOMEM, POD_ECUDA, POD_ERANGE, POD_ENONFINITE, POD_ESING
     0, -1, -2, -3, -4, -5, -6, -7)
 POD_FP64, POD_MIXED = 0, 1
 POD_OPT_SYNC, POD_OPT_PRECISION, POD_OPT_TIMING, POD_OPT_RADIAL, POD_OPT_NEIGHBOR_REUSE = 1, 2, 3, 4, 5
+POD_OPT_DESCRIPTORS = 6
 ERROR_NAMES = {0: "POD_OK", -1: "POD_EINVAL", -2: "POD_ENOMEM", -3: "POD_ECUDA", -4: "POD_ERANGE",
                -5: "POD_ENONFINITE", -6: "POD_ESINGULAR", -7: "POD_ENEIGH"}
 
@@ -329,6 +330,13 @@ class POD:
 
     def set_neighbor_reuse(self, on: bool):
         pod_set_option(self.h, POD_OPT_NEIGHBOR_REUSE, 1 if on else 0)
+
+    def set_descriptor_set(self, which: str):
+        """Three-body columns: 'fast' (default, the fast POD sums of Eq. 26a) or
+        'exclusive' (the original POD sums over pairs k > j, Eq. 15b)."""
+        if which not in ("fast", "exclusive"):
+            raise ValueError("descriptor set must be 'fast' or 'exclusive'")
+        pod_set_option(self.h, POD_OPT_DESCRIPTORS, 1 if which == "exclusive" else 0)
 
     def md_step(self, pos_soa, v, F, c, box, mass, dt, E, pbc=(1, 1, 1), stream=None):
         """One velocity-Verlet step; pos_soa, v, F: (3, N) float64 CUDA tensors updated in place."""

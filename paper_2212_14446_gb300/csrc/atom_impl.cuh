@@ -229,7 +229,9 @@ __global__ void __launch_bounds__(ATOM_MAX_WPB * 32, atom_min_blocks<T, MODE, KT
     return;
   }
 
-  // ---------------- forward: B_m[x] = sum_j R_m(r_ij) A_x(u_ij)   (Eq. 24b)
+  // ---------------- forward: B_m[x] = sum_j R_m(r_ij) A_x(u_ij)   (Eq. 24b),
+  // and S3 = sum_j R_m(r_ij)^2 for the exclusive three-body set (Eq. 15b)
+  T S3 = T(0);
   T B[NA];
 #pragma unroll
   for (int x = 0; x < NA; ++x) B[x] = T(0);
@@ -253,6 +255,7 @@ __global__ void __launch_bounds__(ATOM_MAX_WPB * 32, atom_min_blocks<T, MODE, KT
           const float2 R2 = make_float2(R, R);
 #pragma unroll
           for (int k = 0; k < Mono<PA>::NA2; ++k) B2[k] = __ffma2_rn(A2[k], R2, B2[k]);
+          S3 = fmaf(R, R, S3);
         }
       } else {
         for (int jj = 0; jj < nc; ++jj) {
@@ -262,6 +265,7 @@ __global__ void __launch_bounds__(ATOM_MAX_WPB * 32, atom_min_blocks<T, MODE, KT
           Mono<PA>::eval(u.x, u.y, u.z, Am);
 #pragma unroll
           for (int x = 0; x < NA; ++x) B[x] = fma(R, Am[x], B[x]);
+          S3 = fma(R, R, S3);
         }
       }
     }
@@ -282,9 +286,10 @@ __global__ void __launch_bounds__(ATOM_MAX_WPB * 32, atom_min_blocks<T, MODE, KT
       T d3[PA + 1];
       Mono<PA>::d3(B, d3);
       if (m < p.K3) {
+        // exclusive set (Eq. 15b, pairs k > j): (D3 - sum_j R_m^2) / 2, as (u_j . u_j)^n = 1
 #pragma unroll
         for (int n = 0; n <= PA; ++n)
-          if (n <= p.P3) Di[p.col3 + m * (p.P3 + 1) + n] = (double)d3[n];
+          if (n <= p.P3) Di[p.col3 + m * (p.P3 + 1) + n] = (double)(p.excl3 ? T(0.5) * (d3[n] - S3) : d3[n]);
       }
       if (HAS4 && m < p.K4) {
         T D4[KA];
@@ -522,6 +527,7 @@ __global__ void __launch_bounds__(ATOM_MAX_WPB * 32, atom_min_blocks<T, MODE, KT
 
   // ---------------- energy and adjoint a = dE_i/dB_m  (Eq. 26c generalised)
   T E = T(0);
+  T s3 = T(0);  // exclusive three-body set: dE_i/dS3 of this lane's mode
   {
     T a[NAP];
 #pragma unroll
@@ -537,6 +543,15 @@ __global__ void __launch_bounds__(ATOM_MAX_WPB * 32, atom_min_blocks<T, MODE, KT
       T w4[KA];
 #pragma unroll
       for (int q = 0; q < KA; ++q) w4[q] = (HAS4 && q < p.KA4 && m < p.K4) ? c[p.col4 + m * p.KA4 + q] : T(0);
+      if (p.excl3) {
+        // sum_n c_n (D3_n - S3) / 2: weights c_n / 2 on the inclusive D3_n and
+        // -sum_n c_n / 2 on S3
+#pragma unroll
+        for (int n = 0; n <= PA; ++n) {
+          s3 = fma(T(-0.5), h[n], s3);
+          h[n] *= T(0.5);
+        }
+      }
       T Elin = T(0);  // quadratic model: the linear part c . D of this lane's columns
       if (MODE == 4) {
         const T* Da = reinterpret_cast<const T*>(wb + lay.off_D) + a_loc * lay.MS;
@@ -608,6 +623,7 @@ __global__ void __launch_bounds__(ATOM_MAX_WPB * 32, atom_min_blocks<T, MODE, KT
       Mono<PA>::d3_adjoint(B, h, a);
       a[0] += a0;
       if (m == 0) E += c0;
+      E = fma(s3, S3, E);
       // quadratic model: E above is sum_col (dE/dD_col) D_col = c.D + 2 E_quad, so
       // E_i = (c.D + that) / 2
       if (MODE == 4) E = T(0.5) * (E + Elin);
@@ -639,6 +655,11 @@ __global__ void __launch_bounds__(ATOM_MAX_WPB * 32, atom_min_blocks<T, MODE, KT
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) efix += __shfl_xor_sync(0xffffffffu, efix, o);
     if (lane == 0) ew_add(p.facc + 4 * (size_t)p.N + (gwarp % EW_COPIES) * EW_STRIDE, efix);
+  }
+  if (p.excl3) {  // dE_i/dS3 of every (atom, mode) for the pair pass
+    __syncwarp();
+    se[lane] = s3;
+    __syncwarp();
   }
 
   // ---------------- adjoint pair pass: g_ij = sum_{m,x} a_mx dB_mx/dr_ij  (Eq. 24c)
@@ -709,6 +730,7 @@ __global__ void __launch_bounds__(ATOM_MAX_WPB * 32, atom_min_blocks<T, MODE, KT
             e2[2 * x4 + 1] = __ffma2_rn(hi, R2, e2[2 * x4 + 1]);
           }
           ps = fma(Rpv[mm], u2.x + u2.y, ps);
+          if (p.excl3) ps = fma(T(2) * se[a * K + mm] * Rv[mm], Rpv[mm], ps);  // dS3/dr = 2 R R'
         }
 #pragma unroll
         for (int x = 0; x < NAP; ++x) {
@@ -740,6 +762,7 @@ __global__ void __launch_bounds__(ATOM_MAX_WPB * 32, atom_min_blocks<T, MODE, KT
             e[4 * x4 + 3] = fma(av.w, Rm, e[4 * x4 + 3]);
           }
           ps = fma(Rpm, um, ps);
+          if (p.excl3) ps = fma(T(2) * se[a * K + mm] * Rm, Rpm, ps);  // dS3/dr = 2 R R'
         }
       }
       T gx, gy, gz;

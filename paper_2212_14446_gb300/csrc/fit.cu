@@ -287,6 +287,7 @@ int pod_handle::fit_build(const pod_system* bsys, const double* E_ref, const dou
   int rc_ = validate_system(bsys);
   if (rc_) return rc_;
   if (!E_ref || !F_ref) return fail(POD_EINVAL, "E_ref and F_ref are required");
+  if (excl3) return fail(POD_EINVAL, "the fit takes the fast POD descriptor set");
   if (!(o.w_E >= 0) || !(o.w_F >= 0) || !(o.gamma_reg >= 0)) return fail(POD_EINVAL, "weights and gamma must be >= 0");
   const int Mp = (M + 3) / 4 * 4;
   if (Mp > GRAM_MP) return fail(POD_EINVAL, "the fit supports at most %d descriptors", GRAM_MP);

@@ -231,7 +231,7 @@ bool pod_handle::HostKey::operator==(const HostKey& o) const {
   for (int d = 0; d < 3; ++d)
     if (pbc[d] != o.pbc[d] || box[d] != o.box[d]) return false;
   return N == o.N && precision == o.precision && quad == o.quad && radial == o.radial && tune_gen == o.tune_gen &&
-         emb_deg == o.emb_deg;
+         emb_deg == o.emb_deg && excl3 == o.excl3;
 }
 
 void pod_handle::drop_host_graph() {
@@ -457,6 +457,11 @@ int pod_set_option(pod_handle* h, int option, int value) {
   }
   if (option == POD_OPT_TIMING) {
     h->timing = value ? 1 : 0;
+    return POD_OK;
+  }
+  if (option == POD_OPT_DESCRIPTORS) {
+    if (value != 0 && value != 1) return h->fail(POD_EINVAL, "descriptor set must be 0 (fast POD) or 1");
+    h->excl3 = value;
     return POD_OK;
   }
   if (option == POD_OPT_PRECISION) {
@@ -784,6 +789,7 @@ void pod_handle::fill_args(AtomArgs<T>& a, const Plan& pl) {
   a.P4 = P.P4;
   a.KA4 = KA4;
   a.M = M;
+  a.excl3 = excl3;
   a.col3 = 1 + P.K2;
   a.col4 = a.col3 + P.K3 * (P.P3 + 1);
   a.status = (int*)status.p;
@@ -927,6 +933,8 @@ int pod_handle::energy_forces(const pod_system* sys, const double* c, double* E,
     Plan pl;
     if ((rc_ = plan(sys, pl))) return rc_;
     if (pl.batched && W) return fail(POD_EINVAL, "the virial is not available for batches of configurations");
+    if (excl3 && (quad || emb_deg > 0))
+      return fail(POD_EINVAL, "the quadratic and embedding models take the fast POD descriptor set");
     if ((rc_ = mark(0, st))) return rc_;
     const bool reuse = nbr_mode == 1 && reuse_ok && !pl.batched && last_pl.N == N && last_pl.cg.L[0] == pl.cg.L[0] &&
                        last_pl.cg.L[1] == pl.cg.L[1] && last_pl.cg.L[2] == pl.cg.L[2];
@@ -1087,6 +1095,7 @@ int pod_handle::global_desc(const pod_system* sys, const double* vdir, double* G
   int rc_ = validate_system(sys);
   if (rc_) return rc_;
   if (!Gout) return fail(POD_EINVAL, "output is NULL");
+  if (vdir && excl3) return fail(POD_EINVAL, "the descriptor tangent takes the fast POD descriptor set");
   const int N = sys->n_atoms;
   retries = 0;
   for (;;) {
@@ -1199,6 +1208,7 @@ int pod_energy_forces_host(pod_handle* h, const pod_system* sys, const double* c
   key.precision = h->precision;
   key.quad = h->quad ? 1 : 0;
   key.emb_deg = h->emb_deg;
+  key.excl3 = h->excl3;
   key.radial = h->radial_mode;
   key.tune_gen = h->tune_gen;
   const bool graphable = !h->hgraph_off && st != nullptr && !h->timing && h->nbr_mode == 0 && h->skin == 0 &&

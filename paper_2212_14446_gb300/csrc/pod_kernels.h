@@ -64,6 +64,7 @@ struct AtomArgs {
   const double* emb_a;      // mode 5: density weights a [M] (rho_i = a . D_i)
   const double* emb_alpha;  // mode 5: embedding polynomial F(rho) = sum_k alpha_k rho^k, [emb_deg + 1]
   int emb_deg;
+  int excl3;            // modes 0, 1: three-body columns as the exclusive sums of Eq. 15b
   double* Ei;           // mode 1: atom energies [N]
   Q4<T>* g;             // mode 1, FP64 path: dE_i/dr_ij per pair slot [N * cap]
   unsigned long long* facc;  // mode 1, FP32 path: fixed-point force accumulators [N][4]

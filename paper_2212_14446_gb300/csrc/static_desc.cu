@@ -109,6 +109,7 @@ extern "C" int pod_descriptors_static(pod_handle* h, const pod_system* sys, doub
   if (!h) return POD_EINVAL;
   if (!sys || !sys->pos || !D) return h->fail(POD_EINVAL, "system, positions and D are required");
   if (sys->n_configs > 1) return h->fail(POD_EINVAL, "pod_descriptors_static takes a single configuration");
+  if (h->excl3) return h->fail(POD_EINVAL, "pod_descriptors_static takes the fast POD descriptor set");
   const int N = sys->n_atoms;
   if (N < 1 || N > STATIC_MAX_ATOMS)
     return h->fail(POD_EINVAL, "pod_descriptors_static handles 1..%d atoms (got %d)", STATIC_MAX_ATOMS, N);

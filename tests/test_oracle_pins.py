@@ -598,3 +598,59 @@ def test_embedding_model_energy_and_forces():
     fs = np.max(np.abs(F))
     assert np.allclose(F.sum(0), 0.0, atol=1e-12 * max(fs, 1.0) * cfg.n)
     assert np.allclose(W, W.T, atol=1e-10 * max(np.max(np.abs(W)), 1.0))
+
+
+# ------------------------------------------- exclusive three-body set (Eq. 15b)
+
+def test_exclusive3_descriptors_are_the_pair_sums():
+    """The exclusive three-body columns formed from the inclusive ones (Eq. 15c)
+    equal the plain sums over pairs k > j of Eq. 15b written out in C; the two-,
+    four-body and one-body columns are the inclusive ones."""
+    o = oracle.Oracle(synth.params_full())
+    p = o.params
+    col3, n3 = 1 + p.K2, p.P3 + 1
+    g = synth.rng(101)
+    for n in (1, 2, 7, 19):
+        d = g.normal(0.0, 1.0, size=(n, 3))
+        d *= g.uniform(1.5, 4.8, size=n)[:, None] / np.linalg.norm(d, axis=1)[:, None]
+        Dx = o.exclusive3_descriptors(d, fast=False)
+        Dn = o.atom_descriptors(d, fast=False)
+        ex = o.atom_d3_exclusive(d)
+        assert np.allclose(Dx[col3:col3 + p.K3 * n3].reshape(p.K3, n3), ex, rtol=1e-12, atol=1e-13)
+        assert np.array_equal(Dx[:col3], Dn[:col3]) and np.array_equal(Dx[col3 + p.K3 * n3:], Dn[col3 + p.K3 * n3:])
+
+
+def test_exclusive3_energy_and_forces():
+    """Linear model on the exclusive set: energy from the naive pair sums of
+    Eq. 15b, forces = minus central differences of that energy, net force zero,
+    virial symmetric."""
+    o = oracle.Oracle(synth.params_full())
+    p = o.params
+    col3, n3 = 1 + p.K2, p.P3 + 1
+    cfg = synth.jitter(synth.bcc(2), 0.1, synth.rng(102))
+    c = synth.coefficients(o.M, 103)
+    Ei, E, F, W = o.energy_forces_exclusive3(cfg, c)
+
+    def energy(cf):
+        sysd = o._system(cf)
+        tot = 0.0
+        for i in range(cf.n):
+            _, _, d = o.neighbors(cf, i, sysd)
+            D = np.array(o.atom_descriptors(d, fast=False))
+            D[col3:col3 + p.K3 * n3] = o.atom_d3_exclusive(d).ravel()
+            tot += float(D @ c)
+        return tot
+
+    assert E == pytest.approx(energy(cfg), rel=1e-11)
+    h = 1e-5
+    for k in [0, 13]:
+        for t in range(3):
+            cp = synth.Config(pos=cfg.pos.copy(), box=cfg.box)
+            cm = synth.Config(pos=cfg.pos.copy(), box=cfg.box)
+            cp.pos[k, t] += h
+            cm.pos[k, t] -= h
+            fd = -(energy(cp) - energy(cm)) / (2 * h)
+            assert F[k, t] == pytest.approx(fd, rel=1e-7, abs=1e-7)
+    fs = np.max(np.abs(F))
+    assert np.allclose(F.sum(0), 0.0, atol=1e-12 * max(fs, 1.0) * cfg.n)
+    assert np.allclose(W, W.T, atol=1e-10 * max(np.max(np.abs(W)), 1.0))
