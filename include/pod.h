@@ -94,6 +94,19 @@ typedef struct {
   const int* atom_offs;    /* HOST [n_configs + 1] atom offsets (batch only)    */
   const double* boxes;     /* HOST [n_configs][3] box lengths   (batch only)    */
   const int* pbcs;         /* HOST [n_configs][3] or NULL (= pbc for all)       */
+  int n_local;             /* single configuration, pod_energy_forces(_host):
+                              atoms [0, n_local) are local -- their energies E_i
+                              and pair gradients are evaluated -- and atoms
+                              [n_local, n_atoms) are ghosts (periodic or
+                              neighbouring-domain copies) that only appear as
+                              neighbours; forces are returned on every atom
+                              (ghosts get the reactions of local atoms' terms)
+                              and E, W sum the local terms only.  0 = every atom
+                              is local.  The building block of a spatial domain
+                              decomposition: summing each domain's local-plus-
+                              ghost forces onto the owning atoms gives the forces
+                              of the whole system.  Other entry points evaluate
+                              every atom; pod_md_step refuses ghosts.           */
 } pod_system;
 
 /* Creates a handle: validates params, builds the POD basis on the host (the

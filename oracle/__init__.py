@@ -293,6 +293,22 @@ class Oracle:
         Ei = {i: pg[i][0] for i in need}
         return Ei, None, F, None
 
+    def energy_forces_local(self, cfg, c, n_local: int, fast: bool = True):
+        """Atoms [0, n_local) local, the rest ghosts: E and W of the local atoms'
+        terms (Eq. 57a), forces on every atom from those terms (a ghost receives
+        the reactions -g_ij of its local neighbours' pair gradients)."""
+        c = np.asarray(c, dtype=np.float64)
+        pg = self.pair_grads(cfg, c, range(n_local), fast)
+        Ei = np.zeros(cfg.n)
+        F = np.zeros((cfg.n, 3))
+        W = np.zeros((3, 3))
+        for i in range(n_local):
+            Ei[i], js, _, d, g = pg[i]
+            F[i] += g.sum(axis=0)
+            np.subtract.at(F, js, g)
+            W -= d.T @ g
+        return Ei, math.fsum(Ei[:n_local]), F, W
+
     def energy_forces_quadratic(self, cfg, c, beta, fast: bool = True):
         """Quadratic model of Sec. 4 (the extension of Eq. 57a by products of
         descriptors): E_i = sum_m c_m D_im + sum_{m <= n} beta_mn D_im D_in, with

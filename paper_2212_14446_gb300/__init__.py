@@ -51,7 +51,7 @@ class pod_system(C.Structure):
     _fields_ = [("n_atoms", C.c_int), ("pos", C.POINTER(C.c_double)),
                 ("box", C.c_double * 3), ("pbc", C.c_int * 3),
                 ("n_configs", C.c_int), ("atom_offs", C.POINTER(C.c_int)),
-                ("boxes", C.POINTER(C.c_double)), ("pbcs", C.POINTER(C.c_int))]
+                ("boxes", C.POINTER(C.c_double)), ("pbcs", C.POINTER(C.c_int)), ("n_local", C.c_int)]
 
 
 class pod_fit_opts(C.Structure):
@@ -170,9 +170,10 @@ def _stream(stream):
     return C.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
 
 
-def make_system(pos_ptr, n_atoms, box, pbc=(1, 1, 1), batch=None):
+def make_system(pos_ptr, n_atoms, box, pbc=(1, 1, 1), batch=None, n_local=0):
     s = pod_system()
     s.n_atoms = int(n_atoms)
+    s.n_local = int(n_local)
     s.pos = pos_ptr
     s.box = (C.c_double * 3)(*[float(b) for b in box])
     s.pbc = (C.c_int * 3)(*[int(p) for p in pbc])
@@ -350,8 +351,8 @@ class POD:
     def timing(self):
         return pod_timing(self.h)
 
-    def system(self, pos_soa, box, pbc=(1, 1, 1)):
-        return make_system(_dptr(pos_soa), pos_soa.shape[1], box, pbc)
+    def system(self, pos_soa, box, pbc=(1, 1, 1), n_local=0):
+        return make_system(_dptr(pos_soa), pos_soa.shape[1], box, pbc, n_local=n_local)
 
     def neighbors(self, pos, box, pbc=(1, 1, 1), cap=64, stream=None):
         import torch
@@ -390,7 +391,9 @@ class POD:
         return Gd
 
     def energy_forces(self, pos, box, c, pbc=(1, 1, 1), atom_energies=True, forces=True, virial=True,
-                      stream=None):
+                      stream=None, n_local=0):
+        """E, E_i, F, W.  n_local > 0: atoms [0, n_local) are local and the rest
+        ghosts (forces on all atoms, energies and virial of the local terms)."""
         import torch
         x = _soa(pos)
         n = x.shape[1]
@@ -400,7 +403,7 @@ class POD:
         Ei = torch.empty(n, dtype=torch.float64, device=dev) if atom_energies else None
         F = torch.empty((3, n), dtype=torch.float64, device=dev) if forces else None
         W = torch.empty(9, dtype=torch.float64, device=dev) if virial else None
-        pod_energy_forces(self.h, self.system(x, box, pbc), c, E, Ei, F, W, stream)
+        pod_energy_forces(self.h, self.system(x, box, pbc, n_local), c, E, Ei, F, W, stream)
         return {"E": E, "Ei": Ei, "F": None if F is None else F.t(), "W": None if W is None else W.view(3, 3)}
 
     def set_quadratic(self, beta=None):

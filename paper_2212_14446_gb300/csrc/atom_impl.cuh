@@ -159,19 +159,19 @@ __global__ void __launch_bounds__(ATOM_MAX_WPB * 32, atom_min_blocks<T, MODE, KT
   // FP32 energy modes: E and the virial accumulate in fixed point (the tail of
   // the force accumulators); FP64: per-warp virial partials for the gather
   constexpr bool FIXP = EMODE && std::is_same<T, float>::value;
-  if (atom0 >= p.N) {  // uniform per warp
+  if (atom0 >= p.n_eval) {  // uniform per warp
     if (EMODE && !FIXP && lane < 9) p.wpart[(size_t)gwarp * 9 + lane] = 0.0;
     return;
   }
   if (lane < A) {
     const int i = atom0 + lane;
-    scnt[lane] = (i < p.N) ? min(p.nbr_count[i], p.cap) : 0;
+    scnt[lane] = (i < p.n_eval) ? min(p.nbr_count[i], p.cap) : 0;
   }
   __syncwarp();
   int nmax = 0;
   for (int a = 0; a < A; ++a) nmax = max(nmax, scnt[a]);
   const int nchunks = (nmax + CH - 1) / CH;
-  const bool am = (a_loc < A) && (atom0 + a_loc < p.N);
+  const bool am = (a_loc < A) && (atom0 + a_loc < p.n_eval);
   const int my_n = am ? scnt[a_loc] : 0;
 
   if (MODE == 2) {
@@ -878,7 +878,7 @@ static cudaError_t launch_one(const AtomArgs<T>& p, const AtomLayout& lay, cudaS
   static size_t granted[64] = {};
   if (cudaError_t e = grant_smem((const void*)kern, smem, granted)) return e;
   const int atoms_per_block = wpb * lay.A;
-  const int grid = (p.N + atoms_per_block - 1) / atoms_per_block;
+  const int grid = (p.n_eval + atoms_per_block - 1) / atoms_per_block;
   if (grid > 0) kern<<<grid, wpb * 32, smem, st>>>(p, lay);
   return cudaGetLastError();
 }

@@ -50,7 +50,7 @@ constexpr int GATHER_MIN_BLOCKS = 3;  // 16-warp blocks: 40 registers
 
 template <typename T>
 __global__ void __launch_bounds__(GATHER_MAX_WPB * 32, GATHER_MIN_BLOCKS)
-    gather_reduce_kernel(int N, int cap, const int* __restrict__ nbr_count, const int* __restrict__ nbr_j,
+    gather_reduce_kernel(int N, int n_eval, int cap, const int* __restrict__ nbr_count, const int* __restrict__ nbr_j,
                          const int* __restrict__ nbr_s, const int* __restrict__ rev_in, int* __restrict__ rev_out,
                          const Q4<T>* __restrict__ g, const double* __restrict__ Ei,
                          const double* __restrict__ wpart, int n_wpart, double* __restrict__ F, double fscale,
@@ -87,25 +87,27 @@ __global__ void __launch_bounds__(GATHER_MAX_WPB * 32, GATHER_MIN_BLOCKS)
       }
       if ((v0 && q0 < 0) || (v1 && q1 < 0))
         atomicOr(status, ST_REV);  // a list without its reverse pair: reported, never read out of bounds
-      if (v0) {
+      // only atoms below n_eval have pair gradients (the rest are ghost atoms)
+      const size_t qmax = (size_t)n_eval * cap;
+      if (v0 && k0 < n_eval) {
         const Q4<T> a = g[p0];
         f0 += a.x;
         f1 += a.y;
         f2 += a.z;
       }
-      if (v1) {
+      if (v1 && k1 < n_eval) {
         const Q4<T> a = g[p1];
         h0 += a.x;
         h1 += a.y;
         h2 += a.z;
       }
-      if (q0 >= 0) {
+      if (q0 >= 0 && (size_t)q0 < qmax) {
         const Q4<T> b = g[q0];
         f0 -= b.x;
         f1 -= b.y;
         f2 -= b.z;
       }
-      if (q1 >= 0) {
+      if (q1 >= 0 && (size_t)q1 < qmax) {
         const Q4<T> b = g[q1];
         h0 -= b.x;
         h1 -= b.y;
@@ -130,8 +132,8 @@ __global__ void __launch_bounds__(GATHER_MAX_WPB * 32, GATHER_MIN_BLOCKS)
       if (!isfinite(v)) atomicOr(status, ST_NONFINITE);
     }
     if (lane == 0) {
-      eacc += Ei[k0];
-      if (has1) eacc += Ei[k1];
+      if (k0 < n_eval) eacc += Ei[k0];
+      if (has1 && k1 < n_eval) eacc += Ei[k1];
     }
   }
   // virial partials of the atom kernel, a fixed subset per warp of this block
@@ -210,13 +212,13 @@ cudaError_t launch_finalize(int N, const unsigned long long* facc, double* F, do
 }
 
 template <typename T>
-cudaError_t launch_gather_reduce(int N, int cap, const int* nbr_count, const int* nbr_j, const int* nbr_s,
+cudaError_t launch_gather_reduce(int N, int n_eval, int cap, const int* nbr_count, const int* nbr_j, const int* nbr_s,
                                  const int* rev_in, int* rev_out, const Q4<T>* g, const double* Ei,
                                  const double* wpart, int n_wpart, double* F, double fscale, double* part,
                                  int nblocks, unsigned* ticket, double* E, double* W, int* status, cudaStream_t st,
                                  int wpb) {
   if (wpb < 1 || wpb > GATHER_MAX_WPB) return cudaErrorInvalidValue;
-  gather_reduce_kernel<T><<<nblocks, wpb * 32, 0, st>>>(N, cap, nbr_count, nbr_j, nbr_s, rev_in, rev_out, g,
+  gather_reduce_kernel<T><<<nblocks, wpb * 32, 0, st>>>(N, n_eval, cap, nbr_count, nbr_j, nbr_s, rev_in, rev_out, g,
                                                                Ei, wpart, n_wpart, F, fscale, part, ticket, E, W,
                                                                status);
   return cudaGetLastError();
@@ -230,11 +232,11 @@ int gather_blocks(int N, int wpb, int bps) {
   return want < full ? (want > 0 ? want : 1) : full;
 }
 
-template cudaError_t launch_gather_reduce<float>(int, int, const int*, const int*, const int*, const int*, int*,
+template cudaError_t launch_gather_reduce<float>(int, int, int, const int*, const int*, const int*, const int*, int*,
                                                  const Q4<float>*, const double*, const double*, int, double*,
                                                  double, double*, int, unsigned*, double*, double*, int*,
                                                  cudaStream_t, int);
-template cudaError_t launch_gather_reduce<double>(int, int, const int*, const int*, const int*, const int*, int*,
+template cudaError_t launch_gather_reduce<double>(int, int, int, const int*, const int*, const int*, const int*, int*,
                                                   const Q4<double>*, const double*, const double*, int, double*,
                                                   double, double*, int, unsigned*, double*, double*, int*,
                                                   cudaStream_t, int);

@@ -231,7 +231,7 @@ bool pod_handle::HostKey::operator==(const HostKey& o) const {
   for (int d = 0; d < 3; ++d)
     if (pbc[d] != o.pbc[d] || box[d] != o.box[d]) return false;
   return N == o.N && precision == o.precision && quad == o.quad && radial == o.radial && tune_gen == o.tune_gen &&
-         emb_deg == o.emb_deg && excl3 == o.excl3;
+         emb_deg == o.emb_deg && excl3 == o.excl3 && n_local == o.n_local;
 }
 
 void pod_handle::drop_host_graph() {
@@ -769,6 +769,7 @@ template <typename T>
 void pod_handle::fill_args(AtomArgs<T>& a, const Plan& pl) {
   std::memset(&a, 0, sizeof(a));
   a.N = pl.N;
+  a.n_eval = n_eval_cur > 0 ? n_eval_cur : pl.N;
   a.cap = pl.cap;
   a.nbr_count = (const int*)nbr_count.p;
   a.nbr_j = (const int*)nbr_j.p;
@@ -914,6 +915,7 @@ int pod_handle::validate_system(const pod_system* sys) {
   if (!sys->pos) return fail(POD_EINVAL, "positions are NULL");
   if (sys->n_configs > 1 && (!sys->atom_offs || !sys->boxes))
     return fail(POD_EINVAL, "a batch needs atom_offs and boxes");
+  if (sys->n_local < 0 || sys->n_local > sys->n_atoms) return fail(POD_EINVAL, "n_local must be in [0, n_atoms]");
   if (device >= 0) {
     int cur = -1;
     if (cudaGetDevice(&cur) == cudaSuccess && cur != device)
@@ -935,6 +937,10 @@ int pod_handle::energy_forces(const pod_system* sys, const double* c, double* E,
     if (pl.batched && W) return fail(POD_EINVAL, "the virial is not available for batches of configurations");
     if (excl3 && (quad || emb_deg > 0))
       return fail(POD_EINVAL, "the quadratic and embedding models take the fast POD descriptor set");
+    if (pl.batched && sys->n_local > 0 && sys->n_local != N)
+      return fail(POD_EINVAL, "local and ghost atoms apply to a single configuration");
+    // atoms [0, n_eval) carry energy terms; the rest are ghosts that receive forces
+    const int n_eval = (sys->n_local > 0 && sys->n_local < N) ? sys->n_local : N;
     if ((rc_ = mark(0, st))) return rc_;
     const bool reuse = nbr_mode == 1 && reuse_ok && !pl.batched && last_pl.N == N && last_pl.cg.L[0] == pl.cg.L[0] &&
                        last_pl.cg.L[1] == pl.cg.L[1] && last_pl.cg.L[2] == pl.cg.L[2];
@@ -959,7 +965,7 @@ int pod_handle::energy_forces(const pod_system* sys, const double* c, double* E,
     const int* rev_in = reuse ? (const int*)rev.p : nullptr;
     int* rev_out = keep_rev ? (int*)rev.p : nullptr;
     if (!fixp && (rc_ = ensure(g, sizeof(Q4<double>) * (size_t)N * pl.cap, "pair gradients"))) return rc_;
-    const int nwarp = atom_warps(N, K, pl.shape.atom_wpb);
+    const int nwarp = atom_warps(n_eval, K, pl.shape.atom_wpb);
     if (!fixp && (rc_ = ensure(wpart, sizeof(double) * 9 * (size_t)nwarp, "virial partials"))) return rc_;
     double* Ei_dst = Ei_user;
     if (!Ei_dst) {
@@ -974,13 +980,20 @@ int pod_handle::energy_forces(const pod_system* sys, const double* c, double* E,
       if (e0 != cudaSuccess) return cuda_fail(e0, "ticket init");
     }
     if ((rc_ = mark(1, st))) return rc_;
-    if ((rc_ = run_atoms(quad ? 4 : (emb_deg > 0 ? 5 : 1), pl, nullptr, c, Ei_dst, st))) return rc_;
+    if (n_eval < N) {  // ghost atoms have no energy of their own
+      cudaError_t ez = cudaMemsetAsync(Ei_dst + n_eval, 0, sizeof(double) * (size_t)(N - n_eval), st);
+      if (ez != cudaSuccess) return cuda_fail(ez, "ghost atom energies");
+    }
+    n_eval_cur = n_eval;
+    rc_ = run_atoms(quad ? 4 : (emb_deg > 0 ? 5 : 1), pl, nullptr, c, Ei_dst, st);
+    n_eval_cur = 0;
+    if (rc_) return rc_;
     if ((rc_ = mark(2, st))) return rc_;
     cudaError_t e;
     if (fixp)
       e = launch_finalize(N, fa, F, 1.0, nblk, E, W, st);
     else
-      e = launch_gather_reduce<double>(N, pl.cap, (const int*)nbr_count.p, (const int*)nbr_j.p,
+      e = launch_gather_reduce<double>(N, n_eval, pl.cap, (const int*)nbr_count.p, (const int*)nbr_j.p,
                                        (const int*)nbr_s.p, rev_in, rev_out, (const Q4<double>*)g.p, Ei_dst,
                                        (const double*)wpart.p, nwarp, F, 1.0, (double*)Wat.p, nblk,
                                        (unsigned*)offs.p, E, W, (int*)status.p, st, pl.shape.gather_wpb);
@@ -1009,6 +1022,8 @@ int pod_handle::energy_forces(const pod_system* sys, const double* c, double* E,
 // Units: mass in amu, dt in fs, forces in eV/A (1 eV/(A amu) = 9.648533212e-3 A/fs^2).
 int pod_handle::md_step(const pod_system* sys, double* pos, double* v, double* F, const double* c, double mass,
                         double dt, double* E, cudaStream_t st) {
+  if (sys && sys->n_local > 0 && sys->n_local != sys->n_atoms)
+    return fail(POD_EINVAL, "md_step integrates every atom: no ghost atoms");
   if (!sys || !pos || !v || !F || !c || !E) return fail(POD_EINVAL, "md_step: NULL argument");
   if (sys->n_configs > 1) return fail(POD_EINVAL, "md_step takes a single configuration");
   if (!(mass > 0) || !(dt > 0)) return fail(POD_EINVAL, "mass and dt must be positive");
@@ -1209,6 +1224,7 @@ int pod_energy_forces_host(pod_handle* h, const pod_system* sys, const double* c
   key.quad = h->quad ? 1 : 0;
   key.emb_deg = h->emb_deg;
   key.excl3 = h->excl3;
+  key.n_local = sys->n_local;
   key.radial = h->radial_mode;
   key.tune_gen = h->tune_gen;
   const bool graphable = !h->hgraph_off && st != nullptr && !h->timing && h->nbr_mode == 0 && h->skin == 0 &&

@@ -56,7 +56,7 @@ struct pod_handle {
   // replayed while calls repeat with the same buffers, sizes, box and settings
   struct HostKey {
     const void* ptr[6];
-    int N, pbc[3], precision, quad, radial, tune_gen, emb_deg, excl3;
+    int N, pbc[3], precision, quad, radial, tune_gen, emb_deg, excl3, n_local;
     double box[3];
     bool operator==(const HostKey& o) const;
   };
@@ -113,7 +113,8 @@ struct pod_handle {
   bool quad = false;
   DevBuf embW;        // embedding model: density weights a [M], then the polynomial alpha [deg + 1]
   int emb_deg = 0;    // 0: no embedding model
-  int excl3 = 0;      // 1: three-body descriptors as the exclusive sums of Eq. 15b  // fit: design-matrix pair gradients, per-configuration descriptor sums
+  int excl3 = 0;      // 1: three-body descriptors as the exclusive sums of Eq. 15b
+  int n_eval_cur = 0; // energy calls: atoms evaluated (the system's n_local; 0 = all)  // fit: design-matrix pair gradients, per-configuration descriptor sums
   int dm_q0 = 0, dm_q1 = 0;  // fit: descriptor-index range of the current design pass
   int colsum_table(const Plan& pl, int& nch, int& nrows2);
   int fit_build(const pod_system* batch, const double* E_ref, const double* F_ref, const pod_fit_opts& o);

@@ -47,6 +47,7 @@ struct AtomLayout {
 template <typename T>
 struct AtomArgs {
   int N, cap;
+  int n_eval;           // atoms [0, n_eval) are evaluated; the rest only appear as neighbours (ghosts)
   int wpb;              // warps per block of the launch (0: default)
   int keep_rp;          // table path: R' staged in shared memory for the adjoint pass
   const int* nbr_count;
@@ -120,7 +121,7 @@ cudaError_t launch_atom_emb_f32(const AtomArgs<float>& p, int PA, bool has4, cud
 cudaError_t launch_atom_emb_f64(const AtomArgs<double>& p, int PA, bool has4, cudaStream_t st);
 
 template <typename T>
-cudaError_t launch_gather_reduce(int N, int cap, const int* nbr_count, const int* nbr_j, const int* nbr_s,
+cudaError_t launch_gather_reduce(int N, int n_eval, int cap, const int* nbr_count, const int* nbr_j, const int* nbr_s,
                                  const int* rev_in, int* rev_out, const Q4<T>* g, const double* Ei,
                                  const double* wpart, int n_wpart, double* F, double fscale, double* part,
                                  int nblocks, unsigned* ticket, double* E, double* W, int* status, cudaStream_t st,

@@ -77,6 +77,7 @@ template <typename T>
 void static_args(const pod_handle* h, const Plan& pl, const unsigned char* base, double* D, AtomArgs<T>& a) {
   std::memset(&a, 0, sizeof(a));
   a.N = pl.N;
+  a.n_eval = pl.N;
   a.cap = pl.cap;
   a.nbr_count = reinterpret_cast<const int*>(base + OFF_CNT);
   a.nbr_j = reinterpret_cast<const int*>(base + OFF_NBRJ);

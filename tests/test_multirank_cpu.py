@@ -125,3 +125,98 @@ def test_shard_indices_cover_everything():
             assert got == list(range(n))
             sizes = [len(parallel.shard_indices(n, r, w)) for r in range(w)]
             assert max(sizes) - min(sizes) <= 1
+
+
+# ------------------------------------------------- spatial decomposition (slabs)
+
+def _slab_system():
+    p = synth.params_small()
+    cfg = synth.jitter(synth.bcc(4), 0.1, synth.rng(121))   # 128 atoms, box 13.3 A > 2 r_cut
+    return p, cfg, synth.coefficients(oracle.Oracle(p).M, 122)
+
+
+def _oracle_evaluator(o, c):
+    def evaluate(sub, sub_box, pbc, n_local):
+        cfg = synth.Config(pos=sub, box=sub_box, pbc=pbc)
+        Ei, E, F, W = o.energy_forces_local(cfg, c, n_local)
+        return E, Ei, F, W
+    return evaluate
+
+
+def test_slab_domains_cover_every_atom_once():
+    """Every atom is local in exactly one slab; every ghost lies within r_cut of
+    its slab (along the split axis) and is a periodic image of an atom."""
+    from paper_2212_14446_gb300 import parallel
+    p, cfg, _ = _slab_system()
+    for n_slabs in (2, 3):
+        owners = np.zeros(cfg.n, dtype=int)
+        for idx, sub, sub_box, pbc, n_local in parallel.slab_domains(cfg.pos, cfg.box, p.r_cut, n_slabs):
+            owners[idx[:n_local]] += 1
+            assert pbc == (0, 1, 1)
+            x = sub[:, 0]
+            assert np.all(x >= 0.0) and np.all(x < sub_box[0])
+            width = cfg.box[0] / n_slabs
+            assert np.all((x[:n_local] >= p.r_cut) & (x[:n_local] < p.r_cut + width + 1e-9))
+            # ghosts within r_cut of the slab, images of their atoms by whole boxes
+            xg = x[n_local:]
+            assert np.all((xg < p.r_cut) | (xg >= p.r_cut + width))
+            s_ = int(round(np.min(np.mod(cfg.pos[idx[:n_local], 0], cfg.box[0])) // width)) if n_local else 0
+            k = (sub[:, 0] + (s_ * width - p.r_cut) - cfg.pos[idx, 0]) / cfg.box[0]
+            assert np.allclose(k, np.round(k), atol=1e-9)
+            assert np.array_equal(sub[:, 1:], cfg.pos[idx, 1:])
+        assert np.all(owners == 1)
+
+
+def test_slab_decomposition_equals_whole_system():
+    """The oracle on 2 and 3 slab domains (local atoms + ghosts within r_cut),
+    forces summed onto the owners, equals the oracle on the whole periodic
+    system: the decomposition loses and double-counts no pair term."""
+    from paper_2212_14446_gb300 import parallel
+    p, cfg, c = _slab_system()
+    o = oracle.Oracle(p)
+    Ei, E, F, W = o.energy_forces(cfg, c, fast=True)
+    for n_slabs in (2, 3):
+        Ed, Eid, Fd, Wd = parallel.energy_forces_domains(_oracle_evaluator(o, c), cfg.pos, cfg.box, p.r_cut, n_slabs)
+        assert Ed == pytest.approx(E, rel=1e-12)
+        assert np.allclose(Eid, Ei, rtol=1e-12, atol=1e-14)
+        assert np.max(np.abs(Fd - F)) <= 1e-11 * np.max(np.abs(F))
+        assert np.max(np.abs(Wd - W)) <= 1e-11 * np.max(np.abs(W))
+
+
+def _slab_worker(rank, world, port, q):
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        from paper_2212_14446_gb300 import parallel
+        p, cfg, c = _slab_system()
+        o = oracle.Oracle(p)
+        res = parallel.energy_forces_domains(_oracle_evaluator(o, c), cfg.pos, cfg.box, p.r_cut, 3,
+                                             group=dist.group.WORLD)
+        q.put((rank,) + tuple(res))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_slab_decomposition_two_ranks():
+    """Three slabs on two CPU ranks (gloo): each rank evaluates its slabs, one
+    all-reduce stitches forces, atom energies, E and W; every rank holds the
+    single-process result."""
+    from paper_2212_14446_gb300 import parallel
+    port = _free_port()
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    procs = [ctx.Process(target=_slab_worker, args=(r, 2, port, q)) for r in range(2)]
+    for pr in procs:
+        pr.start()
+    res = [q.get(timeout=300) for _ in procs]
+    for pr in procs:
+        pr.join(timeout=60)
+        assert pr.exitcode == 0
+    p, cfg, c = _slab_system()
+    o = oracle.Oracle(p)
+    E1, Ei1, F1, W1 = parallel.energy_forces_domains(_oracle_evaluator(o, c), cfg.pos, cfg.box, p.r_cut, 3)
+    for _, E, Ei, F, W in res:
+        assert E == pytest.approx(E1, rel=1e-14)
+        assert np.allclose(F, F1, rtol=0, atol=1e-13 * np.max(np.abs(F1)))
+        assert np.allclose(Ei, Ei1, rtol=1e-14, atol=0) and np.allclose(W, W1, rtol=1e-13, atol=1e-15)
