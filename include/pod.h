@@ -55,6 +55,7 @@ extern "C" {
 #define POD_ENONFINITE (-5) /* NaN/Inf in positions or results                    */
 #define POD_ESINGULAR (-6)  /* fit: normal equations not positive definite        */
 #define POD_ENEIGH (-7)     /* neighbour or cell capacity exceeded after retry    */
+#define POD_EIO (-8)        /* a model file could not be read or written          */
 
 #define POD_FP64 0  /* every step in FP64 (reference path)                        */
 #define POD_MIXED 1 /* FP32 pair/contraction/adjoint, FP64 reductions and fit     */
@@ -122,6 +123,22 @@ int pod_create(const pod_params* params, pod_handle** out);
 
 /* Frees the handle, its device tables and workspace.  NULL is allowed. */
 int pod_destroy(pod_handle* h);
+
+/* Model files (the paper defines no format; a deployment feature).  pod_save
+ * writes the handle's parameters (r_in, r_cut, alpha, beta, gamma, K2..K4, P3, P4),
+ * its projection Q and, if c (host [M]) is not NULL, the coefficients of a linear
+ * model, as versioned text with round-trip precision; the file is written under a
+ * temporary name and renamed, so it appears whole or not at all.  Errors:
+ * POD_EINVAL (NULL, non-finite c), POD_EIO.
+ * pod_load creates a handle (precision POD_FP64 or POD_MIXED) from such a file
+ * with the saved Q, so it evaluates bit for bit like the saved handle; if the
+ * file holds coefficients and c_out is not NULL they are copied to c_out (host,
+ * capacity c_capacity >= M), and *n_c (if not NULL) is set to their number (0
+ * when the file holds none).  Errors: POD_EIO (cannot open), POD_EINVAL
+ * (malformed file, bad parameters, c_capacity too small); on errors after the
+ * handle was created *out holds it for pod_last_error and must be destroyed. */
+int pod_save(const pod_handle* h, const char* path, const double* c);
+int pod_load(const char* path, int precision, pod_handle** out, double* c_out, int c_capacity, int* n_c);
 
 /* Sizes and basis of a handle.  Any output pointer may be NULL.
  * M: descriptors per atom; Ns: snapshots; K: radial modes K_r;

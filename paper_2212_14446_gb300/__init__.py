@@ -25,11 +25,12 @@ LIB_PATH = os.path.join(_HERE, "_lib", "libfastpod.so")
 
 POD_OK, POD_EINVAL, POD_ENOMEM, POD_ECUDA, POD_ERANGE, POD_ENONFINITE, POD_ESINGULAR, POD_ENEIGH = (
     0, -1, -2, -3, -4, -5, -6, -7)
+POD_EIO = -8
 POD_FP64, POD_MIXED = 0, 1
 POD_OPT_SYNC, POD_OPT_PRECISION, POD_OPT_TIMING, POD_OPT_RADIAL, POD_OPT_NEIGHBOR_REUSE = 1, 2, 3, 4, 5
 POD_OPT_DESCRIPTORS = 6
 ERROR_NAMES = {0: "POD_OK", -1: "POD_EINVAL", -2: "POD_ENOMEM", -3: "POD_ECUDA", -4: "POD_ERANGE",
-               -5: "POD_ENONFINITE", -6: "POD_ESINGULAR", -7: "POD_ENEIGH"}
+               -5: "POD_ENONFINITE", -6: "POD_ESINGULAR", -7: "POD_ENEIGH", -8: "POD_EIO"}
 
 
 class PodError(RuntimeError):
@@ -63,7 +64,7 @@ EXPORTS = ["pod_create", "pod_destroy", "pod_info", "pod_set_option", "pod_statu
            "pod_neighbors", "pod_descriptors", "pod_energy_forces", "pod_energy_forces_host", "pod_fit",
            "pod_fit_normal", "pod_fit_solve", "pod_fit_residual", "pod_descriptors_static",
            "pod_global_descriptors", "pod_descriptors_jvp", "pod_set_skin", "pod_md_step", "pod_fma_probe", "pod_autotune", "pod_set_quadratic",
-           "pod_set_embedding", "pod_last_error"]
+           "pod_set_embedding", "pod_save", "pod_load", "pod_last_error"]
 
 _lib = None
 _lock = threading.Lock()
@@ -105,6 +106,8 @@ def lib():
                 "pod_autotune": (C.c_int, [H, S, dp, C.c_int, ip, dp, vp]),
                 "pod_set_quadratic": (C.c_int, [H, dp]),
                 "pod_set_embedding": (C.c_int, [H, dp, C.c_int, dp]),
+                "pod_save": (C.c_int, [H, C.c_char_p, dp]),
+                "pod_load": (C.c_int, [C.c_char_p, C.c_int, C.POINTER(H), dp, C.c_int, ip]),
                 "pod_last_error": (C.c_char_p, [H]),
             }
             for name, (res, args) in sig.items():
@@ -294,6 +297,9 @@ class POD:
     def __init__(self, params, precision="fp64", Q=None, n_grid=None):
         self._p = _param_struct(params, precision, Q, n_grid)
         self.h = pod_create(self._p)
+        self._read_info(precision)
+
+    def _read_info(self, precision):
         M, Ns, K = C.c_int(), C.c_int(), C.c_int()
         _check(self.h, lib().pod_info(self.h, C.byref(M), C.byref(Ns), C.byref(K), None, None))
         self.M, self.Ns, self.K = M.value, Ns.value, K.value
@@ -303,6 +309,36 @@ class POD:
                                       eig.ctypes.data_as(C.POINTER(C.c_double))))
         self.Q, self.eig = Qo, eig
         self.precision = precision
+
+    def save(self, path, c=None):
+        """Model file: parameters, Q and (optionally) the coefficients c (M,)."""
+        cp = None
+        if c is not None:
+            cv = np.ascontiguousarray(np.asarray(c.cpu() if hasattr(c, "cpu") else c, dtype=np.float64))
+            if cv.shape != (self.M,):
+                raise ValueError(f"c must be ({self.M},)")
+            cp = cv.ctypes.data_as(C.POINTER(C.c_double))
+        _check(self.h, lib().pod_save(self.h, os.fsencode(path), cp))
+
+    @classmethod
+    def load(cls, path, precision="fp64"):
+        """Handle from a model file; returns (pod, c or None)."""
+        h = C.c_void_p()
+        c = np.zeros(4096)
+        n = C.c_int(0)
+        prec = POD_MIXED if precision in ("mixed", POD_MIXED) else POD_FP64
+        rc = lib().pod_load(os.fsencode(path), prec, C.byref(h), c.ctypes.data_as(C.POINTER(C.c_double)), c.size,
+                            C.byref(n))
+        if rc != POD_OK:
+            msg = pod_last_error(h.value) if h.value else f"cannot load {path}"
+            if h.value:
+                pod_destroy(h.value)
+            raise PodError(rc, msg)
+        obj = cls.__new__(cls)
+        obj._p = None
+        obj.h = h.value
+        obj._read_info(precision)
+        return obj, (c[: n.value].copy() if n.value else None)
 
     def close(self):
         if getattr(self, "h", None):

@@ -429,3 +429,19 @@ def test_host_entry_graph_replay(pkg, prec):
         assert np.array_equal(F_h.T, dev["F"].cpu().numpy()), call
         assert np.array_equal(Ei_h, dev["Ei"].cpu().numpy()), call
         assert np.array_equal(W_h, dev["W"].cpu().numpy().ravel()), call
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_model_file_evaluates_like_the_saved_handle(pkg, full, prec, tmp_path):
+    """A handle loaded from a model file (parameters, Q, c) gives the saved
+    handle's energies and forces bit for bit."""
+    p, o, cfg, c = full
+    pod = pkg.POD(p, precision=prec)
+    path = str(tmp_path / "ta.pod")
+    pod.save(path, c)
+    pod2, c2 = pkg.POD.load(path, prec)
+    x = soa(cfg)
+    a = pod.energy_forces(x, cfg.box, torch.tensor(c, device=DEV))
+    b = pod2.energy_forces(x, cfg.box, torch.tensor(c2, device=DEV))
+    for k in ("E", "Ei", "F", "W"):
+        assert torch.equal(a[k], b[k]), k

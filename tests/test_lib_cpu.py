@@ -87,3 +87,49 @@ def test_user_Q_override(pkg):
     Q = o.Q * 1.0
     pod = pkg.POD(p, Q=Q)
     assert np.array_equal(pod.Q, Q)
+
+
+def test_model_file_round_trip(pkg, tmp_path):
+    """pod_save / pod_load: parameters, Q and c come back bit for bit; a file
+    without coefficients loads with none; no temporary file is left behind."""
+    p = synth.params_full()
+    pod = pkg.POD(p, precision="mixed")
+    c = synth.coefficients(pod.M, 141)
+    path = tmp_path / "ta.pod"
+    pod.save(str(path), c)
+    assert sorted(x.name for x in tmp_path.iterdir()) == ["ta.pod"]
+    pod2, c2 = pkg.POD.load(str(path), "mixed")
+    assert (pod2.M, pod2.Ns, pod2.K) == (pod.M, pod.Ns, pod.K)
+    assert np.array_equal(pod2.Q, pod.Q) and np.array_equal(c2, c)
+    pod.save(str(path))  # overwrite, no coefficients
+    pod3, c3 = pkg.POD.load(str(path), "fp64")
+    assert c3 is None and np.array_equal(pod3.Q, pod.Q)
+    small = pkg.POD(synth.params_small())
+    small.save(str(tmp_path / "small.pod"), synth.coefficients(small.M, 142))
+    pod4, c4 = pkg.POD.load(str(tmp_path / "small.pod"))
+    assert pod4.M == small.M and np.array_equal(c4, synth.coefficients(small.M, 142))
+
+
+def test_model_file_errors(pkg, tmp_path):
+    with pytest.raises(pkg.PodError) as ei:
+        pkg.POD.load(str(tmp_path / "missing.pod"))
+    assert ei.value.code == pkg.POD_EIO
+    bad = tmp_path / "bad.pod"
+    bad.write_text("fastpod-model 1\nr_in 1\nr_cut oops\n")
+    with pytest.raises(pkg.PodError) as ei:
+        pkg.POD.load(str(bad))
+    assert ei.value.code == pkg.POD_EINVAL
+    pod = pkg.POD(synth.params_full())
+    good = tmp_path / "good.pod"
+    pod.save(str(good), synth.coefficients(pod.M, 143))
+    text = good.read_text().replace("c 103", "c 102", 1)  # coefficient count off by one
+    bad.write_text(text)
+    with pytest.raises(pkg.PodError) as ei:
+        pkg.POD.load(str(bad))
+    assert ei.value.code == pkg.POD_EINVAL
+    with pytest.raises(pkg.PodError) as ei:
+        pod.save(str(tmp_path / "nan.pod"), np.full(pod.M, np.nan))
+    assert ei.value.code == pkg.POD_EINVAL
+    with pytest.raises(pkg.PodError) as ei:
+        pod.save(str(tmp_path / "no_such_dir" / "x.pod"))
+    assert ei.value.code == pkg.POD_EIO
