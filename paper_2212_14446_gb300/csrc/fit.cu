@@ -478,12 +478,14 @@ extern "C" {
 
 int pod_fit(pod_handle* h, const pod_system* batch, const double* E_ref, const double* F_ref,
             const pod_fit_opts* opts, double* c_out, double* mae_E, double* mae_F) {
+  NvtxRange nvtx_("pod_fit");
   if (!h) return POD_EINVAL;
   return h->fit(batch, E_ref, F_ref, opts, c_out, mae_E, mae_F);
 }
 
 int pod_fit_normal(pod_handle* h, const pod_system* batch, const double* E_ref, const double* F_ref,
                    const pod_fit_opts* opts, double* G_out, double* r_out) {
+  NvtxRange nvtx_("pod_fit_normal");
   if (!h) return POD_EINVAL;
   if (!G_out || !r_out) return h->fail(POD_EINVAL, "G_out and r_out are required");
   pod_fit_opts o{100.0, 1.0, 1e-12, 1};
@@ -500,6 +502,7 @@ int pod_fit_normal(pod_handle* h, const pod_system* batch, const double* E_ref, 
 }
 
 int pod_fit_solve(pod_handle* h, const double* G, const double* r, double* c_out) {
+  NvtxRange nvtx_("pod_fit_solve");
   if (!h) return POD_EINVAL;
   if (!G || !r || !c_out) return h->fail(POD_EINVAL, "G, r and c_out are required");
   const int M = h->M;
@@ -517,6 +520,7 @@ int pod_fit_solve(pod_handle* h, const double* G, const double* r, double* c_out
 }
 
 int pod_fit_residual(pod_handle* h, const double* c, double* sum_abs_E, double* sum_abs_F, int* n_E, int* n_F) {
+  NvtxRange nvtx_("pod_fit_residual");
   if (!h) return POD_EINVAL;
   if (!c || !sum_abs_E || !sum_abs_F) return h->fail(POD_EINVAL, "c and the sums are required");
   if (h->fit_R == 0) return h->fail(POD_EINVAL, "pod_fit_residual needs a design matrix from pod_fit_normal");

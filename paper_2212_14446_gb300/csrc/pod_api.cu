@@ -364,6 +364,7 @@ std::vector<DevBuf*> pod_handle::all_bufs() {
 extern "C" {
 
 int pod_create(const pod_params* prm, pod_handle** out) {
+  NvtxRange nvtx_("pod_create");
   if (!out) return POD_EINVAL;
   *out = nullptr;
   if (!prm) return POD_EINVAL;
@@ -526,6 +527,7 @@ int pod_set_embedding(pod_handle* h, const double* a, int degree, const double* 
 
 int pod_autotune(pod_handle* h, const pod_system* sys, const double* c, int reps, int* shape, double* ms,
                  void* stream) {
+  NvtxRange nvtx_("pod_autotune");
   if (!h) return POD_EINVAL;
   LaunchShape best{};
   double t[3] = {0, 0, 0};
@@ -555,6 +557,7 @@ int pod_set_skin(pod_handle* h, double skin) {
 
 int pod_md_step(pod_handle* h, const pod_system* sys, double* pos, double* v, double* F, const double* c,
                 double mass, double dt, double* E, void* stream) {
+  NvtxRange nvtx_("pod_md_step");
   if (!h) return POD_EINVAL;
   return h->md_step(sys, pos, v, F, c, mass, dt, E, (cudaStream_t)stream);
 }
@@ -1137,17 +1140,20 @@ int pod_handle::global_desc(const pod_system* sys, const double* vdir, double* G
 extern "C" {
 
 int pod_global_descriptors(pod_handle* h, const pod_system* sys, double* G, void* stream) {
+  NvtxRange nvtx_("pod_global_descriptors");
   if (!h) return POD_EINVAL;
   return h->global_desc(sys, nullptr, G, (cudaStream_t)stream);
 }
 
 int pod_descriptors_jvp(pod_handle* h, const pod_system* sys, const double* v, double* Gdot, void* stream) {
+  NvtxRange nvtx_("pod_descriptors_jvp");
   if (!h) return POD_EINVAL;
   if (!v) return h->fail(POD_EINVAL, "direction v is NULL");
   return h->global_desc(sys, v, Gdot, (cudaStream_t)stream);
 }
 
 int pod_neighbors(pod_handle* h, const pod_system* sys, int cap, int* count, int* nbr, int* shift, void* stream) {
+  NvtxRange nvtx_("pod_neighbors");
   if (!h) return POD_EINVAL;
   int rc = h->neighbors(sys, cap, count, nbr, shift, (cudaStream_t)stream);
   if (rc == POD_OK && h->sync) {
@@ -1162,12 +1168,14 @@ int pod_neighbors(pod_handle* h, const pod_system* sys, int cap, int* count, int
 }
 
 int pod_descriptors(pod_handle* h, const pod_system* sys, double* D, void* stream) {
+  NvtxRange nvtx_("pod_descriptors");
   if (!h) return POD_EINVAL;
   return h->descriptors(sys, D, (cudaStream_t)stream);
 }
 
 int pod_energy_forces(pod_handle* h, const pod_system* sys, const double* c, double* E, double* Ei, double* F,
                       double* W, void* stream) {
+  NvtxRange nvtx_("pod_energy_forces");
   if (!h) return POD_EINVAL;
   return h->energy_forces(sys, c, E, Ei, F, W, (cudaStream_t)stream);
 }
@@ -1193,6 +1201,7 @@ bool host_pinned(const void* p) {
 // retries, or the error).
 int pod_energy_forces_host(pod_handle* h, const pod_system* sys, const double* c, double* E, double* Ei, double* F,
                            double* W, void* stream) {
+  NvtxRange nvtx_("pod_energy_forces_host");
   if (!h) return POD_EINVAL;
   int rc = h->validate_system(sys);
   if (rc) return rc;

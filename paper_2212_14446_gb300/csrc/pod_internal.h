@@ -1,6 +1,7 @@
 // Library-internal handle definition.
 #pragma once
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <cstdarg>
 #include <map>
@@ -10,6 +11,15 @@
 #include "../../include/pod.h"
 #include "pod_common.cuh"
 #include "pod_kernels.h"
+
+// NVTX range over one ABI call (visible in Nsight Systems timelines; a no-op
+// unless a tool is attached).
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 struct HostParams {
   double r_in = 0, r_cut = 0;

@@ -107,6 +107,7 @@ void static_args(const pod_handle* h, const Plan& pl, const unsigned char* base,
 }  // namespace
 
 extern "C" int pod_descriptors_static(pod_handle* h, const pod_system* sys, double* D, void* stream) {
+  NvtxRange nvtx_("pod_descriptors_static");
   if (!h) return POD_EINVAL;
   if (!sys || !sys->pos || !D) return h->fail(POD_EINVAL, "system, positions and D are required");
   if (sys->n_configs > 1) return h->fail(POD_EINVAL, "pod_descriptors_static takes a single configuration");
