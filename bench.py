@@ -461,7 +461,7 @@ def main():
            "d2h_bytes_per_step": int(Eh.nbytes + Eih.nbytes + Fh.nbytes + Wh.nbytes)}
 
     cpu = None
-    if rank == 0:
+    if rank == 0 and world == 1:  # the CPU baseline is measured at N = 1 only
         cpu = cpu_baseline_line(params, cfg, c.cpu().numpy(), args.cpu_budget)
 
     if rank == 0:
