@@ -477,7 +477,7 @@ def main():
                        "neighbor_rebuild": "every step", "l2": "flushed (512 MB write) before each step",
                        "graph": "one CUDA graph per step", "parallelism": f"replicas x{world}",
                        "launch_shape": shape,
-                       "model": "quadratic" if args.quadratic else ("embedding" if args.embedding else "linear")},
+                       "potential": "quadratic" if args.quadratic else ("embedding" if args.embedding else "linear")},
             "roofline": {"bound": "alu", "kernel": "atom_kernel (fused radial/B/contraction/adjoint)",
                          "achieved": achieved_tflops, "peak": peak_tflops, "unit": "TFLOP/s",
                          "frac": achieved_tflops / peak_tflops, "traffic": traffic,
