@@ -169,6 +169,10 @@ int pod_info(const pod_handle* h, int* M, int* Ns, int* K, double* Q_out, double
                                  extra two-body term); the quadratic and embedding models,
                                  the descriptor tangent, the fit entry points and
                                  pod_descriptors_static return POD_EINVAL while it is 1 */
+#define POD_OPT_GRAM 7 /* normal equations of the fit: 0 (default) G = A^T A from exact
+                          8-bit slice products on the BF16 tensor cores (integer sums,
+                          no rounding beyond 2^-59 of the column maxima); 1 an FP64
+                          SYRK on the FP64 pipes */
 int pod_set_option(pod_handle* h, int option, int value);
 
 /* Neighbour-list skin (A, default 0): lists are built with r_cut + skin and pairs

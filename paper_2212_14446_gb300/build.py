@@ -18,7 +18,7 @@ OBJ = os.path.join(HERE, "_build")
 LIBDIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIBDIR, "libfastpod.so")
 SOURCES = ["pod_api.cu", "neigh.cu", "atom_f32.cu", "atom_f64.cu", "atom_emb_f32.cu", "atom_emb_f64.cu", "gather.cu", "batch.cu", "fit.cu", "static_desc.cu", "peak.cu",
-           "model_io.cu"]
+           "model_io.cu", "gram_tc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-Xcompiler", "-Wno-deprecated-declarations"]

@@ -460,6 +460,11 @@ int pod_set_option(pod_handle* h, int option, int value) {
     h->timing = value ? 1 : 0;
     return POD_OK;
   }
+  if (option == POD_OPT_GRAM) {
+    if (value != 0 && value != 1) return h->fail(POD_EINVAL, "Gram mode must be 0 or 1");
+    h->gram_mode = value;
+    return POD_OK;
+  }
   if (option == POD_OPT_DESCRIPTORS) {
     if (value != 0 && value != 1) return h->fail(POD_EINVAL, "descriptor set must be 0 (fast POD) or 1");
     h->excl3 = value;

@@ -192,3 +192,29 @@ def test_shards_one_after_another_equal_the_whole_fit(pkg):
     c = pod.fit_solve(G, r)
     A, b = o.design_matrix(cfgs, E_ref, F_ref)
     assert np.max(np.abs(A @ c - A @ c_all)) <= 1e-8 * np.max(np.abs(b))
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_tensor_core_gram_equals_fp64_syrk(pkg, prec):
+    """The normal-equation matrix from exact 8-bit slice products on the tensor
+    cores (POD_OPT_GRAM = 0) equals the FP64 SYRK (POD_OPT_GRAM = 1) on the same
+    design matrix to the SYRK's own rounding, is exactly symmetric, and gives the
+    same fit."""
+    p = synth.params_full()
+    o = oracle.Oracle(p)
+    cfgs = training_configs(15, replica=7, max_atoms=30)
+    cstar = synth.coefficients(o.M, 41)
+    E_ref, F_ref = _labels(o, cfgs, cstar, noise=1.0, seed=12)
+    pod = pkg.POD(p, precision=prec, Q=o.Q)
+    pkg.pod_set_option(pod.h, pkg.POD_OPT_GRAM, 1)
+    G64, r64 = pod.fit_normal(cfgs, E_ref, F_ref)
+    c64, _, _ = pod.fit(cfgs, E_ref, F_ref)
+    pkg.pod_set_option(pod.h, pkg.POD_OPT_GRAM, 0)
+    Gtc, rtc = pod.fit_normal(cfgs, E_ref, F_ref)
+    ctc, _, _ = pod.fit(cfgs, E_ref, F_ref)
+    assert np.array_equal(Gtc, Gtc.T)
+    d = np.sqrt(np.outer(np.diag(G64), np.diag(G64)))  # Cauchy-Schwarz scale of each entry
+    assert np.max(np.abs(Gtc - G64) / d) <= 1e-13
+    assert np.max(np.abs(rtc - r64)) <= 1e-13 * np.max(np.abs(r64))
+    A, b = o.design_matrix(cfgs, E_ref, F_ref)
+    assert np.max(np.abs(A @ ctc - A @ c64)) <= 1e-8 * np.max(np.abs(b))
