@@ -634,8 +634,8 @@ def run_fit(args, rank, world, local):
     phases = {"neighbors": ph[0], "design_matrix": ph[1], "gram": ph[2], "solve": ph[3]} if calls else None
     n_atoms = int(offs[-1])
     rel = float(np.max(np.abs(c - cstar.numpy())) / np.max(np.abs(cstar.numpy())))
-    line = {"metric": "configs/s (fit: descriptors + gradients into the design matrix, FP64 normal equations, "
-                      "Cholesky)",
+    line = {"metric": "configs/s (fit: descriptors + gradients into the design matrix, exact normal equations, "
+                      "FP64 Cholesky)",
             "value": len(cfgs) / (ms / 1e3), "unit": "configs/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32" if args.precision == "mixed" else "f64", "data": "synthetic",
