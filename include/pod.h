@@ -46,7 +46,8 @@ extern "C" {
 #define POD_OK 0
 #define POD_EINVAL (-1)     /* bad parameter, NULL pointer, unsupported size      */
 #define POD_ENOMEM (-2)     /* device or host allocation failed                   */
-#define POD_ECUDA (-3)      /* a CUDA runtime call failed                         */
+#define POD_ECUDA (-3)      /* a CUDA runtime call failed, or a bounded wait inside
+                               a kernel ran out (the kernel stopped early)        */
 #define POD_ERANGE (-4)     /* a pair closer than r_in (outside (r_in, r_cut)); on
                                the mixed path also a value outside its fixed-point
                                range: a pair gradient of 2^30 eV/A or more, an atom
@@ -170,9 +171,11 @@ int pod_info(const pod_handle* h, int* M, int* Ns, int* K, double* Q_out, double
                                  the descriptor tangent, the fit entry points and
                                  pod_descriptors_static return POD_EINVAL while it is 1 */
 #define POD_OPT_GRAM 7 /* normal equations of the fit: 0 (default) G = A^T A from exact
-                          8-bit slice products on the BF16 tensor cores (integer sums,
-                          no rounding beyond 2^-59 of the column maxima); 1 an FP64
-                          SYRK on the FP64 pipes */
+                          8-bit slice products on the BF16 tensor cores (tcgen05 MMAs
+                          with TMEM accumulators; integer sums, no rounding beyond
+                          2^-59 of the column maxima); 1 an FP64 SYRK on the FP64
+                          pipes; 2 the same exact slice products through mma.sync
+                          (bit-identical to 0) */
 int pod_set_option(pod_handle* h, int option, int value);
 
 /* Neighbour-list skin (A, default 0): lists are built with r_cut + skin and pairs

@@ -387,8 +387,9 @@ int pod_handle::fit_build(const pod_system* bsys, const double* E_ref, const dou
 
 // Stage 2: G = A^T A + gamma I and r = A^T b on the device (fitwork).
 int pod_handle::fit_gram(double gamma) {
-  if (gram_mode == 0 && M <= 128)
-    return fit_gram_tc(gamma, (double*)fitwork.p + (size_t)M * M, (double*)fitwork.p + 2 * (size_t)M * M);
+  if (gram_mode != 1 && M <= 128)
+    return fit_gram_tc(gamma, (double*)fitwork.p + (size_t)M * M, (double*)fitwork.p + 2 * (size_t)M * M,
+                       gram_mode == 2);
   const int Mp = (M + 3) / 4 * 4;
   const long long R = fit_R;
   // two blocks on every SM (the kernel is FP64-pipe bound: an SM holding more

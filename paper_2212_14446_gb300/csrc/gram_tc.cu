@@ -192,6 +192,318 @@ __global__ void __launch_bounds__(2 * NJ * 32)
   }
 }
 
+// ---------------------------------------------------------------------------
+// The same slice products on the fifth-generation tensor cores (tcgen05).
+//
+// Slices are stored tiled for the MMA: VU[s][kb][mg][kg][mr][kr] holds row
+// r = 64 kb + 8 kg + kr of column m = 8 mg + mr, so one 64-row step of a slice
+// (a "tile", Mp x 64 BF16 = Mp x 128 bytes) is contiguous and is already the
+// K-major, unswizzled operand layout of tcgen05.mma: 8 x 8 core matrices of 128
+// bytes, 128 bytes apart along K and 1,024 bytes apart along M/N.  One block
+// per (slice pair, row split); warp roles:
+//   warp 8 lane 0   copies the A and B tiles of each step into a ring of
+//                   U_STAGES shared-memory stages (cp.async.bulk, completion on
+//                   an mbarrier with the byte count);
+//   warp 9 lane 0   issues four M128 x N(Mp) x K16 BF16 MMAs per step into one of
+//                   two TMEM accumulators (FP32), restarting the accumulator at
+//                   every 256-row chunk (every partial sum an integer below
+//                   2^24, exact), and commits the chunk to an mbarrier;
+//   warps 0..7      drain each finished chunk from TMEM (warp w reads TMEM lanes
+//                   32 (w % 4) .. + 31, columns half w / 4), convert the exact
+//                   FP32 integers to int32 and add them in registers; at the end
+//                   they add the block's sums to P[pair][m][n] with 64-bit
+//                   integer atomics (order-independent, so deterministic).
+// A block covers at most U_MAX_ROWS rows, so its int32 sums stay below
+// U_MAX_ROWS * 255^2 < 2^31.  Every wait is bounded (about two seconds of
+// global time); a wait that runs out sets ST_TIMEOUT, tells the other roles to
+// stop, and the block still waits for its own copies and MMAs before freeing
+// TMEM.
+constexpr int U_KB = 64;                    // rows per step (one stage)
+constexpr int U_STAGES = 6;                 // shared-memory ring
+constexpr int U_CHUNK_KB = TC_CHUNK / U_KB;  // steps per exact FP32 chunk
+constexpr int U_EPI_WARPS = 8;
+constexpr int U_THREADS = (U_EPI_WARPS + 2) * 32;
+constexpr long long U_MAX_ROWS = 32768;     // 32768 * 255^2 < 2^31
+constexpr unsigned U_TMEM_COLS = 256;       // two accumulators of up to 128 columns
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;\n" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ void mbar_init(unsigned bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(unsigned bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(unsigned bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Wait for the completion of phase `parity`; false if about two seconds pass or
+// (when stop is given) another role has set *stop.
+__device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity, const volatile int* stop) {
+  unsigned long long t0 = 0;
+  for (unsigned it = 0;; ++it) {
+    if (mbar_try(bar, parity)) return true;
+    if ((it & 63) == 0) {
+      if (stop && *stop) return false;
+      const unsigned long long t = global_ns();
+      if (it == 0)
+        t0 = t;
+      else if (t - t0 > 2000000000ull)
+        return false;
+    }
+  }
+}
+
+__device__ __forceinline__ void bulk_g2s(unsigned dst, const void* src, unsigned bytes, unsigned bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(dst),
+               "l"(src), "r"(bytes), "r"(bar)
+               : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory"); }
+
+// Shared-memory matrix descriptor of tcgen05.mma: start address, leading
+// (K-direction) and stride (M/N-direction) byte offsets, descriptor version 1,
+// no swizzle.
+__device__ __forceinline__ unsigned long long umma_desc(unsigned saddr, unsigned lbo, unsigned sbo) {
+  return (unsigned long long)((saddr & 0x3FFFFu) >> 4) | ((unsigned long long)((lbo >> 4) & 0x3FFFu) << 16) |
+         ((unsigned long long)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+// Instruction descriptor of kind::f16: FP32 accumulator, BF16 A and B, both
+// K-major, N >> 3 and M >> 4.
+constexpr unsigned umma_idesc(int Mm, int Nn) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((unsigned)(Nn >> 3) << 17) | ((unsigned)(Mm >> 4) << 24);
+}
+__device__ __forceinline__ void umma_bf16(unsigned dtmem, unsigned long long adesc, unsigned long long bdesc,
+                                          unsigned idesc, unsigned accumulate) {
+  asm volatile(
+      "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\ntcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+__device__ __forceinline__ void umma_commit(unsigned bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(bar) : "memory");
+}
+// 32 TMEM lanes x 8 columns of 32-bit words; the values are valid after tmem_wait8.
+__device__ __forceinline__ void tmem_ld8(unsigned taddr, unsigned* r) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];\n"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr)
+               : "memory");
+}
+// Waits for this thread's TMEM loads; the operands tie the loaded registers to
+// the wait so no use of them is scheduled before it.
+__device__ __forceinline__ void tmem_wait8(unsigned* r) {
+  asm volatile("tcgen05.wait::ld.sync.aligned;\n"
+               : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7])
+               :
+               : "memory");
+}
+
+// VU (tiled slices, layout above) from A: thread per (column m, row r).
+__global__ void gram_slice_tiled_kernel(int M, int Mp, long long R, long long RP, int slices,
+                                        const double* __restrict__ AT, const int* __restrict__ ex,
+                                        __nv_bfloat16* __restrict__ VU) {
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (long long)Mp * RP) return;
+  const int m = (int)(idx / RP);
+  const long long r = idx - (long long)m * RP;
+  unsigned long long X = 0;
+  bool neg = false;
+  if (m < M && r < R) {
+    const unsigned long long bits = __double_as_longlong(__ldg(AT + (size_t)m * R + r));
+    neg = (bits >> 63) != 0;
+    const int ef = (int)((bits >> 52) & 0x7ff);
+    if (ef != 0) {
+      const unsigned long long mant = (bits & 0xfffffffffffffull) | (1ull << 52);
+      const int sh = ef - 1075 + 64 - ex[m];
+      X = sh >= 0 ? (mant << sh) : (sh > -64 ? (mant >> -sh) : 0ull);
+    }
+  }
+  const long long nKB = RP / U_KB, kb = r / U_KB;
+  const int kg = (int)((r >> 3) & 7), kr = (int)(r & 7), mg = m >> 3, mr = m & 7;
+  const size_t within = ((size_t)(mg * 8 + kg) * 8 + mr) * 8 + kr;
+  for (int s = 0; s < slices; ++s) {
+    const int v = (int)((X >> (56 - 8 * s)) & 0xff);
+    VU[((size_t)s * nKB + kb) * (size_t)Mp * U_KB + within] = __float2bfloat16_rn((float)(neg ? -v : v));
+  }
+}
+
+template <int MP>
+__global__ void __launch_bounds__(U_THREADS, 1)
+    gram_umma_kernel(long long nKB, int splits, const int2* __restrict__ pairs, const __nv_bfloat16* __restrict__ VU,
+                     unsigned long long* __restrict__ P, int* __restrict__ status) {
+  static_assert(MP % 16 == 0 && MP <= 128, "N of the MMA");
+  constexpr unsigned TILE = MP * 128;  // one 64-row step of one slice
+  constexpr unsigned ATILE = 128 * 128;  // A operand: 128 MMA rows, zero beyond MP
+  constexpr unsigned STAGE = ATILE + TILE;
+  constexpr int HALF = MP / 2;  // accumulator columns per epilogue thread
+  constexpr unsigned IDESC = umma_idesc(128, MP);
+  extern __shared__ unsigned char usm_raw[];
+  unsigned char* usm = usm_raw + ((1024u - (smem_u32(usm_raw) & 1023u)) & 1023u);
+  unsigned long long* bars = reinterpret_cast<unsigned long long*>(usm + U_STAGES * STAGE);
+  // bars: full[U_STAGES], empty[U_STAGES], tfull[2], tempty[2], fin
+  unsigned* tslot = reinterpret_cast<unsigned*>(bars + 2 * U_STAGES + 5);
+  volatile int* stop = reinterpret_cast<volatile int*>(tslot + 1);
+  const unsigned sbase = smem_u32(usm), bbase = smem_u32(bars);
+  auto full = [&](int s) { return bbase + 8u * s; };
+  auto empty = [&](int s) { return bbase + 8u * (U_STAGES + s); };
+  auto tfull = [&](int b) { return bbase + 8u * (2 * U_STAGES + b); };
+  auto tempty = [&](int b) { return bbase + 8u * (2 * U_STAGES + 2 + b); };
+  const unsigned fin = bbase + 8u * (2 * U_STAGES + 4);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int2 st = pairs[blockIdx.x];
+  const long long kb0 = nKB * blockIdx.y / splits, kb1 = nKB * (blockIdx.y + 1) / splits;
+  const int nkb = (int)(kb1 - kb0);
+  const int nch = (nkb + U_CHUNK_KB - 1) / U_CHUNK_KB;
+
+  if constexpr (ATILE > TILE) {  // MMA rows MP..127 of every A stage read zeros
+    constexpr int W = (ATILE - TILE) / 16;
+    for (int i = threadIdx.x; i < U_STAGES * W; i += blockDim.x)
+      reinterpret_cast<uint4*>(usm + (i / W) * STAGE + TILE)[i % W] = make_uint4(0u, 0u, 0u, 0u);
+  }
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < U_STAGES; ++s) {
+      mbar_init(full(s), 1);
+      mbar_init(empty(s), 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(tfull(b), 1);
+      mbar_init(tempty(b), U_EPI_WARPS);
+    }
+    mbar_init(fin, 1);
+    *stop = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");  // the zero rows, for the tensor cores
+  if (warp == U_EPI_WARPS + 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(tslot)),
+                 "r"(U_TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const unsigned tbase = *tslot;
+
+  if (warp == U_EPI_WARPS) {
+    if (lane == 0) {  // ---- copies
+      const unsigned char* srcA = reinterpret_cast<const unsigned char*>(VU) + ((size_t)st.x * nKB + kb0) * TILE;
+      const unsigned char* srcB = reinterpret_cast<const unsigned char*>(VU) + ((size_t)st.y * nKB + kb0) * TILE;
+      int issued = 0;
+      for (int i = 0; i < nkb; ++i) {
+        const int s = i % U_STAGES;
+        if (i >= U_STAGES && !mbar_wait(empty(s), (unsigned)((i / U_STAGES - 1) & 1), stop)) {
+          if (!*stop) atomicOr(status, ST_TIMEOUT);
+          *stop = 1;
+          break;
+        }
+        mbar_expect_tx(full(s), 2 * TILE);
+        bulk_g2s(sbase + s * STAGE, srcA + (size_t)i * TILE, TILE, full(s));
+        bulk_g2s(sbase + s * STAGE + ATILE, srcB + (size_t)i * TILE, TILE, full(s));
+        issued = i + 1;
+      }
+      // the last copies of every stage have landed before the block ends
+      for (int i = max(0, issued - U_STAGES); i < issued; ++i)
+        if (!mbar_wait(full(i % U_STAGES), (unsigned)((i / U_STAGES) & 1), nullptr)) atomicOr(status, ST_TIMEOUT);
+    }
+  } else if (warp == U_EPI_WARPS + 1) {
+    if (lane == 0) {  // ---- MMAs
+      int i = 0;
+      bool ok = true;
+      for (int c = 0; c < nch && ok; ++c) {
+        const int b = c & 1;
+        if (c >= 2 && !mbar_wait(tempty(b), (unsigned)(((c >> 1) - 1) & 1), stop)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const unsigned d = tbase + (unsigned)b * 128u;
+        const int kend = min(nkb, (c + 1) * U_CHUNK_KB);
+        for (; i < kend; ++i) {
+          const int s = i % U_STAGES;
+          if (!mbar_wait(full(s), (unsigned)((i / U_STAGES) & 1), stop)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const unsigned a0 = sbase + s * STAGE, b0 = a0 + ATILE;
+#pragma unroll
+          for (int kk = 0; kk < U_KB / 16; ++kk)
+            umma_bf16(d, umma_desc(a0 + kk * 256u, 128u, 1024u), umma_desc(b0 + kk * 256u, 128u, 1024u), IDESC,
+                      (i > c * U_CHUNK_KB || kk > 0) ? 1u : 0u);
+          umma_commit(empty(s));  // the stage is free once these MMAs have read it
+        }
+        if (ok) umma_commit(tfull(b));
+      }
+      if (!ok) {
+        if (!*stop) atomicOr(status, ST_TIMEOUT);
+        *stop = 1;
+      }
+      umma_commit(fin);  // every MMA of this thread has completed before TMEM is freed
+      if (!mbar_wait(fin, 0u, nullptr)) atomicOr(status, ST_TIMEOUT);
+    }
+  } else {  // ---- drain: warps 0..7
+    const int quad = warp & 3, half = warp >> 2;
+    int acc[HALF];
+#pragma unroll
+    for (int j = 0; j < HALF; ++j) acc[j] = 0;
+    for (int c = 0; c < nch; ++c) {
+      const int b = c & 1;
+      const bool ok = __all_sync(0xffffffffu, mbar_wait(tfull(b), (unsigned)((c >> 1) & 1), stop));
+      if (!ok) {  // warp-uniform, so the aligned TMEM loads below stay convergent
+        if (lane == 0 && !*stop) atomicOr(status, ST_TIMEOUT);
+        *stop = 1;
+        break;
+      }
+      tc_fence_after();
+      const unsigned taddr = tbase + ((unsigned)(quad * 32) << 16) + (unsigned)b * 128u + (unsigned)(half * HALF);
+      unsigned r[HALF];
+#pragma unroll
+      for (int g = 0; g < HALF / 8; ++g) tmem_ld8(taddr + 8u * g, r + 8 * g);
+#pragma unroll
+      for (int g = 0; g < HALF / 8; ++g) tmem_wait8(r + 8 * g);
+#pragma unroll
+      for (int j = 0; j < HALF; ++j) acc[j] += __float2int_rn(__uint_as_float(r[j]));
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(tempty(b));
+    }
+    const int m = quad * 32 + lane;
+    if (m < MP && !*stop) {
+      unsigned long long* out = P + ((size_t)blockIdx.x * MP + m) * MP + half * HALF;
+#pragma unroll
+      for (int j = 0; j < HALF; ++j)
+        if (acc[j]) atomicAdd(out + j, (unsigned long long)(long long)acc[j]);
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == U_EPI_WARPS + 1) {
+    __syncwarp();
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tbase), "r"(U_TMEM_COLS) : "memory");
+  }
+}
+
 // G_mn = sum over slice pairs (largest s + t, i.e. smallest terms, first) of
 // 2^(e_m + e_n - 8 (s + t + 2)) (P_st[m][n] (+ P_st[n][m] for s != t)), the
 // integer split sums exact; gamma on the diagonal.
@@ -247,8 +559,9 @@ __global__ void atb_final_kernel(int M, int nblk, const double* __restrict__ par
 
 using namespace fastpod;
 
-// Stage 2 on the tensor cores: G = A^T A + gamma I and r = A^T b into dG, dr.
-int pod_handle::fit_gram_tc(double gamma, double* dG, double* dr) {
+// Stage 2 on the tensor cores: G = A^T A + gamma I and r = A^T b into dG, dr
+// (tcgen05 kernel, or the mma.sync kernel when legacy_mma).
+int pod_handle::fit_gram_tc(double gamma, double* dG, double* dr, bool legacy_mma) {
   const int Mp = M <= 112 ? 112 : 128;
   if (M > 128) return fail(POD_EINVAL, "the tensor-core Gram handles at most 128 descriptors");
   const long long R = fit_R;
@@ -261,10 +574,19 @@ int pod_handle::fit_gram_tc(double gamma, double* dG, double* dr) {
       hp[2 * np + 1] = sum - s;
       ++np;
     }
-  // one block per SM (the kernel holds 128 registers a thread): splits fill one wave
-  const int splits = (int)std::max<long long>(1, std::min<long long>(TC_SPLITS_MAX, 152 / np));
+  // mma.sync: one block per SM (128 registers a thread), splits fill one wave.
+  // tcgen05: about four waves of one block per SM, at most U_MAX_ROWS rows a block.
+  const long long nKB = RP / U_KB;
+  int splits;
+  if (legacy_mma) {
+    splits = (int)std::max<long long>(1, std::min<long long>(TC_SPLITS_MAX, 152 / np));
+  } else {
+    const long long need = (nKB * U_KB + U_MAX_ROWS - 1) / U_MAX_ROWS;
+    splits = (int)std::max<long long>(need, std::min<long long>(nKB, (4 * 152 + np - 1) / np));
+  }
+  const int psplits = legacy_mma ? splits : 1;  // tcgen05 blocks add into one integer sum per pair
   const size_t vt_bytes = sizeof(__nv_bfloat16) * SLICES * (size_t)Mp * RP;
-  const size_t part_bytes = sizeof(long long) * (size_t)np * splits * Mp * Mp;
+  const size_t part_bytes = sizeof(long long) * (size_t)np * psplits * Mp * Mp;
   int rc_;
   const size_t scan_bytes = sizeof(double) * (size_t)M * TC_COLBLK;
   if ((rc_ = ensure(fitG, vt_bytes + part_bytes + sizeof(int) * (2 * 64 + 128) + 2 * scan_bytes + 1024, "Gram slices")))
@@ -282,22 +604,42 @@ int pod_handle::fit_gram_tc(double gamma, double* dG, double* dr) {
   gram_colmax_kernel<<<dim3((unsigned)M, TC_COLBLK), 256, 0, nullptr>>>(R, AT, pmax);
   gram_colexp_kernel<<<(M + 127) / 128, 128, 0, nullptr>>>(M, TC_COLBLK, pmax, dex);
   const long long nel = (long long)Mp * RP;
-  gram_slice_kernel<<<(unsigned)((nel + 255) / 256), 256, 0, nullptr>>>(M, Mp, R, RP, SLICES, AT, dex, VT);
+  if (legacy_mma)
+    gram_slice_kernel<<<(unsigned)((nel + 255) / 256), 256, 0, nullptr>>>(M, Mp, R, RP, SLICES, AT, dex, VT);
+  else
+    gram_slice_tiled_kernel<<<(unsigned)((nel + 255) / 256), 256, 0, nullptr>>>(M, Mp, R, RP, SLICES, AT, dex, VT);
   if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "Gram slicing");
   const dim3 grid((unsigned)np, (unsigned)splits);
-  const size_t smem = (size_t)TC_STAGES * 2 * Mp * 64;
-  static size_t granted7[64] = {}, granted8[64] = {};
-  if (Mp == 112) {
-    if ((e = grant_smem((const void*)gram_tc_kernel<7>, smem, granted7)) != cudaSuccess)
-      return cuda_fail(e, "Gram shared memory");
-    gram_tc_kernel<7><<<grid, 2 * 7 * 32, smem, nullptr>>>(Mp, RP, splits, dpairs, VT, part);
+  if (legacy_mma) {
+    const size_t smem = (size_t)TC_STAGES * 2 * Mp * 64;
+    static size_t granted7[64] = {}, granted8[64] = {};
+    if (Mp == 112) {
+      if ((e = grant_smem((const void*)gram_tc_kernel<7>, smem, granted7)) != cudaSuccess)
+        return cuda_fail(e, "Gram shared memory");
+      gram_tc_kernel<7><<<grid, 2 * 7 * 32, smem, nullptr>>>(Mp, RP, splits, dpairs, VT, part);
+    } else {
+      if ((e = grant_smem((const void*)gram_tc_kernel<8>, smem, granted8)) != cudaSuccess)
+        return cuda_fail(e, "Gram shared memory");
+      gram_tc_kernel<8><<<grid, 2 * 8 * 32, smem, nullptr>>>(Mp, RP, splits, dpairs, VT, part);
+    }
   } else {
-    if ((e = grant_smem((const void*)gram_tc_kernel<8>, smem, granted8)) != cudaSuccess)
-      return cuda_fail(e, "Gram shared memory");
-    gram_tc_kernel<8><<<grid, 2 * 8 * 32, smem, nullptr>>>(Mp, RP, splits, dpairs, VT, part);
+    if ((e = cudaMemsetAsync(part, 0, part_bytes, nullptr)) != cudaSuccess) return cuda_fail(e, "Gram sums clear");
+    // stages, 1,024 bytes of alignment slack, barriers, TMEM address and stop flag
+    const size_t smem = (size_t)U_STAGES * (128 * 128 + Mp * 128) + 1024 + 8 * (2 * U_STAGES + 5) + 16;
+    static size_t grantedu7[64] = {}, grantedu8[64] = {};
+    unsigned long long* P = (unsigned long long*)part;
+    if (Mp == 112) {
+      if ((e = grant_smem((const void*)gram_umma_kernel<112>, smem, grantedu7)) != cudaSuccess)
+        return cuda_fail(e, "Gram shared memory");
+      gram_umma_kernel<112><<<grid, U_THREADS, smem, nullptr>>>(nKB, splits, dpairs, VT, P, (int*)status.p);
+    } else {
+      if ((e = grant_smem((const void*)gram_umma_kernel<128>, smem, grantedu8)) != cudaSuccess)
+        return cuda_fail(e, "Gram shared memory");
+      gram_umma_kernel<128><<<grid, U_THREADS, smem, nullptr>>>(nKB, splits, dpairs, VT, P, (int*)status.p);
+    }
   }
   if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "Gram tensor-core kernel");
-  gram_tc_combine_kernel<<<(M * M + 255) / 256, 256, 0, nullptr>>>(M, Mp, np, splits, dpairs, part, dex, gamma, dG);
+  gram_tc_combine_kernel<<<(M * M + 255) / 256, 256, 0, nullptr>>>(M, Mp, np, psplits, dpairs, part, dex, gamma, dG);
   atb_partial_kernel<<<dim3((unsigned)M, TC_COLBLK), 256, 0, nullptr>>>(R, AT, (const double*)fitb.p, apart);
   atb_final_kernel<<<(M + 127) / 128, 128, 0, nullptr>>>(M, TC_COLBLK, apart, dr);
   if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "Gram assembly");

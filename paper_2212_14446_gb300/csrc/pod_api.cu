@@ -461,7 +461,7 @@ int pod_set_option(pod_handle* h, int option, int value) {
     return POD_OK;
   }
   if (option == POD_OPT_GRAM) {
-    if (value != 0 && value != 1) return h->fail(POD_EINVAL, "Gram mode must be 0 or 1");
+    if (value < 0 || value > 2) return h->fail(POD_EINVAL, "Gram mode must be 0, 1 or 2");
     h->gram_mode = value;
     return POD_OK;
   }
@@ -607,6 +607,7 @@ int pod_handle::read_status(cudaStream_t st) {
   if (s & ST_RANGE) return fail(POD_ERANGE, "a pair is closer than r_in");
   if (s & ST_OVERFLOW)
     return fail(POD_ERANGE, "a force, atom energy or virial exceeds the fixed-point range of the mixed path");
+  if (s & ST_TIMEOUT) return fail(POD_ECUDA, "a bounded wait inside a kernel ran out (status 0x%x)", s);
   return POD_OK;
 }
 

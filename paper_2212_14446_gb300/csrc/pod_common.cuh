@@ -74,6 +74,7 @@ constexpr int ST_RANGE = 4;      // pair with r <= r_in
 constexpr int ST_NONFINITE = 8;  // NaN / Inf in positions
 constexpr int ST_REV = 16;       // reverse pair not found (broken list symmetry)
 constexpr int ST_OVERFLOW = 32;  // a force, energy or virial beyond the mixed path's fixed-point range
+constexpr int ST_TIMEOUT = 64;   // a bounded wait inside a kernel ran out (the kernel stopped early)
 
 // ------------------------------------------------ small vector of 4 T
 template <typename T>

@@ -129,8 +129,8 @@ struct pod_handle {
   int colsum_table(const Plan& pl, int& nch, int& nrows2);
   int fit_build(const pod_system* batch, const double* E_ref, const double* F_ref, const pod_fit_opts& o);
   int fit_gram(double gamma);
-  int fit_gram_tc(double gamma, double* dG, double* dr);
-  int gram_mode = 0;  // 0: exact slice products on the tensor cores; 1: FP64 SYRK
+  int fit_gram_tc(double gamma, double* dG, double* dr, bool legacy_mma);
+  int gram_mode = 0;  // exact slice products: 0 tcgen05, 2 mma.sync; 1: FP64 SYRK
   int fit_solve_dev();
   int fit_residual_dev(double* sumE, double* sumF);
   long long fit_R = 0;

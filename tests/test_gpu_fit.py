@@ -194,27 +194,36 @@ def test_shards_one_after_another_equal_the_whole_fit(pkg):
     assert np.max(np.abs(A @ c - A @ c_all)) <= 1e-8 * np.max(np.abs(b))
 
 
-@pytest.mark.parametrize("prec", ["fp64", "mixed"])
-def test_tensor_core_gram_equals_fp64_syrk(pkg, prec):
+@pytest.mark.parametrize("prec,ncfg,max_atoms", [("fp64", 15, 30), ("mixed", 15, 30), ("mixed", 150, 80)])
+def test_tensor_core_gram_equals_fp64_syrk(pkg, prec, ncfg, max_atoms):
     """The normal-equation matrix from exact 8-bit slice products on the tensor
-    cores (POD_OPT_GRAM = 0) equals the FP64 SYRK (POD_OPT_GRAM = 1) on the same
-    design matrix to the SYRK's own rounding, is exactly symmetric, and gives the
-    same fit."""
+    cores -- tcgen05 (POD_OPT_GRAM = 0) and mma.sync (POD_OPT_GRAM = 2) -- equals
+    the FP64 SYRK (POD_OPT_GRAM = 1) on the same design matrix to the SYRK's own
+    rounding, is exactly symmetric, and gives the same fit; the two exact forms
+    agree bit for bit (the same integer sums).  The larger case spans many
+    256-row chunks and several row splits per slice pair."""
     p = synth.params_full()
     o = oracle.Oracle(p)
-    cfgs = training_configs(15, replica=7, max_atoms=30)
+    cfgs = training_configs(ncfg, replica=7, max_atoms=max_atoms)
     cstar = synth.coefficients(o.M, 41)
     E_ref, F_ref = _labels(o, cfgs, cstar, noise=1.0, seed=12)
     pod = pkg.POD(p, precision=prec, Q=o.Q)
     pkg.pod_set_option(pod.h, pkg.POD_OPT_GRAM, 1)
     G64, r64 = pod.fit_normal(cfgs, E_ref, F_ref)
     c64, _, _ = pod.fit(cfgs, E_ref, F_ref)
+    pkg.pod_set_option(pod.h, pkg.POD_OPT_GRAM, 2)
+    Gmma, rmma = pod.fit_normal(cfgs, E_ref, F_ref)
     pkg.pod_set_option(pod.h, pkg.POD_OPT_GRAM, 0)
     Gtc, rtc = pod.fit_normal(cfgs, E_ref, F_ref)
     ctc, _, _ = pod.fit(cfgs, E_ref, F_ref)
+    assert np.array_equal(Gtc, Gmma)
     assert np.array_equal(Gtc, Gtc.T)
     d = np.sqrt(np.outer(np.diag(G64), np.diag(G64)))  # Cauchy-Schwarz scale of each entry
     assert np.max(np.abs(Gtc - G64) / d) <= 1e-13
     assert np.max(np.abs(rtc - r64)) <= 1e-13 * np.max(np.abs(r64))
-    A, b = o.design_matrix(cfgs, E_ref, F_ref)
-    assert np.max(np.abs(A @ ctc - A @ c64)) <= 1e-8 * np.max(np.abs(b))
+    if ncfg <= 15:  # the oracle's design matrix (slow at the larger size)
+        A, b = o.design_matrix(cfgs, E_ref, F_ref)
+        assert np.max(np.abs(A @ ctc - A @ c64)) <= 1e-8 * np.max(np.abs(b))
+    else:
+        d = ctc - c64  # ||A d|| through the normal equations, against ||A c64||
+        assert np.sqrt(abs(d @ G64 @ d)) <= 1e-8 * np.sqrt(c64 @ G64 @ c64)
