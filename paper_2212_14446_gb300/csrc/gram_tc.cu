@@ -316,32 +316,57 @@ __device__ __forceinline__ void tmem_wait8(unsigned* r) {
                : "memory");
 }
 
-// VU (tiled slices, layout above) from A: thread per (column m, row r).
+// X = floor(|a| 2^(64 - e)) from the double's bits (integer shifts; values below
+// the smallest normal double count as zero); the sign is returned separately.
+__device__ __forceinline__ unsigned long long slice_bits(double a, int e, bool& neg) {
+  const unsigned long long bits = __double_as_longlong(a);
+  neg = (bits >> 63) != 0;
+  const int ef = (int)((bits >> 52) & 0x7ff);
+  if (ef == 0) return 0ull;
+  const unsigned long long mant = (bits & 0xfffffffffffffull) | (1ull << 52);  // |a| = mant 2^(ef - 1075)
+  const int sh = ef - 1075 + 64 - e;                                           // <= 11 as |a| < 2^e
+  return sh >= 0 ? (mant << sh) : (sh > -64 ? (mant >> -sh) : 0ull);
+}
+
+// VU (tiled slices, layout above) from A: thread per (column m, 8-row group), so
+// each thread stores one 16-byte core-matrix row per slice and 64 consecutive
+// threads store one contiguous 1,024-byte group.
 __global__ void gram_slice_tiled_kernel(int M, int Mp, long long R, long long RP, int slices,
                                         const double* __restrict__ AT, const int* __restrict__ ex,
                                         __nv_bfloat16* __restrict__ VU) {
-  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= (long long)Mp * RP) return;
-  const int m = (int)(idx / RP);
-  const long long r = idx - (long long)m * RP;
-  unsigned long long X = 0;
-  bool neg = false;
-  if (m < M && r < R) {
-    const unsigned long long bits = __double_as_longlong(__ldg(AT + (size_t)m * R + r));
-    neg = (bits >> 63) != 0;
-    const int ef = (int)((bits >> 52) & 0x7ff);
-    if (ef != 0) {
-      const unsigned long long mant = (bits & 0xfffffffffffffull) | (1ull << 52);
-      const int sh = ef - 1075 + 64 - ex[m];
-      X = sh >= 0 ? (mant << sh) : (sh > -64 ? (mant >> -sh) : 0ull);
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int MG = Mp >> 3;
+  const long long nKB = RP / U_KB;
+  if (t >= nKB * MG * 64) return;
+  const int mr = (int)(t & 7), kg = (int)((t >> 3) & 7);
+  const long long rest = t >> 6;
+  const int mg = (int)(rest % MG);
+  const long long kb = rest / MG;
+  const int m = mg * 8 + mr;
+  const long long r0 = kb * U_KB + kg * 8;
+  unsigned long long X[8];
+  unsigned negmask = 0;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    X[k] = 0ull;
+    if (m < M && r0 + k < R) {
+      bool neg;
+      X[k] = slice_bits(__ldg(AT + (size_t)m * R + r0 + k), ex[m], neg);
+      negmask |= (neg ? 1u : 0u) << k;
     }
   }
-  const long long nKB = RP / U_KB, kb = r / U_KB;
-  const int kg = (int)((r >> 3) & 7), kr = (int)(r & 7), mg = m >> 3, mr = m & 7;
-  const size_t within = ((size_t)(mg * 8 + kg) * 8 + mr) * 8 + kr;
+  uint4* dst = reinterpret_cast<uint4*>(VU + (size_t)kb * Mp * U_KB) + (size_t)(mg * 8 + kg) * 8 + mr;
+  const size_t slice_words = (size_t)nKB * Mp * U_KB / 8;  // 16-byte words per slice
   for (int s = 0; s < slices; ++s) {
-    const int v = (int)((X >> (56 - 8 * s)) & 0xff);
-    VU[((size_t)s * nKB + kb) * (size_t)Mp * U_KB + within] = __float2bfloat16_rn((float)(neg ? -v : v));
+    unsigned w[4];
+#pragma unroll
+    for (int k = 0; k < 8; k += 2) {
+      const int v0 = (int)((X[k] >> (56 - 8 * s)) & 0xff), v1 = (int)((X[k + 1] >> (56 - 8 * s)) & 0xff);
+      const __nv_bfloat162 h = __floats2bfloat162_rn((float)((negmask >> k) & 1 ? -v0 : v0),
+                                                     (float)((negmask >> (k + 1)) & 1 ? -v1 : v1));  // exact
+      w[k / 2] = *reinterpret_cast<const unsigned*>(&h);
+    }
+    dst[s * slice_words] = make_uint4(w[0], w[1], w[2], w[3]);
   }
 }
 
@@ -582,7 +607,7 @@ int pod_handle::fit_gram_tc(double gamma, double* dG, double* dr, bool legacy_mm
     splits = (int)std::max<long long>(1, std::min<long long>(TC_SPLITS_MAX, 152 / np));
   } else {
     const long long need = (nKB * U_KB + U_MAX_ROWS - 1) / U_MAX_ROWS;
-    splits = (int)std::max<long long>(need, std::min<long long>(nKB, (4 * 152 + np - 1) / np));
+    splits = (int)std::max<long long>(need, std::min<long long>(nKB, std::max(1, 4 * 152 / np)));
   }
   const int psplits = legacy_mma ? splits : 1;  // tcgen05 blocks add into one integer sum per pair
   const size_t vt_bytes = sizeof(__nv_bfloat16) * SLICES * (size_t)Mp * RP;
@@ -607,7 +632,8 @@ int pod_handle::fit_gram_tc(double gamma, double* dG, double* dr, bool legacy_mm
   if (legacy_mma)
     gram_slice_kernel<<<(unsigned)((nel + 255) / 256), 256, 0, nullptr>>>(M, Mp, R, RP, SLICES, AT, dex, VT);
   else
-    gram_slice_tiled_kernel<<<(unsigned)((nel + 255) / 256), 256, 0, nullptr>>>(M, Mp, R, RP, SLICES, AT, dex, VT);
+    gram_slice_tiled_kernel<<<(unsigned)((nel / 8 + 255) / 256), 256, 0, nullptr>>>(M, Mp, R, RP, SLICES, AT, dex,
+                                                                                       VT);
   if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "Gram slicing");
   const dim3 grid((unsigned)np, (unsigned)splits);
   if (legacy_mma) {
