@@ -237,13 +237,35 @@ __global__ void __launch_bounds__(256)
     const int ql = v / (K * 3), rem = v - ql * (K * 3);
     const T* base = gdm + ql * plane + rem;
     T s = T(0);
-    for (int t = 0; t < n; ++t) {
+    bool broken = false;
+    int t = 0;
+    // four slots per step: their eight loads are issued before the (in-order) sums
+    for (; t + 4 <= n; t += 4) {
+      const size_t p0 = (size_t)k * cap + t;
+      int q[4];
+      T own[4], oth[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) q[j] = rev[p0 + j];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        own[j] = base[(p0 + j) * K * 3];
+        oth[j] = q[j] >= 0 ? base[(size_t)q[j] * K * 3] : T(0);
+        broken |= q[j] < 0;
+      }
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        s += own[j];
+        s -= oth[j];
+      }
+    }
+    for (; t < n; ++t) {
       const size_t pidx = (size_t)k * cap + t;
       const int q = rev[pidx];
       s += base[pidx * K * 3];
       if (q >= 0) s -= base[(size_t)q * K * 3];
-      else atomicOr(status, ST_REV);
+      else broken = true;
     }
+    if (broken) atomicOr(status, ST_REV);
     const int m = rem / 3, comp = rem - 3 * m;
     const int col = design_column(q0 + ql, m, K2, K3, P3, K4, KA4, col3, col4);
     if (col >= 0) AT[(size_t)col * R + nc + (size_t)comp * N + k] = wF * (double)s;
