@@ -373,7 +373,7 @@ __global__ void __launch_bounds__(ATOM_MAX_WPB * 32, atom_min_blocks<T, MODE, KT
           const int jj = f - base, slot = ch * CH + jj, i = atom0 + a;
           const Q4<T> u = geo[a * lay.GA + jj];
           T Rv[KT], Rpv[KT];
-          if (p.rad.tab) {
+          if (p.rad.tab && !p.keep_rp) {
             if (u.w > p.rad.r_in && u.w < p.rmask) {
               radial_pair<T, KT>(p.rad, u.w, Rv, Rpv);
             } else {

@@ -221,6 +221,7 @@ __device__ __forceinline__ int design_column(int q, int m, int K2, int K3, int P
 // Force rows of the design matrix, warp per atom k: lane v of the Qc x K x 3
 // (descriptor index, mode, component) values adds g[k,t] - g[rev(k,t)] over the
 // atom's slots t in order, then writes w_F times the sum to AT[col][nc + c N + k].
+constexpr int DG_UNROLL = 8;
 template <typename T>
 __global__ void __launch_bounds__(256)
     design_gather_kernel(int N, int cap, int K, int q0, int Qc, const int* __restrict__ nbr_count,
@@ -239,21 +240,21 @@ __global__ void __launch_bounds__(256)
     T s = T(0);
     bool broken = false;
     int t = 0;
-    // four slots per step: their eight loads are issued before the (in-order) sums
-    for (; t + 4 <= n; t += 4) {
+    // DG_UNROLL slots per step: their loads are issued before the (in-order) sums
+    for (; t + DG_UNROLL <= n; t += DG_UNROLL) {
       const size_t p0 = (size_t)k * cap + t;
-      int q[4];
-      T own[4], oth[4];
+      int q[DG_UNROLL];
+      T own[DG_UNROLL], oth[DG_UNROLL];
 #pragma unroll
-      for (int j = 0; j < 4; ++j) q[j] = rev[p0 + j];
+      for (int j = 0; j < DG_UNROLL; ++j) q[j] = rev[p0 + j];
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
+      for (int j = 0; j < DG_UNROLL; ++j) {
         own[j] = base[(p0 + j) * K * 3];
         oth[j] = q[j] >= 0 ? base[(size_t)q[j] * K * 3] : T(0);
         broken |= q[j] < 0;
       }
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
+      for (int j = 0; j < DG_UNROLL; ++j) {
         s += own[j];
         s -= oth[j];
       }

@@ -880,6 +880,7 @@ int pod_handle::run_atoms(int mode, const Plan& pl, double* D, const double* c, 
     a.gdm = (float*)gdm.p;
     a.q0 = dm_q0;
     a.q1 = dm_q1;
+    if (mode == 3) a.keep_rp = 1;  // the design pass reads R, R' of every pair once per descriptor index
     e = mode == 5 ? launch_atom_emb_f32(a, PA, has4, st) : launch_atom_f32(mode, a, PA, has4, st);
   } else {
     AtomArgs<double> a;
