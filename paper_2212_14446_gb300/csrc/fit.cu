@@ -126,8 +126,73 @@ __global__ void gram_reduce_kernel(int M, int Mp, int nblk, const double* __rest
 }
 
 // In-place Cholesky G = L L^T (lower triangle) and the two triangular solves,
-// one block, fixed order.  info = 0 on success, k + 1 if pivot k is not positive.
-__global__ void cholesky_solve_kernel(int M, double* __restrict__ G, double* __restrict__ r, double* __restrict__ c,
+// one block, fixed order, on a copy of G and r in shared memory (M M + M doubles;
+// the factor is written back to G).  Every entry sees the same operations in the
+// same order whatever the thread mapping.  info = 0 on success, k + 1 if pivot k
+// is not positive.
+__global__ void __launch_bounds__(512)
+    cholesky_solve_kernel(int M, double* __restrict__ G, double* __restrict__ r, double* __restrict__ c,
+                          int* __restrict__ info) {
+  extern __shared__ double chs[];
+  double* sG = chs;
+  double* sr = chs + (size_t)M * M;
+  __shared__ double piv;
+  __shared__ int bad;
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  const int lane = tid & 31, warp = tid >> 5, nwarp = nthr >> 5;
+  for (int e = tid; e < M * M; e += nthr) sG[e] = G[e];
+  for (int e = tid; e < M; e += nthr) sr[e] = r[e];
+  if (tid == 0) bad = 0;
+  __syncthreads();
+  for (int k = 0; k < M; ++k) {
+    if (tid == 0) {
+      const double d = sG[k * M + k];
+      if (!(d > 0.0) || !isfinite(d)) {
+        bad = k + 1;
+        piv = 1.0;
+      } else {
+        piv = sqrt(d);
+      }
+      sG[k * M + k] = piv;
+    }
+    __syncthreads();
+    if (bad) break;
+    for (int i = k + 1 + tid; i < M; i += nthr) sG[i * M + k] /= piv;
+    __syncthreads();
+    // trailing lower triangle: warp per row i, lanes over j in (k, i]
+    for (int i = k + 1 + warp; i < M; i += nwarp) {
+      const double lik = sG[i * M + k];
+      for (int j = k + 1 + lane; j <= i; j += 32) sG[i * M + j] -= lik * sG[j * M + k];
+    }
+    __syncthreads();
+  }
+  if (bad) {
+    if (tid == 0) *info = bad;
+    return;
+  }
+  // L y = r (y overwrites r)
+  for (int k = 0; k < M; ++k) {
+    if (tid == 0) sr[k] /= sG[k * M + k];
+    __syncthreads();
+    for (int i = k + 1 + tid; i < M; i += nthr) sr[i] -= sG[i * M + k] * sr[k];
+    __syncthreads();
+  }
+  // L^T c = y
+  for (int k = M - 1; k >= 0; --k) {
+    if (tid == 0) c[k] = sr[k] / sG[k * M + k];
+    __syncthreads();
+    const double ck = c[k];
+    for (int i = tid; i < k; i += nthr) sr[i] -= sG[k * M + i] * ck;
+    __syncthreads();
+  }
+  for (int e = tid; e < M * M; e += nthr) G[e] = sG[e];
+  for (int e = tid; e < M; e += nthr) r[e] = sr[e];
+  if (tid == 0) *info = 0;
+}
+
+// The same factorisation and solves on G and r in global memory, for M too large
+// for shared memory (the same operations in the same order).
+__global__ void cholesky_solve_global_kernel(int M, double* __restrict__ G, double* __restrict__ r, double* __restrict__ c,
                                       int* __restrict__ info) {
   __shared__ double piv;
   __shared__ int bad;
@@ -445,8 +510,17 @@ int pod_handle::fit_solve_dev() {
   double* dr = dG + (size_t)M * M;
   double* dc = dr + M;
   int* dinfo = (int*)(dc + M + 2 * 1024 + 8);
-  cholesky_solve_kernel<<<1, 256, 0, nullptr>>>(M, dG, dr, dc, dinfo);
-  cudaError_t e = cudaGetLastError();
+  const size_t smem = sizeof(double) * ((size_t)M * M + M);
+  cudaError_t e;
+  if (smem <= (size_t)200 * 1024) {
+    static size_t granted[64] = {};
+    e = grant_smem((const void*)cholesky_solve_kernel, smem, granted);
+    if (e != cudaSuccess) return cuda_fail(e, "cholesky shared memory");
+    cholesky_solve_kernel<<<1, 512, smem, nullptr>>>(M, dG, dr, dc, dinfo);
+  } else {
+    cholesky_solve_global_kernel<<<1, 256, 0, nullptr>>>(M, dG, dr, dc, dinfo);
+  }
+  e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "cholesky kernel");
   int info = 0;
   e = cudaMemcpy(&info, dinfo, sizeof(int), cudaMemcpyDeviceToHost);

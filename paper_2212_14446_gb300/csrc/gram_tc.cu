@@ -10,6 +10,9 @@
 // the rest are below 2^(-59) of the column maxima, so G carries no summation
 // error beyond that (the FP64 SYRK it replaces rounds once per row).  G_mn is
 // then assembled in FP64 from the integer sums, smallest slice pairs first.
+// Two forms of the slice products, with identical integer sums: tcgen05 MMAs
+// with TMEM accumulators (gram_umma_kernel, the default) and warp-level mma.sync
+// (gram_tc_kernel).
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
