@@ -214,6 +214,9 @@ def test_tensor_core_gram_equals_fp64_syrk(pkg, prec, ncfg, max_atoms):
     pkg.pod_set_option(pod.h, pkg.POD_OPT_GRAM, 2)
     Gmma, rmma = pod.fit_normal(cfgs, E_ref, F_ref)
     pkg.pod_set_option(pod.h, pkg.POD_OPT_GRAM, 0)
+    with pytest.raises(pkg.PodError) as ei:  # only 0, 1 and 2 exist
+        pkg.pod_set_option(pod.h, pkg.POD_OPT_GRAM, 3)
+    assert ei.value.code == pkg.POD_EINVAL
     Gtc, rtc = pod.fit_normal(cfgs, E_ref, F_ref)
     ctc, _, _ = pod.fit(cfgs, E_ref, F_ref)
     assert np.array_equal(Gtc, Gmma)
