@@ -381,6 +381,15 @@ int pod_autotune(pod_handle* h, const pod_system* sys, const double* c, int reps
  * bad kind/iters/null flops, POD_ECUDA on a launch failure. */
 int pod_fma_probe(int kind, int iters, double* flops, void* stream);
 
+/* Self-test of the bounded waits that the tensor-core kernels use (not a step of
+ * the method): one thread of a one-block launch on the current device waits on an
+ * mbarrier that nothing arrives at, gives up after limit_ns nanoseconds of global
+ * time (0 .. 1e10) and reports it as the status bit ST_TIMEOUT (64) in
+ * *status_out; the context stays usable.  Synchronous (default stream).
+ * POD_EINVAL on a bad limit or a null status_out, POD_ENOMEM / POD_ECUDA on a
+ * failed allocation or launch. */
+int pod_selftest_wait(long long limit_ns, int* status_out);
+
 /* Message of the last error on this handle ("" if none).  Owned by the handle. */
 const char* pod_last_error(const pod_handle* h);
 

@@ -65,7 +65,7 @@ EXPORTS = ["pod_create", "pod_destroy", "pod_info", "pod_set_option", "pod_statu
            "pod_neighbors", "pod_descriptors", "pod_energy_forces", "pod_energy_forces_host", "pod_fit",
            "pod_fit_normal", "pod_fit_solve", "pod_fit_residual", "pod_descriptors_static",
            "pod_global_descriptors", "pod_descriptors_jvp", "pod_set_skin", "pod_md_step", "pod_fma_probe", "pod_autotune", "pod_set_quadratic",
-           "pod_set_embedding", "pod_save", "pod_load", "pod_last_error"]
+           "pod_set_embedding", "pod_save", "pod_load", "pod_selftest_wait", "pod_last_error"]
 
 _lib = None
 _lock = threading.Lock()
@@ -104,6 +104,7 @@ def lib():
                 "pod_fit_solve": (C.c_int, [H, dp, dp, dp]),
                 "pod_fit_residual": (C.c_int, [H, dp, dp, dp, ip, ip]),
                 "pod_fma_probe": (C.c_int, [C.c_int, C.c_int, dp, vp]),
+                "pod_selftest_wait": (C.c_int, [C.c_longlong, C.POINTER(C.c_int)]),
                 "pod_autotune": (C.c_int, [H, S, dp, C.c_int, ip, dp, vp]),
                 "pod_set_quadratic": (C.c_int, [H, dp]),
                 "pod_set_embedding": (C.c_int, [H, dp, C.c_int, dp]),
@@ -138,6 +139,16 @@ def pod_destroy(h):
 
 def pod_last_error(h) -> str:
     return lib().pod_last_error(h).decode()
+
+
+def pod_selftest_wait(limit_ns: int) -> int:
+    """Run the bounded-wait self-test (a wait on a barrier nothing arrives at,
+    limit ``limit_ns`` ns); returns the status bits it reported (64 = ST_TIMEOUT)."""
+    st = C.c_int(0)
+    rc = lib().pod_selftest_wait(int(limit_ns), C.byref(st))
+    if rc != POD_OK:
+        raise PodError(rc, "pod_selftest_wait failed")
+    return st.value
 
 
 def pod_fma_probe(kind: int, iters: int, stream=None) -> float:

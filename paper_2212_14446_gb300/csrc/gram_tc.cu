@@ -255,9 +255,11 @@ __device__ __forceinline__ bool mbar_try(unsigned bar, unsigned parity) {
       : "memory");
   return ok != 0;
 }
-// Wait for the completion of phase `parity`; false if about two seconds pass or
-// (when stop is given) another role has set *stop.
-__device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity, const volatile int* stop) {
+// Wait for the completion of phase `parity`; false if limit_ns of global time
+// pass (about two seconds by default) or (when stop is given) another role has
+// set *stop.
+__device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity, const volatile int* stop,
+                                          unsigned long long limit_ns = 2000000000ull) {
   unsigned long long t0 = 0;
   for (unsigned it = 0;; ++it) {
     if (mbar_try(bar, parity)) return true;
@@ -266,10 +268,21 @@ __device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity, const v
       const unsigned long long t = global_ns();
       if (it == 0)
         t0 = t;
-      else if (t - t0 > 2000000000ull)
+      else if (t - t0 > limit_ns)
         return false;
     }
   }
+}
+
+// Self-test of the bounded wait: one thread waits on an mbarrier that nothing
+// arrives at and reports ST_TIMEOUT when the limit runs out.
+__global__ void wait_selftest_kernel(unsigned long long limit_ns, int* __restrict__ status) {
+  __shared__ __align__(8) unsigned long long bar;
+  if (threadIdx.x != 0) return;
+  const unsigned b = smem_u32(&bar);
+  mbar_init(b, 1);
+  asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  if (!mbar_wait(b, 0u, nullptr, limit_ns)) atomicOr(status, ST_TIMEOUT);
 }
 
 __device__ __forceinline__ void bulk_g2s(unsigned dst, const void* src, unsigned bytes, unsigned bar) {
@@ -673,4 +686,19 @@ int pod_handle::fit_gram_tc(double gamma, double* dG, double* dr, bool legacy_mm
   atb_final_kernel<<<(M + 127) / 128, 128, 0, nullptr>>>(M, TC_COLBLK, apart, dr);
   if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "Gram assembly");
   return POD_OK;
+}
+
+extern "C" int pod_selftest_wait(long long limit_ns, int* status_out) {
+  if (!status_out || limit_ns < 0 || limit_ns > 10000000000LL) return POD_EINVAL;
+  int* d = nullptr;
+  cudaError_t e = cudaMalloc(&d, sizeof(int));
+  if (e != cudaSuccess) return POD_ENOMEM;
+  e = cudaMemset(d, 0, sizeof(int));
+  if (e == cudaSuccess) {
+    wait_selftest_kernel<<<1, 32>>>((unsigned long long)limit_ns, d);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpy(status_out, d, sizeof(int), cudaMemcpyDeviceToHost);
+  cudaFree(d);
+  return e == cudaSuccess ? POD_OK : POD_ECUDA;
 }

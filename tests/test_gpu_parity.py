@@ -13,6 +13,8 @@ with the oracle's separately in test_lib_cpu.py).
 """
 import math
 
+import time
+
 import numpy as np
 import pytest
 
@@ -336,6 +338,22 @@ def test_error_codes(pkg):
     # the handle stays usable after errors
     ok = synth.config_small()
     pod.energy_forces(soa(ok), ok.box, c)
+
+
+def test_bounded_wait_reports_timeout(pkg):
+    """The bounded mbarrier wait of the tensor-core kernels, on a barrier that
+    nothing arrives at: it gives up after its limit (50 ms here), reports
+    ST_TIMEOUT (64) through the status word, and the context stays usable."""
+    t0 = time.perf_counter()
+    st = pkg.pod_selftest_wait(50_000_000)
+    elapsed = time.perf_counter() - t0
+    assert st == 64
+    assert 0.04 <= elapsed < 5.0
+    ok = synth.config_small()
+    pod = pkg.POD(synth.params_full())
+    c = torch.zeros(pod.M, dtype=torch.float64, device=DEV)
+    out = pod.energy_forces(soa(ok), ok.box, c)
+    assert float(out["E"]) == 0.0
 
 
 def test_mixed_energy_virial_totals(pkg, full):

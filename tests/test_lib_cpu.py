@@ -55,6 +55,14 @@ def test_param_validation(pkg):
         assert ei.value.code == pkg.POD_EINVAL
 
 
+def test_selftest_wait_validates_arguments(pkg):
+    # refused before any CUDA call, so this runs without a GPU
+    for limit in (-1, 10**10 + 1):
+        with pytest.raises(pkg.PodError) as ei:
+            pkg.pod_selftest_wait(limit)
+        assert ei.value.code == pkg.POD_EINVAL
+
+
 def test_sizes_match_oracle(pkg):
     for p in (synth.params_small(), synth.params_full(),
               synth.PODParams(K2=2, K3=1, K4=1, P3=2, P4=1), synth.PODParams(K2=5, K3=3, K4=3, P3=2, P4=2)):
