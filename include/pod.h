@@ -207,7 +207,8 @@ int pod_md_step(pod_handle* h, const pod_system* sys, double* pos, double* v, do
 int pod_timing(pod_handle* h, double* ms, int* calls);
 
 /* Waits for `stream` and returns the device-side status accumulated since the
- * last report (POD_OK, POD_ERANGE, POD_ENONFINITE, POD_ENEIGH), then clears it. */
+ * last report (POD_OK, POD_ERANGE, POD_ENONFINITE, POD_ENEIGH, or POD_ECUDA when a
+ * bounded wait inside a kernel ran out), then clears it. */
 int pod_status(pod_handle* h, void* stream);
 
 /* Full neighbour list of one configuration (the cut-off region of Section 2.2):
