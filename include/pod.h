@@ -305,19 +305,27 @@ int pod_fit_residual(pod_handle* h, const double* c, double* sum_abs_E, double* 
  * all device memory in their own pool with a fixed budget and forbid other code
  * from calling cudaMalloc / cudaFree (which synchronise the device and fragment
  * the pool).  The caller passes the positions (device [3][N]) and the output D
- * (device [N][M]), as for pod_descriptors; every intermediate buffer lives in one
- * file-scope device array of about 6.3 MB that each GPU loading the library holds
- * until the process exits.
+ * (device [N][M]), as for pod_descriptors; every intermediate buffer, the mixed
+ * path's radial table included, lives in one file-scope device array of about
+ * 6.8 MB that each GPU loading the library holds until the process exits.  The
+ * call allocates nothing: no cudaMalloc, cudaFree or allocating library routine.
  *   Limits: one configuration of 1..4096 atoms (POD_EINVAL beyond), at most 64
- *   neighbours per atom and 32 atoms per cell (POD_ENEIGH beyond).
- *   The mixed path evaluates the radial snapshots per pair (POD_OPT_RADIAL = 1
- *   behaviour; descriptor error ~1e-5); the FP64 path is identical to
- *   pod_descriptors.
- *   The first call on a device looks up the array's device address with that
- *   device current (cudaGetSymbolAddress) and caches it.
- *   All calls share the array and it keeps the previous call's contents: calls
- *   that overlap on the GPU (other streams or host threads) race and must be
- *   serialised by the caller.  Waits for `stream` before returning. */
+ *   neighbours per atom and 32 atoms per cell (POD_ENEIGH beyond); every atom is
+ *   evaluated (n_local in (0, N) is refused with POD_EINVAL).  The handle's
+ *   device must be current (POD_EINVAL otherwise), as for every other call.
+ *   Results: the same kernels and radial evaluation as pod_descriptors on the
+ *   handle (mixed path: the FP64-built radial table by default, per-pair
+ *   snapshots under POD_OPT_RADIAL = 1; FP64 path unchanged).
+ *   Set-up: pod_create, on its device and with that device current, looks up
+ *   the array's device address (cudaGetSymbolAddress) and caches it; under
+ *   CUDA's lazy module loading this is where the array is loaded.  Should that
+ *   lookup fail there, the first call repeats it (it then belongs before any
+ *   stream capture).  The first call of a handle copies its radial table (mixed
+ *   path, up to 512 KB) into the array from host memory.
+ *   All calls share the array and it keeps the previous call's contents (the
+ *   call clears what must start at zero): calls that overlap on the GPU (other
+ *   streams or host threads) race and must be serialised by the caller.  Waits
+ *   for `stream` before returning. */
 int pod_descriptors_static(pod_handle* h, const pod_system* sys, double* D, void* stream);
 
 /* Quadratic POD model (Sec. 4, the extension of Eq. 57a with products of

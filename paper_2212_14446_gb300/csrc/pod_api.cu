@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -370,6 +371,8 @@ int pod_create(const pod_params* prm, pod_handle** out) {
   if (!prm) return POD_EINVAL;
   pod_handle* h = new (std::nothrow) pod_handle();
   if (!h) return POD_ENOMEM;
+  static std::atomic<unsigned long long> next_uid{1};
+  h->uid = next_uid.fetch_add(1);
   if (cudaGetDevice(&h->device) != cudaSuccess) {
     cudaGetLastError();
     h->device = -1;
@@ -422,6 +425,9 @@ int pod_create(const pod_params* prm, pod_handle** out) {
   }
   fill_radial<float>(h, h->rad32);
   fill_radial<double>(h, h->rad64);
+  // set-up of the allocation-free entry point on this device (address of its
+  // static scratch array); a failure here is reported by that entry point
+  if (h->device >= 0) static_scratch_setup(h->device);
   *out = h;
   return POD_OK;
 }
@@ -814,8 +820,9 @@ void pod_handle::fill_args(AtomArgs<T>& a, const Plan& pl) {
 // Cubic Hermite pieces of R_k on TAB_N equal intervals of (r_in, r_cut), from
 // FP64 values and derivatives of the snapshot projection at the nodes (the first
 // node is taken 1e-4 h inside the interval, where phi has its removable 0/0).
-int pod_handle::ensure_table(cudaStream_t st) {
-  if (tab_ready) return POD_OK;
+// Built once per handle on the host (h_tab) and uploaded on first use.
+void pod_handle::build_table_host() {
+  if (!h_tab.empty()) return;
   const int n = TAB_N;
   const double h = (P.r_cut - P.r_in) / n;
   std::vector<double> R((size_t)(n + 1) * K), dR((size_t)(n + 1) * K), phi(Ns), dphi(Ns);
@@ -844,9 +851,15 @@ int pod_handle::ensure_table(cudaStream_t st) {
       q.z = (float)(3.0 * (f1 - f0) - 2.0 * d0 - d1);
       q.w = (float)(2.0 * (f0 - f1) + d0 + d1);
     }
+  h_tab.swap(tab);
+}
+
+int pod_handle::ensure_table(cudaStream_t st) {
+  if (tab_ready) return POD_OK;
+  build_table_host();
   int rc_;
-  if ((rc_ = ensure(rtab, sizeof(Q4<float>) * tab.size(), "radial table"))) return rc_;
-  cudaError_t e = cudaMemcpy(rtab.p, tab.data(), sizeof(Q4<float>) * tab.size(), cudaMemcpyHostToDevice);
+  if ((rc_ = ensure(rtab, sizeof(Q4<float>) * h_tab.size(), "radial table"))) return rc_;
+  cudaError_t e = cudaMemcpy(rtab.p, h_tab.data(), sizeof(Q4<float>) * h_tab.size(), cudaMemcpyHostToDevice);
   if (e != cudaSuccess) return cuda_fail(e, "radial table upload");
   (void)st;
   tab_ready = true;

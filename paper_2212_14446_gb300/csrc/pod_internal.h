@@ -89,7 +89,10 @@ struct pod_handle {
   static constexpr int TAB_N = 2048;
   int radial_mode = 0;  // mixed path: 0 = tabulated R_k, 1 = snapshots evaluated per pair
   bool tab_ready = false;
+  std::vector<fastpod::Q4<float>> h_tab;  // the table's host copy ([TAB_N][K] cubic pieces)
+  void build_table_host();
   int ensure_table(cudaStream_t st);
+  unsigned long long uid = 0;  // unique per handle for the process lifetime (never reused)
 
   ~pod_handle();
   std::vector<DevBuf*> all_bufs();
@@ -147,3 +150,7 @@ struct pod_handle {
   int descriptors(const pod_system* sys, double* D, cudaStream_t st);
   int neighbors(const pod_system* sys, int cap_out, int* count, int* nbr, int* shift, cudaStream_t st);
 };
+
+// Looks up (once per device, with that device current) the device address of
+// the static scratch array of pod_descriptors_static; returns a cudaError_t.
+int static_scratch_setup(int device);
