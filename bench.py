@@ -24,7 +24,8 @@ Multi-GPU (torchrun): every rank evaluates its own independent configuration
 (weak scaling, no collective on the data path); rank 0 prints the JSON line.
 
 ``--impl reference`` times the FP64 CPU oracle (the only reference this method
-has: the paper publishes no code) on a bounded sample of the same workload.
+has: the paper publishes no code) on the same workload, through its fast route
+(cell list + atom-density energy and pair gradients) on every host core.
 """
 from __future__ import annotations
 
@@ -63,19 +64,34 @@ def monomials(P):
 
 
 def algorithmic_flops_per_atom(params, n_pairs_per_atom):
-    """Arithmetic the method needs per atom for energy + forces, counted from
-    the formulation (not from the kernel's instruction mix):
-      per pair  snapshots -> R, R' projection      4 Ns K
-                angular monomials (degree >= 2)     N_a - 4
-                B += R A                            2 K N_a
-                adjoint: u_m = a_m . A, e = a^T R   4 K N_a
-                R' . u                              2 K
-                grad of sum_x e_x A_x               2 * #(x, d : e_d(x) > 0)
-                tangential projection and output    15
-      per atom  three-body sums of squares          2 N_a K
-                four-body cubic adjoint             7 * merged triple terms * K
-                energy and adjoint bookkeeping      4 N_a K
-    Transcendentals (about 5 per pair) are not counted."""
+    """Algorithmic arithmetic of one energy + force evaluation per atom, the
+    per-unit figures of the method's operation count (independent of how the
+    kernel schedules it):
+      per pair  forward: snapshots (~12 Ns), projection R and R' (4 Ns K),
+                monomials (N_a - 4), B += R A (2 K N_a)             ~0.7 kflop
+                adjoint: e = a^T R and R' (a . A) (4 K N_a), grad of
+                the angular polynomial and tangential output          ~1.15 kflop
+                -> 1.9 kflop per pair at K = 6, N_a = 35 (Ns = 8)
+      per atom  three- and four-body contraction and its adjoint over the
+                K C_a triple terms of Eq. 30a (C_a of Table 5)        ~13 kflop
+                at K = 6, C_a = 209
+    For other parameters the per-pair figure scales with K N_a and the per-atom
+    one with K C_a (K N_a for a three-body-only model)."""
+    K, Pa = params.Kr, params.Pa
+    NA = len(monomials(Pa))
+    pair = 1900.0 * (K * NA) / (6 * 35)
+    if params.P4 >= 0:
+        Ca = sum(_nmono(a) * _nmono(b) * _nmono(c) for a, b, c in _partitions_upto(params.P4))
+        atom = 13000.0 * (K * Ca) / (6 * 209)
+    else:
+        atom = 13000.0 * (K * NA) / (6 * 209)
+    return n_pairs_per_atom * pair + atom
+
+
+def kernel_flops_per_atom(params, n_pairs_per_atom):
+    """The fused kernel's own count (duplicate Eq. 30a triples merged, transcendentals
+    not counted): per pair 4 Ns K + (N_a - 4) + 6 K N_a + 2 K + 2 #(grad terms) + 15,
+    per atom 2 N_a K + 7 (merged four-body terms) K + 4 N_a K."""
     Ns, K, Pa = params.Ns, params.Kr, params.Pa
     mons = monomials(Pa)
     NA = len(mons)
@@ -84,6 +100,15 @@ def algorithmic_flops_per_atom(params, n_pairs_per_atom):
     nterms = four_body_terms(params.P4)
     atom = 2 * NA * K + 7 * nterms * K + 4 * NA * K
     return n_pairs_per_atom * pair + atom
+
+
+def _nmono(n):
+    return (n + 1) * (n + 2) // 2
+
+
+def _partitions_upto(P):
+    return [(a, b, n - a - b) for n in range(P + 1) for a in range(n, -1, -1)
+            for b in range(min(a, n - a), -1, -1) if 0 <= n - a - b <= b]
 
 
 def four_body_terms(P4):
@@ -212,46 +237,45 @@ def host_cores():
         return os.cpu_count() or 1
 
 
-def oracle_sample(params, cfg, c, budget_s, max_atoms=None, threads=1):
-    """Time the FP64 oracle (brute-force neighbour list + atom-density energy and
-    pair gradients) on a sample of atoms, on `threads` host threads (the oracle's
-    C routines keep no shared state and run without the interpreter lock).
-    Returns (atoms done, elapsed seconds)."""
-    import concurrent.futures as cf
+SAMPLE_ATOMS = 65536  # the largest block of atoms one timed oracle evaluation covers
+
+
+def oracle_eval(orc, cfg, c, threads):
+    """One evaluation by the FP64 oracle's fast route: cell list, atom-density
+    energy and pair gradients, forces and virial of every atom (systems of more
+    than SAMPLE_ATOMS atoms: of a block of that many atoms).  Returns atoms done."""
+    if cfg.n <= SAMPLE_ATOMS:
+        orc.energy_forces_cells(cfg, c, threads=threads)
+        return cfg.n
+    orc.energy_forces_cells(cfg, c, threads=threads, atom_range=(0, SAMPLE_ATOMS))
+    return SAMPLE_ATOMS
+
+
+def oracle_sample(params, cfg, c, budget_s, threads=1):
+    """Repeat oracle_eval on `threads` host threads until `budget_s` has passed
+    (at least once).  Returns (atoms done, elapsed seconds)."""
     import oracle
     orc = oracle.Oracle(params)
-    sysd = orc._system(cfg)
+    n = 0
     t0 = time.perf_counter()
-
-    def worker(t):
-        n = 0
-        k = t
-        while True:
-            i = (k * 7919) % cfg.n
-            _, _, d = orc.neighbors(cfg, i, sysd)
-            orc.atom_energy_grad(d, c)
-            n += 1
-            k += threads
-            if time.perf_counter() - t0 >= budget_s or (max_atoms and n * threads >= max_atoms):
-                return n
-
-    if threads <= 1:
-        n = worker(0)
-    else:
-        with cf.ThreadPoolExecutor(max_workers=threads) as ex:
-            n = sum(ex.map(worker, range(threads)))
+    while True:
+        n += oracle_eval(orc, cfg, c, threads)
+        if time.perf_counter() - t0 >= budget_s:
+            break
     return n, time.perf_counter() - t0
 
 
 def cpu_baseline_line(params, cfg, c, budget_s, unit="atom-steps/s"):
-    """The oracle on every host core of this machine, plus its one-core figure."""
+    """The oracle's fast route on every host core of this machine, plus its one-core figure."""
     cores = host_cores()
     n1, e1 = oracle_sample(params, cfg, c, budget_s / 4, threads=1)
     nn, en = oracle_sample(params, cfg, c, budget_s, threads=cores)
+    what = (f"all {cfg.n} atoms" if cfg.n <= SAMPLE_ATOMS else f"the first {SAMPLE_ATOMS} atoms")
     return {"value": nn / en, "unit": unit, "cores": cores, "kind": "oracle",
-            "sample": f"{nn} atoms of the same configuration on {cores} host threads in {en:.1f} s "
-                      f"(brute-force neighbour list + atom-density energy and pair gradients, FP64); "
-                      f"one core: {n1} atoms in {e1:.1f} s",
+            "sample": f"{nn // min(cfg.n, SAMPLE_ATOMS)} evaluations of {what} of the same configuration on "
+                      f"{cores} host threads in {en:.1f} s (FP64 oracle, fast route: cell-list neighbours + "
+                      f"atom-density energy, pair gradients, forces, virial); one core: {n1} atom evaluations "
+                      f"in {e1:.1f} s",
             "single_core_value": n1 / e1}
 
 
@@ -386,6 +410,7 @@ def main():
     count = pkg.POD(params, precision=args.precision).neighbors(pos, box, cap=96)[0]
     n_pairs = float(count.double().mean().item())
     fl_atom = algorithmic_flops_per_atom(params, n_pairs)
+    fl_kernel = kernel_flops_per_atom(params, n_pairs)
     atom_ms = phase_avg[1]
     achieved_tflops = fl_atom * N / (atom_ms / 1e3) / 1e12
     peak_tflops = N_SM * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
@@ -482,6 +507,9 @@ def main():
                          "achieved": achieved_tflops, "peak": peak_tflops, "unit": "TFLOP/s",
                          "frac": achieved_tflops / peak_tflops, "traffic": traffic,
                          "flops_per_atom": fl_atom, "atom_kernel_ms": atom_ms,
+                         "flop_model": "1.9 kflop per pair + 13 kflop per atom (K = 6, N_a = 35, C_a = 209)",
+                         "kernel_count_flops_per_atom": fl_kernel,
+                         "frac_kernel_count": fl_kernel * N / (atom_ms / 1e3) / 1e12 / peak_tflops,
                          "peak_basis": ("152 SMs x 128 FP32 lanes x 2 x 2070 MHz (nominal max clock)"
                                         if args.precision == "mixed" else "nominal FP64 1.25 TFLOP/s"),
                          "measured_vector_tflops": vec_peaks,
@@ -667,31 +695,36 @@ def kernel_revision():
 
 
 def run_reference(args, rank, world):
+    """The reference arm: the FP64 oracle's fast route (cell list + atom-density
+    energy, pair gradients, forces and virial) on every host core; one step is
+    one evaluation of the workload (of a block of SAMPLE_ATOMS atoms for larger
+    systems).  Under torchrun only rank 0 runs."""
     if rank != 0:
         return
+    import oracle
     params, cfg, wname = workload(args.workload, replica=0)
     c = synth.coefficients(1 + params.K2 + params.K3 * (params.P3 + 1) + params.K4 * _ka(params.P4), 2001)
-    budget = max(1.0, args.cpu_budget / max(1, args.steps + args.warmup))
     cores = host_cores()
+    orc = oracle.Oracle(params)
     for _ in range(args.warmup):
-        oracle_sample(params, cfg, c, budget / 4, threads=cores)
+        oracle_eval(orc, cfg, c, cores)
     tot_atoms, tot_s = 0, 0.0
-    per_step = []
     for _ in range(args.steps):
-        n, el = oracle_sample(params, cfg, c, budget, threads=cores)
-        tot_atoms += n
-        tot_s += el
-        per_step.append(el)
+        t0 = time.perf_counter()
+        tot_atoms += oracle_eval(orc, cfg, c, cores)
+        tot_s += time.perf_counter() - t0
     value = tot_atoms / tot_s
+    per = min(cfg.n, SAMPLE_ATOMS)
     line = {"impl": "reference",
             "metric": "atom-steps/s (E+F) mixed vs FP64 at stated force error; % of roofline",
             "value": value, "unit": "atom-steps/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * tot_s / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": wname, "atoms_per_gpu": cfg.n},
+            "config": {"workload": wname, "atoms_per_gpu": cfg.n, "atoms_per_step": per},
             "cpu_baseline": {"value": value, "unit": "atom-steps/s", "cores": cores, "kind": "oracle",
-                             "sample": f"{tot_atoms} atom evaluations (brute-force neighbours + FP64 "
-                                       f"atom-density energy and pair gradients) on {cores} host threads"},
+                             "sample": f"{args.steps} evaluations of {per} atoms (FP64 oracle, fast route: "
+                                       f"cell-list neighbours + atom-density energy, pair gradients, forces, "
+                                       f"virial) on {cores} host threads"},
             "e2e": {"value": value, "unit": "atom-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 

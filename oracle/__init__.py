@@ -87,6 +87,9 @@ def lib():
                 "orc_monomial_table": (i, [i, ip, dp]), "orc_snapshots": (i, [P, d, dp, dp]),
                 "orc_basis": (i, [P, i, i, dp, dp, dp]), "orc_radial_eval": (None, [P, dp, i, i, dp, dp, dp]),
                 "orc_neighbors_of": (i, [S, d, i, i, ip, ip, dp]),
+                "orc_cells_build": (C.c_void_p, [S, d]), "orc_cells_free": (None, [C.c_void_p]),
+                "orc_cells_neighbors_of": (i, [C.c_void_p, d, i, i, ip, ip, dp]),
+                "orc_energy_forces_range": (i, [P, dp, dp, C.c_void_p, d, i, i, i, dp, dp, dp, dp]),
                 "orc_atom_descriptors_naive": (i, [P, dp, i, dp, dp]),
                 "orc_atom_descriptors_fast": (i, [P, dp, i, dp, dp]),
                 "orc_atom_dD_naive": (i, [P, dp, i, dp, dp]),
@@ -133,6 +136,25 @@ def num_monomials(P: int) -> int:
 
 # ------------------------------------------------------------------- oracle
 
+class _SysData:
+    """One configuration as the oracle's C routines take it (atom-major FP64
+    positions), with an optional cell list built by the C side."""
+
+    def __init__(self, cfg, r_cut: float, cells: bool):
+        self.pos = np.ascontiguousarray(cfg.pos, dtype=np.float64)
+        self.s = _System(self.pos.shape[0], _dp(self.pos), (C.c_double * 3)(*cfg.box), (C.c_int * 3)(*cfg.pbc))
+        self.cells = None
+        if cells:
+            self.cells = lib().orc_cells_build(C.byref(self.s), float(r_cut))
+            if not self.cells:
+                raise MemoryError("oracle cell list")
+
+    def __del__(self):
+        if getattr(self, "cells", None):
+            lib().orc_cells_free(self.cells)
+            self.cells = None
+
+
 class Oracle:
     """FP64 oracle bound to one parameter set.  Q is computed by the oracle's own
     POD (Gram matrix + cyclic Jacobi) unless given."""
@@ -175,24 +197,32 @@ class Oracle:
         return R, dR
 
     # -- neighbours
-    @staticmethod
-    def _system(cfg):
-        pos = np.ascontiguousarray(cfg.pos, dtype=np.float64)
-        s = _System(pos.shape[0], _dp(pos), (C.c_double * 3)(*cfg.box), (C.c_int * 3)(*cfg.pbc))
-        return s, pos
+    # Two routes to the same list: the brute-force scan over every atom and image
+    # (orc_neighbors_of, the definition), and a cell list (orc_cells_neighbors_of)
+    # that the CPU tests pin to it entry for entry; systems of CELLS_MIN atoms or
+    # more take the cell list.
+    CELLS_MIN = 4096
+
+    def _system(self, cfg, cells=None):
+        return _SysData(cfg, self.params.r_cut, (cfg.n >= self.CELLS_MIN) if cells is None else cells)
 
     def neighbors(self, cfg, i: int, _sys=None):
-        s, keep = _sys if _sys is not None else self._system(cfg)
+        sd = _sys if _sys is not None else self._system(cfg)
         js = np.zeros(CAP, dtype=np.int32)
         sh = np.zeros((CAP, 3), dtype=np.int32)
         d = np.zeros((CAP, 3))
-        n = lib().orc_neighbors_of(C.byref(s), self.params.r_cut, int(i), CAP, _ip(js), _ip(sh), _dp(d))
+        if sd.cells:
+            n = lib().orc_cells_neighbors_of(sd.cells, self.params.r_cut, int(i), CAP, _ip(js), _ip(sh), _dp(d))
+        else:
+            n = lib().orc_neighbors_of(C.byref(sd.s), self.params.r_cut, int(i), CAP, _ip(js), _ip(sh), _dp(d))
+        if n < 0:
+            raise MemoryError("oracle neighbour search")
         if n > CAP:
             raise ValueError("oracle neighbour capacity exceeded")
         return js[:n].copy(), sh[:n].copy(), d[:n].copy()
 
-    def neighbor_lists(self, cfg, atoms=None):
-        sysd = self._system(cfg)
+    def neighbor_lists(self, cfg, atoms=None, cells=None):
+        sysd = self._system(cfg, cells)
         atoms = range(cfg.n) if atoms is None else atoms
         return [self.neighbors(cfg, i, sysd) for i in atoms]
 
@@ -411,6 +441,47 @@ class Oracle:
             W -= d.T @ g
         return Ei, math.fsum(Ei), F, W
 
+    def energy_forces_cells(self, cfg, c, threads: int = 1, cap: int = CAP, atom_range=None, escale=None):
+        """Linear-model E_i, E, F and W of every atom through the cell list and the
+        atom-density form (Eq. 24b, 26a, 27a, 30a and their adjoint), in C over
+        chunks of atoms on `threads` host threads (each with its own force and
+        virial accumulators, summed afterwards).  The faster CPU route to the
+        quantities of ``energy_forces``; the CPU tests pin the two together.
+        With ``atom_range`` = (i0, i1) only those atoms' energy terms are formed
+        (their pair gradients still reach every atom's force).  With ``escale``
+        an array of N, escale[i] receives sum_m |c_m D_im| (the energy-error scale
+        of the tolerances)."""
+        import concurrent.futures as cf
+        c = np.ascontiguousarray(c, dtype=np.float64)
+        sd = self._system(cfg, cells=True)
+        N = cfg.n
+        i0, i1 = (0, N) if atom_range is None else (int(atom_range[0]), int(atom_range[1]))
+        Ei = np.zeros(N)
+        T = max(1, min(int(threads), i1 - i0))
+        Fs = [np.zeros((N, 3)) for _ in range(T)]
+        Ws = [np.zeros((3, 3)) for _ in range(T)]
+        bounds = [i0 + (i1 - i0) * t // T for t in range(T + 1)]
+
+        def run(t):
+            return lib().orc_energy_forces_range(self.pp, _dp(self.Q), _dp(c), sd.cells, self.params.r_cut,
+                                                 bounds[t], bounds[t + 1], int(cap), _dp(Ei), _dp(Fs[t]),
+                                                 _dp(Ws[t]), _dp(escale) if escale is not None else None)
+
+        if T == 1:
+            res = [run(0)]
+        else:
+            with cf.ThreadPoolExecutor(max_workers=T) as ex:
+                res = list(ex.map(run, range(T)))
+        if min(res) < 0:
+            raise ValueError("oracle neighbour capacity exceeded")
+        F = Fs[0]
+        for t in range(1, T):
+            F += Fs[t]
+        W = Ws[0]
+        for t in range(1, T):
+            W += Ws[t]
+        return Ei, math.fsum(Ei), F, W
+
     # -- fit (Eq. 63a)
     def config_rows(self, cfg, fast: bool = True):
         """Global descriptors G (M,) and dG/dr_k (N, 3, M) of one configuration."""
@@ -434,6 +505,29 @@ class Oracle:
             rows.append(w_F * (-dG.reshape(-1, self.M)))
             rhs.append(w_F * np.asarray(F, dtype=np.float64).reshape(-1))
         return np.vstack(rows), np.concatenate(rhs)
+
+    def normal_equations(self, configs, E_ref, F_ref, w_E=100.0, w_F=1.0, gamma=1e-12, fast=True, threads=1):
+        """A^T A + gamma I and A^T b of ``design_matrix`` (Eq. 63a), each
+        configuration's block of rows formed on one of `threads` host threads and
+        the blocks' products summed in configuration order."""
+        import concurrent.futures as cf
+
+        def block(k):
+            A, b = self.design_matrix([configs[k]], [E_ref[k]], [F_ref[k]], w_E, w_F, fast)
+            return A.T @ A, A.T @ b
+
+        if threads <= 1:
+            parts = [block(k) for k in range(len(configs))]
+        else:
+            with cf.ThreadPoolExecutor(max_workers=threads) as ex:
+                parts = list(ex.map(block, range(len(configs))))
+        G = np.zeros((self.M, self.M))
+        r = np.zeros(self.M)
+        for Gk, rk in parts:
+            G += Gk
+            r += rk
+        G += gamma * np.eye(self.M)
+        return G, r
 
     def fit(self, configs, E_ref, F_ref, w_E=100.0, w_F=1.0, gamma=1e-12, fast=True):
         A, b = self.design_matrix(configs, E_ref, F_ref, w_E, w_F, fast)

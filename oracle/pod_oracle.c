@@ -342,6 +342,164 @@ int orc_neighbors_of(const orc_system* sy, double rcut, int i, int cap, int* js,
   return cnt;
 }
 
+/* Cell-list form of the same neighbour search (a second, faster route to the
+ * list above, for large systems and the timed CPU baseline).  Cells are at
+ * least r_cut wide; every (cell, image) whose unwrapped cell index lies within
+ * ceil(r_cut / cell) + 1 of the atom's cell is scanned (one cell of margin
+ * against rounding in the cell assignment), each candidate is tested with the
+ * same FP64 expression as orc_neighbors_of, and the hits are sorted by
+ * (j, s_x, s_y, s_z), so both routes give the same list entry for entry. */
+typedef struct {
+  int N, nc[3], S[3], pbc[3];
+  double lo[3], cs[3], box[3];
+  double* xw;      /* N x 3 wrapped (periodic) or raw (open) positions */
+  int* start;      /* ncells + 1 */
+  int* atoms;      /* N, ascending atom index within each cell */
+} orc_cells;
+
+void orc_cells_free(orc_cells* cl) {
+  if (!cl) return;
+  free(cl->xw);
+  free(cl->start);
+  free(cl->atoms);
+  free(cl);
+}
+
+static int orc_cell_of(const orc_cells* cl, int a, double x) {
+  int c = (int)floor((x - cl->lo[a]) / cl->cs[a]);
+  if (c < 0) c = 0;
+  if (c >= cl->nc[a]) c = cl->nc[a] - 1;
+  return c;
+}
+
+orc_cells* orc_cells_build(const orc_system* sy, double rcut) {
+  orc_cells* cl = (orc_cells*)calloc(1, sizeof(orc_cells));
+  if (!cl) return NULL;
+  const int N = sy->N;
+  cl->N = N;
+  cl->xw = (double*)malloc(sizeof(double) * 3 * (size_t)(N + 1));
+  if (!cl->xw) { orc_cells_free(cl); return NULL; }
+  long long ncells = 1;
+  for (int a = 0; a < 3; ++a) {
+    cl->pbc[a] = sy->pbc[a] ? 1 : 0;
+    cl->box[a] = sy->box[a];
+    double lo = 0.0, hi = 0.0;
+    for (int i = 0; i < N; ++i) {
+      const double x = sy->pos[3 * i + a];
+      const double v = cl->pbc[a] ? orc_wrap(x, sy->box[a]) : x;
+      cl->xw[3 * i + a] = v;
+      if (i == 0 || v < lo) lo = v;
+      if (i == 0 || v > hi) hi = v;
+    }
+    if (cl->pbc[a]) {
+      lo = 0.0;
+      hi = sy->box[a];
+    }
+    int nc = (int)floor((hi - lo) / rcut);
+    if (nc < 1) nc = 1;
+    if (nc > 256) nc = 256;
+    cl->nc[a] = nc;
+    cl->lo[a] = lo;
+    cl->cs[a] = hi > lo ? (hi - lo) / nc : 1.0;
+    cl->S[a] = (int)ceil(rcut / cl->cs[a]) + 1;
+    ncells *= nc;
+  }
+  cl->start = (int*)calloc((size_t)ncells + 1, sizeof(int));
+  cl->atoms = (int*)malloc(sizeof(int) * (size_t)(N + 1));
+  int* cell = (int*)malloc(sizeof(int) * (size_t)(N + 1));
+  if (!cl->start || !cl->atoms || !cell) { free(cell); orc_cells_free(cl); return NULL; }
+  for (int i = 0; i < N; ++i) {
+    const int cx = orc_cell_of(cl, 0, cl->xw[3 * i]);
+    const int cy = orc_cell_of(cl, 1, cl->xw[3 * i + 1]);
+    const int cz = orc_cell_of(cl, 2, cl->xw[3 * i + 2]);
+    cell[i] = (cz * cl->nc[1] + cy) * cl->nc[0] + cx;
+    cl->start[cell[i] + 1]++;
+  }
+  for (long long c = 0; c < ncells; ++c) cl->start[c + 1] += cl->start[c];
+  int* fill = (int*)malloc(sizeof(int) * (size_t)(ncells + 1));
+  if (!fill) { free(cell); orc_cells_free(cl); return NULL; }
+  memcpy(fill, cl->start, sizeof(int) * (size_t)ncells);
+  for (int i = 0; i < N; ++i) cl->atoms[fill[cell[i]]++] = i;  /* ascending within a cell */
+  free(fill);
+  free(cell);
+  return cl;
+}
+
+typedef struct {
+  int j, s[3];
+  double d[3];
+} orc_hit;
+
+static int orc_hit_cmp(const void* pa, const void* pb) {
+  const orc_hit* a = (const orc_hit*)pa;
+  const orc_hit* b = (const orc_hit*)pb;
+  if (a->j != b->j) return a->j < b->j ? -1 : 1;
+  for (int t = 0; t < 3; ++t)
+    if (a->s[t] != b->s[t]) return a->s[t] < b->s[t] ? -1 : 1;
+  return 0;
+}
+
+/* Neighbours of atom i through the cell list; same output contract as
+ * orc_neighbors_of (returns the true count, writes at most cap entries). */
+int orc_cells_neighbors_of(const orc_cells* cl, double rcut, int i, int cap, int* js, int* sh, double* d) {
+  const double* xi = cl->xw + 3 * i;
+  int ci[3], lo[3], hi[3];
+  for (int a = 0; a < 3; ++a) {
+    ci[a] = orc_cell_of(cl, a, xi[a]);
+    lo[a] = ci[a] - cl->S[a];
+    hi[a] = ci[a] + cl->S[a];
+    if (!cl->pbc[a]) {
+      if (lo[a] < 0) lo[a] = 0;
+      if (hi[a] > cl->nc[a] - 1) hi[a] = cl->nc[a] - 1;
+    }
+  }
+  const double rc2 = rcut * rcut;
+  int nhit = 0, hcap = 64;
+  orc_hit* hits = (orc_hit*)malloc(sizeof(orc_hit) * hcap);
+  if (!hits) return -1;
+  for (int tz = lo[2]; tz <= hi[2]; ++tz)
+    for (int ty = lo[1]; ty <= hi[1]; ++ty)
+      for (int tx = lo[0]; tx <= hi[0]; ++tx) {
+        const int t[3] = {tx, ty, tz};
+        int c[3], s[3];
+        for (int a = 0; a < 3; ++a) {
+          /* unwrapped cell index t -> (cell in [0, nc), image shift floor(t / nc)) */
+          const int nc = cl->nc[a];
+          s[a] = t[a] >= 0 ? t[a] / nc : -((-t[a] + nc - 1) / nc);
+          c[a] = t[a] - s[a] * nc;
+        }
+        const int cell = (c[2] * cl->nc[1] + c[1]) * cl->nc[0] + c[0];
+        for (int q = cl->start[cell]; q < cl->start[cell + 1]; ++q) {
+          const int j = cl->atoms[q];
+          if (j == i && s[0] == 0 && s[1] == 0 && s[2] == 0) continue;
+          const double* xj = cl->xw + 3 * j;
+          const double dx = (xj[0] + s[0] * cl->box[0]) - xi[0];
+          const double dy = (xj[1] + s[1] * cl->box[1]) - xi[1];
+          const double dz = (xj[2] + s[2] * cl->box[2]) - xi[2];
+          const double r2 = (dx * dx + dy * dy) + dz * dz;
+          if (!(r2 < rc2)) continue;
+          if (nhit == hcap) {
+            hcap *= 2;
+            orc_hit* nh = (orc_hit*)realloc(hits, sizeof(orc_hit) * hcap);
+            if (!nh) { free(hits); return -1; }
+            hits = nh;
+          }
+          orc_hit* h = hits + nhit++;
+          h->j = j;
+          h->s[0] = s[0]; h->s[1] = s[1]; h->s[2] = s[2];
+          h->d[0] = dx; h->d[1] = dy; h->d[2] = dz;
+        }
+      }
+  qsort(hits, nhit, sizeof(orc_hit), orc_hit_cmp);
+  for (int k = 0; k < nhit && k < cap; ++k) {
+    if (js) js[k] = hits[k].j;
+    if (sh) { sh[3 * k] = hits[k].s[0]; sh[3 * k + 1] = hits[k].s[1]; sh[3 * k + 2] = hits[k].s[2]; }
+    if (d) { d[3 * k] = hits[k].d[0]; d[3 * k + 1] = hits[k].d[1]; d[3 * k + 2] = hits[k].d[2]; }
+  }
+  free(hits);
+  return nhit;
+}
+
 /* ----------------------------------------------------- per-atom geometry */
 
 typedef struct {
@@ -714,6 +872,48 @@ double orc_atom_energy_grad_fast(const orc_params* p, const double* Q, const dou
   free(G);
   orc_geom_free(&g);
   return E;
+}
+
+/* Linear-model atom energies and forces over the atoms [i0, i1) of a system,
+ * through the cell list and the atom-density form above: Ei[i] = E_i, and every
+ * pair gradient g_ij = dE_i/dr_ij added to F[i] and subtracted from F[j]
+ * (F: N x 3, accumulated, not cleared), W -= r_ij (x) g_ij (3 x 3, accumulated).
+ * With escale != NULL also escale[i] = sum_m |c_m D_im| (the scale of the
+ * energy tolerance), from the atom's descriptors.
+ * Returns the largest neighbour count, or -1 when it exceeds cap. */
+int orc_energy_forces_range(const orc_params* p, const double* Q, const double* c, const orc_cells* cl,
+                            double rcut, int i0, int i1, int cap, double* Ei, double* F, double* W,
+                            double* escale) {
+  const int M = orc_num_descriptors(p);
+  double* Dv = escale ? (double*)malloc(sizeof(double) * M) : NULL;
+  int* js = (int*)malloc(sizeof(int) * cap);
+  double* d = (double*)malloc(sizeof(double) * 3 * cap);
+  double* g = (double*)malloc(sizeof(double) * 3 * cap);
+  int nmax = 0;
+  if (!js || !d || !g) { free(js); free(d); free(g); return -1; }
+  for (int i = i0; i < i1; ++i) {
+    const int n = orc_cells_neighbors_of(cl, rcut, i, cap, js, NULL, d);
+    if (n < 0 || n > cap) { nmax = -1; break; }
+    if (n > nmax) nmax = n;
+    Ei[i] = orc_atom_energy_grad_fast(p, Q, c, n, d, g);
+    if (escale) {
+      orc_atom_descriptors_fast(p, Q, n, d, Dv);
+      double sc = 0.0;
+      for (int q = 0; q < M; ++q) sc += fabs(c[q] * Dv[q]);
+      escale[i] = sc;
+    }
+    for (int k = 0; k < n; ++k)
+      for (int t = 0; t < 3; ++t) {
+        F[3 * i + t] += g[3 * k + t];
+        F[3 * js[k] + t] -= g[3 * k + t];
+        for (int a = 0; a < 3; ++a) W[3 * a + t] -= d[3 * k + a] * g[3 * k + t];
+      }
+  }
+  free(js);
+  free(d);
+  free(g);
+  free(Dv);
+  return nmax;
 }
 
 /* Explicit descriptor derivatives dD[j][col][3] in the atom-density form: for

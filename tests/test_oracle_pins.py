@@ -227,6 +227,71 @@ def test_neighbor_count_against_kdtree():
         assert sorted(ref) == sorted(js.tolist())
 
 
+def _lists_equal(a, b):
+    for (ja, sa, da), (jb, sb, db) in zip(a, b):
+        assert np.array_equal(ja, jb)
+        assert np.array_equal(sa, sb)
+        assert np.array_equal(da, db)  # same FP64 expression: identical bits
+
+
+def _band_config():
+    """Pairs placed 1e-9 A inside, on, and outside r_cut along each axis."""
+    rc = 5.0
+    pos = [[10.0, 10.0, 10.0], [10.0 + rc - 1e-9, 10.0, 10.0], [10.0, 10.0 + rc, 10.0],
+           [10.0, 10.0, 10.0 + rc + 1e-9], [10.0 - rc + 1e-12, 10.0, 10.0]]
+    return synth.Config(pos=np.array(pos), box=np.array([30.0, 30.0, 30.0]), pbc=(1, 1, 1))
+
+
+@pytest.mark.parametrize("which", ["small", "train", "cluster", "mixed_pbc", "band", "full_sample", "gas"])
+def test_cell_list_equals_brute_force(which):
+    """The cell-list neighbour pass gives the brute-force list entry for entry
+    (indices, image shifts and displacement bits) on every kind of geometry:
+    minimum-image boxes, training boxes shorter than r_cut (many images), open
+    clusters, a box periodic in one direction only, pairs within 1e-9 A of r_cut,
+    and atoms of the 8,192-atom system."""
+    o = oracle.Oracle(synth.params_small())
+    if which == "small":
+        cfgs, atoms = [synth.config_small(0)], None
+    elif which == "train":
+        cfgs, atoms = [synth.config_train(k) for k in range(24)], None
+    elif which == "cluster":
+        cfgs, atoms = [synth.cluster(12, 7)], None
+    elif which == "mixed_pbc":
+        c = synth.config_train(3)
+        cfgs, atoms = [synth.Config(pos=c.pos, box=c.box, pbc=(1, 0, 1))], None
+    elif which == "band":
+        cfgs, atoms = [_band_config()], None
+    elif which == "gas":
+        cfgs, atoms = [synth.liquid(300, synth.rng(9), density=300 / 60.0 ** 3)], None
+    else:
+        cfgs, atoms = [synth.config_full(0)], list(range(0, 8192, 97))
+    for cfg in cfgs:
+        brute = o.neighbor_lists(cfg, atoms, cells=False)
+        cells = o.neighbor_lists(cfg, atoms, cells=True)
+        _lists_equal(brute, cells)
+    if which == "band":
+        js, _, _ = o.neighbors(cfgs[0], 0, o._system(cfgs[0], cells=True))
+        assert sorted(js.tolist()) == [1, 4]  # strictly inside r_cut only
+
+
+@pytest.mark.parametrize("threads", [1, 3])
+def test_cell_list_energy_forces_equal_brute_force(threads):
+    """The threaded cell-list energy/force route equals the brute-force assembly
+    of ``energy_forces`` (same per-atom arithmetic; forces and virial summed in
+    another order)."""
+    for p, cfg in [(synth.params_small(), synth.config_small(0)),
+                   (synth.params_full(), synth.config_train(11))]:
+        o = oracle.Oracle(p)
+        c = synth.coefficients(o.M, 17)
+        Ei0, E0, F0, W0 = o.energy_forces(cfg, c)
+        Ei1, E1, F1, W1 = o.energy_forces_cells(cfg, c, threads=threads)
+        assert np.array_equal(Ei0, Ei1)
+        assert E0 == E1
+        fmax = np.max(np.abs(F0))
+        assert np.max(np.abs(F1 - F0)) <= 1e-13 * fmax
+        assert np.max(np.abs(W1 - W0)) <= 1e-13 * np.max(np.abs(W0))
+
+
 # ---------------------------------------------------- descriptor identities
 
 def _cluster_disp(n, seed):
