@@ -176,6 +176,13 @@ int pod_info(const pod_handle* h, int* M, int* Ns, int* K, double* Q_out, double
                           2^-59 of the column maxima); 1 an FP64 SYRK on the FP64
                           pipes; 2 the same exact slice products through mma.sync
                           (bit-identical to 0) */
+#define POD_OPT_ADJOINT 8 /* mixed path, linear model: where the adjoint pair pass g_ij of
+                             Eq. 24c runs. -1 (default) by the autotuned launch shape, else
+                             by size (a kernel of its own up to 131,072 atoms); 0 inside the
+                             fused atom kernel; 1 as its own kernel (warp per atom, lane per
+                             pair) after a forward-only atom kernel.  Forces and atom
+                             energies are the same bits either way; E and W differ only in
+                             the grouping of their exact fixed-point sums */
 int pod_set_option(pod_handle* h, int option, int value);
 
 /* Neighbour-list skin (A, default 0): lists are built with r_cut + skin and pairs
@@ -269,12 +276,21 @@ typedef struct {
   double w_F;         /* force-row weight (paper: 1)                             */
   double gamma_reg;   /* ridge parameter (paper: 1e-12)                          */
   int per_atom_energy;/* 1: energy rows are G_m / N against E / N (default)      */
+  int solver;         /* 0 (default): Cholesky of the normal equations, and when
+                         a pivot is not positive a Householder QR of the weighted
+                         design matrix [A; sqrt(gamma_reg) I] (condition number
+                         of A instead of its square); 1: Cholesky only
+                         (POD_ESINGULAR on a non-positive pivot); 2: QR only      */
 } pod_fit_opts;
 
 /* Fits c (host [M]) to reference energies and forces of a batch of
  * configurations: rows w_E G_m(cfg) / N_cfg against w_E E_ref / N_cfg and rows
- * -w_F dG_m/dr_ka against w_F F_ref, plus gamma_reg I; normal equations
- * (A^T A + gamma I) c = A^T b solved by Cholesky, all in FP64 on the GPU.
+ * -w_F dG_m/dr_ka against w_F F_ref, plus gamma_reg I.  Normal equations
+ * (A^T A + gamma I) c = A^T b with G = A^T A formed exactly from 8-bit slice
+ * products on the tensor cores (POD_OPT_GRAM 0, default; rounding below 2^-59 of
+ * the column maxima) or by an FP64 SYRK (POD_OPT_GRAM 1), solved by FP64
+ * Cholesky; with opts->solver 0 or 2 a tall-skinny FP64 Householder QR of the
+ * weighted design matrix instead (fallback on a non-positive pivot, or always).
  *   E_ref: device [n_configs]; F_ref: device [3][N]; mae_E (per atom) and
  *   mae_F (per component) receive the training errors (host, may be NULL).
  * Synchronous.  Errors: POD_EINVAL, POD_ESINGULAR, POD_ERANGE, POD_ENEIGH,
@@ -328,6 +344,30 @@ int pod_fit_residual(pod_handle* h, const double* c, double* sum_abs_E, double* 
  *   for `stream` before returning. */
 int pod_descriptors_static(pod_handle* h, const pod_system* sys, double* D, void* stream);
 
+/* Spatial decomposition of one periodic system into slabs along an axis, one GPU
+ * per slab (the per-atom evaluation of Sec. 2 split over GPUs; the paper has no
+ * multi-GPU counterpart).  Each domain is evaluated by pod_energy_forces with
+ * its own atoms first and the ghosts after them (pod_system.n_local), the axis
+ * open; these two calls are the device side of the exchange between domains.
+ *
+ * pod_halo_select: the atoms i of pos (device [3][n_atoms]) whose coordinate
+ * along `axis`, wrapped into [0, L) as x - L floor(x / L), lies in [x0, x1), in
+ * ascending index order: idx (device [cap]) receives i, out (device [3][cap])
+ * the position with the axis coordinate replaced by (x + shift) - offset (shift:
+ * a periodic image, -L, 0 or L; offset: the origin of the receiving domain) and
+ * the other two coordinates unchanged, *count (host) the number selected.
+ * Synchronous.  POD_ENEIGH if more than cap atoms are selected (*count holds the
+ * number; nothing beyond cap is written); POD_EINVAL on bad arguments or when
+ * the handle's device is not current. */
+int pod_halo_select(pod_handle* h, const double* pos, int n_atoms, int axis, double L, double x0, double x1,
+                    double shift, double offset, int cap, int* idx, double* out, int* count, void* stream);
+
+/* pod_halo_add: F[d][idx[k]] += G[d][k] for k < n (G device [3][n], idx device
+ * [n] of distinct atom indices in [0, n_atoms), F device [3][n_atoms]): ghost
+ * forces returned by a neighbouring domain added onto the owning atoms.  An index
+ * out of range is skipped and reported (POD_ENEIGH, when POD_OPT_SYNC is on). */
+int pod_halo_add(pod_handle* h, const double* G, const int* idx, int n, double* F, int n_atoms, void* stream);
+
 /* Quadratic POD model (Sec. 4, the extension of Eq. 57a with products of
  * descriptors): E_i = sum_m c_m D_im + sum_m sum_{n >= m} beta_mn D_im D_in.
  * beta: host [M][M] row-major; only the entries with m <= n are read (the
@@ -372,10 +412,12 @@ int pod_set_embedding(pod_handle* h, const double* a, int degree, const double* 
  * pod_energy_forces about 15 x (reps + 1) times); not for use during stream
  * capture.
  *   shape (host int[5], or NULL): neighbour wpb, atom wpb, gather wpb, gather
- *   blocks per SM, and 1 when the atom kernel stages R' in shared memory (FP32
- *   table path; a candidate of the atom-kernel search) instead of re-evaluating
- *   it in the adjoint pass.  ms (host double[3], or NULL): mean times of the neighbour,
- *   atom and gather phases with the chosen shape.
+ *   blocks per SM, and the form of the adjoint pair pass: 0 inside the fused atom
+ *   kernel, re-evaluating R'; 1 the same with R' staged in shared memory (FP32
+ *   table path); 2 as its own kernel after a forward-only atom kernel (FP32 linear
+ *   model; see POD_OPT_ADJOINT) -- all candidates of the atom-phase search.
+ *   ms (host double[3], or NULL): mean times of the neighbour, atom and gather
+ *   phases with the chosen shape.
  * Errors as pod_energy_forces; POD_EINVAL for a batch. */
 int pod_autotune(pod_handle* h, const pod_system* sys, const double* c, int reps, int* shape, double* ms,
                  void* stream);

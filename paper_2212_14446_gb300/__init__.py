@@ -30,6 +30,7 @@ POD_FP64, POD_MIXED = 0, 1
 POD_OPT_SYNC, POD_OPT_PRECISION, POD_OPT_TIMING, POD_OPT_RADIAL, POD_OPT_NEIGHBOR_REUSE = 1, 2, 3, 4, 5
 POD_OPT_DESCRIPTORS = 6
 POD_OPT_GRAM = 7
+POD_OPT_ADJOINT = 8
 ERROR_NAMES = {0: "POD_OK", -1: "POD_EINVAL", -2: "POD_ENOMEM", -3: "POD_ECUDA", -4: "POD_ERANGE",
                -5: "POD_ENONFINITE", -6: "POD_ESINGULAR", -7: "POD_ENEIGH", -8: "POD_EIO"}
 
@@ -56,16 +57,20 @@ class pod_system(C.Structure):
                 ("boxes", C.POINTER(C.c_double)), ("pbcs", C.POINTER(C.c_int)), ("n_local", C.c_int)]
 
 
+_SOLVERS = {"auto": 0, "cholesky": 1, "qr": 2}
+
+
 class pod_fit_opts(C.Structure):
     _fields_ = [("w_E", C.c_double), ("w_F", C.c_double), ("gamma_reg", C.c_double),
-                ("per_atom_energy", C.c_int)]
+                ("per_atom_energy", C.c_int), ("solver", C.c_int)]
 
 
 EXPORTS = ["pod_create", "pod_destroy", "pod_info", "pod_set_option", "pod_status", "pod_timing",
            "pod_neighbors", "pod_descriptors", "pod_energy_forces", "pod_energy_forces_host", "pod_fit",
            "pod_fit_normal", "pod_fit_solve", "pod_fit_residual", "pod_descriptors_static",
            "pod_global_descriptors", "pod_descriptors_jvp", "pod_set_skin", "pod_md_step", "pod_fma_probe", "pod_autotune", "pod_set_quadratic",
-           "pod_set_embedding", "pod_save", "pod_load", "pod_selftest_wait", "pod_last_error"]
+           "pod_set_embedding", "pod_save", "pod_load", "pod_selftest_wait", "pod_halo_select", "pod_halo_add",
+           "pod_last_error"]
 
 _lib = None
 _lock = threading.Lock()
@@ -110,6 +115,9 @@ def lib():
                 "pod_set_embedding": (C.c_int, [H, dp, C.c_int, dp]),
                 "pod_save": (C.c_int, [H, C.c_char_p, dp]),
                 "pod_load": (C.c_int, [C.c_char_p, C.c_int, C.POINTER(H), dp, C.c_int, ip]),
+                "pod_halo_select": (C.c_int, [H, dp, C.c_int, C.c_int, C.c_double, C.c_double, C.c_double,
+                                              C.c_double, C.c_double, C.c_int, ip, dp, ip, vp]),
+                "pod_halo_add": (C.c_int, [H, dp, ip, C.c_int, dp, C.c_int, vp]),
                 "pod_last_error": (C.c_char_p, [H]),
             }
             for name, (res, args) in sig.items():
@@ -219,14 +227,30 @@ def pod_descriptors_static(h, sys, D, stream=None):
     _check(h, lib().pod_descriptors_static(h, C.byref(sys), _dptr(D), _stream(stream)))
 
 
+def pod_halo_select(h, pos, axis, L, x0, x1, shift, offset, cap, idx, out, stream=None):
+    """Atoms of pos (device (3, N)) whose wrapped coordinate along `axis` lies in
+    [x0, x1), ascending: idx (device int32 [cap]) and out (device (3, cap)) the
+    positions with that coordinate moved to x + shift - offset.  Returns the count."""
+    n = C.c_int(0)
+    _check(h, lib().pod_halo_select(h, _dptr(pos), int(pos.shape[1]), int(axis), float(L), float(x0), float(x1),
+                                    float(shift), float(offset), int(cap), _iptr(idx), _dptr(out), C.byref(n),
+                                    _stream(stream)))
+    return n.value
+
+
+def pod_halo_add(h, G, idx, n, F, stream=None):
+    """F[:, idx[k]] += G[:, k] for k < n (device tensors; F (3, N), G (3, n))."""
+    _check(h, lib().pod_halo_add(h, _dptr(G), _iptr(idx), int(n), _dptr(F), int(F.shape[1]), _stream(stream)))
+
+
 def pod_energy_forces(h, sys, c, E, Ei=None, F=None, W=None, stream=None):
     _check(h, lib().pod_energy_forces(h, C.byref(sys), _dptr(c), _dptr(E), _dptr(Ei), _dptr(F), _dptr(W),
                                       _stream(stream)))
 
 
 def pod_autotune(h, sys, c, reps=5, stream=None):
-    """Returns ([neigh wpb, atom wpb, gather wpb, gather blocks per SM, atom R' staging],
-    [ms neigh, atom, gather])."""
+    """Returns ([neigh wpb, atom wpb, gather wpb, gather blocks per SM, adjoint form
+    (0 fused, 1 fused with R' staged, 2 separate kernel)], [ms neigh, atom, gather])."""
     shape = (C.c_int * 5)()
     ms = (C.c_double * 3)()
     _check(h, lib().pod_autotune(h, C.byref(sys), _dptr(c), int(reps), shape, ms, _stream(stream)))
@@ -396,6 +420,10 @@ class POD:
     def set_timing(self, on: bool):
         pod_set_option(self.h, POD_OPT_TIMING, 1 if on else 0)
 
+    def set_adjoint_kernel(self, which: str):
+        """Mixed linear path: "auto" (launch shape / size), "fused" or "separate"."""
+        pod_set_option(self.h, POD_OPT_ADJOINT, {"auto": -1, "fused": 0, "separate": 1}[which])
+
     def timing(self):
         return pod_timing(self.h)
 
@@ -525,16 +553,17 @@ class POD:
         pod_energy_forces(self.h, self.batch_system(x, offs, boxes, pbcs), c, E, Ei, F, None, stream)
         return {"E": E, "Ei": Ei, "F": F.t(), "offs": offs}
 
-    def fit(self, configs, E_ref, F_ref, w_E=100.0, w_F=1.0, gamma=1e-12, per_atom_energy=True):
+    def fit(self, configs, E_ref, F_ref, w_E=100.0, w_F=1.0, gamma=1e-12, per_atom_energy=True, solver="auto"):
         """Ridge least-squares fit (Eq. 63a) on the GPU.  E_ref: (n_cfg,), F_ref: list of
-        (N_c, 3) arrays.  Returns (c, mae_E per atom, mae_F per component)."""
+        (N_c, 3) arrays; solver: "auto" (Cholesky, QR when a pivot is not positive),
+        "cholesky" or "qr".  Returns (c, mae_E per atom, mae_F per component)."""
         import torch
         pos, offs, boxes, pbcs = self.pack_batch(configs)
         x = torch.tensor(pos, dtype=torch.float64, device="cuda")
         Er = torch.tensor(np.asarray(E_ref, dtype=np.float64), device=x.device)
         Fr = torch.tensor(np.ascontiguousarray(np.concatenate([np.asarray(f) for f in F_ref], axis=0).T),
                           dtype=torch.float64, device=x.device)
-        o = pod_fit_opts(float(w_E), float(w_F), float(gamma), 1 if per_atom_energy else 0)
+        o = pod_fit_opts(float(w_E), float(w_F), float(gamma), 1 if per_atom_energy else 0, _SOLVERS[solver])
         c = np.zeros(self.M)
         mE, mF = C.c_double(), C.c_double()
         sysb = self.batch_system(x, offs, boxes, pbcs)
@@ -543,10 +572,10 @@ class POD:
         return c, mE.value, mF.value
 
     def fit_device(self, pos_soa, offs, boxes, pbcs, E_ref, F_ref, w_E=100.0, w_F=1.0, gamma=1e-12,
-                   per_atom_energy=True):
+                   per_atom_energy=True, solver="auto"):
         """pod_fit on a batch already on the device (pos_soa (3, N), E_ref (n_cfg,), F_ref (3, N)
         CUDA float64 tensors; offs/boxes/pbcs host arrays from pack_batch)."""
-        o = pod_fit_opts(float(w_E), float(w_F), float(gamma), 1 if per_atom_energy else 0)
+        o = pod_fit_opts(float(w_E), float(w_F), float(gamma), 1 if per_atom_energy else 0, _SOLVERS[solver])
         c = np.zeros(self.M)
         mE, mF = C.c_double(), C.c_double()
         sysb = self.batch_system(pos_soa, offs, boxes, pbcs)
@@ -563,7 +592,7 @@ class POD:
         Er = torch.tensor(np.asarray(E_ref, dtype=np.float64), device=x.device)
         Fr = torch.tensor(np.ascontiguousarray(np.concatenate([np.asarray(f) for f in F_ref], axis=0).T),
                           dtype=torch.float64, device=x.device)
-        o = pod_fit_opts(float(w_E), float(w_F), float(gamma), 1 if per_atom_energy else 0)
+        o = pod_fit_opts(float(w_E), float(w_F), float(gamma), 1 if per_atom_energy else 0, 0)
         G = np.zeros((self.M, self.M))
         r = np.zeros(self.M)
         sysb = self.batch_system(x, offs, boxes, pbcs)

@@ -22,6 +22,20 @@
 
 namespace fastpod {
 
+// (u, r) of a displacement: r = |d|, u = d / r.  Every kernel forming pair
+// geometry uses this one expression, so they agree bit for bit.
+template <typename T>
+__device__ __forceinline__ Q4<T> pair_unit(T dx, T dy, T dz) {
+  const T r = d_sqrt(dx * dx + dy * dy + dz * dz);
+  const T ir = T(1) / r;
+  Q4<T> q;
+  q.x = dx * ir;
+  q.y = dy * ir;
+  q.z = dz * ir;
+  q.w = r;
+  return q;
+}
+
 template <typename T>
 __device__ __forceinline__ void pair_disp(const AtomArgs<T>& p, int i, int j, int sx, int sy, int sz, T& dx, T& dy,
                                           T& dz);
@@ -58,7 +72,7 @@ __device__ __forceinline__ int chunk_count(int n, int ch) { return min(max(n - c
 template <typename T, int KT, bool TANGENT = false>
 __device__ __forceinline__ void pair_pass(const AtomArgs<T>& p, const AtomLayout& lay, Q4<T>* geo, T* sR, T* sRp,
                                           const int* scnt, int atom0, int A, int K, int ch, int lane,
-                                          Q4<T>* sV = nullptr) {
+                                          Q4<T>* sV = nullptr, int* sj = nullptr) {
   int tot = 0;
   for (int a = 0; a < A; ++a) tot += chunk_count(scnt[a], ch);
   for (int f = lane; f < tot; f += 32) {
@@ -70,19 +84,25 @@ __device__ __forceinline__ void pair_pass(const AtomArgs<T>& p, const AtomLayout
     }
     const int jj = f - base, slot = ch * CH + jj, i = atom0 + a;
     const size_t pidx = (size_t)i * p.cap + slot;
-    const int j = p.nbr_j[pidx];
-    const int code = p.nbr_s[pidx];
-    int sx, sy, sz;
-    shift_unpack(code, sx, sy, sz);
     T dx, dy, dz;
-    pair_disp<T>(p, i, j, sx, sy, sz, dx, dy, dz);
-    const T r = d_sqrt(dx * dx + dy * dy + dz * dz);
-    const T ir = T(1) / r;
-    Q4<T> gq;
-    gq.x = dx * ir;
-    gq.y = dy * ir;
-    gq.z = dz * ir;
-    gq.w = r;
+    int j;
+    if (std::is_same<T, float>::value && p.pd) {
+      // displacement formed by the neighbour search (same arithmetic, same bits)
+      const float4 q = __ldg(p.pd + pidx);
+      dx = (T)q.x;
+      dy = (T)q.y;
+      dz = (T)q.z;
+      j = __float_as_int(q.w);
+    } else {
+      j = p.nbr_j[pidx];
+      const int code = p.nbr_s[pidx];
+      int sx, sy, sz;
+      shift_unpack(code, sx, sy, sz);
+      pair_disp<T>(p, i, j, sx, sy, sz, dx, dy, dz);
+    }
+    if (sj) sj[a * lay.GA + jj] = j;
+    const Q4<T> gq = pair_unit(dx, dy, dz);
+    const T r = gq.w;
     geo[a * lay.GA + jj] = gq;
     T R[KT], Rp[KT];
     if (r > p.rad.r_in && r < p.rmask) {
@@ -118,6 +138,92 @@ __device__ __forceinline__ void pair_pass(const AtomArgs<T>& p, const AtomLayout
   }
 }
 
+// Pair gradient g_ij = sum_{m,x} a_mx dB_mx/dr_ij of one pair (Eq. 24c): u = (unit
+// vector, r), R and R' of the pair, adj = the atom's rows dE/dB_m (K rows of NAP,
+// shared memory), s3m = dE/dS3 per mode for the exclusive three-body set (or
+// NULL).  dA/dr = (grad_u A - (u . grad_u A) u) / r for homogeneous A (Euler).
+// Both the fused atom kernel and the separate adjoint kernel call this, so the
+// two give the same bits.
+template <typename T, int PA, int KT>
+__device__ __forceinline__ Q4<T> pair_gradient(const Q4<T>& u, const T* Rv, const T* Rpv, const T* adj, int K,
+                                               const T* s3m) {
+  constexpr int NA = Mono<PA>::NA;
+  constexpr int NAP = (NA + 3) / 4 * 4;
+  T Am[NAP];
+  T e[NAP];
+  T ps = T(0);
+  if constexpr (std::is_same<T, float>::value) {
+    // paired FP32 multiply-add over the basis components (a_m loaded as float4)
+    float2 A2[NAP / 2], e2[NAP / 2];
+    Mono<PA>::eval2(u.x, u.y, u.z, A2);
+#pragma unroll
+    for (int k = Mono<PA>::NA2; k < NAP / 2; ++k) A2[k] = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int k = 0; k < NAP / 2; ++k) e2[k] = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int mm = 0; mm < KT; ++mm) {
+      if (KT == MAXK && mm >= K) break;
+      const float2 R2 = make_float2(Rv[mm], Rv[mm]);
+      const float4* a4 = reinterpret_cast<const float4*>(adj + mm * NAP);
+      float2 u2 = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int x4 = 0; x4 < NAP / 4; ++x4) {
+        const float4 av = a4[x4];
+        const float2 lo = make_float2(av.x, av.y), hi = make_float2(av.z, av.w);
+        u2 = __ffma2_rn(lo, A2[2 * x4], u2);
+        u2 = __ffma2_rn(hi, A2[2 * x4 + 1], u2);
+        e2[2 * x4] = __ffma2_rn(lo, R2, e2[2 * x4]);
+        e2[2 * x4 + 1] = __ffma2_rn(hi, R2, e2[2 * x4 + 1]);
+      }
+      ps = fma(Rpv[mm], u2.x + u2.y, ps);
+      if (s3m) ps = fma(T(2) * s3m[mm] * Rv[mm], Rpv[mm], ps);  // dS3/dr = 2 R R'
+    }
+#pragma unroll
+    for (int x = 0; x < NAP; ++x) {
+      Am[x] = (x & 1) ? A2[x >> 1].y : A2[x >> 1].x;
+      e[x] = (x & 1) ? e2[x >> 1].y : e2[x >> 1].x;
+    }
+  } else {
+    Mono<PA>::eval(u.x, u.y, u.z, Am);
+#pragma unroll
+    for (int x = NA; x < NAP; ++x) Am[x] = T(0);
+#pragma unroll
+    for (int x = 0; x < NAP; ++x) e[x] = T(0);
+#pragma unroll
+    for (int mm = 0; mm < KT; ++mm) {
+      if (KT == MAXK && mm >= K) break;
+      const T Rm = Rv[mm], Rpm = Rpv[mm];
+      const Q4<T>* a4 = reinterpret_cast<const Q4<T>*>(adj + mm * NAP);
+      T um = T(0);
+#pragma unroll
+      for (int x4 = 0; x4 < NAP / 4; ++x4) {
+        const Q4<T> av = a4[x4];
+        um = fma(av.x, Am[4 * x4 + 0], um);
+        um = fma(av.y, Am[4 * x4 + 1], um);
+        um = fma(av.z, Am[4 * x4 + 2], um);
+        um = fma(av.w, Am[4 * x4 + 3], um);
+        e[4 * x4 + 0] = fma(av.x, Rm, e[4 * x4 + 0]);
+        e[4 * x4 + 1] = fma(av.y, Rm, e[4 * x4 + 1]);
+        e[4 * x4 + 2] = fma(av.z, Rm, e[4 * x4 + 2]);
+        e[4 * x4 + 3] = fma(av.w, Rm, e[4 * x4 + 3]);
+      }
+      ps = fma(Rpm, um, ps);
+      if (s3m) ps = fma(T(2) * s3m[mm] * Rm, Rpm, ps);  // dS3/dr = 2 R R'
+    }
+  }
+  T gx, gy, gz;
+  Mono<PA>::grad(e, Am, gx, gy, gz);
+  // dA/dr = (grad_u A - (u . grad_u A) u) / r for homogeneous A (Euler)
+  const T ug = u.x * gx + u.y * gy + u.z * gz;
+  const T ir = T(1) / u.w;
+  Q4<T> out;
+  out.x = fma(ps, u.x, (gx - ug * u.x) * ir);
+  out.y = fma(ps, u.y, (gy - ug * u.y) * ir);
+  out.z = fma(ps, u.z, (gz - ug * u.z) * ir);
+  out.w = T(0);
+  return out;
+}
+
 // FP32 specialised kernels are held to 128 registers (4 blocks of 4 warps per SM): the
 // paired multiply-add operands otherwise push them past that without a gain.
 template <typename T, int MODE, int KT>
@@ -141,6 +247,8 @@ __global__ void __launch_bounds__(ATOM_MAX_WPB * 32, atom_min_blocks<T, MODE, KT
   T* se = reinterpret_cast<T*>(wb + lay.off_e);
   int* scnt = reinterpret_cast<int*>(wb + lay.off_cnt);
   Q4<T>* sV = reinterpret_cast<Q4<T>*>(wb + lay.off_V);
+  // neighbour index of each staged pair (energy modes with a displacement list)
+  int* sj = (std::is_same<T, float>::value && p.pd && lay.off_J) ? reinterpret_cast<int*>(wb + lay.off_J) : nullptr;
 
   const int K = (KT == MAXK) ? p.K : KT;
   const int A = (KT == MAXK) ? lay.A : 32 / KT;
@@ -239,7 +347,7 @@ __global__ void __launch_bounds__(ATOM_MAX_WPB * 32, atom_min_blocks<T, MODE, KT
 #pragma unroll
   for (int k = 0; k < Mono<PA>::NA2; ++k) B2[k] = make_float2(0.f, 0.f);
   for (int ch = 0; ch < nchunks; ++ch) {
-    pair_pass<T, KT, false>(p, lay, geo, sR, sRp, scnt, atom0, A, K, ch, lane);
+    pair_pass<T, KT, false>(p, lay, geo, sR, sRp, scnt, atom0, A, K, ch, lane, nullptr, sj);
     __syncwarp();
     if (am) {
       const int nc = chunk_count(my_n, ch);
@@ -661,6 +769,18 @@ __global__ void __launch_bounds__(ATOM_MAX_WPB * 32, atom_min_blocks<T, MODE, KT
     se[lane] = s3;
     __syncwarp();
   }
+  if (MODE == 1 && p.adj_out) {
+    // the adjoint pair pass runs as its own kernel: hand it dE_i/dB_m (and dE_i/dS3)
+    if (am) {
+      const int i = atom0 + a_loc;
+      const Q4<T>* asrc = reinterpret_cast<const Q4<T>*>(sadj + a_loc * lay.AS + m * NAP);
+      Q4<T>* adst = reinterpret_cast<Q4<T>*>(p.adj_out + ((size_t)i * K + m) * NAP);
+#pragma unroll
+      for (int x4 = 0; x4 < NAP / 4; ++x4) adst[x4] = asrc[x4];
+      if (p.excl3) p.s3_out[(size_t)i * K + m] = s3;
+    }
+    return;
+  }
 
   // ---------------- adjoint pair pass: g_ij = sum_{m,x} a_mx dB_mx/dr_ij  (Eq. 24c)
   T wv[9];
@@ -669,7 +789,7 @@ __global__ void __launch_bounds__(ATOM_MAX_WPB * 32, atom_min_blocks<T, MODE, KT
   for (int ch = 0; ch < nchunks; ++ch) {
     if (nchunks > 1) {
       __syncwarp();
-      pair_pass<T, KT, false>(p, lay, geo, sR, sRp, scnt, atom0, A, K, ch, lane);
+      pair_pass<T, KT, false>(p, lay, geo, sR, sRp, scnt, atom0, A, K, ch, lane, nullptr, sj);
       __syncwarp();
     }
     int tot = 0;
@@ -702,83 +822,12 @@ __global__ void __launch_bounds__(ATOM_MAX_WPB * 32, atom_min_blocks<T, MODE, KT
           Rpv[k] = Rprow[k];
         }
       }
-      T Am[NAP];
-      T e[NAP];
-      T ps = T(0);
-      const T* adj = sadj + a * lay.AS;
-      if constexpr (std::is_same<T, float>::value) {
-        // paired FP32 multiply-add over the basis components (a_m loaded as float4)
-        float2 A2[NAP / 2], e2[NAP / 2];
-        Mono<PA>::eval2(u.x, u.y, u.z, A2);
-#pragma unroll
-        for (int k = Mono<PA>::NA2; k < NAP / 2; ++k) A2[k] = make_float2(0.f, 0.f);
-#pragma unroll
-        for (int k = 0; k < NAP / 2; ++k) e2[k] = make_float2(0.f, 0.f);
-#pragma unroll
-        for (int mm = 0; mm < KT; ++mm) {
-          if (KT == MAXK && mm >= K) break;
-          const float2 R2 = make_float2(Rv[mm], Rv[mm]);
-          const float4* a4 = reinterpret_cast<const float4*>(adj + mm * NAP);
-          float2 u2 = make_float2(0.f, 0.f);
-#pragma unroll
-          for (int x4 = 0; x4 < NAP / 4; ++x4) {
-            const float4 av = a4[x4];
-            const float2 lo = make_float2(av.x, av.y), hi = make_float2(av.z, av.w);
-            u2 = __ffma2_rn(lo, A2[2 * x4], u2);
-            u2 = __ffma2_rn(hi, A2[2 * x4 + 1], u2);
-            e2[2 * x4] = __ffma2_rn(lo, R2, e2[2 * x4]);
-            e2[2 * x4 + 1] = __ffma2_rn(hi, R2, e2[2 * x4 + 1]);
-          }
-          ps = fma(Rpv[mm], u2.x + u2.y, ps);
-          if (p.excl3) ps = fma(T(2) * se[a * K + mm] * Rv[mm], Rpv[mm], ps);  // dS3/dr = 2 R R'
-        }
-#pragma unroll
-        for (int x = 0; x < NAP; ++x) {
-          Am[x] = (x & 1) ? A2[x >> 1].y : A2[x >> 1].x;
-          e[x] = (x & 1) ? e2[x >> 1].y : e2[x >> 1].x;
-        }
-      } else {
-        Mono<PA>::eval(u.x, u.y, u.z, Am);
-#pragma unroll
-        for (int x = NA; x < NAP; ++x) Am[x] = T(0);
-#pragma unroll
-        for (int x = 0; x < NAP; ++x) e[x] = T(0);
-#pragma unroll
-        for (int mm = 0; mm < KT; ++mm) {
-          if (KT == MAXK && mm >= K) break;
-          const T Rm = Rv[mm], Rpm = Rpv[mm];
-          const Q4<T>* a4 = reinterpret_cast<const Q4<T>*>(adj + mm * NAP);
-          T um = T(0);
-#pragma unroll
-          for (int x4 = 0; x4 < NAP / 4; ++x4) {
-            const Q4<T> av = a4[x4];
-            um = fma(av.x, Am[4 * x4 + 0], um);
-            um = fma(av.y, Am[4 * x4 + 1], um);
-            um = fma(av.z, Am[4 * x4 + 2], um);
-            um = fma(av.w, Am[4 * x4 + 3], um);
-            e[4 * x4 + 0] = fma(av.x, Rm, e[4 * x4 + 0]);
-            e[4 * x4 + 1] = fma(av.y, Rm, e[4 * x4 + 1]);
-            e[4 * x4 + 2] = fma(av.z, Rm, e[4 * x4 + 2]);
-            e[4 * x4 + 3] = fma(av.w, Rm, e[4 * x4 + 3]);
-          }
-          ps = fma(Rpm, um, ps);
-          if (p.excl3) ps = fma(T(2) * se[a * K + mm] * Rm, Rpm, ps);  // dS3/dr = 2 R R'
-        }
-      }
-      T gx, gy, gz;
-      Mono<PA>::grad(e, Am, gx, gy, gz);
-      // dA/dr = (grad_u A - (u . grad_u A) u) / r for homogeneous A (Euler)
-      const T ug = u.x * gx + u.y * gy + u.z * gz;
-      const T ir = T(1) / u.w;
-      Q4<T> out;
-      out.x = fma(ps, u.x, (gx - ug * u.x) * ir);
-      out.y = fma(ps, u.y, (gy - ug * u.y) * ir);
-      out.z = fma(ps, u.z, (gz - ug * u.z) * ir);
-      out.w = T(0);
+      const Q4<T> out =
+          pair_gradient<T, PA, KT>(u, Rv, Rpv, sadj + a * lay.AS, K, p.excl3 ? se + a * K : static_cast<T*>(nullptr));
       const size_t pidx = (size_t)i * p.cap + slot;
       if constexpr (std::is_same<T, float>::value) {
         // F_i += g_ij, F_j -= g_ij as fixed-point integers (order-independent sums)
-        const int j = p.nbr_j[pidx];
+        const int j = sj ? sj[a * lay.GA + jj] : p.nbr_j[pidx];
         if (!(fabsf(out.x) < FIX_GMAX && fabsf(out.y) < FIX_GMAX && fabsf(out.z) < FIX_GMAX)) {
           atomicOr(p.status, isfinite(out.x) && isfinite(out.y) && isfinite(out.z) ? ST_OVERFLOW : ST_NONFINITE);
         } else {
@@ -832,7 +881,7 @@ __global__ void __launch_bounds__(ATOM_MAX_WPB * 32, atom_min_blocks<T, MODE, KT
 
 // ------------------------------------------------------------------ layout
 template <typename T>
-AtomLayout make_layout(int K, int PA, bool table, bool tangent = false, int quadM = 0) {
+AtomLayout make_layout(int K, int PA, bool table, bool tangent = false, int quadM = 0, bool pair_j = false) {
   if (tangent) table = false;  // the tangent pass reads R' from shared memory
   AtomLayout L{};
   const int NA = (PA + 1) * (PA + 2) * (PA + 3) / 6;
@@ -863,6 +912,11 @@ AtomLayout make_layout(int K, int PA, bool table, bool tangent = false, int quad
   L.off_D = off;  // quadratic model: descriptors of the warp's atoms, then dE/dD
   L.MS = quadM > 0 ? (quadM + 3) / 4 * 4 : 0;  // rows of 16-byte multiples (float4 reads)
   off = al(off + 2 * sizeof(T) * (size_t)L.A * L.MS, 32);
+  L.off_J = 0;
+  if (pair_j) {  // neighbour index per staged pair (displacement lists)
+    L.off_J = off;
+    off = al(off + sizeof(int) * (size_t)L.A * L.GA, 32);
+  }
   L.warp_bytes = off;
   return L;
 }
@@ -913,7 +967,7 @@ static cudaError_t dispatch_generic(const AtomArgs<T>& p, const AtomLayout& lay,
 template <typename T>
 cudaError_t launch_atom_emb_t(const AtomArgs<T>& p, int PA, bool has4, cudaStream_t st) {
   if (!p.emb_a || !p.emb_alpha || p.emb_deg < 1) return cudaErrorInvalidValue;
-  const AtomLayout lay = make_layout<T>(p.K, PA, p.rad.tab != nullptr && !p.keep_rp, false, 0);
+  const AtomLayout lay = make_layout<T>(p.K, PA, p.rad.tab != nullptr && !p.keep_rp, false, 0, p.pd != nullptr);
   if (p.K == 6 && PA == 4 && has4) return launch_one<T, 4, true, 5, 6>(p, lay, st);
   if (p.K == 3 && PA == 3 && !has4) return launch_one<T, 3, false, 5, 3>(p, lay, st);
   return dispatch_generic<T, 5>(p, lay, PA, has4, st);
@@ -923,7 +977,8 @@ cudaError_t launch_atom_emb_t(const AtomArgs<T>& p, int PA, bool has4, cudaStrea
 // (K = 3, P = 3, no 4-body; K = 6, P = 4, 4-body), generic K <= 16 otherwise.
 template <typename T>
 cudaError_t launch_atom_t(int mode, const AtomArgs<T>& p, int PA, bool has4, cudaStream_t st) {
-  const AtomLayout lay = make_layout<T>(p.K, PA, p.rad.tab != nullptr && !p.keep_rp, mode == 2, mode == 4 ? p.M : 0);
+  const AtomLayout lay = make_layout<T>(p.K, PA, p.rad.tab != nullptr && !p.keep_rp, mode == 2, mode == 4 ? p.M : 0,
+                                        p.pd != nullptr);
   const bool spec6 = (p.K == 6 && PA == 4 && has4);
   const bool spec3 = (p.K == 3 && PA == 3 && !has4);
   if (mode == 2) {

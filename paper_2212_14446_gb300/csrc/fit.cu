@@ -529,6 +529,51 @@ int pod_handle::fit_solve_dev() {
   return POD_OK;
 }
 
+// Stage 3, QR form: the least-squares problem min || [A; sqrt(gamma) I] c - [b; 0] ||
+// solved from a tall-skinny Householder QR of the weighted design matrix (qr.cu)
+// into the device c; needs the A and b of the last fit_build.  The condition
+// number is that of A, not of A^T A, so this solves systems whose normal
+// equations lose positive definiteness in rounding.
+int pod_handle::fit_solve_qr(double gamma) {
+  const long long R = fit_R;
+  if (R < 1 || !fitA.p || !fitb.p) return fail(POD_EINVAL, "the QR solve needs a design matrix");
+  if (M > 256) return fail(POD_EINVAL, "the QR solve supports at most 256 descriptors");
+  // panel rows: the factor's M rows plus up to M new rows, within 200 KB of shared memory
+  int cmax = std::min(M, (int)((200 * 1024) / (sizeof(double) * (M + 1))) - M);
+  if (cmax < 8) return fail(POD_EINVAL, "too many descriptors for the QR panel");
+  const int nb0 = (int)std::max<long long>(1, std::min<long long>(2 * 152, (R + 511) / 512));
+  const long long rows_per = (R + nb0 - 1) / nb0;
+  const size_t fbytes = sizeof(double) * (size_t)(M + 1) * M;
+  const int g = 4;
+  const int nb1 = (nb0 + g - 1) / g;
+  int rc_;
+  if ((rc_ = ensure(qrw, fbytes * (size_t)(nb0 + nb1), "QR factors"))) return rc_;
+  double* buf0 = (double*)qrw.p;
+  double* buf1 = buf0 + (size_t)nb0 * (M + 1) * M;
+  double* dG = (double*)fitwork.p + (size_t)M * M;
+  double* dc = dG + (size_t)M * M + M;
+  int* dinfo = (int*)(dc + M + 2 * 1024 + 8);
+  cudaStream_t st = nullptr;
+  cudaError_t e = launch_tsqr_rows(M, R, (const double*)fitA.p, (const double*)fitb.p, nb0, rows_per, cmax, buf0, st);
+  if (e != cudaSuccess) return cuda_fail(e, "QR row stage");
+  int n = nb0;
+  double* src = buf0;
+  double* dst = buf1;
+  while (n > g) {  // merge g factors per block until one block can take the rest
+    e = launch_tsqr_merge(M, n, g, src, cmax, 0.0, dst, nullptr, nullptr, st);
+    if (e != cudaSuccess) return cuda_fail(e, "QR merge stage");
+    n = (n + g - 1) / g;
+    std::swap(src, dst);
+  }
+  e = launch_tsqr_merge(M, n, n, src, cmax, std::sqrt(gamma), nullptr, dc, dinfo, st);
+  if (e != cudaSuccess) return cuda_fail(e, "QR final stage");
+  int info = 0;
+  e = cudaMemcpy(&info, dinfo, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(e, "QR status");
+  if (info) return fail(POD_ESINGULAR, "the design matrix is rank deficient (zero pivot %d in its QR factor)", info - 1);
+  return POD_OK;
+}
+
 // Stage 4: sums of |A c - b| over the energy rows and the force rows (unweighted back by w).
 int pod_handle::fit_residual_dev(double* sumE, double* sumF) {
   double* dc = (double*)fitwork.p + 2 * (size_t)M * M + M;
@@ -556,11 +601,21 @@ int pod_handle::fit(const pod_system* bsys, const double* E_ref, const double* F
   if (!c_out) return fail(POD_EINVAL, "c_out is required");
   pod_fit_opts o{100.0, 1.0, 1e-12, 1};
   if (opts) o = *opts;
+  if (o.solver < 0 || o.solver > 2) return fail(POD_EINVAL, "solver must be 0 (Cholesky, QR fallback), 1 or 2");
   int rc_;
   if ((rc_ = fit_build(bsys, E_ref, F_ref, o))) return rc_;
-  if ((rc_ = fit_gram(o.gamma_reg))) return rc_;
+  if (o.solver != 2 && (rc_ = fit_gram(o.gamma_reg))) return rc_;
   if ((rc_ = mark(3, nullptr))) return rc_;
-  if ((rc_ = fit_solve_dev())) return rc_;
+  if (o.solver == 2) {
+    rc_ = fit_solve_qr(o.gamma_reg);
+  } else {
+    rc_ = fit_solve_dev();
+    if (rc_ == POD_ESINGULAR && o.solver == 0) {  // the normal equations lost definiteness: QR of A
+      err.clear();
+      rc_ = fit_solve_qr(o.gamma_reg);
+    }
+  }
+  if (rc_) return rc_;
   if ((rc_ = mark(4, nullptr))) return rc_;
   if ((rc_ = timing_collect())) return rc_;
   double se = 0, sf = 0;
@@ -588,7 +643,7 @@ int pod_fit_normal(pod_handle* h, const pod_system* batch, const double* E_ref, 
   NvtxRange nvtx_("pod_fit_normal");
   if (!h) return POD_EINVAL;
   if (!G_out || !r_out) return h->fail(POD_EINVAL, "G_out and r_out are required");
-  pod_fit_opts o{100.0, 1.0, 1e-12, 1};
+  pod_fit_opts o{100.0, 1.0, 1e-12, 1, 0};
   if (opts) o = *opts;
   int rc;
   if ((rc = h->fit_build(batch, E_ref, F_ref, o))) return rc;

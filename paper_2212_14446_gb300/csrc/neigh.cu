@@ -260,37 +260,44 @@ __global__ void __launch_bounds__(NEIGH_MAX_WPB * 32)
   neigh_finish_row(N, cg, wpos, rc2, cap, keycap, i, lane, nhit, keys, nbr_count, nbr_j, nbr_s, status);
 }
 
-// Block per cell, for a search depth of one cell in every direction: the
-// candidates of the 27 neighbouring (cell, image) pairs are staged once in
-// shared memory as image-shifted FP32 positions with their shift codes (one
-// coalesced copy per neighbouring cell, shared by all of the cell's atoms), then
-// each warp takes one of the cell's atoms and tests every candidate with lanes
-// over candidates (full lanes, no per-cell imbalance).  The row is finished as
-// in the warp-per-atom kernel (FP64 band decision, sort, sentinel padding), so
-// the list is the same bit for bit.  Atoms that did not fit in their cell are
-// given an empty row by the bin kernel (and the call is retried).
+// Block per cell, for a search depth of one cell in every direction (image
+// shifts in {-1, 0, 1}): the candidates of the 27 neighbouring (cell, image)
+// pairs are staged once in shared memory as image-shifted FP32 positions with
+// their image id (one coalesced copy per neighbouring cell, shared by all of the
+// cell's atoms), then each warp takes one of the cell's atoms and tests every
+// candidate with lanes over candidates.  Keys are 32-bit, (j << 5) | image id
+// with id = 9 (s_x + 1) + 3 (s_y + 1) + (s_z + 1), so their order is the list
+// order (j, s_x, s_y, s_z); bit 31 marks a band candidate until the exact FP64
+// decision (R6) drops or keeps it.  The row is written as (j, packed shift),
+// padded with a sentinel up to cap when the reverse-slot search will read it
+// (pad), and, when pd is given, as the pair displacement x_j + s L - x_i in FP32
+// from the double-float split of both positions (the arithmetic of the atom
+// kernels, so the same bits) with j in the fourth word.  Requires N < 2^26.
+// Atoms that did not fit in their cell are given an empty row by the bin kernel
+// (and the call is retried).
+constexpr unsigned KEY_BAND = 0x80000000u;
+
 __global__ void __launch_bounds__(NEIGH_MAX_WPB * 32)
-    neigh_cell_kernel(int N, CellGrid cg, const double* __restrict__ wpos, const int* __restrict__ cell_count,
+    neigh_cell_kernel(int N, CellGrid cg, const double* __restrict__ wpos, const float4* __restrict__ phi,
+                      const float4* __restrict__ plo, const int* __restrict__ cell_count,
                       const float4* __restrict__ cell_pos, double rc2, float rc2_lo, float rc2_hi, int cap,
-                      int keycap, int* __restrict__ nbr_count, int* __restrict__ nbr_j, int* __restrict__ nbr_s,
-                      int* __restrict__ status) {
+                      int keycap, int pad, int* __restrict__ nbr_count, int* __restrict__ nbr_j,
+                      int* __restrict__ nbr_s, float4* __restrict__ pd, int* __restrict__ status) {
   extern __shared__ __align__(16) unsigned char csm[];
-  __shared__ int soff[28], scell[27], scode[27];
+  __shared__ int soff[28], scell[27];
   __shared__ float spx[27], spy[27], spz[27];
   const int ccap = 27 * cg.cap;
   float4* cand = reinterpret_cast<float4*>(csm);
-  int* ccode = reinterpret_cast<int*>(cand + ccap);
-  unsigned long long* kbuf =
-      reinterpret_cast<unsigned long long*>(csm + ((sizeof(float4) + sizeof(int)) * (size_t)ccap + 15) / 16 * 16);
+  unsigned char* cid = reinterpret_cast<unsigned char*>(cand + ccap);
+  unsigned* kbuf = reinterpret_cast<unsigned*>(csm + (sizeof(float4) * (size_t)ccap + (size_t)ccap + 15) / 16 * 16);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   const int cell = blockIdx.x;
-  const int zero = shift_pack(0, 0, 0);
   if (warp == 0) {
     const int ci[3] = {cell % cg.nc[0], (cell / cg.nc[0]) % cg.nc[1], cell / (cg.nc[0] * cg.nc[1])};
-    int cnt = 0, tcell = 0, code = zero;
+    int cnt = 0, tcell = 0;
     float px = 0.f, py = 0.f, pz = 0.f;
     if (lane < 27) {
-      const int oc[3] = {lane % 3 - 1, (lane / 3) % 3 - 1, lane / 9 - 1};
+      const int oc[3] = {lane / 9 - 1, (lane / 3) % 3 - 1, lane % 3 - 1};  // stencil entry = image-id order
       int tc[3], sh[3];
       bool ok = true;
 #pragma unroll
@@ -309,11 +316,18 @@ __global__ void __launch_bounds__(NEIGH_MAX_WPB * 32)
       if (ok) {
         tcell = (tc[2] * cg.nc[1] + tc[1]) * cg.nc[0] + tc[0];
         cnt = min(cell_count[tcell], cg.cap);
-        code = shift_pack(sh[0], sh[1], sh[2]);
         px = (float)sh[0] * cg.Lf[0];
         py = (float)sh[1] * cg.Lf[1];
         pz = (float)sh[2] * cg.Lf[2];
+        // image id of this entry (its shift, not its cell offset)
+        scell[lane] = tcell;
       }
+      spx[lane] = px;
+      spy[lane] = py;
+      spz[lane] = pz;
+      if (!ok) scell[lane] = 0;
+      // the shift of the entry decides the key; keep it beside the offsets
+      soff[lane] = (sh[0] + 1) * 9 + (sh[1] + 1) * 3 + (sh[2] + 1);
     }
     int x = cnt;  // inclusive prefix sum over the stencil entries
 #pragma unroll
@@ -321,21 +335,16 @@ __global__ void __launch_bounds__(NEIGH_MAX_WPB * 32)
       const int y = __shfl_up_sync(0xffffffffu, x, o);
       if (lane >= o) x += y;
     }
+    const int sid = lane < 27 ? soff[lane] : 0;
+    __syncwarp();
     if (lane < 27) {
       soff[lane] = x - cnt;
-      scell[lane] = tcell;
-      scode[lane] = code;
-      spx[lane] = px;
-      spy[lane] = py;
-      spz[lane] = pz;
+      kbuf[lane] = (unsigned)sid;  // temporary: image id per stencil entry (the key buffers are unused yet)
     }
     if (lane == 26) soff[27] = x;
   }
   __syncthreads();
   const int ncand = soff[27];
-  // copy the candidates with all threads, two per thread per round (both loads
-  // in flight before either is stored); candidate f belongs to the stencil entry
-  // e with soff[e] <= f < soff[e + 1]
   auto entry_of = [&](int f) {
     int lo = 0, hi = 27;  // soff[lo] <= f < soff[hi]
     while (hi - lo > 1) {
@@ -347,6 +356,8 @@ __global__ void __launch_bounds__(NEIGH_MAX_WPB * 32)
     }
     return lo;
   };
+  // copy the candidates with all threads, two per thread per round (both loads
+  // in flight before either is stored)
   for (int f0 = threadIdx.x; f0 < ncand; f0 += 2 * blockDim.x) {
     const int f1 = f0 + blockDim.x;
     const int e0 = entry_of(f0), e1 = f1 < ncand ? entry_of(f1) : 0;
@@ -354,40 +365,44 @@ __global__ void __launch_bounds__(NEIGH_MAX_WPB * 32)
     float4 q1 = make_float4(0.f, 0.f, 0.f, 0.f);
     if (f1 < ncand) q1 = cell_pos[(size_t)scell[e1] * cg.cap + (f1 - soff[e1])];
     cand[f0] = make_float4(q0.x + spx[e0], q0.y + spy[e0], q0.z + spz[e0], q0.w);
-    ccode[f0] = scode[e0];
+    cid[f0] = (unsigned char)kbuf[e0];
     if (f1 < ncand) {
       cand[f1] = make_float4(q1.x + spx[e1], q1.y + spy[e1], q1.z + spz[e1], q1.w);
-      ccode[f1] = scode[e1];
+      cid[f1] = (unsigned char)kbuf[e1];
     }
   }
   __syncthreads();
-  // the cell's own atoms are the centre stencil entry (offset 0, image 0)
+  // the cell's own atoms are the centre stencil entry (offset 0, image 0: id 13)
   const int own0 = soff[13], own_n = soff[14] - soff[13];
-  unsigned long long* keys = kbuf + (size_t)warp * keycap;
+  unsigned* keys = kbuf + (size_t)warp * keycap;
+  const unsigned below = (1u << lane) - 1u;
+  float Ll[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) Ll[d] = __double2float_rn(cg.L[d] - (double)cg.Lf[d]);
   for (int k = warp; k < own_n; k += nwarps) {
     const float4 qi = cand[own0 + k];
     const int i = __float_as_int(qi.w);
     int nhit = 0;
+    unsigned anyband = 0;
     // candidate f: (hit, key) of the FP32 test (band keys marked for the FP64 decision)
-    auto test = [&](int f, unsigned long long& key) {
+    auto test = [&](int f, unsigned& key) {
       bool hit = false;
       key = 0;
       if (f < ncand) {
         const float4 q = cand[f];
         const int j = __float_as_int(q.w);
-        const int code = ccode[f];
-        if (!(j == i && code == zero)) {
+        const int id = cid[f];
+        if (!(j == i && id == 13)) {
           const float dx = q.x - qi.x, dy = q.y - qi.y, dz = q.z - qi.z;
           const float r2f = dx * dx + dy * dy + dz * dz;
           hit = r2f < rc2_hi;
-          key = ((unsigned long long)j << 24) | (unsigned long long)code | (r2f < rc2_lo ? 0ull : BAND_MARK);
+          key = ((unsigned)j << 5) | (unsigned)id | (r2f < rc2_lo ? 0u : KEY_BAND);
         }
       }
       return hit;
     };
-    const unsigned below = (1u << lane) - 1u;
     for (int f0 = 0; f0 < ncand; f0 += 64) {  // two rounds of 32 candidates per iteration
-      unsigned long long key0, key1;
+      unsigned key0, key1;
       const bool hit0 = test(f0 + lane, key0);
       const bool hit1 = test(f0 + 32 + lane, key1);
       const unsigned m0 = __ballot_sync(0xffffffffu, hit0);
@@ -395,14 +410,107 @@ __global__ void __launch_bounds__(NEIGH_MAX_WPB * 32)
       if (hit0) {
         const int pos = nhit + __popc(m0 & below);
         if (pos < keycap) keys[pos] = key0;
+        anyband |= key0 & KEY_BAND;
       }
       if (hit1) {
         const int pos = nhit + __popc(m0) + __popc(m1 & below);
         if (pos < keycap) keys[pos] = key1;
+        anyband |= key1 & KEY_BAND;
       }
       nhit += __popc(m0) + __popc(m1);
     }
-    neigh_finish_row(N, cg, wpos, rc2, cap, keycap, i, lane, nhit, keys, nbr_count, nbr_j, nbr_s, status);
+    __syncwarp();
+    const int n = min(nhit, keycap);
+    if (__any_sync(0xffffffffu, anyband != 0)) {
+      // decide the band candidates exactly in FP64 (R6): drop the misses
+      const double xi0 = wpos[i], xi1 = wpos[(size_t)N + i], xi2 = wpos[(size_t)2 * N + i];
+      int dropped = 0;
+      for (int t = lane; t < n; t += 32) {
+        unsigned key = keys[t];
+        if (key & KEY_BAND) {
+          key &= ~KEY_BAND;
+          const int j = (int)(key >> 5), id = (int)(key & 31u);
+          const int sx = id / 9 - 1, sy = (id / 3) % 3 - 1, sz = id % 3 - 1;
+          const double ddx = disp_fp64(xi0, wpos[j], sx, cg.L[0]);
+          const double ddy = disp_fp64(xi1, wpos[(size_t)N + j], sy, cg.L[1]);
+          const double ddz = disp_fp64(xi2, wpos[(size_t)2 * N + j], sz, cg.L[2]);
+          const double r2 = __dadd_rn(__dadd_rn(__dmul_rn(ddx, ddx), __dmul_rn(ddy, ddy)), __dmul_rn(ddz, ddz));
+          const bool drop = !(r2 < rc2);
+          keys[t] = drop ? 0xffffffffu : key;
+          dropped += drop ? 1 : 0;
+        }
+      }
+#pragma unroll
+      for (int d = 16; d > 0; d >>= 1) dropped += __shfl_xor_sync(0xffffffffu, dropped, d);
+      // an overflowed key buffer lost candidates: keep the preliminary count (> cap)
+      // so the call reports it and retries with a larger capacity
+      if (nhit <= keycap) nhit -= dropped;
+      __syncwarp();
+    }
+    if (n <= 32) {
+      // bitonic sort of one key per lane in registers (dropped keys sort last)
+      unsigned v = lane < n ? keys[lane] : 0xffffffffu;
+#pragma unroll
+      for (int kk = 2; kk <= 32; kk <<= 1)
+#pragma unroll
+        for (int jj = kk >> 1; jj > 0; jj >>= 1) {
+          const unsigned w = __shfl_xor_sync(0xffffffffu, v, jj);
+          const bool up = (lane & kk) == 0;
+          const bool lower = (lane & jj) == 0;
+          v = (lower == up) ? min(v, w) : max(v, w);
+        }
+      if (lane < n) keys[lane] = v;
+      __syncwarp();
+    } else {
+      int np = 1;
+      while (np < n) np <<= 1;
+      for (int t = n + lane; t < np; t += 32) keys[t] = 0xffffffffu;
+      __syncwarp();
+      for (int kk = 2; kk <= np; kk <<= 1)
+        for (int jj = kk >> 1; jj > 0; jj >>= 1) {
+          for (int t = lane; t < np; t += 32) {
+            const int u = t ^ jj;
+            if (u > t) {
+              const unsigned a = keys[t], b = keys[u];
+              const bool up = (t & kk) == 0;
+              if ((a > b) == up) { keys[t] = b; keys[u] = a; }
+            }
+          }
+          __syncwarp();
+        }
+    }
+    // the nhit valid keys lead the sorted array (when nothing overflowed)
+    const int nw = min(min(n, nhit), cap);
+    float4 hi_i = make_float4(0.f, 0.f, 0.f, 0.f), lo_i = hi_i;
+    if (pd) {
+      hi_i = phi[i];
+      lo_i = plo[i];
+    }
+    const int tend = pad ? cap : nw;
+    for (int t = lane; t < tend; t += 32) {
+      if (t < nw) {
+        const unsigned key = keys[t];
+        const int j = (int)(key >> 5), id = (int)(key & 31u);
+        const int sx = id / 9 - 1, sy = (id / 3) % 3 - 1, sz = id % 3 - 1;
+        if (!pd || pad) {  // with displacement rows only (and no padding) the index rows are not read
+          nbr_j[(size_t)i * cap + t] = j;
+          nbr_s[(size_t)i * cap + t] = shift_pack(sx, sy, sz);
+        }
+        if (pd) {
+          const float4 hj = phi[j], lj = plo[j];
+          const float dx = disp_f32(hi_i.x, lo_i.x, hj.x, lj.x, sx, cg.Lf[0], Ll[0]);
+          const float dy = disp_f32(hi_i.y, lo_i.y, hj.y, lj.y, sy, cg.Lf[1], Ll[1]);
+          const float dz = disp_f32(hi_i.z, lo_i.z, hj.z, lj.z, sz, cg.Lf[2], Ll[2]);
+          pd[(size_t)i * cap + t] = make_float4(dx, dy, dz, __int_as_float(j));
+        }
+      } else {
+        nbr_j[(size_t)i * cap + t] = 0x7fffffff;  // sentinel: rows stay sorted to cap
+      }
+    }
+    if (lane == 0) {
+      nbr_count[i] = nhit;
+      if (nhit > cap) atomicOr(status, ST_NEIGH);
+    }
     __syncwarp();
   }
 }
@@ -522,7 +630,9 @@ static size_t neigh_smem_bytes(int keycap, int wpb) { return (size_t)wpb * keyca
 
 cudaError_t launch_neigh(int N, const CellGrid& cg, const double* wpos, const float4* phi, const float4* plo,
                          const int* cell_count, const float4* cell_pos, double rcut, int cap, int* nbr_count,
-                         int* nbr_j, int* nbr_s, int* status, cudaStream_t st, int wpb) {
+                         int* nbr_j, int* nbr_s, int* status, cudaStream_t st, int wpb, float4* pd, bool pad,
+                         bool* wrote_pd) {
+  if (wrote_pd) *wrote_pd = false;
   if (wpb < 1 || wpb > NEIGH_MAX_WPB) return cudaErrorInvalidValue;
   const double rc2 = rcut * rcut;
   // Error of the FP32 prefilter: each displacement component is formed from
@@ -536,19 +646,25 @@ cudaError_t launch_neigh(int N, const CellGrid& cg, const double* wpos, const fl
   const double band = fmax(4.0 * err_r2, 1e-6 * rc2);
   const float rc2_lo = (float)(rc2 - band);
   const float rc2_hi = (float)(rc2 + band);
+  const bool s1 = cg.S[0] == 1 && cg.S[1] == 1 && cg.S[2] == 1;
+  // block per cell when there are enough cells to fill the GPU (two per SM)
+  if (s1 && cg.ncells >= 2 * 152 && N < (1 << 26)) {
+    int keycap = 32;
+    while (keycap < cap) keycap <<= 1;
+    const size_t cell_smem = (sizeof(float4) * 27 * (size_t)cg.cap + 27 * (size_t)cg.cap + 15) / 16 * 16 +
+                             (size_t)wpb * keycap * sizeof(unsigned);
+    if (cell_smem <= 96 * 1024) {
+      static size_t cgranted[64] = {};
+      if (cudaError_t e = grant_smem((const void*)neigh_cell_kernel, cell_smem, cgranted)) return e;
+      neigh_cell_kernel<<<cg.ncells, wpb * 32, cell_smem, st>>>(N, cg, wpos, phi, plo, cell_count, cell_pos, rc2,
+                                                                rc2_lo, rc2_hi, cap, keycap, pad ? 1 : 0, nbr_count,
+                                                                nbr_j, nbr_s, pd, status);
+      if (wrote_pd) *wrote_pd = pd != nullptr;
+      return cudaGetLastError();
+    }
+  }
   int keycap = 32;
   while (keycap < cap) keycap <<= 1;
-  const bool s1 = cg.S[0] == 1 && cg.S[1] == 1 && cg.S[2] == 1;
-  const size_t cell_smem = ((sizeof(float4) + sizeof(int)) * 27 * (size_t)cg.cap + 15) / 16 * 16 +
-                           (size_t)wpb * keycap * sizeof(unsigned long long);
-  // block per cell when there are enough cells to fill the GPU (two per SM)
-  if (s1 && cg.ncells >= 2 * 152 && cell_smem <= 96 * 1024) {
-    static size_t cgranted[64] = {};
-    if (cudaError_t e = grant_smem((const void*)neigh_cell_kernel, cell_smem, cgranted)) return e;
-    neigh_cell_kernel<<<cg.ncells, wpb * 32, cell_smem, st>>>(N, cg, wpos, cell_count, cell_pos, rc2, rc2_lo,
-                                                              rc2_hi, cap, keycap, nbr_count, nbr_j, nbr_s, status);
-    return cudaGetLastError();
-  }
   const size_t smem = neigh_smem_bytes(keycap, wpb);
   static size_t granted[64] = {};
   if (cudaError_t e = grant_smem((const void*)neigh_kernel, smem, granted)) return e;

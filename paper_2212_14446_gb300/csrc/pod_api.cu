@@ -304,19 +304,24 @@ int pod_handle::autotune(const pod_system* sys, const double* c, int reps, cudaS
   static const int gather_c[][2] = {{16, 3}, {16, 2}, {8, 6}, {8, 4}, {4, 12}};
   double best_atom = 1e30, best_neigh = 1e30, best_gather = 1e30;
   LaunchShape win = cur;
-  for (int a : atom_c)
-    for (int rp = 0; rp < 2 && !rc_; ++rp) {
-      if (rp && (precision != POD_MIXED || radial_mode != 0)) break;  // R' staging: table path only
-      LaunchShape s = win;
-      s.atom_wpb = a;
-      s.atom_rp = rp;
-      if ((rc_ = measure(s, t))) break;
-      if (t[1] < best_atom) {
-        best_atom = t[1];
-        win.atom_wpb = a;
-        win.atom_rp = rp;
+  // the separate adjoint kernel exists for the linear mixed path only
+  const bool can_split = precision == POD_MIXED && !quad && emb_deg == 0 && adj_force < 0;
+  for (int sp = 0; sp < (can_split ? 2 : 1) && !rc_; ++sp)
+    for (int a : atom_c)
+      for (int rp = 0; rp < 2 && !rc_; ++rp) {
+        if (rp && (precision != POD_MIXED || radial_mode != 0 || sp)) break;  // R' staging: fused table path only
+        LaunchShape s = win;
+        s.atom_wpb = a;
+        s.atom_rp = rp;
+        s.atom_split = can_split ? sp : -1;
+        if ((rc_ = measure(s, t))) break;
+        if (t[1] < best_atom) {
+          best_atom = t[1];
+          win.atom_wpb = a;
+          win.atom_rp = rp;
+          win.atom_split = s.atom_split;
+        }
       }
-    }
   for (int n = 0; !rc_ && n < 3; ++n) {
     LaunchShape s = win;
     s.neigh_wpb = neigh_c[n];
@@ -357,7 +362,7 @@ int pod_handle::autotune(const pod_system* sys, const double* c, int reps, cudaS
 std::vector<DevBuf*> pod_handle::all_bufs() {
   return {&cell_count, &cell_atoms, &wpos, &phi, &plo, &nbr_count, &nbr_j, &nbr_s, &rev, &g, &Ei,
           &Wat, &status, &offs, &pos_in, &c_in, &E_out, &F_out, &W_out, &Ei_out, &fitA, &fitG, &fitb,
-          &fitwork, &cfg_of, &boxes, &rtab, &wpart, &Dws, &chunks, &cpart, &wrapk, &gdm, &dmG, &facc, &qS32, &qS64,
+          &fitwork, &cfg_of, &boxes, &rtab, &wpart, &Dws, &chunks, &cpart, &wrapk, &gdm, &dmG, &facc, &qS32, &qS64, &pdisp, &adjb, &qrw, &halo_cnt,
           &embW};
 }
 
@@ -476,6 +481,11 @@ int pod_set_option(pod_handle* h, int option, int value) {
     h->excl3 = value;
     return POD_OK;
   }
+  if (option == POD_OPT_ADJOINT) {
+    if (value < -1 || value > 1) return h->fail(POD_EINVAL, "adjoint kernel must be -1 (by shape), 0 or 1");
+    h->adj_force = value;
+    return POD_OK;
+  }
   if (option == POD_OPT_PRECISION) {
     if (value != POD_FP64 && value != POD_MIXED) return h->fail(POD_EINVAL, "precision must be POD_FP64 or POD_MIXED");
     h->precision = value;
@@ -549,7 +559,7 @@ int pod_autotune(pod_handle* h, const pod_system* sys, const double* c, int reps
     shape[1] = best.atom_wpb;
     shape[2] = best.gather_wpb;
     shape[3] = best.gather_bps;
-    shape[4] = best.atom_rp;
+    shape[4] = best.atom_split == 1 ? 2 : best.atom_rp;
   }
   if (ms)
     for (int k = 0; k < 3; ++k) ms[k] = t[k];
@@ -730,7 +740,8 @@ int pod_handle::plan(const pod_system* sys, Plan& pl) {
 }
 
 int pod_handle::build_neighbors(const double* pos, Plan& pl, bool need_rev, cudaStream_t st,
-                                unsigned long long* facc_zero) {
+                                unsigned long long* facc_zero, float4* pd, bool pad, bool* wrote_pd) {
+  if (wrote_pd) *wrote_pd = false;
   const int N = pl.N;
   int rc_;
   reuse_ok = false;
@@ -768,7 +779,8 @@ int pod_handle::build_neighbors(const double* pos, Plan& pl, bool need_rev, cuda
   if (e != cudaSuccess) return cuda_fail(e, "bin kernel");
   e = launch_neigh(N, pl.cg, (const double*)wpos.p, (const float4*)phi.p, (const float4*)plo.p,
                    (const int*)cell_count.p, (const float4*)cell_atoms.p, rlist(), pl.cap, (int*)nbr_count.p,
-                   (int*)nbr_j.p, (int*)nbr_s.p, (int*)status.p, st, pl.shape.neigh_wpb);
+                   (int*)nbr_j.p, (int*)nbr_s.p, (int*)status.p, st, pl.shape.neigh_wpb, pd, pad || need_rev,
+                   wrote_pd);
   if (e != cudaSuccess) return cuda_fail(e, "neighbour kernel");
   }
   if (need_rev) {
@@ -866,6 +878,16 @@ int pod_handle::ensure_table(cudaStream_t st) {
   return POD_OK;
 }
 
+// Whether the linear mixed path runs its adjoint pair pass as a kernel of its own
+// (warp per atom, lane per pair) after a forward-only atom kernel, instead of
+// inside the fused kernel: the option when set, else the launch shape, else by
+// size -- small systems, where the fused kernel is one latency-bound wave.
+bool pod_handle::split_adjoint(const Plan& pl) const {
+  if (adj_force >= 0) return adj_force == 1;
+  if (pl.shape.atom_split >= 0) return pl.shape.atom_split == 1;
+  return pl.N <= 131072;
+}
+
 int pod_handle::run_atoms(int mode, const Plan& pl, double* D, const double* c, double* Ei_dst, cudaStream_t st) {
   cudaError_t e;
   const bool has4 = P.P4 >= 0;
@@ -884,6 +906,7 @@ int pod_handle::run_atoms(int mode, const Plan& pl, double* D, const double* c, 
     a.c = c;
     a.Ei = Ei_dst;
     a.g = nullptr;
+    a.pd = pd_ok ? (const float4*)pdisp.p : nullptr;
     a.facc = (unsigned long long*)facc.p;
     a.qbeta = (const float*)qS32.p;
     a.emb_a = (const double*)embW.p;
@@ -894,7 +917,18 @@ int pod_handle::run_atoms(int mode, const Plan& pl, double* D, const double* c, 
     a.q0 = dm_q0;
     a.q1 = dm_q1;
     if (mode == 3) a.keep_rp = 1;  // the design pass reads R, R' of every pair once per descriptor index
+    const bool split = mode == 1 && split_adjoint(pl);
+    if (split) {
+      const int nap = ((PA + 1) * (PA + 2) * (PA + 3) / 6 + 3) / 4 * 4;
+      const size_t rows = (size_t)a.n_eval * K;
+      int rc_ = ensure(adjb, sizeof(float) * rows * (nap + 1), "atom adjoints");
+      if (rc_) return rc_;
+      a.adj_out = (float*)adjb.p;
+      a.s3_out = (float*)adjb.p + rows * nap;
+      a.keep_rp = 0;  // the forward-only kernel needs no R'
+    }
     e = mode == 5 ? launch_atom_emb_f32(a, PA, has4, st) : launch_atom_f32(mode, a, PA, has4, st);
+    if (e == cudaSuccess && split) e = launch_pair_adjoint_f32(a, PA, has4, st);
   } else {
     AtomArgs<double> a;
     fill_args(a, pl);
@@ -980,9 +1014,16 @@ int pod_handle::energy_forces(const pod_system* sys, const double* c, double* E,
       if (ew != cudaSuccess) return cuda_fail(ew, "rewrap kernel");
     } else {
       // the FP64 gather searches the reverse slots; when the list may be reused
-      // (a skin, or reuse switched on) it also stores them for the reusing steps
-      if ((rc_ = build_neighbors(sys->pos, pl, false, st, fa))) return rc_;
+      // (a skin, or reuse switched on) it also stores them for the reusing steps.
+      // The mixed path rebuilding every call takes each pair's displacement from
+      // the neighbour search (rows without sentinel padding; not kept for reuse).
+      const bool want_pd = fixp && !pl.batched && skin == 0.0 && nbr_mode == 0;
+      if (want_pd && (rc_ = ensure(pdisp, sizeof(float4) * (size_t)N * pl.cap, "pair displacements"))) return rc_;
+      if ((rc_ = build_neighbors(sys->pos, pl, false, st, fa, want_pd ? (float4*)pdisp.p : nullptr, !want_pd,
+                                 &pd_ok)))
+        return rc_;
     }
+    if (reuse) pd_ok = false;
     const bool keep_rev = !fixp && !reuse && !pl.batched && (skin > 0 || nbr_mode == 1);
     if (keep_rev && (rc_ = ensure(rev, sizeof(int) * (size_t)N * pl.cap, "reverse index"))) return rc_;
     const int* rev_in = reuse ? (const int*)rev.p : nullptr;
@@ -1008,8 +1049,10 @@ int pod_handle::energy_forces(const pod_system* sys, const double* c, double* E,
       if (ez != cudaSuccess) return cuda_fail(ez, "ghost atom energies");
     }
     n_eval_cur = n_eval;
+    const bool pd_used = pd_ok;
     rc_ = run_atoms(quad ? 4 : (emb_deg > 0 ? 5 : 1), pl, nullptr, c, Ei_dst, st);
     n_eval_cur = 0;
+    pd_ok = false;
     if (rc_) return rc_;
     if ((rc_ = mark(2, st))) return rc_;
     cudaError_t e;
@@ -1032,7 +1075,7 @@ int pod_handle::energy_forces(const pod_system* sys, const double* c, double* E,
     if ((rc_ = finish(st, pl, retry))) return rc_;
     if (!retry) {
       // a list can be reused (FP64 path: once its reverse slots are stored)
-      if (!pl.batched && (fixp || reuse || rev_out)) {
+      if (!pl.batched && (fixp || reuse || rev_out) && !pd_used) {
         last_pl = pl;
         reuse_ok = true;
       }

@@ -135,12 +135,21 @@ struct pod_handle {
   int fit_gram_tc(double gamma, double* dG, double* dr, bool legacy_mma);
   int gram_mode = 0;  // exact slice products: 0 tcgen05, 2 mma.sync; 1: FP64 SYRK
   int fit_solve_dev();
+  int fit_solve_qr(double gamma);
+  DevBuf qrw;  // QR solve: factors of the row and merge stages
+  DevBuf halo_cnt;  // pod_halo_select: count of the selected atoms
   int fit_residual_dev(double* sumE, double* sumF);
   long long fit_R = 0;
   int fit_nc = 0, fit_N = 0;
   double fit_wE = 0, fit_wF = 0;
   int build_neighbors(const double* pos, Plan& pl, bool need_rev, cudaStream_t st,
-                      unsigned long long* facc = nullptr);
+                      unsigned long long* facc = nullptr, float4* pd = nullptr, bool pad = true,
+                      bool* wrote_pd = nullptr);
+  DevBuf pdisp;        // mixed path: per-slot pair displacements from the neighbour search
+  DevBuf adjb;         // mixed linear path, separate adjoint kernel: dE_i/dB [N][K][NAP], then dE_i/dS3 [N][K]
+  int adj_force = -1;  // POD_OPT_ADJOINT: -1 launch shape / size, 0 fused, 1 separate kernel
+  bool split_adjoint(const Plan& pl) const;
+  bool pd_ok = false;  // pdisp holds the current list's displacements (for the next atom-kernel launch)
   template <typename T>
   void fill_args(fastpod::AtomArgs<T>& a, const Plan& pl);
   int run_atoms(int mode, const Plan& pl, double* D, const double* c, double* Ei_dst, cudaStream_t st);

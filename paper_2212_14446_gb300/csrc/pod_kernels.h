@@ -32,6 +32,7 @@ struct LaunchShape {
   int gather_wpb = 16;
   int gather_bps = 3;
   int atom_rp = 0;  // table path: stage R' in shared memory in the pair pass (else re-evaluate it)
+  int atom_split = -1;  // mixed linear path: 1 adjoint pair pass as its own kernel, 0 fused, -1 by size
 };
 
 struct AtomLayout {
@@ -40,7 +41,7 @@ struct AtomLayout {
   int SA;   // per-atom stride of R / R' (CH * KS + K: lanes (atom, m) hit distinct banks)
   int GA;   // per-atom stride of the staged (u, r), in Q4 units
   int AS;   // per-atom stride of the adjoint dE/dB (multiple of 4, odd number of 16-byte units)
-  size_t off_geo, off_R, off_Rp, off_adj, off_e, off_cnt, off_V, off_D, warp_bytes;
+  size_t off_geo, off_R, off_Rp, off_adj, off_e, off_cnt, off_V, off_D, off_J, warp_bytes;
   int MS;   // per-atom stride of the staged descriptors (quadratic model)
 };
 
@@ -53,6 +54,7 @@ struct AtomArgs {
   const int* nbr_count;
   const int* nbr_j;
   const int* nbr_s;
+  const float4* pd;     // FP32 path (optional): per-slot displacement x_j + s L - x_i, j in .w (N * cap)
   const double* wpos;   // wrapped positions [3][N] (FP64 path)
   const float4* phi;    // FP32 hi part of the wrapped positions (mixed path)
   const float4* plo;    // FP32 lo part
@@ -69,6 +71,9 @@ struct AtomArgs {
   double* Ei;           // mode 1: atom energies [N]
   Q4<T>* g;             // mode 1, FP64 path: dE_i/dr_ij per pair slot [N * cap]
   unsigned long long* facc;  // mode 1, FP32 path: fixed-point force accumulators [N][4]
+  T* adj_out;           // mode 1 (optional): stop after the adjoint, writing dE_i/dB [N][K][NAP] here
+  T* s3_out;            //   and dE_i/dS3 [N][K] (exclusive three-body set); the pair pass then runs
+                        //   as launch_pair_adjoint_f32
   double* wpart;        // mode 1: per-warp virial partials [warps][9]
   const double* vdir;   // mode 2: displacement direction per atom [3][N] (tangent of D written to D)
   T* gdm;               // mode 3: design-matrix pair gradients [q - q0][N * cap][K][3]
@@ -97,9 +102,14 @@ cudaError_t launch_rewrap(int N, const double* pos, const int* wrapk, const doub
                           float4* plo, int* status, cudaStream_t st, unsigned long long* facc = nullptr);
 cudaError_t launch_kick(int N3, double* v, const double* F, double half_dt_over_m, double* x, double dt,
                         cudaStream_t st);
+// Neighbour search over the binned atoms.  pad: fill each row with a sentinel up
+// to cap (needed by the reverse-slot search); pd (optional): also write each
+// slot's FP32 displacement with j in .w -- *wrote_pd says whether the kernel
+// that ran did (the block-per-cell search does, the general search does not).
 cudaError_t launch_neigh(int N, const CellGrid& cg, const double* wpos, const float4* phi, const float4* plo,
                          const int* cell_count, const float4* cell_pos, double rcut, int cap, int* nbr_count,
-                         int* nbr_j, int* nbr_s, int* status, cudaStream_t st, int wpb = WPB_NEIGH);
+                         int* nbr_j, int* nbr_s, int* status, cudaStream_t st, int wpb = WPB_NEIGH,
+                         float4* pd = nullptr, bool pad = true, bool* wrote_pd = nullptr);
 cudaError_t launch_rev(int N, int cap, const int* nbr_count, const int* nbr_j, const int* nbr_s, int* rev,
                        int* status, cudaStream_t st);
 cudaError_t launch_export_neighbors(int N, int cap, const int* nbr_count, const int* nbr_j, const int* nbr_s,
@@ -116,6 +126,10 @@ cudaError_t launch_segsum(int n_cfg, const CfgBox* cbox, const double* v, double
 
 cudaError_t launch_atom_f32(int mode, const AtomArgs<float>& p, int PA, bool has4, cudaStream_t st);
 cudaError_t launch_atom_f64(int mode, const AtomArgs<double>& p, int PA, bool has4, cudaStream_t st);
+// Adjoint pair pass of the linear FP32 path as its own kernel (warp per atom, lane
+// per pair), after launch_atom_f32 in mode 1 with adj_out set: g_ij from dE_i/dB,
+// fixed-point forces, energy-free virial totals.
+cudaError_t launch_pair_adjoint_f32(const AtomArgs<float>& p, int PA, bool has4, cudaStream_t st);
 // Embedding model (energy mode 5), compiled in translation units of their own.
 cudaError_t launch_atom_emb_f32(const AtomArgs<float>& p, int PA, bool has4, cudaStream_t st);
 cudaError_t launch_atom_emb_f64(const AtomArgs<double>& p, int PA, bool has4, cudaStream_t st);
@@ -129,6 +143,16 @@ cudaError_t launch_gather_reduce(int N, int n_eval, int cap, const int* nbr_coun
 int atom_warps(int N, int K, int wpb);
 cudaError_t launch_colsum(int n_chunks, const int* chunk_rows /*[n_chunks][2]*/, int n_cfg, const int* cfg_chunks,
                           int M, const double* D, double* part, double* G, cudaStream_t st);
+// Tall-skinny Householder QR of the fit's design matrix (qr.cu): shared memory of
+// one panel (M + 1 columns of M + cmax rows); the row stage (one factor per block
+// from rows of A and b), the merge stage (g factors into one per block) and the
+// final stage (c_out set: one block absorbs every factor and sqrt(gamma) I, then
+// back substitution; info = k + 1 for a zero pivot R_kk, else 0).
+size_t tsqr_smem_bytes(int M, int cmax);
+cudaError_t launch_tsqr_rows(int M, long long R, const double* AT, const double* b, int nblocks,
+                             long long rows_per_block, int cmax, double* out, cudaStream_t st);
+cudaError_t launch_tsqr_merge(int M, int nin, int g, const double* in, int cmax, double sqrt_gamma, double* out,
+                              double* c_out, int* info, cudaStream_t st);
 int gather_blocks(int N, int wpb, int bps);
 int finalize_blocks(int N);
 cudaError_t launch_finalize(int N, const unsigned long long* facc, double* F, double fscale, int nblocks, double* E,

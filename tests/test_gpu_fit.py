@@ -230,3 +230,79 @@ def test_tensor_core_gram_equals_fp64_syrk(pkg, prec, ncfg, max_atoms):
     else:
         d = ctc - c64  # ||A d|| through the normal equations, against ||A c64||
         assert np.sqrt(abs(d @ G64 @ d)) <= 1e-8 * np.sqrt(c64 @ G64 @ c64)
+
+
+def _dimer_set(n, seed):
+    """Open dimers at random lengths and orientations: every three-body column of
+    a mode equals every other of that mode (R_m^2) and every four-body column R_m^3,
+    so A has rank 19 of 103 and A^T A + gamma I is positive definite only by
+    gamma = 1e-12, far below the rounding of its entries."""
+    g = synth.rng(seed)
+    cfgs = []
+    for _ in range(n):
+        r = g.uniform(2.2, 4.8)
+        u = g.normal(size=3)
+        u /= np.linalg.norm(u)
+        pos = np.array([[10.0, 10.0, 10.0], [10.0, 10.0, 10.0] + r * u])
+        cfgs.append(synth.Config(pos=pos, box=np.array([30.0, 30.0, 30.0]), pbc=(0, 0, 0)))
+    return cfgs
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_qr_fallback_on_singular_normal_equations(pkg, prec):
+    """Cholesky of the normal equations fails (POD_ESINGULAR) on a rank-deficient
+    design matrix with the paper's gamma = 1e-12; the QR solve of [A; sqrt(gamma) I]
+    (the default fallback, or selected) matches the oracle's SVD least squares of
+    the same augmented system through the fitted values A c."""
+    p = synth.params_full()
+    o = oracle.Oracle(p)
+    cfgs = _dimer_set(40, 11)
+    cstar = synth.coefficients(o.M, 14)
+    E_ref, F_ref = _labels(o, cfgs, cstar, noise=1.0, seed=15)
+    pod = pkg.POD(p, precision=prec, Q=o.Q)
+    with pytest.raises(pkg.PodError) as ei:
+        pod.fit(cfgs, E_ref, F_ref, solver="cholesky")
+    assert ei.value.code == pkg.POD_ESINGULAR
+    c_auto, maeE, maeF = pod.fit(cfgs, E_ref, F_ref)
+    c_qr, _, _ = pod.fit(cfgs, E_ref, F_ref, solver="qr")
+    assert np.array_equal(c_auto, c_qr)
+    assert np.all(np.isfinite(c_qr))
+    if prec == "mixed":
+        # FP32 rounding breaks the exact collinearity of the mixed design matrix's
+        # columns, so its regularised solution is not the FP64 one's; the solve path
+        # is what is checked here
+        return
+    c_o, A, b = o.fit(cfgs, E_ref, F_ref)
+    assert np.max(np.abs(A @ c_qr - A @ c_o)) <= 1e-8 * np.max(np.abs(b))
+    res = np.abs(A @ c_o - b)
+    assert maeF == pytest.approx(res[np.arange(len(b)) % 7 != 0].mean(), rel=1e-3)
+
+
+@pytest.mark.parametrize("ncfg,max_atoms", [(12, 30), (150, 80)])
+def test_qr_solve_equals_cholesky_when_well_posed(pkg, ncfg, max_atoms):
+    """On well-conditioned training sets the QR solve (row blocks, merge levels,
+    final block) and the Cholesky solve give the same fitted values; the larger
+    set spans hundreds of row blocks and two merge levels."""
+    p = synth.params_full()
+    o = oracle.Oracle(p)
+    cfgs = training_configs(ncfg, replica=9, max_atoms=max_atoms)
+    cstar = synth.coefficients(o.M, 51)
+    if ncfg <= 12:
+        E_ref, F_ref = _labels(o, cfgs, cstar, noise=1.0, seed=16)
+    else:
+        pod64 = pkg.POD(p, precision="fp64", Q=o.Q)
+        out = pod64.energy_forces_batch(cfgs, torch.tensor(cstar))
+        E_ref = out["E"].cpu().numpy() + 1e-3 * synth.rng(17).normal(size=len(cfgs))
+        Fall = out["F"].cpu().numpy()
+        offs = out["offs"]
+        F_ref = [Fall[offs[k]:offs[k + 1]] for k in range(len(cfgs))]
+    pod = pkg.POD(p, precision="fp64", Q=o.Q)
+    c_ch, mE_ch, mF_ch = pod.fit(cfgs, E_ref, F_ref, solver="cholesky")
+    c_qr, mE_qr, mF_qr = pod.fit(cfgs, E_ref, F_ref, solver="qr")
+    G, _ = pod.fit_normal(cfgs, E_ref, F_ref)
+    d = c_qr - c_ch
+    assert np.sqrt(abs(d @ G @ d)) <= 1e-8 * np.sqrt(c_ch @ G @ c_ch)
+    assert mF_qr == pytest.approx(mF_ch, rel=1e-6)
+    if ncfg <= 12:
+        c_o, A, b = o.fit(cfgs, E_ref, F_ref)
+        assert np.max(np.abs(A @ c_qr - A @ c_o)) <= 1e-8 * np.max(np.abs(b))

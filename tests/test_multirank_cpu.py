@@ -220,3 +220,120 @@ def test_slab_decomposition_two_ranks():
         assert E == pytest.approx(E1, rel=1e-14)
         assert np.allclose(F, F1, rtol=0, atol=1e-13 * np.max(np.abs(F1)))
         assert np.allclose(Ei, Ei1, rtol=1e-14, atol=0) and np.allclose(W, W1, rtol=1e-13, atol=1e-15)
+
+
+# ------------------------------------- slab halo exchange (point to point, O(surface))
+
+def _halo_system():
+    p = synth.params_small()
+    cfg = synth.jitter(synth.bcc(6), 0.1, synth.rng(131))   # 432 atoms, box 19.9 A: slabs of >= r_cut
+    return p, cfg, synth.coefficients(oracle.Oracle(p).M, 132)
+
+
+def _host_ops(o, c):
+    from paper_2212_14446_gb300 import parallel
+
+    def evaluate(sub, sub_box, pbc, n_local, c_):
+        cfg = synth.Config(pos=np.ascontiguousarray(sub.T), box=sub_box, pbc=pbc)
+        Ei, E, F, W = o.energy_forces_local(cfg, c, n_local)
+        return E, Ei, F.T, W
+    return parallel.HostOps(evaluate)
+
+
+def _halo_rank(rank, world, p, cfg, c, comm_for):
+    from paper_2212_14446_gb300 import parallel
+    o = oracle.Oracle(p)
+    dom = parallel.SlabDomain(cfg.box, p.r_cut, axis=0, rank=rank, world=world)
+    own = parallel.owned_atoms(dom, cfg.pos)
+    x = torch.tensor(np.ascontiguousarray(cfg.pos[own].T))
+    E, Ei, F, W = parallel.slab_energy_forces(dom, _host_ops(o, c), x, c, comm_for(dom))
+    return own, float(E), Ei.numpy(), F.numpy(), W.numpy()
+
+
+def _assemble(n, parts):
+    F = np.zeros((n, 3))
+    Ei = np.zeros(n)
+    seen = np.zeros(n, dtype=int)
+    for own, _, ei, f, _ in parts:
+        F[own] = f.T
+        Ei[own] = ei
+        seen[own] += 1
+    assert np.all(seen == 1)  # every atom owned by exactly one slab
+    return Ei, F
+
+
+def _check_whole(p, cfg, c, parts):
+    o = oracle.Oracle(p)
+    Ei0, E0, F0, W0 = o.energy_forces(cfg, c, fast=True)
+    Ei, F = _assemble(cfg.n, parts)
+    for _, E, _, _, W in parts:  # E and W summed over ranks: the same on every rank
+        assert E == pytest.approx(E0, rel=1e-12)
+        assert np.max(np.abs(W.reshape(3, 3) - W0)) <= 1e-11 * np.max(np.abs(W0))
+    assert np.allclose(Ei, Ei0, rtol=1e-12, atol=1e-14)
+    assert np.max(np.abs(F - F0)) <= 1e-11 * np.max(np.abs(F0))
+
+
+def test_halo_exchange_one_rank_is_the_periodic_system():
+    """One slab: its halo layers come back to it as its own ghosts (the periodic
+    images across the split axis), so the domain equals the whole system."""
+    from paper_2212_14446_gb300 import parallel
+    p, cfg, c = _halo_system()
+    _check_whole(p, cfg, c, [_halo_rank(0, 1, p, cfg, c, lambda dom: parallel.LoopComm())])
+
+
+@pytest.mark.parametrize("world", [2, 3])
+def test_halo_exchange_ranks_as_threads(world):
+    """Two and three slabs run as threads exchanging halos and ghost forces
+    through mailboxes: owned forces, atom energies, E and W equal the whole
+    system's (two slabs: both neighbours of a slab are the same rank)."""
+    import threading
+    from paper_2212_14446_gb300 import parallel
+    p, cfg, c = _halo_system()
+    tc = parallel.ThreadComm(world)
+    out, errs = [None] * world, []
+
+    def run(r):
+        try:
+            out[r] = _halo_rank(r, world, p, cfg, c, tc.rank)
+        except Exception as ex:  # surfaced below
+            errs.append(ex)
+
+    th = [threading.Thread(target=run, args=(r,)) for r in range(world)]
+    for t in th:
+        t.start()
+    for t in th:
+        t.join(timeout=300)
+    assert not errs, errs
+    _check_whole(p, cfg, c, out)
+
+
+def _halo_worker(rank, world, port, q):
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        from paper_2212_14446_gb300 import parallel
+        p, cfg, c = _halo_system()
+        q.put(_halo_rank(rank, world, p, cfg, c, lambda dom: parallel.DistComm(dom, dist.group.WORLD)))
+    finally:
+        dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("world", [2])
+def test_halo_exchange_gloo_ranks(world):
+    """Two CPU ranks (gloo, point-to-point messages; both neighbours of a slab
+    are the other rank, so message order matters): each rank sends
+    only the atoms within r_cut of its slab faces and receives only its ghosts'
+    forces; the stitched result equals the single-process whole system."""
+    port = _free_port()
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    procs = [ctx.Process(target=_halo_worker, args=(r, world, port, q)) for r in range(world)]
+    for pr in procs:
+        pr.start()
+    res = [q.get(timeout=300) for _ in procs]
+    for pr in procs:
+        pr.join(timeout=60)
+        assert pr.exitcode == 0
+    p, cfg, c = _halo_system()
+    _check_whole(p, cfg, c, res)
