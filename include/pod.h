@@ -264,6 +264,30 @@ int pod_global_descriptors(pod_handle* h, const pod_system* sys, double* G, void
  * is dL/dc = -Gdot evaluated at v = dL/dF.  Errors as pod_descriptors. */
 int pod_descriptors_jvp(pod_handle* h, const pod_system* sys, const double* v, double* Gdot, void* stream);
 
+/* Per-atom directional derivatives of the descriptors along per-atom
+ * displacements: Ddot[i][m] = sum_k (dD_im/dr_k) . v_k (v device [3][N], Ddot
+ * device [N][M]), the forward-mode pass of pod_descriptors_jvp (Eq. 24b / 26a /
+ * 27a / 30a with dB/dr of Eq. 24c) without the sum over atoms.  Batches are
+ * supported.  Errors as pod_descriptors. */
+int pod_descriptors_tangent(pod_handle* h, const pod_system* sys, const double* v, double* Ddot, void* stream);
+
+/* Gradient of a force-matching loss (Eq. 63b) with respect to the parameters of
+ * the handle's current model, from per-atom descriptors D and their directional
+ * derivatives Ddot along v = F - F_ref (device [n_atoms][M] each, from
+ * pod_descriptors and pod_descriptors_tangent):
+ *   grad = sum_i w_i dE_i/dtheta + t (d/de) [sum_i dE_i/dtheta](r + e v)
+ * with w (device [n_atoms]) the weight of each atom's energy term -- for
+ * L = sum_c w_E^2 ((E_c - E_c^ref) / N_c)^2 + w_F^2 |F - F^ref|^2 it is
+ * 2 w_E^2 (E_c - E_c^ref) / N_c^2 on the atoms of configuration c -- and t the
+ * weight of the force term (-2 w_F^2 for that loss).  grad (host) receives:
+ *   linear model     dL/dc (M)
+ *   quadratic model  dL/dc (M), then dL/dbeta_mn for m <= n, row-major (M (M + 1) / 2)
+ *   embedding model  dL/dc (M), dL/da (M), dL/dalpha_k for k = 0..degree
+ * FP64, sums in a fixed order; synchronous.  Errors: POD_EINVAL, POD_ENOMEM,
+ * POD_ECUDA. */
+int pod_model_gradients(pod_handle* h, int n_atoms, const double* D, const double* Ddot, const double* w, double t,
+                        double* grad, void* stream);
+
 /* pod_energy_forces with HOST buffers: sys->pos, c, E, Ei, F, W are host
  * pointers (pinned memory is fastest).  Copies inputs to library-owned device
  * buffers, computes, copies results back and waits for the stream. */

@@ -70,7 +70,7 @@ EXPORTS = ["pod_create", "pod_destroy", "pod_info", "pod_set_option", "pod_statu
            "pod_fit_normal", "pod_fit_solve", "pod_fit_residual", "pod_descriptors_static",
            "pod_global_descriptors", "pod_descriptors_jvp", "pod_set_skin", "pod_md_step", "pod_fma_probe", "pod_autotune", "pod_set_quadratic",
            "pod_set_embedding", "pod_save", "pod_load", "pod_selftest_wait", "pod_halo_select", "pod_halo_add",
-           "pod_last_error"]
+           "pod_descriptors_tangent", "pod_model_gradients", "pod_last_error"]
 
 _lib = None
 _lock = threading.Lock()
@@ -118,6 +118,8 @@ def lib():
                 "pod_halo_select": (C.c_int, [H, dp, C.c_int, C.c_int, C.c_double, C.c_double, C.c_double,
                                               C.c_double, C.c_double, C.c_int, ip, dp, ip, vp]),
                 "pod_halo_add": (C.c_int, [H, dp, ip, C.c_int, dp, C.c_int, vp]),
+                "pod_descriptors_tangent": (C.c_int, [H, S, dp, dp, vp]),
+                "pod_model_gradients": (C.c_int, [H, C.c_int, dp, dp, dp, C.c_double, dp, vp]),
                 "pod_last_error": (C.c_char_p, [H]),
             }
             for name, (res, args) in sig.items():
@@ -241,6 +243,20 @@ def pod_halo_select(h, pos, axis, L, x0, x1, shift, offset, cap, idx, out, strea
 def pod_halo_add(h, G, idx, n, F, stream=None):
     """F[:, idx[k]] += G[:, k] for k < n (device tensors; F (3, N), G (3, n))."""
     _check(h, lib().pod_halo_add(h, _dptr(G), _iptr(idx), int(n), _dptr(F), int(F.shape[1]), _stream(stream)))
+
+
+def pod_descriptors_tangent(h, sys, v, Ddot, stream=None):
+    """Per-atom Ddot[i] = sum_k (dD_i/dr_k) . v_k (v device (3, N), Ddot device (N, M))."""
+    _check(h, lib().pod_descriptors_tangent(h, C.byref(sys), _dptr(v), _dptr(Ddot), _stream(stream)))
+
+
+def pod_model_gradients(h, D, Ddot, w, t, n_out, stream=None):
+    """Loss gradient of the handle's current model (see include/pod.h); returns a
+    numpy array of n_out values."""
+    g = np.zeros(n_out)
+    _check(h, lib().pod_model_gradients(h, int(D.shape[0]), _dptr(D), _dptr(Ddot), _dptr(w), float(t),
+                                        g.ctypes.data_as(C.POINTER(C.c_double)), _stream(stream)))
+    return g
 
 
 def pod_energy_forces(h, sys, c, E, Ei=None, F=None, W=None, stream=None):

@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 OBJ = os.path.join(HERE, "_build")
 LIBDIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIBDIR, "libfastpod.so")
-SOURCES = ["pod_api.cu", "neigh.cu", "atom_f32.cu", "atom_f64.cu", "atom_emb_f32.cu", "atom_emb_f64.cu", "gather.cu", "batch.cu", "fit.cu", "static_desc.cu", "peak.cu", "adjoint_f32.cu", "qr.cu", "halo.cu",
+SOURCES = ["pod_api.cu", "neigh.cu", "atom_f32.cu", "atom_f64.cu", "atom_emb_f32.cu", "atom_emb_f64.cu", "gather.cu", "batch.cu", "fit.cu", "static_desc.cu", "peak.cu", "adjoint_f32.cu", "qr.cu", "halo.cu", "model_grad.cu",
            "model_io.cu", "gram_tc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",

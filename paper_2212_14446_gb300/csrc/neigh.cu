@@ -80,6 +80,7 @@ __device__ __forceinline__ void neigh_finish_row(int N, const CellGrid& cg, cons
                                                  int* __restrict__ status) {
   __syncwarp();
   int n = min(nhit, keycap);
+  int dropped_all = 0;  // band keys dropped among the n kept
   // decide the band candidates exactly in FP64 (R6): drop the misses
   {
     const double xi0 = wpos[i], xi1 = wpos[(size_t)N + i], xi2 = wpos[(size_t)2 * N + i];
@@ -103,6 +104,7 @@ __device__ __forceinline__ void neigh_finish_row(int N, const CellGrid& cg, cons
     }
 #pragma unroll
     for (int d = 16; d > 0; d >>= 1) dropped += __shfl_xor_sync(0xffffffffu, dropped, d);
+    dropped_all = dropped;
     // an overflowed key buffer lost candidates: keep the preliminary count (> cap)
     // so the call reports it and retries with a larger capacity
     if (nhit <= keycap) nhit -= dropped;
@@ -140,11 +142,17 @@ __device__ __forceinline__ void neigh_finish_row(int N, const CellGrid& cg, cons
         __syncwarp();
       }
   }
-  // the nhit valid keys lead the sorted array (when nothing overflowed)
-  const int nw = min(min(n, nhit), cap);
+  // The valid keys lead the sorted array.  The kernels that read the list take
+  // min(count, cap) slots, so every one of them must hold a valid pair: after an
+  // overflow (count above cap, the call is retried) slots past the valid keys
+  // repeat the last valid one (or, with none, the atom itself: r = 0, reported).
+  const int nvalid = n - dropped_all;
+  const int nfill = min(nhit, cap);
+  const unsigned long long fill_key =
+      nvalid > 0 ? keys[nvalid - 1] : (((unsigned long long)i << 24) | (unsigned long long)shift_pack(0, 0, 0));
   for (int t = lane; t < cap; t += 32) {
-    if (t < nw) {
-      const unsigned long long key = keys[t];
+    if (t < nfill) {
+      const unsigned long long key = t < nvalid ? keys[t] : fill_key;
       nbr_j[(size_t)i * cap + t] = (int)(key >> 24);
       nbr_s[(size_t)i * cap + t] = (int)(key & 0xFFFFFFull);
     } else {
@@ -261,20 +269,23 @@ __global__ void __launch_bounds__(NEIGH_MAX_WPB * 32)
 }
 
 // Block per cell, for a search depth of one cell in every direction (image
-// shifts in {-1, 0, 1}): the candidates of the 27 neighbouring (cell, image)
+// shifts in {-1, 0, 1}).  The candidates of the 27 neighbouring (cell, image)
 // pairs are staged once in shared memory as image-shifted FP32 positions with
-// their image id (one coalesced copy per neighbouring cell, shared by all of the
-// cell's atoms), then each warp takes one of the cell's atoms and tests every
-// candidate with lanes over candidates.  Keys are 32-bit, (j << 5) | image id
-// with id = 9 (s_x + 1) + 3 (s_y + 1) + (s_z + 1), so their order is the list
-// order (j, s_x, s_y, s_z); bit 31 marks a band candidate until the exact FP64
-// decision (R6) drops or keeps it.  The row is written as (j, packed shift),
-// padded with a sentinel up to cap when the reverse-slot search will read it
-// (pad), and, when pd is given, as the pair displacement x_j + s L - x_i in FP32
-// from the double-float split of both positions (the arithmetic of the atom
-// kernels, so the same bits) with j in the fourth word.  Requires N < 2^26.
-// Atoms that did not fit in their cell are given an empty row by the bin kernel
-// (and the call is retried).
+// their image id (one coalesced copy per neighbouring cell).  Every thread of the
+// block then takes candidates and tests each against all of the cell's own
+// atoms (the candidate stays in registers, the own atoms are shared-memory
+// broadcasts), appending hits to the own atom's key list; afterwards a warp per
+// own atom decides its band keys, sorts them and writes its row.  Keys are
+// 32-bit, (j << 5) | image id with id = 9 (s_x + 1) + 3 (s_y + 1) + (s_z + 1),
+// so their order is the list order (j, s_x, s_y, s_z); bit 31 marks a band
+// candidate until the exact FP64 decision (R6) keeps or drops it.  The order in
+// which hits are appended does not matter: each row is sorted.  The row is
+// written as (j, packed shift), padded with a sentinel up to cap when the
+// reverse-slot search will read it (pad), and, when pd is given, as the pair
+// displacement x_j + s L - x_i in FP32 from the double-float split of both
+// positions (the arithmetic of the atom kernels, so the same bits) with j in the
+// fourth word.  Requires N < 2^26.  Atoms that did not fit in their cell are
+// given an empty row by the bin kernel (and the call is retried).
 constexpr unsigned KEY_BAND = 0x80000000u;
 
 __global__ void __launch_bounds__(NEIGH_MAX_WPB * 32)
@@ -284,20 +295,21 @@ __global__ void __launch_bounds__(NEIGH_MAX_WPB * 32)
                       int keycap, int pad, int* __restrict__ nbr_count, int* __restrict__ nbr_j,
                       int* __restrict__ nbr_s, float4* __restrict__ pd, int* __restrict__ status) {
   extern __shared__ __align__(16) unsigned char csm[];
-  __shared__ int soff[28], scell[27];
+  __shared__ int soff[28], scell[27], sid[27];
   __shared__ float spx[27], spy[27], spz[27];
   const int ccap = 27 * cg.cap;
   float4* cand = reinterpret_cast<float4*>(csm);
   unsigned char* cid = reinterpret_cast<unsigned char*>(cand + ccap);
-  unsigned* kbuf = reinterpret_cast<unsigned*>(csm + (sizeof(float4) * (size_t)ccap + (size_t)ccap + 15) / 16 * 16);
+  int* ncnt = reinterpret_cast<int*>(csm + (sizeof(float4) * (size_t)ccap + (size_t)ccap + 15) / 16 * 16);
+  unsigned* kbuf = reinterpret_cast<unsigned*>(ncnt + (cg.cap + 3) / 4 * 4);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   const int cell = blockIdx.x;
   if (warp == 0) {
     const int ci[3] = {cell % cg.nc[0], (cell / cg.nc[0]) % cg.nc[1], cell / (cg.nc[0] * cg.nc[1])};
-    int cnt = 0, tcell = 0;
+    int cnt = 0, tcell = 0, id = 13;
     float px = 0.f, py = 0.f, pz = 0.f;
     if (lane < 27) {
-      const int oc[3] = {lane / 9 - 1, (lane / 3) % 3 - 1, lane % 3 - 1};  // stencil entry = image-id order
+      const int oc[3] = {lane / 9 - 1, (lane / 3) % 3 - 1, lane % 3 - 1};
       int tc[3], sh[3];
       bool ok = true;
 #pragma unroll
@@ -319,15 +331,8 @@ __global__ void __launch_bounds__(NEIGH_MAX_WPB * 32)
         px = (float)sh[0] * cg.Lf[0];
         py = (float)sh[1] * cg.Lf[1];
         pz = (float)sh[2] * cg.Lf[2];
-        // image id of this entry (its shift, not its cell offset)
-        scell[lane] = tcell;
+        id = (sh[0] + 1) * 9 + (sh[1] + 1) * 3 + (sh[2] + 1);  // the image shift decides the key
       }
-      spx[lane] = px;
-      spy[lane] = py;
-      spz[lane] = pz;
-      if (!ok) scell[lane] = 0;
-      // the shift of the entry decides the key; keep it beside the offsets
-      soff[lane] = (sh[0] + 1) * 9 + (sh[1] + 1) * 3 + (sh[2] + 1);
     }
     int x = cnt;  // inclusive prefix sum over the stencil entries
 #pragma unroll
@@ -335,16 +340,20 @@ __global__ void __launch_bounds__(NEIGH_MAX_WPB * 32)
       const int y = __shfl_up_sync(0xffffffffu, x, o);
       if (lane >= o) x += y;
     }
-    const int sid = lane < 27 ? soff[lane] : 0;
-    __syncwarp();
     if (lane < 27) {
       soff[lane] = x - cnt;
-      kbuf[lane] = (unsigned)sid;  // temporary: image id per stencil entry (the key buffers are unused yet)
+      scell[lane] = tcell;
+      sid[lane] = id;
+      spx[lane] = px;
+      spy[lane] = py;
+      spz[lane] = pz;
     }
     if (lane == 26) soff[27] = x;
   }
   __syncthreads();
   const int ncand = soff[27];
+  // the cell's own atoms are the centre stencil entry (offset 0, image 0: id 13)
+  const int own0 = soff[13], own_n = soff[14] - soff[13];
   auto entry_of = [&](int f) {
     int lo = 0, hi = 27;  // soff[lo] <= f < soff[hi]
     while (hi - lo > 1) {
@@ -365,62 +374,42 @@ __global__ void __launch_bounds__(NEIGH_MAX_WPB * 32)
     float4 q1 = make_float4(0.f, 0.f, 0.f, 0.f);
     if (f1 < ncand) q1 = cell_pos[(size_t)scell[e1] * cg.cap + (f1 - soff[e1])];
     cand[f0] = make_float4(q0.x + spx[e0], q0.y + spy[e0], q0.z + spz[e0], q0.w);
-    cid[f0] = (unsigned char)kbuf[e0];
+    cid[f0] = (unsigned char)sid[e0];
     if (f1 < ncand) {
       cand[f1] = make_float4(q1.x + spx[e1], q1.y + spy[e1], q1.z + spz[e1], q1.w);
-      cid[f1] = (unsigned char)kbuf[e1];
+      cid[f1] = (unsigned char)sid[e1];
+    }
+  }
+  for (int a = threadIdx.x; a < own_n; a += blockDim.x) ncnt[a] = 0;
+  __syncthreads();
+  // every candidate against every own atom; hits appended to the atom's keys
+  for (int f = threadIdx.x; f < ncand; f += blockDim.x) {
+    const float4 q = cand[f];
+    const int j = __float_as_int(q.w);
+    const unsigned kj = ((unsigned)j << 5) | (unsigned)cid[f];
+    const bool self_img = cid[f] == 13;
+    for (int a = 0; a < own_n; ++a) {
+      const float4 qi = cand[own0 + a];
+      const float dx = q.x - qi.x, dy = q.y - qi.y, dz = q.z - qi.z;
+      const float r2f = dx * dx + dy * dy + dz * dz;
+      if (r2f < rc2_hi && !(self_img && j == __float_as_int(qi.w))) {
+        const int pos = atomicAdd(&ncnt[a], 1);
+        if (pos < keycap) kbuf[(size_t)a * keycap + pos] = kj | (r2f < rc2_lo ? 0u : KEY_BAND);
+      }
     }
   }
   __syncthreads();
-  // the cell's own atoms are the centre stencil entry (offset 0, image 0: id 13)
-  const int own0 = soff[13], own_n = soff[14] - soff[13];
-  unsigned* keys = kbuf + (size_t)warp * keycap;
-  const unsigned below = (1u << lane) - 1u;
   float Ll[3];
 #pragma unroll
   for (int d = 0; d < 3; ++d) Ll[d] = __double2float_rn(cg.L[d] - (double)cg.Lf[d]);
-  for (int k = warp; k < own_n; k += nwarps) {
-    const float4 qi = cand[own0 + k];
-    const int i = __float_as_int(qi.w);
-    int nhit = 0;
-    unsigned anyband = 0;
-    // candidate f: (hit, key) of the FP32 test (band keys marked for the FP64 decision)
-    auto test = [&](int f, unsigned& key) {
-      bool hit = false;
-      key = 0;
-      if (f < ncand) {
-        const float4 q = cand[f];
-        const int j = __float_as_int(q.w);
-        const int id = cid[f];
-        if (!(j == i && id == 13)) {
-          const float dx = q.x - qi.x, dy = q.y - qi.y, dz = q.z - qi.z;
-          const float r2f = dx * dx + dy * dy + dz * dz;
-          hit = r2f < rc2_hi;
-          key = ((unsigned)j << 5) | (unsigned)id | (r2f < rc2_lo ? 0u : KEY_BAND);
-        }
-      }
-      return hit;
-    };
-    for (int f0 = 0; f0 < ncand; f0 += 64) {  // two rounds of 32 candidates per iteration
-      unsigned key0, key1;
-      const bool hit0 = test(f0 + lane, key0);
-      const bool hit1 = test(f0 + 32 + lane, key1);
-      const unsigned m0 = __ballot_sync(0xffffffffu, hit0);
-      const unsigned m1 = __ballot_sync(0xffffffffu, hit1);
-      if (hit0) {
-        const int pos = nhit + __popc(m0 & below);
-        if (pos < keycap) keys[pos] = key0;
-        anyband |= key0 & KEY_BAND;
-      }
-      if (hit1) {
-        const int pos = nhit + __popc(m0) + __popc(m1 & below);
-        if (pos < keycap) keys[pos] = key1;
-        anyband |= key1 & KEY_BAND;
-      }
-      nhit += __popc(m0) + __popc(m1);
-    }
-    __syncwarp();
+  for (int a = warp; a < own_n; a += nwarps) {
+    const int i = __float_as_int(cand[own0 + a].w);
+    unsigned* keys = kbuf + (size_t)a * keycap;
+    int nhit = ncnt[a];
     const int n = min(nhit, keycap);
+    int dropped_all = 0;  // band keys dropped among the n kept
+    unsigned anyband = 0;
+    for (int t = lane; t < n; t += 32) anyband |= keys[t] & KEY_BAND;
     if (__any_sync(0xffffffffu, anyband != 0)) {
       // decide the band candidates exactly in FP64 (R6): drop the misses
       const double xi0 = wpos[i], xi1 = wpos[(size_t)N + i], xi2 = wpos[(size_t)2 * N + i];
@@ -442,6 +431,7 @@ __global__ void __launch_bounds__(NEIGH_MAX_WPB * 32)
       }
 #pragma unroll
       for (int d = 16; d > 0; d >>= 1) dropped += __shfl_xor_sync(0xffffffffu, dropped, d);
+      dropped_all = dropped;
       // an overflowed key buffer lost candidates: keep the preliminary count (> cap)
       // so the call reports it and retries with a larger capacity
       if (nhit <= keycap) nhit -= dropped;
@@ -459,6 +449,7 @@ __global__ void __launch_bounds__(NEIGH_MAX_WPB * 32)
           const bool lower = (lane & jj) == 0;
           v = (lower == up) ? min(v, w) : max(v, w);
         }
+      __syncwarp();
       if (lane < n) keys[lane] = v;
       __syncwarp();
     } else {
@@ -471,16 +462,22 @@ __global__ void __launch_bounds__(NEIGH_MAX_WPB * 32)
           for (int t = lane; t < np; t += 32) {
             const int u = t ^ jj;
             if (u > t) {
-              const unsigned a = keys[t], b = keys[u];
+              const unsigned x = keys[t], y = keys[u];
               const bool up = (t & kk) == 0;
-              if ((a > b) == up) { keys[t] = b; keys[u] = a; }
+              if ((x > y) == up) { keys[t] = y; keys[u] = x; }
             }
           }
           __syncwarp();
         }
     }
-    // the nhit valid keys lead the sorted array (when nothing overflowed)
-    const int nw = min(min(n, nhit), cap);
+    // The valid keys lead the sorted array.  The kernels that read the list take
+    // min(count, cap) slots, so every one of them must hold a valid pair: after
+    // an overflow (count above cap, the call is retried) slots past the valid
+    // keys repeat the last valid one (or, with none, the atom itself: r = 0,
+    // reported).
+    const int nvalid = n - dropped_all;
+    const int nw = min(nhit, cap);
+    const unsigned fill_key = nvalid > 0 ? keys[nvalid - 1] : (((unsigned)i << 5) | 13u);
     float4 hi_i = make_float4(0.f, 0.f, 0.f, 0.f), lo_i = hi_i;
     if (pd) {
       hi_i = phi[i];
@@ -489,7 +486,7 @@ __global__ void __launch_bounds__(NEIGH_MAX_WPB * 32)
     const int tend = pad ? cap : nw;
     for (int t = lane; t < tend; t += 32) {
       if (t < nw) {
-        const unsigned key = keys[t];
+        const unsigned key = t < nvalid ? keys[t] : fill_key;
         const int j = (int)(key >> 5), id = (int)(key & 31u);
         const int sx = id / 9 - 1, sy = (id / 3) % 3 - 1, sz = id % 3 - 1;
         if (!pd || pad) {  // with displacement rows only (and no padding) the index rows are not read
@@ -651,8 +648,10 @@ cudaError_t launch_neigh(int N, const CellGrid& cg, const double* wpos, const fl
   if (s1 && cg.ncells >= 2 * 152 && N < (1 << 26)) {
     int keycap = 32;
     while (keycap < cap) keycap <<= 1;
+    // candidates and their image ids, hit counts and key lists of the cell's own atoms
     const size_t cell_smem = (sizeof(float4) * 27 * (size_t)cg.cap + 27 * (size_t)cg.cap + 15) / 16 * 16 +
-                             (size_t)wpb * keycap * sizeof(unsigned);
+                             sizeof(int) * (size_t)((cg.cap + 3) / 4 * 4) +
+                             (size_t)cg.cap * keycap * sizeof(unsigned);
     if (cell_smem <= 96 * 1024) {
       static size_t cgranted[64] = {};
       if (cudaError_t e = grant_smem((const void*)neigh_cell_kernel, cell_smem, cgranted)) return e;

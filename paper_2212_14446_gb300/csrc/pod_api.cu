@@ -362,7 +362,7 @@ int pod_handle::autotune(const pod_system* sys, const double* c, int reps, cudaS
 std::vector<DevBuf*> pod_handle::all_bufs() {
   return {&cell_count, &cell_atoms, &wpos, &phi, &plo, &nbr_count, &nbr_j, &nbr_s, &rev, &g, &Ei,
           &Wat, &status, &offs, &pos_in, &c_in, &E_out, &F_out, &W_out, &Ei_out, &fitA, &fitG, &fitb,
-          &fitwork, &cfg_of, &boxes, &rtab, &wpart, &Dws, &chunks, &cpart, &wrapk, &gdm, &dmG, &facc, &qS32, &qS64, &pdisp, &adjb, &qrw, &halo_cnt,
+          &fitwork, &cfg_of, &boxes, &rtab, &wpart, &Dws, &chunks, &cpart, &wrapk, &gdm, &dmG, &facc, &qS32, &qS64, &pdisp, &adjb, &qrw, &halo_cnt, &mgrad,
           &embW};
 }
 
@@ -667,9 +667,12 @@ int pod_handle::plan_single(int N, const double box[3], const int pbc[3], Plan& 
     cg.S[dmax] = cg.pbc[dmax] ? (int)std::ceil(rc / cs * (1.0 + 1e-12)) : (cg.nc[dmax] > 1 ? 1 : 0);
   }
   pl.cg.ncells = (int)ncells;
+  // cell capacity: mean occupancy plus four standard deviations of a Poisson count
+  // plus a margin (a fuller cell is reported and the call retried with twice it);
+  // it sizes the neighbour search's shared memory, so it is kept tight
   const double expect_cell = (double)N / ncells;
-  int capc = (int)(2.0 * expect_cell + 16);
-  capc = (capc + 15) / 16 * 16;
+  int capc = (int)(expect_cell + 4.0 * std::sqrt(expect_cell) + 8.0);
+  capc = (capc + 7) / 8 * 8;
   pl.cg.cap = std::max(capc, cap_cell);
   const double expect = N / vol * (4.0 / 3.0) * M_PI * rc * rc * rc;
   int cap = (int)(1.5 * expect + 16);
@@ -1172,10 +1175,11 @@ int pod_handle::colsum_table(const Plan& pl, int& nch, int& nrows2) {
   return POD_OK;
 }
 
-int pod_handle::global_desc(const pod_system* sys, const double* vdir, double* Gout, cudaStream_t st) {
+int pod_handle::global_desc(const pod_system* sys, const double* vdir, double* Gout, cudaStream_t st,
+                            double* per_atom) {
   int rc_ = validate_system(sys);
   if (rc_) return rc_;
-  if (!Gout) return fail(POD_EINVAL, "output is NULL");
+  if (!Gout && !per_atom) return fail(POD_EINVAL, "output is NULL");
   if (vdir && excl3) return fail(POD_EINVAL, "the descriptor tangent takes the fast POD descriptor set");
   const int N = sys->n_atoms;
   retries = 0;
@@ -1183,17 +1187,23 @@ int pod_handle::global_desc(const pod_system* sys, const double* vdir, double* G
     Plan pl;
     if ((rc_ = plan(sys, pl))) return rc_;
     if ((rc_ = build_neighbors(sys->pos, pl, false, st))) return rc_;
-    if ((rc_ = ensure(Dws, sizeof(double) * (size_t)N * M, "descriptor workspace"))) return rc_;
-    int nch = 0, nrows2 = 0;
-    if ((rc_ = colsum_table(pl, nch, nrows2))) return rc_;
+    double* rows = per_atom;  // per-atom rows to the caller, or to the workspace for the sums
+    if (!rows) {
+      if ((rc_ = ensure(Dws, sizeof(double) * (size_t)N * M, "descriptor workspace"))) return rc_;
+      rows = (double*)Dws.p;
+    }
     vdir_cur = vdir;
-    rc_ = run_atoms(vdir ? 2 : 0, pl, (double*)Dws.p, nullptr, nullptr, st);
+    rc_ = run_atoms(vdir ? 2 : 0, pl, rows, nullptr, nullptr, st);
     vdir_cur = nullptr;
     if (rc_) return rc_;
-    const int ncfg = pl.batched ? pl.n_cfg : 1;
-    cudaError_t e = launch_colsum(nch, (const int*)chunks.p, ncfg, (const int*)chunks.p + nrows2, M,
-                                  (const double*)Dws.p, (double*)cpart.p, Gout, st);
-    if (e != cudaSuccess) return cuda_fail(e, "column sums");
+    if (Gout) {
+      int nch = 0, nrows2 = 0;
+      if ((rc_ = colsum_table(pl, nch, nrows2))) return rc_;
+      const int ncfg = pl.batched ? pl.n_cfg : 1;
+      cudaError_t e = launch_colsum(nch, (const int*)chunks.p, ncfg, (const int*)chunks.p + nrows2, M,
+                                    (const double*)rows, (double*)cpart.p, Gout, st);
+      if (e != cudaSuccess) return cuda_fail(e, "column sums");
+    }
     bool retry;
     if ((rc_ = finish(st, pl, retry))) return rc_;
     if (!retry) return POD_OK;

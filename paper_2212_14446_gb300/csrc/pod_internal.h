@@ -117,7 +117,7 @@ struct pod_handle {
   double rlist() const { return P.r_cut + skin; }
   int md_step(const pod_system* sys, double* pos, double* v, double* F, const double* c, double mass, double dt,
               double* E, cudaStream_t st);
-  int global_desc(const pod_system* sys, const double* vdir, double* G, cudaStream_t st);
+  int global_desc(const pod_system* sys, const double* vdir, double* G, cudaStream_t st, double* per_atom = nullptr);
   const double* vdir_cur = nullptr;
   DevBuf Dws, chunks, cpart;
   DevBuf gdm, dmG;
@@ -138,6 +138,7 @@ struct pod_handle {
   int fit_solve_qr(double gamma);
   DevBuf qrw;  // QR solve: factors of the row and merge stages
   DevBuf halo_cnt;  // pod_halo_select: count of the selected atoms
+  DevBuf mgrad;     // pod_model_gradients: per-block partial sums, then the result
   int fit_residual_dev(double* sumE, double* sumF);
   long long fit_R = 0;
   int fit_nc = 0, fit_N = 0;
