@@ -288,6 +288,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="full", choices=["full", "md", "small", "fig4", "mdrun", "fit"])
     ap.add_argument("--fit-configs", type=int, default=2000)
+    ap.add_argument("--solver", default="auto", choices=["auto", "cholesky", "qr"],
+                    help="fit workload: Cholesky with QR fallback, Cholesky only, or the QR solve")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64-path comparison line items")
@@ -518,7 +520,8 @@ def main():
                                                        else achieved_tflops / vec_peaks["fp64_fma"])},
             "phases_ms": {"neighbors": phase_avg[0], "atom": phase_avg[1], "gather": phase_avg[2],
                           "reduce": phase_avg[3]},
-            "gpu_launches": 4 * args.steps,
+            # per step: bin, neighbour search, atom kernel (+ separate adjoint kernel), finalize
+            "gpu_launches": (5 if shape and shape.get("atom_rp") == 2 else 4) * args.steps,
             "e2e": e2e,
             "cpu_baseline": cpu,
             "fp64_path": fp64,
@@ -637,14 +640,14 @@ def run_fit(args, rank, world, local):
     Er = torch.tensor(np.asarray(E_ref, dtype=np.float64), device="cuda")
     Fr = torch.tensor(np.ascontiguousarray(np.concatenate(F_ref, axis=0).T), dtype=torch.float64, device="cuda")
     for _ in range(max(1, args.warmup)):
-        pod.fit_device(x, boffs, boxes, pbcs, Er, Fr)
+        pod.fit_device(x, boffs, boxes, pbcs, Er, Fr, solver=args.solver)
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     ts = []
     for _ in range(args.steps):
         torch.cuda.synchronize()
         e0.record()
-        c, maeE, maeF = pod.fit_device(x, boffs, boxes, pbcs, Er, Fr)
+        c, maeE, maeF = pod.fit_device(x, boffs, boxes, pbcs, Er, Fr, solver=args.solver)
         e1.record()
         torch.cuda.synchronize()
         ts.append(e0.elapsed_time(e1))
@@ -656,7 +659,7 @@ def run_fit(args, rank, world, local):
     # per-phase device time of one more fit (library CUDA events)
     pod.set_timing(True)
     pod.timing()
-    pod.fit_device(x, boffs, boxes, pbcs, Er, Fr)
+    pod.fit_device(x, boffs, boxes, pbcs, Er, Fr, solver=args.solver)
     ph, calls = pod.timing()
     pod.set_timing(False)
     phases = {"neighbors": ph[0], "design_matrix": ph[1], "gram": ph[2], "solve": ph[3]} if calls else None
@@ -668,7 +671,7 @@ def run_fit(args, rank, world, local):
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32" if args.precision == "mixed" else "f64", "data": "synthetic",
             "config": {"workload": f"training_set_{len(cfgs)}", "atoms": n_atoms, "design_rows": len(cfgs) + 3 * n_atoms,
-                       "descriptors": pod.M},
+                       "descriptors": pod.M, "solver": args.solver},
             "teacher_recovery_max_rel": rel, "mae_E_per_atom": maeE, "mae_F": maeF, "phases_ms": phases,
             "e2e": {"value": len(cfgs) / te, "unit": "configs/s",
                     "h2d_bytes_per_step": int(pos.nbytes + Er.numel() * 8 + Fr.numel() * 8),

@@ -178,11 +178,18 @@ int pod_info(const pod_handle* h, int* M, int* Ns, int* K, double* Q_out, double
                           (bit-identical to 0) */
 #define POD_OPT_ADJOINT 8 /* mixed path, linear model: where the adjoint pair pass g_ij of
                              Eq. 24c runs. -1 (default) by the autotuned launch shape, else
-                             by size (a kernel of its own up to 131,072 atoms); 0 inside the
+                             inside the fused kernel, which measured faster); 0 inside the
                              fused atom kernel; 1 as its own kernel (warp per atom, lane per
                              pair) after a forward-only atom kernel.  Forces and atom
                              energies are the same bits either way; E and W differ only in
                              the grouping of their exact fixed-point sums */
+#define POD_OPT_NEIGHBOR_TESTS 9 /* candidate tests of the block-per-cell neighbour search:
+                                    -1 (default) by the autotuned launch shape, else by size
+                                    (block-wide up to 131,072 atoms); 1 block-wide (every
+                                    thread of a cell's block over candidates x the cell's own
+                                    atoms, shared-memory atomics per atom); 0 a warp per own
+                                    atom (lanes over candidates, ballot compaction).  The lists
+                                    are the same either way (sorted rows) */
 int pod_set_option(pod_handle* h, int option, int value);
 
 /* Neighbour-list skin (A, default 0): lists are built with r_cut + skin and pairs
@@ -424,7 +431,8 @@ int pod_set_embedding(pod_handle* h, const double* a, int degree, const double* 
 /* Launch-shape autotuner (a deployment feature; the paper has no counterpart).
  * Times the three phases of pod_energy_forces on `sys` (one configuration,
  * device positions as for pod_energy_forces; c: device [M]) for a small set of
- * candidate launch shapes -- warps per block of the neighbour search {2, 4, 8},
+ * candidate launch shapes -- warps per block of the neighbour search {2, 4, 8}
+ * each with block-wide candidate tests and with a warp per own atom,
  * of the fused atom kernel {1, 2, 4} (FP32 table path: each with and without R'
  * staged in shared memory), and, on the FP64 path, warps per block x blocks per
  * SM of the gather {16x3, 16x2, 8x6, 8x4, 4x12} -- with CUDA events on `stream`, `reps`
@@ -435,11 +443,13 @@ int pod_set_embedding(pod_handle* h, const double* a, int degree, const double* 
  * for the rounding order of the energy and virial sums.  Synchronous (calls
  * pod_energy_forces about 15 x (reps + 1) times); not for use during stream
  * capture.
- *   shape (host int[5], or NULL): neighbour wpb, atom wpb, gather wpb, gather
+ *   shape (host int[6], or NULL): neighbour wpb, atom wpb, gather wpb, gather
  *   blocks per SM, and the form of the adjoint pair pass: 0 inside the fused atom
  *   kernel, re-evaluating R'; 1 the same with R' staged in shared memory (FP32
  *   table path); 2 as its own kernel after a forward-only atom kernel (FP32 linear
- *   model; see POD_OPT_ADJOINT) -- all candidates of the atom-phase search.
+ *   model; see POD_OPT_ADJOINT) -- all candidates of the atom-phase search; and
+ *   the neighbour search's candidate tests: 1 block-wide (every thread of the
+ *   cell's block over candidates x the cell's own atoms), 0 a warp per own atom.
  *   ms (host double[3], or NULL): mean times of the neighbour, atom and gather
  *   phases with the chosen shape.
  * Errors as pod_energy_forces; POD_EINVAL for a batch. */

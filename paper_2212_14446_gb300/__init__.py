@@ -31,6 +31,7 @@ POD_OPT_SYNC, POD_OPT_PRECISION, POD_OPT_TIMING, POD_OPT_RADIAL, POD_OPT_NEIGHBO
 POD_OPT_DESCRIPTORS = 6
 POD_OPT_GRAM = 7
 POD_OPT_ADJOINT = 8
+POD_OPT_NEIGHBOR_TESTS = 9
 ERROR_NAMES = {0: "POD_OK", -1: "POD_EINVAL", -2: "POD_ENOMEM", -3: "POD_ECUDA", -4: "POD_ERANGE",
                -5: "POD_ENONFINITE", -6: "POD_ESINGULAR", -7: "POD_ENEIGH", -8: "POD_EIO"}
 
@@ -266,8 +267,9 @@ def pod_energy_forces(h, sys, c, E, Ei=None, F=None, W=None, stream=None):
 
 def pod_autotune(h, sys, c, reps=5, stream=None):
     """Returns ([neigh wpb, atom wpb, gather wpb, gather blocks per SM, adjoint form
-    (0 fused, 1 fused with R' staged, 2 separate kernel)], [ms neigh, atom, gather])."""
-    shape = (C.c_int * 5)()
+    (0 fused, 1 fused with R' staged, 2 separate kernel), neighbour tests (1
+    block-wide, 0 warp per atom)], [ms neigh, atom, gather])."""
+    shape = (C.c_int * 6)()
     ms = (C.c_double * 3)()
     _check(h, lib().pod_autotune(h, C.byref(sys), _dptr(c), int(reps), shape, ms, _stream(stream)))
     return list(shape), list(ms)
@@ -440,6 +442,11 @@ class POD:
         """Mixed linear path: "auto" (launch shape / size), "fused" or "separate"."""
         pod_set_option(self.h, POD_OPT_ADJOINT, {"auto": -1, "fused": 0, "separate": 1}[which])
 
+    def set_neighbor_tests(self, which: str):
+        """Neighbour search candidate tests: "auto" (launch shape / size),
+        "blockwide" or "warp"."""
+        pod_set_option(self.h, POD_OPT_NEIGHBOR_TESTS, {"auto": -1, "warp": 0, "blockwide": 1}[which])
+
     def timing(self):
         return pod_timing(self.h)
 
@@ -526,13 +533,14 @@ class POD:
 
     def autotune(self, pos, box, c, pbc=(1, 1, 1), reps=5, stream=None):
         """Pick the launch shape for this system size (pod_autotune); returns
-        {"neigh_wpb", "atom_wpb", "gather_wpb", "gather_bps", "ms": [neigh, atom, gather]}."""
+        {"neigh_wpb", "atom_wpb", "gather_wpb", "gather_bps", "atom_rp", "neigh_blockwide",
+        "ms": [neigh, atom, gather]}."""
         import torch
         x = _soa(pos)
         c = c.to(device=x.device, dtype=torch.float64).contiguous()
         shape, ms = pod_autotune(self.h, self.system(x, box, pbc), c, reps, stream)
         return {"neigh_wpb": shape[0], "atom_wpb": shape[1], "gather_wpb": shape[2], "gather_bps": shape[3],
-                "atom_rp": shape[4], "ms": ms}
+                "atom_rp": shape[4], "neigh_blockwide": shape[5], "ms": ms}
 
     # -- batches of configurations --------------------------------------
     @staticmethod

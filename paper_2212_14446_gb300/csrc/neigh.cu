@@ -288,6 +288,7 @@ __global__ void __launch_bounds__(NEIGH_MAX_WPB * 32)
 // given an empty row by the bin kernel (and the call is retried).
 constexpr unsigned KEY_BAND = 0x80000000u;
 
+template <bool BLOCKWIDE>
 __global__ void __launch_bounds__(NEIGH_MAX_WPB * 32)
     neigh_cell_kernel(int N, CellGrid cg, const double* __restrict__ wpos, const float4* __restrict__ phi,
                       const float4* __restrict__ plo, const int* __restrict__ cell_count,
@@ -380,32 +381,77 @@ __global__ void __launch_bounds__(NEIGH_MAX_WPB * 32)
       cid[f1] = (unsigned char)sid[e1];
     }
   }
-  for (int a = threadIdx.x; a < own_n; a += blockDim.x) ncnt[a] = 0;
-  __syncthreads();
-  // every candidate against every own atom; hits appended to the atom's keys
-  for (int f = threadIdx.x; f < ncand; f += blockDim.x) {
-    const float4 q = cand[f];
-    const int j = __float_as_int(q.w);
-    const unsigned kj = ((unsigned)j << 5) | (unsigned)cid[f];
-    const bool self_img = cid[f] == 13;
-    for (int a = 0; a < own_n; ++a) {
-      const float4 qi = cand[own0 + a];
-      const float dx = q.x - qi.x, dy = q.y - qi.y, dz = q.z - qi.z;
-      const float r2f = dx * dx + dy * dy + dz * dz;
-      if (r2f < rc2_hi && !(self_img && j == __float_as_int(qi.w))) {
-        const int pos = atomicAdd(&ncnt[a], 1);
-        if (pos < keycap) kbuf[(size_t)a * keycap + pos] = kj | (r2f < rc2_lo ? 0u : KEY_BAND);
+  const unsigned below = (1u << lane) - 1u;
+  if (BLOCKWIDE) {
+    for (int a = threadIdx.x; a < own_n; a += blockDim.x) ncnt[a] = 0;
+    __syncthreads();
+    // every candidate against every own atom; hits appended to the atom's keys
+    for (int f = threadIdx.x; f < ncand; f += blockDim.x) {
+      const float4 q = cand[f];
+      const int j = __float_as_int(q.w);
+      const unsigned kj = ((unsigned)j << 5) | (unsigned)cid[f];
+      const bool self_img = cid[f] == 13;
+      for (int a = 0; a < own_n; ++a) {
+        const float4 qi = cand[own0 + a];
+        const float dx = q.x - qi.x, dy = q.y - qi.y, dz = q.z - qi.z;
+        const float r2f = dx * dx + dy * dy + dz * dz;
+        if (r2f < rc2_hi && !(self_img && j == __float_as_int(qi.w))) {
+          const int pos = atomicAdd(&ncnt[a], 1);
+          if (pos < keycap) kbuf[(size_t)a * keycap + pos] = kj | (r2f < rc2_lo ? 0u : KEY_BAND);
+        }
       }
     }
+    __syncthreads();
+  } else {
+    __syncthreads();
   }
-  __syncthreads();
   float Ll[3];
 #pragma unroll
   for (int d = 0; d < 3; ++d) Ll[d] = __double2float_rn(cg.L[d] - (double)cg.Lf[d]);
   for (int a = warp; a < own_n; a += nwarps) {
     const int i = __float_as_int(cand[own0 + a].w);
-    unsigned* keys = kbuf + (size_t)a * keycap;
-    int nhit = ncnt[a];
+    // BLOCKWIDE: the atom's own key list; else this warp's list, filled here by
+    // the warp testing every candidate with lanes over candidates
+    unsigned* keys = BLOCKWIDE ? kbuf + (size_t)a * keycap : kbuf + (size_t)warp * keycap;
+    int nhit = 0;
+    if (BLOCKWIDE) {
+      nhit = ncnt[a];
+    } else {
+      const float4 qi = cand[own0 + a];
+      auto test = [&](int f, unsigned& key) {  // FP32 test of candidate f (band keys marked)
+        bool hit = false;
+        key = 0;
+        if (f < ncand) {
+          const float4 q = cand[f];
+          const int j = __float_as_int(q.w);
+          const int id = cid[f];
+          if (!(j == i && id == 13)) {
+            const float dx = q.x - qi.x, dy = q.y - qi.y, dz = q.z - qi.z;
+            const float r2f = dx * dx + dy * dy + dz * dz;
+            hit = r2f < rc2_hi;
+            key = ((unsigned)j << 5) | (unsigned)id | (r2f < rc2_lo ? 0u : KEY_BAND);
+          }
+        }
+        return hit;
+      };
+      for (int f0 = 0; f0 < ncand; f0 += 64) {  // two rounds of 32 candidates per iteration
+        unsigned key0, key1;
+        const bool hit0 = test(f0 + lane, key0);
+        const bool hit1 = test(f0 + 32 + lane, key1);
+        const unsigned m0 = __ballot_sync(0xffffffffu, hit0);
+        const unsigned m1 = __ballot_sync(0xffffffffu, hit1);
+        if (hit0) {
+          const int pos = nhit + __popc(m0 & below);
+          if (pos < keycap) keys[pos] = key0;
+        }
+        if (hit1) {
+          const int pos = nhit + __popc(m0) + __popc(m1 & below);
+          if (pos < keycap) keys[pos] = key1;
+        }
+        nhit += __popc(m0) + __popc(m1);
+      }
+      __syncwarp();
+    }
     const int n = min(nhit, keycap);
     int dropped_all = 0;  // band keys dropped among the n kept
     unsigned anyband = 0;
@@ -628,7 +674,7 @@ static size_t neigh_smem_bytes(int keycap, int wpb) { return (size_t)wpb * keyca
 cudaError_t launch_neigh(int N, const CellGrid& cg, const double* wpos, const float4* phi, const float4* plo,
                          const int* cell_count, const float4* cell_pos, double rcut, int cap, int* nbr_count,
                          int* nbr_j, int* nbr_s, int* status, cudaStream_t st, int wpb, float4* pd, bool pad,
-                         bool* wrote_pd) {
+                         bool* wrote_pd, bool blockwide) {
   if (wrote_pd) *wrote_pd = false;
   if (wpb < 1 || wpb > NEIGH_MAX_WPB) return cudaErrorInvalidValue;
   const double rc2 = rcut * rcut;
@@ -648,16 +694,24 @@ cudaError_t launch_neigh(int N, const CellGrid& cg, const double* wpos, const fl
   if (s1 && cg.ncells >= 2 * 152 && N < (1 << 26)) {
     int keycap = 32;
     while (keycap < cap) keycap <<= 1;
-    // candidates and their image ids, hit counts and key lists of the cell's own atoms
+    // candidates and their image ids, hit counts and key lists: per own atom of
+    // the cell (block-wide tests) or per warp
+    const int nlists = blockwide ? cg.cap : wpb;
     const size_t cell_smem = (sizeof(float4) * 27 * (size_t)cg.cap + 27 * (size_t)cg.cap + 15) / 16 * 16 +
                              sizeof(int) * (size_t)((cg.cap + 3) / 4 * 4) +
-                             (size_t)cg.cap * keycap * sizeof(unsigned);
+                             (size_t)nlists * keycap * sizeof(unsigned);
     if (cell_smem <= 96 * 1024) {
-      static size_t cgranted[64] = {};
-      if (cudaError_t e = grant_smem((const void*)neigh_cell_kernel, cell_smem, cgranted)) return e;
-      neigh_cell_kernel<<<cg.ncells, wpb * 32, cell_smem, st>>>(N, cg, wpos, phi, plo, cell_count, cell_pos, rc2,
-                                                                rc2_lo, rc2_hi, cap, keycap, pad ? 1 : 0, nbr_count,
-                                                                nbr_j, nbr_s, pd, status);
+      static size_t cgranted[2][64] = {};
+      const void* kern = blockwide ? (const void*)neigh_cell_kernel<true> : (const void*)neigh_cell_kernel<false>;
+      if (cudaError_t e = grant_smem(kern, cell_smem, cgranted[blockwide ? 1 : 0])) return e;
+      if (blockwide)
+        neigh_cell_kernel<true><<<cg.ncells, wpb * 32, cell_smem, st>>>(
+            N, cg, wpos, phi, plo, cell_count, cell_pos, rc2, rc2_lo, rc2_hi, cap, keycap, pad ? 1 : 0, nbr_count,
+            nbr_j, nbr_s, pd, status);
+      else
+        neigh_cell_kernel<false><<<cg.ncells, wpb * 32, cell_smem, st>>>(
+            N, cg, wpos, phi, plo, cell_count, cell_pos, rc2, rc2_lo, rc2_hi, cap, keycap, pad ? 1 : 0, nbr_count,
+            nbr_j, nbr_s, pd, status);
       if (wrote_pd) *wrote_pd = pd != nullptr;
       return cudaGetLastError();
     }

@@ -322,12 +322,18 @@ int pod_handle::autotune(const pod_system* sys, const double* c, int reps, cudaS
           win.atom_split = s.atom_split;
         }
       }
-  for (int n = 0; !rc_ && n < 3; ++n) {
-    LaunchShape s = win;
-    s.neigh_wpb = neigh_c[n];
-    if ((rc_ = measure(s, t))) break;
-    if (t[0] < best_neigh) { best_neigh = t[0]; win.neigh_wpb = neigh_c[n]; }
-  }
+  for (int bw = 0; !rc_ && bw < 2; ++bw)
+    for (int n = 0; !rc_ && n < 3; ++n) {
+      LaunchShape s = win;
+      s.neigh_wpb = neigh_c[n];
+      s.neigh_blockwide = bw;
+      if ((rc_ = measure(s, t))) break;
+      if (t[0] < best_neigh) {
+        best_neigh = t[0];
+        win.neigh_wpb = neigh_c[n];
+        win.neigh_blockwide = bw;
+      }
+    }
   // the FP32 path sums forces in the atom kernel (fixed point) and has no gather
   for (int g = 0; !rc_ && precision != POD_MIXED && g < 5; ++g) {
     LaunchShape s = win;
@@ -486,6 +492,11 @@ int pod_set_option(pod_handle* h, int option, int value) {
     h->adj_force = value;
     return POD_OK;
   }
+  if (option == POD_OPT_NEIGHBOR_TESTS) {
+    if (value < -1 || value > 1) return h->fail(POD_EINVAL, "neighbour tests must be -1 (by shape), 0 or 1");
+    h->neigh_force = value;
+    return POD_OK;
+  }
   if (option == POD_OPT_PRECISION) {
     if (value != POD_FP64 && value != POD_MIXED) return h->fail(POD_EINVAL, "precision must be POD_FP64 or POD_MIXED");
     h->precision = value;
@@ -560,6 +571,7 @@ int pod_autotune(pod_handle* h, const pod_system* sys, const double* c, int reps
     shape[2] = best.gather_wpb;
     shape[3] = best.gather_bps;
     shape[4] = best.atom_split == 1 ? 2 : best.atom_rp;
+    shape[5] = best.neigh_blockwide == 1 ? 1 : 0;
   }
   if (ms)
     for (int k = 0; k < 3; ++k) ms[k] = t[k];
@@ -789,7 +801,7 @@ int pod_handle::build_neighbors(const double* pos, Plan& pl, bool need_rev, cuda
   e = launch_neigh(N, pl.cg, (const double*)wpos.p, (const float4*)phi.p, (const float4*)plo.p,
                    (const int*)cell_count.p, (const float4*)cell_atoms.p, rlist(), pl.cap, (int*)nbr_count.p,
                    (int*)nbr_j.p, (int*)nbr_s.p, (int*)status.p, st, pl.shape.neigh_wpb, pd, pad || need_rev,
-                   wrote_pd);
+                   wrote_pd, neigh_blockwide(pl, N));
   if (e != cudaSuccess) return cuda_fail(e, "neighbour kernel");
   }
   if (need_rev) {
@@ -903,7 +915,17 @@ int pod_handle::ensure_table(cudaStream_t st) {
 bool pod_handle::split_adjoint(const Plan& pl) const {
   if (adj_force >= 0) return adj_force == 1;
   if (pl.shape.atom_split >= 0) return pl.shape.atom_split == 1;
-  return pl.N <= 131072;
+  return false;  // the fused pass measured faster at every size tried
+}
+
+// Candidate tests of the block-per-cell neighbour search: block-wide (every
+// thread of the block over candidates x own atoms) or a warp per own atom; the
+// option when set, the launch shape when tuned, else block-wide for small systems (fewer cells than
+// SMs' worth of warps per atom) and a warp per atom for large ones.
+bool pod_handle::neigh_blockwide(const Plan& pl, int N) const {
+  if (neigh_force >= 0) return neigh_force == 1;
+  if (pl.shape.neigh_blockwide >= 0) return pl.shape.neigh_blockwide == 1;
+  return neigh_blockwide_default(N);
 }
 
 int pod_handle::run_atoms(int mode, const Plan& pl, double* D, const double* c, double* Ei_dst, cudaStream_t st) {

@@ -158,6 +158,8 @@ struct pod_handle {
   DevBuf adjb;         // mixed linear path, separate adjoint kernel: dE_i/dB [N][K][NAP], then dE_i/dS3 [N][K]
   int adj_force = -1;  // POD_OPT_ADJOINT: -1 launch shape / size, 0 fused, 1 separate kernel
   bool split_adjoint(const Plan& pl) const;
+  bool neigh_blockwide(const Plan& pl, int N) const;
+  int neigh_force = -1;  // POD_OPT_NEIGHBOR_TESTS: -1 launch shape / size, 0 warp per atom, 1 block-wide
   bool pd_ok = false;  // pdisp holds the current list's displacements (for the next atom-kernel launch)
   template <typename T>
   void fill_args(fastpod::AtomArgs<T>& a, const Plan& pl);

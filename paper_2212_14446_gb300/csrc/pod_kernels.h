@@ -33,6 +33,7 @@ struct LaunchShape {
   int gather_bps = 3;
   int atom_rp = 0;  // table path: stage R' in shared memory in the pair pass (else re-evaluate it)
   int atom_split = -1;  // mixed linear path: 1 adjoint pair pass as its own kernel, 0 fused, -1 by size
+  int neigh_blockwide = -1;  // block-per-cell search: 1 block-wide candidate tests, 0 a warp per atom, -1 by size
 };
 
 struct AtomLayout {
@@ -106,10 +107,15 @@ cudaError_t launch_kick(int N3, double* v, const double* F, double half_dt_over_
 // to cap (needed by the reverse-slot search); pd (optional): also write each
 // slot's FP32 displacement with j in .w -- *wrote_pd says whether the kernel
 // that ran did (the block-per-cell search does, the general search does not).
+// Block-per-cell neighbour search, candidate tests when no shape says otherwise:
+// block-wide (all threads over candidates x own atoms) for small systems, a warp
+// per own atom for large ones (measured crossover between 8,192 and 1,024,000 atoms).
+inline bool neigh_blockwide_default(int N) { return N <= 131072; }
+
 cudaError_t launch_neigh(int N, const CellGrid& cg, const double* wpos, const float4* phi, const float4* plo,
                          const int* cell_count, const float4* cell_pos, double rcut, int cap, int* nbr_count,
                          int* nbr_j, int* nbr_s, int* status, cudaStream_t st, int wpb = WPB_NEIGH,
-                         float4* pd = nullptr, bool pad = true, bool* wrote_pd = nullptr);
+                         float4* pd = nullptr, bool pad = true, bool* wrote_pd = nullptr, bool blockwide = true);
 cudaError_t launch_rev(int N, int cap, const int* nbr_count, const int* nbr_j, const int* nbr_s, int* rev,
                        int* status, cudaStream_t st);
 cudaError_t launch_export_neighbors(int N, int cap, const int* nbr_count, const int* nbr_j, const int* nbr_s,

@@ -197,7 +197,8 @@ extern "C" int pod_descriptors_static(pod_handle* h, const pod_system* sys, doub
                    reinterpret_cast<const float4*>(base + OFF_PHI), reinterpret_cast<const float4*>(base + OFF_PLO),
                    cellc, reinterpret_cast<const float4*>(base + OFF_CELLA), rc_list, pl.cap,
                    reinterpret_cast<int*>(base + OFF_CNT), reinterpret_cast<int*>(base + OFF_NBRJ),
-                   reinterpret_cast<int*>(base + OFF_NBRS), status, st);
+                   reinterpret_cast<int*>(base + OFF_NBRS), status, st, WPB_NEIGH, nullptr, true, nullptr,
+                   neigh_blockwide_default(N));
   if (e != cudaSuccess) return h->cuda_fail(e, "neighbour kernel");
   const bool has4 = h->P.P4 >= 0;
   if (mixed) {

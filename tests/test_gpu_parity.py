@@ -73,8 +73,9 @@ def full_oracle_ef(full):
     return o.energy_forces(cfg, c, fast=True)
 
 
-def neighbor_compare(pkg, o, p, cfg, atoms, cap=96):
+def neighbor_compare(pkg, o, p, cfg, atoms, cap=96, tests="auto"):
     pod = pkg.POD(p, Q=o.Q)
+    pod.set_neighbor_tests(tests)
     count, nbr, shift = pod.neighbors(soa(cfg), cfg.box, cfg.pbc, cap=cap)
     count, nbr, shift = count.cpu().numpy(), nbr.cpu().numpy(), shift.cpu().numpy()
     for i in atoms:
@@ -92,11 +93,37 @@ def test_neighbors_bitexact_small(pkg, small):
     neighbor_compare(pkg, o, p, cfg, range(cfg.n))
 
 
-def test_neighbors_bitexact_full_sampled(pkg, full):
+@pytest.mark.parametrize("tests", ["blockwide", "warp"])
+def test_neighbors_bitexact_full_sampled(pkg, full, tests):
+    """8,192 atoms: the block-per-cell search, with either form of its candidate tests."""
     p, o, cfg, _ = full
     g = synth.rng(5)
-    count = neighbor_compare(pkg, o, p, cfg, g.choice(cfg.n, 200, replace=False))
+    count = neighbor_compare(pkg, o, p, cfg, g.choice(cfg.n, 200, replace=False), tests=tests)
     assert 18 <= count.min() and count.max() <= 40
+
+
+@pytest.mark.parametrize("tests", ["blockwide", "warp"])
+def test_neighbors_cell_search_on_cutoff_band(pkg, full, tests):
+    """The block-per-cell search decides pairs at r_cut (1 -+ 1e-7), r_cut and
+    r_cut (1 - 1e-15) -- some across the periodic boundary -- in the exact FP64
+    band like the oracle."""
+    p, o, cfg0, _ = full
+    pos = cfg0.pos.copy()
+    rc = p.r_cut
+    L = cfg0.box
+    moved = []
+    for k, (f, u) in enumerate([(1 - 1e-7, (1, 0, 0)), (1 + 1e-7, (0, 1, 0)), (1.0, (0, 0, 1)),
+                                (1 - 1e-15, (1, 1, 0)), (1 + 1e-7, (-1, 0, 1)), (1 - 1e-7, (0, -1, -1))]):
+        i, j = 1000 * k + 3, 1000 * k + 611
+        u = np.array(u, dtype=np.float64)
+        pos[j] = np.mod(pos[i] + rc * f * u / np.linalg.norm(u), L)
+        moved += [i, j]
+    pos[moved[-2]] = np.array([0.25, 7.0, 9.0])  # the last pair straddles the x = 0 face
+    pos[moved[-1]] = np.mod(pos[moved[-2]] + rc * (1 - 1e-7) * np.array([-1.0, 0.0, 0.0]), L)
+    cfg = synth.Config(pos=pos, box=L, pbc=cfg0.pbc)
+    g = synth.rng(6)
+    neighbor_compare(pkg, o, p, cfg, sorted(set(moved) | set(g.choice(cfg.n, 40, replace=False).tolist())),
+                     tests=tests)
 
 
 @pytest.mark.parametrize("k", [0, 1, 2, 3, 5, 8, 13, 21])
@@ -392,9 +419,11 @@ def test_mixed_energy_virial_totals(pkg, full):
     assert torch.equal(again["E"], out["E"]) and torch.equal(again["F"], out["F"])
 
 
-def test_capacity_retry(pkg):
+@pytest.mark.parametrize("tests", ["blockwide", "warp"])
+def test_capacity_retry(pkg, tests):
     """A dense cluster in a large open box: the density-based capacity estimate
-    is far too small, the call overflows, grows its lists and succeeds."""
+    is far too small, the call overflows, grows its lists and succeeds (the
+    block-per-cell search, with either form of its candidate tests)."""
     p = synth.params_full()
     o = oracle.Oracle(p)
     g = synth.rng(17)
@@ -405,6 +434,7 @@ def test_capacity_retry(pkg):
             pts.append(q)
     cfg = synth.Config(pos=np.array(pts) + 40.0, box=np.array([80.0, 80.0, 80.0]), pbc=(0, 0, 0))
     pod = pkg.POD(p, precision="fp64", Q=o.Q)
+    pod.set_neighbor_tests(tests)
     D = pod.descriptors(soa(cfg), cfg.box, cfg.pbc).cpu().numpy()
     Dref = o.descriptors(cfg, atoms=range(0, 60, 6), fast=True)
     assert desc_err(D[::6], Dref) <= 1e-12
