@@ -228,7 +228,9 @@ __device__ __forceinline__ Q4<T> pair_gradient(const Q4<T>& u, const T* Rv, cons
 // paired multiply-add operands otherwise push them past that without a gain.
 template <typename T, int MODE, int KT>
 constexpr int atom_min_blocks() {
-  return (std::is_same<T, float>::value && MODE != 2 && KT != MAXK) ? 4 : 1;
+  // the design mode is held to 6 blocks of 2 warps per SM by its shared memory,
+  // so it takes up to 168 registers at no cost in occupancy
+  return (std::is_same<T, float>::value && MODE != 2 && KT != MAXK) ? (MODE == 3 ? 3 : 4) : 1;
 }
 
 template <typename T, int PA, bool HAS4, int MODE, int KT>
@@ -420,7 +422,26 @@ __global__ void __launch_bounds__(ATOM_MAX_WPB * 32, atom_min_blocks<T, MODE, KT
     Mono<PA>::d3(B, d3v);
     const int n3 = p.P3 + 1;
     const int Qd = 1 + n3 + p.KA4;
+    // Columns whose adjoint rows live on single degrees of the monomials -- D2
+    // (a = e_0), D3_n (a_x = 2 mu_x B_x for deg x = n, Eq. 26a) and the
+    // partitions (n, 0, 0) of D4 = B_0 D3_n (Eq. 27a: a = B_0 times the D3_n row
+    // plus D3_n e_0) -- come out of one pass over the pairs: per pair and mode
+    // the degree-resolved sums s_n = sum_{deg x = n} 2 mu_x B_x A_x and their
+    // gradients, combined per column.  The general partitions (Eq. 30a) have
+    // dense rows and keep a pass each (first, below).
+    auto sparse_q = [&](int q) {
+      if (q <= n3) return true;
+      if (!HAS4) return false;
+      const int pp = q - 1 - n3;
+      bool hit = false;
+#pragma unroll
+      for (int n = 0; n <= PA; ++n) hit |= Four<PA>::p_n00(n) == pp;
+      return hit;
+    };
+    bool any_sparse = false;
+    for (int q = p.q0; q < p.q1 && q < Qd; ++q) any_sparse |= sparse_q(q);
     for (int q = p.q0; q < p.q1 && q < Qd; ++q) {
+      if (sparse_q(q)) continue;  // in the pass below
       __syncwarp();
       if (am) {
         T a[NAP];
@@ -528,6 +549,120 @@ __global__ void __launch_bounds__(ATOM_MAX_WPB * 32, atom_min_blocks<T, MODE, KT
             out[3 * mm + 0] = fma(s1, u.x, s2 * (gx - ug * u.x));
             out[3 * mm + 1] = fma(s1, u.y, s2 * (gy - ug * u.y));
             out[3 * mm + 2] = fma(s1, u.z, s2 * (gz - ug * u.z));
+          }
+        }
+      }
+    }
+    // (after the general columns, which still need B in registers)
+    T* sd3 = reinterpret_cast<T*>(wb + lay.off_d3);
+    if (any_sparse) {
+      __syncwarp();
+      if (am) {
+        T h[NAP], one[PA + 1];
+#pragma unroll
+        for (int x = 0; x < NAP; ++x) h[x] = T(0);
+#pragma unroll
+        for (int n = 0; n <= PA; ++n) one[n] = T(1);
+        Mono<PA>::d3_adjoint(B, one, h);  // h_x = 2 mu_x B_x
+        T* adst = sadj + a_loc * lay.AS + m * NAP;
+#pragma unroll
+        for (int x = 0; x < NAP; ++x) adst[x] = h[x];
+#pragma unroll
+        for (int n = 0; n <= PA; ++n) sd3[(a_loc * K + m) * (PA + 1) + n] = d3v[n];
+      }
+      __syncwarp();
+      for (int ch = 0; ch < nchunks; ++ch) {
+        if (nchunks > 1) {
+          __syncwarp();
+          pair_pass<T, KT, false>(p, lay, geo, sR, sRp, scnt, atom0, A, K, ch, lane);
+          __syncwarp();
+        }
+        int tot = 0;
+        for (int a = 0; a < A; ++a) tot += chunk_count(scnt[a], ch);
+        for (int f = lane; f < tot; f += 32) {
+          int a = 0, base = 0;
+          for (; a < A; ++a) {
+            const int nca = chunk_count(scnt[a], ch);
+            if (f < base + nca) break;
+            base += nca;
+          }
+          const int jj = f - base, slot = ch * CH + jj, i = atom0 + a;
+          const Q4<T> u = geo[a * lay.GA + jj];
+          T Rv[KT], Rpv[KT];
+          if (p.rad.tab && !p.keep_rp) {
+            if (u.w > p.rad.r_in && u.w < p.rmask) {
+              radial_pair<T, KT>(p.rad, u.w, Rv, Rpv);
+            } else {
+#pragma unroll
+              for (int k = 0; k < KT; ++k) { Rv[k] = T(0); Rpv[k] = T(0); }
+            }
+          } else {
+            const T* Rrow = sR + a * lay.SA + jj * lay.KS;
+            const T* Rprow = sRp + a * lay.SA + jj * lay.KS;
+#pragma unroll
+            for (int k = 0; k < KT; ++k) {
+              if (KT == MAXK && k >= K) break;
+              Rv[k] = Rrow[k];
+              Rpv[k] = Rprow[k];
+            }
+          }
+          T Am[NAP];
+          Mono<PA>::eval(u.x, u.y, u.z, Am);
+#pragma unroll
+          for (int x = NA; x < NAP; ++x) Am[x] = T(0);
+          const T ir = T(1) / u.w;
+          const size_t pbase = ((size_t)i * p.cap + slot) * (size_t)K * 3;
+          const size_t plane = (size_t)p.N * p.cap * (size_t)K * 3;
+#pragma unroll 1
+          for (int mm = 0; mm < K; ++mm) {
+            T R = Rv[0], Rp = Rpv[0];  // (selected, so that Rv and Rpv stay in registers)
+#pragma unroll
+            for (int k = 1; k < KT; ++k)
+              if (k == mm) {
+                R = Rv[k];
+                Rp = Rpv[k];
+              }
+            T hm[NAP];
+            const Q4<T>* h4 = reinterpret_cast<const Q4<T>*>(sadj + a * lay.AS + mm * NAP);
+#pragma unroll
+            for (int x4 = 0; x4 < NAP / 4; ++x4) {
+              const Q4<T> hv = h4[x4];
+              hm[4 * x4 + 0] = hv.x;
+              hm[4 * x4 + 1] = hv.y;
+              hm[4 * x4 + 2] = hv.z;
+              hm[4 * x4 + 3] = hv.w;
+            }
+            T sn[PA + 1], gxn[PA + 1], gyn[PA + 1], gzn[PA + 1];
+            Mono<PA>::dot_grad_deg(hm, Am, sn, gxn, gyn, gzn);
+            const T B0 = T(0.5) * hm[0];
+            const T s2 = R * ir;
+            // g = R' (a . A) u + (R / r) (G - (u . G) u) for a column with a . A = dot, a . grad A = G
+            auto emit = [&](int q, T dot, T Gx, T Gy, T Gz) {
+              if (q < p.q0 || q >= p.q1) return;
+              T* out = p.gdm + (size_t)(q - p.q0) * plane + pbase + 3 * mm;
+              const T ug = u.x * Gx + u.y * Gy + u.z * Gz;
+              const T s1 = Rp * dot;
+              out[0] = fma(s1, u.x, s2 * (Gx - ug * u.x));
+              out[1] = fma(s1, u.y, s2 * (Gy - ug * u.y));
+              out[2] = fma(s1, u.z, s2 * (Gz - ug * u.z));
+            };
+            emit(0, mm < p.K2 ? T(1) : T(0), T(0), T(0), T(0));  // D2 = B_m,0, A_0 = 1
+#pragma unroll
+            for (int n = 0; n <= PA; ++n) {
+              if (n <= p.P3) {
+                const bool on = mm < p.K3;
+                emit(1 + n, on ? sn[n] : T(0), on ? gxn[n] : T(0), on ? gyn[n] : T(0), on ? gzn[n] : T(0));
+              }
+              if (HAS4) {
+                const int pp = Four<PA>::p_n00(n);
+                if (pp < p.KA4) {
+                  const bool on = mm < p.K4;
+                  const T d3n = sd3[(a * K + mm) * (PA + 1) + n];
+                  emit(1 + n3 + pp, on ? fma(B0, sn[n], d3n) : T(0), on ? B0 * gxn[n] : T(0),
+                       on ? B0 * gyn[n] : T(0), on ? B0 * gzn[n] : T(0));
+                }
+              }
+            }
           }
         }
       }
@@ -881,7 +1016,8 @@ __global__ void __launch_bounds__(ATOM_MAX_WPB * 32, atom_min_blocks<T, MODE, KT
 
 // ------------------------------------------------------------------ layout
 template <typename T>
-AtomLayout make_layout(int K, int PA, bool table, bool tangent = false, int quadM = 0, bool pair_j = false) {
+AtomLayout make_layout(int K, int PA, bool table, bool tangent = false, int quadM = 0, bool pair_j = false,
+                       bool design = false) {
   if (tangent) table = false;  // the tangent pass reads R' from shared memory
   AtomLayout L{};
   const int NA = (PA + 1) * (PA + 2) * (PA + 3) / 6;
@@ -916,6 +1052,11 @@ AtomLayout make_layout(int K, int PA, bool table, bool tangent = false, int quad
   if (pair_j) {  // neighbour index per staged pair (displacement lists)
     L.off_J = off;
     off = al(off + sizeof(int) * (size_t)L.A * L.GA, 32);
+  }
+  L.off_d3 = 0;
+  if (design) {  // design mode: D3_n of every (atom, mode) of the warp
+    L.off_d3 = off;
+    off = al(off + sizeof(T) * (size_t)L.A * K * (PA + 1), 32);
   }
   L.warp_bytes = off;
   return L;
@@ -978,7 +1119,7 @@ cudaError_t launch_atom_emb_t(const AtomArgs<T>& p, int PA, bool has4, cudaStrea
 template <typename T>
 cudaError_t launch_atom_t(int mode, const AtomArgs<T>& p, int PA, bool has4, cudaStream_t st) {
   const AtomLayout lay = make_layout<T>(p.K, PA, p.rad.tab != nullptr && !p.keep_rp, mode == 2, mode == 4 ? p.M : 0,
-                                        p.pd != nullptr);
+                                        p.pd != nullptr, mode == 3);
   const bool spec6 = (p.K == 6 && PA == 4 && has4);
   const bool spec3 = (p.K == 3 && PA == 3 && !has4);
   if (mode == 2) {

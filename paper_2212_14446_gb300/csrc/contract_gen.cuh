@@ -26,6 +26,11 @@ template <> struct Mono<0> {
     gx = g0; gy = g1; gz = g2;
   }
   template <typename T>
+  static __device__ __forceinline__ void dot_grad_deg(const T* e, const T* A, T* s, T* gx, T* gy, T* gz) {
+    for (int n = 0; n <= 0; ++n) { s[n] = T(0); gx[n] = T(0); gy[n] = T(0); gz[n] = T(0); }
+    s[0] = fma(e[0], A[0], s[0]);
+  }
+  template <typename T>
   static __device__ __forceinline__ void d3(const T* B, T* d) {
     d[0] = B[0] * B[0];
   }
@@ -93,6 +98,17 @@ template <> struct Mono<1> {
     g1 = fma(e[2], A[0], g1);
     g2 = fma(e[3], A[0], g2);
     gx = g0; gy = g1; gz = g2;
+  }
+  template <typename T>
+  static __device__ __forceinline__ void dot_grad_deg(const T* e, const T* A, T* s, T* gx, T* gy, T* gz) {
+    for (int n = 0; n <= 1; ++n) { s[n] = T(0); gx[n] = T(0); gy[n] = T(0); gz[n] = T(0); }
+    s[0] = fma(e[0], A[0], s[0]);
+    s[1] = fma(e[1], A[1], s[1]);
+    gx[1] = fma(e[1], A[0], gx[1]);
+    s[1] = fma(e[2], A[2], s[1]);
+    gy[1] = fma(e[2], A[0], gy[1]);
+    s[1] = fma(e[3], A[3], s[1]);
+    gz[1] = fma(e[3], A[0], gz[1]);
   }
   template <typename T>
   static __device__ __forceinline__ void d3(const T* B, T* d) {
@@ -203,6 +219,32 @@ template <> struct Mono<2> {
     g1 = fma(e[9], A[3], g1);
     g2 = fma(e[9], A[2], g2);
     gx = g0; gy = g1; gz = g2;
+  }
+  template <typename T>
+  static __device__ __forceinline__ void dot_grad_deg(const T* e, const T* A, T* s, T* gx, T* gy, T* gz) {
+    for (int n = 0; n <= 2; ++n) { s[n] = T(0); gx[n] = T(0); gy[n] = T(0); gz[n] = T(0); }
+    s[0] = fma(e[0], A[0], s[0]);
+    s[1] = fma(e[1], A[1], s[1]);
+    gx[1] = fma(e[1], A[0], gx[1]);
+    s[1] = fma(e[2], A[2], s[1]);
+    gy[1] = fma(e[2], A[0], gy[1]);
+    s[1] = fma(e[3], A[3], s[1]);
+    gz[1] = fma(e[3], A[0], gz[1]);
+    s[2] = fma(e[4], A[4], s[2]);
+    gx[2] = fma(T(2) * e[4], A[1], gx[2]);
+    s[2] = fma(e[5], A[5], s[2]);
+    gy[2] = fma(T(2) * e[5], A[2], gy[2]);
+    s[2] = fma(e[6], A[6], s[2]);
+    gz[2] = fma(T(2) * e[6], A[3], gz[2]);
+    s[2] = fma(e[7], A[7], s[2]);
+    gx[2] = fma(e[7], A[2], gx[2]);
+    gy[2] = fma(e[7], A[1], gy[2]);
+    s[2] = fma(e[8], A[8], s[2]);
+    gx[2] = fma(e[8], A[3], gx[2]);
+    gz[2] = fma(e[8], A[1], gz[2]);
+    s[2] = fma(e[9], A[9], s[2]);
+    gy[2] = fma(e[9], A[3], gy[2]);
+    gz[2] = fma(e[9], A[2], gz[2]);
   }
   template <typename T>
   static __device__ __forceinline__ void d3(const T* B, T* d) {
@@ -408,6 +450,60 @@ template <> struct Mono<3> {
     g1 = fma(e[19], A[8], g1);
     g2 = fma(e[19], A[7], g2);
     gx = g0; gy = g1; gz = g2;
+  }
+  template <typename T>
+  static __device__ __forceinline__ void dot_grad_deg(const T* e, const T* A, T* s, T* gx, T* gy, T* gz) {
+    for (int n = 0; n <= 3; ++n) { s[n] = T(0); gx[n] = T(0); gy[n] = T(0); gz[n] = T(0); }
+    s[0] = fma(e[0], A[0], s[0]);
+    s[1] = fma(e[1], A[1], s[1]);
+    gx[1] = fma(e[1], A[0], gx[1]);
+    s[1] = fma(e[2], A[2], s[1]);
+    gy[1] = fma(e[2], A[0], gy[1]);
+    s[1] = fma(e[3], A[3], s[1]);
+    gz[1] = fma(e[3], A[0], gz[1]);
+    s[2] = fma(e[4], A[4], s[2]);
+    gx[2] = fma(T(2) * e[4], A[1], gx[2]);
+    s[2] = fma(e[5], A[5], s[2]);
+    gy[2] = fma(T(2) * e[5], A[2], gy[2]);
+    s[2] = fma(e[6], A[6], s[2]);
+    gz[2] = fma(T(2) * e[6], A[3], gz[2]);
+    s[2] = fma(e[7], A[7], s[2]);
+    gx[2] = fma(e[7], A[2], gx[2]);
+    gy[2] = fma(e[7], A[1], gy[2]);
+    s[2] = fma(e[8], A[8], s[2]);
+    gx[2] = fma(e[8], A[3], gx[2]);
+    gz[2] = fma(e[8], A[1], gz[2]);
+    s[2] = fma(e[9], A[9], s[2]);
+    gy[2] = fma(e[9], A[3], gy[2]);
+    gz[2] = fma(e[9], A[2], gz[2]);
+    s[3] = fma(e[10], A[10], s[3]);
+    gx[3] = fma(T(3) * e[10], A[4], gx[3]);
+    s[3] = fma(e[11], A[11], s[3]);
+    gy[3] = fma(T(3) * e[11], A[5], gy[3]);
+    s[3] = fma(e[12], A[12], s[3]);
+    gz[3] = fma(T(3) * e[12], A[6], gz[3]);
+    s[3] = fma(e[13], A[13], s[3]);
+    gx[3] = fma(T(2) * e[13], A[7], gx[3]);
+    gy[3] = fma(e[13], A[4], gy[3]);
+    s[3] = fma(e[14], A[14], s[3]);
+    gx[3] = fma(T(2) * e[14], A[8], gx[3]);
+    gz[3] = fma(e[14], A[4], gz[3]);
+    s[3] = fma(e[15], A[15], s[3]);
+    gx[3] = fma(e[15], A[5], gx[3]);
+    gy[3] = fma(T(2) * e[15], A[7], gy[3]);
+    s[3] = fma(e[16], A[16], s[3]);
+    gy[3] = fma(T(2) * e[16], A[9], gy[3]);
+    gz[3] = fma(e[16], A[5], gz[3]);
+    s[3] = fma(e[17], A[17], s[3]);
+    gx[3] = fma(e[17], A[6], gx[3]);
+    gz[3] = fma(T(2) * e[17], A[8], gz[3]);
+    s[3] = fma(e[18], A[18], s[3]);
+    gy[3] = fma(e[18], A[6], gy[3]);
+    gz[3] = fma(T(2) * e[18], A[9], gz[3]);
+    s[3] = fma(e[19], A[19], s[3]);
+    gx[3] = fma(e[19], A[9], gx[3]);
+    gy[3] = fma(e[19], A[8], gy[3]);
+    gz[3] = fma(e[19], A[7], gz[3]);
   }
   template <typename T>
   static __device__ __forceinline__ void d3(const T* B, T* d) {
@@ -829,6 +925,105 @@ template <> struct Mono<4> {
     g1 = fma(e[34], A[17], g1);
     g2 = fma(T(2) * e[34], A[19], g2);
     gx = g0; gy = g1; gz = g2;
+  }
+  template <typename T>
+  static __device__ __forceinline__ void dot_grad_deg(const T* e, const T* A, T* s, T* gx, T* gy, T* gz) {
+    for (int n = 0; n <= 4; ++n) { s[n] = T(0); gx[n] = T(0); gy[n] = T(0); gz[n] = T(0); }
+    s[0] = fma(e[0], A[0], s[0]);
+    s[1] = fma(e[1], A[1], s[1]);
+    gx[1] = fma(e[1], A[0], gx[1]);
+    s[1] = fma(e[2], A[2], s[1]);
+    gy[1] = fma(e[2], A[0], gy[1]);
+    s[1] = fma(e[3], A[3], s[1]);
+    gz[1] = fma(e[3], A[0], gz[1]);
+    s[2] = fma(e[4], A[4], s[2]);
+    gx[2] = fma(T(2) * e[4], A[1], gx[2]);
+    s[2] = fma(e[5], A[5], s[2]);
+    gy[2] = fma(T(2) * e[5], A[2], gy[2]);
+    s[2] = fma(e[6], A[6], s[2]);
+    gz[2] = fma(T(2) * e[6], A[3], gz[2]);
+    s[2] = fma(e[7], A[7], s[2]);
+    gx[2] = fma(e[7], A[2], gx[2]);
+    gy[2] = fma(e[7], A[1], gy[2]);
+    s[2] = fma(e[8], A[8], s[2]);
+    gx[2] = fma(e[8], A[3], gx[2]);
+    gz[2] = fma(e[8], A[1], gz[2]);
+    s[2] = fma(e[9], A[9], s[2]);
+    gy[2] = fma(e[9], A[3], gy[2]);
+    gz[2] = fma(e[9], A[2], gz[2]);
+    s[3] = fma(e[10], A[10], s[3]);
+    gx[3] = fma(T(3) * e[10], A[4], gx[3]);
+    s[3] = fma(e[11], A[11], s[3]);
+    gy[3] = fma(T(3) * e[11], A[5], gy[3]);
+    s[3] = fma(e[12], A[12], s[3]);
+    gz[3] = fma(T(3) * e[12], A[6], gz[3]);
+    s[3] = fma(e[13], A[13], s[3]);
+    gx[3] = fma(T(2) * e[13], A[7], gx[3]);
+    gy[3] = fma(e[13], A[4], gy[3]);
+    s[3] = fma(e[14], A[14], s[3]);
+    gx[3] = fma(T(2) * e[14], A[8], gx[3]);
+    gz[3] = fma(e[14], A[4], gz[3]);
+    s[3] = fma(e[15], A[15], s[3]);
+    gx[3] = fma(e[15], A[5], gx[3]);
+    gy[3] = fma(T(2) * e[15], A[7], gy[3]);
+    s[3] = fma(e[16], A[16], s[3]);
+    gy[3] = fma(T(2) * e[16], A[9], gy[3]);
+    gz[3] = fma(e[16], A[5], gz[3]);
+    s[3] = fma(e[17], A[17], s[3]);
+    gx[3] = fma(e[17], A[6], gx[3]);
+    gz[3] = fma(T(2) * e[17], A[8], gz[3]);
+    s[3] = fma(e[18], A[18], s[3]);
+    gy[3] = fma(e[18], A[6], gy[3]);
+    gz[3] = fma(T(2) * e[18], A[9], gz[3]);
+    s[3] = fma(e[19], A[19], s[3]);
+    gx[3] = fma(e[19], A[9], gx[3]);
+    gy[3] = fma(e[19], A[8], gy[3]);
+    gz[3] = fma(e[19], A[7], gz[3]);
+    s[4] = fma(e[20], A[20], s[4]);
+    gx[4] = fma(T(4) * e[20], A[10], gx[4]);
+    s[4] = fma(e[21], A[21], s[4]);
+    gy[4] = fma(T(4) * e[21], A[11], gy[4]);
+    s[4] = fma(e[22], A[22], s[4]);
+    gz[4] = fma(T(4) * e[22], A[12], gz[4]);
+    s[4] = fma(e[23], A[23], s[4]);
+    gx[4] = fma(T(3) * e[23], A[13], gx[4]);
+    gy[4] = fma(e[23], A[10], gy[4]);
+    s[4] = fma(e[24], A[24], s[4]);
+    gx[4] = fma(T(3) * e[24], A[14], gx[4]);
+    gz[4] = fma(e[24], A[10], gz[4]);
+    s[4] = fma(e[25], A[25], s[4]);
+    gx[4] = fma(e[25], A[11], gx[4]);
+    gy[4] = fma(T(3) * e[25], A[15], gy[4]);
+    s[4] = fma(e[26], A[26], s[4]);
+    gy[4] = fma(T(3) * e[26], A[16], gy[4]);
+    gz[4] = fma(e[26], A[11], gz[4]);
+    s[4] = fma(e[27], A[27], s[4]);
+    gx[4] = fma(e[27], A[12], gx[4]);
+    gz[4] = fma(T(3) * e[27], A[17], gz[4]);
+    s[4] = fma(e[28], A[28], s[4]);
+    gy[4] = fma(e[28], A[12], gy[4]);
+    gz[4] = fma(T(3) * e[28], A[18], gz[4]);
+    s[4] = fma(e[29], A[29], s[4]);
+    gx[4] = fma(T(2) * e[29], A[15], gx[4]);
+    gy[4] = fma(T(2) * e[29], A[13], gy[4]);
+    s[4] = fma(e[30], A[30], s[4]);
+    gx[4] = fma(T(2) * e[30], A[17], gx[4]);
+    gz[4] = fma(T(2) * e[30], A[14], gz[4]);
+    s[4] = fma(e[31], A[31], s[4]);
+    gy[4] = fma(T(2) * e[31], A[18], gy[4]);
+    gz[4] = fma(T(2) * e[31], A[16], gz[4]);
+    s[4] = fma(e[32], A[32], s[4]);
+    gx[4] = fma(T(2) * e[32], A[19], gx[4]);
+    gy[4] = fma(e[32], A[14], gy[4]);
+    gz[4] = fma(e[32], A[13], gz[4]);
+    s[4] = fma(e[33], A[33], s[4]);
+    gx[4] = fma(e[33], A[16], gx[4]);
+    gy[4] = fma(T(2) * e[33], A[19], gy[4]);
+    gz[4] = fma(e[33], A[15], gz[4]);
+    s[4] = fma(e[34], A[34], s[4]);
+    gx[4] = fma(e[34], A[18], gx[4]);
+    gy[4] = fma(e[34], A[17], gy[4]);
+    gz[4] = fma(T(2) * e[34], A[19], gz[4]);
   }
   template <typename T>
   static __device__ __forceinline__ void d3(const T* B, T* d) {

@@ -10,6 +10,8 @@ For each PA the generated structs hold
                          paired FP32 multiply-add);
   * ``Mono<PA>::grad``   gradient with respect to u of the polynomial
                          sum_x e_x A_x(u)  (used by the adjoint pair pass, Eq. 24c);
+  * ``Mono<PA>::dot_grad_deg``  sum_x e_x A_x and its gradient, split by the
+                         degree of x (design-matrix columns of D3 and D4_n00);
   * ``Mono<PA>::d3``     three-body contraction sum_l c_nl B_nl^2 per degree n
                          with the multinomial coefficients of Table 4 (Eq. 26a);
   * ``Four<PA>::desc``   four-body descriptors for every partition a >= b >= c
@@ -159,6 +161,28 @@ def gen_pa(PA):
             else:
                 L.append(f"    {gn[d]} = fma({lit(k)} * e[{x}], A[{lo}], {gn[d]});")
     L.append("    gx = g0; gy = g1; gz = g2;")
+    L.append("  }")
+    # --- degree-resolved dot and gradient: s[n] = sum_{x of degree n} e_x A_x and
+    # g[n] = sum_{x of degree n} e_x grad_u A_x (the adjoint rows of the three-body
+    # descriptors D3_n are supported on the monomials of degree n)
+    L.append("  template <typename T>")
+    L.append("  static __device__ __forceinline__ void dot_grad_deg(const T* e, const T* A, T* s, T* gx, T* gy, T* gz) {")
+    L.append(f"    for (int n = 0; n <= {PA}; ++n) {{ s[n] = T(0); gx[n] = T(0); gy[n] = T(0); gz[n] = T(0); }}")
+    gdn = ["gx", "gy", "gz"]
+    for x, ex in enumerate(mons):
+        n = sum(ex)
+        L.append(f"    s[{n}] = fma(e[{x}], A[{x}], s[{n}]);")
+        for d in range(3):
+            if ex[d] == 0:
+                continue
+            lower = list(ex)
+            lower[d] -= 1
+            lo = index[tuple(lower)]
+            k = ex[d]
+            if k == 1:
+                L.append(f"    {gdn[d]}[{n}] = fma(e[{x}], A[{lo}], {gdn[d]}[{n}]);")
+            else:
+                L.append(f"    {gdn[d]}[{n}] = fma({lit(k)} * e[{x}], A[{lo}], {gdn[d]}[{n}]);")
     L.append("  }")
     # --- d3 per degree
     L.append("  template <typename T>")

@@ -43,6 +43,7 @@ struct AtomLayout {
   int GA;   // per-atom stride of the staged (u, r), in Q4 units
   int AS;   // per-atom stride of the adjoint dE/dB (multiple of 4, odd number of 16-byte units)
   size_t off_geo, off_R, off_Rp, off_adj, off_e, off_cnt, off_V, off_D, off_J, warp_bytes;
+  size_t off_d3;   // design mode: D3_n per (atom, mode) of the warp
   int MS;   // per-atom stride of the staged descriptors (quadratic model)
 };
 
