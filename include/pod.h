@@ -431,7 +431,7 @@ int pod_set_embedding(pod_handle* h, const double* a, int degree, const double* 
 /* Launch-shape autotuner (a deployment feature; the paper has no counterpart).
  * Times the three phases of pod_energy_forces on `sys` (one configuration,
  * device positions as for pod_energy_forces; c: device [M]) for a small set of
- * candidate launch shapes -- warps per block of the neighbour search {2, 4, 8}
+ * candidate launch shapes -- warps per block of the neighbour search {2, 4, 6, 8}
  * each with block-wide candidate tests and with a warp per own atom,
  * of the fused atom kernel {1, 2, 4} (FP32 table path: each with and without R'
  * staged in shared memory), and, on the FP64 path, warps per block x blocks per
@@ -441,7 +441,7 @@ int pod_set_embedding(pod_handle* h, const double* a, int degree, const double* 
  * N)) and used by later calls on systems of that class; the other classes keep
  * the default shape (4, 2, 16x3).  Results do not depend on the shape except
  * for the rounding order of the energy and virial sums.  Synchronous (calls
- * pod_energy_forces about 15 x (reps + 1) times); not for use during stream
+ * pod_energy_forces about 25 x (reps + 1) times); not for use during stream
  * capture.
  *   shape (host int[6], or NULL): neighbour wpb, atom wpb, gather wpb, gather
  *   blocks per SM, and the form of the adjoint pair pass: 0 inside the fused atom

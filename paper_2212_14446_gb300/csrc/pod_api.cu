@@ -300,7 +300,7 @@ int pod_handle::autotune(const pod_system* sys, const double* c, int reps, cudaS
   LaunchShape cur{};
   double t[3];
   static const int atom_c[] = {1, 2, 4};
-  static const int neigh_c[] = {2, 4, 8};
+  static const int neigh_c[] = {2, 4, 6, 8};
   static const int gather_c[][2] = {{16, 3}, {16, 2}, {8, 6}, {8, 4}, {4, 12}};
   double best_atom = 1e30, best_neigh = 1e30, best_gather = 1e30;
   LaunchShape win = cur;
@@ -323,7 +323,7 @@ int pod_handle::autotune(const pod_system* sys, const double* c, int reps, cudaS
         }
       }
   for (int bw = 0; !rc_ && bw < 2; ++bw)
-    for (int n = 0; !rc_ && n < 3; ++n) {
+    for (int n = 0; !rc_ && n < 4; ++n) {
       LaunchShape s = win;
       s.neigh_wpb = neigh_c[n];
       s.neigh_blockwide = bw;
