@@ -528,6 +528,7 @@ def main():
             "clocks": clk,
             "wall_s": t_wall,
         }
+        line["roofline"].update(hbm_subentries(N, n_pairs, phase_avg, args.precision))
         print(json.dumps(line))
     if dist:
         dist.barrier()
@@ -683,6 +684,40 @@ def run_fit(args, rank, world, local):
 
 ATOM_KERNEL_SOURCES = ("atom_impl.cuh", "atom_f32.cu", "atom_f64.cu", "pod_common.cuh", "pod_kernels.h",
                        "gen_contract.py")
+
+
+def hbm_peak():
+    """Measured HBM copy bandwidth of the GB300s (generated file), else the
+    profiling recipe's fallback."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, ValueError, KeyError):
+        return 6800.0, "fallback"
+
+
+def hbm_subentries(N, n_pairs, phase_avg, precision):
+    """The step's memory-side kernels graded on HBM bandwidth with the algorithmic bytes
+    per atom of the method's cost model: the neighbour build (positions in, 24 B; the list
+    out, one 4-byte index per pair plus the count) and the force finalize / gather (mixed:
+    fixed-point force sums in, 32 B, FP64 forces out, 24 B; FP64: per pair the gradient
+    (32 B) and the reverse index (4 B) in, FP64 forces out).  `kernel_bytes_per_atom` is
+    what this build's kernels move instead where that differs (the mixed search writes a
+    16-byte displacement row per pair)."""
+    peak, basis = hbm_peak()
+    nb_alg = 24.0 + 4.0 * n_pairs + 4.0
+    nb_own = 24.0 + 24.0 + 32.0 + 16.0 + (16.0 if precision == "mixed" else 8.0) * n_pairs + 4.0
+    if precision == "mixed":
+        fin = 32.0 + 24.0
+    else:
+        fin = n_pairs * (32.0 + 4.0) + 24.0
+    out = {}
+    for key, ms, alg, own in (("neighbor", phase_avg[0], nb_alg, nb_own), ("finalize", phase_avg[2], fin, fin)):
+        gbs = alg * N / (ms / 1e3) / 1e9 if ms > 0 else None
+        out[key] = {"bound": "hbm", "bytes_per_atom": alg, "kernel_bytes_per_atom": own, "achieved": gbs,
+                    "peak": peak, "unit": "GB/s", "frac": (gbs / peak) if gbs else None,
+                    "peak_basis": basis, "phase_ms": ms}
+    return out
 
 
 def kernel_revision():

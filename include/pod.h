@@ -190,6 +190,15 @@ int pod_info(const pod_handle* h, int* M, int* Ns, int* K, double* Q_out, double
                                     atoms, shared-memory atomics per atom); 0 a warp per own
                                     atom (lanes over candidates, ballot compaction).  The lists
                                     are the same either way (sorted rows) */
+#define POD_OPT_FIT_GRAPH 10 /* pod_fit: 1 (default) a fit records its device chain (neighbour
+                                lists, design matrix, normal equations or QR, solve, residual)
+                                into a CUDA graph after it has run, and a later pod_fit with the
+                                same batch layout (sizes, offsets, boxes, periodicity), the same
+                                device arrays, options and handle settings replays the graph
+                                instead of issuing ~20 launches with host synchronisations
+                                between them; results are the same bits.  A replay whose lists
+                                no longer fit the recorded capacities falls back to the ordinary
+                                path.  Phase timing (POD_OPT_TIMING) disables recording.  0: off */
 int pod_set_option(pod_handle* h, int option, int value);
 
 /* Neighbour-list skin (A, default 0): lists are built with r_cut + skin and pairs
@@ -328,6 +337,10 @@ typedef struct {
  * POD_ECUDA. */
 int pod_fit(pod_handle* h, const pod_system* batch, const double* E_ref, const double* F_ref,
             const pod_fit_opts* opts, double* c_out, double* mae_E, double* mae_F);
+
+/* Number of pod_fit calls on this handle that replayed a recorded fit
+ * (POD_OPT_FIT_GRAPH).  POD_EINVAL on a null argument. */
+int pod_fit_replays(const pod_handle* h, int* replays);
 
 /* The fit in stages, for sharding configurations over several GPUs or processes
  * (the normal equations are additive over configurations):

@@ -32,6 +32,7 @@ POD_OPT_DESCRIPTORS = 6
 POD_OPT_GRAM = 7
 POD_OPT_ADJOINT = 8
 POD_OPT_NEIGHBOR_TESTS = 9
+POD_OPT_FIT_GRAPH = 10
 ERROR_NAMES = {0: "POD_OK", -1: "POD_EINVAL", -2: "POD_ENOMEM", -3: "POD_ECUDA", -4: "POD_ERANGE",
                -5: "POD_ENONFINITE", -6: "POD_ESINGULAR", -7: "POD_ENEIGH", -8: "POD_EIO"}
 
@@ -68,7 +69,7 @@ class pod_fit_opts(C.Structure):
 
 EXPORTS = ["pod_create", "pod_destroy", "pod_info", "pod_set_option", "pod_status", "pod_timing",
            "pod_neighbors", "pod_descriptors", "pod_energy_forces", "pod_energy_forces_host", "pod_fit",
-           "pod_fit_normal", "pod_fit_solve", "pod_fit_residual", "pod_descriptors_static",
+           "pod_fit_normal", "pod_fit_solve", "pod_fit_residual", "pod_fit_replays", "pod_descriptors_static",
            "pod_global_descriptors", "pod_descriptors_jvp", "pod_set_skin", "pod_md_step", "pod_fma_probe", "pod_autotune", "pod_set_quadratic",
            "pod_set_embedding", "pod_save", "pod_load", "pod_selftest_wait", "pod_halo_select", "pod_halo_add",
            "pod_descriptors_tangent", "pod_model_gradients", "pod_last_error"]
@@ -121,6 +122,7 @@ def lib():
                 "pod_halo_add": (C.c_int, [H, dp, ip, C.c_int, dp, C.c_int, vp]),
                 "pod_descriptors_tangent": (C.c_int, [H, S, dp, dp, vp]),
                 "pod_model_gradients": (C.c_int, [H, C.c_int, dp, dp, dp, C.c_double, dp, vp]),
+                "pod_fit_replays": (C.c_int, [H, ip]),
                 "pod_last_error": (C.c_char_p, [H]),
             }
             for name, (res, args) in sig.items():
@@ -446,6 +448,16 @@ class POD:
         """Neighbour search candidate tests: "auto" (launch shape / size),
         "blockwide" or "warp"."""
         pod_set_option(self.h, POD_OPT_NEIGHBOR_TESTS, {"auto": -1, "warp": 0, "blockwide": 1}[which])
+
+    def set_fit_graph(self, on: bool):
+        """pod_fit: record the fit's device chain and replay it on repeated calls (default on)."""
+        pod_set_option(self.h, POD_OPT_FIT_GRAPH, 1 if on else 0)
+
+    def fit_replays(self):
+        """Number of pod_fit calls on this handle served by a recorded fit."""
+        n = C.c_int(0)
+        _check(self.h, lib().pod_fit_replays(self.h, C.byref(n)))
+        return n.value
 
     def timing(self):
         return pod_timing(self.h)

@@ -639,16 +639,19 @@ int pod_handle::fit_gram_tc(double gamma, double* dG, double* dr, bool legacy_mm
   int2* dpairs = (int2*)(dex + 128);
   unsigned long long* pmax = (unsigned long long*)((unsigned char*)(dpairs + 64) + 256);
   double* apart = (double*)(pmax + (size_t)M * TC_COLBLK);
-  cudaError_t e = cudaMemcpy(dpairs, hp, sizeof(int) * 2 * np, cudaMemcpyHostToDevice);
-  if (e != cudaSuccess) return cuda_fail(e, "Gram slice pairs");
+  cudaError_t e = cudaSuccess;
+  if (!fit_capturing) {  // (a recorded fit reuses the pairs its first run uploaded)
+    e = cudaMemcpy(dpairs, hp, sizeof(int) * 2 * np, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(e, "Gram slice pairs");
+  }
   const double* AT = (const double*)fitA.p;
-  gram_colmax_kernel<<<dim3((unsigned)M, TC_COLBLK), 256, 0, nullptr>>>(R, AT, pmax);
-  gram_colexp_kernel<<<(M + 127) / 128, 128, 0, nullptr>>>(M, TC_COLBLK, pmax, dex);
+  gram_colmax_kernel<<<dim3((unsigned)M, TC_COLBLK), 256, 0, fit_st>>>(R, AT, pmax);
+  gram_colexp_kernel<<<(M + 127) / 128, 128, 0, fit_st>>>(M, TC_COLBLK, pmax, dex);
   const long long nel = (long long)Mp * RP;
   if (legacy_mma)
-    gram_slice_kernel<<<(unsigned)((nel + 255) / 256), 256, 0, nullptr>>>(M, Mp, R, RP, SLICES, AT, dex, VT);
+    gram_slice_kernel<<<(unsigned)((nel + 255) / 256), 256, 0, fit_st>>>(M, Mp, R, RP, SLICES, AT, dex, VT);
   else
-    gram_slice_tiled_kernel<<<(unsigned)((nel / 8 + 255) / 256), 256, 0, nullptr>>>(M, Mp, R, RP, SLICES, AT, dex,
+    gram_slice_tiled_kernel<<<(unsigned)((nel / 8 + 255) / 256), 256, 0, fit_st>>>(M, Mp, R, RP, SLICES, AT, dex,
                                                                                        VT);
   if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "Gram slicing");
   const dim3 grid((unsigned)np, (unsigned)splits);
@@ -658,14 +661,14 @@ int pod_handle::fit_gram_tc(double gamma, double* dG, double* dr, bool legacy_mm
     if (Mp == 112) {
       if ((e = grant_smem((const void*)gram_tc_kernel<7>, smem, granted7)) != cudaSuccess)
         return cuda_fail(e, "Gram shared memory");
-      gram_tc_kernel<7><<<grid, 2 * 7 * 32, smem, nullptr>>>(Mp, RP, splits, dpairs, VT, part);
+      gram_tc_kernel<7><<<grid, 2 * 7 * 32, smem, fit_st>>>(Mp, RP, splits, dpairs, VT, part);
     } else {
       if ((e = grant_smem((const void*)gram_tc_kernel<8>, smem, granted8)) != cudaSuccess)
         return cuda_fail(e, "Gram shared memory");
-      gram_tc_kernel<8><<<grid, 2 * 8 * 32, smem, nullptr>>>(Mp, RP, splits, dpairs, VT, part);
+      gram_tc_kernel<8><<<grid, 2 * 8 * 32, smem, fit_st>>>(Mp, RP, splits, dpairs, VT, part);
     }
   } else {
-    if ((e = cudaMemsetAsync(part, 0, part_bytes, nullptr)) != cudaSuccess) return cuda_fail(e, "Gram sums clear");
+    if ((e = cudaMemsetAsync(part, 0, part_bytes, fit_st)) != cudaSuccess) return cuda_fail(e, "Gram sums clear");
     // stages, 1,024 bytes of alignment slack, barriers, TMEM address and stop flag
     const size_t smem = (size_t)U_STAGES * (128 * 128 + Mp * 128) + 1024 + 8 * (2 * U_STAGES + 5) + 16;
     static size_t grantedu7[64] = {}, grantedu8[64] = {};
@@ -673,17 +676,17 @@ int pod_handle::fit_gram_tc(double gamma, double* dG, double* dr, bool legacy_mm
     if (Mp == 112) {
       if ((e = grant_smem((const void*)gram_umma_kernel<112>, smem, grantedu7)) != cudaSuccess)
         return cuda_fail(e, "Gram shared memory");
-      gram_umma_kernel<112><<<grid, U_THREADS, smem, nullptr>>>(nKB, splits, dpairs, VT, P, (int*)status.p);
+      gram_umma_kernel<112><<<grid, U_THREADS, smem, fit_st>>>(nKB, splits, dpairs, VT, P, (int*)status.p);
     } else {
       if ((e = grant_smem((const void*)gram_umma_kernel<128>, smem, grantedu8)) != cudaSuccess)
         return cuda_fail(e, "Gram shared memory");
-      gram_umma_kernel<128><<<grid, U_THREADS, smem, nullptr>>>(nKB, splits, dpairs, VT, P, (int*)status.p);
+      gram_umma_kernel<128><<<grid, U_THREADS, smem, fit_st>>>(nKB, splits, dpairs, VT, P, (int*)status.p);
     }
   }
   if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "Gram tensor-core kernel");
-  gram_tc_combine_kernel<<<(M * M + 255) / 256, 256, 0, nullptr>>>(M, Mp, np, psplits, dpairs, part, dex, gamma, dG);
-  atb_partial_kernel<<<dim3((unsigned)M, TC_COLBLK), 256, 0, nullptr>>>(R, AT, (const double*)fitb.p, apart);
-  atb_final_kernel<<<(M + 127) / 128, 128, 0, nullptr>>>(M, TC_COLBLK, apart, dr);
+  gram_tc_combine_kernel<<<(M * M + 255) / 256, 256, 0, fit_st>>>(M, Mp, np, psplits, dpairs, part, dex, gamma, dG);
+  atb_partial_kernel<<<dim3((unsigned)M, TC_COLBLK), 256, 0, fit_st>>>(R, AT, (const double*)fitb.p, apart);
+  atb_final_kernel<<<(M + 127) / 128, 128, 0, fit_st>>>(M, TC_COLBLK, apart, dr);
   if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "Gram assembly");
   return POD_OK;
 }

@@ -224,6 +224,8 @@ pod_handle::~pod_handle() {
   for (cudaEvent_t& e : ev)
     if (e) cudaEventDestroy(e);
   drop_host_graph();
+  if (fhost) cudaFreeHost(fhost);
+  if (fcap_st) cudaStreamDestroy(fcap_st);
 }
 
 bool pod_handle::HostKey::operator==(const HostKey& o) const {
@@ -239,6 +241,7 @@ void pod_handle::drop_host_graph() {
   if (hgraph) cudaGraphExecDestroy(hgraph);
   hgraph = nullptr;
   hkey_valid = false;
+  fit_graph_drop();  // a recorded fit holds buffer addresses too
 }
 
 int pod_handle::mark(int k, cudaStream_t st) {
@@ -492,6 +495,12 @@ int pod_set_option(pod_handle* h, int option, int value) {
     h->adj_force = value;
     return POD_OK;
   }
+  if (option == POD_OPT_FIT_GRAPH) {
+    if (value != 0 && value != 1) return h->fail(POD_EINVAL, "fit recording must be 0 or 1");
+    h->fit_off = value == 0;
+    if (h->fit_off) h->fit_graph_drop();
+    return POD_OK;
+  }
   if (option == POD_OPT_NEIGHBOR_TESTS) {
     if (value < -1 || value > 1) return h->fail(POD_EINVAL, "neighbour tests must be -1 (by shape), 0 or 1");
     h->neigh_force = value;
@@ -629,6 +638,11 @@ int pod_handle::read_status(cudaStream_t st) {
   last_status = s;
   e = cudaMemsetAsync(status.p, 0, sizeof(int), st);
   if (e != cudaSuccess) return cuda_fail(e, "status clear");
+  return status_error(s);
+}
+
+// The error a device status word stands for (POD_OK for 0).
+int pod_handle::status_error(int s) {
   if (s & (ST_NEIGH | ST_CELL)) return fail(POD_ENEIGH, "neighbour or cell capacity exceeded (status 0x%x)", s);
   if (s & ST_REV) return fail(POD_ENEIGH, "neighbour list is not symmetric (status 0x%x)", s);
   if (s & ST_NONFINITE) return fail(POD_ENONFINITE, "non-finite positions or results");
@@ -694,6 +708,7 @@ int pod_handle::plan_single(int N, const double box[3], const int pbc[3], Plan& 
 }
 
 int pod_handle::plan_batch(const pod_system* sys, Plan& pl) {
+  fit_graph_drop();  // the batch layout buffers below change under a recorded fit
   const int nc = sys->n_configs;
   const double rc = rlist();
   pl.N = sys->n_atoms;
@@ -756,6 +771,7 @@ int pod_handle::plan(const pod_system* sys, Plan& pl) {
 
 int pod_handle::build_neighbors(const double* pos, Plan& pl, bool need_rev, cudaStream_t st,
                                 unsigned long long* facc_zero, float4* pd, bool pad, bool* wrote_pd) {
+  pd_ok = false;  // a new list makes any earlier displacement rows stale
   if (wrote_pd) *wrote_pd = false;
   const int N = pl.N;
   int rc_;
@@ -946,7 +962,8 @@ int pod_handle::run_atoms(int mode, const Plan& pl, double* D, const double* c, 
     a.c = c;
     a.Ei = Ei_dst;
     a.g = nullptr;
-    a.pd = pd_ok ? (const float4*)pdisp.p : nullptr;
+    // displacement rows: energy modes only, of the list built by this call
+    a.pd = (pd_ok && (mode == 1 || mode == 4 || mode == 5)) ? (const float4*)pdisp.p : nullptr;
     a.facc = (unsigned long long*)facc.p;
     a.qbeta = (const float*)qS32.p;
     a.emb_a = (const double*)embW.p;

@@ -140,6 +140,39 @@ struct pod_handle {
   DevBuf halo_cnt;  // pod_halo_select: count of the selected atoms
   DevBuf mgrad;     // pod_model_gradients: per-block partial sums, then the result
   int fit_residual_dev(double* sumE, double* sumF);
+  // The plan of the last fit_build, from which its launches can be issued again
+  // (fit_design_launch) and recorded into a CUDA graph.
+  struct FitCtx {
+    Plan pl;
+    const double* pos = nullptr;
+    const double* E_ref = nullptr;
+    const double* F_ref = nullptr;
+    pod_fit_opts o{};
+    int qchunk = 1, nch = 0, nrows2 = 0;
+    long long R = 0;
+  } fctx;
+  int fit_design_launch();
+  int* fit_info_dev();
+  int fit_solve_launch();
+  int fit_qr_launch(double gamma);
+  int fit_residual_launch();
+  void fit_residual_sums(const double* res, double* sumE, double* sumF) const;
+  cudaStream_t fit_st = nullptr;  // stream of the fit's launches: the legacy stream, or the recording stream
+  bool fit_capturing = false;     // recording: no host synchronisation, no uploads
+  // Recorded fit: repeated pod_fit calls with the same batch layout, buffers,
+  // options and settings replay one CUDA graph of the whole device chain.
+  cudaGraphExec_t fgraph = nullptr;
+  cudaStream_t fcap_st = nullptr;
+  std::vector<unsigned long long> fkey;
+  void* fhost = nullptr;  // pinned: status, pivot status, residual sums, c
+  int fit_replays = 0;    // fits served by a replay (pod_fit_replays)
+  bool fit_off = false;   // POD_OPT_FIT_GRAPH = 0: no recording
+  std::vector<unsigned long long> fit_key(const pod_system* b, const double* E_ref, const double* F_ref,
+                                          const pod_fit_opts& o) const;
+  int fit_record(const std::vector<unsigned long long>& key);
+  int fit_replay(const pod_fit_opts& o, double* c_out, double* mae_E, double* mae_F, bool& redo);
+  void fit_graph_drop();
+  int status_error(int s);
   long long fit_R = 0;
   int fit_nc = 0, fit_N = 0;
   double fit_wE = 0, fit_wF = 0;
