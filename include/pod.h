@@ -465,7 +465,12 @@ int pod_set_embedding(pod_handle* h, const double* a, int degree, const double* 
  *   cell's block over candidates x the cell's own atoms), 0 a warp per own atom.
  *   ms (host double[3], or NULL): mean times of the neighbour, atom and gather
  *   phases with the chosen shape.
- * Errors as pod_energy_forces; POD_EINVAL for a batch. */
+ * A batch (n_configs > 1) tunes the fit's design pass instead: the atom kernel in
+ * design mode {1, 2, 4} warps per block and the force-row gather {2, 4, 8}, timed
+ * around the design-matrix stage of pod_fit with zero labels (c may be NULL);
+ * shape then holds (0, atom wpb, gather wpb, 0, 0, 0) and ms[1] the stage's time;
+ * later fits of batches of that size class use it (results do not depend on it).
+ * Errors as pod_energy_forces / pod_fit. */
 int pod_autotune(pod_handle* h, const pod_system* sys, const double* c, int reps, int* shape, double* ms,
                  void* stream);
 

@@ -449,6 +449,12 @@ class POD:
         "blockwide" or "warp"."""
         pod_set_option(self.h, POD_OPT_NEIGHBOR_TESTS, {"auto": -1, "warp": 0, "blockwide": 1}[which])
 
+    def autotune_fit(self, pos_soa, offs, boxes, pbcs, reps=3, stream=None):
+        """Tune the fit's design pass on a device batch (pod_autotune with a batch);
+        returns {"atom_wpb", "design_wpb", "ms"}."""
+        shape, ms = pod_autotune(self.h, self.batch_system(pos_soa, offs, boxes, pbcs), None, reps, stream)
+        return {"atom_wpb": shape[1], "design_wpb": shape[2], "ms": ms[1]}
+
     def set_fit_graph(self, on: bool):
         """pod_fit: record the fit's device chain and replay it on repeated calls (default on)."""
         pod_set_option(self.h, POD_OPT_FIT_GRAPH, 1 if on else 0)

@@ -397,6 +397,8 @@ int pod_handle::fit_build(const pod_system* bsys, const double* E_ref, const dou
   if ((rc_ = mark(0, st))) return rc_;  // timing phases: neighbours, design matrix, Gram, solve
   for (;;) {
     if ((rc_ = plan_batch(&sys, pl))) break;
+    auto tf = tuned_fit.find(size_class(N));  // design-pass shapes from the batch tuner
+    pl.shape = tf != tuned_fit.end() ? tf->second : LaunchShape{};
     if ((rc_ = build_neighbors(sys.pos, pl, true, st))) break;
     bool retry;
     if ((rc_ = finish(st, pl, retry))) break;
@@ -470,7 +472,7 @@ int pod_handle::fit_design_launch() {
     dm_q1 = std::min(Qd, q0 + qchunk);
     rc_ = run_atoms(3, pl, q0 == 0 ? (double*)Dws.p : nullptr, nullptr, nullptr, st);
     if (rc_) return rc_;
-    const int wpb = 8;
+    const int wpb = pl.shape.design_wpb;
     const unsigned blocks = (unsigned)((N + wpb - 1) / wpb);
     if (precision == POD_MIXED)
       design_gather_kernel<float><<<blocks, wpb * 32, 0, st>>>(

@@ -278,7 +278,7 @@ int pod_handle::autotune(const pod_system* sys, const double* c, int reps, cudaS
                          double ms[3]) {
   int rc_ = validate_system(sys);
   if (rc_) return rc_;
-  if (sys->n_configs > 1) return fail(POD_EINVAL, "autotune takes a single configuration");
+  if (sys->n_configs > 1) return autotune_fit(sys, reps, best, ms);
   if (!c) return fail(POD_EINVAL, "coefficients are required");
   if (reps < 1) reps = 5;
   if ((rc_ = ensure(E_out, sizeof(double), "energy"))) return rc_;
@@ -368,10 +368,84 @@ int pod_handle::autotune(const pod_system* sys, const double* c, int reps, cudaS
   return POD_OK;
 }
 
+// Batch form of the tuner: the fit's design pass (atom kernel in design mode and
+// the force-row gather), timed with CUDA events around the design-matrix stage
+// of pod_fit (zero labels) for atom-kernel warps per block {1, 2, 4} and gather
+// warps per block {2, 4, 8} (coordinate search); the winner serves later fits
+// of batches of the same size class.
+int pod_handle::autotune_fit(const pod_system* sys, int reps, LaunchShape& best, double ms[3]) {
+  if (reps < 1) reps = 3;
+  const int cls = size_class(sys->n_atoms);
+  const long long rows = (long long)sys->n_configs + 3LL * sys->n_atoms;
+  int rc_;
+  if ((rc_ = ensure(tune_ref, sizeof(double) * (size_t)rows, "tuning labels"))) return rc_;
+  cudaError_t e = cudaMemset(tune_ref.p, 0, sizeof(double) * (size_t)rows);
+  if (e != cudaSuccess) return cuda_fail(e, "tuning labels");
+  const double* Er = (const double*)tune_ref.p;
+  const double* Fr = Er + sys->n_configs;
+  const pod_fit_opts o{100.0, 1.0, 1e-12, 1, 0};
+  const int keep_timing = timing;
+  timing = 0;
+  cudaEvent_t t0 = nullptr, t1 = nullptr;
+  if (cudaEventCreate(&t0) != cudaSuccess || cudaEventCreate(&t1) != cudaSuccess) {
+    if (t0) cudaEventDestroy(t0);
+    timing = keep_timing;
+    return cuda_fail(cudaGetLastError(), "tuning events");
+  }
+  auto measure = [&](const LaunchShape& s, double& out) -> int {
+    tuned_fit[cls] = s;
+    int r = fit_build(sys, Er, Fr, o);  // warm-up (sizes the workspace)
+    if (r) return r;
+    float acc = 0.f;
+    for (int i = 0; i < reps && !r; ++i) {
+      cudaEventRecord(t0, nullptr);
+      r = fit_build(sys, Er, Fr, o);
+      cudaEventRecord(t1, nullptr);
+      if (cudaEventSynchronize(t1) != cudaSuccess) return cuda_fail(cudaGetLastError(), "tuning events");
+      float m = 0.f;
+      cudaEventElapsedTime(&m, t0, t1);
+      acc += m;
+    }
+    out = acc / reps;
+    return r;
+  };
+  static const int atom_c[] = {1, 2, 4};
+  static const int gather_c[] = {2, 4, 8};  // the gather is bounded to 256 threads a block
+  LaunchShape win{};
+  double best_ms = 1e30, t = 0;
+  for (int a : atom_c) {
+    LaunchShape s = win;
+    s.atom_wpb = a;
+    if ((rc_ = measure(s, t))) break;
+    if (t < best_ms) { best_ms = t; win.atom_wpb = a; }
+  }
+  for (int k = 0; !rc_ && k < 3; ++k) {
+    LaunchShape s = win;
+    s.design_wpb = gather_c[k];
+    if ((rc_ = measure(s, t))) break;
+    if (t < best_ms) { best_ms = t; win.design_wpb = gather_c[k]; }
+  }
+  cudaEventDestroy(t0);
+  cudaEventDestroy(t1);
+  timing = keep_timing;
+  fit_R = 0;  // the tuning design matrices are not a fit's
+  if (rc_) {
+    tuned_fit.erase(cls);
+    return rc_;
+  }
+  tuned_fit[cls] = win;
+  ++tune_gen;
+  best = win;
+  ms[0] = 0.0;
+  ms[1] = best_ms;
+  ms[2] = 0.0;
+  return POD_OK;
+}
+
 std::vector<DevBuf*> pod_handle::all_bufs() {
   return {&cell_count, &cell_atoms, &wpos, &phi, &plo, &nbr_count, &nbr_j, &nbr_s, &rev, &g, &Ei,
           &Wat, &status, &offs, &pos_in, &c_in, &E_out, &F_out, &W_out, &Ei_out, &fitA, &fitG, &fitb,
-          &fitwork, &cfg_of, &boxes, &rtab, &wpart, &Dws, &chunks, &cpart, &wrapk, &gdm, &dmG, &facc, &qS32, &qS64, &pdisp, &adjb, &qrw, &halo_cnt, &mgrad,
+          &fitwork, &cfg_of, &boxes, &rtab, &wpart, &Dws, &chunks, &cpart, &wrapk, &gdm, &dmG, &facc, &qS32, &qS64, &pdisp, &adjb, &qrw, &halo_cnt, &mgrad, &tune_ref,
           &embW};
 }
 
@@ -574,7 +648,12 @@ int pod_autotune(pod_handle* h, const pod_system* sys, const double* c, int reps
   double t[3] = {0, 0, 0};
   const int rc = h->autotune(sys, c, reps, (cudaStream_t)stream, best, t);
   if (rc) return rc;
-  if (shape) {
+  if (shape && sys && sys->n_configs > 1) {  // batch: the fit's design pass
+    shape[0] = 0;
+    shape[1] = best.atom_wpb;
+    shape[2] = best.design_wpb;
+    shape[3] = shape[4] = shape[5] = 0;
+  } else if (shape) {
     shape[0] = best.neigh_wpb;
     shape[1] = best.atom_wpb;
     shape[2] = best.gather_wpb;

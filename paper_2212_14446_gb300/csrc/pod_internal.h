@@ -61,6 +61,9 @@ struct pod_handle {
   int timing = 0;
   cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
   std::map<int, fastpod::LaunchShape> tuned;  // autotuned launch shapes by size class (floor log2 N)
+  std::map<int, fastpod::LaunchShape> tuned_fit;  // the fit's design-pass shapes by size class of the batch
+  DevBuf tune_ref;  // zero labels for timing the fit's design pass
+  int autotune_fit(const pod_system* sys, int reps, fastpod::LaunchShape& best, double ms[3]);
   int tune_gen = 0;                            // bumped by every autotune (invalidates host graphs)
   // host-buffer entry point: one CUDA graph (copies in, step, copies out, status)
   // replayed while calls repeat with the same buffers, sizes, box and settings

@@ -34,6 +34,7 @@ struct LaunchShape {
   int atom_rp = 0;  // table path: stage R' in shared memory in the pair pass (else re-evaluate it)
   int atom_split = -1;  // mixed linear path: 1 adjoint pair pass as its own kernel, 0 fused, -1 by size
   int neigh_blockwide = -1;  // block-per-cell search: 1 block-wide candidate tests, 0 a warp per atom, -1 by size
+  int design_wpb = 8;        // fit: warps per block of the force-row gather
 };
 
 struct AtomLayout {

@@ -63,16 +63,18 @@ def test_every_candidate_shape_gives_the_same_forces(pkg):
         assert torch.equal(pod.energy_forces(x, cfg.box, c)["F"], ref)
 
 
-def test_autotune_rejects_a_batch(pkg):
+def test_batch_tuner_refuses_what_the_fit_refuses(pkg):
+    """A batch goes to the fit's tuner, which refuses what pod_fit refuses (the
+    exclusive three-body set)."""
     p = synth.params_small()
     pod = pkg.POD(p, precision="fp64")
+    pod.set_descriptor_set("exclusive")
     cfgs = [synth.config_small(replica=r) for r in range(2)]
     pos, offs, boxes, pbcs = pod.pack_batch(cfgs)
     xs = torch.tensor(pos, device="cuda")
     sysd = pod.batch_system(xs, offs, boxes, pbcs)
-    c = torch.tensor(synth.coefficients(pod.M, 64), device="cuda")
     with pytest.raises(pkg.PodError) as ei:
-        pkg.pod_autotune(pod.h, sysd, c)
+        pkg.pod_autotune(pod.h, sysd, None)
     assert ei.value.code == pkg.POD_EINVAL
 
 
@@ -103,3 +105,29 @@ def test_separate_adjoint_kernel_equals_fused(pkg, which):
         assert torch.equal(sep["Ei"], fused["Ei"])
         assert sep["E"].item() == fused["E"].item()  # exact fixed-point sum of the same E_i
         assert torch.allclose(sep["W"], fused["W"], rtol=0, atol=1e-5 * fused["W"].abs().max().item())
+
+
+def test_batch_tuner_picks_design_shapes_with_the_same_fit(pkg):
+    """pod_autotune on a batch tunes the fit's design pass; the fit afterwards
+    gives the same bits as on an untuned handle."""
+    p = synth.params_full()
+    cfgs = []
+    k = 0
+    while len(cfgs) < 30:
+        cf = synth.config_train(k, 71)
+        k += 1
+        if cf.n <= 60:
+            cfgs.append(cf)
+    pod = pkg.POD(p, precision="mixed")
+    teacher = pkg.POD(p, precision="fp64", Q=pod.Q)
+    out = teacher.energy_forces_batch(cfgs, torch.tensor(synth.coefficients(pod.M, 72)))
+    pos, offs, boxes, pbcs = pod.pack_batch(cfgs)
+    x = torch.tensor(pos, dtype=torch.float64, device="cuda")
+    Er = out["E"].to("cuda").contiguous()
+    Fr = out["F"].to("cuda").t().contiguous()
+    ref = pkg.POD(p, precision="mixed", Q=pod.Q)
+    c_ref, _, _ = ref.fit_device(x, offs, boxes, pbcs, Er, Fr)
+    t = pod.autotune_fit(x, offs, boxes, pbcs, reps=1)
+    assert t["atom_wpb"] in (1, 2, 4) and t["design_wpb"] in (2, 4, 8) and t["ms"] > 0
+    c, _, _ = pod.fit_device(x, offs, boxes, pbcs, Er, Fr)
+    assert np.array_equal(c, c_ref)
