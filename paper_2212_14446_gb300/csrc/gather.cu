@@ -198,16 +198,24 @@ __global__ void __launch_bounds__(256)
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < N; k += gridDim.x * blockDim.x) {
     const ulonglong2 a = *reinterpret_cast<const ulonglong2*>(facc + 4 * (size_t)k);
     const unsigned long long b = facc[4 * (size_t)k + 2];
-    F[k] = sc * (double)(long long)a.x;
-    F[(size_t)N + k] = sc * (double)(long long)a.y;
-    F[(size_t)2 * N + k] = sc * (double)(long long)b;
+    if (fscale == 1.0) {  // x 2^-32 by integer operations (the same bits, off the FP64 pipe)
+      F[k] = fixed_to_double((long long)a.x, -32);
+      F[(size_t)N + k] = fixed_to_double((long long)a.y, -32);
+      F[(size_t)2 * N + k] = fixed_to_double((long long)b, -32);
+    } else {
+      F[k] = sc * (double)(long long)a.x;
+      F[(size_t)N + k] = sc * (double)(long long)a.y;
+      F[(size_t)2 * N + k] = sc * (double)(long long)b;
+    }
   }
 }
 
 constexpr int FINALIZE_THREADS = 256;
+// One atom per thread (a streaming pass: every thread's loads in flight at once),
+// at most 64 blocks per SM's worth, striding beyond that.
 int finalize_blocks(int N) {
   const int want = (N + FINALIZE_THREADS - 1) / FINALIZE_THREADS;
-  return want < 8 * 152 ? (want > 0 ? want : 1) : 8 * 152;
+  return want < 64 * 152 ? (want > 0 ? want : 1) : 64 * 152;
 }
 
 cudaError_t launch_finalize(int N, const unsigned long long* facc, double* F, double fscale, int nblocks, double* E,

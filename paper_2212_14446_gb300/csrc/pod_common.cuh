@@ -127,6 +127,43 @@ struct CfgBox {
 };
 
 // ------------------------------------------------ packed image shift
+// x * 2^e as a double, rounded to nearest even exactly as (double)x * 2^e is
+// (x a 64-bit integer with |x| < 2^63; e such that nonzero results stay normal),
+// with integer operations only: the FP64 pipe, slow on this part, bounds a
+// streaming pass that converts three fixed-point values per atom through it.
+__host__ __device__ __forceinline__ double fixed_to_double(long long x, int e) {
+  if (x == 0) return 0.0;
+  const unsigned long long sign = x < 0 ? (1ull << 63) : 0ull;
+  unsigned long long m = x < 0 ? 0ull - (unsigned long long)x : (unsigned long long)x;
+#ifdef __CUDA_ARCH__
+  int p = 63 - __clzll((long long)m);  // position of the leading one
+#else
+  int p = 63 - __builtin_clzll(m);
+#endif
+  unsigned long long q;
+  if (p <= 52) {
+    q = m << (52 - p);
+  } else {  // round the bits below the 53 kept ones to nearest even
+    const int sh = p - 52;
+    const unsigned long long rem = m & ((1ull << sh) - 1ull), half = 1ull << (sh - 1);
+    q = m >> sh;
+    if (rem > half || (rem == half && (q & 1ull))) ++q;
+    if (q >> 53) {  // the rounding carried into a new leading bit
+      q >>= 1;
+      ++p;
+    }
+  }
+  const unsigned long long bits = sign | ((unsigned long long)(p + 1023 + e) << 52) | (q & ((1ull << 52) - 1ull));
+#ifdef __CUDA_ARCH__
+  return __longlong_as_double((long long)bits);
+#else
+  double d;
+  static_assert(sizeof(d) == sizeof(bits), "64-bit double");
+  __builtin_memcpy(&d, &bits, sizeof(d));
+  return d;
+#endif
+}
+
 __host__ __device__ __forceinline__ int shift_pack(int sx, int sy, int sz) {
   return ((sx + 128) << 16) | ((sy + 128) << 8) | (sz + 128);
 }
