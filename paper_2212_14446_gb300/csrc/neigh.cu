@@ -405,9 +405,9 @@ __global__ void __launch_bounds__(NEIGH_MAX_WPB * 32)
   } else {
     __syncthreads();
   }
-  float Ll[3];
-#pragma unroll
-  for (int d = 0; d < 3; ++d) Ll[d] = __double2float_rn(cg.L[d] - (double)cg.Lf[d]);
+  // (the box's low part comes with the grid: formed per thread in FP64 it had
+  // occupied the slow FP64 pipe of every block)
+  const float* Ll = cg.Ll;
   for (int a = warp; a < own_n; a += nwarps) {
     const int i = __float_as_int(cand[own0 + a].w);
     // BLOCKWIDE: the atom's own key list; else this warp's list, filled here by

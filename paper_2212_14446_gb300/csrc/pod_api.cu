@@ -745,6 +745,7 @@ int pod_handle::plan_single(int N, const double box[3], const int pbc[3], Plan& 
     if (!(L >= 0) || !std::isfinite(L)) return fail(POD_EINVAL, "box length %d is not finite", d);
     cg.L[d] = L;
     cg.Lf[d] = (float)L;
+    cg.Ll[d] = (float)(L - (double)cg.Lf[d]);
     int nc = L > 0 ? (int)std::floor(L / (rc * (1.0 + 1e-9))) : 1;
     nc = std::max(1, std::min(nc, 1024));
     cg.nc[d] = nc;

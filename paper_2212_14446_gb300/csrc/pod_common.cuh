@@ -112,6 +112,7 @@ struct CellGrid {
   int pbc[3];
   double L[3];    // box lengths
   float Lf[3];    // box lengths rounded to FP32 (image offsets of the FP32 prefilter)
+  float Ll[3];    // L - Lf rounded to FP32 (low part of the box for double-float displacements)
   double inv_cs[3];
   int ncells;
   int cap;        // atoms per cell
