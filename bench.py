@@ -471,13 +471,14 @@ def main():
     Wh = torch.zeros(9, dtype=torch.float64).pin_memory().numpy()
     import ctypes as C
     hsys = pkg.make_system(pos_h.ctypes.data_as(C.POINTER(C.c_double)), N, box)
+    call = pkg.HostEnergyForces(pod.h, hsys, c_h, Eh, Eih, Fh, Wh, stream=stream)  # the public repeated-call form
     for _ in range(3):
-        pkg.pod_energy_forces_host(pod.h, hsys, c_h, Eh, Eih, Fh, Wh, stream=stream)
+        call()
     if dist:
         dist.barrier()
     te0 = time.perf_counter()
     for k in range(args.steps):
-        pkg.pod_energy_forces_host(pod.h, hsys, c_h, Eh, Eih, Fh, Wh, stream=stream)
+        call()
     te = time.perf_counter() - te0
     if dist:
         t = torch.tensor([te], dtype=torch.float64, device=dev)

@@ -285,6 +285,25 @@ def pod_energy_forces_host(h, sys, c, E, Ei=None, F=None, W=None, stream=None):
                                            _stream(stream)))
 
 
+class HostEnergyForces:
+    """pod_energy_forces_host on fixed host arrays, called repeatedly (an MD driver,
+    a benchmark): the pointers and the stream are marshalled once, so each call
+    costs one foreign call.  The arrays and `sys` must stay alive and in place."""
+
+    def __init__(self, h, sys, c, E, Ei=None, F=None, W=None, stream=None):
+        def hp(a):
+            return C.c_void_p(None if a is None else a.ctypes.data)
+        self.h = h
+        self._keep = (sys, c, E, Ei, F, W, stream)
+        self._fn = lib().pod_energy_forces_host
+        self._args = (h, C.byref(sys), hp(c), hp(E), hp(Ei), hp(F), hp(W), _stream(stream))
+
+    def __call__(self):
+        rc = self._fn(*self._args)
+        if rc != POD_OK:
+            raise PodError(rc, pod_last_error(self.h))
+
+
 def pod_neighbors(h, sys, cap, count, nbr, shift, stream=None):
     _check(h, lib().pod_neighbors(h, C.byref(sys), int(cap), _iptr(count), _iptr(nbr), _iptr(shift),
                                   _stream(stream)))

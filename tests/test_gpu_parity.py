@@ -481,10 +481,14 @@ def test_host_entry_graph_replay(pkg, prec):
     pos_h, c_h, E_h, Ei_h, F_h, W_h = (t.numpy() for t in (pos_t, c_t, E_t, Ei_t, F_t, W_t))
     sysd = pkg.make_system(pos_h.ctypes.data_as(C.POINTER(C.c_double)), n, cfg.box)
     rng = synth.rng(93)
+    prepared = pkg.HostEnergyForces(pod.h, sysd, c_h, E_h, Ei_h, F_h, W_h, stream=s)
     for call in range(6):
         if call == 4:  # new positions in the same buffer: the replay must copy them in
             pos_h[...] = np.ascontiguousarray((cfg.pos + rng.normal(0, 0.02, size=cfg.pos.shape)).T)
-        pkg.pod_energy_forces_host(pod.h, sysd, c_h, E_h, Ei_h, F_h, W_h, stream=s)
+        if call % 2:  # the prepared repeated-call form, the same entry point
+            prepared()
+        else:
+            pkg.pod_energy_forces_host(pod.h, sysd, c_h, E_h, Ei_h, F_h, W_h, stream=s)
         dev = pod.energy_forces(torch.tensor(pos_h, device=DEV), cfg.box, torch.tensor(c, device=DEV))
         assert E_h[0] == dev["E"].item(), call
         assert np.array_equal(F_h.T, dev["F"].cpu().numpy()), call
