@@ -2,6 +2,7 @@
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <type_traits>
 
 namespace fastpod {
 
@@ -247,6 +248,15 @@ __device__ __forceinline__ Q4<float> ldg_q4(const Q4<float>* p) {
 }
 __device__ __forceinline__ Q4<double> ldg_q4(const Q4<double>* p) { return *p; }
 
+// Two consecutive table entries with one 256-bit read-only load (sm_100 and
+// later; p 32-byte aligned): half the load instructions, and half the L1
+// wavefronts, of two 128-bit loads of lanes that each read a different row.
+__device__ __forceinline__ void ldg_q4x2(const Q4<float>* p, Q4<float>& a, Q4<float>& b) {
+  asm volatile("ld.global.nc.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=f"(a.x), "=f"(a.y), "=f"(a.z), "=f"(a.w), "=f"(b.x), "=f"(b.y), "=f"(b.z), "=f"(b.w)
+               : "l"(p));
+}
+
 // ------------------------------------------------ radial basis of one pair
 // R_k(r) = sum_l Q_lk Phi_l(r) and R'_k(r), Phi_l = f_c psi_l (Eq. 3-12).
 // KT is a compile-time bound on K (K = KT in the specialised kernels).
@@ -257,6 +267,20 @@ __device__ __forceinline__ void radial_pair(const RadialConst<T>& rc, T r, T* R,
     const int g = min((int)tr, rc.tab_n - 1);
     const T t = tr - T(g);
     const Q4<T>* row = rc.tab + (size_t)g * rc.K;
+    if constexpr (std::is_same<T, float>::value && KT != MAXK && KT % 2 == 0) {
+      // rows of an even number of 16-byte entries start on 32 bytes (the table
+      // itself is 256-byte aligned): entries in pairs
+#pragma unroll
+      for (int k = 0; k < KT; k += 2) {
+        Q4<T> q0, q1;
+        ldg_q4x2(row + k, q0, q1);
+        R[k] = fma(t, fma(t, fma(t, q0.w, q0.z), q0.y), q0.x);
+        Rp[k] = fma(t, fma(t * T(3), q0.w, T(2) * q0.z), q0.y) * rc.tab_inv_h;
+        R[k + 1] = fma(t, fma(t, fma(t, q1.w, q1.z), q1.y), q1.x);
+        Rp[k + 1] = fma(t, fma(t * T(3), q1.w, T(2) * q1.z), q1.y) * rc.tab_inv_h;
+      }
+      return;
+    }
 #pragma unroll
     for (int k = 0; k < KT; ++k) {
       if (KT == MAXK && k >= rc.K) {
