@@ -356,7 +356,9 @@ __global__ void __launch_bounds__(ATOM_MAX_WPB * 32, atom_min_blocks<T, MODE, KT
       const Q4<T>* ga = geo + a_loc * lay.GA;
       const T* Ra = sR + a_loc * lay.SA + m;
       if constexpr (std::is_same<T, float>::value) {
-        // paired FP32 multiply-add: two basis components per instruction
+        // paired FP32 multiply-add: two basis components per instruction (two pairs
+        // per iteration, so that their shared-memory reads overlap)
+#pragma unroll 2
         for (int jj = 0; jj < nc; ++jj) {
           const Q4<T> u = ga[jj];
           const float R = Ra[jj * lay.KS];
