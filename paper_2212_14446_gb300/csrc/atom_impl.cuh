@@ -528,9 +528,17 @@ __global__ void __launch_bounds__(ATOM_MAX_WPB * 32, atom_min_blocks<T, MODE, KT
           const T ir = T(1) / u.w;
           const T* adj = sadj + a * lay.AS;
           T* out = p.gdm + (((size_t)(q - p.q0) * p.N + i) * p.cap + slot) * (size_t)K * 3;
+          // modes one at a time (a rolled loop: the unrolled body overflowed the
+          // instruction cache); R and R' of the mode selected, not indexed
+#pragma unroll 1
+          for (int mm = 0; mm < K; ++mm) {
+            T Rsel = Rv[0], Rpsel = Rpv[0];
 #pragma unroll
-          for (int mm = 0; mm < KT; ++mm) {
-            if (KT == MAXK && mm >= K) break;
+            for (int k = 1; k < KT; ++k)
+              if (k == mm) {
+                Rsel = Rv[k];
+                Rpsel = Rpv[k];
+              }
             T am_[NAP];
             const Q4<T>* a4 = reinterpret_cast<const Q4<T>*>(adj + mm * NAP);
 #pragma unroll
@@ -547,7 +555,7 @@ __global__ void __launch_bounds__(ATOM_MAX_WPB * 32, atom_min_blocks<T, MODE, KT
             T gx, gy, gz;
             Mono<PA>::grad(am_, Am, gx, gy, gz);
             const T ug = u.x * gx + u.y * gy + u.z * gz;
-            const T s1 = Rpv[mm] * dot, s2 = Rv[mm] * ir;
+            const T s1 = Rpsel * dot, s2 = Rsel * ir;
             out[3 * mm + 0] = fma(s1, u.x, s2 * (gx - ug * u.x));
             out[3 * mm + 1] = fma(s1, u.y, s2 * (gy - ug * u.y));
             out[3 * mm + 2] = fma(s1, u.z, s2 * (gz - ug * u.z));
