@@ -199,6 +199,10 @@ int pod_info(const pod_handle* h, int* M, int* Ns, int* K, double* Q_out, double
                                 between them; results are the same bits.  A replay whose lists
                                 no longer fit the recorded capacities falls back to the ordinary
                                 path.  Phase timing (POD_OPT_TIMING) disables recording.  0: off */
+#define POD_OPT_HOST_MAPPED 11 /* pod_energy_forces_host replays: 1 (default) the kernels read
+                                  and write mapped pinned host buffers directly (on Grace,
+                                  coherent over NVLink-C2C); 0 copy nodes into and out of
+                                  library-owned device buffers.  Results are the same bits */
 int pod_set_option(pod_handle* h, int option, int value);
 
 /* Neighbour-list skin (A, default 0): lists are built with r_cut + skin and pairs
@@ -306,7 +310,14 @@ int pod_model_gradients(pod_handle* h, int n_atoms, const double* D, const doubl
 
 /* pod_energy_forces with HOST buffers: sys->pos, c, E, Ei, F, W are host
  * pointers (pinned memory is fastest).  Copies inputs to library-owned device
- * buffers, computes, copies results back and waits for the stream. */
+ * buffers, computes, copies results back and waits for the stream.  Calls that
+ * repeat with the same pinned buffers, size, box and settings on a non-default
+ * stream replay a CUDA graph from the third call on; with POD_OPT_HOST_MAPPED
+ * (default) and buffers mapped into the device's address space (pinned memory
+ * under unified addressing), that graph's kernels read the positions and
+ * coefficients and write E, Ei, F and W through the buffers' device addresses
+ * instead of copying them (same bits).  The buffers must hold the documented
+ * sizes either way. */
 int pod_energy_forces_host(pod_handle* h, const pod_system* sys, const double* c, double* E, double* Ei,
                            double* F, double* W, void* stream);
 

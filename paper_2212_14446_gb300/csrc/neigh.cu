@@ -16,8 +16,12 @@ namespace fastpod {
 __global__ void bin_kernel(int N, const double* __restrict__ pos, CellGrid cg, double* __restrict__ wpos,
                            float4* __restrict__ phi, float4* __restrict__ plo, int* __restrict__ cell_count,
                            float4* __restrict__ cell_pos, int* __restrict__ wrapk, int* __restrict__ status,
-                           unsigned long long* __restrict__ facc, int* __restrict__ nbr_count) {
+                           unsigned long long* __restrict__ facc, int* __restrict__ nbr_count,
+                           const double* __restrict__ csrc, double* __restrict__ cdst, int cn) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  // an optional copy of cn values (the coefficients of a host-buffer call, read
+  // through the pinned buffer's device address) rides on this launch
+  for (int q = i; q < cn; q += gridDim.x * blockDim.x) cdst[q] = csrc[q];
   if (i >= N) return;
   if (facc) {  // fixed-point force, energy and virial accumulators of this call start at zero
     ulonglong2* fz = reinterpret_cast<ulonglong2*>(facc + 4 * (size_t)i);
@@ -597,10 +601,10 @@ __global__ void export_neighbors_kernel(int N, int cap, const int* __restrict__ 
 // ------------------------------------------------------------ launchers
 cudaError_t launch_bin(int N, const double* pos, const CellGrid& cg, double* wpos, float4* phi, float4* plo,
                        int* cell_count, float4* cell_pos, int* status, cudaStream_t st, int* wrapk,
-                       unsigned long long* facc, int* nbr_count) {
+                       unsigned long long* facc, int* nbr_count, const double* csrc, double* cdst, int cn) {
   const int tb = 64;  // small blocks spread the FP64 work of small systems over all SMs
   bin_kernel<<<(N + tb - 1) / tb, tb, 0, st>>>(N, pos, cg, wpos, phi, plo, cell_count, cell_pos, wrapk, status,
-                                               facc, nbr_count);
+                                               facc, nbr_count, csrc, cdst, cn);
   return cudaGetLastError();
 }
 

@@ -569,6 +569,12 @@ int pod_set_option(pod_handle* h, int option, int value) {
     h->adj_force = value;
     return POD_OK;
   }
+  if (option == POD_OPT_HOST_MAPPED) {
+    if (value != 0 && value != 1) return h->fail(POD_EINVAL, "host mapping must be 0 or 1");
+    h->host_mapped_off = value == 0;
+    h->drop_host_graph();
+    return POD_OK;
+  }
   if (option == POD_OPT_FIT_GRAPH) {
     if (value != 0 && value != 1) return h->fail(POD_EINVAL, "fit recording must be 0 or 1");
     h->fit_off = value == 0;
@@ -892,7 +898,9 @@ int pod_handle::build_neighbors(const double* pos, Plan& pl, bool need_rev, cuda
   last_ncells = pl.cg.ncells;
   if ((rc_ = ensure(wrapk, sizeof(int) * 3 * (size_t)N, "wrap offsets"))) return rc_;
   e = launch_bin(N, pos, pl.cg, (double*)wpos.p, (float4*)phi.p, (float4*)plo.p, (int*)cell_count.p,
-                 (float4*)cell_atoms.p, (int*)status.p, st, (int*)wrapk.p, facc_zero, (int*)nbr_count.p);
+                 (float4*)cell_atoms.p, (int*)status.p, st, (int*)wrapk.p, facc_zero, (int*)nbr_count.p, bin_csrc,
+                 bin_cdst, bin_cn);
+  if (bin_cn > 0) bin_cdone = true;
   if (e != cudaSuccess) return cuda_fail(e, "bin kernel");
   e = launch_neigh(N, pl.cg, (const double*)wpos.p, (const float4*)phi.p, (const float4*)plo.p,
                    (const int*)cell_count.p, (const float4*)cell_atoms.p, rlist(), pl.cap, (int*)nbr_count.p,
@@ -1406,15 +1414,30 @@ bool host_pinned(const void* p) {
   }
   return a.type == cudaMemoryTypeHost;
 }
+// The device address of pinned host memory (NULL stays NULL); false when p is
+// not pinned host memory mapped into the device's address space.
+bool mapped_ptr(const void* p, void** d) {
+  *d = nullptr;
+  if (!p) return true;
+  cudaPointerAttributes a{};
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  if (a.type != cudaMemoryTypeHost || !a.devicePointer) return false;
+  *d = a.devicePointer;
+  return true;
+}
 }  // namespace
 
 // Host-buffer energy and forces.  Copies in, one evaluation, copies out.  When
 // calls repeat with the same (pinned) buffers, size, box and settings on a
-// non-default stream, the second such call captures the copies, the step and a
-// read of the status word into a CUDA graph and later calls replay it (one
-// launch instead of one per kernel and copy); a status other than OK after a
-// replay drops the graph and re-runs the call on the direct path (capacity
-// retries, or the error).
+// non-default stream, the second such call captures the step and a read of the
+// status word into a CUDA graph (with the copies, or with the kernels reading
+// and writing the pinned buffers directly: the mapped form above) and later
+// calls replay it (one launch instead of one per kernel and copy); a status
+// other than OK after a replay drops the graph and re-runs the call on the
+// direct path (capacity retries, or the error).
 int pod_energy_forces_host(pod_handle* h, const pod_system* sys, const double* c, double* E, double* Ei, double* F,
                            double* W, void* stream) {
   NvtxRange nvtx_("pod_energy_forces_host");
@@ -1499,7 +1522,35 @@ int pod_energy_forces_host(pod_handle* h, const pod_system* sys, const double* c
     return POD_OK;
   }
   if (!h->h_status || !h->status.p) return POD_OK;
-  // capture: copies in, the asynchronous step, copies out, status word out and clear
+  // Mapped form (on Grace, pinned host memory is coherent with the GPU over
+  // NVLink-C2C): the step reads the positions and writes E, Ei, F and W through
+  // the pinned buffers' device addresses, and the bin kernel copies c, so the
+  // graph holds no copy but the status word's.  Otherwise copies in and out.
+  void *pos_d = nullptr, *c_d = nullptr, *E_d = nullptr, *Ei_d = nullptr, *F_d = nullptr, *W_d = nullptr;
+  const bool mapped = !h->host_mapped_off && (sys->n_local == 0 || sys->n_local == N) &&
+                      mapped_ptr(sys->pos, &pos_d) && mapped_ptr(c, &c_d) && mapped_ptr(E, &E_d) &&
+                      mapped_ptr(Ei, &Ei_d) && mapped_ptr(F, &F_d) && mapped_ptr(W, &W_d);
+  auto enqueue_mapped = [&]() -> int {
+    pod_system msys = *sys;
+    msys.pos = (const double*)pos_d;
+    h->bin_csrc = (const double*)c_d;
+    h->bin_cdst = (double*)h->c_in.p;
+    h->bin_cn = h->M;
+    h->bin_cdone = false;
+    const int keep_sync = h->sync;
+    h->sync = 0;
+    int r = h->energy_forces(&msys, (const double*)h->c_in.p, (double*)E_d, (double*)Ei_d, (double*)F_d,
+                             (double*)W_d, st);
+    h->sync = keep_sync;
+    const bool copied = h->bin_cdone;
+    h->bin_csrc = nullptr;
+    h->bin_cdst = nullptr;
+    h->bin_cn = 0;
+    h->bin_cdone = false;
+    if (r == POD_OK && !copied) r = POD_EINVAL;  // no bin kernel took the coefficients: not this form
+    return r;
+  };
+  // capture: (copies in,) the asynchronous step, (copies out,) status word out and clear
   h->drop_host_graph();
   cudaGraph_t g = nullptr;
   e = cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed);
@@ -1508,7 +1559,7 @@ int pod_energy_forces_host(pod_handle* h, const pod_system* sys, const double* c
     h->hgraph_off = true;
     return POD_OK;
   }
-  rc = enqueue_step(0);
+  rc = mapped ? enqueue_mapped() : enqueue_step(0);
   cudaError_t ec = cudaSuccess;
   if (rc == POD_OK) {
     ec = cudaMemcpyAsync(h->h_status, h->status.p, sizeof(int), cudaMemcpyDeviceToHost, st);

@@ -75,6 +75,12 @@ struct pod_handle {
   };
   HostKey hkey{}, hkey_prev{};
   bool hkey_valid = false, hgraph_off = false;
+  bool host_mapped_off = false;  // POD_OPT_HOST_MAPPED = 0: the graph copies in and out
+  // a copy that the next bin kernel performs (the mapped host graph's coefficients)
+  const double* bin_csrc = nullptr;
+  double* bin_cdst = nullptr;
+  int bin_cn = 0;
+  bool bin_cdone = false;
   cudaGraphExec_t hgraph = nullptr;
   void drop_host_graph();
   static int size_class(int N);

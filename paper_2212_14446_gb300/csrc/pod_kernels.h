@@ -100,7 +100,8 @@ inline T mask_radius(double r) {
 
 cudaError_t launch_bin(int N, const double* pos, const CellGrid& cg, double* wpos, float4* phi, float4* plo,
                        int* cell_count, float4* cell_pos, int* status, cudaStream_t st, int* wrapk = nullptr,
-                       unsigned long long* facc = nullptr, int* nbr_count = nullptr);
+                       unsigned long long* facc = nullptr, int* nbr_count = nullptr, const double* csrc = nullptr,
+                       double* cdst = nullptr, int cn = 0);
 cudaError_t launch_rewrap(int N, const double* pos, const int* wrapk, const double L[3], double* wpos, float4* phi,
                           float4* plo, int* status, cudaStream_t st, unsigned long long* facc = nullptr);
 cudaError_t launch_kick(int N3, double* v, const double* F, double half_dt_over_m, double* x, double dt,

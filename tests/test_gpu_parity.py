@@ -460,16 +460,19 @@ def test_fma_probe(pkg):
         pkg.pod_fma_probe(3, 1, s)
 
 
-@pytest.mark.parametrize("prec", ["fp64", "mixed"])
-def test_host_entry_graph_replay(pkg, prec):
+@pytest.mark.parametrize("prec,mapped", [("fp64", True), ("mixed", True), ("fp64", False), ("mixed", False)])
+def test_host_entry_graph_replay(pkg, prec, mapped):
     """Repeated host-buffer calls with the same pinned buffers on a stream replay a
     captured graph: every call (direct, capturing, replayed) equals the device
-    entry point bit for bit, including after the positions change in place."""
+    entry point bit for bit, including after the positions and the coefficients
+    change in place.  Both graph forms: kernels on the mapped pinned buffers, or
+    copies in and out."""
     import ctypes as C
     p = synth.params_full()
     cfg = synth.jitter(synth.bcc(4), 0.1, synth.rng(91))
     n = cfg.n
     pod = pkg.POD(p, precision=prec)
+    pod.set_host_mapped(mapped)
     c = synth.coefficients(pod.M, 92)
     s = torch.cuda.Stream()
     pos_t = torch.tensor(np.ascontiguousarray(cfg.pos.T)).pin_memory()
@@ -482,9 +485,12 @@ def test_host_entry_graph_replay(pkg, prec):
     sysd = pkg.make_system(pos_h.ctypes.data_as(C.POINTER(C.c_double)), n, cfg.box)
     rng = synth.rng(93)
     prepared = pkg.HostEnergyForces(pod.h, sysd, c_h, E_h, Ei_h, F_h, W_h, stream=s)
-    for call in range(6):
-        if call == 4:  # new positions in the same buffer: the replay must copy them in
+    for call in range(8):
+        if call == 4:  # new positions in the same buffer: the replay must take them
             pos_h[...] = np.ascontiguousarray((cfg.pos + rng.normal(0, 0.02, size=cfg.pos.shape)).T)
+        if call == 6:  # new coefficients in the same buffer
+            c = synth.coefficients(pod.M, 94)
+            c_h[...] = c
         if call % 2:  # the prepared repeated-call form, the same entry point
             prepared()
         else:
