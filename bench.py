@@ -18,7 +18,8 @@ pair; value = atoms * K / sum of the K step times, max over ranks.  The fused
 atom kernel is timed separately with CUDA events recorded by the library on the
 launching stream around that kernel (roofline).  ``e2e`` goes through the
 host-buffer entry point with pinned host memory (positions and coefficients in,
-energy, atom energies, forces and virial out, copies inside the timed region).
+energy, atom energies, forces and virial out, the transfers inside the timed
+region; the host rewrites the inputs before each call, outside it).
 
 Multi-GPU (torchrun): every rank evaluates its own independent configuration
 (weak scaling, no collective on the data path); rank 0 prints the JSON line.
@@ -472,14 +473,20 @@ def main():
     import ctypes as C
     hsys = pkg.make_system(pos_h.ctypes.data_as(C.POINTER(C.c_double)), N, box)
     call = pkg.HostEnergyForces(pod.h, hsys, c_h, Eh, Eih, Fh, Wh, stream=stream)  # the public repeated-call form
+    pos_src, c_src = pos_h.copy(), c_h.copy()
     for _ in range(3):
         call()
     if dist:
         dist.barrier()
-    te0 = time.perf_counter()
+    # the host writes its inputs before every call (as an MD driver would), outside
+    # the timed window: no call finds them already in a GPU cache
+    te = 0.0
     for k in range(args.steps):
+        pos_h[...] = pos_src
+        c_h[...] = c_src
+        te0 = time.perf_counter()
         call()
-    te = time.perf_counter() - te0
+        te += time.perf_counter() - te0
     if dist:
         t = torch.tensor([te], dtype=torch.float64, device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)

@@ -178,8 +178,14 @@ __global__ void __launch_bounds__(GATHER_MAX_WPB * 32, GATHER_MIN_BLOCKS)
 __global__ void __launch_bounds__(256)
     finalize_kernel(int N, const unsigned long long* __restrict__ facc, double* __restrict__ F, double fscale,
                     double* __restrict__ E_out, double* __restrict__ W_out, int* __restrict__ cell_count,
-                    int ncells) {
+                    int ncells, int* __restrict__ status, int* __restrict__ status_out) {
   const double sc = fscale * FIX_INV_SCALE;
+  // as the step's last kernel: hand the status word of this call (every earlier
+  // kernel has finished) to status_out and clear it for the next call
+  if (status_out && blockIdx.x == 0 && threadIdx.x == 0) {
+    status_out[0] = status[0];
+    status[0] = 0;
+  }
   if (cell_count)
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < ncells; c += gridDim.x * blockDim.x) cell_count[c] = 0;
   if (blockIdx.x == 0) {  // warp w sums quantities w, w + 8 (0: E, 1..9: W)
@@ -219,8 +225,9 @@ int finalize_blocks(int N) {
 }
 
 cudaError_t launch_finalize(int N, const unsigned long long* facc, double* F, double fscale, int nblocks, double* E,
-                            double* W, cudaStream_t st, int* cell_count, int ncells) {
-  finalize_kernel<<<nblocks, FINALIZE_THREADS, 0, st>>>(N, facc, F, fscale, E, W, cell_count, ncells);
+                            double* W, cudaStream_t st, int* cell_count, int ncells, int* status, int* status_out) {
+  finalize_kernel<<<nblocks, FINALIZE_THREADS, 0, st>>>(N, facc, F, fscale, E, W, cell_count, ncells, status,
+                                                        status_out);
   return cudaGetLastError();
 }
 

@@ -1202,14 +1202,18 @@ int pod_handle::energy_forces(const pod_system* sys, const double* c, double* E,
     if ((rc_ = mark(2, st))) return rc_;
     cudaError_t e;
     const bool clear_in_finalize = fixp && !pl.batched && cell_count.p && !reuse;
-    if (fixp)
+    if (fixp) {
+      // the finalize is this step's last kernel when it clears the cell counts
+      int* sout = (clear_in_finalize && fin_status_out) ? fin_status_out : nullptr;
       e = launch_finalize(N, fa, F, 1.0, nblk, E, W, st, clear_in_finalize ? (int*)cell_count.p : nullptr,
-                          pl.cg.ncells);
-    else
+                          pl.cg.ncells, (int*)status.p, sout);
+      if (sout) fin_status_done = true;
+    } else {
       e = launch_gather_reduce<double>(N, n_eval, pl.cap, (const int*)nbr_count.p, (const int*)nbr_j.p,
                                        (const int*)nbr_s.p, rev_in, rev_out, (const Q4<double>*)g.p, Ei_dst,
                                        (const double*)wpart.p, nwarp, F, 1.0, (double*)Wat.p, nblk,
                                        (unsigned*)offs.p, E, W, (int*)status.p, st, pl.shape.gather_wpb);
+    }
     if (e != cudaSuccess) return cuda_fail(e, "gather kernel");
     if (clear_in_finalize)
       cells_clean = pl.cg.ncells;
@@ -1526,10 +1530,14 @@ int pod_energy_forces_host(pod_handle* h, const pod_system* sys, const double* c
   // NVLink-C2C): the step reads the positions and writes E, Ei, F and W through
   // the pinned buffers' device addresses, and the bin kernel copies c, so the
   // graph holds no copy but the status word's.  Otherwise copies in and out.
+  // The mixed path's finalize also hands over the status word (no copy node).
   void *pos_d = nullptr, *c_d = nullptr, *E_d = nullptr, *Ei_d = nullptr, *F_d = nullptr, *W_d = nullptr;
+  void* hs_d = nullptr;
   const bool mapped = !h->host_mapped_off && (sys->n_local == 0 || sys->n_local == N) &&
                       mapped_ptr(sys->pos, &pos_d) && mapped_ptr(c, &c_d) && mapped_ptr(E, &E_d) &&
-                      mapped_ptr(Ei, &Ei_d) && mapped_ptr(F, &F_d) && mapped_ptr(W, &W_d);
+                      mapped_ptr(Ei, &Ei_d) && mapped_ptr(F, &F_d) && mapped_ptr(W, &W_d) &&
+                      mapped_ptr(h->h_status, &hs_d);
+  bool status_by_finalize = false;
   auto enqueue_mapped = [&]() -> int {
     pod_system msys = *sys;
     msys.pos = (const double*)pos_d;
@@ -1537,16 +1545,21 @@ int pod_energy_forces_host(pod_handle* h, const pod_system* sys, const double* c
     h->bin_cdst = (double*)h->c_in.p;
     h->bin_cn = h->M;
     h->bin_cdone = false;
+    h->fin_status_out = (int*)hs_d;
+    h->fin_status_done = false;
     const int keep_sync = h->sync;
     h->sync = 0;
     int r = h->energy_forces(&msys, (const double*)h->c_in.p, (double*)E_d, (double*)Ei_d, (double*)F_d,
                              (double*)W_d, st);
     h->sync = keep_sync;
     const bool copied = h->bin_cdone;
+    status_by_finalize = h->fin_status_done;
     h->bin_csrc = nullptr;
     h->bin_cdst = nullptr;
     h->bin_cn = 0;
     h->bin_cdone = false;
+    h->fin_status_out = nullptr;
+    h->fin_status_done = false;
     if (r == POD_OK && !copied) r = POD_EINVAL;  // no bin kernel took the coefficients: not this form
     return r;
   };
@@ -1561,7 +1574,7 @@ int pod_energy_forces_host(pod_handle* h, const pod_system* sys, const double* c
   }
   rc = mapped ? enqueue_mapped() : enqueue_step(0);
   cudaError_t ec = cudaSuccess;
-  if (rc == POD_OK) {
+  if (rc == POD_OK && !status_by_finalize) {
     ec = cudaMemcpyAsync(h->h_status, h->status.p, sizeof(int), cudaMemcpyDeviceToHost, st);
     if (ec == cudaSuccess) ec = cudaMemsetAsync(h->status.p, 0, sizeof(int), st);
   }

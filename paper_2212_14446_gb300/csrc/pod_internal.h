@@ -81,6 +81,9 @@ struct pod_handle {
   double* bin_cdst = nullptr;
   int bin_cn = 0;
   bool bin_cdone = false;
+  // where the next finalize hands the status word (the mapped host graph's)
+  int* fin_status_out = nullptr;
+  bool fin_status_done = false;
   cudaGraphExec_t hgraph = nullptr;
   void drop_host_graph();
   static int size_class(int N);

@@ -165,6 +165,7 @@ cudaError_t launch_tsqr_merge(int M, int nin, int g, const double* in, int cmax,
 int gather_blocks(int N, int wpb, int bps);
 int finalize_blocks(int N);
 cudaError_t launch_finalize(int N, const unsigned long long* facc, double* F, double fscale, int nblocks, double* E,
-                            double* W, cudaStream_t st, int* cell_count = nullptr, int ncells = 0);
+                            double* W, cudaStream_t st, int* cell_count = nullptr, int ncells = 0,
+                            int* status = nullptr, int* status_out = nullptr);
 
 }  // namespace fastpod

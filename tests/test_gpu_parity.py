@@ -502,6 +502,58 @@ def test_host_entry_graph_replay(pkg, prec, mapped):
         assert np.array_equal(W_h, dev["W"].cpu().numpy().ravel()), call
 
 
+@pytest.mark.parametrize("mapped", [True, False])
+def test_host_graph_replay_redoes_an_overflowing_call(pkg, mapped):
+    """A replayed host-buffer call whose cell and neighbour lists overflow (the
+    positions changed in place into a dense cluster) reports it through the status
+    word the graph hands back, drops the graph and redoes the call on the direct
+    path with larger capacities: every call equals the device entry point."""
+    import ctypes as C
+    p = synth.params_full()
+    cfg = synth.jitter(synth.bcc(4), 0.05, synth.rng(95))  # 128 atoms, 2 x 2 x 2 cells
+    n, L = cfg.n, cfg.box
+    pod = pkg.POD(p, precision="mixed")
+    pod.set_host_mapped(mapped)
+    c = synth.coefficients(pod.M, 96)
+    s = torch.cuda.Stream()
+    pos_t = torch.tensor(np.ascontiguousarray(cfg.pos.T)).pin_memory()
+    c_t = torch.tensor(c).pin_memory()
+    E_t = torch.zeros(1, dtype=torch.float64).pin_memory()
+    F_t = torch.zeros((3, n), dtype=torch.float64).pin_memory()
+    W_t = torch.zeros(9, dtype=torch.float64).pin_memory()
+    pos_h, c_h, E_h, F_h, W_h = (t.numpy() for t in (pos_t, c_t, E_t, F_t, W_t))
+    sysd = pkg.make_system(pos_h.ctypes.data_as(C.POINTER(C.c_double)), n, L)
+    call = pkg.HostEnergyForces(pod.h, sysd, c_h, E_h, None, F_h, W_h, stream=s)
+    # atoms 0..59 moved into one 6 A cube (one cell), at least 1.2 A (> r_in) from
+    # every other atom and periodic image
+    g = synth.rng(97)
+    dense = cfg.pos.copy()
+    placed = [q for q in dense[60:]]
+    for i in range(60):
+        while True:
+            q = g.uniform(0.3, 6.3, size=3)
+            d = np.asarray(placed) - q
+            d -= L * np.round(d / L)
+            if np.min(np.linalg.norm(d, axis=1)) > 1.2:
+                break
+        dense[i] = q
+        placed.append(q)
+
+    def check(x, tag):
+        dev = pod.energy_forces(torch.tensor(np.ascontiguousarray(x.T), device=DEV), L, torch.tensor(c, device=DEV))
+        assert E_h[0] == dev["E"].item(), tag
+        assert np.array_equal(F_h.T, dev["F"].cpu().numpy()), tag
+        assert np.array_equal(W_h, dev["W"].cpu().numpy().ravel()), tag
+
+    for k in range(3):  # direct, capturing, replayed
+        call()
+        check(cfg.pos, k)
+    pos_h[...] = np.ascontiguousarray(dense.T)
+    for k in range(3, 7):  # the replay overflows and is redone; then direct, capture, replay
+        call()
+        check(dense, k)
+
+
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
 def test_model_file_evaluates_like_the_saved_handle(pkg, full, prec, tmp_path):
     """A handle loaded from a model file (parameters, Q, c) gives the saved
