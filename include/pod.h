@@ -317,7 +317,9 @@ int pod_model_gradients(pod_handle* h, int n_atoms, const double* D, const doubl
  * under unified addressing), that graph's kernels read the positions and
  * coefficients and write E, Ei, F and W through the buffers' device addresses
  * instead of copying them (same bits).  The buffers must hold the documented
- * sizes either way. */
+ * sizes either way, and buffers passed again at the same addresses must still
+ * be allocated and pinned: a replay reads and writes them without re-checking
+ * (a call with other pointers takes the direct path and records anew). */
 int pod_energy_forces_host(pod_handle* h, const pod_system* sys, const double* c, double* E, double* Ei,
                            double* F, double* W, void* stream);
 
