@@ -20,6 +20,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <type_traits>
 #include <vector>
 
 #include "pod_internal.h"
@@ -300,6 +301,61 @@ __global__ void __launch_bounds__(256)
   const int n = min(nbr_count[k], cap);
   const int per = Qc * K * 3;
   const size_t plane = (size_t)N * cap * K * 3;
+  if ((K & 1) == 0) {
+    // an even row of K x 3 values: lane v takes two adjacent values of one row (one
+    // 8- or 16-byte load per slot), each summed in slot order as below
+    using V2 = typename std::conditional<std::is_same<T, float>::value, float2, double2>::type;
+    const int row2 = (K * 3) >> 1;
+    for (int v = lane; v < (per >> 1); v += 32) {
+      const int ql = v / row2, rem = 2 * (v - ql * row2);
+      const V2* base = reinterpret_cast<const V2*>(gdm + ql * plane + rem);
+      T sx = T(0), sy = T(0);
+      bool broken = false;
+      int t = 0;
+      for (; t + DG_UNROLL <= n; t += DG_UNROLL) {
+        const size_t p0 = (size_t)k * cap + t;
+        int q[DG_UNROLL];
+        V2 own[DG_UNROLL], oth[DG_UNROLL];
+#pragma unroll
+        for (int j = 0; j < DG_UNROLL; ++j) q[j] = rev[p0 + j];
+#pragma unroll
+        for (int j = 0; j < DG_UNROLL; ++j) {
+          own[j] = base[(p0 + j) * row2];
+          oth[j] = q[j] >= 0 ? base[(size_t)q[j] * row2] : V2{T(0), T(0)};
+          broken |= q[j] < 0;
+        }
+#pragma unroll
+        for (int j = 0; j < DG_UNROLL; ++j) {
+          sx += own[j].x;
+          sx -= oth[j].x;
+          sy += own[j].y;
+          sy -= oth[j].y;
+        }
+      }
+      for (; t < n; ++t) {
+        const size_t pidx = (size_t)k * cap + t;
+        const int q = rev[pidx];
+        const V2 a = base[pidx * row2];
+        sx += a.x;
+        sy += a.y;
+        if (q >= 0) {
+          const V2 b = base[(size_t)q * row2];
+          sx -= b.x;
+          sy -= b.y;
+        } else {
+          broken = true;
+        }
+      }
+      if (broken) atomicOr(status, ST_REV);
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int r = rem + h, m = r / 3, comp = r - 3 * m;
+        const int col = design_column(q0 + ql, m, K2, K3, P3, K4, KA4, col3, col4);
+        if (col >= 0) AT[(size_t)col * R + nc + (size_t)comp * N + k] = wF * (double)(h ? sy : sx);
+      }
+    }
+    return;
+  }
   for (int v = lane; v < per; v += 32) {
     const int ql = v / (K * 3), rem = v - ql * (K * 3);
     const T* base = gdm + ql * plane + rem;
