@@ -76,42 +76,67 @@ __global__ void __launch_bounds__(WPB_NEIGH * 32)
   const int wx = smax[0] - smin[0] + 1, wy = smax[1] - smin[1] + 1, wz = smax[2] - smin[2] + 1;
   const int nimg = wx * wy * wz;
   const int nat = b.a1 - b.a0;
-  const long long total = (long long)nimg * nat;
+  const int total = nimg * nat;
   const int zero = shift_pack(0, 0, 0);
   int nhit = 0;
-  for (long long f0 = 0; f0 < total; f0 += 32) {
-    const long long f = f0 + lane;
+  // candidate j under image (sx, sy, sz): the FP32 prefilter, the exact FP64 band
+  // decision, and its key
+  auto test = [&](int j, int sx, int sy, int sz, int code, unsigned long long& key) {
+    if (j == i && code == zero) return false;
+    const float4 hj = phi[j];
+    const float dx = (hj.x + (float)sx * Lh[0]) - hi.x;
+    const float dy = (hj.y + (float)sy * Lh[1]) - hi.y;
+    const float dz = (hj.z + (float)sz * Lh[2]) - hi.z;
+    const float r2f = dx * dx + dy * dy + dz * dz;
     bool hit = false;
-    unsigned long long key = 0;
-    if (f < total) {
-      const int img = (int)(f / nat);
-      const int j = b.a0 + (int)(f - (long long)img * nat);
-      const int sx = img % wx + smin[0], sy = (img / wx) % wy + smin[1], sz = img / (wx * wy) + smin[2];
-      const int code = shift_pack(sx, sy, sz);
-      if (!(j == i && code == zero)) {
-        const float4 hj = phi[j];
-        const float dx = (hj.x + (float)sx * Lh[0]) - hi.x;
-        const float dy = (hj.y + (float)sy * Lh[1]) - hi.y;
-        const float dz = (hj.z + (float)sz * Lh[2]) - hi.z;
-        const float r2f = dx * dx + dy * dy + dz * dz;
-        if (r2f < rc2_lo) {
-          hit = true;
-        } else if (r2f < rc2_hi) {
-          const double ddx = disp_fp64(wpos[i], wpos[j], sx, b.L[0]);
-          const double ddy = disp_fp64(wpos[(size_t)N + i], wpos[(size_t)N + j], sy, b.L[1]);
-          const double ddz = disp_fp64(wpos[(size_t)2 * N + i], wpos[(size_t)2 * N + j], sz, b.L[2]);
-          const double r2 = __dadd_rn(__dadd_rn(__dmul_rn(ddx, ddx), __dmul_rn(ddy, ddy)), __dmul_rn(ddz, ddz));
-          hit = r2 < rc2;
-        }
-        key = ((unsigned long long)j << 24) | (unsigned long long)code;
-      }
+    if (r2f < rc2_lo) {
+      hit = true;
+    } else if (r2f < rc2_hi) {
+      const double ddx = disp_fp64(wpos[i], wpos[j], sx, b.L[0]);
+      const double ddy = disp_fp64(wpos[(size_t)N + i], wpos[(size_t)N + j], sy, b.L[1]);
+      const double ddz = disp_fp64(wpos[(size_t)2 * N + i], wpos[(size_t)2 * N + j], sz, b.L[2]);
+      const double r2 = __dadd_rn(__dadd_rn(__dmul_rn(ddx, ddx), __dmul_rn(ddy, ddy)), __dmul_rn(ddz, ddz));
+      hit = r2 < rc2;
     }
+    key = ((unsigned long long)j << 24) | (unsigned long long)code;
+    return hit;
+  };
+  // hits are appended in candidate order (image-major, then atom) either way
+  auto append = [&](bool hit, unsigned long long key) {
     const unsigned m = __ballot_sync(0xffffffffu, hit);
     if (hit) {
       const int pos = nhit + __popc(m & ((1u << lane) - 1u));
       if (pos < keycap) keys[pos] = key;
     }
     nhit += __popc(m);
+  };
+  if (nat >= 32) {
+    // image by image, lanes over the configuration's atoms: no division per candidate
+    for (int img = 0; img < nimg; ++img) {
+      const int sx = img % wx + smin[0], sy = (img / wx) % wy + smin[1], sz = img / (wx * wy) + smin[2];
+      const int code = shift_pack(sx, sy, sz);
+      for (int j0 = 0; j0 < nat; j0 += 32) {
+        unsigned long long key = 0;
+        const bool hit = j0 + lane < nat && test(b.a0 + j0 + lane, sx, sy, sz, code, key);
+        append(hit, key);
+      }
+    }
+  } else {
+    // small configurations: 32 consecutive (image, atom) candidates per round;
+    // 32-bit indices (a 64-bit division per candidate runs on the FP64 pipe, 1/64
+    // of the FP32 rate on this part; a batch whose count does not fit is refused
+    // on the host)
+    for (int f0 = 0; f0 < total; f0 += 32) {
+      const int f = f0 + lane;
+      unsigned long long key = 0;
+      bool hit = false;
+      if (f < total) {
+        const int img = f / nat;
+        const int sx = img % wx + smin[0], sy = (img / wx) % wy + smin[1], sz = img / (wx * wy) + smin[2];
+        hit = test(b.a0 + (f - img * nat), sx, sy, sz, shift_pack(sx, sy, sz), key);
+      }
+      append(hit, key);
+    }
   }
   __syncwarp();
   const int n = min(nhit, keycap);

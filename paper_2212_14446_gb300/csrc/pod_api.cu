@@ -827,6 +827,11 @@ int pod_handle::plan_batch(const pod_system* sys, Plan& pl) {
       pl.Lmax = std::max(pl.Lmax, L);
       vol *= std::max(L, rc);
     }
+    // the batch search indexes an atom's candidates (images x atoms) with 32-bit ints
+    const long long ncand =
+        (long long)(2 * b.S[0] + 1) * (2 * b.S[1] + 1) * (2 * b.S[2] + 1) * (long long)(b.a1 - b.a0);
+    if (ncand > (1LL << 31) - 64)
+      return fail(POD_EINVAL, "configuration %d: %lld periodic-image candidates per atom, more than 2^31", c, ncand);
     for (int i = b.a0; i < b.a1; ++i) h_cfg_of[i] = c;
     max_expect = std::max(max_expect, (b.a1 - b.a0) / vol * (4.0 / 3.0) * M_PI * rc * rc * rc);
   }
