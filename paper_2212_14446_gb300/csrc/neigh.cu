@@ -572,7 +572,8 @@ __global__ void rev_kernel(int N, int cap, const int* __restrict__ nbr_count, co
   if (p >= (size_t)N * cap) return;
   const int j = nbr_j[p];
   if (j >= N) return;  // sentinel slot
-  const int i = (int)(p / cap);
+  // a 32-bit division where the slot index fits (a 64-bit one runs on the FP64 pipe)
+  const int i = p < 0x80000000ull ? (int)((unsigned)p / (unsigned)cap) : (int)(p / cap);
   const int q = find_reverse(nbr_j, nbr_s, cap, i, j, nbr_s[p]);
   if (q < 0) atomicOr(status, ST_REV);
   rev[p] = q;  // -1: the gather skips it (and the status reports the broken list)
@@ -585,7 +586,8 @@ __global__ void export_neighbors_kernel(int N, int cap, const int* __restrict__ 
                                         int* __restrict__ s_out) {
   const size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= (size_t)N * cap_out) return;
-  const int i = (int)(p / cap_out), t = (int)(p % cap_out);
+  const int i = p < 0x80000000ull ? (int)((unsigned)p / (unsigned)cap_out) : (int)(p / cap_out);
+  const int t = (int)(p - (size_t)i * cap_out);
   const int n = nbr_count[i];
   if (t == 0) count_out[i] = n;
   if (t >= min(n, cap)) return;
