@@ -145,6 +145,25 @@ def test_fit_singular_reports_error(pkg):
     assert ei.value.code == pkg.POD_ESINGULAR
 
 
+def test_batch_with_too_many_image_candidates_is_refused(pkg):
+    """The batch neighbour search indexes an atom's (image, atom) candidates with
+    32-bit integers; a configuration whose count can exceed that (1,300 atoms in a
+    periodic box of 0.084 A: 121^3 images each) is refused while the batch is
+    planned, before any kernel runs."""
+    p = synth.params_full()
+    pod = pkg.POD(p, precision="mixed")
+    g = synth.rng(41)
+    L = np.array([0.084, 0.084, 0.084])
+    tiny = synth.Config(pos=g.uniform(0.0, 0.084, size=(1300, 3)), box=L, pbc=(1, 1, 1))
+    ok = synth.config_train(0)
+    with pytest.raises(pkg.PodError) as ei:
+        pod.descriptors_batch([ok, tiny])
+    assert ei.value.code == pkg.POD_EINVAL
+    assert "candidates" in str(ei.value)
+    D = pod.descriptors_batch([ok])  # the handle stays usable
+    assert torch.isfinite(D).all()
+
+
 def test_fit_stages_equal_single_call(pkg):
     """pod_fit_normal + pod_fit_solve + pod_fit_residual (the sharded-fit
     building blocks) reproduce pod_fit bit for bit on one GPU."""
