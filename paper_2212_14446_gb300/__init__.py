@@ -34,6 +34,7 @@ POD_OPT_ADJOINT = 8
 POD_OPT_NEIGHBOR_TESTS = 9
 POD_OPT_FIT_GRAPH = 10
 POD_OPT_HOST_MAPPED = 11
+POD_EMB_MAX_DEGREE = 8
 ERROR_NAMES = {0: "POD_OK", -1: "POD_EINVAL", -2: "POD_ENOMEM", -3: "POD_ECUDA", -4: "POD_ERANGE",
                -5: "POD_ENONFINITE", -6: "POD_ESINGULAR", -7: "POD_ENEIGH", -8: "POD_EIO"}
 

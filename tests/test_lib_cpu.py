@@ -37,6 +37,17 @@ def test_exports_every_declared_symbol(pkg):
     assert sorted(pkg.EXPORTS) == syms
 
 
+def test_binding_constants_match_header(pkg):
+    """Every #define POD_* integer of include/pod.h has the same value in the binding."""
+    with open(os.path.join(ROOT, "include", "pod.h")) as f:
+        text = f.read()
+    defs = re.findall(r"^#define (POD_\w+) \(?(-?\d+)\)?", text, re.M)
+    assert len(defs) >= 20
+    for name, val in defs:
+        assert hasattr(pkg, name), name
+        assert getattr(pkg, name) == int(val), name
+
+
 def test_library_links_no_oracle(pkg):
     # the product library must not contain or reference any oracle symbol
     with open(pkg.LIB_PATH, "rb") as f:
