@@ -502,6 +502,34 @@ def test_host_entry_graph_replay(pkg, prec, mapped):
         assert np.array_equal(W_h, dev["W"].cpu().numpy().ravel()), call
 
 
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_host_graph_replay_without_optional_outputs(pkg, prec):
+    """Host-buffer replays with E_i and W left NULL (E and F only): the mapped graph
+    writes just those, and every call equals the device entry point."""
+    import ctypes as C
+    p = synth.params_full()
+    cfg = synth.jitter(synth.bcc(5), 0.08, synth.rng(98))
+    n = cfg.n
+    pod = pkg.POD(p, precision=prec)
+    c = synth.coefficients(pod.M, 99)
+    s = torch.cuda.Stream()
+    pos_t = torch.tensor(np.ascontiguousarray(cfg.pos.T)).pin_memory()
+    c_t = torch.tensor(c).pin_memory()
+    E_t = torch.zeros(1, dtype=torch.float64).pin_memory()
+    F_t = torch.zeros((3, n), dtype=torch.float64).pin_memory()
+    pos_h, c_h, E_h, F_h = (t.numpy() for t in (pos_t, c_t, E_t, F_t))
+    sysd = pkg.make_system(pos_h.ctypes.data_as(C.POINTER(C.c_double)), n, cfg.box)
+    call = pkg.HostEnergyForces(pod.h, sysd, c_h, E_h, None, F_h, None, stream=s)
+    rng = synth.rng(100)
+    for k in range(5):
+        if k == 3:
+            pos_h[...] = np.ascontiguousarray((cfg.pos + rng.normal(0, 0.02, size=cfg.pos.shape)).T)
+        call()
+        dev = pod.energy_forces(torch.tensor(pos_h, device=DEV), cfg.box, torch.tensor(c, device=DEV))
+        assert E_h[0] == dev["E"].item(), k
+        assert np.array_equal(F_h.T, dev["F"].cpu().numpy()), k
+
+
 @pytest.mark.parametrize("mapped", [True, False])
 def test_host_graph_replay_redoes_an_overflowing_call(pkg, mapped):
     """A replayed host-buffer call whose cell and neighbour lists overflow (the
