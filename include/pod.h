@@ -203,6 +203,12 @@ int pod_info(const pod_handle* h, int* M, int* Ns, int* K, double* Q_out, double
                                   and write mapped pinned host buffers directly (on Grace,
                                   coherent over NVLink-C2C); 0 copy nodes into and out of
                                   library-owned device buffers.  Results are the same bits */
+#define POD_OPT_WORKSPACE_LIMIT_MB 12 /* a cap, in MiB, on the device workspace this handle
+                                         allocates (0, the default: none).  A call whose
+                                         buffers would grow past it returns POD_ENOMEM before
+                                         freeing or allocating anything, and the handle stays
+                                         usable (raise or clear the cap and call again); a cap
+                                         below what is already held frees nothing */
 int pod_set_option(pod_handle* h, int option, int value);
 
 /* Neighbour-list skin (A, default 0): lists are built with r_cut + skin and pairs

@@ -34,6 +34,7 @@ POD_OPT_ADJOINT = 8
 POD_OPT_NEIGHBOR_TESTS = 9
 POD_OPT_FIT_GRAPH = 10
 POD_OPT_HOST_MAPPED = 11
+POD_OPT_WORKSPACE_LIMIT_MB = 12
 POD_EMB_MAX_DEGREE = 8
 ERROR_NAMES = {0: "POD_OK", -1: "POD_EINVAL", -2: "POD_ENOMEM", -3: "POD_ECUDA", -4: "POD_ERANGE",
                -5: "POD_ENONFINITE", -6: "POD_ESINGULAR", -7: "POD_ENEIGH", -8: "POD_EIO"}
@@ -475,6 +476,11 @@ class POD:
         returns {"atom_wpb", "design_wpb", "ms"}."""
         shape, ms = pod_autotune(self.h, self.batch_system(pos_soa, offs, boxes, pbcs), None, reps, stream)
         return {"atom_wpb": shape[1], "design_wpb": shape[2], "ms": ms[1]}
+
+    def set_workspace_limit_mb(self, mb: int):
+        """Cap the handle's device workspace at mb MiB (0: no cap); growth past it
+        raises PodError(POD_ENOMEM)."""
+        pod_set_option(self.h, POD_OPT_WORKSPACE_LIMIT_MB, int(mb))
 
     def set_host_mapped(self, on: bool):
         """pod_energy_forces_host graph replays: kernels read and write mapped pinned

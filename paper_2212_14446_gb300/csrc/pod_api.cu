@@ -197,14 +197,23 @@ int pod_handle::cuda_fail(cudaError_t e, const char* what) {
 
 int pod_handle::ensure(DevBuf& b, size_t bytes, const char* what) {
   if (bytes <= b.bytes && b.p) return POD_OK;
+  size_t nb = std::max<size_t>(bytes, 256);
+  nb = nb + nb / 4;
+  if (ws_limit) {  // POD_OPT_WORKSPACE_LIMIT_MB: refuse growth past the cap, before freeing anything
+    size_t others = 0;
+    for (DevBuf* o : all_bufs())
+      if (o != &b) others += o->bytes;
+    if (others + nb > ws_limit) nb = std::max<size_t>(bytes, 256);  // without the growth margin
+    if (others + nb > ws_limit)
+      return fail(POD_ENOMEM, "%s: %zu bytes would take the workspace to %zu, above its limit of %zu", what, nb,
+                  others + nb, ws_limit);
+  }
   if (b.p) {
     drop_host_graph();  // a captured host graph may hold this buffer's address
     cudaFree(b.p);
     b.p = nullptr;
     b.bytes = 0;
   }
-  size_t nb = std::max<size_t>(bytes, 256);
-  nb = nb + nb / 4;
   cudaError_t e = cudaMalloc(&b.p, nb);
   if (e != cudaSuccess) {
     b.p = nullptr;
@@ -567,6 +576,11 @@ int pod_set_option(pod_handle* h, int option, int value) {
   if (option == POD_OPT_ADJOINT) {
     if (value < -1 || value > 1) return h->fail(POD_EINVAL, "adjoint kernel must be -1 (by shape), 0 or 1");
     h->adj_force = value;
+    return POD_OK;
+  }
+  if (option == POD_OPT_WORKSPACE_LIMIT_MB) {
+    if (value < 0) return h->fail(POD_EINVAL, "workspace limit must be >= 0 MiB (0: none)");
+    h->ws_limit = (size_t)value << 20;
     return POD_OK;
   }
   if (option == POD_OPT_HOST_MAPPED) {

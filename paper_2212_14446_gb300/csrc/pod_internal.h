@@ -76,6 +76,7 @@ struct pod_handle {
   HostKey hkey{}, hkey_prev{};
   bool hkey_valid = false, hgraph_off = false;
   bool host_mapped_off = false;  // POD_OPT_HOST_MAPPED = 0: the graph copies in and out
+  size_t ws_limit = 0;           // POD_OPT_WORKSPACE_LIMIT_MB in bytes (0: no limit)
   // a copy that the next bin kernel performs (the mapped host graph's coefficients)
   const double* bin_csrc = nullptr;
   double* bin_cdst = nullptr;

@@ -380,6 +380,27 @@ def test_error_codes(pkg):
     pod.energy_forces(soa(ok), ok.box, c)
 
 
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_workspace_limit_reports_enomem(pkg, full, prec):
+    """An allocation failure injected on the host: with a 1 MiB workspace cap the
+    8,192-atom call cannot grow its buffers and returns POD_ENOMEM (nothing is
+    freed or allocated past the cap, no kernel faults); with the cap cleared the
+    same handle gives the bits of a fresh one."""
+    p, o, cfg, c = full
+    ct = torch.tensor(c, device=DEV)
+    pod = pkg.POD(p, precision=prec)
+    pod.set_workspace_limit_mb(1)
+    with pytest.raises(pkg.PodError) as ei:
+        pod.energy_forces(soa(cfg), cfg.box, ct)
+    assert ei.value.code == pkg.POD_ENOMEM
+    assert "limit" in str(ei.value)
+    pod.set_workspace_limit_mb(0)
+    a = pod.energy_forces(soa(cfg), cfg.box, ct)
+    b = pkg.POD(p, precision=prec).energy_forces(soa(cfg), cfg.box, ct)
+    for k in ("E", "F", "W"):
+        assert torch.equal(a[k], b[k]), k
+
+
 def test_bounded_wait_reports_timeout(pkg):
     """The bounded mbarrier wait of the tensor-core kernels, on a barrier that
     nothing arrives at: it gives up after its limit (50 ms here), reports

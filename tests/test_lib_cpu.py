@@ -48,6 +48,16 @@ def test_binding_constants_match_header(pkg):
         assert getattr(pkg, name) == int(val), name
 
 
+def test_workspace_limit_option(pkg):
+    """POD_OPT_WORKSPACE_LIMIT_MB takes a cap >= 0 (0: none); a negative one is refused."""
+    pod = pkg.POD(synth.params_small())
+    pod.set_workspace_limit_mb(16)
+    pod.set_workspace_limit_mb(0)
+    with pytest.raises(pkg.PodError) as ei:
+        pod.set_workspace_limit_mb(-1)
+    assert ei.value.code == pkg.POD_EINVAL
+
+
 def test_library_links_no_oracle(pkg):
     # the product library must not contain or reference any oracle symbol
     with open(pkg.LIB_PATH, "rb") as f:
